@@ -1,0 +1,114 @@
+"""Seeded synthetic inputs: planted trend-bicluster matrices and random populations.
+
+This module holds none of the method's arithmetic: it only draws inputs.  The tests, the smoke
+check and the benchmark use it for both the CUDA path and the CPU oracle, which then share the
+same inputs and nothing else.
+
+Recipe (stands in for the paper's Unibic / RecBic collections, Sec. 2.1, which are not shipped):
+  * background N(0, 1) float32 (or log-normal(0, 1) rounded to 0.1 for the tie-heavy workload);
+  * each planted bicluster takes rows and columns without replacement; its column order is a
+    random permutation; a planted row gets s ~ N(0, 1) at the first column of the order and adds
+    an increment ~ U(0.5, 1.5) at each next column, plus N(0, 0.1) noise per entry; a negative
+    bicluster stores the values along the reversed order; later biclusters overwrite earlier ones;
+  * a population has lengths uniform in [len_lo, len_hi] and distinct columns drawn uniformly.
+Generators are numpy ``Generator(Philox(seed))``.
+"""
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 20210710
+
+
+@dataclass
+class Workload:
+    name: str
+    rows: int
+    cols: int
+    n_bic: int
+    bic_rows: tuple
+    bic_cols: tuple
+    pop: int
+    len_lo: int
+    len_hi: int
+    ratio: tuple          # (num, den)
+    neg_trends: int
+    generations: int
+    background: str = "normal"
+    round_to: float = 0.0
+    neg_fraction: float = 0.5
+    seed: int = SEED_BASE
+    extra: dict = field(default_factory=dict)
+
+
+# The five workload shapes of the evaluation: tiny, default scale, batched, tie-heavy, serving.
+WORKLOADS = {
+    "tiny": Workload("tiny", 200, 20, 2, (30, 30), (5, 5), 64, 2, 6, (1, 1), 0, 1,
+                     neg_fraction=0.0, seed=SEED_BASE + 0),
+    "default": Workload("default", 10_000, 100, 5, (100, 500), (5, 20), 800, 2, 20, (85, 100), 1,
+                        100, seed=SEED_BASE + 1),
+    "batched": Workload("batched", 20_000, 500, 10, (50, 2000), (5, 40), 4096, 2, 64, (85, 100),
+                        1, 200, seed=SEED_BASE + 2),
+    "tieheavy": Workload("tieheavy", 60_000, 1000, 20, (100, 5000), (5, 50), 8192, 2, 64,
+                         (85, 100), 1, 100, background="lognormal", round_to=0.1,
+                         seed=SEED_BASE + 3),
+}
+
+
+def rng(seed):
+    return np.random.Generator(np.random.Philox(int(seed)))
+
+
+def planted_matrix(rows, cols, n_bic, bic_rows, bic_cols, seed, background="normal",
+                   round_to=0.0, neg_fraction=0.5, noise=0.1):
+    """Returns (x float32 [rows, cols] row-major, truth list of (row_idx, col_order, sign))."""
+    g = rng(seed)
+    if background == "normal":
+        x = g.standard_normal((rows, cols), dtype=np.float32)
+    elif background == "lognormal":
+        x = g.lognormal(0.0, 1.0, size=(rows, cols)).astype(np.float32)
+    else:
+        raise ValueError(background)
+    truth = []
+    n_neg = int(round(n_bic * neg_fraction))
+    for b in range(n_bic):
+        nr = int(g.integers(bic_rows[0], bic_rows[1] + 1))
+        nc = int(g.integers(bic_cols[0], bic_cols[1] + 1))
+        nr, nc = min(nr, rows), min(nc, cols)
+        ridx = np.sort(g.choice(rows, size=nr, replace=False))
+        order = g.choice(cols, size=nc, replace=False)
+        sign = -1 if b < n_neg else 1
+        start = g.standard_normal(nr)
+        steps = g.uniform(0.5, 1.5, size=(nr, nc - 1))
+        vals = np.concatenate([start[:, None], start[:, None] + np.cumsum(steps, axis=1)], axis=1)
+        vals = vals + g.normal(0.0, noise, size=(nr, nc))
+        if background == "lognormal":
+            vals = np.abs(vals) + 0.0  # keep the planted values on the positive log-normal scale
+        target = order if sign > 0 else order[::-1]
+        x[np.ix_(ridx, target)] = vals.astype(np.float32)
+        truth.append((ridx, np.asarray(order), sign))
+    if round_to:
+        x = (np.round(x / round_to) * round_to).astype(np.float32)
+    return np.ascontiguousarray(x, dtype=np.float32), truth
+
+
+def random_population(n_ind, cols, len_lo, len_hi, seed):
+    """CSR population: (col_idx int32 [sum L], offsets int32 [n_ind + 1])."""
+    g = rng(seed)
+    lens = g.integers(len_lo, len_hi + 1, size=n_ind)
+    offsets = np.zeros(n_ind + 1, dtype=np.int32)
+    offsets[1:] = np.cumsum(lens)
+    col_idx = np.empty(int(offsets[-1]), dtype=np.int32)
+    for i, L in enumerate(lens):
+        col_idx[offsets[i]:offsets[i + 1]] = g.choice(cols, size=int(L), replace=False)
+    return col_idx, offsets
+
+
+def workload_inputs(w):
+    """Matrix, ground truth and evaluation population of a named workload."""
+    x, truth = planted_matrix(w.rows, w.cols, w.n_bic, w.bic_rows, w.bic_cols, w.seed,
+                              background=w.background, round_to=w.round_to,
+                              neg_fraction=w.neg_fraction)
+    col_idx, offsets = random_population(w.pop, w.cols, w.len_lo, w.len_hi, w.seed + 1000)
+    return x, truth, col_idx, offsets
