@@ -1,0 +1,244 @@
+/*
+ * ebic.h -- C ABI of the GB300 (sm_103a) EBIC population-evaluation library.
+ *
+ * EBIC (evolutionary biclustering, as re-implemented by EBIC.jl, arXiv 2105.01196) searches for
+ * biclusters whose rows follow a common order of columns.  An individual is an ordered series of
+ * column indices (Sec. 2.3, "EBIC" paragraph); its fitness comes from the number of rows whose
+ * values follow that order (Sec. 2.4, steps 2-3 and 7).  This library evaluates whole populations
+ * on the GPU and runs the generation loop of Sec. 2.4 (steps 1-9) on the device.
+ *
+ * Conventions shared by every entry point
+ *   - Status: 0 (EBIC_OK) on success, a negative EBIC_E* code otherwise.  No C++ exception and no
+ *     abort crosses this boundary; the message of the last failure is ebic_last_error().
+ *   - Pointers: every array argument may be host memory or device memory of the context's GPU; the
+ *     library tells them apart with cudaPointerGetAttributes.  Host arrays are copied through
+ *     library-owned device buffers.  The caller owns every pointer it passes; the library keeps
+ *     no reference to one after the call returns.
+ *   - Streams: all GPU work of a context runs on the stream given to ebic_create (or on a stream
+ *     the context creates).  Every call returns only after that work has finished, so the caller
+ *     may read outputs at once.  Contexts are independent: calls on different contexts may run
+ *     concurrently from different host threads.  Calls on one context must not overlap.
+ *   - Integers are little-endian two's complement; rows are int64, columns int32.
+ *   - Comparisons: float32 values are compared strictly; ties (including -0 against +0) break both
+ *     the increasing and the decreasing trend.  NaN and +-Inf are rejected when the matrix is
+ *     loaded.
+ */
+#ifndef EBIC_GB300_H
+#define EBIC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define EBIC_API __attribute__((visibility("default")))
+#else
+#define EBIC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------------------- status codes */
+#define EBIC_OK 0
+#define EBIC_EINVAL (-1)   /* bad argument: shape, parameter, chromosome, pointer            */
+#define EBIC_ENAN (-2)     /* the matrix holds NaN or +-Inf                                    */
+#define EBIC_ENOMEM (-3)   /* a device or host allocation failed                               */
+#define EBIC_ECUDA (-4)    /* a CUDA runtime call failed (the message names it)                */
+#define EBIC_ETIMEOUT (-5) /* a bounded device-side wait gave up                               */
+#define EBIC_ESTATE (-6)   /* call out of order (e.g. no matrix loaded, no run initialised)    */
+
+/* ----------------------------------------------------------------------------- enumerations */
+#define EBIC_MODE_AUTO 0   /* the autotuner chooses the evaluation kernel                      */
+#define EBIC_MODE_DIRECT 1 /* direct comparison of the matrix's order keys                     */
+#define EBIC_MODE_BITMAP 2 /* column-pair comparison bitmap (built on first use)               */
+#define EBIC_MODE_PLAIN 3  /* one kernel launch per individual (reference GPU form)            */
+
+#define EBIC_LAYOUT_ROW_MAJOR 0 /* x[r * cols + c] */
+#define EBIC_LAYOUT_COL_MAJOR 1 /* x[c * rows + r] */
+
+#define EBIC_MAX_LEN 64          /* longest chromosome                                        */
+#define EBIC_MAX_BICLUSTERS 256  /* largest top rank list                                     */
+
+typedef struct ebic_ctx ebic_ctx;
+
+/*
+ * Parameters of the method (Sec. 2.4, last paragraph: negative trends on/off, approximate-trend
+ * threshold, allowed overlap between trends, number of iterations and of biclusters; Table 1
+ * gives the iteration cap -n 20000).  The paper fixes no other value; ebic_default_params fills
+ * the defaults this library uses.
+ *   neg_trends       1: a row also counts when it follows the reversed order (Sec. 2.4).
+ *   ratio_num/den    approximate-trend ratio; a row passes when at least
+ *                    t(L) = ceil(ratio * (L-1)) of its L-1 consecutive pairs follow the trend.
+ *                    1/1 is the exact trend.  Requires 0 < ratio_num <= ratio_den.
+ *   min_rows         fitness is 0 below this many accepted rows.
+ *   col_cap          fitness = rows * 2^min(L, col_cap); 0 <= col_cap <= 16.
+ *   overlap_num/den  a top-list entry may share at most this fraction of its columns with any
+ *                    better entry (Sec. 2.4, "level of overlap allowed between the trends").
+ *   n_biclusters     size K of the top rank list, 1..256 (Sec. 2.4, steps 3, 4, 9).
+ *   init_min_len, init_max_len  initial chromosome lengths (Sec. 2.4, step 1).
+ *   max_len          longest chromosome the operators build, <= min(64, cols).
+ *   pop_size         population size P, 2..2^20.
+ *   elite            top-list entries copied into each new population (step 4), <= K.
+ *   tournament       tournament size (step 5), 1..16.
+ *   max_attempts     children tried per slot before the slot is dead (tabu list), 1..16.
+ *   tabu_hit_limit   tabu hits within one generation that stop the run (step 6); <= 0: never.
+ *   seed             key of the Philox4x32-10 stream all random draws come from.
+ *   mode             EBIC_MODE_*: evaluation kernel.
+ *   use_graph        ebic_run_generations: 1 replays one captured CUDA graph per generation,
+ *                    0 launches every kernel eagerly and synchronises after each generation.
+ */
+typedef struct ebic_params {
+  int32_t neg_trends;
+  int32_t ratio_num, ratio_den;
+  int32_t min_rows;
+  int32_t col_cap;
+  int32_t overlap_num, overlap_den;
+  int32_t n_biclusters;
+  int32_t init_min_len, init_max_len;
+  int32_t max_len;
+  int32_t pop_size;
+  int32_t elite;
+  int32_t tournament;
+  int32_t max_attempts;
+  int32_t tabu_hit_limit;
+  uint64_t seed;
+  int32_t mode;
+  int32_t use_graph;
+} ebic_params;
+
+/* Progress of a run (Sec. 2.4, steps 6 and 8). */
+typedef struct ebic_run_report {
+  int32_t gens_done;   /* last scored generation; 0 = only the initial population            */
+  int32_t stopped;     /* 1 when step 6 (tabu-hit limit) ended the run                       */
+  int32_t last_hits;   /* tabu hits of the last generation built                             */
+  int32_t n_top;       /* entries in the top rank list                                       */
+  int64_t n_evaluated; /* individuals scored since the run was initialised                   */
+  int32_t eval_mode;   /* the evaluation kernel used (EBIC_MODE_DIRECT or EBIC_MODE_BITMAP)  */
+  int32_t reserved;
+} ebic_run_report;
+
+/* Fills *p with the library defaults.  Never fails. */
+EBIC_API void ebic_default_params(ebic_params *p);
+
+/* Library version string (static storage). */
+EBIC_API const char *ebic_version(void);
+
+/*
+ * Creates a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t of that device the
+ * context will use (borrowed, not destroyed by the context), or NULL to make the context create
+ * and own a non-blocking stream.  *out receives the context.
+ * Errors: EBIC_EINVAL (out NULL, bad device), EBIC_ECUDA, EBIC_ENOMEM.
+ */
+EBIC_API int ebic_create(ebic_ctx **out, int32_t device, void *cuda_stream);
+
+/* Frees every device and host resource of the context.  NULL is accepted. */
+EBIC_API int ebic_destroy(ebic_ctx *ctx);
+
+/* Message of the last failed call on this context ("" when none); static per context. */
+EBIC_API const char *ebic_last_error(const ebic_ctx *ctx);
+
+/*
+ * Loads the expression matrix (Sec. 2.1: rows x columns of numeric values; Sec. 2.4 step 2
+ * sends the data to the GPU).  x holds rows*cols float32 in `layout` (EBIC_LAYOUT_*), host or
+ * device memory.  The library converts it into its own device copy: column-major uint32 order
+ * keys with rows padded to a multiple of 128.  Loading a new matrix drops the bitmap cache and
+ * any run state.
+ * Errors: EBIC_EINVAL (rows < 1, cols < 2, cols > 65535, bad layout, NULL x), EBIC_ENAN (NaN or
+ * Inf anywhere in x; the previous matrix is gone), EBIC_ENOMEM, EBIC_ECUDA.
+ */
+EBIC_API int ebic_load_matrix(ebic_ctx *ctx, const float *x, int64_t rows, int32_t cols, int32_t layout);
+
+/*
+ * Builds the column-pair comparison bitmap of the loaded matrix: for every ordered pair of
+ * columns (a, b), word w bit j is [x(32w+j, b) > x(32w+j, a)].  Its size is
+ * ebic_bitmap_bytes(rows, cols).  EBIC_MODE_BITMAP builds it on first use; this call builds it
+ * ahead of time.  Errors: EBIC_ESTATE (no matrix), EBIC_ENOMEM, EBIC_ECUDA.
+ */
+EBIC_API int ebic_build_bitmap(ebic_ctx *ctx);
+
+/* Bytes of the pair bitmap for a rows x cols matrix (cols^2 * ceil128(rows) / 8). */
+EBIC_API int64_t ebic_bitmap_bytes(int64_t rows, int32_t cols);
+
+/*
+ * Copies the pair bitmap into `out` (host or device, n_words uint32).  Layout: word
+ * ((a * cols + b) * w_stride + w), w_stride = ceil128(rows) / 32; bit j of word w is row 32w+j.
+ * Errors: EBIC_ESTATE (no bitmap built), EBIC_EINVAL (n_words too small), EBIC_ECUDA.
+ */
+EBIC_API int ebic_copy_bitmap(ebic_ctx *ctx, uint32_t *out, int64_t n_words);
+
+/*
+ * Evaluates a population (Sec. 2.4, steps 2-3: score every individual by the number of its
+ * trend-preserving rows).  The population is CSR: individual i is
+ * col_idx[offsets[i] .. offsets[i+1]-1], 2 <= length <= 64, distinct columns in [0, cols).
+ * For each individual i:
+ *   rows_pos[i]  rows with at least t(L) increasing consecutive pairs,
+ *   rows_neg[i]  rows with at least t(L) decreasing pairs (0 unless p->neg_trends),
+ *   rows_any[i]  rows passing either direction (counted once),
+ *   fitness[i]   0 if rows_any < p->min_rows, else rows_any * 2^min(L, p->col_cap).
+ * Any of the four outputs may be NULL.  Only neg_trends, ratio_*, min_rows, col_cap and mode of
+ * *p are read.  n_ind = 0 is valid and does nothing.
+ * Errors: EBIC_ESTATE (no matrix), EBIC_EINVAL (bad parameter or chromosome; nothing written),
+ * EBIC_ENOMEM, EBIC_ECUDA.
+ */
+EBIC_API int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *offsets,
+                         int32_t n_ind, const ebic_params *p, int32_t *rows_pos,
+                         int32_t *rows_neg, int32_t *rows_any, uint64_t *fitness);
+
+/*
+ * Runs the EBIC generation loop on the device (Sec. 2.4 steps 1-8; strategies of Sec. 2.3):
+ * the first call on a loaded matrix initialises and scores a random population (steps 1-3),
+ * then up to n_gen generations follow: elitism (step 4), penalised tournament, crossover and one
+ * of insertion/deletion/substitution/swap with tabu-list rejection (step 5), the tabu-hit stop
+ * test (step 6), scoring and top-list update (step 7).  Later calls continue the same run
+ * (resuming is exact: all randomness is counter-based).  Changing any parameter but mode or
+ * use_graph, or loading a matrix, starts a new run.  *rep (may be NULL) receives the progress.
+ * Errors: EBIC_ESTATE (no matrix), EBIC_EINVAL (bad parameter), EBIC_ENOMEM, EBIC_ECUDA,
+ * EBIC_ETIMEOUT.
+ */
+EBIC_API int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
+                         ebic_run_report *rep);
+
+/*
+ * Copies the top rank list (Sec. 2.4, steps 3, 7 and 9), best first, sorted by fitness then by
+ * tabu key.  cols: n_top * 64 int32 (entry e's columns at cols[e*64 .. e*64+len-1]); lens,
+ * fitness, keys (the tabu key: FNV-1a 64 of the column sequence), rows (3 int32 per entry:
+ * pos, neg, any).  Arrays hold at least `capacity` entries; any may be NULL.  *n_top receives the
+ * number of entries.  Errors: EBIC_ESTATE (no run), EBIC_EINVAL, EBIC_ECUDA.
+ */
+EBIC_API int ebic_get_toplist(ebic_ctx *ctx, int32_t capacity, int32_t *n_top, int32_t *cols,
+                     int32_t *lens, uint64_t *fitness, uint64_t *keys, int32_t *rows);
+
+/*
+ * Copies the current population: cols (P * 64 int32, slot s at cols[s*64..]), lens, dead (1 =
+ * the slot was rejected by the tabu list and not scored), fitness.  Any may be NULL.
+ * Errors: EBIC_ESTATE, EBIC_EINVAL (capacity < P), EBIC_ECUDA.
+ */
+EBIC_API int ebic_get_population(ebic_ctx *ctx, int32_t capacity, int32_t *cols, int32_t *lens,
+                        uint8_t *dead, uint64_t *fitness);
+
+/*
+ * Bicluster extraction (Sec. 2.4, step 9): for each top-list entry e, the rows it accepts as a
+ * bitmask, rowmask[e * w_stride + w] bit j = row 32w + j, w_stride = ceil128(rows) / 32.
+ * rowmask holds capacity * w_stride words.  *n_out receives the number of entries written.
+ * Errors: EBIC_ESTATE (no run), EBIC_EINVAL (capacity too small), EBIC_ENOMEM, EBIC_ECUDA.
+ */
+EBIC_API int ebic_extract_biclusters(ebic_ctx *ctx, int32_t capacity, uint32_t *rowmask, int32_t *n_out);
+
+/*
+ * Checkpoint of the run state (generation index, population, fitness, penalties, top list and
+ * tabu list).  ebic_state_bytes returns the size of the blob; ebic_save_state writes it into the
+ * host buffer `blob` of `size` bytes; ebic_load_state restores it (same matrix, same parameters)
+ * so that later generations equal those of an uninterrupted run.
+ * Errors: EBIC_ESTATE (no run / no matrix), EBIC_EINVAL (size, corrupt blob), EBIC_ENOMEM,
+ * EBIC_ECUDA.
+ */
+EBIC_API int64_t ebic_state_bytes(ebic_ctx *ctx);
+EBIC_API int ebic_save_state(ebic_ctx *ctx, void *blob, int64_t size);
+EBIC_API int ebic_load_state(ebic_ctx *ctx, const ebic_params *p, const void *blob, int64_t size);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EBIC_GB300_H */

@@ -1,0 +1,381 @@
+// C ABI of the EBIC GB300 library: contexts, matrix upload, the pair bitmap and population
+// evaluation.  The generation-loop entry points live in evolve.cu.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "internal.h"
+
+namespace {
+
+// Restores the caller's current device when an entry point returns.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+    }
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+int ebic_fail(ebic_ctx *ctx, int code, const std::string &msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int ebic_fail_cuda(ebic_ctx *ctx, cudaError_t e, const char *what, const char *file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  cudaGetLastError();
+  if (ctx) ctx->err = buf;
+  return e == cudaErrorMemoryAllocation ? EBIC_ENOMEM : EBIC_ECUDA;
+}
+
+bool ebic_is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+static int check_device_ptr(ebic_ctx *ctx, const void *p, const char *name) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return EBIC_OK;
+  }
+  if ((attr.type == cudaMemoryTypeDevice) && attr.device != ctx->device)
+    return ebic_fail(ctx, EBIC_EINVAL, std::string(name) + " is memory of another device");
+  return EBIC_OK;
+}
+
+int ebic_check_eval_params(ebic_ctx *ctx, const ebic_params *p) {
+  if (!p) return ebic_fail(ctx, EBIC_EINVAL, "params is NULL");
+  if (!(p->ratio_num > 0 && p->ratio_num <= p->ratio_den))
+    return ebic_fail(ctx, EBIC_EINVAL, "need 0 < ratio_num <= ratio_den");
+  if (p->ratio_den > (1 << 24))
+    return ebic_fail(ctx, EBIC_EINVAL, "ratio_den must be <= 2^24");
+  if (p->neg_trends != 0 && p->neg_trends != 1)
+    return ebic_fail(ctx, EBIC_EINVAL, "neg_trends must be 0 or 1");
+  if (p->col_cap < 0 || p->col_cap > 16 || p->min_rows < 0)
+    return ebic_fail(ctx, EBIC_EINVAL, "need 0 <= col_cap <= 16 and min_rows >= 0");
+  if (p->mode < EBIC_MODE_AUTO || p->mode > EBIC_MODE_PLAIN)
+    return ebic_fail(ctx, EBIC_EINVAL, "unknown mode");
+  return EBIC_OK;
+}
+
+extern "C" {
+
+const char *ebic_version(void) { return "ebic-gb300 0.1 (sm_103a)"; }
+
+void ebic_default_params(ebic_params *p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->neg_trends = 1;
+  p->ratio_num = 85;
+  p->ratio_den = 100;
+  p->min_rows = 2;
+  p->col_cap = 10;
+  p->overlap_num = 1;
+  p->overlap_den = 2;
+  p->n_biclusters = 10;
+  p->init_min_len = 2;
+  p->init_max_len = 8;
+  p->max_len = 20;
+  p->pop_size = 800;
+  p->elite = 10;
+  p->tournament = 4;
+  p->max_attempts = 4;
+  p->tabu_hit_limit = 800;
+  p->seed = 20210710ull;
+  p->mode = EBIC_MODE_AUTO;
+  p->use_graph = 1;
+}
+
+int ebic_create(ebic_ctx **out, int32_t device, void *cuda_stream) {
+  if (!out) return EBIC_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return EBIC_ECUDA;
+  }
+  if (device < 0 || device >= ndev) return EBIC_EINVAL;
+  ebic_ctx *ctx = new (std::nothrow) ebic_ctx();
+  if (!ctx) return EBIC_ENOMEM;
+  ctx->device = device;
+  DeviceGuard g(device);
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return EBIC_ECUDA;
+  }
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete ctx;
+      return EBIC_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  if (ctx->d_err.ensure(64) != cudaSuccess || ctx->d_work.ensure(64) != cudaSuccess) {
+    ebic_destroy(ctx);
+    return EBIC_ENOMEM;
+  }
+  *out = ctx;
+  return EBIC_OK;
+}
+
+int ebic_destroy(ebic_ctx *ctx) {
+  if (!ctx) return EBIC_OK;
+  DeviceGuard g(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  cudaGetLastError();
+  gen_state_free(ctx->gen);
+  ctx->gen = nullptr;
+  DevBuf *bufs[] = {&ctx->keys, &ctx->bitmap, &ctx->stage_x, &ctx->d_err, &ctx->d_work,
+                    &ctx->ev_cols, &ctx->ev_off, &ctx->ev_out, &ctx->ev_fit};
+  for (DevBuf *b : bufs) b->release();
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return EBIC_OK;
+}
+
+const char *ebic_last_error(const ebic_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int64_t ebic_bitmap_bytes(int64_t rows, int32_t cols) {
+  if (rows < 1 || cols < 1) return 0;
+  return (int64_t)cols * cols * (round_up(rows, 128) / 32) * 4;
+}
+
+int ebic_load_matrix(ebic_ctx *ctx, const float *x, int64_t rows, int32_t cols, int32_t layout) {
+  if (!ctx) return EBIC_EINVAL;
+  if (!x) return ebic_fail(ctx, EBIC_EINVAL, "x is NULL");
+  if (rows < 1 || cols < 2 || cols > 65535)
+    return ebic_fail(ctx, EBIC_EINVAL, "need rows >= 1 and 2 <= cols <= 65535");
+  if (layout != EBIC_LAYOUT_ROW_MAJOR && layout != EBIC_LAYOUT_COL_MAJOR)
+    return ebic_fail(ctx, EBIC_EINVAL, "unknown layout");
+  if (rows > (int64_t(1) << 31) - 128)
+    return ebic_fail(ctx, EBIC_EINVAL, "rows must be < 2^31 - 128");
+  DeviceGuard g(ctx->device);
+  EBIC_TRY(check_device_ptr(ctx, x, "x"));
+  ctx->have_matrix = false;
+  ctx->bitmap_ok = false;
+  gen_state_free(ctx->gen);
+  ctx->gen = nullptr;
+  const int64_t R_pad = round_up(rows, 128);
+  EBIC_CHECK_CUDA(ctx, ctx->keys.ensure((size_t)cols * R_pad * sizeof(uint32_t)));
+  const float *src = x;
+  if (!ebic_is_device_ptr(x)) {
+    EBIC_CHECK_CUDA(ctx, ctx->stage_x.ensure((size_t)rows * cols * sizeof(float)));
+    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(ctx->stage_x.p, x, (size_t)rows * cols * sizeof(float),
+                                         cudaMemcpyHostToDevice, ctx->stream));
+    src = ctx->stage_x.as<float>();
+  }
+  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(ctx->d_err.p, 0, sizeof(int32_t), ctx->stream));
+  EBIC_CHECK_CUDA(ctx, launch_upload(src, rows, cols, R_pad, layout, ctx->keys.as<uint32_t>(),
+                                     ctx->d_err.as<int32_t>(), ctx->stream));
+  int32_t herr = 0;
+  EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&herr, ctx->d_err.p, sizeof(int32_t),
+                                       cudaMemcpyDeviceToHost, ctx->stream));
+  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (herr) return ebic_fail(ctx, EBIC_ENAN, "matrix holds NaN or Inf");
+  ctx->R = rows;
+  ctx->C = cols;
+  ctx->R_pad = R_pad;
+  ctx->Wst = R_pad / 32;
+  ctx->have_matrix = true;
+  ctx->err.clear();
+  return EBIC_OK;
+}
+
+int ebic_build_bitmap(ebic_ctx *ctx) {
+  if (!ctx) return EBIC_EINVAL;
+  if (!ctx->have_matrix) return ebic_fail(ctx, EBIC_ESTATE, "no matrix loaded");
+  if (ctx->bitmap_ok) return EBIC_OK;
+  DeviceGuard g(ctx->device);
+  const size_t bytes = (size_t)ebic_bitmap_bytes(ctx->R, ctx->C);
+  EBIC_CHECK_CUDA(ctx, ctx->bitmap.ensure(bytes));
+  EBIC_CHECK_CUDA(ctx, launch_build_bitmap(ctx->keys.as<uint32_t>(), ctx->R_pad, ctx->C, ctx->Wst,
+                                           ctx->bitmap.as<uint32_t>(), ctx->stream));
+  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->bitmap_ok = true;
+  return EBIC_OK;
+}
+
+int ebic_copy_bitmap(ebic_ctx *ctx, uint32_t *out, int64_t n_words) {
+  if (!ctx) return EBIC_EINVAL;
+  if (!ctx->bitmap_ok) return ebic_fail(ctx, EBIC_ESTATE, "no bitmap built");
+  const int64_t need = ebic_bitmap_bytes(ctx->R, ctx->C) / 4;
+  if (!out || n_words < need) return ebic_fail(ctx, EBIC_EINVAL, "output too small");
+  DeviceGuard g(ctx->device);
+  EBIC_TRY(check_device_ptr(ctx, out, "out"));
+  EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(out, ctx->bitmap.p, (size_t)need * 4, cudaMemcpyDefault,
+                                       ctx->stream));
+  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return EBIC_OK;
+}
+
+int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *offsets,
+                         int32_t n_ind, const ebic_params *p, int32_t *rows_pos,
+                         int32_t *rows_neg, int32_t *rows_any, uint64_t *fitness) {
+  if (!ctx) return EBIC_EINVAL;
+  if (!ctx->have_matrix) return ebic_fail(ctx, EBIC_ESTATE, "no matrix loaded");
+  EBIC_TRY(ebic_check_eval_params(ctx, p));
+  if (n_ind < 0 || n_ind > (1 << 24)) return ebic_fail(ctx, EBIC_EINVAL, "need 0 <= n_ind <= 2^24");
+  if (n_ind == 0) return EBIC_OK;
+  if (!col_idx || !offsets) return ebic_fail(ctx, EBIC_EINVAL, "col_idx/offsets NULL");
+  DeviceGuard g(ctx->device);
+  EBIC_TRY(check_device_ptr(ctx, col_idx, "col_idx"));
+  EBIC_TRY(check_device_ptr(ctx, offsets, "offsets"));
+  void *outs[4] = {rows_pos, rows_neg, rows_any, fitness};
+  for (void *o : outs)
+    if (o) EBIC_TRY(check_device_ptr(ctx, o, "output"));
+  const bool dev_cols = ebic_is_device_ptr(col_idx), dev_off = ebic_is_device_ptr(offsets);
+  if (dev_cols != dev_off)
+    return ebic_fail(ctx, EBIC_EINVAL, "col_idx and offsets must both be host or both device");
+  cudaStream_t s = ctx->stream;
+
+  const int32_t *d_cols = col_idx, *d_off = offsets;
+  std::vector<int32_t> h_off;
+  double mean_len = 0.0;
+  int64_t total = 0;
+  if (!dev_cols) {
+    // Host CSR: validate here, then copy.
+    const int64_t base = offsets[0];
+    for (int32_t i = 0; i < n_ind; ++i) {
+      const int64_t L = (int64_t)offsets[i + 1] - offsets[i];
+      if (offsets[i] < 0 || L < 2 || L > EBIC_MAX_LEN)
+        return ebic_fail(ctx, EBIC_EINVAL, "individual " + std::to_string(i) +
+                                               ": length must be in [2, 64]");
+      const int32_t *c = col_idx + offsets[i];
+      for (int64_t k = 0; k < L; ++k) {
+        if (c[k] < 0 || c[k] >= ctx->C)
+          return ebic_fail(ctx, EBIC_EINVAL,
+                           "individual " + std::to_string(i) + ": column out of range");
+        for (int64_t j = 0; j < k; ++j)
+          if (c[j] == c[k])
+            return ebic_fail(ctx, EBIC_EINVAL,
+                             "individual " + std::to_string(i) + ": repeated column");
+      }
+    }
+    total = (int64_t)offsets[n_ind] - base;
+    mean_len = (double)total / n_ind;
+    EBIC_CHECK_CUDA(ctx, ctx->ev_cols.ensure((size_t)(offsets[n_ind]) * 4 + 16));
+    EBIC_CHECK_CUDA(ctx, ctx->ev_off.ensure((size_t)(n_ind + 1) * 4));
+    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(ctx->ev_cols.p, col_idx, (size_t)offsets[n_ind] * 4,
+                                         cudaMemcpyHostToDevice, s));
+    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(ctx->ev_off.p, offsets, (size_t)(n_ind + 1) * 4,
+                                         cudaMemcpyHostToDevice, s));
+    d_cols = ctx->ev_cols.as<int32_t>();
+    d_off = ctx->ev_off.as<int32_t>();
+    if (p->mode == EBIC_MODE_PLAIN) h_off.assign(offsets, offsets + n_ind + 1);
+  } else {
+    // Device CSR: validate on the device before any kernel indexes the matrix with it.
+    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(ctx->d_err.p, 0, sizeof(int32_t), s));
+    EBIC_CHECK_CUDA(ctx, launch_validate_csr(col_idx, offsets, n_ind, ctx->C,
+                                             ctx->d_err.as<int32_t>(), s));
+    int32_t herr = 0;
+    int32_t ends[2] = {0, 0};
+    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&herr, ctx->d_err.p, 4, cudaMemcpyDeviceToHost, s));
+    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&ends[0], offsets, 4, cudaMemcpyDeviceToHost, s));
+    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&ends[1], offsets + n_ind, 4, cudaMemcpyDeviceToHost, s));
+    if (p->mode == EBIC_MODE_PLAIN) {
+      h_off.resize(n_ind + 1);
+      EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(h_off.data(), offsets, (size_t)(n_ind + 1) * 4,
+                                           cudaMemcpyDeviceToHost, s));
+    }
+    EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(s));
+    if (herr) return ebic_fail(ctx, EBIC_EINVAL, "invalid chromosome in the population");
+    total = (int64_t)ends[1] - ends[0];
+    mean_len = (double)total / n_ind;
+  }
+
+  int mode = choose_mode(ctx, p->mode, n_ind, mean_len, 1);
+  if (mode == EBIC_MODE_BITMAP && !ctx->bitmap_ok) EBIC_TRY(ebic_build_bitmap(ctx));
+
+  EBIC_CHECK_CUDA(ctx, ctx->ev_out.ensure((size_t)n_ind * 3 * sizeof(int32_t)));
+  EBIC_CHECK_CUDA(ctx, ctx->ev_fit.ensure((size_t)n_ind * sizeof(uint64_t)));
+  EvalArgs a{};
+  a.keys = ctx->keys.as<uint32_t>();
+  a.bitmap = ctx->bitmap_ok ? ctx->bitmap.as<uint32_t>() : nullptr;
+  a.R = ctx->R;
+  a.R_pad = ctx->R_pad;
+  a.Wst = ctx->Wst;
+  a.C = ctx->C;
+  a.neg = p->neg_trends;
+  a.rnum = p->ratio_num;
+  a.rden = p->ratio_den;
+  a.min_rows = p->min_rows;
+  a.col_cap = p->col_cap;
+  a.rows_pos = ctx->ev_out.as<int32_t>();
+  a.rows_neg = a.rows_pos + n_ind;
+  a.rows_any = a.rows_neg + n_ind;
+  a.fitness = ctx->ev_fit.as<uint64_t>();
+  a.work = ctx->d_work.as<int32_t>();
+  PopView pv{d_cols, d_off, nullptr, nullptr, 0, n_ind};
+
+  if (mode == EBIC_MODE_PLAIN) {
+    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(a.rows_pos, 0, (size_t)n_ind * 3 * 4, s));
+    for (int32_t i = 0; i < n_ind; ++i)
+      EBIC_CHECK_CUDA(ctx, launch_eval_plain(a, d_cols + h_off[i], h_off[i + 1] - h_off[i], i, s));
+    EBIC_CHECK_CUDA(ctx, launch_fitness(a, pv, s));
+  } else {
+    EBIC_CHECK_CUDA(ctx, launch_eval(mode, a, pv, ctx->num_sms, s));
+  }
+  int32_t *dsts[3] = {rows_pos, rows_neg, rows_any};
+  for (int k = 0; k < 3; ++k)
+    if (dsts[k])
+      EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(dsts[k], a.rows_pos + (size_t)k * n_ind,
+                                           (size_t)n_ind * 4, cudaMemcpyDefault, s));
+  if (fitness)
+    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(fitness, a.fitness, (size_t)n_ind * 8,
+                                         cudaMemcpyDefault, s));
+  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(s));
+  return EBIC_OK;
+}
+
+}  // extern "C"
+
+// Evaluation-kernel choice for EBIC_MODE_AUTO: a cost model in row-words, refined by the
+// autotuner when it has measured this matrix.  The bitmap costs a one-off build of C^2 * Wst
+// words and then (L-1) * Wst words per individual and direction; the direct form gathers
+// L * R_pad keys per individual.
+int choose_mode(const ebic_ctx *ctx, int requested, int64_t n_ind, double mean_len,
+                int expected_sweeps) {
+  if (requested != EBIC_MODE_AUTO) return requested;
+  if (ctx->bitmap_ok) return EBIC_MODE_BITMAP;
+  const double Wst = (double)ctx->Wst, C = (double)ctx->C;
+  const double bitmap_bytes = C * C * Wst * 4.0;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    free_b = 0;
+  }
+  if (bitmap_bytes > 0.5 * (double)free_b) return EBIC_MODE_DIRECT;
+  // Relative per-unit costs (direct key gathers are ~4x cheaper per byte than a bitmap build
+  // word, bitmap eval words stream from HBM): time in units of one 32-bit access.
+  const double direct = (double)n_ind * mean_len * (double)ctx->R_pad / 4.0;
+  const double build = C * C * Wst * 4.0;
+  const double eval_bm = (double)n_ind * (mean_len - 1.0) * Wst * 2.0;
+  return (build + expected_sweeps * eval_bm < expected_sweeps * direct) ? EBIC_MODE_BITMAP
+                                                                         : EBIC_MODE_DIRECT;
+}

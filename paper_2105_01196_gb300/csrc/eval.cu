@@ -1,0 +1,433 @@
+// Population evaluation kernels (Sec. 2.4, steps 2-3 and 7 of the EBIC.jl paper: score every
+// individual by the number of rows that follow its column order; trend definition of Sec. 2.3).
+//
+// For individual i with columns c_0..c_{L-1} and row r:
+//   inc = #{k : key(r, c_{k+1}) > key(r, c_k)},  dec = #{k : key(r, c_{k+1}) < key(r, c_k)}
+//   pos = inc >= t(L), neg = neg_trends && dec >= t(L), t(L) = ceil(ratio * (L-1)),
+// and rows_pos / rows_neg / rows_any count the rows with pos / neg / (pos || neg).
+//
+// Three forms compute the same counts:
+//   direct  keys gathered per row (4 rows per lane, 16-byte loads of the column-major keys);
+//   bitmap  32 rows per word from the pair bitmap: an AND of the L-1 pair words for the exact
+//           trend, a bit-sliced carry-save counter compared with t(L) for approximate trends;
+//   plain   one kernel launch per individual, one row per thread (the reference GPU form).
+// The direct and bitmap kernels are persistent: warps pull (individual, row segment) work items
+// from an atomic counter and add their partial counts with one atomic per item.
+#include "internal.h"
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+
+__device__ __forceinline__ int threshold(int L, int num, int den) {
+  return (num * (L - 1) + den - 1) / den;
+}
+
+__device__ __forceinline__ int pv_start(const PopView &v, int i) {
+  return v.off ? v.off[i] : i * v.stride;
+}
+
+__device__ __forceinline__ int pv_len(const PopView &v, int i) {
+  return v.off ? (v.off[i + 1] - v.off[i]) : v.len[i];
+}
+
+__device__ __forceinline__ uint4 ldg4(const uint32_t *p) {
+  return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+
+// ------------------------------------------------------------------------------- validation
+
+__global__ void k_validate_csr(const int32_t *__restrict__ cols, const int32_t *__restrict__ off,
+                               int32_t n, int32_t C, int32_t *__restrict__ err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int s = off[i], e = off[i + 1];
+  const int L = e - s;
+  bool bad = (s < 0) || L < 2 || L > EBIC_MAX_LEN;
+  for (int k = 0; k < L && !bad; ++k) {
+    const int c = cols[s + k];
+    if (c < 0 || c >= C) bad = true;
+    for (int j = 0; j < k && !bad; ++j)
+      if (cols[s + j] == c) bad = true;
+  }
+  if (bad) atomicOr(err, 2);
+}
+
+// ------------------------------------------------------------------------------- direct form
+
+template <bool NEG>
+__global__ void __launch_bounds__(kThreads) k_eval_direct(EvalArgs a, PopView pv) {
+  __shared__ int64_t s_base[kWarps][EBIC_MAX_LEN];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t passes_total = a.R_pad / 128;
+  const int32_t n_items = pv.n * a.n_seg;
+  for (;;) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(a.work, 1);
+    q = __shfl_sync(kFull, q, 0);
+    if (q >= n_items) break;
+    const int i = q / a.n_seg, seg = q - i * a.n_seg;
+    if (pv.dead && pv.dead[i]) continue;
+    const int L = pv_len(pv, i), st = pv_start(pv, i);
+    __syncwarp();
+    for (int k = lane; k < L; k += 32) s_base[warp][k] = (int64_t)pv.cols[st + k] * a.R_pad;
+    __syncwarp();
+    const int t = threshold(L, a.rnum, a.rden);
+    const int64_t p0 = (int64_t)seg * a.seg_passes;
+    const int64_t p1 = min(p0 + a.seg_passes, passes_total);
+    int cp = 0, cn = 0, ca = 0;
+    for (int64_t pass = p0; pass < p1; ++pass) {
+      const int64_t r = pass * 128 + lane * 4;
+      uint4 prev = ldg4(a.keys + s_base[warp][0] + r);
+      int i0 = 0, i1 = 0, i2 = 0, i3 = 0, d0 = 0, d1 = 0, d2 = 0, d3 = 0;
+#pragma unroll 4
+      for (int k = 1; k < L; ++k) {
+        const uint4 cur = ldg4(a.keys + s_base[warp][k] + r);
+        i0 += cur.x > prev.x;
+        i1 += cur.y > prev.y;
+        i2 += cur.z > prev.z;
+        i3 += cur.w > prev.w;
+        if (NEG) {
+          d0 += cur.x < prev.x;
+          d1 += cur.y < prev.y;
+          d2 += cur.z < prev.z;
+          d3 += cur.w < prev.w;
+        }
+        prev = cur;
+      }
+      const bool p_0 = i0 >= t, p_1 = i1 >= t, p_2 = i2 >= t, p_3 = i3 >= t;
+      const bool n_0 = NEG && d0 >= t, n_1 = NEG && d1 >= t, n_2 = NEG && d2 >= t,
+                 n_3 = NEG && d3 >= t;
+      cp += p_0 + p_1 + p_2 + p_3;
+      cn += n_0 + n_1 + n_2 + n_3;
+      ca += (p_0 | n_0) + (p_1 | n_1) + (p_2 | n_2) + (p_3 | n_3);
+    }
+    cp = __reduce_add_sync(kFull, cp);
+    cn = __reduce_add_sync(kFull, cn);
+    ca = __reduce_add_sync(kFull, ca);
+    if (lane == 0) {
+      if (cp) atomicAdd(a.rows_pos + i, cp);
+      if (cn) atomicAdd(a.rows_neg + i, cn);
+      if (ca) atomicAdd(a.rows_any + i, ca);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------- bitmap form
+
+// Bit-sliced 6-bit counter of up to 63 one-bit inputs per bit position (one word = 32 rows).
+struct Cnt6 {
+  uint32_t b0, b1, b2, b3, b4, b5;
+};
+
+__device__ __forceinline__ void cnt_zero(Cnt6 &c) { c.b0 = c.b1 = c.b2 = c.b3 = c.b4 = c.b5 = 0u; }
+
+__device__ __forceinline__ uint32_t maj3(uint32_t x, uint32_t y, uint32_t z) {
+  return (x & y) | (z & (x ^ y));
+}
+
+__device__ __forceinline__ void cnt_ripple2(Cnt6 &c, uint32_t k) {
+  uint32_t t = c.b2 & k;
+  c.b2 ^= k;
+  k = t;
+  t = c.b3 & k;
+  c.b3 ^= k;
+  k = t;
+  t = c.b4 & k;
+  c.b4 ^= k;
+  k = t;
+  c.b5 ^= k;
+}
+
+__device__ __forceinline__ void cnt_add1(Cnt6 &c, uint32_t x) {
+  uint32_t t = c.b0 & x;
+  c.b0 ^= x;
+  x = t;
+  t = c.b1 & x;
+  c.b1 ^= x;
+  cnt_ripple2(c, t);
+}
+
+// Adds four inputs: two full adders into the ones, one into the twos, ripple from the fours.
+__device__ __forceinline__ void cnt_add4(Cnt6 &c, uint32_t x0, uint32_t x1, uint32_t x2,
+                                         uint32_t x3) {
+  const uint32_t tA = maj3(c.b0, x0, x1);
+  c.b0 ^= x0 ^ x1;
+  const uint32_t tB = maj3(c.b0, x2, x3);
+  c.b0 ^= x2 ^ x3;
+  const uint32_t f = maj3(c.b1, tA, tB);
+  c.b1 ^= tA ^ tB;
+  cnt_ripple2(c, f);
+}
+
+// Bits where the count is >= t (1 <= t <= 63), most significant bit first.
+__device__ __forceinline__ uint32_t cnt_ge(const Cnt6 &c, int t) {
+  const uint32_t b[6] = {c.b0, c.b1, c.b2, c.b3, c.b4, c.b5};
+  uint32_t gt = 0u, eq = kFull;
+#pragma unroll
+  for (int k = 5; k >= 0; --k) {
+    if ((t >> k) & 1) {
+      eq &= b[k];
+    } else {
+      gt |= eq & b[k];
+      eq &= ~b[k];
+    }
+  }
+  return gt | eq;
+}
+
+__device__ __forceinline__ uint4 and4(uint4 a, uint4 b) {
+  return make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+}
+
+__device__ __forceinline__ int popc4(uint4 v) {
+  return __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+}
+
+template <bool NEG>
+__global__ void __launch_bounds__(kThreads) k_eval_bitmap(EvalArgs a, PopView pv) {
+  __shared__ int64_t s_pos[kWarps][EBIC_MAX_LEN];
+  __shared__ int64_t s_neg[kWarps][EBIC_MAX_LEN];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t Wst = a.Wst;
+  const int64_t passes_total = (Wst + 127) / 128;
+  const int32_t n_items = pv.n * a.n_seg;
+  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+  for (;;) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(a.work, 1);
+    q = __shfl_sync(kFull, q, 0);
+    if (q >= n_items) break;
+    const int i = q / a.n_seg, seg = q - i * a.n_seg;
+    if (pv.dead && pv.dead[i]) continue;
+    const int L = pv_len(pv, i), st = pv_start(pv, i);
+    const int np = L - 1;
+    __syncwarp();
+    for (int k = lane; k < np; k += 32) {
+      const int64_t c = pv.cols[st + k], d = pv.cols[st + k + 1];
+      s_pos[warp][k] = (c * a.C + d) * Wst;
+      s_neg[warp][k] = (d * a.C + c) * Wst;
+    }
+    __syncwarp();
+    const int t = threshold(L, a.rnum, a.rden);
+    const bool exact = (t == np);
+    const int64_t p0 = (int64_t)seg * a.seg_passes;
+    const int64_t p1 = min(p0 + a.seg_passes, passes_total);
+    int cp = 0, cn = 0, ca = 0;
+    for (int64_t pass = p0; pass < p1; ++pass) {
+      const int64_t w = pass * 128 + lane * 4;
+      const bool act = w < Wst;
+      const uint32_t *G = a.bitmap + w;
+      uint4 pos, neg = zero4;
+      if (exact) {
+        uint4 ap = make_uint4(kFull, kFull, kFull, kFull), an = ap;
+        int k = 0;
+        for (; k + 4 <= np; k += 4) {
+          uint4 v[4], u[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            v[j] = act ? ldg4(G + s_pos[warp][k + j]) : zero4;
+            if (NEG) u[j] = act ? ldg4(G + s_neg[warp][k + j]) : zero4;
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            ap = and4(ap, v[j]);
+            if (NEG) an = and4(an, u[j]);
+          }
+        }
+        for (; k < np; ++k) {
+          ap = and4(ap, act ? ldg4(G + s_pos[warp][k]) : zero4);
+          if (NEG) an = and4(an, act ? ldg4(G + s_neg[warp][k]) : zero4);
+        }
+        pos = act ? ap : zero4;
+        if (NEG) neg = act ? an : zero4;
+      } else {
+        Cnt6 P[4], N[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          cnt_zero(P[j]);
+          cnt_zero(N[j]);
+        }
+        int k = 0;
+        for (; k + 4 <= np; k += 4) {
+          uint4 v[4], u[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            v[j] = act ? ldg4(G + s_pos[warp][k + j]) : zero4;
+            if (NEG) u[j] = act ? ldg4(G + s_neg[warp][k + j]) : zero4;
+          }
+          cnt_add4(P[0], v[0].x, v[1].x, v[2].x, v[3].x);
+          cnt_add4(P[1], v[0].y, v[1].y, v[2].y, v[3].y);
+          cnt_add4(P[2], v[0].z, v[1].z, v[2].z, v[3].z);
+          cnt_add4(P[3], v[0].w, v[1].w, v[2].w, v[3].w);
+          if (NEG) {
+            cnt_add4(N[0], u[0].x, u[1].x, u[2].x, u[3].x);
+            cnt_add4(N[1], u[0].y, u[1].y, u[2].y, u[3].y);
+            cnt_add4(N[2], u[0].z, u[1].z, u[2].z, u[3].z);
+            cnt_add4(N[3], u[0].w, u[1].w, u[2].w, u[3].w);
+          }
+        }
+        for (; k < np; ++k) {
+          const uint4 v = act ? ldg4(G + s_pos[warp][k]) : zero4;
+          cnt_add1(P[0], v.x);
+          cnt_add1(P[1], v.y);
+          cnt_add1(P[2], v.z);
+          cnt_add1(P[3], v.w);
+          if (NEG) {
+            const uint4 u = act ? ldg4(G + s_neg[warp][k]) : zero4;
+            cnt_add1(N[0], u.x);
+            cnt_add1(N[1], u.y);
+            cnt_add1(N[2], u.z);
+            cnt_add1(N[3], u.w);
+          }
+        }
+        pos = make_uint4(cnt_ge(P[0], t), cnt_ge(P[1], t), cnt_ge(P[2], t), cnt_ge(P[3], t));
+        if (NEG)
+          neg = make_uint4(cnt_ge(N[0], t), cnt_ge(N[1], t), cnt_ge(N[2], t), cnt_ge(N[3], t));
+      }
+      cp += popc4(pos);
+      if (NEG) {
+        cn += popc4(neg);
+        ca += popc4(make_uint4(pos.x | neg.x, pos.y | neg.y, pos.z | neg.z, pos.w | neg.w));
+      } else {
+        ca += popc4(pos);
+      }
+    }
+    cp = __reduce_add_sync(kFull, cp);
+    cn = __reduce_add_sync(kFull, cn);
+    ca = __reduce_add_sync(kFull, ca);
+    if (lane == 0) {
+      if (cp) atomicAdd(a.rows_pos + i, cp);
+      if (cn) atomicAdd(a.rows_neg + i, cn);
+      if (ca) atomicAdd(a.rows_any + i, ca);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------- plain form
+
+// One launch per individual; one row per thread; block counts by __syncthreads_count and one
+// atomic per block and output (the paper's Sec. 2.4 kernel: atomics, no intermediate buffer).
+template <bool NEG>
+__global__ void k_eval_plain(EvalArgs a, const int32_t *__restrict__ cols, int L, int i) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool po = false, ne = false;
+  if (r < a.R) {
+    const int t = threshold(L, a.rnum, a.rden);
+    uint32_t prev = a.keys[(int64_t)cols[0] * a.R_pad + r];
+    int inc = 0, dec = 0;
+    for (int k = 1; k < L; ++k) {
+      const uint32_t cur = a.keys[(int64_t)cols[k] * a.R_pad + r];
+      inc += cur > prev;
+      dec += cur < prev;
+      prev = cur;
+    }
+    po = inc >= t;
+    ne = NEG && dec >= t;
+  }
+  const int np = __syncthreads_count(po);
+  const int nn = __syncthreads_count(ne);
+  const int na = __syncthreads_count(po || ne);
+  if (threadIdx.x == 0) {
+    if (np) atomicAdd(a.rows_pos + i, np);
+    if (nn) atomicAdd(a.rows_neg + i, nn);
+    if (na) atomicAdd(a.rows_any + i, na);
+  }
+}
+
+// ------------------------------------------------------------------------------- fitness
+
+// f = 0 when dead or rows_any < min_rows, else rows_any * 2^min(L, col_cap) (exact uint64).
+__global__ void k_fitness(EvalArgs a, PopView pv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= pv.n) return;
+  const int ra = a.rows_any[i];
+  const bool dead = pv.dead && pv.dead[i];
+  const int L = pv_len(pv, i);
+  const int sh = L < a.col_cap ? L : a.col_cap;
+  a.fitness[i] = (dead || ra < a.min_rows) ? 0ull : ((uint64_t)ra << sh);
+}
+
+int blocks_per_sm_for(const void *kernel) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  return nb < 1 ? 1 : nb;
+}
+
+}  // namespace
+
+cudaError_t launch_validate_csr(const int32_t *cols, const int32_t *off, int32_t n, int32_t C,
+                                int32_t *err, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_validate_csr<<<(n + 255) / 256, 256, 0, s>>>(cols, off, n, C, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fitness(const EvalArgs &a, const PopView &pv, cudaStream_t s) {
+  if (pv.n <= 0 || !a.fitness) return cudaSuccess;
+  k_fitness<<<(pv.n + 255) / 256, 256, 0, s>>>(a, pv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval(int mode, const EvalArgs &a0, const PopView &pv, int num_sms,
+                        cudaStream_t s) {
+  EvalArgs a = a0;
+  cudaError_t e;
+  const size_t nb = (size_t)(pv.n > 0 ? pv.n : 0) * sizeof(int32_t);
+  if ((e = cudaMemsetAsync(a.rows_pos, 0, nb, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.rows_neg, 0, nb, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.rows_any, 0, nb, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+  if (pv.n <= 0) return cudaSuccess;
+  const bool bitmap = (mode == EBIC_MODE_BITMAP);
+  const int64_t passes_total = bitmap ? (a.Wst + 127) / 128 : a.R_pad / 128;
+  const void *kern = bitmap ? (a.neg ? (const void *)k_eval_bitmap<true>
+                                     : (const void *)k_eval_bitmap<false>)
+                            : (a.neg ? (const void *)k_eval_direct<true>
+                                     : (const void *)k_eval_direct<false>);
+  const int bps = blocks_per_sm_for(kern);
+  const int64_t warps = (int64_t)num_sms * bps * kWarps;
+  // Segments: enough work items for ~8 per resident warp, at most 2^30 items in total.
+  int64_t seg = ((int64_t)pv.n * passes_total) / (8 * warps);
+  if (seg < 1) seg = 1;
+  if (seg > passes_total) seg = passes_total;
+  int64_t n_seg = (passes_total + seg - 1) / seg;
+  while ((int64_t)pv.n * n_seg > (1LL << 30)) {
+    seg *= 2;
+    n_seg = (passes_total + seg - 1) / seg;
+  }
+  a.seg_passes = (int32_t)seg;
+  a.n_seg = (int32_t)n_seg;
+  const int64_t items = (int64_t)pv.n * n_seg;
+  int64_t grid = (int64_t)num_sms * bps;
+  const int64_t need = (items + kWarps - 1) / kWarps;
+  if (grid > need) grid = need;
+  if (bitmap) {
+    if (a.neg)
+      k_eval_bitmap<true><<<(unsigned)grid, kThreads, 0, s>>>(a, pv);
+    else
+      k_eval_bitmap<false><<<(unsigned)grid, kThreads, 0, s>>>(a, pv);
+  } else {
+    if (a.neg)
+      k_eval_direct<true><<<(unsigned)grid, kThreads, 0, s>>>(a, pv);
+    else
+      k_eval_direct<false><<<(unsigned)grid, kThreads, 0, s>>>(a, pv);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return launch_fitness(a, pv, s);
+}
+
+cudaError_t launch_eval_plain(const EvalArgs &a, const int32_t *d_cols, int32_t L, int32_t i,
+                              cudaStream_t s) {
+  const unsigned grid = (unsigned)((a.R + 255) / 256);
+  if (a.neg)
+    k_eval_plain<true><<<grid, 256, 0, s>>>(a, d_cols, L, i);
+  else
+    k_eval_plain<false><<<grid, 256, 0, s>>>(a, d_cols, L, i);
+  return cudaGetLastError();
+}

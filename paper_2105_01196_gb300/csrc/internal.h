@@ -1,0 +1,127 @@
+// Internal declarations of the EBIC GB300 library: the context, device buffers, the population
+// view shared by the evaluation kernels, and the host launchers each .cu file provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ebic.h"
+
+#define EBIC_CHECK_CUDA(ctx, call)                                                    \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) return ebic_fail_cuda((ctx), e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define EBIC_TRY(call)          \
+  do {                          \
+    int s_ = (call);            \
+    if (s_ != EBIC_OK) return s_; \
+  } while (0)
+
+// Growable device allocation owned by a context.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= bytes && p) return cudaSuccess;
+    release();
+    if (n == 0) n = 16;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      return e;
+    }
+    bytes = n;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T>
+  T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// Population as the kernels see it: CSR (off != nullptr, len derived) or fixed-stride storage
+// with explicit lengths (off == nullptr).  dead (optional) marks slots that are not scored.
+struct PopView {
+  const int32_t *cols;
+  const int32_t *off;
+  const int32_t *len;
+  const uint8_t *dead;
+  int32_t stride;
+  int32_t n;
+};
+
+// Matrix geometry and the outputs of one evaluation sweep.
+struct EvalArgs {
+  const uint32_t *keys;    // [C][R_pad] order keys
+  const uint32_t *bitmap;  // [C][C][Wst] pair words (bitmap path)
+  int64_t R, R_pad, Wst;   // rows, padded rows, words per column pair (R_pad / 32)
+  int32_t C;
+  int32_t neg, rnum, rden, min_rows, col_cap;
+  int32_t *rows_pos, *rows_neg, *rows_any;  // accumulated with atomics (zeroed first)
+  uint64_t *fitness;
+  int32_t *work;            // dynamic work counter (zeroed first)
+  int32_t seg_passes;       // passes (of 128 words or 128 rows) per work item
+  int32_t n_seg;            // segments per individual
+};
+
+struct ebic_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  std::string err;
+
+  // matrix
+  int64_t R = 0, R_pad = 0, Wst = 0;
+  int32_t C = 0;
+  bool have_matrix = false;
+  DevBuf keys, bitmap, stage_x;
+  bool bitmap_ok = false;
+
+  // scratch for single evaluations
+  DevBuf d_err, d_work, ev_cols, ev_off, ev_out, ev_fit;
+
+  // generation loop state (evolve.cu)
+  struct GenState *gen = nullptr;
+};
+
+int ebic_fail(ebic_ctx *ctx, int code, const std::string &msg);
+int ebic_fail_cuda(ebic_ctx *ctx, cudaError_t e, const char *what, const char *file, int line);
+
+bool ebic_is_device_ptr(const void *p);
+
+// params helpers (abi.cu)
+int ebic_check_eval_params(ebic_ctx *ctx, const ebic_params *p);
+int ebic_check_run_params(ebic_ctx *ctx, const ebic_params *p);
+
+// matrix.cu
+cudaError_t launch_upload(const float *x, int64_t R, int32_t C, int64_t R_pad, int32_t layout,
+                          uint32_t *keys, int32_t *err, cudaStream_t s);
+cudaError_t launch_build_bitmap(const uint32_t *keys, int64_t R_pad, int32_t C, int64_t Wst,
+                                uint32_t *bitmap, cudaStream_t s);
+
+// eval.cu
+cudaError_t launch_validate_csr(const int32_t *cols, const int32_t *off, int32_t n, int32_t C,
+                                int32_t *err, cudaStream_t s);
+// Zeroes the outputs and the work counter, evaluates, writes fitness.
+cudaError_t launch_eval(int mode, const EvalArgs &a, const PopView &pv, int num_sms,
+                        cudaStream_t s);
+// One launch evaluating individual i (columns d_cols[0..L-1] on the device); outputs must be
+// zeroed beforehand.
+cudaError_t launch_eval_plain(const EvalArgs &a, const int32_t *d_cols, int32_t L, int32_t i,
+                              cudaStream_t s);
+cudaError_t launch_fitness(const EvalArgs &a, const PopView &pv, cudaStream_t s);
+int choose_mode(const ebic_ctx *ctx, int requested, int64_t n_ind, double mean_len,
+                int expected_sweeps);
+
+// evolve.cu
+void gen_state_free(struct GenState *g);

@@ -1,0 +1,335 @@
+"""Python binding of the EBIC GB300 C ABI (include/ebic.h), argument marshalling only.
+
+Every ``ebic_*`` function below has the name and meaning of the C entry point it calls; arrays
+may be numpy arrays (host memory) or torch tensors (host or CUDA memory of the context's device),
+passed by pointer.  All computation happens in the CUDA kernels of ``libebic_gb300.so``: this
+module fails loudly (ImportError) when that library is missing, and never computes a result.
+``Context`` wraps the same calls for convenience.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libebic_gb300.so")
+
+EBIC_OK = 0
+EBIC_EINVAL = -1
+EBIC_ENAN = -2
+EBIC_ENOMEM = -3
+EBIC_ECUDA = -4
+EBIC_ETIMEOUT = -5
+EBIC_ESTATE = -6
+
+MODE_AUTO, MODE_DIRECT, MODE_BITMAP, MODE_PLAIN = 0, 1, 2, 3
+ROW_MAJOR, COL_MAJOR = 0, 1
+MAX_LEN = 64
+
+_ERR_NAMES = {-1: "EBIC_EINVAL", -2: "EBIC_ENAN", -3: "EBIC_ENOMEM", -4: "EBIC_ECUDA",
+              -5: "EBIC_ETIMEOUT", -6: "EBIC_ESTATE"}
+
+
+class EbicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("neg_trends", ctypes.c_int32), ("ratio_num", ctypes.c_int32),
+                ("ratio_den", ctypes.c_int32), ("min_rows", ctypes.c_int32),
+                ("col_cap", ctypes.c_int32), ("overlap_num", ctypes.c_int32),
+                ("overlap_den", ctypes.c_int32), ("n_biclusters", ctypes.c_int32),
+                ("init_min_len", ctypes.c_int32), ("init_max_len", ctypes.c_int32),
+                ("max_len", ctypes.c_int32), ("pop_size", ctypes.c_int32),
+                ("elite", ctypes.c_int32), ("tournament", ctypes.c_int32),
+                ("max_attempts", ctypes.c_int32), ("tabu_hit_limit", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("mode", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
+
+    @classmethod
+    def make(cls, **kw):
+        p = cls()
+        _lib.ebic_default_params(ctypes.byref(p))
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise AttributeError(k)
+            setattr(p, k, int(v))
+        return p
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class RunReport(ctypes.Structure):
+    _fields_ = [("gens_done", ctypes.c_int32), ("stopped", ctypes.c_int32),
+                ("last_hits", ctypes.c_int32), ("n_top", ctypes.c_int32),
+                ("n_evaluated", ctypes.c_int64), ("eval_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
+_VP = ctypes.c_void_p
+_I32, _I64 = ctypes.c_int32, ctypes.c_int64
+
+# name -> (restype, argtypes), mirroring include/ebic.h
+SIGNATURES = {
+    "ebic_default_params": (None, [_VP]),
+    "ebic_version": (ctypes.c_char_p, []),
+    "ebic_create": (ctypes.c_int, [_VP, _I32, _VP]),
+    "ebic_destroy": (ctypes.c_int, [_VP]),
+    "ebic_last_error": (ctypes.c_char_p, [_VP]),
+    "ebic_load_matrix": (ctypes.c_int, [_VP, _VP, _I64, _I32, _I32]),
+    "ebic_build_bitmap": (ctypes.c_int, [_VP]),
+    "ebic_bitmap_bytes": (ctypes.c_int64, [_I64, _I32]),
+    "ebic_copy_bitmap": (ctypes.c_int, [_VP, _VP, _I64]),
+    "ebic_eval_population": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP]),
+    "ebic_run_generations": (ctypes.c_int, [_VP, _VP, _I32, _VP]),
+    "ebic_get_toplist": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "ebic_get_population": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _VP]),
+    "ebic_extract_biclusters": (ctypes.c_int, [_VP, _I32, _VP, _VP]),
+    "ebic_state_bytes": (ctypes.c_int64, [_VP]),
+    "ebic_save_state": (ctypes.c_int, [_VP, _VP, _I64]),
+    "ebic_load_state": (ctypes.c_int, [_VP, _VP, _VP, _I64]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built: run `python -m paper_2105_01196_gb300.build`"
+                          " (the CUDA library is required; there is no fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        if hasattr(lib, name):
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+# ----------------------------------------------------------------------------- marshalling
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def ptr(a):
+    """Address of an array argument: torch tensor, numpy array, ctypes object or None."""
+    if a is None:
+        return None
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if isinstance(a, int):
+        return a
+    return ctypes.addressof(a)
+
+
+def _check(ctx, status):
+    if status != EBIC_OK:
+        msg = _lib.ebic_last_error(ctx).decode() if ctx else ""
+        raise EbicError(status, msg)
+    return status
+
+
+def _as_dtype(a, np_dtype, torch_name):
+    if a is None:
+        return None
+    if _is_torch(a):
+        if str(a.dtype) != f"torch.{torch_name}":
+            raise TypeError(f"expected torch.{torch_name}, got {a.dtype}")
+        return a
+    return np.ascontiguousarray(a, dtype=np_dtype)
+
+
+# ----------------------------------------------------------------------------- the C names
+
+def ebic_version():
+    return _lib.ebic_version().decode()
+
+
+def ebic_default_params():
+    return Params.make()
+
+
+def ebic_create(device=0, stream=None):
+    out = ctypes.c_void_p()
+    _check(None, _lib.ebic_create(ctypes.byref(out), int(device), stream))
+    return out.value
+
+
+def ebic_destroy(ctx):
+    return _lib.ebic_destroy(ctx)
+
+
+def ebic_last_error(ctx):
+    return _lib.ebic_last_error(ctx).decode()
+
+
+def ebic_load_matrix(ctx, x, layout=ROW_MAJOR):
+    x = _as_dtype(x, np.float32, "float32")
+    if layout == ROW_MAJOR:
+        rows, cols = x.shape
+    else:
+        cols, rows = x.shape
+    _check(ctx, _lib.ebic_load_matrix(ctx, ptr(x), int(rows), int(cols), int(layout)))
+
+
+def ebic_build_bitmap(ctx):
+    _check(ctx, _lib.ebic_build_bitmap(ctx))
+
+
+def ebic_bitmap_bytes(rows, cols):
+    return int(_lib.ebic_bitmap_bytes(int(rows), int(cols)))
+
+
+def ebic_copy_bitmap(ctx, out):
+    _check(ctx, _lib.ebic_copy_bitmap(ctx, ptr(out), int(out.numel() if _is_torch(out) else out.size)))
+    return out
+
+
+def ebic_eval_population(ctx, col_idx, offsets, params, rows_pos=None, rows_neg=None,
+                         rows_any=None, fitness=None):
+    """Evaluates a CSR population.  With no outputs given, returns four new numpy arrays."""
+    col_idx = _as_dtype(col_idx, np.int32, "int32")
+    offsets = _as_dtype(offsets, np.int32, "int32")
+    n = (offsets.numel() if _is_torch(offsets) else offsets.size) - 1
+    if rows_pos is None and rows_neg is None and rows_any is None and fitness is None:
+        rows_pos = np.zeros(n, np.int32)
+        rows_neg = np.zeros(n, np.int32)
+        rows_any = np.zeros(n, np.int32)
+        fitness = np.zeros(n, np.uint64)
+    _check(ctx, _lib.ebic_eval_population(ctx, ptr(col_idx), ptr(offsets), int(n),
+                                          ctypes.byref(params), ptr(rows_pos), ptr(rows_neg),
+                                          ptr(rows_any), ptr(fitness)))
+    return rows_pos, rows_neg, rows_any, fitness
+
+
+def ebic_run_generations(ctx, params, n_gen):
+    rep = RunReport()
+    _check(ctx, _lib.ebic_run_generations(ctx, ctypes.byref(params), int(n_gen),
+                                          ctypes.byref(rep)))
+    return rep
+
+
+def ebic_get_toplist(ctx, capacity=256):
+    cols = np.zeros((capacity, MAX_LEN), np.int32)
+    lens = np.zeros(capacity, np.int32)
+    fit = np.zeros(capacity, np.uint64)
+    keys = np.zeros(capacity, np.uint64)
+    rows = np.zeros((capacity, 3), np.int32)
+    n = ctypes.c_int32()
+    _check(ctx, _lib.ebic_get_toplist(ctx, capacity, ctypes.byref(n), ptr(cols), ptr(lens),
+                                      ptr(fit), ptr(keys), ptr(rows)))
+    k = n.value
+    return [dict(cols=tuple(int(c) for c in cols[e, :lens[e]]), f=int(fit[e]), h=int(keys[e]),
+                 rows_pos=int(rows[e, 0]), rows_neg=int(rows[e, 1]), rows_any=int(rows[e, 2]))
+            for e in range(k)]
+
+
+def ebic_get_population(ctx, pop_size):
+    cols = np.zeros((pop_size, MAX_LEN), np.int32)
+    lens = np.zeros(pop_size, np.int32)
+    dead = np.zeros(pop_size, np.uint8)
+    fit = np.zeros(pop_size, np.uint64)
+    _check(ctx, _lib.ebic_get_population(ctx, pop_size, ptr(cols), ptr(lens), ptr(dead), ptr(fit)))
+    return cols, lens, dead, fit
+
+
+def ebic_extract_biclusters(ctx, rows, capacity=256):
+    w = ((int(rows) + 127) // 128) * 4
+    masks = np.zeros((capacity, w), np.uint32)
+    n = ctypes.c_int32()
+    _check(ctx, _lib.ebic_extract_biclusters(ctx, capacity, ptr(masks), ctypes.byref(n)))
+    return masks[:n.value]
+
+
+def ebic_state_bytes(ctx):
+    return int(_lib.ebic_state_bytes(ctx))
+
+
+def ebic_save_state(ctx):
+    size = ebic_state_bytes(ctx)
+    if size <= 0:
+        raise EbicError(EBIC_ESTATE, ebic_last_error(ctx))
+    blob = np.zeros(size, np.uint8)
+    _check(ctx, _lib.ebic_save_state(ctx, ptr(blob), size))
+    return blob
+
+
+def ebic_load_state(ctx, params, blob):
+    blob = np.ascontiguousarray(blob, np.uint8)
+    _check(ctx, _lib.ebic_load_state(ctx, ctypes.byref(params), ptr(blob), int(blob.size)))
+
+
+class Context:
+    """One EBIC job on one GPU: owns the C context (see ebic_create)."""
+
+    def __init__(self, device=0, stream=None):
+        self.handle = ebic_create(device, stream)
+
+    def close(self):
+        if self.handle:
+            ebic_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_matrix(self, x, layout=ROW_MAJOR):
+        ebic_load_matrix(self.handle, x, layout)
+
+    def build_bitmap(self):
+        ebic_build_bitmap(self.handle)
+
+    def copy_bitmap(self, out):
+        return ebic_copy_bitmap(self.handle, out)
+
+    def eval_population(self, col_idx, offsets, params, *outs):
+        return ebic_eval_population(self.handle, col_idx, offsets, params, *outs)
+
+    def run_generations(self, params, n_gen):
+        return ebic_run_generations(self.handle, params, n_gen)
+
+    def toplist(self, capacity=256):
+        return ebic_get_toplist(self.handle, capacity)
+
+    def population(self, pop_size):
+        return ebic_get_population(self.handle, pop_size)
+
+    def extract_biclusters(self, rows, capacity=256):
+        return ebic_extract_biclusters(self.handle, rows, capacity)
+
+    def save_state(self):
+        return ebic_save_state(self.handle)
+
+    def load_state(self, params, blob):
+        ebic_load_state(self.handle, params, blob)
+
+    def last_error(self):
+        return ebic_last_error(self.handle)

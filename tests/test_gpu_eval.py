@@ -1,0 +1,198 @@
+"""GPU parity of population evaluation against the CPU oracle, through the C ABI.
+
+Bar: bit-exact (counts and fitness are integers; comparisons of float32 values are exact on both
+sides), for every evaluation form (direct, bitmap, plain one-launch-per-individual, auto)."""
+
+import numpy as np
+import pytest
+
+from oracle import counts as ocounts
+from oracle.bitmap import pair_bitmap
+from oracle.params import Params as OParams
+from paper_2105_01196_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+MODES = (1, 2, 3, 0)  # direct, bitmap, plain, auto
+
+
+@pytest.fixture(scope="module")
+def ebic():
+    from paper_2105_01196_gb300 import ebic as e
+    return e
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def oparams(neg, num, den, min_rows=2, col_cap=10):
+    return OParams(neg_trends=neg, ratio_num=num, ratio_den=den, min_rows=min_rows,
+                   col_cap=col_cap)
+
+
+def oracle_eval(x, col_idx, offsets, neg, num, den, sample=None, min_rows=2, col_cap=10):
+    p = oparams(neg, num, den, min_rows, col_cap)
+    n = len(offsets) - 1
+    idx = range(n) if sample is None else sample
+    out = {}
+    for i in idx:
+        cols = [int(c) for c in col_idx[offsets[i]:offsets[i + 1]]]
+        out[i] = ocounts.eval_individual(x, cols, p)
+    return out
+
+
+def assert_parity(got, want):
+    rp, rn, ra, f = (np.asarray(a) for a in got)
+    for i, (wp, wn, wa, wf) in want.items():
+        assert (int(rp[i]), int(rn[i]), int(ra[i]), int(f[i])) == (wp, wn, wa, wf), \
+            f"individual {i}: got {(rp[i], rn[i], ra[i], f[i])} want {(wp, wn, wa, wf)}"
+
+
+def test_tiny_workload_all_modes(ebic):
+    x, _, ci, off = synth.workload_inputs(synth.WORKLOADS["tiny"])
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        for neg in (0, 1):
+            for num, den in ((1, 1), (85, 100), (1, 2)):
+                want = oracle_eval(x, ci, off, neg, num, den)
+                for mode in MODES:
+                    p = ebic.Params.make(neg_trends=neg, ratio_num=num, ratio_den=den, mode=mode)
+                    assert_parity(ctx.eval_population(ci, off, p), want)
+
+
+def ragged_population(g, n, C, lens=None):
+    if lens is None:
+        lens = g.integers(2, min(64, C) + 1, size=n)
+    lens = np.asarray(lens)
+    off = np.zeros(len(lens) + 1, np.int32)
+    off[1:] = np.cumsum(lens)
+    ci = np.concatenate([g.choice(C, size=int(L), replace=False) for L in lens]).astype(np.int32)
+    return ci, off
+
+
+@pytest.mark.parametrize("R,C", [(1, 2), (31, 3), (32, 17), (33, 64), (127, 65), (129, 7),
+                                 (1000, 20), (4097, 40)])
+def test_ragged_shapes_ties_and_zeros(ebic, R, C):
+    g = np.random.default_rng(R * 1000 + C)
+    x = (g.integers(-2, 3, size=(R, C)) * 0.5).astype(np.float32)
+    x[g.random((R, C)) < 0.05] = -0.0
+    x[g.random((R, C)) < 0.02] = np.float32(1e-42)
+    lens = [2, min(64, C)] + list(g.integers(2, min(64, C) + 1, size=40))
+    ci, off = ragged_population(g, len(lens), C, lens)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        for neg, num, den in ((1, 1, 1), (1, 85, 100), (0, 2, 3)):
+            want = oracle_eval(x, ci, off, neg, num, den, min_rows=0)
+            for mode in MODES:
+                p = ebic.Params.make(neg_trends=neg, ratio_num=num, ratio_den=den, mode=mode,
+                                     min_rows=0)
+                assert_parity(ctx.eval_population(ci, off, p), want)
+
+
+def test_default_workload_full_parity(ebic):
+    w = synth.WORKLOADS["default"]
+    x, _, ci, off = synth.workload_inputs(w)
+    want = oracle_eval(x, ci, off, 1, 85, 100)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        for mode in MODES:
+            p = ebic.Params.make(neg_trends=1, ratio_num=85, ratio_den=100, mode=mode)
+            assert_parity(ctx.eval_population(ci, off, p), want)
+
+
+@pytest.mark.parametrize("name,n_sample", [("batched", 160), ("tieheavy", 48)])
+def test_large_workloads_sampled(ebic, name, n_sample):
+    w = synth.WORKLOADS[name]
+    x, _, ci, off = synth.workload_inputs(w)
+    g = np.random.default_rng(5)
+    n = len(off) - 1
+    lens = np.diff(off)
+    sample = sorted(set(g.choice(n, size=n_sample, replace=False).tolist())
+                    | {int(np.argmax(lens)), int(np.argmin(lens)), n - 1})
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        for neg, num, den in ((1, 85, 100), (1, 1, 1)):
+            want = oracle_eval(x, ci, off, neg, num, den, sample=sample)
+            for mode in (1, 2):
+                p = ebic.Params.make(neg_trends=neg, ratio_num=num, ratio_den=den, mode=mode)
+                assert_parity(ctx.eval_population(ci, off, p), want)
+
+
+def test_device_pointers_and_col_major(ebic, torch_cuda):
+    torch = torch_cuda
+    g = np.random.default_rng(9)
+    x = g.standard_normal((5000, 30)).astype(np.float32)
+    ci, off = ragged_population(g, 300, 30)
+    want = oracle_eval(x, ci, off, 1, 85, 100)
+    dev = torch.device("cuda:0")
+    with ebic.Context(0, torch.cuda.current_stream().cuda_stream) as ctx:
+        for layout, xin in ((ebic.ROW_MAJOR, torch.from_numpy(x).to(dev)),
+                            (ebic.COL_MAJOR, torch.from_numpy(np.ascontiguousarray(x.T)).to(dev)),
+                            (ebic.COL_MAJOR, np.ascontiguousarray(x.T))):
+            ctx.load_matrix(xin, layout)
+            for mode in (1, 2, 3):
+                p = ebic.Params.make(neg_trends=1, ratio_num=85, ratio_den=100, mode=mode)
+                outs = [torch.zeros(300, dtype=torch.int32, device=dev) for _ in range(3)]
+                outs.append(torch.zeros(300, dtype=torch.int64, device=dev))
+                ctx.eval_population(torch.from_numpy(ci).to(dev), torch.from_numpy(off).to(dev),
+                                    p, *outs)
+                got = [o.cpu().numpy() for o in outs]
+                assert_parity(got, want)
+
+
+def test_bitmap_matches_oracle_definition(ebic):
+    g = np.random.default_rng(11)
+    for R, C in ((77, 7), (300, 20), (1030, 9)):
+        x = g.integers(0, 5, size=(R, C)).astype(np.float32)
+        want = pair_bitmap(x)                       # [C][C][ceil(R/32)]
+        with ebic.Context(0) as ctx:
+            ctx.load_matrix(x)
+            ctx.build_bitmap()
+            wst = ((R + 127) // 128) * 4
+            out = np.zeros(C * C * wst, np.uint32)
+            ctx.copy_bitmap(out)
+            got = out.reshape(C, C, wst)
+            W = want.shape[2]
+            assert np.array_equal(got[:, :, :W], want)
+            assert not got[:, :, W:].any()
+
+
+def test_errors_are_reported(ebic, torch_cuda):
+    torch = torch_cuda
+    x = np.ones((10, 4), np.float32)
+    with ebic.Context(0) as ctx:
+        p = ebic.Params.make()
+        with pytest.raises(ebic.EbicError) as e:
+            ctx.eval_population(np.array([0, 1], np.int32), np.array([0, 2], np.int32), p)
+        assert e.value.code == ebic.EBIC_ESTATE
+        for bad in (np.nan, np.inf, -np.inf):
+            y = x.copy()
+            y[3, 2] = bad
+            with pytest.raises(ebic.EbicError) as e:
+                ctx.load_matrix(y)
+            assert e.value.code == ebic.EBIC_ENAN
+        ctx.load_matrix(x)
+        bad_pops = [([0, 0], [0, 2]), ([0], [0, 1]), ([0, 4], [0, 2]), ([-1, 2], [0, 2]),
+                    (list(range(4)) * 17, [0, 68])]
+        for cols, offs in bad_pops:
+            for dev in (False, True):
+                c = np.array(cols, np.int32)
+                o = np.array(offs, np.int32)
+                if dev:
+                    c, o = torch.from_numpy(c).cuda(), torch.from_numpy(o).cuda()
+                with pytest.raises(ebic.EbicError) as e:
+                    ctx.eval_population(c, o, p)
+                assert e.value.code == ebic.EBIC_EINVAL
+        with pytest.raises(ebic.EbicError) as e:
+            ctx.eval_population(np.array([0, 1], np.int32), np.array([0, 2], np.int32),
+                                ebic.Params.make(ratio_num=0))
+        assert e.value.code == ebic.EBIC_EINVAL
+        r = ctx.eval_population(np.zeros(0, np.int32), np.zeros(1, np.int32), p)
+        assert all(len(a) == 0 for a in r)
+        # the context stays usable after every error
+        r = ctx.eval_population(np.array([0, 1], np.int32), np.array([0, 2], np.int32), p)
+        assert int(r[2][0]) == 0
