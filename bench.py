@@ -1,0 +1,320 @@
+"""EBIC population-evaluation benchmark on GB300.
+
+One step = one pass of the whole hot path over one synthetic workload, through the C ABI:
+  matrix upload (order keys) -> pair-bitmap build (when the autotuner picks the bitmap form)
+  -> full evaluation of the workload's population -> the EBIC generation loop (initial
+  population + `--gens` generations, graph-replayed) -> bicluster extraction of the top list.
+The metric is (individual, row) trend evaluations per second over the step; generations per
+second are reported beside it.  Default workload: 10,000 x 100 float32, population 800, lengths
+2-20, approximate ratio 0.85, negative trends, 100 generations.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload default|tiny|batched|tieheavy] [--gens G] [--mode auto|...]
+Multi-GPU (torchrun): every rank runs an independent job (its own seed) on its own GPU; the
+value is all ranks' evaluations divided by the slowest rank's time ("weak" scaling).
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "individual·row trend evaluations/sec and EBIC generations/sec vs plain GPU form"
+UNIT = "evals/s"
+MODES = {"auto": 0, "direct": 1, "bitmap": 2, "plain": 3}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="default")
+    ap.add_argument("--gens", type=int, default=None, help="generations per step")
+    ap.add_argument("--mode", default="auto", choices=list(MODES))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local, dist
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples taken while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(w, x, ci, off, seconds):
+    """The CPU oracle as it stands, single-threaded, on a bounded sample of the workload: full
+    trend counts of the first individuals of the workload's population until `seconds` pass."""
+    from oracle import counts as ocounts
+    from oracle.params import Params as OParams
+    p = OParams(neg_trends=w.neg_trends, ratio_num=w.ratio[0], ratio_den=w.ratio[1])
+    n = len(off) - 1
+    t0 = time.perf_counter()
+    done = 0
+    while done < n and time.perf_counter() - t0 < seconds:
+        cols = [int(c) for c in ci[off[done]:off[done + 1]]]
+        ocounts.eval_individual(x, cols, p)
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": done * x.shape[0] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle trend counts of {done} of {n} individuals x {x.shape[0]} rows "
+                      f"({dt:.1f} s, single thread)"}
+
+
+def run_reference(args, w, world, rank, dist):
+    """Reference arm: the CPU oracle on the host cores, each step a bounded sample."""
+    from paper_2105_01196_gb300 import synth
+    if rank != 0:
+        return
+    x, _, ci, off = synth.workload_inputs(w)
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(w, x, ci, off, per_step / 4)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(w, x, ci, off, per_step)
+        vals.append(last["value"])
+    total = time.perf_counter() - t0
+    v = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32-compare/int32",
+            "data": "synthetic", "config": {"workload": w.name, "rows": w.rows, "cols": w.cols,
+                                             "pop": w.pop, "len": [w.len_lo, w.len_hi],
+                                             "ratio": list(w.ratio), "neg_trends": w.neg_trends},
+            "cpu_baseline": dict(last, value=v),
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local, dist = dist_setup(args)
+    from paper_2105_01196_gb300 import synth
+    import dataclasses
+    w = dataclasses.replace(synth.WORKLOADS[args.workload])
+    if args.impl == "reference":
+        run_reference(args, w, world, rank, dist)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    import torch
+    from paper_2105_01196_gb300 import ebic
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    w = dataclasses.replace(w, seed=w.seed + 7919 * rank)
+    gens = w.generations if args.gens is None else args.gens
+    x, truth, ci, off = synth.workload_inputs(w)
+    R = w.rows
+    x_d = torch.from_numpy(x).to(dev)
+    ci_d = torch.from_numpy(ci).to(dev)
+    off_d = torch.from_numpy(off).to(dev)
+    P = len(off) - 1
+    outs_d = [torch.zeros(P, dtype=torch.int32, device=dev) for _ in range(3)]
+    outs_d.append(torch.zeros(P, dtype=torch.int64, device=dev))
+    x_h = torch.from_numpy(x).pin_memory()
+    outs_h = [torch.zeros(P, dtype=torch.int32).pin_memory() for _ in range(3)]
+    outs_h.append(torch.zeros(P, dtype=torch.int64).pin_memory())
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    params = ebic.Params.make(neg_trends=w.neg_trends, ratio_num=w.ratio[0],
+                              ratio_den=w.ratio[1], pop_size=w.pop, max_len=min(w.len_hi, 64),
+                              init_min_len=w.len_lo, init_max_len=min(w.len_hi, 64),
+                              n_biclusters=max(10, w.n_bic), elite=max(10, w.n_bic),
+                              tabu_hit_limit=0, seed=w.seed, mode=MODES[args.mode])
+    ctx = ebic.Context(local, stream.cuda_stream)
+
+    def step(host):
+        """One pass of the hot path; returns (individual,row) evaluations done."""
+        units = 0
+        if host:
+            ctx.load_matrix(x_h)
+            ctx.eval_population(ci, off, params, *outs_h)
+        else:
+            ctx.load_matrix(x_d)
+            ctx.eval_population(ci_d, off_d, params, *outs_d)
+        units += P * R
+        if gens > 0:
+            rep = ctx.run_generations(params, gens)
+            units += int(rep.n_evaluated) * R
+            masks = ctx.extract_biclusters(R)
+            units += len(masks) * R
+        return units
+
+    for _ in range(max(3, args.warmup)):
+        step(False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.profile_enable(True)
+    total_ms = 0.0
+    units = 0
+    for _ in range(args.steps):
+        flush.zero_()                       # L2 flush between timed steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        units += step(False)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    st_eval = ctx.profile_read(ebic.KERNEL_EVAL)
+    st_all = ctx.profile_read(ebic.KERNEL_ALL)
+    st_build = ctx.profile_read(ebic.KERNEL_BITMAP_BUILD)
+    ctx.profile_enable(False)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        u = torch.tensor([float(units)], device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        units = float(u.item())
+        dist.barrier()
+
+    e2e = None
+    if not args.no_e2e:
+        # End to end through the same C ABI with host buffers: the copies run inside the calls.
+        torch.cuda.synchronize()
+        e2e_units = 0
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_units += step(True)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        h2d = x.nbytes + ci.nbytes + off.nbytes
+        d2h = sum(o.numel() * o.element_size() for o in outs_h)
+        if gens > 0:
+            d2h += 256 * ((R + 127) // 128) * 16
+        e2e = {"value": e2e_units / e2e_s * (world if dist else 1), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = load_peaks()
+    roof = None
+    if st_eval["timed_launches"] > 0:
+        n_l = st_eval["timed_launches"]
+        avg_s = st_eval["ms"] / n_l / 1e3
+        per_launch = st_eval["alg_bytes"] / n_l
+        achieved = per_launch / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_eval_bitmap",
+                "peak_kind": peak_kind, "alg_bytes_per_launch": per_launch,
+                "avg_launch_us": avg_s * 1e6, "launches": n_l}
+    line = {"metric": METRIC, "value": units / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32-compare/int32", "data": "synthetic",
+            "config": {"workload": w.name, "rows": w.rows, "cols": w.cols, "pop": w.pop,
+                       "len": [w.len_lo, w.len_hi], "ratio": list(w.ratio),
+                       "neg_trends": w.neg_trends, "generations": gens, "mode": args.mode,
+                       "l2": "flushed between steps (512 MB write)",
+                       "parallelism": f"independent job per GPU x{world}"},
+            "gpu_launches": int(st_all["launches"]),
+            "roofline": roof,
+            "kernels": {"eval": st_eval, "bitmap_build": st_build},
+            "clocks": clk,
+            "e2e": e2e}
+    if gens > 0:
+        line["generations_per_s"] = gens * args.steps / (total_ms / 1e3)
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, x, ci, off, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

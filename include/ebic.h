@@ -237,6 +237,36 @@ EBIC_API int64_t ebic_state_bytes(ebic_ctx *ctx);
 EBIC_API int ebic_save_state(ebic_ctx *ctx, void *blob, int64_t size);
 EBIC_API int ebic_load_state(ebic_ctx *ctx, const ebic_params *p, const void *blob, int64_t size);
 
+/*
+ * Kernel statistics for roofline accounting (no counterpart in the paper).  While enabled, the
+ * context records CUDA events on its stream around every launch of the evaluation kernel and of
+ * the bitmap build, and counts every kernel it launches (graph replays included).
+ *   kernel  EBIC_KERNEL_EVAL (direct or bitmap evaluation), EBIC_KERNEL_BITMAP_BUILD, or
+ *           EBIC_KERNEL_ALL (launches only).
+ *   ms         summed event time of the timed launches;
+ *   alg_bytes  algorithmic bytes of those launches: the bitmap form reads sum_i (L_i - 1) pair
+ *              words per 32 rows and direction, the direct form gathers sum_i L_i keys per row,
+ *              the build writes cols^2 words per 32 rows;
+ *   alg_ops    algorithmic comparisons: sum_i (L_i - 1) * rows per direction;
+ *   units      (individual, row) evaluations.
+ * ebic_profile_enable(ctx, 1) resets the counters; 0 stops recording.
+ */
+#define EBIC_KERNEL_EVAL 0
+#define EBIC_KERNEL_BITMAP_BUILD 1
+#define EBIC_KERNEL_ALL 2
+
+typedef struct ebic_kernel_stats {
+  int64_t launches;
+  int64_t timed_launches;
+  double ms;
+  double alg_bytes;
+  double alg_ops;
+  double units;
+} ebic_kernel_stats;
+
+EBIC_API int ebic_profile_enable(ebic_ctx *ctx, int32_t on);
+EBIC_API int ebic_profile_read(ebic_ctx *ctx, int32_t kernel, ebic_kernel_stats *out);
+
 #ifdef __cplusplus
 }
 #endif

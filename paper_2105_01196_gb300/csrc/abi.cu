@@ -79,7 +79,112 @@ int ebic_check_eval_params(ebic_ctx *ctx, const ebic_params *p) {
   return EBIC_OK;
 }
 
+cudaEvent_t prof_event(ebic_ctx *ctx) {
+  if (!ctx->prof) return nullptr;
+  cudaEvent_t e = nullptr;
+  if (!ctx->ev_pool.empty()) {
+    e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+void prof_push(ebic_ctx *ctx, cudaEvent_t a, cudaEvent_t b, int kernel, double bytes, double ops,
+               double units) {
+  if (a && b) {
+    ctx->pending.push_back(PendingTiming{a, b, kernel, bytes, ops, units});
+  } else {
+    if (a) ctx->ev_pool.push_back(a);
+    if (b) ctx->ev_pool.push_back(b);
+  }
+}
+
+cudaEvent_t prof_begin(ebic_ctx *ctx) {
+  if (!ctx->prof) return nullptr;
+  cudaEvent_t e = nullptr;
+  if (!ctx->ev_pool.empty()) {
+    e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaEventRecord(e, ctx->stream);
+  return e;
+}
+
+void prof_end(ebic_ctx *ctx, cudaEvent_t a, int kernel, double bytes, double ops, double units) {
+  if (!a) return;
+  cudaEvent_t b = nullptr;
+  if (!ctx->ev_pool.empty()) {
+    b = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+  } else if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ev_pool.push_back(a);
+    return;
+  }
+  cudaEventRecord(b, ctx->stream);
+  ctx->pending.push_back(PendingTiming{a, b, kernel, bytes, ops, units});
+}
+
+void prof_count(ebic_ctx *ctx, int kernel, int64_t n) {
+  if (kernel >= 0 && kernel < 2) ctx->kst[kernel].launches += n;
+  ctx->kst[EBIC_KERNEL_ALL].launches += n;
+}
+
+void prof_collect(ebic_ctx *ctx) {
+  for (const PendingTiming &t : ctx->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+      KStats &k = ctx->kst[t.kernel];
+      k.timed += 1;
+      k.ms += ms;
+      k.bytes += t.bytes;
+      k.ops += t.ops;
+      k.units += t.units;
+    } else {
+      cudaGetLastError();
+    }
+    ctx->ev_pool.push_back(t.a);
+    ctx->ev_pool.push_back(t.b);
+  }
+  ctx->pending.clear();
+}
+
 extern "C" {
+
+int ebic_profile_enable(ebic_ctx *ctx, int32_t on) {
+  if (!ctx) return EBIC_EINVAL;
+  DeviceGuard g(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  cudaGetLastError();
+  prof_collect(ctx);
+  if (on) {
+    for (KStats &k : ctx->kst) k = KStats();
+  }
+  ctx->prof = on != 0;
+  return EBIC_OK;
+}
+
+int ebic_profile_read(ebic_ctx *ctx, int32_t kernel, ebic_kernel_stats *out) {
+  if (!ctx || !out || kernel < 0 || kernel > 2) return EBIC_EINVAL;
+  DeviceGuard g(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  cudaGetLastError();
+  prof_collect(ctx);
+  const KStats &k = ctx->kst[kernel];
+  out->launches = k.launches;
+  out->timed_launches = k.timed;
+  out->ms = k.ms;
+  out->alg_bytes = k.bytes;
+  out->alg_ops = k.ops;
+  out->units = k.units;
+  return EBIC_OK;
+}
 
 const char *ebic_version(void) { return "ebic-gb300 0.1 (sm_103a)"; }
 
@@ -154,6 +259,8 @@ int ebic_destroy(ebic_ctx *ctx) {
   DevBuf *bufs[] = {&ctx->keys, &ctx->bitmap, &ctx->stage_x, &ctx->d_err, &ctx->d_work,
                     &ctx->ev_cols, &ctx->ev_off, &ctx->ev_out, &ctx->ev_fit};
   for (DevBuf *b : bufs) b->release();
+  prof_collect(ctx);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return EBIC_OK;
@@ -193,6 +300,7 @@ int ebic_load_matrix(ebic_ctx *ctx, const float *x, int64_t rows, int32_t cols, 
   EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(ctx->d_err.p, 0, sizeof(int32_t), ctx->stream));
   EBIC_CHECK_CUDA(ctx, launch_upload(src, rows, cols, R_pad, layout, ctx->keys.as<uint32_t>(),
                                      ctx->d_err.as<int32_t>(), ctx->stream));
+  prof_count(ctx, -1, 1);
   int32_t herr = 0;
   EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&herr, ctx->d_err.p, sizeof(int32_t),
                                        cudaMemcpyDeviceToHost, ctx->stream));
@@ -214,9 +322,14 @@ int ebic_build_bitmap(ebic_ctx *ctx) {
   DeviceGuard g(ctx->device);
   const size_t bytes = (size_t)ebic_bitmap_bytes(ctx->R, ctx->C);
   EBIC_CHECK_CUDA(ctx, ctx->bitmap.ensure(bytes));
+  cudaEvent_t ev = prof_begin(ctx);
   EBIC_CHECK_CUDA(ctx, launch_build_bitmap(ctx->keys.as<uint32_t>(), ctx->R_pad, ctx->C, ctx->Wst,
                                            ctx->bitmap.as<uint32_t>(), ctx->stream));
+  prof_end(ctx, ev, EBIC_KERNEL_BITMAP_BUILD, (double)bytes,
+           (double)ctx->C * ctx->C * (double)ctx->R, 0.0);
+  prof_count(ctx, EBIC_KERNEL_BITMAP_BUILD, 1);
   EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  prof_collect(ctx);
   ctx->bitmap_ok = true;
   return EBIC_OK;
 }
@@ -293,6 +406,7 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
     EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(ctx->d_err.p, 0, sizeof(int32_t), s));
     EBIC_CHECK_CUDA(ctx, launch_validate_csr(col_idx, offsets, n_ind, ctx->C,
                                              ctx->d_err.as<int32_t>(), s));
+    prof_count(ctx, -1, 1);
     int32_t herr = 0;
     int32_t ends[2] = {0, 0};
     EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&herr, ctx->d_err.p, 4, cudaMemcpyDeviceToHost, s));
@@ -333,13 +447,26 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
   a.work = ctx->d_work.as<int32_t>();
   PopView pv{d_cols, d_off, nullptr, nullptr, 0, n_ind};
 
+  const double pairs = (double)(total - n_ind), nd = a.neg ? 2.0 : 1.0;
+  const double ev_bytes = (mode == EBIC_MODE_BITMAP) ? pairs * (double)ctx->Wst * 4.0 * nd
+                                                     : (double)total * (double)ctx->R_pad * 4.0;
+  const double ev_ops = pairs * (double)ctx->R * nd, ev_units = (double)n_ind * (double)ctx->R;
   if (mode == EBIC_MODE_PLAIN) {
     EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(a.rows_pos, 0, (size_t)n_ind * 3 * 4, s));
+    cudaEvent_t ev = prof_begin(ctx);
     for (int32_t i = 0; i < n_ind; ++i)
       EBIC_CHECK_CUDA(ctx, launch_eval_plain(a, d_cols + h_off[i], h_off[i + 1] - h_off[i], i, s));
+    prof_end(ctx, ev, EBIC_KERNEL_EVAL, (double)total * (double)ctx->R_pad * 4.0, ev_ops,
+             ev_units);
+    prof_count(ctx, EBIC_KERNEL_EVAL, n_ind);
     EBIC_CHECK_CUDA(ctx, launch_fitness(a, pv, s));
+    prof_count(ctx, -1, 1);
   } else {
-    EBIC_CHECK_CUDA(ctx, launch_eval(mode, a, pv, ctx->num_sms, s));
+    cudaEvent_t e0 = prof_event(ctx), e1 = prof_event(ctx);
+    EBIC_CHECK_CUDA(ctx, launch_eval(mode, a, pv, ctx->num_sms, s, e0, e1));
+    prof_push(ctx, e0, e1, EBIC_KERNEL_EVAL, ev_bytes, ev_ops, ev_units);
+    prof_count(ctx, EBIC_KERNEL_EVAL, 1);
+    prof_count(ctx, -1, 1);
   }
   int32_t *dsts[3] = {rows_pos, rows_neg, rows_any};
   for (int k = 0; k < 3; ++k)
@@ -350,6 +477,7 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
     EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(fitness, a.fitness, (size_t)n_ind * 8,
                                          cudaMemcpyDefault, s));
   EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(s));
+  prof_collect(ctx);
   return EBIC_OK;
 }
 

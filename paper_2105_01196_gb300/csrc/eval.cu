@@ -375,7 +375,7 @@ cudaError_t launch_fitness(const EvalArgs &a, const PopView &pv, cudaStream_t s)
 }
 
 cudaError_t launch_eval(int mode, const EvalArgs &a0, const PopView &pv, int num_sms,
-                        cudaStream_t s) {
+                        cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
   EvalArgs a = a0;
   cudaError_t e;
   const size_t nb = (size_t)(pv.n > 0 ? pv.n : 0) * sizeof(int32_t);
@@ -383,7 +383,11 @@ cudaError_t launch_eval(int mode, const EvalArgs &a0, const PopView &pv, int num
   if ((e = cudaMemsetAsync(a.rows_neg, 0, nb, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(a.rows_any, 0, nb, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
-  if (pv.n <= 0) return cudaSuccess;
+  if (pv.n <= 0) {
+    if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
+    if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return e;
+    return cudaSuccess;
+  }
   const bool bitmap = (mode == EBIC_MODE_BITMAP);
   const int64_t passes_total = bitmap ? (a.Wst + 127) / 128 : a.R_pad / 128;
   const void *kern = bitmap ? (a.neg ? (const void *)k_eval_bitmap<true>
@@ -407,6 +411,7 @@ cudaError_t launch_eval(int mode, const EvalArgs &a0, const PopView &pv, int num
   int64_t grid = (int64_t)num_sms * bps;
   const int64_t need = (items + kWarps - 1) / kWarps;
   if (grid > need) grid = need;
+  if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
   if (bitmap) {
     if (a.neg)
       k_eval_bitmap<true><<<(unsigned)grid, kThreads, 0, s>>>(a, pv);
@@ -419,6 +424,7 @@ cudaError_t launch_eval(int mode, const EvalArgs &a0, const PopView &pv, int num
       k_eval_direct<false><<<(unsigned)grid, kThreads, 0, s>>>(a, pv);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return e;
   return launch_fitness(a, pv, s);
 }
 

@@ -73,6 +73,18 @@ struct EvalArgs {
   int32_t n_seg;            // segments per individual
 };
 
+// Kernel statistics (ebic_profile_*): launches counted always, event pairs while enabled.
+struct KStats {
+  int64_t launches = 0, timed = 0;
+  double ms = 0, bytes = 0, ops = 0, units = 0;
+};
+
+struct PendingTiming {
+  cudaEvent_t a, b;
+  int kernel;
+  double bytes, ops, units;
+};
+
 struct ebic_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -92,7 +104,26 @@ struct ebic_ctx {
 
   // generation loop state (evolve.cu)
   struct GenState *gen = nullptr;
+
+  // profiling
+  bool prof = false;
+  KStats kst[3];
+  std::vector<PendingTiming> pending;
+  std::vector<cudaEvent_t> ev_pool;
 };
+
+// An event from the context's pool (nullptr when not profiling), and queuing a recorded pair.
+cudaEvent_t prof_event(ebic_ctx *ctx);
+void prof_push(ebic_ctx *ctx, cudaEvent_t a, cudaEvent_t b, int kernel, double bytes, double ops,
+               double units);
+// Records an event on the context stream before a timed launch (nullptr when not profiling).
+cudaEvent_t prof_begin(ebic_ctx *ctx);
+// Records the closing event and queues the pair with its algorithmic work.
+void prof_end(ebic_ctx *ctx, cudaEvent_t a, int kernel, double bytes, double ops, double units);
+// Counts launches of `kernel` (and of EBIC_KERNEL_ALL).
+void prof_count(ebic_ctx *ctx, int kernel, int64_t n);
+// After a stream synchronisation: turns queued event pairs into times.
+void prof_collect(ebic_ctx *ctx);
 
 int ebic_fail(ebic_ctx *ctx, int code, const std::string &msg);
 int ebic_fail_cuda(ebic_ctx *ctx, cudaError_t e, const char *what, const char *file, int line);
@@ -112,9 +143,10 @@ cudaError_t launch_build_bitmap(const uint32_t *keys, int64_t R_pad, int32_t C, 
 // eval.cu
 cudaError_t launch_validate_csr(const int32_t *cols, const int32_t *off, int32_t n, int32_t C,
                                 int32_t *err, cudaStream_t s);
-// Zeroes the outputs and the work counter, evaluates, writes fitness.
+// Zeroes the outputs and the work counter, evaluates, writes fitness.  When ev0/ev1 are not
+// null they are recorded on `s` immediately before and after the evaluation kernel.
 cudaError_t launch_eval(int mode, const EvalArgs &a, const PopView &pv, int num_sms,
-                        cudaStream_t s);
+                        cudaStream_t s, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 // One launch evaluating individual i (columns d_cols[0..L-1] on the device); outputs must be
 // zeroed beforehand.
 cudaError_t launch_eval_plain(const EvalArgs &a, const int32_t *d_cols, int32_t L, int32_t i,

@@ -95,6 +95,8 @@ SIGNATURES = {
     "ebic_state_bytes": (ctypes.c_int64, [_VP]),
     "ebic_save_state": (ctypes.c_int, [_VP, _VP, _I64]),
     "ebic_load_state": (ctypes.c_int, [_VP, _VP, _VP, _I64]),
+    "ebic_profile_enable": (ctypes.c_int, [_VP, _I32]),
+    "ebic_profile_read": (ctypes.c_int, [_VP, _I32, _VP]),
 }
 
 
@@ -278,6 +280,28 @@ def ebic_load_state(ctx, params, blob):
     _check(ctx, _lib.ebic_load_state(ctx, ctypes.byref(params), ptr(blob), int(blob.size)))
 
 
+KERNEL_EVAL, KERNEL_BITMAP_BUILD, KERNEL_ALL = 0, 1, 2
+
+
+class KernelStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("timed_launches", ctypes.c_int64),
+                ("ms", ctypes.c_double), ("alg_bytes", ctypes.c_double),
+                ("alg_ops", ctypes.c_double), ("units", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def ebic_profile_enable(ctx, on=True):
+    _check(ctx, _lib.ebic_profile_enable(ctx, int(bool(on))))
+
+
+def ebic_profile_read(ctx, kernel):
+    st = KernelStats()
+    _check(ctx, _lib.ebic_profile_read(ctx, int(kernel), ctypes.byref(st)))
+    return st.as_dict()
+
+
 class Context:
     """One EBIC job on one GPU: owns the C context (see ebic_create)."""
 
@@ -333,3 +357,9 @@ class Context:
 
     def last_error(self):
         return ebic_last_error(self.handle)
+
+    def profile_enable(self, on=True):
+        ebic_profile_enable(self.handle, on)
+
+    def profile_read(self, kernel):
+        return ebic_profile_read(self.handle, kernel)
