@@ -89,14 +89,18 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
+            t0 = time.time()
+            while time.time() - t0 < 3.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.01)          # first sample in before the timed region starts
         except Exception:
             self.proc = None
 
     def stop(self):
         if not self.proc:
             return None
+        time.sleep(0.05)                  # one more sample at the end of the timed region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)

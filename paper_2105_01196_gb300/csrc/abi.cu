@@ -445,7 +445,10 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
   a.rows_any = a.rows_neg + n_ind;
   a.fitness = ctx->ev_fit.as<uint64_t>();
   a.work = ctx->d_work.as<int32_t>();
-  PopView pv{d_cols, d_off, nullptr, nullptr, 0, n_ind};
+  PopView pv{};
+  pv.cols = d_cols;
+  pv.off = d_off;
+  pv.n = n_ind;
 
   const double pairs = (double)(total - n_ind), nd = a.neg ? 2.0 : 1.0;
   const double ev_bytes = (mode == EBIC_MODE_BITMAP) ? pairs * (double)ctx->Wst * 4.0 * nd

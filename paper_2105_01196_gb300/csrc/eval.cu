@@ -14,6 +14,7 @@
 // The direct and bitmap kernels are persistent: warps pull (individual, row segment) work items
 // from an atomic counter and add their partial counts with one atomic per item.
 #include "internal.h"
+#include "tables.cuh"
 
 namespace {
 
@@ -31,6 +32,12 @@ __device__ __forceinline__ int pv_start(const PopView &v, int i) {
 
 __device__ __forceinline__ int pv_len(const PopView &v, int i) {
   return v.off ? (v.off[i + 1] - v.off[i]) : v.len[i];
+}
+
+__device__ __forceinline__ bool pv_dead(const PopView &v, int i) {
+  if (v.dead && v.dead[i]) return true;
+  if (v.dkeys) return dedup_is_dup(v.dkeys, v.dslot, v.dmask, v.hash[i], i);
+  return false;
 }
 
 __device__ __forceinline__ uint4 ldg4(const uint32_t *p) {
@@ -60,6 +67,7 @@ __global__ void k_validate_csr(const int32_t *__restrict__ cols, const int32_t *
 template <bool NEG>
 __global__ void __launch_bounds__(kThreads) k_eval_direct(EvalArgs a, PopView pv) {
   __shared__ int64_t s_base[kWarps][EBIC_MAX_LEN];
+  if (pv.stop && *pv.stop) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t passes_total = a.R_pad / 128;
   const int32_t n_items = pv.n * a.n_seg;
@@ -69,8 +77,9 @@ __global__ void __launch_bounds__(kThreads) k_eval_direct(EvalArgs a, PopView pv
     q = __shfl_sync(kFull, q, 0);
     if (q >= n_items) break;
     const int i = q / a.n_seg, seg = q - i * a.n_seg;
-    if (pv.dead && pv.dead[i]) continue;
+    if (pv_dead(pv, i)) continue;
     const int L = pv_len(pv, i), st = pv_start(pv, i);
+    if (L < 2) continue;
     __syncwarp();
     for (int k = lane; k < L; k += 32) s_base[warp][k] = (int64_t)pv.cols[st + k] * a.R_pad;
     __syncwarp();
@@ -190,6 +199,7 @@ template <bool NEG>
 __global__ void __launch_bounds__(kThreads) k_eval_bitmap(EvalArgs a, PopView pv) {
   __shared__ int64_t s_pos[kWarps][EBIC_MAX_LEN];
   __shared__ int64_t s_neg[kWarps][EBIC_MAX_LEN];
+  if (pv.stop && *pv.stop) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t Wst = a.Wst;
   const int64_t passes_total = (Wst + 127) / 128;
@@ -201,8 +211,9 @@ __global__ void __launch_bounds__(kThreads) k_eval_bitmap(EvalArgs a, PopView pv
     q = __shfl_sync(kFull, q, 0);
     if (q >= n_items) break;
     const int i = q / a.n_seg, seg = q - i * a.n_seg;
-    if (pv.dead && pv.dead[i]) continue;
+    if (pv_dead(pv, i)) continue;
     const int L = pv_len(pv, i), st = pv_start(pv, i);
+    if (L < 2) continue;
     const int np = L - 1;
     __syncwarp();
     for (int k = lane; k < np; k += 32) {
@@ -344,7 +355,7 @@ __global__ void k_fitness(EvalArgs a, PopView pv) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= pv.n) return;
   const int ra = a.rows_any[i];
-  const bool dead = pv.dead && pv.dead[i];
+  const bool dead = pv_dead(pv, i);
   const int L = pv_len(pv, i);
   const int sh = L < a.col_cap ? L : a.col_cap;
   a.fitness[i] = (dead || ra < a.min_rows) ? 0ull : ((uint64_t)ra << sh);
@@ -374,20 +385,10 @@ cudaError_t launch_fitness(const EvalArgs &a, const PopView &pv, cudaStream_t s)
   return cudaGetLastError();
 }
 
-cudaError_t launch_eval(int mode, const EvalArgs &a0, const PopView &pv, int num_sms,
-                        cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+cudaError_t launch_eval_kernel(int mode, const EvalArgs &a0, const PopView &pv, int num_sms,
+                               cudaStream_t s) {
+  if (pv.n <= 0) return cudaSuccess;
   EvalArgs a = a0;
-  cudaError_t e;
-  const size_t nb = (size_t)(pv.n > 0 ? pv.n : 0) * sizeof(int32_t);
-  if ((e = cudaMemsetAsync(a.rows_pos, 0, nb, s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(a.rows_neg, 0, nb, s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(a.rows_any, 0, nb, s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
-  if (pv.n <= 0) {
-    if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
-    if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return e;
-    return cudaSuccess;
-  }
   const bool bitmap = (mode == EBIC_MODE_BITMAP);
   const int64_t passes_total = bitmap ? (a.Wst + 127) / 128 : a.R_pad / 128;
   const void *kern = bitmap ? (a.neg ? (const void *)k_eval_bitmap<true>
@@ -411,7 +412,6 @@ cudaError_t launch_eval(int mode, const EvalArgs &a0, const PopView &pv, int num
   int64_t grid = (int64_t)num_sms * bps;
   const int64_t need = (items + kWarps - 1) / kWarps;
   if (grid > need) grid = need;
-  if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
   if (bitmap) {
     if (a.neg)
       k_eval_bitmap<true><<<(unsigned)grid, kThreads, 0, s>>>(a, pv);
@@ -423,7 +423,19 @@ cudaError_t launch_eval(int mode, const EvalArgs &a0, const PopView &pv, int num
     else
       k_eval_direct<false><<<(unsigned)grid, kThreads, 0, s>>>(a, pv);
   }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval(int mode, const EvalArgs &a, const PopView &pv, int num_sms,
+                        cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1) {
+  cudaError_t e;
+  const size_t nb = (size_t)(pv.n > 0 ? pv.n : 0) * sizeof(int32_t);
+  if ((e = cudaMemsetAsync(a.rows_pos, 0, nb, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.rows_neg, 0, nb, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.rows_any, 0, nb, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.work, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+  if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
+  if ((e = launch_eval_kernel(mode, a, pv, num_sms, s)) != cudaSuccess) return e;
   if (ev1 && (e = cudaEventRecord(ev1, s)) != cudaSuccess) return e;
   return launch_fitness(a, pv, s);
 }

@@ -1,41 +1,1284 @@
-// Device-side EBIC generation loop (Sec. 2.4, steps 1-9).  Filled in by the generation kernels.
+// Device-side EBIC generation loop (EBIC.jl paper, Sec. 2.4 steps 1-9; strategies of Sec. 2.3:
+// elitism, tournament selection with an exponential penalty on overused columns, tabu list of
+// chromosome hashes, tabu-hit termination; parameters of Sec. 2.4's last paragraph).
+//
+// One generation is five kernels, captured once per buffer parity as a CUDA graph and replayed:
+//   k_evolve    one thread per slot: elites from the top list (step 4), otherwise tournament,
+//               optional one-point crossover and one mutation, tabu probe with up to
+//               max_attempts retries (step 5); live children enter the duplicate table;
+//   k_eval_*    the persistent evaluation kernel (eval.cu) over the new population, skipping
+//               tabu-dead and duplicate slots (step 7);
+//   k_score     one thread per slot: final dead flags, tabu hits, fitness, candidates that can
+//               enter the top list;
+//   k_toplist   one block: tabu-hit stop test (step 6), then the top rank list update
+//               (step 7), column usage;
+//   k_post      one thread per slot: penalties for the next tournament, tabu insertion,
+//               clearing of the per-generation tables.
+// Generation g reads population buffer (g-1)&1 and writes g&1.  Once the stop flag is set every
+// kernel returns at once, so further replays are no-ops.  The random words come from
+// Philox4x32-10 (Salmon et al., SC'11) with counter (generation, slot, attempt, block).
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "internal.h"
+#include "tables.cuh"
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kS = EBIC_MAX_LEN;  // population slot stride (columns)
+constexpr int kSlotThreads = 64;
+constexpr int kTopThreads = 1024;
+constexpr int kSortSmem = 4096;   // candidates sorted in shared memory up to this many
+
+struct TopEntry {
+  uint64_t f, h;
+  int32_t len, rp, rn, ra;
+  int32_t cols[kS];
+};
+
+struct GenCtl {
+  int32_t gen;         // last scored generation, -1 before initialisation
+  int32_t stopped;     // step 6 ended the run
+  int32_t hits_cur;    // tabu hits of the generation being built
+  int32_t hits_last;   // tabu hits of the last generation built
+  int32_t n_top;       // entries in the top list
+  int32_t live_cur;    // live slots of the generation being scored
+  int32_t n_cand;      // top-list candidates collected by k_score
+  int32_t err;
+  long long n_evaluated;
+  long long tabu_count;
+};
+
+// One population buffer (P slots of stride kS).
+struct Buf {
+  int32_t *cols, *len, *att_hits, *rows;  // rows: [3][P] pos, neg, any
+  uint8_t *att_dead, *dead;
+  uint64_t *hash, *fit;
+  int32_t *pen;
+};
+
+struct GenArgs {
+  GenCtl *ctl;
+  TopEntry *top;
+  int32_t *usage;
+  uint64_t *tabu;
+  uint32_t tmask;
+  uint64_t *dkeys;
+  uint32_t *dslot;
+  uint32_t dmask;
+  int32_t *rows_scr;  // [3][P] evaluation output (zeroed by k_post)
+  int32_t *work;
+  uint64_t *cand_f, *cand_h;
+  int32_t *cand_s;
+  int32_t cand_cap;
+  uint64_t seed;
+  int32_t P, C, K, E, T, A, max_len, init_min, init_max;
+  int32_t min_rows, col_cap, ov_num, ov_den, tabu_limit;
+};
+
+// ------------------------------------------------------------------ Philox4x32-10 word stream
+
+constexpr uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
+constexpr uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
+
+struct WordStream {
+  uint32_t k0, k1, c0, c1, c2, blk;
+  uint32_t buf[4];
+  int pos;
+  __device__ WordStream(uint64_t seed, uint32_t g, uint32_t s, uint32_t a)
+      : k0((uint32_t)seed), k1((uint32_t)(seed >> 32)), c0(g), c1(s), c2(a), blk(0), pos(4) {}
+  __device__ void refill() {
+    uint32_t x0 = c0, x1 = c1, x2 = c2, x3 = blk, a0 = k0, a1 = k1;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+      if (r) {
+        a0 += kWeyl0;
+        a1 += kWeyl1;
+      }
+      const uint32_t lo0 = kMul0 * x0, hi0 = __umulhi(kMul0, x0);
+      const uint32_t lo1 = kMul1 * x2, hi1 = __umulhi(kMul1, x2);
+      const uint32_t y0 = hi1 ^ x1 ^ a0, y2 = hi0 ^ x3 ^ a1;
+      x0 = y0;
+      x1 = lo1;
+      x2 = y2;
+      x3 = lo0;
+    }
+    buf[0] = x0;
+    buf[1] = x1;
+    buf[2] = x2;
+    buf[3] = x3;
+    ++blk;
+    pos = 0;
+  }
+  __device__ uint32_t next() {
+    if (pos == 4) refill();
+    return buf[pos++];
+  }
+  // Uniform integer in [0, n): high word of word * n.
+  __device__ uint32_t below(uint32_t n) { return __umulhi(next(), n); }
+};
+
+// ------------------------------------------------------------------ FNV-1a 64 chromosome key
+
+__device__ uint64_t chromosome_key(const int32_t *c, int L) {
+  uint64_t h = 0xCBF29CE484222325ull;
+  for (int k = 0; k < L; ++k) {
+    const uint32_t v = (uint32_t)c[k];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      h ^= (v >> (8 * b)) & 0xFFu;
+      h *= 0x100000001B3ull;
+    }
+  }
+  return h ? h : 0x9E3779B97F4A7C15ull;
+}
+
+// ------------------------------------------------------------------ selection
+
+// Sign of fa * 2^-ua - fb * 2^-ub, exactly (ua, ub >= 0).
+__device__ int cmp_penalised(uint64_t fa, int ua, uint64_t fb, int ub) {
+  if (ub < ua) return -cmp_penalised(fb, ub, fa, ua);
+  const int s = ub - ua;  // compare fa * 2^s with fb
+  if (fa == 0ull) return fb == 0ull ? 0 : -1;
+  if (s >= 64) return 1;
+  const uint64_t q = fb >> s;
+  if (fa > q) return 1;
+  if (fa < q) return -1;
+  const uint64_t rem = fb & ((s ? (1ull << s) : 1ull) - 1ull);
+  return rem ? -1 : 0;
+}
+
+__device__ int tournament(WordStream &st, const GenArgs &ga, const Buf &pb) {
+  int best = -1;
+  for (int t = 0; t < ga.T; ++t) {
+    const int i = (int)st.below((uint32_t)ga.P);
+    if (best < 0) {
+      best = i;
+    } else {
+      const int c = cmp_penalised(pb.fit[i], pb.pen[i], pb.fit[best], pb.pen[best]);
+      if (c > 0 || (c == 0 && i < best)) best = i;
+    }
+  }
+  return best;
+}
+
+// ------------------------------------------------------------------ variation
+
+__device__ __forceinline__ bool contains(const int32_t *c, int L, int v) {
+  for (int k = 0; k < L; ++k)
+    if (c[k] == v) return true;
+  return false;
+}
+
+// A column not in c[0..L), by up to 64 uniform draws; -1 when every draw hit.
+__device__ int draw_free(WordStream &st, int C, const int32_t *c, int L) {
+  for (int t = 0; t < 64; ++t) {
+    const int v = (int)st.below((uint32_t)C);
+    if (!contains(c, L, v)) return v;
+  }
+  return -1;
+}
+
+__device__ void swap_op(WordStream &st, int32_t *c, int L) {
+  if (L < 2) return;  // never reached: every live chromosome has at least two columns
+  const int p = (int)st.below((uint32_t)L);
+  int q = (int)st.below((uint32_t)(L - 1));
+  if (q >= p) ++q;
+  const int t = c[p];
+  c[p] = c[q];
+  c[q] = t;
+}
+
+__device__ void mutate(WordStream &st, int32_t *c, int &L, int C, int max_len) {
+  for (int tries = 0; tries < 8; ++tries) {
+    const uint32_t op = st.next() >> 30;
+    if (op == 0u) {  // insertion
+      if (L >= max_len || L >= C) continue;
+      const int pos = (int)st.below((uint32_t)(L + 1));
+      const int v = draw_free(st, C, c, L);
+      if (v < 0) continue;
+      for (int k = L; k > pos; --k) c[k] = c[k - 1];
+      c[pos] = v;
+      ++L;
+      return;
+    }
+    if (op == 1u) {  // deletion
+      if (L <= 2) continue;
+      const int pos = (int)st.below((uint32_t)L);
+      for (int k = pos; k < L - 1; ++k) c[k] = c[k + 1];
+      --L;
+      return;
+    }
+    if (op == 2u) {  // substitution
+      if (L >= C) continue;
+      const int pos = (int)st.below((uint32_t)L);
+      const int v = draw_free(st, C, c, L);
+      if (v < 0) continue;
+      c[pos] = v;
+      return;
+    }
+    swap_op(st, c, L);
+    return;
+  }
+  swap_op(st, c, L);
+}
+
+__device__ void make_child(const GenArgs &ga, const Buf &pb, int g, int s, int a, int32_t *c,
+                           int &L) {
+  WordStream st(ga.seed, (uint32_t)g, (uint32_t)s, (uint32_t)a);
+  const int p1 = tournament(st, ga, pb);
+  const int32_t *A = pb.cols + (size_t)p1 * kS;
+  const int LA = pb.len[p1];
+  if (st.next() < (1u << 30)) {  // one-point crossover, probability 1/4
+    const int p2 = tournament(st, ga, pb);
+    const int32_t *B = pb.cols + (size_t)p2 * kS;
+    const int LB = pb.len[p2];
+    // (the min() guards only matter for a chromosome shorter than 2, which is never built)
+    const int cut1 = min(1 + (int)st.below((uint32_t)(LA - 1)), max(LA, 1));
+    const int cut2 = min(1 + (int)st.below((uint32_t)(LB - 1)), LB);
+    L = 0;
+    for (int k = 0; k < cut1; ++k) c[L++] = A[k];
+    for (int k = cut2; k < LB && L < ga.max_len; ++k)
+      if (!contains(c, cut1, B[k])) c[L++] = B[k];
+    if (L < 2) {
+      for (int k = 0; k < LA; ++k) c[k] = A[k];
+      L = LA;
+    }
+  } else {
+    for (int k = 0; k < LA; ++k) c[k] = A[k];
+    L = LA;
+  }
+  mutate(st, c, L, ga.C, ga.max_len);
+}
+
+// ------------------------------------------------------------------ kernels
+
+__global__ void __launch_bounds__(kSlotThreads) k_init(GenArgs ga, Buf nb) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ga.P) return;
+  WordStream st(ga.seed, 0u, (uint32_t)s, 0u);
+  int32_t c[kS];
+  const int want = ga.init_min + (int)st.below((uint32_t)(ga.init_max - ga.init_min + 1));
+  int L = 0;
+  for (int j = 0; j < want; ++j) {
+    const int v = draw_free(st, ga.C, c, L);
+    if (v < 0) break;
+    c[L++] = v;
+  }
+  int32_t *out = nb.cols + (size_t)s * kS;
+  for (int k = 0; k < L; ++k) out[k] = c[k];
+  nb.len[s] = L;
+  const bool dead = L < 2;
+  nb.att_dead[s] = dead;
+  nb.att_hits[s] = 0;
+  const uint64_t h = chromosome_key(c, L);
+  nb.hash[s] = h;
+  if (!dead) dedup_insert(ga.dkeys, ga.dslot, ga.dmask, h, s);
+}
+
+__global__ void __launch_bounds__(kSlotThreads) k_evolve(GenArgs ga, Buf pb, Buf nb) {
+  if (ga.ctl->stopped) return;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ga.P) return;
+  const int g = ga.ctl->gen + 1;
+  const int n_el = min(ga.E, ga.ctl->n_top);
+  int32_t *out = nb.cols + (size_t)s * kS;
+  if (s < n_el) {  // elitism: copy top-list entry s (its key is already in the tabu list)
+    const TopEntry &e = ga.top[s];
+    for (int k = 0; k < e.len; ++k) out[k] = e.cols[k];
+    nb.len[s] = e.len;
+    nb.hash[s] = e.h;
+    nb.att_dead[s] = 0;
+    nb.att_hits[s] = 0;
+    return;
+  }
+  int32_t c[kS];
+  int L = 0, hits = 0;
+  uint64_t h = 0;
+  bool dead = true;
+  for (int a = 0; a < ga.A; ++a) {
+    make_child(ga, pb, g, s, a, c, L);
+    h = chromosome_key(c, L);
+    if (!tabu_contains(ga.tabu, ga.tmask, h)) {
+      dead = false;
+      break;
+    }
+    ++hits;
+  }
+  for (int k = 0; k < L; ++k) out[k] = c[k];
+  nb.len[s] = L;
+  nb.hash[s] = h;
+  nb.att_dead[s] = dead;
+  nb.att_hits[s] = hits;
+  if (!dead) dedup_insert(ga.dkeys, ga.dslot, ga.dmask, h, s);
+}
+
+__device__ __forceinline__ bool key_before(uint64_t fa, uint64_t ha, uint64_t fb, uint64_t hb) {
+  return fa > fb || (fa == fb && ha < hb);
+}
+
+__global__ void __launch_bounds__(256) k_score(GenArgs ga, Buf nb) {
+  if (ga.ctl->stopped) return;
+  __shared__ int s_hits, s_live;
+  if (threadIdx.x == 0) {
+    s_hits = 0;
+    s_live = 0;
+  }
+  __syncthreads();
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < ga.P) {
+    const bool att_dead = nb.att_dead[s] != 0;
+    const uint64_t h = nb.hash[s];
+    const bool dup = !att_dead && dedup_is_dup(ga.dkeys, ga.dslot, ga.dmask, h, s);
+    const bool dead = att_dead || dup;
+    nb.dead[s] = dead;
+    const int rp = ga.rows_scr[s], rn = ga.rows_scr[ga.P + s], ra = ga.rows_scr[2 * ga.P + s];
+    nb.rows[s] = rp;
+    nb.rows[ga.P + s] = rn;
+    nb.rows[2 * ga.P + s] = ra;
+    const int L = nb.len[s];
+    const uint64_t f =
+        (dead || ra < ga.min_rows) ? 0ull : ((uint64_t)ra << (L < ga.col_cap ? L : ga.col_cap));
+    nb.fit[s] = f;
+    const int hits = nb.att_hits[s] + (dup ? 1 : 0);
+    if (hits) atomicAdd(&s_hits, hits);
+    if (!dead) atomicAdd(&s_live, 1);
+    if (!dead && f > 0ull) {
+      const int nt = ga.ctl->n_top;
+      bool potential = true;
+      if (nt >= ga.K) {
+        const TopEntry &last = ga.top[ga.K - 1];
+        potential = key_before(f, h, last.f, last.h);
+      }
+      if (potential) {
+        const int q = atomicAdd(&ga.ctl->n_cand, 1);
+        ga.cand_f[q] = f;
+        ga.cand_h[q] = h;
+        ga.cand_s[q] = s;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_hits) atomicAdd(&ga.ctl->hits_cur, s_hits);
+    if (s_live) atomicAdd(&ga.ctl->live_cur, s_live);
+  }
+}
+
+// Bitonic sort of n (f, h, s) candidates into "rank" order (f descending, key ascending) by the
+// whole block; arrays hold N = next power of two >= n entries (padding written here).
+__device__ void block_sort(uint64_t *f, uint64_t *h, int32_t *sl, int n) {
+  int N = 1;
+  while (N < n) N <<= 1;
+  for (int i = n + threadIdx.x; i < N; i += blockDim.x) {
+    f[i] = 0ull;
+    h[i] = ~0ull;
+    sl[i] = 0x7FFFFFFF;
+  }
+  __syncthreads();
+  for (int k = 2; k <= N; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool asc = (i & k) == 0;
+          const uint64_t fi = f[i], fl = f[l], hi = h[i], hl = h[l];
+          const bool l_first = key_before(fl, hl, fi, hi);
+          if (asc ? l_first : !l_first) {
+            f[i] = fl;
+            f[l] = fi;
+            h[i] = hl;
+            h[l] = hi;
+            const int32_t t = sl[i];
+            sl[i] = sl[l];
+            sl[l] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+struct TopSmem {
+  TopEntry *pool;    // K + 1 entries
+  uint32_t *colbits; // ceil(C / 32) words
+  int32_t *idx;      // K + 1: pool index of list position
+  int32_t *idx2;     // K + 1
+  uint8_t *used;     // K + 1
+  uint64_t *sf, *sh; // kSortSmem
+  int32_t *ss;
+};
+
+// Number of columns of pool entry e present in colbits (warp-wide).
+__device__ __forceinline__ int overlap(const TopSmem &sm, const TopEntry &e, int lane) {
+  int cnt = 0;
+  for (int k = lane; k < e.len; k += 32) {
+    const int v = e.cols[k];
+    cnt += (sm.colbits[v >> 5] >> (v & 31)) & 1u;
+  }
+  return __reduce_add_sync(kFull, cnt);
+}
+
+// Sequential top-list update by one warp over sorted candidates (f, h, s); returns new n.
+__device__ int process_candidates(const GenArgs &ga, const Buf &nb, const TopSmem &sm, int n,
+                                  const uint64_t *cf, const uint64_t *ch, const int32_t *cs,
+                                  int count, int lane) {
+  for (int q = 0; q < count; ++q) {
+    const uint64_t f = cf[q], h = ch[q];
+    const int s = cs[q];
+    int pos = 0;
+    bool dup = false;
+    for (int e0 = 0; e0 < n; e0 += 32) {
+      const int e = e0 + lane;
+      bool isdup = false, before = false;
+      if (e < n) {
+        const TopEntry &E = sm.pool[sm.idx[e]];
+        isdup = E.h == h;
+        before = key_before(E.f, E.h, f, h);
+      }
+      dup |= __any_sync(kFull, isdup);
+      pos += __popc(__ballot_sync(kFull, before));
+    }
+    if (dup) continue;
+    if (pos >= ga.K) break;  // the list is full and every later candidate ranks after it
+    const int L = nb.len[s];
+    const int32_t *cc = nb.cols + (size_t)s * kS;
+    for (int k = lane; k < L; k += 32) atomicOr(&sm.colbits[cc[k] >> 5], 1u << (cc[k] & 31));
+    __syncwarp();
+    bool ok = true;
+    for (int e = 0; e < pos && ok; ++e) {
+      const int inter = overlap(sm, sm.pool[sm.idx[e]], lane);
+      if ((long long)inter * ga.ov_den > (long long)ga.ov_num * L) ok = false;
+    }
+    if (ok) {
+      // a free pool slot: the pool has K + 1 entries and the list at most K
+      int fr = -1;
+      for (int b0 = 0; b0 <= ga.K && fr < 0; b0 += 32) {
+        const int b = b0 + lane;
+        const unsigned m = __ballot_sync(kFull, b <= ga.K && !sm.used[b]);
+        if (m) fr = b0 + __ffs(m) - 1;
+      }
+      TopEntry &ne = sm.pool[fr];
+      for (int k = lane; k < L; k += 32) ne.cols[k] = cc[k];
+      if (lane == 0) {
+        ne.len = L;
+        ne.f = f;
+        ne.h = h;
+        ne.rp = nb.rows[s];
+        ne.rn = nb.rows[ga.P + s];
+        ne.ra = nb.rows[2 * ga.P + s];
+        sm.used[fr] = 1;
+      }
+      for (int e = lane; e < pos; e += 32) sm.idx2[e] = sm.idx[e];
+      int m = pos + 1;
+      for (int e = pos; e < n; ++e) {
+        const int pe = sm.idx[e];
+        const TopEntry &E = sm.pool[pe];
+        const int inter = overlap(sm, E, lane);
+        const bool keep = (long long)inter * ga.ov_den <= (long long)ga.ov_num * E.len;
+        if (keep && m < ga.K) {
+          if (lane == 0) sm.idx2[m] = pe;
+          ++m;
+        } else if (lane == 0) {
+          sm.used[pe] = 0;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) sm.idx2[pos] = fr;
+      __syncwarp();
+      for (int e = lane; e < m; e += 32) sm.idx[e] = sm.idx2[e];
+      n = m;
+      __syncwarp();
+    }
+    for (int k = lane; k < L; k += 32) atomicAnd(&sm.colbits[cc[k] >> 5], ~(1u << (cc[k] & 31)));
+    __syncwarp();
+  }
+  return n;
+}
+
+// Sorts `count` candidates held in global arrays (in shared memory when they fit) and lets
+// warp 0 process them.  Returns the new list length (valid in every thread).
+__device__ int sort_and_process(const GenArgs &ga, const Buf &nb, const TopSmem &sm, int n,
+                                int count, int *s_n) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int N = 1;
+  while (N < count) N <<= 1;
+  const uint64_t *cf;
+  const uint64_t *ch;
+  const int32_t *cs;
+  if (N <= kSortSmem) {
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+      sm.sf[i] = ga.cand_f[i];
+      sm.sh[i] = ga.cand_h[i];
+      sm.ss[i] = ga.cand_s[i];
+    }
+    __syncthreads();
+    block_sort(sm.sf, sm.sh, sm.ss, count);
+    cf = sm.sf;
+    ch = sm.sh;
+    cs = sm.ss;
+  } else {
+    block_sort(ga.cand_f, ga.cand_h, ga.cand_s, count);
+    cf = ga.cand_f;
+    ch = ga.cand_h;
+    cs = ga.cand_s;
+  }
+  if (warp == 0) {
+    const int m = process_candidates(ga, nb, sm, n, cf, ch, cs, count, lane);
+    if (lane == 0) *s_n = m;
+  }
+  __syncthreads();
+  return *s_n;
+}
+
+__global__ void __launch_bounds__(kTopThreads, 1) k_toplist(GenArgs ga, Buf nb) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_n, s_cnt;
+  GenCtl *ctl = ga.ctl;
+  if (ctl->stopped) return;
+  const bool init = ctl->gen < 0;
+  const int hits = ctl->hits_cur;
+  __syncthreads();
+  if (!init && ga.tabu_limit > 0 && hits >= ga.tabu_limit) {  // step 6
+    if (threadIdx.x == 0) {
+      ctl->hits_last = hits;
+      ctl->stopped = 1;
+    }
+    return;
+  }
+  TopSmem sm;
+  const int cw = (ga.C + 31) / 32;
+  sm.pool = reinterpret_cast<TopEntry *>(smem);
+  sm.sf = reinterpret_cast<uint64_t *>(sm.pool + ga.K + 1);
+  sm.sh = sm.sf + kSortSmem;
+  sm.colbits = reinterpret_cast<uint32_t *>(sm.sh + kSortSmem);
+  sm.ss = reinterpret_cast<int32_t *>(sm.colbits + cw);
+  sm.idx = sm.ss + kSortSmem;
+  sm.idx2 = sm.idx + ga.K + 1;
+  sm.used = reinterpret_cast<uint8_t *>(sm.idx2 + ga.K + 1);
+
+  const int n0 = ctl->n_top;
+  for (int i = threadIdx.x; i < cw; i += blockDim.x) sm.colbits[i] = 0u;
+  for (int e = threadIdx.x; e <= ga.K; e += blockDim.x) {
+    sm.used[e] = e < n0;
+    sm.idx[e] = e;
+  }
+  for (int q = threadIdx.x; q < n0 * (int)(sizeof(TopEntry) / 4); q += blockDim.x)
+    reinterpret_cast<int32_t *>(sm.pool)[q] = reinterpret_cast<const int32_t *>(ga.top)[q];
+  __syncthreads();
+  const bool had_threshold = n0 >= ga.K;
+  const uint64_t tf = had_threshold ? sm.pool[ga.K - 1].f : 0ull;
+  const uint64_t th = had_threshold ? sm.pool[ga.K - 1].h : 0ull;
+  int n = n0;
+  const int nc = ctl->n_cand;
+  if (nc > 0) n = sort_and_process(ga, nb, sm, n, nc, &s_n);
+  if (had_threshold && n < ga.K) {
+    // Evictions left room: the candidates ranking after the old threshold come next.
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (int s = threadIdx.x; s < ga.P; s += blockDim.x) {
+      const uint64_t f = nb.fit[s], h = nb.hash[s];
+      if (!nb.dead[s] && f > 0ull && !key_before(f, h, tf, th)) {
+        const int q = atomicAdd(&s_cnt, 1);
+        ga.cand_f[q] = f;
+        ga.cand_h[q] = h;
+        ga.cand_s[q] = s;
+      }
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    __syncthreads();
+    if (cnt > 0) n = sort_and_process(ga, nb, sm, n, cnt, &s_n);
+  }
+  // write back in rank order
+  const int words = (int)(sizeof(TopEntry) / 4);
+  for (int q = threadIdx.x; q < n * words; q += blockDim.x) {
+    const int e = q / words, w = q - e * words;
+    reinterpret_cast<int32_t *>(ga.top + e)[w] =
+        reinterpret_cast<const int32_t *>(sm.pool + sm.idx[e])[w];
+  }
+  for (int c = threadIdx.x; c < ga.C; c += blockDim.x) ga.usage[c] = 0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < n * kS; q += blockDim.x) {
+    const int e = q / kS, k = q - e * kS;
+    const TopEntry &E = sm.pool[sm.idx[e]];
+    if (k < E.len) atomicAdd(&ga.usage[E.cols[k]], 1);
+  }
+  if (threadIdx.x == 0) {
+    ctl->hits_last = hits;
+    ctl->n_top = n;
+    ctl->gen += 1;
+    ctl->n_evaluated += ctl->live_cur;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_post(GenArgs ga, Buf cb, int32_t dcap) {
+  if (ga.ctl->stopped) return;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  for (int s = tid; s < ga.P; s += stride) {
+    int u = 0;
+    const int32_t *c = cb.cols + (size_t)s * kS;
+    const int L = cb.len[s];
+    for (int k = 0; k < L; ++k) u += ga.usage[c[k]];
+    cb.pen[s] = u;
+    if (!cb.dead[s] && tabu_insert(ga.tabu, ga.tmask, cb.hash[s]))
+      atomicAdd(reinterpret_cast<unsigned long long *>(&ga.ctl->tabu_count), 1ull);
+    ga.rows_scr[s] = 0;
+    ga.rows_scr[ga.P + s] = 0;
+    ga.rows_scr[2 * ga.P + s] = 0;
+  }
+  for (int i = tid; i < dcap; i += stride) {
+    ga.dkeys[i] = 0ull;
+    ga.dslot[i] = 0u;
+  }
+  if (tid == 0) {
+    ga.ctl->hits_cur = 0;
+    ga.ctl->live_cur = 0;
+    ga.ctl->n_cand = 0;
+    *ga.work = 0;
+  }
+}
+
+// Step 9: row masks of the top-list entries, one warp per (entry, 32-row word), from the keys.
+__global__ void __launch_bounds__(256) k_extract(const uint32_t *__restrict__ keys, int64_t R,
+                                                 int64_t R_pad, int64_t Wst, const TopEntry *top,
+                                                 const GenCtl *ctl, int neg, int rnum, int rden,
+                                                 uint32_t *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int n = ctl->n_top;
+  if (gw >= (int64_t)n * Wst) return;
+  const int e = (int)(gw / Wst);
+  const int64_t w = gw - (int64_t)e * Wst;
+  const TopEntry &E = top[e];
+  const int64_t r = w * 32 + lane;
+  bool acc = false;
+  if (r < R) {
+    const int t = (rnum * (E.len - 1) + rden - 1) / rden;
+    uint32_t prev = keys[(int64_t)E.cols[0] * R_pad + r];
+    int inc = 0, dec = 0;
+    for (int k = 1; k < E.len; ++k) {
+      const uint32_t cur = keys[(int64_t)E.cols[k] * R_pad + r];
+      inc += cur > prev;
+      dec += cur < prev;
+      prev = cur;
+    }
+    acc = inc >= t || (neg && dec >= t);
+  }
+  const uint32_t m = __ballot_sync(kFull, acc);
+  if (lane == 0) out[(int64_t)e * Wst + w] = m;
+}
+
+__global__ void k_rehash(const uint64_t *old_keys, uint32_t old_cap, uint64_t *keys,
+                         uint32_t mask) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < old_cap && old_keys[i]) tabu_insert(keys, mask, old_keys[i]);
+}
+
+__global__ void k_tabu_load(const uint64_t *list, int64_t n, uint64_t *keys, uint32_t mask) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) tabu_insert(keys, mask, list[i]);
+}
+
+uint32_t next_pow2(uint64_t v) {
+  uint64_t p = 1;
+  while (p < v) p <<= 1;
+  return (uint32_t)p;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ host state
 
 struct GenState {
-  int dummy;
+  ebic_params p{};
+  int P = 0, K = 0, C = 0, eval_mode = EBIC_MODE_DIRECT;
+  bool initialised = false;
+  DevBuf cols[2], len[2], att_hits[2], rows[2], att_dead[2], dead[2], hash[2], fit[2], pen[2];
+  DevBuf rows_scr, work, tabu, dkeys, dslot, top, ctl, usage, cand_f, cand_h, cand_s, extract;
+  uint32_t tcap = 0, dcap = 0, ccap = 0;
+  size_t top_smem = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaStream_t cap_stream = nullptr;
+
+  void drop_graphs() {
+    for (auto &g : graph)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+  }
+  ~GenState() {
+    drop_graphs();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    DevBuf *all[] = {&rows_scr, &work, &tabu, &dkeys, &dslot, &top, &ctl, &usage, &cand_f,
+                     &cand_h, &cand_s, &extract};
+    for (DevBuf *b : all) b->release();
+    for (int k = 0; k < 2; ++k) {
+      DevBuf *bs[] = {&cols[k], &len[k], &att_hits[k], &rows[k], &att_dead[k], &dead[k],
+                      &hash[k], &fit[k], &pen[k]};
+      for (DevBuf *b : bs) b->release();
+    }
+  }
+  Buf buf(int k) {
+    Buf b;
+    b.cols = cols[k].as<int32_t>();
+    b.len = len[k].as<int32_t>();
+    b.att_hits = att_hits[k].as<int32_t>();
+    b.rows = rows[k].as<int32_t>();
+    b.att_dead = att_dead[k].as<uint8_t>();
+    b.dead = dead[k].as<uint8_t>();
+    b.hash = hash[k].as<uint64_t>();
+    b.fit = fit[k].as<uint64_t>();
+    b.pen = pen[k].as<int32_t>();
+    return b;
+  }
 };
 
 void gen_state_free(GenState *g) { delete g; }
+
+namespace {
+
+bool same_run_params(const ebic_params &a, const ebic_params &b) {
+  ebic_params x = a, y = b;
+  x.mode = y.mode = 0;
+  x.use_graph = y.use_graph = 0;
+  return memcmp(&x, &y, sizeof(x)) == 0;
+}
+
+GenArgs gen_args(ebic_ctx *ctx, GenState *g) {
+  GenArgs ga{};
+  ga.ctl = g->ctl.as<GenCtl>();
+  ga.top = g->top.as<TopEntry>();
+  ga.usage = g->usage.as<int32_t>();
+  ga.tabu = g->tabu.as<uint64_t>();
+  ga.tmask = g->tcap - 1;
+  ga.dkeys = g->dkeys.as<uint64_t>();
+  ga.dslot = g->dslot.as<uint32_t>();
+  ga.dmask = g->dcap - 1;
+  ga.rows_scr = g->rows_scr.as<int32_t>();
+  ga.work = g->work.as<int32_t>();
+  ga.cand_f = g->cand_f.as<uint64_t>();
+  ga.cand_h = g->cand_h.as<uint64_t>();
+  ga.cand_s = g->cand_s.as<int32_t>();
+  ga.cand_cap = (int32_t)g->ccap;
+  const ebic_params &p = g->p;
+  ga.seed = p.seed;
+  ga.P = p.pop_size;
+  ga.C = ctx->C;
+  ga.K = p.n_biclusters;
+  ga.E = p.elite;
+  ga.T = p.tournament;
+  ga.A = p.max_attempts;
+  ga.max_len = p.max_len;
+  ga.init_min = p.init_min_len;
+  ga.init_max = p.init_max_len;
+  ga.min_rows = p.min_rows;
+  ga.col_cap = p.col_cap;
+  ga.ov_num = p.overlap_num;
+  ga.ov_den = p.overlap_den;
+  ga.tabu_limit = p.tabu_hit_limit;
+  return ga;
+}
+
+EvalArgs gen_eval_args(ebic_ctx *ctx, GenState *g) {
+  EvalArgs a{};
+  a.keys = ctx->keys.as<uint32_t>();
+  a.bitmap = ctx->bitmap_ok ? ctx->bitmap.as<uint32_t>() : nullptr;
+  a.R = ctx->R;
+  a.R_pad = ctx->R_pad;
+  a.Wst = ctx->Wst;
+  a.C = ctx->C;
+  a.neg = g->p.neg_trends;
+  a.rnum = g->p.ratio_num;
+  a.rden = g->p.ratio_den;
+  a.min_rows = g->p.min_rows;
+  a.col_cap = g->p.col_cap;
+  a.rows_pos = g->rows_scr.as<int32_t>();
+  a.rows_neg = a.rows_pos + g->P;
+  a.rows_any = a.rows_neg + g->P;
+  a.fitness = nullptr;
+  a.work = g->work.as<int32_t>();
+  return a;
+}
+
+PopView gen_view(GenState *g, int k) {
+  PopView v{};
+  v.cols = g->cols[k].as<int32_t>();
+  v.len = g->len[k].as<int32_t>();
+  v.dead = g->att_dead[k].as<uint8_t>();
+  v.stride = kS;
+  v.n = g->P;
+  v.stop = &g->ctl.as<GenCtl>()->stopped;
+  v.hash = g->hash[k].as<uint64_t>();
+  v.dkeys = g->dkeys.as<uint64_t>();
+  v.dslot = g->dslot.as<uint32_t>();
+  v.dmask = g->dcap - 1;
+  return v;
+}
+
+// Scoring kernels shared by initialisation and every generation (buffer k was just built).
+cudaError_t launch_scoring(ebic_ctx *ctx, GenState *g, int k, cudaStream_t s) {
+  const GenArgs ga = gen_args(ctx, g);
+  const Buf nb = g->buf(k);
+  cudaError_t e;
+  if ((e = launch_eval_kernel(g->eval_mode, gen_eval_args(ctx, g), gen_view(g, k), ctx->num_sms,
+                              s)) != cudaSuccess)
+    return e;
+  const unsigned sblocks = (unsigned)((g->P + 255) / 256);
+  k_score<<<sblocks, 256, 0, s>>>(ga, nb);
+  k_toplist<<<1, kTopThreads, g->top_smem, s>>>(ga, nb);
+  int pblocks = (int)((std::max<int64_t>(g->P, g->dcap) + 255) / 256);
+  if (pblocks > ctx->num_sms * 8) pblocks = ctx->num_sms * 8;
+  k_post<<<pblocks, 256, 0, s>>>(ga, nb, (int32_t)g->dcap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_generation(ebic_ctx *ctx, GenState *g, int parity, cudaStream_t s) {
+  const GenArgs ga = gen_args(ctx, g);
+  k_evolve<<<(g->P + kSlotThreads - 1) / kSlotThreads, kSlotThreads, 0, s>>>(
+      ga, g->buf(parity ^ 1), g->buf(parity));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_scoring(ctx, g, parity, s);
+}
+
+int check_run_params(ebic_ctx *ctx, const ebic_params *p) {
+  EBIC_TRY(ebic_check_eval_params(ctx, p));
+  const int maxlen_cap = std::min(EBIC_MAX_LEN, ctx->C);
+  if (!(2 <= p->init_min_len && p->init_min_len <= p->init_max_len &&
+        p->init_max_len <= p->max_len && p->max_len <= maxlen_cap))
+    return ebic_fail(ctx, EBIC_EINVAL,
+                     "need 2 <= init_min_len <= init_max_len <= max_len <= min(64, cols)");
+  if (!(p->overlap_den > 0 && p->overlap_num >= 0 && p->overlap_num <= p->overlap_den))
+    return ebic_fail(ctx, EBIC_EINVAL, "need 0 <= overlap_num <= overlap_den, overlap_den > 0");
+  if (p->n_biclusters < 1 || p->n_biclusters > EBIC_MAX_BICLUSTERS)
+    return ebic_fail(ctx, EBIC_EINVAL, "n_biclusters must be in [1, 256]");
+  if (p->pop_size < 2 || p->pop_size > (1 << 20))
+    return ebic_fail(ctx, EBIC_EINVAL, "pop_size must be in [2, 2^20]");
+  if (p->elite < 0 || p->elite > p->n_biclusters || p->elite >= p->pop_size)
+    return ebic_fail(ctx, EBIC_EINVAL, "elite must be in [0, min(n_biclusters, pop_size - 1)]");
+  if (p->tournament < 1 || p->tournament > 16 || p->max_attempts < 1 || p->max_attempts > 16)
+    return ebic_fail(ctx, EBIC_EINVAL, "tournament and max_attempts must be in [1, 16]");
+  if (p->mode == EBIC_MODE_PLAIN)
+    return ebic_fail(ctx, EBIC_EINVAL, "the generation loop evaluates with DIRECT or BITMAP");
+  return EBIC_OK;
+}
+
+#define GEN_ALLOC(buf, bytes) EBIC_CHECK_CUDA(ctx, (buf).ensure(bytes))
+
+int gen_create(ebic_ctx *ctx, const ebic_params *p) {
+  gen_state_free(ctx->gen);
+  ctx->gen = nullptr;
+  GenState *g = new (std::nothrow) GenState();
+  if (!g) return ebic_fail(ctx, EBIC_ENOMEM, "host allocation failed");
+  ctx->gen = g;
+  g->p = *p;
+  g->P = p->pop_size;
+  g->K = p->n_biclusters;
+  g->C = ctx->C;
+  const size_t P = (size_t)g->P;
+  for (int k = 0; k < 2; ++k) {
+    GEN_ALLOC(g->cols[k], P * kS * 4);
+    GEN_ALLOC(g->len[k], P * 4);
+    GEN_ALLOC(g->att_hits[k], P * 4);
+    GEN_ALLOC(g->rows[k], P * 3 * 4);
+    GEN_ALLOC(g->att_dead[k], P);
+    GEN_ALLOC(g->dead[k], P);
+    GEN_ALLOC(g->hash[k], P * 8);
+    GEN_ALLOC(g->fit[k], P * 8);
+    GEN_ALLOC(g->pen[k], P * 4);
+    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->cols[k].p, 0, P * kS * 4, ctx->stream));
+    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->pen[k].p, 0, P * 4, ctx->stream));
+    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->fit[k].p, 0, P * 8, ctx->stream));
+  }
+  GEN_ALLOC(g->rows_scr, P * 3 * 4);
+  GEN_ALLOC(g->work, 64);
+  g->dcap = next_pow2(2 * P);
+  GEN_ALLOC(g->dkeys, (size_t)g->dcap * 8);
+  GEN_ALLOC(g->dslot, (size_t)g->dcap * 4);
+  g->ccap = next_pow2(P);
+  GEN_ALLOC(g->cand_f, (size_t)g->ccap * 8);
+  GEN_ALLOC(g->cand_h, (size_t)g->ccap * 8);
+  GEN_ALLOC(g->cand_s, (size_t)g->ccap * 4);
+  GEN_ALLOC(g->top, (size_t)g->K * sizeof(TopEntry));
+  GEN_ALLOC(g->ctl, sizeof(GenCtl));
+  GEN_ALLOC(g->usage, (size_t)ctx->C * 4);
+  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->rows_scr.p, 0, P * 3 * 4, ctx->stream));
+  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->work.p, 0, 64, ctx->stream));
+  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->dkeys.p, 0, (size_t)g->dcap * 8, ctx->stream));
+  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->dslot.p, 0, (size_t)g->dcap * 4, ctx->stream));
+  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->usage.p, 0, (size_t)ctx->C * 4, ctx->stream));
+  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->top.p, 0, (size_t)g->K * sizeof(TopEntry), ctx->stream));
+  GenCtl c0{};
+  c0.gen = -1;
+  EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(g->ctl.p, &c0, sizeof(c0), cudaMemcpyHostToDevice,
+                                       ctx->stream));
+  const int cw = (ctx->C + 31) / 32;
+  g->top_smem = (size_t)(g->K + 1) * sizeof(TopEntry) + (size_t)kSortSmem * 16 +
+                (size_t)cw * 4 + (size_t)kSortSmem * 4 + (size_t)(g->K + 1) * 8 +
+                (size_t)(g->K + 1) + 16;
+  EBIC_CHECK_CUDA(ctx, cudaFuncSetAttribute(k_toplist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)g->top_smem));
+  EBIC_CHECK_CUDA(ctx, cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return EBIC_OK;
+}
+
+int read_ctl(ebic_ctx *ctx, GenState *g, GenCtl *out) {
+  EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(out, g->ctl.p, sizeof(GenCtl), cudaMemcpyDeviceToHost,
+                                       ctx->stream));
+  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return EBIC_OK;
+}
+
+// Grows the tabu table to hold `need` keys at load factor <= 1/2 (rehashing live keys).
+int ensure_tabu(ebic_ctx *ctx, GenState *g, int64_t need) {
+  const uint64_t want = next_pow2((uint64_t)std::max<int64_t>(2 * need, 1024));
+  if (want > (1ull << 31)) return ebic_fail(ctx, EBIC_ENOMEM, "tabu list beyond 2^31 keys");
+  if (g->tcap >= want) return EBIC_OK;
+  DevBuf fresh;
+  EBIC_CHECK_CUDA(ctx, fresh.ensure(want * 8));
+  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(fresh.p, 0, want * 8, ctx->stream));
+  if (g->tcap) {
+    k_rehash<<<(g->tcap + 255) / 256, 256, 0, ctx->stream>>>(g->tabu.as<uint64_t>(), g->tcap,
+                                                           fresh.as<uint64_t>(),
+                                                           (uint32_t)want - 1);
+    EBIC_CHECK_CUDA(ctx, cudaGetLastError());
+    prof_count(ctx, -1, 1);
+  }
+  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  g->tabu.release();
+  g->tabu = fresh;
+  fresh.p = nullptr;
+  fresh.bytes = 0;
+  g->tcap = (uint32_t)want;
+  g->drop_graphs();
+  return EBIC_OK;
+}
+
+int ensure_eval_ready(ebic_ctx *ctx, GenState *g, const ebic_params *p, int n_gen) {
+  int mode = choose_mode(ctx, p->mode, g->P, 0.5 * (p->init_min_len + p->max_len), n_gen + 1);
+  if (mode == EBIC_MODE_PLAIN) mode = EBIC_MODE_DIRECT;
+  if (mode == EBIC_MODE_BITMAP && !ctx->bitmap_ok) EBIC_TRY(ebic_build_bitmap(ctx));
+  if (mode != g->eval_mode) g->drop_graphs();
+  g->eval_mode = mode;
+  return EBIC_OK;
+}
+
+int capture_graph(ebic_ctx *ctx, GenState *g, int parity) {
+  cudaGraph_t graph = nullptr;
+  EBIC_CHECK_CUDA(ctx, cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = launch_generation(ctx, g, parity, g->cap_stream);
+  cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return ebic_fail_cuda(ctx, e, "generation capture", __FILE__, __LINE__);
+  }
+  EBIC_CHECK_CUDA(ctx, e2);
+  e = cudaGraphInstantiate(&g->graph[parity], graph, 0);
+  cudaGraphDestroy(graph);
+  EBIC_CHECK_CUDA(ctx, e);
+  return EBIC_OK;
+}
+
+constexpr int kKernelsPerGeneration = 5;
+
+}  // namespace
 
 extern "C" {
 
 int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
                          ebic_run_report *rep) {
-  (void)p; (void)n_gen; (void)rep;
-  return ebic_fail(ctx, EBIC_ESTATE, "generation loop not available");
+  if (!ctx) return EBIC_EINVAL;
+  if (!ctx->have_matrix) return ebic_fail(ctx, EBIC_ESTATE, "no matrix loaded");
+  EBIC_TRY(check_run_params(ctx, p));
+  if (n_gen < 0) return ebic_fail(ctx, EBIC_EINVAL, "n_gen must be >= 0");
+  int prev_dev = -1;
+  cudaGetDevice(&prev_dev);
+  cudaSetDevice(ctx->device);
+  struct Restore {
+    int d;
+    ~Restore() {
+      if (d >= 0) cudaSetDevice(d);
+    }
+  } restore{prev_dev};
+  GenState *g = ctx->gen;
+  if (!g || !same_run_params(g->p, *p)) {
+    EBIC_TRY(gen_create(ctx, p));
+    g = ctx->gen;
+  }
+  g->p.mode = p->mode;
+  g->p.use_graph = p->use_graph;
+  EBIC_TRY(ensure_eval_ready(ctx, g, p, n_gen));
+  GenCtl c{};
+  EBIC_TRY(read_ctl(ctx, g, &c));
+  EBIC_TRY(ensure_tabu(ctx, g, c.tabu_count + (int64_t)g->P * ((int64_t)n_gen + 1)));
+  cudaStream_t s = ctx->stream;
+  const unsigned iblocks = (unsigned)((g->P + kSlotThreads - 1) / kSlotThreads);
+  if (!g->initialised) {
+    k_init<<<iblocks, kSlotThreads, 0, s>>>(gen_args(ctx, g), g->buf(0));
+    EBIC_CHECK_CUDA(ctx, cudaGetLastError());
+    EBIC_CHECK_CUDA(ctx, launch_scoring(ctx, g, 0, s));
+    prof_count(ctx, EBIC_KERNEL_EVAL, 1);
+    prof_count(ctx, -1, kKernelsPerGeneration - 1);
+    g->initialised = true;
+    EBIC_TRY(read_ctl(ctx, g, &c));
+  }
+  if (!c.stopped) {
+    for (int i = 0; i < n_gen; ++i) {
+      const int gnext = c.gen + 1 + i;
+      const int parity = gnext & 1;
+      if (p->use_graph) {
+        if (!g->graph[parity]) EBIC_TRY(capture_graph(ctx, g, parity));
+        EBIC_CHECK_CUDA(ctx, cudaGraphLaunch(g->graph[parity], s));
+      } else {
+        EBIC_CHECK_CUDA(ctx, launch_generation(ctx, g, parity, s));
+      }
+      prof_count(ctx, EBIC_KERNEL_EVAL, 1);
+      prof_count(ctx, -1, kKernelsPerGeneration - 1);
+      if (!p->use_graph) {
+        GenCtl cc{};
+        EBIC_TRY(read_ctl(ctx, g, &cc));
+        if (cc.stopped) break;
+      }
+    }
+  }
+  EBIC_TRY(read_ctl(ctx, g, &c));
+  if (c.err) return ebic_fail(ctx, EBIC_ECUDA, "device error in the generation loop");
+  if (rep) {
+    memset(rep, 0, sizeof(*rep));
+    rep->gens_done = c.gen;
+    rep->stopped = c.stopped;
+    rep->last_hits = c.hits_last;
+    rep->n_top = c.n_top;
+    rep->n_evaluated = c.n_evaluated;
+    rep->eval_mode = g->eval_mode;
+  }
+  return EBIC_OK;
 }
+
 int ebic_get_toplist(ebic_ctx *ctx, int32_t capacity, int32_t *n_top, int32_t *cols,
                      int32_t *lens, uint64_t *fitness, uint64_t *keys, int32_t *rows) {
-  (void)capacity; (void)n_top; (void)cols; (void)lens; (void)fitness; (void)keys; (void)rows;
-  return ebic_fail(ctx, EBIC_ESTATE, "no run");
+  if (!ctx) return EBIC_EINVAL;
+  GenState *g = ctx->gen;
+  if (!g || !g->initialised) return ebic_fail(ctx, EBIC_ESTATE, "no run");
+  cudaSetDevice(ctx->device);
+  GenCtl c{};
+  EBIC_TRY(read_ctl(ctx, g, &c));
+  if (capacity < c.n_top) return ebic_fail(ctx, EBIC_EINVAL, "capacity below the list size");
+  std::vector<TopEntry> host(c.n_top > 0 ? c.n_top : 1);
+  if (c.n_top > 0)
+    EBIC_CHECK_CUDA(ctx, cudaMemcpy(host.data(), g->top.p, sizeof(TopEntry) * c.n_top,
+                                    cudaMemcpyDeviceToHost));
+  std::vector<int32_t> hc((size_t)c.n_top * kS, 0), hl(c.n_top), hr((size_t)c.n_top * 3);
+  std::vector<uint64_t> hf(c.n_top), hk(c.n_top);
+  for (int e = 0; e < c.n_top; ++e) {
+    for (int k = 0; k < host[e].len; ++k) hc[(size_t)e * kS + k] = host[e].cols[k];
+    hl[e] = host[e].len;
+    hf[e] = host[e].f;
+    hk[e] = host[e].h;
+    hr[e * 3] = host[e].rp;
+    hr[e * 3 + 1] = host[e].rn;
+    hr[e * 3 + 2] = host[e].ra;
+  }
+  if (n_top) *n_top = c.n_top;
+  if (c.n_top > 0) {
+    if (cols) EBIC_CHECK_CUDA(ctx, cudaMemcpy(cols, hc.data(), hc.size() * 4, cudaMemcpyDefault));
+    if (lens) EBIC_CHECK_CUDA(ctx, cudaMemcpy(lens, hl.data(), hl.size() * 4, cudaMemcpyDefault));
+    if (fitness)
+      EBIC_CHECK_CUDA(ctx, cudaMemcpy(fitness, hf.data(), hf.size() * 8, cudaMemcpyDefault));
+    if (keys) EBIC_CHECK_CUDA(ctx, cudaMemcpy(keys, hk.data(), hk.size() * 8, cudaMemcpyDefault));
+    if (rows) EBIC_CHECK_CUDA(ctx, cudaMemcpy(rows, hr.data(), hr.size() * 4, cudaMemcpyDefault));
+  }
+  return EBIC_OK;
 }
+
 int ebic_get_population(ebic_ctx *ctx, int32_t capacity, int32_t *cols, int32_t *lens,
                         uint8_t *dead, uint64_t *fitness) {
-  (void)capacity; (void)cols; (void)lens; (void)dead; (void)fitness;
-  return ebic_fail(ctx, EBIC_ESTATE, "no run");
+  if (!ctx) return EBIC_EINVAL;
+  GenState *g = ctx->gen;
+  if (!g || !g->initialised) return ebic_fail(ctx, EBIC_ESTATE, "no run");
+  if (capacity < g->P) return ebic_fail(ctx, EBIC_EINVAL, "capacity below pop_size");
+  cudaSetDevice(ctx->device);
+  GenCtl c{};
+  EBIC_TRY(read_ctl(ctx, g, &c));
+  const int k = c.gen & 1;
+  const size_t P = (size_t)g->P;
+  if (cols) EBIC_CHECK_CUDA(ctx, cudaMemcpy(cols, g->cols[k].p, P * kS * 4, cudaMemcpyDefault));
+  if (lens) EBIC_CHECK_CUDA(ctx, cudaMemcpy(lens, g->len[k].p, P * 4, cudaMemcpyDefault));
+  if (dead) EBIC_CHECK_CUDA(ctx, cudaMemcpy(dead, g->dead[k].p, P, cudaMemcpyDefault));
+  if (fitness) EBIC_CHECK_CUDA(ctx, cudaMemcpy(fitness, g->fit[k].p, P * 8, cudaMemcpyDefault));
+  return EBIC_OK;
 }
+
 int ebic_extract_biclusters(ebic_ctx *ctx, int32_t capacity, uint32_t *rowmask, int32_t *n_out) {
-  (void)capacity; (void)rowmask; (void)n_out;
-  return ebic_fail(ctx, EBIC_ESTATE, "no run");
+  if (!ctx) return EBIC_EINVAL;
+  GenState *g = ctx->gen;
+  if (!g || !g->initialised) return ebic_fail(ctx, EBIC_ESTATE, "no run");
+  if (!rowmask) return ebic_fail(ctx, EBIC_EINVAL, "rowmask is NULL");
+  cudaSetDevice(ctx->device);
+  GenCtl c{};
+  EBIC_TRY(read_ctl(ctx, g, &c));
+  if (capacity < c.n_top) return ebic_fail(ctx, EBIC_EINVAL, "capacity below the list size");
+  const size_t words = (size_t)c.n_top * ctx->Wst;
+  const bool dev = ebic_is_device_ptr(rowmask);
+  uint32_t *dst = rowmask;
+  if (!dev) {
+    EBIC_CHECK_CUDA(ctx, g->extract.ensure(words * 4 + 4));
+    dst = g->extract.as<uint32_t>();
+  }
+  if (words) {
+    const int64_t threads = (int64_t)words * 32;
+    k_extract<<<(unsigned)((threads + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->keys.as<uint32_t>(), ctx->R, ctx->R_pad, ctx->Wst, g->top.as<TopEntry>(),
+        g->ctl.as<GenCtl>(), g->p.neg_trends, g->p.ratio_num, g->p.ratio_den, dst);
+    EBIC_CHECK_CUDA(ctx, cudaGetLastError());
+    prof_count(ctx, -1, 1);
+    if (!dev)
+      EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(rowmask, dst, words * 4, cudaMemcpyDeviceToHost,
+                                           ctx->stream));
+  }
+  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (n_out) *n_out = c.n_top;
+  return EBIC_OK;
 }
-int64_t ebic_state_bytes(ebic_ctx *ctx) { (void)ctx; return 0; }
+
+// Checkpoint blob: header, GenCtl, current buffer (cols, len, dead, hash, fit, pen, rows,
+// att_dead), top list, tabu keys.
+struct StateHeader {
+  uint64_t magic;
+  int64_t rows;
+  int32_t cols, P, K, k;
+  int64_t n_tabu;
+  ebic_params p;
+};
+
+static const uint64_t kMagic = 0x4542494347423330ull;  // "EBICGB30"
+
+static int64_t state_size(const GenState *g, int64_t n_tabu) {
+  const int64_t P = g->P;
+  return (int64_t)sizeof(StateHeader) + (int64_t)sizeof(GenCtl) + P * kS * 4 + P * 4 + P + P * 8 +
+         P * 8 + P * 4 + P * 12 + P + (int64_t)g->K * (int64_t)sizeof(TopEntry) + n_tabu * 8;
+}
+
+int64_t ebic_state_bytes(ebic_ctx *ctx) {
+  if (!ctx || !ctx->gen || !ctx->gen->initialised) return 0;
+  GenCtl c{};
+  if (read_ctl(ctx, ctx->gen, &c) != EBIC_OK) return 0;
+  return state_size(ctx->gen, c.tabu_count);
+}
+
 int ebic_save_state(ebic_ctx *ctx, void *blob, int64_t size) {
-  (void)blob; (void)size;
-  return ebic_fail(ctx, EBIC_ESTATE, "no run");
+  if (!ctx) return EBIC_EINVAL;
+  GenState *g = ctx->gen;
+  if (!g || !g->initialised) return ebic_fail(ctx, EBIC_ESTATE, "no run");
+  cudaSetDevice(ctx->device);
+  GenCtl c{};
+  EBIC_TRY(read_ctl(ctx, g, &c));
+  std::vector<uint64_t> table(g->tcap);
+  EBIC_CHECK_CUDA(ctx, cudaMemcpy(table.data(), g->tabu.p, (size_t)g->tcap * 8,
+                                  cudaMemcpyDeviceToHost));
+  std::vector<uint64_t> keys;
+  for (uint64_t k : table)
+    if (k) keys.push_back(k);
+  std::sort(keys.begin(), keys.end());
+  const int64_t need = state_size(g, (int64_t)keys.size());
+  if (!blob || size < need) return ebic_fail(ctx, EBIC_EINVAL, "blob too small");
+  unsigned char *o = static_cast<unsigned char *>(blob);
+  StateHeader h{};
+  h.magic = kMagic;
+  h.rows = ctx->R;
+  h.cols = ctx->C;
+  h.P = g->P;
+  h.K = g->K;
+  h.k = c.gen & 1;
+  h.n_tabu = (int64_t)keys.size();
+  h.p = g->p;
+  memcpy(o, &h, sizeof(h));
+  o += sizeof(h);
+  memcpy(o, &c, sizeof(c));
+  o += sizeof(c);
+  const int k = h.k;
+  const size_t P = (size_t)g->P;
+  struct Part {
+    DevBuf *b;
+    size_t n;
+  } parts[] = {{&g->cols[k], P * kS * 4}, {&g->len[k], P * 4},  {&g->dead[k], P},
+               {&g->hash[k], P * 8},      {&g->fit[k], P * 8},  {&g->pen[k], P * 4},
+               {&g->rows[k], P * 12},     {&g->att_dead[k], P}, {&g->top, (size_t)g->K * sizeof(TopEntry)}};
+  for (const Part &pt : parts) {
+    EBIC_CHECK_CUDA(ctx, cudaMemcpy(o, pt.b->p, pt.n, cudaMemcpyDeviceToHost));
+    o += pt.n;
+  }
+  memcpy(o, keys.data(), keys.size() * 8);
+  return EBIC_OK;
 }
+
 int ebic_load_state(ebic_ctx *ctx, const ebic_params *p, const void *blob, int64_t size) {
-  (void)p; (void)blob; (void)size;
-  return ebic_fail(ctx, EBIC_ESTATE, "no run");
+  if (!ctx) return EBIC_EINVAL;
+  if (!ctx->have_matrix) return ebic_fail(ctx, EBIC_ESTATE, "no matrix loaded");
+  EBIC_TRY(check_run_params(ctx, p));
+  if (!blob || size < (int64_t)sizeof(StateHeader))
+    return ebic_fail(ctx, EBIC_EINVAL, "blob too small");
+  StateHeader h;
+  memcpy(&h, blob, sizeof(h));
+  if (h.magic != kMagic || h.rows != ctx->R || h.cols != ctx->C || h.P != p->pop_size ||
+      h.K != p->n_biclusters || !same_run_params(h.p, *p) || h.n_tabu < 0)
+    return ebic_fail(ctx, EBIC_EINVAL, "state blob does not match this matrix and parameters");
+  cudaSetDevice(ctx->device);
+  EBIC_TRY(gen_create(ctx, p));
+  GenState *g = ctx->gen;
+  if (size < state_size(g, h.n_tabu)) return ebic_fail(ctx, EBIC_EINVAL, "blob truncated");
+  const unsigned char *o = static_cast<const unsigned char *>(blob) + sizeof(h);
+  GenCtl c;
+  memcpy(&c, o, sizeof(c));
+  o += sizeof(c);
+  const int k = c.gen & 1;
+  const size_t P = (size_t)g->P;
+  struct Part {
+    DevBuf *b;
+    size_t n;
+  } parts[] = {{&g->cols[k], P * kS * 4}, {&g->len[k], P * 4},  {&g->dead[k], P},
+               {&g->hash[k], P * 8},      {&g->fit[k], P * 8},  {&g->pen[k], P * 4},
+               {&g->rows[k], P * 12},     {&g->att_dead[k], P}, {&g->top, (size_t)g->K * sizeof(TopEntry)}};
+  for (const Part &pt : parts) {
+    EBIC_CHECK_CUDA(ctx, cudaMemcpy(pt.b->p, o, pt.n, cudaMemcpyHostToDevice));
+    o += pt.n;
+  }
+  EBIC_TRY(ensure_tabu(ctx, g, h.n_tabu + (int64_t)g->P));
+  if (h.n_tabu > 0) {
+    DevBuf list;
+    EBIC_CHECK_CUDA(ctx, list.ensure((size_t)h.n_tabu * 8));
+    EBIC_CHECK_CUDA(ctx, cudaMemcpy(list.p, o, (size_t)h.n_tabu * 8, cudaMemcpyHostToDevice));
+    k_tabu_load<<<(unsigned)((h.n_tabu + 255) / 256), 256, 0, ctx->stream>>>(
+        list.as<uint64_t>(), h.n_tabu, g->tabu.as<uint64_t>(), g->tcap - 1);
+    EBIC_CHECK_CUDA(ctx, cudaGetLastError());
+    EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    list.release();
+  }
+  c.tabu_count = h.n_tabu;
+  c.hits_cur = 0;
+  c.live_cur = 0;
+  c.n_cand = 0;
+  EBIC_CHECK_CUDA(ctx, cudaMemcpy(g->ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice));
+  // column usage of the restored top list
+  std::vector<TopEntry> top(g->K);
+  memcpy(top.data(), static_cast<const unsigned char *>(blob) + sizeof(h) + sizeof(GenCtl) +
+                         P * kS * 4 + P * 4 + P + P * 8 + P * 8 + P * 4 + P * 12 + P,
+         sizeof(TopEntry) * g->K);
+  std::vector<int32_t> usage(ctx->C, 0);
+  for (int e = 0; e < c.n_top; ++e)
+    for (int q = 0; q < top[e].len; ++q) usage[top[e].cols[q]] += 1;
+  EBIC_CHECK_CUDA(ctx, cudaMemcpy(g->usage.p, usage.data(), usage.size() * 4,
+                                  cudaMemcpyHostToDevice));
+  g->initialised = true;
+  return EBIC_OK;
 }
 
 }  // extern "C"

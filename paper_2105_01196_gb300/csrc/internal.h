@@ -49,7 +49,9 @@ struct DevBuf {
 };
 
 // Population as the kernels see it: CSR (off != nullptr, len derived) or fixed-stride storage
-// with explicit lengths (off == nullptr).  dead (optional) marks slots that are not scored.
+// with explicit lengths (off == nullptr).  dead (optional) marks slots that are not scored.  In
+// the generation loop, a slot whose key a lower slot also produced is not scored either (dkeys,
+// the duplicate table), and a set *stop flag turns the whole launch into a no-op.
 struct PopView {
   const int32_t *cols;
   const int32_t *off;
@@ -57,6 +59,11 @@ struct PopView {
   const uint8_t *dead;
   int32_t stride;
   int32_t n;
+  const int32_t *stop;
+  const uint64_t *hash;
+  const uint64_t *dkeys;
+  const uint32_t *dslot;
+  uint32_t dmask;
 };
 
 // Matrix geometry and the outputs of one evaluation sweep.
@@ -151,6 +158,9 @@ cudaError_t launch_eval(int mode, const EvalArgs &a, const PopView &pv, int num_
 // zeroed beforehand.
 cudaError_t launch_eval_plain(const EvalArgs &a, const int32_t *d_cols, int32_t L, int32_t i,
                               cudaStream_t s);
+// The evaluation kernel alone (outputs and a.work must be zero): work split, grid, launch.
+cudaError_t launch_eval_kernel(int mode, const EvalArgs &a, const PopView &pv, int num_sms,
+                               cudaStream_t s);
 cudaError_t launch_fitness(const EvalArgs &a, const PopView &pv, cudaStream_t s);
 int choose_mode(const ebic_ctx *ctx, int requested, int64_t n_ind, double mean_len,
                 int expected_sweeps);

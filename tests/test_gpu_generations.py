@@ -1,0 +1,158 @@
+"""GPU parity of the device generation loop with the oracle's step-by-step EBIC (Sec. 2.4 steps
+1-9), through the C ABI.  Bar: identical populations, dead flags, fitness, top lists (columns,
+fitness, keys, row counts), tabu-hit counts, stop generation and extracted row masks."""
+
+import copy
+
+import numpy as np
+import pytest
+
+from oracle import ebic as oebic
+from oracle.fnv import chromosome_hash, tabu_key
+from oracle.params import Params as OParams
+from paper_2105_01196_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+OKEYS = [f for f in OParams.__dataclass_fields__]
+
+
+@pytest.fixture(scope="module")
+def ebic():
+    from paper_2105_01196_gb300 import ebic as e
+    return e
+
+
+def both_params(ebic, **kw):
+    base = dict(neg_trends=1, ratio_num=85, ratio_den=100, max_len=6, init_min_len=2,
+                init_max_len=6, pop_size=64, elite=4, n_biclusters=4, tabu_hit_limit=0, seed=11,
+                min_rows=2, col_cap=10, overlap_num=1, overlap_den=2, tournament=4,
+                max_attempts=4)
+    base.update(kw)
+    gp = ebic.Params.make(**base)
+    op = OParams(**{k: v for k, v in base.items() if k in OKEYS})
+    return gp, op
+
+
+def assert_same_state(ctx, st, gp):
+    top = ctx.toplist()
+    assert len(top) == len(st.top)
+    for g_e, o_e in zip(top, st.top):
+        assert g_e["cols"] == tuple(o_e.cols)
+        assert (g_e["f"], g_e["h"]) == (o_e.f, o_e.h)
+        assert (g_e["rows_pos"], g_e["rows_neg"], g_e["rows_any"]) == \
+            (o_e.rows_pos, o_e.rows_neg, o_e.rows_any)
+        assert g_e["h"] == tabu_key(chromosome_hash(g_e["cols"]))
+    cols, lens, dead, fit = ctx.population(gp.pop_size)
+    for s in range(gp.pop_size):
+        assert int(lens[s]) == len(st.pop[s]), f"slot {s}"
+        assert list(cols[s, :lens[s]]) == list(st.pop[s]), f"slot {s}"
+        assert bool(dead[s]) == st.dead[s], f"slot {s}"
+        assert int(fit[s]) == st.fit[s], f"slot {s}"
+
+
+def tiny_matrix():
+    x, _, _, _ = synth.workload_inputs(synth.WORKLOADS["tiny"])
+    return x
+
+
+@pytest.mark.parametrize("mode,use_graph", [(1, 1), (2, 1), (2, 0)])
+def test_generation_by_generation(ebic, mode, use_graph):
+    x = tiny_matrix()
+    gp, op = both_params(ebic, mode=mode, use_graph=use_graph)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        rep = ctx.run_generations(gp, 0)
+        st = oebic.initialise(x, op)
+        assert rep.gens_done == 0 and rep.n_evaluated == st.n_evaluated
+        assert_same_state(ctx, st, gp)
+        for g in range(1, 13):
+            rep = ctx.run_generations(gp, 1)
+            assert oebic.next_generation(x, st, op)
+            assert rep.gens_done == g == st.gen
+            assert rep.last_hits == st.hits[-1]
+            assert rep.n_evaluated == st.n_evaluated
+            assert_same_state(ctx, st, gp)
+
+
+def test_long_run_and_extraction(ebic):
+    x = tiny_matrix()
+    gp, op = both_params(ebic, neg_trends=0, ratio_num=1, ratio_den=1, seed=3)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        rep = ctx.run_generations(gp, 60)
+        st = oebic.run(x, op, 60)
+        assert rep.gens_done == 60 and not rep.stopped
+        assert rep.n_evaluated == st.n_evaluated
+        assert_same_state(ctx, st, gp)
+        masks = ctx.extract_biclusters(x.shape[0])
+        want = oebic.extract(x, st, op)
+        assert np.array_equal(masks[:, :want.shape[1]], want)
+        assert not masks[:, want.shape[1]:].any()
+
+
+def test_tabu_limit_stop(ebic):
+    x = tiny_matrix()
+    gp, op = both_params(ebic, pop_size=16, max_len=3, init_max_len=3, tabu_hit_limit=4, seed=5,
+                         elite=2, n_biclusters=2)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        rep = ctx.run_generations(gp, 200)
+        st = oebic.run(x, op, 200)
+        assert st.stopped and rep.stopped == 1
+        assert rep.gens_done == st.gen and rep.last_hits == st.hits[-1]
+        assert_same_state(ctx, st, gp)
+        rep2 = ctx.run_generations(gp, 5)           # a stopped run stays stopped
+        assert rep2.gens_done == rep.gens_done
+
+
+def test_checkpoint_resume(ebic):
+    x = tiny_matrix()
+    gp, op = both_params(ebic, seed=9)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        ctx.run_generations(gp, 5)
+        blob = ctx.save_state()
+        full = ctx.run_generations(gp, 7)
+        top_full = ctx.toplist()
+        pop_full = ctx.population(gp.pop_size)
+    with ebic.Context(0) as ctx2:
+        ctx2.load_matrix(x)
+        ctx2.load_state(gp, blob)
+        rep = ctx2.run_generations(gp, 7)
+        assert rep.gens_done == full.gens_done == 12
+        assert ctx2.toplist() == top_full
+        for a, b in zip(ctx2.population(gp.pop_size), pop_full):
+            assert np.array_equal(a, b)
+    st = oebic.run(x, op, 12)
+    assert [e["cols"] for e in top_full] == [tuple(e.cols) for e in st.top]
+
+
+def test_default_workload_generations(ebic):
+    """The default workload (10,000 x 100, P = 800, lengths 2-20, ratio 0.85, negative trends)
+    for 20 generations against the oracle."""
+    w = synth.WORKLOADS["default"]
+    x, _, _, _ = synth.workload_inputs(w)
+    gp, op = both_params(ebic, max_len=20, init_min_len=2, init_max_len=20, pop_size=800,
+                         elite=10, n_biclusters=10, seed=w.seed)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        rep = ctx.run_generations(gp, 20)
+        st = oebic.run(x, op, 20)
+        assert rep.gens_done == st.gen == 20
+        assert rep.n_evaluated == st.n_evaluated
+        assert_same_state(ctx, st, gp)
+
+
+def test_run_parameter_errors(ebic):
+    x = tiny_matrix()
+    with ebic.Context(0) as ctx:
+        with pytest.raises(ebic.EbicError):
+            ctx.run_generations(ebic.Params.make(), 1)        # no matrix
+        ctx.load_matrix(x)
+        for bad in (dict(max_len=30), dict(elite=20, n_biclusters=10), dict(pop_size=1),
+                    dict(tournament=0), dict(overlap_den=0), dict(mode=3)):
+            gp, _ = both_params(ebic, **bad)
+            with pytest.raises(ebic.EbicError) as e:
+                ctx.run_generations(gp, 1)
+            assert e.value.code == ebic.EBIC_EINVAL
