@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(kSlotThreads) k_init(GenArgs ga, Buf nb) {
     c[L++] = v;
   }
   int32_t *out = nb.cols + (size_t)s * kS;
-  for (int k = 0; k < L; ++k) out[k] = c[k];
+  for (int k = 0; k < kS; ++k) out[k] = k < L ? c[k] : 0;
   nb.len[s] = L;
   const bool dead = L < 2;
   nb.att_dead[s] = dead;
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(kSlotThreads) k_evolve(GenArgs ga, Buf pb, Buf
   int32_t *out = nb.cols + (size_t)s * kS;
   if (s < n_el) {  // elitism: copy top-list entry s (its key is already in the tabu list)
     const TopEntry &e = ga.top[s];
-    for (int k = 0; k < e.len; ++k) out[k] = e.cols[k];
+    for (int k = 0; k < kS; ++k) out[k] = k < e.len ? e.cols[k] : 0;
     nb.len[s] = e.len;
     nb.hash[s] = e.h;
     nb.att_dead[s] = 0;
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kSlotThreads) k_evolve(GenArgs ga, Buf pb, Buf
     }
     ++hits;
   }
-  for (int k = 0; k < L; ++k) out[k] = c[k];
+  for (int k = 0; k < kS; ++k) out[k] = k < L ? c[k] : 0;
   nb.len[s] = L;
   nb.hash[s] = h;
   nb.att_dead[s] = dead;
@@ -463,7 +463,7 @@ __device__ int process_candidates(const GenArgs &ga, const Buf &nb, const TopSme
         if (m) fr = b0 + __ffs(m) - 1;
       }
       TopEntry &ne = sm.pool[fr];
-      for (int k = lane; k < L; k += 32) ne.cols[k] = cc[k];
+      for (int k = lane; k < kS; k += 32) ne.cols[k] = k < L ? cc[k] : 0;
       if (lane == 0) {
         ne.len = L;
         ne.f = f;
