@@ -267,6 +267,41 @@ typedef struct ebic_kernel_stats {
 EBIC_API int ebic_profile_enable(ebic_ctx *ctx, int32_t on);
 EBIC_API int ebic_profile_read(ebic_ctx *ctx, int32_t kernel, ebic_kernel_stats *out);
 
+/*
+ * Population evaluation that allocates no memory.  The paper has no counterpart: this entry
+ * point exists for callers that cannot let a library allocate GPU memory.  One case is a
+ * serving process whose framework has already reserved the device memory in its own pool, so
+ * that a cudaMalloc fails or fragments the pool.  Another is a latency-critical caller that
+ * cannot afford cudaMalloc's unbounded latency or cudaFree's device-wide synchronisation.  It
+ * calls no cudaMalloc, cudaFree or other allocating routine and needs no context.
+ *
+ * Computes the same rows_pos / rows_neg / rows_any / fitness as ebic_eval_population (strict
+ * float32 comparisons, ties break both trends, t(L) = ceil(ratio * (L-1))), with the direct
+ * comparison form, from caller memory only:
+ *   x         rows * cols float32, COLUMN-major (x[c * rows + r]), device memory of `device`;
+ *   col_idx, offsets  CSR population as in ebic_eval_population, device memory;
+ *   outputs   device memory of `device`; any may be NULL;
+ *   p         neg_trends, ratio_num/den, min_rows and col_cap are read (mode is ignored);
+ *   cuda_stream  a cudaStream_t of `device` (NULL = the legacy default stream);
+ *   msg       optional buffer of msg_len bytes for the message of a failure.
+ * Scratch: the per-individual accumulators, a work counter and an error word live in one
+ * file-scope static device array of 3 * EBIC_NOALLOC_MAX_IND + 2 int32 (768 KB), which every
+ * GPU that loads the library holds until the process exits.  Its device address is looked up on
+ * the first call for each device, so make that first call before any stream capture.  Every
+ * call shares the array and clears the part it uses; calls whose work overlaps on the GPU (on
+ * different streams or from different threads) race on it and must be serialised by the caller.
+ * The call returns after the work has finished on `cuda_stream`.
+ * Errors: EBIC_EINVAL (n_ind > EBIC_NOALLOC_MAX_IND, a host pointer, bad shape, parameter or
+ * chromosome), EBIC_ENAN (NaN or Inf in x), EBIC_ECUDA.
+ */
+#define EBIC_NOALLOC_MAX_IND 65536
+EBIC_API int ebic_eval_population_noalloc(const float *x, int64_t rows, int32_t cols,
+                                          const int32_t *col_idx, const int32_t *offsets,
+                                          int32_t n_ind, const ebic_params *p,
+                                          int32_t *rows_pos, int32_t *rows_neg,
+                                          int32_t *rows_any, uint64_t *fitness, int32_t device,
+                                          void *cuda_stream, char *msg, int32_t msg_len);
+
 #ifdef __cplusplus
 }
 #endif

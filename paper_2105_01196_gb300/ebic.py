@@ -97,6 +97,8 @@ SIGNATURES = {
     "ebic_load_state": (ctypes.c_int, [_VP, _VP, _VP, _I64]),
     "ebic_profile_enable": (ctypes.c_int, [_VP, _I32]),
     "ebic_profile_read": (ctypes.c_int, [_VP, _I32, _VP]),
+    "ebic_eval_population_noalloc": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _I32, _VP, _VP,
+                                                    _VP, _VP, _VP, _I32, _VP, _VP, _I32]),
 }
 
 
@@ -300,6 +302,28 @@ def ebic_profile_read(ctx, kernel):
     st = KernelStats()
     _check(ctx, _lib.ebic_profile_read(ctx, int(kernel), ctypes.byref(st)))
     return st.as_dict()
+
+
+NOALLOC_MAX_IND = 65536
+
+
+def ebic_eval_population_noalloc(x_colmajor, col_idx, offsets, params, rows_pos=None,
+                                 rows_neg=None, rows_any=None, fitness=None, device=0,
+                                 stream=None):
+    """Allocation-free evaluation for callers that cannot let the library allocate GPU memory.
+
+    Every array is caller-owned device memory; x_colmajor is float32 [cols, rows].  Returns the
+    outputs passed in.  Raises EbicError with the library's message on failure."""
+    cols, rows = x_colmajor.shape
+    n = (offsets.numel() if _is_torch(offsets) else offsets.size) - 1
+    buf = ctypes.create_string_buffer(256)
+    status = _lib.ebic_eval_population_noalloc(
+        ptr(x_colmajor), int(rows), int(cols), ptr(col_idx), ptr(offsets), int(n),
+        ctypes.byref(params), ptr(rows_pos), ptr(rows_neg), ptr(rows_any), ptr(fitness),
+        int(device), stream, buf, 256)
+    if status != EBIC_OK:
+        raise EbicError(status, buf.value.decode())
+    return rows_pos, rows_neg, rows_any, fitness
 
 
 class Context:
