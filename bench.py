@@ -249,9 +249,10 @@ def main():
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
     torch.cuda.synchronize()
-    st_eval = ctx.profile_read(ebic.KERNEL_EVAL)
+    stats = {name: ctx.profile_read(kid) for name, kid in
+             (("eval", ebic.KERNEL_EVAL), ("evolve", ebic.KERNEL_EVOLVE),
+              ("finish", ebic.KERNEL_FINISH), ("bitmap_build", ebic.KERNEL_BITMAP_BUILD))}
     st_all = ctx.profile_read(ebic.KERNEL_ALL)
-    st_build = ctx.profile_read(ebic.KERNEL_BITMAP_BUILD)
     ctx.profile_enable(False)
     clk = clocks.stop()
     if dist:
@@ -286,16 +287,26 @@ def main():
         return
 
     peak, peak_kind = load_peaks()
+    timed_ms = sum(v["ms"] for v in stats.values())
+    for v in stats.values():
+        v["avg_us"] = 1e3 * v["ms"] / v["timed_launches"] if v["timed_launches"] else None
+        v["share_of_kernel_time"] = v["ms"] / timed_ms if timed_ms else None
+    dominant = max(stats, key=lambda k: stats[k]["ms"])
+    kernel_names = {"eval": "k_eval_bitmap" if args.mode != "direct" else "k_eval_direct",
+                    "evolve": "k_evolve", "finish": "k_finish", "bitmap_build": "k_build_bitmap"}
     roof = None
-    if st_eval["timed_launches"] > 0:
-        n_l = st_eval["timed_launches"]
-        avg_s = st_eval["ms"] / n_l / 1e3
-        per_launch = st_eval["alg_bytes"] / n_l
+    se = stats["eval"]
+    if se["timed_launches"] > 0 and se["ms"] > 0:
+        n_l = se["timed_launches"]
+        avg_s = se["ms"] / n_l / 1e3
+        per_launch = se["alg_bytes"] / n_l
         achieved = per_launch / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_eval_bitmap",
+                "frac": achieved / peak, "traffic": None, "kernel": kernel_names["eval"],
                 "peak_kind": peak_kind, "alg_bytes_per_launch": per_launch,
-                "avg_launch_us": avg_s * 1e6, "launches": n_l}
+                "avg_launch_us": avg_s * 1e6, "launches": n_l,
+                "share_of_kernel_time": se["share_of_kernel_time"],
+                "dominant_kernel": kernel_names[dominant]}
     line = {"metric": METRIC, "value": units / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup),
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -307,7 +318,7 @@ def main():
                        "parallelism": f"independent job per GPU x{world}"},
             "gpu_launches": int(st_all["launches"]),
             "roofline": roof,
-            "kernels": {"eval": st_eval, "bitmap_build": st_build},
+            "kernels": stats,
             "clocks": clk,
             "e2e": e2e}
     if gens > 0:

@@ -239,10 +239,13 @@ EBIC_API int ebic_load_state(ebic_ctx *ctx, const ebic_params *p, const void *bl
 
 /*
  * Kernel statistics for roofline accounting (no counterpart in the paper).  While enabled, the
- * context records CUDA events on its stream around every launch of the evaluation kernel and of
- * the bitmap build, and counts every kernel it launches (graph replays included).
- *   kernel  EBIC_KERNEL_EVAL (direct or bitmap evaluation), EBIC_KERNEL_BITMAP_BUILD, or
- *           EBIC_KERNEL_ALL (launches only).
+ * context records CUDA events on its stream around every launch of the evaluation kernel, the
+ * bitmap build and the generation-loop kernels (inside replayed CUDA graphs too, through event
+ * nodes re-pointed at fresh events before each replay), and it counts every kernel it launches.
+ *   kernel  EBIC_KERNEL_EVAL (direct or bitmap evaluation, single sweeps and generations),
+ *           EBIC_KERNEL_BITMAP_BUILD, EBIC_KERNEL_EVOLVE (children of one generation),
+ *           EBIC_KERNEL_FINISH (scoring, tabu list and top-list update of one generation), or
+ *           EBIC_KERNEL_ALL (launch count only).
  *   ms         summed event time of the timed launches;
  *   alg_bytes  algorithmic bytes of those launches: the bitmap form reads sum_i (L_i - 1) pair
  *              words per 32 rows and direction, the direct form gathers sum_i L_i keys per row,
@@ -254,6 +257,9 @@ EBIC_API int ebic_load_state(ebic_ctx *ctx, const ebic_params *p, const void *bl
 #define EBIC_KERNEL_EVAL 0
 #define EBIC_KERNEL_BITMAP_BUILD 1
 #define EBIC_KERNEL_ALL 2
+#define EBIC_KERNEL_EVOLVE 3
+#define EBIC_KERNEL_FINISH 4
+#define EBIC_KERNEL_COUNT 5
 
 typedef struct ebic_kernel_stats {
   int64_t launches;

@@ -93,9 +93,9 @@ cudaEvent_t prof_event(ebic_ctx *ctx) {
 }
 
 void prof_push(ebic_ctx *ctx, cudaEvent_t a, cudaEvent_t b, int kernel, double bytes, double ops,
-               double units) {
+               double units, bool own_a, bool own_b) {
   if (a && b) {
-    ctx->pending.push_back(PendingTiming{a, b, kernel, bytes, ops, units});
+    ctx->pending.push_back(PendingTiming{a, b, kernel, bytes, ops, units, own_a, own_b});
   } else {
     if (a) ctx->ev_pool.push_back(a);
     if (b) ctx->ev_pool.push_back(b);
@@ -128,11 +128,12 @@ void prof_end(ebic_ctx *ctx, cudaEvent_t a, int kernel, double bytes, double ops
     return;
   }
   cudaEventRecord(b, ctx->stream);
-  ctx->pending.push_back(PendingTiming{a, b, kernel, bytes, ops, units});
+  ctx->pending.push_back(PendingTiming{a, b, kernel, bytes, ops, units, true, true});
 }
 
 void prof_count(ebic_ctx *ctx, int kernel, int64_t n) {
-  if (kernel >= 0 && kernel < 2) ctx->kst[kernel].launches += n;
+  if (kernel >= 0 && kernel < EBIC_KERNEL_COUNT && kernel != EBIC_KERNEL_ALL)
+    ctx->kst[kernel].launches += n;
   ctx->kst[EBIC_KERNEL_ALL].launches += n;
 }
 
@@ -149,8 +150,8 @@ void prof_collect(ebic_ctx *ctx) {
     } else {
       cudaGetLastError();
     }
-    ctx->ev_pool.push_back(t.a);
-    ctx->ev_pool.push_back(t.b);
+    if (t.own_a) ctx->ev_pool.push_back(t.a);
+    if (t.own_b) ctx->ev_pool.push_back(t.b);
   }
   ctx->pending.clear();
 }
@@ -171,7 +172,7 @@ int ebic_profile_enable(ebic_ctx *ctx, int32_t on) {
 }
 
 int ebic_profile_read(ebic_ctx *ctx, int32_t kernel, ebic_kernel_stats *out) {
-  if (!ctx || !out || kernel < 0 || kernel > 2) return EBIC_EINVAL;
+  if (!ctx || !out || kernel < 0 || kernel >= EBIC_KERNEL_COUNT) return EBIC_EINVAL;
   DeviceGuard g(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   cudaGetLastError();

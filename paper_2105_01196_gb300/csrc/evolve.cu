@@ -2,20 +2,22 @@
 // elitism, tournament selection with an exponential penalty on overused columns, tabu list of
 // chromosome hashes, tabu-hit termination; parameters of Sec. 2.4's last paragraph).
 //
-// One generation is five kernels, captured once per buffer parity as a CUDA graph and replayed:
-//   k_evolve    one thread per slot: elites from the top list (step 4), otherwise tournament,
-//               optional one-point crossover and one mutation, tabu probe with up to
-//               max_attempts retries (step 5); live children enter the duplicate table;
+// One generation is three kernels, captured once per buffer parity as a CUDA graph and replayed:
+//   k_evolve    one lane per (slot, attempt): elites from the top list (step 4), otherwise
+//               penalised tournament, optional one-point crossover and one mutation, tabu probe;
+//               the lowest attempt that misses the tabu list wins (step 5); live children enter
+//               this generation's duplicate table;
 //   k_eval_*    the persistent evaluation kernel (eval.cu) over the new population, skipping
 //               tabu-dead and duplicate slots (step 7);
-//   k_score     one thread per slot: final dead flags, tabu hits, fitness, candidates that can
-//               enter the top list;
-//   k_toplist   one block: tabu-hit stop test (step 6), then the top rank list update
-//               (step 7), column usage;
-//   k_post      one thread per slot: penalties for the next tournament, tabu insertion,
-//               clearing of the per-generation tables.
-// Generation g reads population buffer (g-1)&1 and writes g&1.  Once the stop flag is set every
-// kernel returns at once, so further replays are no-ops.  The random words come from
+//   k_finish    all blocks: final dead flags, tabu hits, fitness, candidates for the top list,
+//               and the previous generation's keys moved from its duplicate table into the tabu
+//               list; then the last block to finish: tabu-hit stop test (step 6), top rank list
+//               update (step 7), column usage, counters for the next generation.
+// Generation g reads population buffer (g-1)&1 and writes g&1, and uses duplicate table g&1.
+// The tabu list a child is probed against is the hashed set of generations <= g-2 plus the
+// duplicate table of generation g-1 (its live non-elite keys), which is the whole tabu list as
+// it stood at the start of generation g.  Once the stop flag is set every kernel returns at once,
+// so further replays are no-ops.  The random words come from
 // Philox4x32-10 (Salmon et al., SC'11) with counter (generation, slot, attempt, block).
 #include <string.h>
 
@@ -31,7 +33,7 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kS = EBIC_MAX_LEN;  // population slot stride (columns)
 constexpr int kSlotThreads = 64;
 constexpr int kTopThreads = 1024;
-constexpr int kSortSmem = 4096;   // candidates sorted in shared memory up to this many
+constexpr int kSortSmemMax = 4096;  // most candidates sorted in shared memory
 
 struct TopEntry {
   uint64_t f, h;
@@ -46,10 +48,12 @@ struct GenCtl {
   int32_t hits_last;   // tabu hits of the last generation built
   int32_t n_top;       // entries in the top list
   int32_t live_cur;    // live slots of the generation being scored
-  int32_t n_cand;      // top-list candidates collected by k_score
-  int32_t err;
+  int32_t n_cand;      // top-list candidates collected by k_finish
+  int32_t done;        // blocks of k_finish that have finished their slots
   long long n_evaluated;
   long long tabu_count;
+  long long sum_len;   // sum of the lengths of all scored live slots (evaluation work)
+  long long len_cur;   // the same for the generation being scored
 };
 
 // One population buffer (P slots of stride kS).
@@ -57,7 +61,6 @@ struct Buf {
   int32_t *cols, *len, *att_hits, *rows;  // rows: [3][P] pos, neg, any
   uint8_t *att_dead, *dead;
   uint64_t *hash, *fit;
-  int32_t *pen;
 };
 
 struct GenArgs {
@@ -66,14 +69,15 @@ struct GenArgs {
   int32_t *usage;
   uint64_t *tabu;
   uint32_t tmask;
-  uint64_t *dkeys;
-  uint32_t *dslot;
+  uint64_t *dkeys[2];  // duplicate tables, one per generation parity
+  uint32_t *dslot[2];
   uint32_t dmask;
-  int32_t *rows_scr;  // [3][P] evaluation output (zeroed by k_post)
+  int32_t *rows_scr;  // [3][P] evaluation output (zeroed by k_finish)
   int32_t *work;
   uint64_t *cand_f, *cand_h;
   int32_t *cand_s;
   int32_t cand_cap;
+  int32_t sort_cap;   // candidates sorted in shared memory up to this many (a power of two)
   uint64_t seed;
   int32_t P, C, K, E, T, A, max_len, init_min, init_max;
   int32_t min_rows, col_cap, ov_num, ov_den, tabu_limit;
@@ -86,7 +90,7 @@ constexpr uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
 
 struct WordStream {
   uint32_t k0, k1, c0, c1, c2, blk;
-  uint32_t buf[4];
+  uint32_t w0, w1, w2, w3;
   int pos;
   __device__ WordStream(uint64_t seed, uint32_t g, uint32_t s, uint32_t a)
       : k0((uint32_t)seed), k1((uint32_t)(seed >> 32)), c0(g), c1(s), c2(a), blk(0), pos(4) {}
@@ -106,16 +110,19 @@ struct WordStream {
       x2 = y2;
       x3 = lo0;
     }
-    buf[0] = x0;
-    buf[1] = x1;
-    buf[2] = x2;
-    buf[3] = x3;
+    w0 = x0;
+    w1 = x1;
+    w2 = x2;
+    w3 = x3;
     ++blk;
     pos = 0;
   }
+  // Next word of the stream (the four words of a block in order; kept in registers).
   __device__ uint32_t next() {
     if (pos == 4) refill();
-    return buf[pos++];
+    const uint32_t w = pos == 0 ? w0 : (pos == 1 ? w1 : (pos == 2 ? w2 : w3));
+    ++pos;
+    return w;
   }
   // Uniform integer in [0, n): high word of word * n.
   __device__ uint32_t below(uint32_t n) { return __umulhi(next(), n); }
@@ -138,28 +145,64 @@ __device__ uint64_t chromosome_key(const int32_t *c, int L) {
 
 // ------------------------------------------------------------------ selection
 
-// Sign of fa * 2^-ua - fb * 2^-ub, exactly (ua, ub >= 0).
-__device__ int cmp_penalised(uint64_t fa, int ua, uint64_t fb, int ub) {
-  if (ub < ua) return -cmp_penalised(fb, ub, fa, ua);
-  const int s = ub - ua;  // compare fa * 2^s with fb
+// Sign of fa * 2^s - fb for s >= 0, exactly.
+__device__ __forceinline__ int cmp_shifted(uint64_t fa, int s, uint64_t fb) {
   if (fa == 0ull) return fb == 0ull ? 0 : -1;
   if (s >= 64) return 1;
-  const uint64_t q = fb >> s;
+  const uint64_t q = fb >> s;  // fa * 2^s > fb  <=>  fa > floor(fb / 2^s)
   if (fa > q) return 1;
   if (fa < q) return -1;
-  const uint64_t rem = fb & ((s ? (1ull << s) : 1ull) - 1ull);
-  return rem ? -1 : 0;
+  return (fb & ((s ? (1ull << s) : 1ull) - 1ull)) ? -1 : 0;
 }
 
+// Sign of fa * 2^-ua - fb * 2^-ub, exactly (ua, ub >= 0).
+__device__ __forceinline__ int cmp_penalised(uint64_t fa, int ua, uint64_t fb, int ub) {
+  return ub >= ua ? cmp_shifted(fa, ub - ua, fb) : -cmp_shifted(fb, ua - ub, fa);
+}
+
+// T uniform candidates of the previous population; the best penalised score f * 2^-U wins,
+// ties to the lower slot.  U = sum over the candidate's columns of their top-list usage, computed
+// here from the usage table.  Candidates are drawn four at a time and their loads issued together.
 __device__ int tournament(WordStream &st, const GenArgs &ga, const Buf &pb) {
-  int best = -1;
-  for (int t = 0; t < ga.T; ++t) {
-    const int i = (int)st.below((uint32_t)ga.P);
-    if (best < 0) {
-      best = i;
-    } else {
-      const int c = cmp_penalised(pb.fit[i], pb.pen[i], pb.fit[best], pb.pen[best]);
-      if (c > 0 || (c == 0 && i < best)) best = i;
+  int best = -1, ub = 0;
+  uint64_t fb = 0ull;
+  for (int t0 = 0; t0 < ga.T; t0 += 4) {
+    int idx[4], Lc[4], u[4];
+    uint64_t f[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) idx[j] = (t0 + j < ga.T) ? (int)st.below((uint32_t)ga.P) : -1;
+    int maxL = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      f[j] = idx[j] >= 0 ? pb.fit[idx[j]] : 0ull;
+      Lc[j] = idx[j] >= 0 ? pb.len[idx[j]] : 0;
+      u[j] = 0;
+      maxL = max(maxL, Lc[j]);
+    }
+    for (int k = 0; k < maxL; k += 4) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (k >= Lc[j]) continue;
+        const int4 v = reinterpret_cast<const int4 *>(pb.cols + (size_t)idx[j] * kS)[k >> 2];
+        const int u0 = ga.usage[v.x], u1 = ga.usage[v.y], u2 = ga.usage[v.z], u3 = ga.usage[v.w];
+        u[j] += u0 + (k + 1 < Lc[j] ? u1 : 0) + (k + 2 < Lc[j] ? u2 : 0) + (k + 3 < Lc[j] ? u3 : 0);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (idx[j] < 0) continue;
+      if (best < 0) {
+        best = idx[j];
+        fb = f[j];
+        ub = u[j];
+        continue;
+      }
+      const int c = cmp_penalised(f[j], u[j], fb, ub);
+      if (c > 0 || (c == 0 && idx[j] < best)) {
+        best = idx[j];
+        fb = f[j];
+        ub = u[j];
+      }
     }
   }
   return best;
@@ -276,96 +319,65 @@ __global__ void __launch_bounds__(kSlotThreads) k_init(GenArgs ga, Buf nb) {
   nb.att_hits[s] = 0;
   const uint64_t h = chromosome_key(c, L);
   nb.hash[s] = h;
-  if (!dead) dedup_insert(ga.dkeys, ga.dslot, ga.dmask, h, s);
+  if (!dead) dedup_insert(ga.dkeys[0], ga.dslot[0], ga.dmask, h, s);
 }
 
-__global__ void __launch_bounds__(kSlotThreads) k_evolve(GenArgs ga, Buf pb, Buf nb) {
+// One lane per (slot, attempt): the attempts of a slot run side by side in a group of G lanes
+// (G = the power of two >= max_attempts) and the lowest attempt whose key misses the tabu list
+// wins, which is exactly the sequential retry rule; when every attempt hits, the slot is dead
+// and keeps the last attempt's child.  Children are built in shared memory.
+constexpr int kEvolveThreads = 128;
+
+__global__ void __launch_bounds__(kEvolveThreads) k_evolve(GenArgs ga, Buf pb, Buf nb, int G,
+                                                           int par) {
+  __shared__ int32_t s_child[kEvolveThreads][kS + 1];
   if (ga.ctl->stopped) return;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= ga.P) return;
+  const int lane = threadIdx.x & 31;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = gtid / G, a = gtid - (gtid / G) * G;
+  const bool valid = s < ga.P;
   const int g = ga.ctl->gen + 1;
   const int n_el = min(ga.E, ga.ctl->n_top);
-  int32_t *out = nb.cols + (size_t)s * kS;
-  if (s < n_el) {  // elitism: copy top-list entry s (its key is already in the tabu list)
-    const TopEntry &e = ga.top[s];
-    for (int k = 0; k < kS; ++k) out[k] = k < e.len ? e.cols[k] : 0;
-    nb.len[s] = e.len;
-    nb.hash[s] = e.h;
-    nb.att_dead[s] = 0;
-    nb.att_hits[s] = 0;
-    return;
-  }
-  int32_t c[kS];
-  int L = 0, hits = 0;
-  uint64_t h = 0;
-  bool dead = true;
-  for (int a = 0; a < ga.A; ++a) {
+  const bool elite = valid && s < n_el;
+  int32_t *c = s_child[threadIdx.x];
+  int L = 0;
+  uint64_t h = 0ull;
+  bool ok = false;
+  if (valid && !elite && a < ga.A) {
     make_child(ga, pb, g, s, a, c, L);
     h = chromosome_key(c, L);
-    if (!tabu_contains(ga.tabu, ga.tmask, h)) {
-      dead = false;
-      break;
-    }
-    ++hits;
+    ok = !tabu_contains(ga.tabu, ga.tmask, h) &&
+         !tabu_contains(ga.dkeys[par ^ 1], ga.dmask, h);  // generation g-1's live keys
   }
+  const unsigned m = __ballot_sync(kFull, ok);
+  if (!valid) return;
+  int32_t *out = nb.cols + (size_t)s * kS;
+  if (elite) {  // elitism: copy top-list entry s (its key is already in the tabu list)
+    if (a == 0) {
+      const TopEntry &e = ga.top[s];
+      for (int k = 0; k < kS; ++k) out[k] = k < e.len ? e.cols[k] : 0;
+      nb.len[s] = e.len;
+      nb.hash[s] = e.h;
+      nb.att_dead[s] = 0;
+      nb.att_hits[s] = 0;
+    }
+    return;
+  }
+  const int gbase = lane - (lane % G);
+  const unsigned gm = (m >> gbase) & (G >= 32 ? kFull : ((1u << G) - 1u));
+  const bool dead = gm == 0u;
+  const int win = dead ? ga.A - 1 : __ffs(gm) - 1;
+  if (a != win) return;
   for (int k = 0; k < kS; ++k) out[k] = k < L ? c[k] : 0;
   nb.len[s] = L;
   nb.hash[s] = h;
   nb.att_dead[s] = dead;
-  nb.att_hits[s] = hits;
-  if (!dead) dedup_insert(ga.dkeys, ga.dslot, ga.dmask, h, s);
+  nb.att_hits[s] = dead ? ga.A : win;
+  if (!dead) dedup_insert(ga.dkeys[par], ga.dslot[par], ga.dmask, h, s);
 }
 
 __device__ __forceinline__ bool key_before(uint64_t fa, uint64_t ha, uint64_t fb, uint64_t hb) {
   return fa > fb || (fa == fb && ha < hb);
-}
-
-__global__ void __launch_bounds__(256) k_score(GenArgs ga, Buf nb) {
-  if (ga.ctl->stopped) return;
-  __shared__ int s_hits, s_live;
-  if (threadIdx.x == 0) {
-    s_hits = 0;
-    s_live = 0;
-  }
-  __syncthreads();
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < ga.P) {
-    const bool att_dead = nb.att_dead[s] != 0;
-    const uint64_t h = nb.hash[s];
-    const bool dup = !att_dead && dedup_is_dup(ga.dkeys, ga.dslot, ga.dmask, h, s);
-    const bool dead = att_dead || dup;
-    nb.dead[s] = dead;
-    const int rp = ga.rows_scr[s], rn = ga.rows_scr[ga.P + s], ra = ga.rows_scr[2 * ga.P + s];
-    nb.rows[s] = rp;
-    nb.rows[ga.P + s] = rn;
-    nb.rows[2 * ga.P + s] = ra;
-    const int L = nb.len[s];
-    const uint64_t f =
-        (dead || ra < ga.min_rows) ? 0ull : ((uint64_t)ra << (L < ga.col_cap ? L : ga.col_cap));
-    nb.fit[s] = f;
-    const int hits = nb.att_hits[s] + (dup ? 1 : 0);
-    if (hits) atomicAdd(&s_hits, hits);
-    if (!dead) atomicAdd(&s_live, 1);
-    if (!dead && f > 0ull) {
-      const int nt = ga.ctl->n_top;
-      bool potential = true;
-      if (nt >= ga.K) {
-        const TopEntry &last = ga.top[ga.K - 1];
-        potential = key_before(f, h, last.f, last.h);
-      }
-      if (potential) {
-        const int q = atomicAdd(&ga.ctl->n_cand, 1);
-        ga.cand_f[q] = f;
-        ga.cand_h[q] = h;
-        ga.cand_s[q] = s;
-      }
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if (s_hits) atomicAdd(&ga.ctl->hits_cur, s_hits);
-    if (s_live) atomicAdd(&ga.ctl->live_cur, s_live);
-  }
 }
 
 // Bitonic sort of n (f, h, s) candidates into "rank" order (f descending, key ascending) by the
@@ -403,14 +415,18 @@ __device__ void block_sort(uint64_t *f, uint64_t *h, int32_t *sl, int n) {
   }
 }
 
+constexpr int kChunk = 32;  // candidates whose data is staged in shared memory at a time
+
 struct TopSmem {
   TopEntry *pool;    // K + 1 entries
   uint32_t *colbits; // ceil(C / 32) words
   int32_t *idx;      // K + 1: pool index of list position
   int32_t *idx2;     // K + 1
   uint8_t *used;     // K + 1
-  uint64_t *sf, *sh; // kSortSmem
+  uint64_t *sf, *sh; // sort_cap
   int32_t *ss;
+  int32_t *ccols;    // kChunk x kS: columns of the staged candidates
+  int32_t *cmeta;    // kChunk x 4: length, rows_pos, rows_neg, rows_any
 };
 
 // Number of columns of pool entry e present in colbits (warp-wide).
@@ -423,13 +439,13 @@ __device__ __forceinline__ int overlap(const TopSmem &sm, const TopEntry &e, int
   return __reduce_add_sync(kFull, cnt);
 }
 
-// Sequential top-list update by one warp over sorted candidates (f, h, s); returns new n.
-__device__ int process_candidates(const GenArgs &ga, const Buf &nb, const TopSmem &sm, int n,
-                                  const uint64_t *cf, const uint64_t *ch, const int32_t *cs,
-                                  int count, int lane) {
-  for (int q = 0; q < count; ++q) {
+// Sequential top-list update by one warp over the staged, sorted candidates q0..q1-1 (their data
+// is in sm.ccols / sm.cmeta at q - q0).  Returns the new list length; *stop is set when a
+// candidate ranks at position >= K (every later candidate ranks lower still).
+__device__ int process_chunk(const GenArgs &ga, const TopSmem &sm, int n, const uint64_t *cf,
+                             const uint64_t *ch, int q0, int q1, int lane, bool *stop) {
+  for (int q = q0; q < q1; ++q) {
     const uint64_t f = cf[q], h = ch[q];
-    const int s = cs[q];
     int pos = 0;
     bool dup = false;
     for (int e0 = 0; e0 < n; e0 += 32) {
@@ -444,10 +460,15 @@ __device__ int process_candidates(const GenArgs &ga, const Buf &nb, const TopSme
       pos += __popc(__ballot_sync(kFull, before));
     }
     if (dup) continue;
-    if (pos >= ga.K) break;  // the list is full and every later candidate ranks after it
-    const int L = nb.len[s];
-    const int32_t *cc = nb.cols + (size_t)s * kS;
-    for (int k = lane; k < L; k += 32) atomicOr(&sm.colbits[cc[k] >> 5], 1u << (cc[k] & 31));
+    if (pos >= ga.K) {  // the list is full and every later candidate ranks after it
+      *stop = true;
+      break;
+    }
+    const int32_t *cc = sm.ccols + (q - q0) * kS;
+    const int L = sm.cmeta[(q - q0) * 4];
+    const int c0 = lane < L ? cc[lane] : 0, c1 = lane + 32 < L ? cc[lane + 32] : 0;
+    if (lane < L) atomicOr(&sm.colbits[c0 >> 5], 1u << (c0 & 31));
+    if (lane + 32 < L) atomicOr(&sm.colbits[c1 >> 5], 1u << (c1 & 31));
     __syncwarp();
     bool ok = true;
     for (int e = 0; e < pos && ok; ++e) {
@@ -463,14 +484,15 @@ __device__ int process_candidates(const GenArgs &ga, const Buf &nb, const TopSme
         if (m) fr = b0 + __ffs(m) - 1;
       }
       TopEntry &ne = sm.pool[fr];
-      for (int k = lane; k < kS; k += 32) ne.cols[k] = k < L ? cc[k] : 0;
+      ne.cols[lane] = lane < L ? c0 : 0;
+      ne.cols[lane + 32] = lane + 32 < L ? c1 : 0;
       if (lane == 0) {
         ne.len = L;
         ne.f = f;
         ne.h = h;
-        ne.rp = nb.rows[s];
-        ne.rn = nb.rows[ga.P + s];
-        ne.ra = nb.rows[2 * ga.P + s];
+        ne.rp = sm.cmeta[(q - q0) * 4 + 1];
+        ne.rn = sm.cmeta[(q - q0) * 4 + 2];
+        ne.ra = sm.cmeta[(q - q0) * 4 + 3];
         sm.used[fr] = 1;
       }
       for (int e = lane; e < pos; e += 32) sm.idx2[e] = sm.idx[e];
@@ -494,27 +516,64 @@ __device__ int process_candidates(const GenArgs &ga, const Buf &nb, const TopSme
       n = m;
       __syncwarp();
     }
-    for (int k = lane; k < L; k += 32) atomicAnd(&sm.colbits[cc[k] >> 5], ~(1u << (cc[k] & 31)));
+    if (lane < L) atomicAnd(&sm.colbits[c0 >> 5], ~(1u << (c0 & 31)));
+    if (lane + 32 < L) atomicAnd(&sm.colbits[c1 >> 5], ~(1u << (c1 & 31)));
     __syncwarp();
   }
   return n;
 }
 
-// Sorts `count` candidates held in global arrays (in shared memory when they fit) and lets
-// warp 0 process them.  Returns the new list length (valid in every thread).
+// Bitonic sort of up to 32 candidates across the lanes of one warp (lane i holds candidate i or
+// a sentinel that sorts last); results land in sf/sh/ss[0..count).
+__device__ void warp_sort(const uint64_t *gf, const uint64_t *gh, const int32_t *gs, int count,
+                          uint64_t *sf, uint64_t *sh, int32_t *ss, int lane) {
+  uint64_t f = lane < count ? __ldcg(gf + lane) : 0ull;
+  uint64_t h = lane < count ? __ldcg(gh + lane) : ~0ull;
+  int32_t sl = lane < count ? __ldcg(gs + lane) : 0x7FFFFFFF;
+  for (int k = 2; k <= 32; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const uint64_t pf = __shfl_xor_sync(kFull, f, j), ph = __shfl_xor_sync(kFull, h, j);
+      const int32_t ps = __shfl_xor_sync(kFull, sl, j);
+      const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+      const bool partner_first = key_before(pf, ph, f, h);
+      const bool partner_later = key_before(f, h, pf, ph);
+      const bool take = (lower == up) ? partner_first : partner_later;
+      if (take) {
+        f = pf;
+        h = ph;
+        sl = ps;
+      }
+    }
+  }
+  if (lane < count) {
+    sf[lane] = f;
+    sh[lane] = h;
+    ss[lane] = sl;
+  }
+}
+
+// Sorts `count` candidates held in global arrays (within a warp, in shared memory, or in place
+// in global memory, by size), then stages them kChunk at a time in shared memory and lets warp 0
+// process each chunk.  Returns the new list length (valid in every thread).
 __device__ int sort_and_process(const GenArgs &ga, const Buf &nb, const TopSmem &sm, int n,
-                                int count, int *s_n) {
+                                int count, int *s_n, int *s_stop) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int N = 1;
   while (N < count) N <<= 1;
   const uint64_t *cf;
   const uint64_t *ch;
   const int32_t *cs;
-  if (N <= kSortSmem) {
+  if (count <= 32) {
+    if (warp == 0) warp_sort(ga.cand_f, ga.cand_h, ga.cand_s, count, sm.sf, sm.sh, sm.ss, lane);
+    __syncthreads();
+    cf = sm.sf;
+    ch = sm.sh;
+    cs = sm.ss;
+  } else if (N <= ga.sort_cap) {
     for (int i = threadIdx.x; i < count; i += blockDim.x) {
-      sm.sf[i] = ga.cand_f[i];
-      sm.sh[i] = ga.cand_h[i];
-      sm.ss[i] = ga.cand_s[i];
+      sm.sf[i] = __ldcg(ga.cand_f + i);
+      sm.sh[i] = __ldcg(ga.cand_h + i);
+      sm.ss[i] = __ldcg(ga.cand_s + i);
     }
     __syncthreads();
     block_sort(sm.sf, sm.sh, sm.ss, count);
@@ -527,26 +586,130 @@ __device__ int sort_and_process(const GenArgs &ga, const Buf &nb, const TopSmem 
     ch = ga.cand_h;
     cs = ga.cand_s;
   }
-  if (warp == 0) {
-    const int m = process_candidates(ga, nb, sm, n, cf, ch, cs, count, lane);
-    if (lane == 0) *s_n = m;
+  if (threadIdx.x == 0) {
+    *s_n = n;
+    *s_stop = 0;
   }
-  __syncthreads();
+  for (int q0 = 0; q0 < count; q0 += kChunk) {
+    const int q1 = min(count, q0 + kChunk);
+    for (int i = threadIdx.x; i < (q1 - q0) * kS; i += blockDim.x) {
+      const int q = q0 + i / kS, k = i - (i / kS) * kS;
+      sm.ccols[i] = __ldcg(nb.cols + (size_t)cs[q] * kS + k);
+    }
+    for (int i = threadIdx.x; i < q1 - q0; i += blockDim.x) {
+      const int sl = cs[q0 + i];
+      sm.cmeta[i * 4] = __ldcg(nb.len + sl);
+      sm.cmeta[i * 4 + 1] = __ldcg(nb.rows + sl);
+      sm.cmeta[i * 4 + 2] = __ldcg(nb.rows + ga.P + sl);
+      sm.cmeta[i * 4 + 3] = __ldcg(nb.rows + 2 * ga.P + sl);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      bool stop = false;
+      const int m = process_chunk(ga, sm, *s_n, cf, ch, q0, q1, lane, &stop);
+      __syncwarp();
+      if (lane == 0) {
+        *s_n = m;
+        *s_stop = stop;
+      }
+    }
+    __syncthreads();
+    if (*s_stop) break;
+  }
   return *s_n;
 }
 
-__global__ void __launch_bounds__(kTopThreads, 1) k_toplist(GenArgs ga, Buf nb) {
+// Scoring, tabu bookkeeping and the top-list update of generation g (parity par).  Every block
+// scores a share of the slots and moves a share of generation g-1's duplicate table into the tabu
+// list (clearing it for generation g+1); the last block to finish then runs the single-block part.
+__global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, int par) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_n, s_cnt;
+  __shared__ int s_hits, s_live, s_lsum, s_last, s_n, s_cnt, s_stop;
   GenCtl *ctl = ga.ctl;
   if (ctl->stopped) return;
-  const bool init = ctl->gen < 0;
-  const int hits = ctl->hits_cur;
+  if (threadIdx.x == 0) {
+    s_hits = 0;
+    s_live = 0;
+    s_lsum = 0;
+  }
   __syncthreads();
-  if (!init && ga.tabu_limit > 0 && hits >= ga.tabu_limit) {  // step 6
+  const int n0 = ctl->n_top;
+  const bool had_threshold = n0 >= ga.K;
+  const uint64_t tf = had_threshold ? ga.top[ga.K - 1].f : 0ull;
+  const uint64_t th = had_threshold ? ga.top[ga.K - 1].h : 0ull;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  int hits = 0, live = 0, lsum = 0;
+  for (int s = tid; s < ga.P; s += stride) {
+    const bool att_dead = nb.att_dead[s] != 0;
+    const uint64_t h = nb.hash[s];
+    const bool dup = !att_dead && dedup_is_dup(ga.dkeys[par], ga.dslot[par], ga.dmask, h, s);
+    const bool dead = att_dead || dup;
+    nb.dead[s] = dead;
+    const int rp = ga.rows_scr[s], rn = ga.rows_scr[ga.P + s], ra = ga.rows_scr[2 * ga.P + s];
+    ga.rows_scr[s] = 0;
+    ga.rows_scr[ga.P + s] = 0;
+    ga.rows_scr[2 * ga.P + s] = 0;
+    nb.rows[s] = rp;
+    nb.rows[ga.P + s] = rn;
+    nb.rows[2 * ga.P + s] = ra;
+    const int L = nb.len[s];
+    const uint64_t f =
+        (dead || ra < ga.min_rows) ? 0ull : ((uint64_t)ra << (L < ga.col_cap ? L : ga.col_cap));
+    nb.fit[s] = f;
+    hits += nb.att_hits[s] + (dup ? 1 : 0);
+    live += !dead;
+    lsum += dead ? 0 : L;
+    if (!dead && f > 0ull && (!had_threshold || key_before(f, h, tf, th))) {
+      const int q = atomicAdd(&ctl->n_cand, 1);
+      ga.cand_f[q] = f;
+      ga.cand_h[q] = h;
+      ga.cand_s[q] = s;
+    }
+  }
+  // generation g-1's live keys join the tabu list; its duplicate table is cleared for g+1
+  uint64_t *pk = ga.dkeys[par ^ 1];
+  uint32_t *ps = ga.dslot[par ^ 1];
+  unsigned long long added = 0ull;
+  for (int i = tid; i <= (int)ga.dmask; i += stride) {
+    const uint64_t k = pk[i];
+    if (k) {
+      added += tabu_insert(ga.tabu, ga.tmask, k) ? 1ull : 0ull;
+      pk[i] = 0ull;
+      ps[i] = 0u;
+    }
+  }
+  hits = __reduce_add_sync(kFull, hits);
+  live = __reduce_add_sync(kFull, live);
+  lsum = __reduce_add_sync(kFull, lsum);
+  if ((threadIdx.x & 31) == 0) {
+    if (hits) atomicAdd(&s_hits, hits);
+    if (live) atomicAdd(&s_live, live);
+    if (lsum) atomicAdd(&s_lsum, lsum);
+  }
+  if (added) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->tabu_count), added);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_hits) atomicAdd(&ctl->hits_cur, s_hits);
+    if (s_live) atomicAdd(&ctl->live_cur, s_live);
+    if (s_lsum) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->len_cur), (unsigned long long)s_lsum);
+    __threadfence();
+    s_last = atomicAdd(&ctl->done, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+
+  // ---- last block: step 6, then the top rank list (step 7)
+  const bool init = ctl->gen < 0;
+  const int hits_g = __ldcg(&ctl->hits_cur);
+  const int live_g = __ldcg(&ctl->live_cur);
+  const int nc = __ldcg(&ctl->n_cand);
+  if (!init && ga.tabu_limit > 0 && hits_g >= ga.tabu_limit) {
     if (threadIdx.x == 0) {
-      ctl->hits_last = hits;
+      ctl->hits_last = hits_g;
       ctl->stopped = 1;
+      ctl->n_evaluated += live_g;          // the generation was evaluated, then discarded
+      ctl->sum_len += __ldcg(&ctl->len_cur);
     }
     return;
   }
@@ -554,14 +717,14 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_toplist(GenArgs ga, Buf nb) 
   const int cw = (ga.C + 31) / 32;
   sm.pool = reinterpret_cast<TopEntry *>(smem);
   sm.sf = reinterpret_cast<uint64_t *>(sm.pool + ga.K + 1);
-  sm.sh = sm.sf + kSortSmem;
-  sm.colbits = reinterpret_cast<uint32_t *>(sm.sh + kSortSmem);
+  sm.sh = sm.sf + ga.sort_cap;
+  sm.colbits = reinterpret_cast<uint32_t *>(sm.sh + ga.sort_cap);
   sm.ss = reinterpret_cast<int32_t *>(sm.colbits + cw);
-  sm.idx = sm.ss + kSortSmem;
+  sm.idx = sm.ss + ga.sort_cap;
   sm.idx2 = sm.idx + ga.K + 1;
-  sm.used = reinterpret_cast<uint8_t *>(sm.idx2 + ga.K + 1);
-
-  const int n0 = ctl->n_top;
+  sm.ccols = sm.idx2 + ga.K + 1;
+  sm.cmeta = sm.ccols + kChunk * kS;
+  sm.used = reinterpret_cast<uint8_t *>(sm.cmeta + kChunk * 4);
   for (int i = threadIdx.x; i < cw; i += blockDim.x) sm.colbits[i] = 0u;
   for (int e = threadIdx.x; e <= ga.K; e += blockDim.x) {
     sm.used[e] = e < n0;
@@ -570,19 +733,15 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_toplist(GenArgs ga, Buf nb) 
   for (int q = threadIdx.x; q < n0 * (int)(sizeof(TopEntry) / 4); q += blockDim.x)
     reinterpret_cast<int32_t *>(sm.pool)[q] = reinterpret_cast<const int32_t *>(ga.top)[q];
   __syncthreads();
-  const bool had_threshold = n0 >= ga.K;
-  const uint64_t tf = had_threshold ? sm.pool[ga.K - 1].f : 0ull;
-  const uint64_t th = had_threshold ? sm.pool[ga.K - 1].h : 0ull;
   int n = n0;
-  const int nc = ctl->n_cand;
-  if (nc > 0) n = sort_and_process(ga, nb, sm, n, nc, &s_n);
+  if (nc > 0) n = sort_and_process(ga, nb, sm, n, nc, &s_n, &s_stop);
   if (had_threshold && n < ga.K) {
     // Evictions left room: the candidates ranking after the old threshold come next.
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
     for (int s = threadIdx.x; s < ga.P; s += blockDim.x) {
-      const uint64_t f = nb.fit[s], h = nb.hash[s];
-      if (!nb.dead[s] && f > 0ull && !key_before(f, h, tf, th)) {
+      const uint64_t f = __ldcg(nb.fit + s), h = __ldcg(nb.hash + s);
+      if (!__ldcg(nb.dead + s) && f > 0ull && !key_before(f, h, tf, th)) {
         const int q = atomicAdd(&s_cnt, 1);
         ga.cand_f[q] = f;
         ga.cand_h[q] = h;
@@ -592,9 +751,8 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_toplist(GenArgs ga, Buf nb) 
     __syncthreads();
     const int cnt = s_cnt;
     __syncthreads();
-    if (cnt > 0) n = sort_and_process(ga, nb, sm, n, cnt, &s_n);
+    if (cnt > 0) n = sort_and_process(ga, nb, sm, n, cnt, &s_n, &s_stop);
   }
-  // write back in rank order
   const int words = (int)(sizeof(TopEntry) / 4);
   for (int q = threadIdx.x; q < n * words; q += blockDim.x) {
     const int e = q / words, w = q - e * words;
@@ -609,37 +767,16 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_toplist(GenArgs ga, Buf nb) 
     if (k < E.len) atomicAdd(&ga.usage[E.cols[k]], 1);
   }
   if (threadIdx.x == 0) {
-    ctl->hits_last = hits;
+    ctl->hits_last = hits_g;
     ctl->n_top = n;
     ctl->gen += 1;
-    ctl->n_evaluated += ctl->live_cur;
-  }
-}
-
-__global__ void __launch_bounds__(256) k_post(GenArgs ga, Buf cb, int32_t dcap) {
-  if (ga.ctl->stopped) return;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int stride = gridDim.x * blockDim.x;
-  for (int s = tid; s < ga.P; s += stride) {
-    int u = 0;
-    const int32_t *c = cb.cols + (size_t)s * kS;
-    const int L = cb.len[s];
-    for (int k = 0; k < L; ++k) u += ga.usage[c[k]];
-    cb.pen[s] = u;
-    if (!cb.dead[s] && tabu_insert(ga.tabu, ga.tmask, cb.hash[s]))
-      atomicAdd(reinterpret_cast<unsigned long long *>(&ga.ctl->tabu_count), 1ull);
-    ga.rows_scr[s] = 0;
-    ga.rows_scr[ga.P + s] = 0;
-    ga.rows_scr[2 * ga.P + s] = 0;
-  }
-  for (int i = tid; i < dcap; i += stride) {
-    ga.dkeys[i] = 0ull;
-    ga.dslot[i] = 0u;
-  }
-  if (tid == 0) {
-    ga.ctl->hits_cur = 0;
-    ga.ctl->live_cur = 0;
-    ga.ctl->n_cand = 0;
+    ctl->n_evaluated += live_g;
+    ctl->sum_len += __ldcg(&ctl->len_cur);
+    ctl->len_cur = 0;
+    ctl->hits_cur = 0;
+    ctl->live_cur = 0;
+    ctl->n_cand = 0;
+    ctl->done = 0;
     *ga.work = 0;
   }
 }
@@ -699,11 +836,17 @@ struct GenState {
   ebic_params p{};
   int P = 0, K = 0, C = 0, eval_mode = EBIC_MODE_DIRECT;
   bool initialised = false;
-  DevBuf cols[2], len[2], att_hits[2], rows[2], att_dead[2], dead[2], hash[2], fit[2], pen[2];
-  DevBuf rows_scr, work, tabu, dkeys, dslot, top, ctl, usage, cand_f, cand_h, cand_s, extract;
+  DevBuf cols[2], len[2], att_hits[2], rows[2], att_dead[2], dead[2], hash[2], fit[2];
+  DevBuf dkeys[2], dslot[2];
+  DevBuf rows_scr, work, tabu, top, ctl, usage, cand_f, cand_h, cand_s, extract;
   uint32_t tcap = 0, dcap = 0, ccap = 0;
+  int32_t sort_cap = 0;
+  int finish_blocks = 1;
   size_t top_smem = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphNode_t mark_node[2][4] = {};
+  bool marks_moved[2] = {false, false};
+  cudaEvent_t cap_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaStream_t cap_stream = nullptr;
 
   void drop_graphs() {
@@ -716,12 +859,14 @@ struct GenState {
   ~GenState() {
     drop_graphs();
     if (cap_stream) cudaStreamDestroy(cap_stream);
-    DevBuf *all[] = {&rows_scr, &work, &tabu, &dkeys, &dslot, &top, &ctl, &usage, &cand_f,
-                     &cand_h, &cand_s, &extract};
+    for (cudaEvent_t e : cap_ev)
+      if (e) cudaEventDestroy(e);
+    DevBuf *all[] = {&rows_scr, &work, &tabu, &dkeys[0], &dslot[0], &dkeys[1], &dslot[1], &top,
+                     &ctl, &usage, &cand_f, &cand_h, &cand_s, &extract};
     for (DevBuf *b : all) b->release();
     for (int k = 0; k < 2; ++k) {
       DevBuf *bs[] = {&cols[k], &len[k], &att_hits[k], &rows[k], &att_dead[k], &dead[k],
-                      &hash[k], &fit[k], &pen[k]};
+                      &hash[k], &fit[k]};
       for (DevBuf *b : bs) b->release();
     }
   }
@@ -735,7 +880,6 @@ struct GenState {
     b.dead = dead[k].as<uint8_t>();
     b.hash = hash[k].as<uint64_t>();
     b.fit = fit[k].as<uint64_t>();
-    b.pen = pen[k].as<int32_t>();
     return b;
   }
 };
@@ -758,8 +902,10 @@ GenArgs gen_args(ebic_ctx *ctx, GenState *g) {
   ga.usage = g->usage.as<int32_t>();
   ga.tabu = g->tabu.as<uint64_t>();
   ga.tmask = g->tcap - 1;
-  ga.dkeys = g->dkeys.as<uint64_t>();
-  ga.dslot = g->dslot.as<uint32_t>();
+  for (int k = 0; k < 2; ++k) {
+    ga.dkeys[k] = g->dkeys[k].as<uint64_t>();
+    ga.dslot[k] = g->dslot[k].as<uint32_t>();
+  }
   ga.dmask = g->dcap - 1;
   ga.rows_scr = g->rows_scr.as<int32_t>();
   ga.work = g->work.as<int32_t>();
@@ -767,6 +913,7 @@ GenArgs gen_args(ebic_ctx *ctx, GenState *g) {
   ga.cand_h = g->cand_h.as<uint64_t>();
   ga.cand_s = g->cand_s.as<int32_t>();
   ga.cand_cap = (int32_t)g->ccap;
+  ga.sort_cap = g->sort_cap;
   const ebic_params &p = g->p;
   ga.seed = p.seed;
   ga.P = p.pop_size;
@@ -816,36 +963,76 @@ PopView gen_view(GenState *g, int k) {
   v.n = g->P;
   v.stop = &g->ctl.as<GenCtl>()->stopped;
   v.hash = g->hash[k].as<uint64_t>();
-  v.dkeys = g->dkeys.as<uint64_t>();
-  v.dslot = g->dslot.as<uint32_t>();
+  v.dkeys = g->dkeys[k].as<uint64_t>();
+  v.dslot = g->dslot[k].as<uint32_t>();
   v.dmask = g->dcap - 1;
   return v;
 }
 
+// Event marks between the kernels of one generation: 0 before k_evolve, 1 before the evaluation,
+// 2 before k_finish, 3 after it.  While a graph is captured they become event-record nodes whose
+// events are swapped before each profiled replay.
+struct Marks {
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaGraphNode_t node[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool capture = false;
+};
+
+cudaError_t mark(cudaStream_t s, Marks *m, int i) {
+  if (!m || !m->ev[i]) return cudaSuccess;
+  if (!m->capture) return cudaEventRecord(m->ev[i], s);
+  cudaError_t e = cudaEventRecordWithFlags(m->ev[i], s, cudaEventRecordExternal);
+  if (e != cudaSuccess) return e;
+  cudaStreamCaptureStatus st;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  e = cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &nd);
+  if (e == cudaSuccess && nd == 1) m->node[i] = deps[0];
+  return e;
+}
+
 // Scoring kernels shared by initialisation and every generation (buffer k was just built).
-cudaError_t launch_scoring(ebic_ctx *ctx, GenState *g, int k, cudaStream_t s) {
-  const GenArgs ga = gen_args(ctx, g);
-  const Buf nb = g->buf(k);
+cudaError_t launch_scoring(ebic_ctx *ctx, GenState *g, int k, cudaStream_t s, Marks *m) {
   cudaError_t e;
+  if ((e = mark(s, m, 1)) != cudaSuccess) return e;
   if ((e = launch_eval_kernel(g->eval_mode, gen_eval_args(ctx, g), gen_view(g, k), ctx->num_sms,
                               s)) != cudaSuccess)
     return e;
-  const unsigned sblocks = (unsigned)((g->P + 255) / 256);
-  k_score<<<sblocks, 256, 0, s>>>(ga, nb);
-  k_toplist<<<1, kTopThreads, g->top_smem, s>>>(ga, nb);
-  int pblocks = (int)((std::max<int64_t>(g->P, g->dcap) + 255) / 256);
-  if (pblocks > ctx->num_sms * 8) pblocks = ctx->num_sms * 8;
-  k_post<<<pblocks, 256, 0, s>>>(ga, nb, (int32_t)g->dcap);
-  return cudaGetLastError();
+  if ((e = mark(s, m, 2)) != cudaSuccess) return e;
+  k_finish<<<g->finish_blocks, kTopThreads, g->top_smem, s>>>(gen_args(ctx, g), g->buf(k), k);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return mark(s, m, 3);
 }
 
-cudaError_t launch_generation(ebic_ctx *ctx, GenState *g, int parity, cudaStream_t s) {
-  const GenArgs ga = gen_args(ctx, g);
-  k_evolve<<<(g->P + kSlotThreads - 1) / kSlotThreads, kSlotThreads, 0, s>>>(
-      ga, g->buf(parity ^ 1), g->buf(parity));
-  cudaError_t e = cudaGetLastError();
+cudaError_t launch_generation(ebic_ctx *ctx, GenState *g, int parity, cudaStream_t s, Marks *m) {
+  int G = 1;
+  while (G < g->p.max_attempts) G <<= 1;
+  const int64_t threads = (int64_t)g->P * G;
+  cudaError_t e = mark(s, m, 0);
   if (e != cudaSuccess) return e;
-  return launch_scoring(ctx, g, parity, s);
+  k_evolve<<<(unsigned)((threads + kEvolveThreads - 1) / kEvolveThreads), kEvolveThreads, 0, s>>>(
+      gen_args(ctx, g), g->buf(parity ^ 1), g->buf(parity), G, parity);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return launch_scoring(ctx, g, parity, s, m);
+}
+
+// Queues the event pairs of one profiled generation (evolve, evaluation, finish).
+void push_generation_timing(ebic_ctx *ctx, const Marks &m, bool with_evolve) {
+  if (with_evolve) prof_push(ctx, m.ev[0], m.ev[1], EBIC_KERNEL_EVOLVE, 0, 0, 0, true, false);
+  prof_push(ctx, m.ev[1], m.ev[2], EBIC_KERNEL_EVAL, 0, 0, 0, true, false);
+  prof_push(ctx, m.ev[2], m.ev[3], EBIC_KERNEL_FINISH, 0, 0, 0, true, true);
+}
+
+bool take_marks(ebic_ctx *ctx, Marks *m, bool with_evolve) {
+  for (int i = with_evolve ? 0 : 1; i < 4; ++i) {
+    m->ev[i] = prof_event(ctx);
+    if (!m->ev[i]) {
+      for (int j = 0; j < i; ++j)
+        if (m->ev[j]) ctx->ev_pool.push_back(m->ev[j]);
+      return false;
+    }
+  }
+  return true;
 }
 
 int check_run_params(ebic_ctx *ctx, const ebic_params *p) {
@@ -892,16 +1079,19 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
     GEN_ALLOC(g->dead[k], P);
     GEN_ALLOC(g->hash[k], P * 8);
     GEN_ALLOC(g->fit[k], P * 8);
-    GEN_ALLOC(g->pen[k], P * 4);
     EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->cols[k].p, 0, P * kS * 4, ctx->stream));
-    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->pen[k].p, 0, P * 4, ctx->stream));
+    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->len[k].p, 0, P * 4, ctx->stream));
     EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->fit[k].p, 0, P * 8, ctx->stream));
   }
   GEN_ALLOC(g->rows_scr, P * 3 * 4);
   GEN_ALLOC(g->work, 64);
   g->dcap = next_pow2(2 * P);
-  GEN_ALLOC(g->dkeys, (size_t)g->dcap * 8);
-  GEN_ALLOC(g->dslot, (size_t)g->dcap * 4);
+  for (int k = 0; k < 2; ++k) {
+    GEN_ALLOC(g->dkeys[k], (size_t)g->dcap * 8);
+    GEN_ALLOC(g->dslot[k], (size_t)g->dcap * 4);
+    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->dkeys[k].p, 0, (size_t)g->dcap * 8, ctx->stream));
+    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->dslot[k].p, 0, (size_t)g->dcap * 4, ctx->stream));
+  }
   g->ccap = next_pow2(P);
   GEN_ALLOC(g->cand_f, (size_t)g->ccap * 8);
   GEN_ALLOC(g->cand_h, (size_t)g->ccap * 8);
@@ -911,8 +1101,6 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
   GEN_ALLOC(g->usage, (size_t)ctx->C * 4);
   EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->rows_scr.p, 0, P * 3 * 4, ctx->stream));
   EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->work.p, 0, 64, ctx->stream));
-  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->dkeys.p, 0, (size_t)g->dcap * 8, ctx->stream));
-  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->dslot.p, 0, (size_t)g->dcap * 4, ctx->stream));
   EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->usage.p, 0, (size_t)ctx->C * 4, ctx->stream));
   EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->top.p, 0, (size_t)g->K * sizeof(TopEntry), ctx->stream));
   GenCtl c0{};
@@ -920,12 +1108,18 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
   EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(g->ctl.p, &c0, sizeof(c0), cudaMemcpyHostToDevice,
                                        ctx->stream));
   const int cw = (ctx->C + 31) / 32;
-  g->top_smem = (size_t)(g->K + 1) * sizeof(TopEntry) + (size_t)kSortSmem * 16 +
-                (size_t)cw * 4 + (size_t)kSortSmem * 4 + (size_t)(g->K + 1) * 8 +
-                (size_t)(g->K + 1) + 16;
-  EBIC_CHECK_CUDA(ctx, cudaFuncSetAttribute(k_toplist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  g->sort_cap = (int32_t)std::min<uint32_t>(kSortSmemMax, next_pow2(P));
+  g->top_smem = (size_t)(g->K + 1) * sizeof(TopEntry) + (size_t)g->sort_cap * 16 +
+                (size_t)cw * 4 + (size_t)g->sort_cap * 4 + (size_t)(g->K + 1) * 8 +
+                (size_t)kChunk * (kS + 4) * 4 + (size_t)(g->K + 1) + 16;
+  EBIC_CHECK_CUDA(ctx, cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)g->top_smem));
+  // enough blocks to spread the slot and table loops, few enough to be co-resident quickly
+  const int64_t work = std::max<int64_t>(g->P, g->dcap);
+  g->finish_blocks = (int)std::max<int64_t>(
+      1, std::min<int64_t>((work + 4 * kTopThreads - 1) / (4 * kTopThreads), ctx->num_sms));
   EBIC_CHECK_CUDA(ctx, cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+  for (cudaEvent_t &e : g->cap_ev) EBIC_CHECK_CUDA(ctx, cudaEventCreate(&e));
   EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return EBIC_OK;
 }
@@ -974,7 +1168,12 @@ int ensure_eval_ready(ebic_ctx *ctx, GenState *g, const ebic_params *p, int n_ge
 int capture_graph(ebic_ctx *ctx, GenState *g, int parity) {
   cudaGraph_t graph = nullptr;
   EBIC_CHECK_CUDA(ctx, cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = launch_generation(ctx, g, parity, g->cap_stream);
+  Marks m;
+  m.capture = true;
+  for (int i = 0; i < 4; ++i) m.ev[i] = g->cap_ev[i];
+  cudaError_t e = launch_generation(ctx, g, parity, g->cap_stream, &m);
+  for (int i = 0; i < 4; ++i) g->mark_node[parity][i] = m.node[i];
+  g->marks_moved[parity] = false;
   cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
   if (e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -987,7 +1186,7 @@ int capture_graph(ebic_ctx *ctx, GenState *g, int parity) {
   return EBIC_OK;
 }
 
-constexpr int kKernelsPerGeneration = 5;
+constexpr int kKernelsPerGeneration = 3;
 
 }  // namespace
 
@@ -1018,15 +1217,20 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
   EBIC_TRY(ensure_eval_ready(ctx, g, p, n_gen));
   GenCtl c{};
   EBIC_TRY(read_ctl(ctx, g, &c));
-  EBIC_TRY(ensure_tabu(ctx, g, c.tabu_count + (int64_t)g->P * ((int64_t)n_gen + 1)));
+  EBIC_TRY(ensure_tabu(ctx, g, c.tabu_count + (int64_t)g->P * ((int64_t)n_gen + 2)));
   cudaStream_t s = ctx->stream;
   const unsigned iblocks = (unsigned)((g->P + kSlotThreads - 1) / kSlotThreads);
+  const GenCtl c_start = c;
   if (!g->initialised) {
+    Marks m;
+    const bool timed = ctx->prof && take_marks(ctx, &m, false);
     k_init<<<iblocks, kSlotThreads, 0, s>>>(gen_args(ctx, g), g->buf(0));
     EBIC_CHECK_CUDA(ctx, cudaGetLastError());
-    EBIC_CHECK_CUDA(ctx, launch_scoring(ctx, g, 0, s));
+    EBIC_CHECK_CUDA(ctx, launch_scoring(ctx, g, 0, s, timed ? &m : nullptr));
+    if (timed) push_generation_timing(ctx, m, false);
     prof_count(ctx, EBIC_KERNEL_EVAL, 1);
-    prof_count(ctx, -1, kKernelsPerGeneration - 1);
+    prof_count(ctx, EBIC_KERNEL_FINISH, 1);
+    prof_count(ctx, -1, 1);
     g->initialised = true;
     EBIC_TRY(read_ctl(ctx, g, &c));
   }
@@ -1034,14 +1238,26 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
     for (int i = 0; i < n_gen; ++i) {
       const int gnext = c.gen + 1 + i;
       const int parity = gnext & 1;
+      Marks m;
+      const bool timed = ctx->prof && take_marks(ctx, &m, true);
       if (p->use_graph) {
         if (!g->graph[parity]) EBIC_TRY(capture_graph(ctx, g, parity));
+        if (timed || g->marks_moved[parity]) {
+          // point the graph's event nodes at this replay's events (or back at the placeholders)
+          for (int k = 0; k < 4; ++k)
+            EBIC_CHECK_CUDA(ctx, cudaGraphExecEventRecordNodeSetEvent(
+                                     g->graph[parity], g->mark_node[parity][k],
+                                     timed ? m.ev[k] : g->cap_ev[k]));
+          g->marks_moved[parity] = timed;
+        }
         EBIC_CHECK_CUDA(ctx, cudaGraphLaunch(g->graph[parity], s));
       } else {
-        EBIC_CHECK_CUDA(ctx, launch_generation(ctx, g, parity, s));
+        EBIC_CHECK_CUDA(ctx, launch_generation(ctx, g, parity, s, timed ? &m : nullptr));
       }
+      if (timed) push_generation_timing(ctx, m, true);
+      prof_count(ctx, EBIC_KERNEL_EVOLVE, 1);
       prof_count(ctx, EBIC_KERNEL_EVAL, 1);
-      prof_count(ctx, -1, kKernelsPerGeneration - 1);
+      prof_count(ctx, EBIC_KERNEL_FINISH, 1);
       if (!p->use_graph) {
         GenCtl cc{};
         EBIC_TRY(read_ctl(ctx, g, &cc));
@@ -1050,7 +1266,19 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
     }
   }
   EBIC_TRY(read_ctl(ctx, g, &c));
-  if (c.err) return ebic_fail(ctx, EBIC_ECUDA, "device error in the generation loop");
+  if (ctx->prof) {
+    // algorithmic work of the evaluations run by this call (live slots only)
+    const double dlen = (double)(c.sum_len - c_start.sum_len);
+    const double dlive = (double)(c.n_evaluated - c_start.n_evaluated);
+    const double nd = g->p.neg_trends ? 2.0 : 1.0;
+    KStats &k = ctx->kst[EBIC_KERNEL_EVAL];
+    k.bytes += g->eval_mode == EBIC_MODE_BITMAP ? (dlen - dlive) * (double)ctx->Wst * 4.0 * nd
+                                                : dlen * (double)ctx->R_pad * 4.0;
+    k.ops += (dlen - dlive) * (double)ctx->R * nd;
+    k.units += dlive * (double)ctx->R;
+    prof_collect(ctx);
+  }
+  EBIC_TRY(read_ctl(ctx, g, &c));
   if (rep) {
     memset(rep, 0, sizeof(*rep));
     rep->gens_done = c.gen;
@@ -1149,8 +1377,9 @@ int ebic_extract_biclusters(ebic_ctx *ctx, int32_t capacity, uint32_t *rowmask, 
   return EBIC_OK;
 }
 
-// Checkpoint blob: header, GenCtl, current buffer (cols, len, dead, hash, fit, pen, rows,
-// att_dead), top list, tabu keys.
+// Checkpoint blob: header, GenCtl, current buffer (cols, len, dead, hash, fit, rows, att_dead),
+// top list, then the tabu list as sorted keys (the hashed table plus the last scored
+// generation's keys, which still sit in its duplicate table).
 struct StateHeader {
   uint64_t magic;
   int64_t rows;
@@ -1159,19 +1388,38 @@ struct StateHeader {
   ebic_params p;
 };
 
-static const uint64_t kMagic = 0x4542494347423330ull;  // "EBICGB30"
+static const uint64_t kMagic = 0x4542494347423331ull;  // "EBICGB31"
 
-static int64_t state_size(const GenState *g, int64_t n_tabu) {
+static int64_t state_fixed_size(const GenState *g) {
   const int64_t P = g->P;
   return (int64_t)sizeof(StateHeader) + (int64_t)sizeof(GenCtl) + P * kS * 4 + P * 4 + P + P * 8 +
-         P * 8 + P * 4 + P * 12 + P + (int64_t)g->K * (int64_t)sizeof(TopEntry) + n_tabu * 8;
+         P * 8 + P * 12 + P + (int64_t)g->K * (int64_t)sizeof(TopEntry);
+}
+
+static int collect_tabu(ebic_ctx *ctx, GenState *g, int k, std::vector<uint64_t> *keys) {
+  std::vector<uint64_t> table(g->tcap), pend(g->dcap);
+  EBIC_CHECK_CUDA(ctx, cudaMemcpy(table.data(), g->tabu.p, (size_t)g->tcap * 8,
+                                  cudaMemcpyDeviceToHost));
+  EBIC_CHECK_CUDA(ctx, cudaMemcpy(pend.data(), g->dkeys[k].p, (size_t)g->dcap * 8,
+                                  cudaMemcpyDeviceToHost));
+  keys->clear();
+  for (uint64_t v : table)
+    if (v) keys->push_back(v);
+  for (uint64_t v : pend)
+    if (v) keys->push_back(v);
+  std::sort(keys->begin(), keys->end());
+  keys->erase(std::unique(keys->begin(), keys->end()), keys->end());
+  return EBIC_OK;
 }
 
 int64_t ebic_state_bytes(ebic_ctx *ctx) {
   if (!ctx || !ctx->gen || !ctx->gen->initialised) return 0;
+  cudaSetDevice(ctx->device);
   GenCtl c{};
   if (read_ctl(ctx, ctx->gen, &c) != EBIC_OK) return 0;
-  return state_size(ctx->gen, c.tabu_count);
+  std::vector<uint64_t> keys;
+  if (collect_tabu(ctx, ctx->gen, c.gen & 1, &keys) != EBIC_OK) return 0;
+  return state_fixed_size(ctx->gen) + (int64_t)keys.size() * 8;
 }
 
 int ebic_save_state(ebic_ctx *ctx, void *blob, int64_t size) {
@@ -1181,14 +1429,10 @@ int ebic_save_state(ebic_ctx *ctx, void *blob, int64_t size) {
   cudaSetDevice(ctx->device);
   GenCtl c{};
   EBIC_TRY(read_ctl(ctx, g, &c));
-  std::vector<uint64_t> table(g->tcap);
-  EBIC_CHECK_CUDA(ctx, cudaMemcpy(table.data(), g->tabu.p, (size_t)g->tcap * 8,
-                                  cudaMemcpyDeviceToHost));
+  const int k = c.gen & 1;
   std::vector<uint64_t> keys;
-  for (uint64_t k : table)
-    if (k) keys.push_back(k);
-  std::sort(keys.begin(), keys.end());
-  const int64_t need = state_size(g, (int64_t)keys.size());
+  EBIC_TRY(collect_tabu(ctx, g, k, &keys));
+  const int64_t need = state_fixed_size(g) + (int64_t)keys.size() * 8;
   if (!blob || size < need) return ebic_fail(ctx, EBIC_EINVAL, "blob too small");
   unsigned char *o = static_cast<unsigned char *>(blob);
   StateHeader h{};
@@ -1197,21 +1441,20 @@ int ebic_save_state(ebic_ctx *ctx, void *blob, int64_t size) {
   h.cols = ctx->C;
   h.P = g->P;
   h.K = g->K;
-  h.k = c.gen & 1;
+  h.k = k;
   h.n_tabu = (int64_t)keys.size();
   h.p = g->p;
   memcpy(o, &h, sizeof(h));
   o += sizeof(h);
   memcpy(o, &c, sizeof(c));
   o += sizeof(c);
-  const int k = h.k;
   const size_t P = (size_t)g->P;
   struct Part {
     DevBuf *b;
     size_t n;
   } parts[] = {{&g->cols[k], P * kS * 4}, {&g->len[k], P * 4},  {&g->dead[k], P},
-               {&g->hash[k], P * 8},      {&g->fit[k], P * 8},  {&g->pen[k], P * 4},
-               {&g->rows[k], P * 12},     {&g->att_dead[k], P}, {&g->top, (size_t)g->K * sizeof(TopEntry)}};
+               {&g->hash[k], P * 8},      {&g->fit[k], P * 8},  {&g->rows[k], P * 12},
+               {&g->att_dead[k], P},      {&g->top, (size_t)g->K * sizeof(TopEntry)}};
   for (const Part &pt : parts) {
     EBIC_CHECK_CUDA(ctx, cudaMemcpy(o, pt.b->p, pt.n, cudaMemcpyDeviceToHost));
     o += pt.n;
@@ -1234,7 +1477,8 @@ int ebic_load_state(ebic_ctx *ctx, const ebic_params *p, const void *blob, int64
   cudaSetDevice(ctx->device);
   EBIC_TRY(gen_create(ctx, p));
   GenState *g = ctx->gen;
-  if (size < state_size(g, h.n_tabu)) return ebic_fail(ctx, EBIC_EINVAL, "blob truncated");
+  if (size < state_fixed_size(g) + h.n_tabu * 8)
+    return ebic_fail(ctx, EBIC_EINVAL, "blob truncated");
   const unsigned char *o = static_cast<const unsigned char *>(blob) + sizeof(h);
   GenCtl c;
   memcpy(&c, o, sizeof(c));
@@ -1245,8 +1489,8 @@ int ebic_load_state(ebic_ctx *ctx, const ebic_params *p, const void *blob, int64
     DevBuf *b;
     size_t n;
   } parts[] = {{&g->cols[k], P * kS * 4}, {&g->len[k], P * 4},  {&g->dead[k], P},
-               {&g->hash[k], P * 8},      {&g->fit[k], P * 8},  {&g->pen[k], P * 4},
-               {&g->rows[k], P * 12},     {&g->att_dead[k], P}, {&g->top, (size_t)g->K * sizeof(TopEntry)}};
+               {&g->hash[k], P * 8},      {&g->fit[k], P * 8},  {&g->rows[k], P * 12},
+               {&g->att_dead[k], P},      {&g->top, (size_t)g->K * sizeof(TopEntry)}};
   for (const Part &pt : parts) {
     EBIC_CHECK_CUDA(ctx, cudaMemcpy(pt.b->p, o, pt.n, cudaMemcpyHostToDevice));
     o += pt.n;
@@ -1266,11 +1510,12 @@ int ebic_load_state(ebic_ctx *ctx, const ebic_params *p, const void *blob, int64
   c.hits_cur = 0;
   c.live_cur = 0;
   c.n_cand = 0;
+  c.done = 0;
   EBIC_CHECK_CUDA(ctx, cudaMemcpy(g->ctl.p, &c, sizeof(c), cudaMemcpyHostToDevice));
   // column usage of the restored top list
   std::vector<TopEntry> top(g->K);
   memcpy(top.data(), static_cast<const unsigned char *>(blob) + sizeof(h) + sizeof(GenCtl) +
-                         P * kS * 4 + P * 4 + P + P * 8 + P * 8 + P * 4 + P * 12 + P,
+                         P * kS * 4 + P * 4 + P + P * 8 + P * 8 + P * 12 + P,
          sizeof(TopEntry) * g->K);
   std::vector<int32_t> usage(ctx->C, 0);
   for (int e = 0; e < c.n_top; ++e)

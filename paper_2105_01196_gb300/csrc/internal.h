@@ -90,6 +90,7 @@ struct PendingTiming {
   cudaEvent_t a, b;
   int kernel;
   double bytes, ops, units;
+  bool own_a, own_b;  // the pair returns these events to the pool (shared ends are owned once)
 };
 
 struct ebic_ctx {
@@ -114,7 +115,7 @@ struct ebic_ctx {
 
   // profiling
   bool prof = false;
-  KStats kst[3];
+  KStats kst[EBIC_KERNEL_COUNT];
   std::vector<PendingTiming> pending;
   std::vector<cudaEvent_t> ev_pool;
 };
@@ -122,7 +123,7 @@ struct ebic_ctx {
 // An event from the context's pool (nullptr when not profiling), and queuing a recorded pair.
 cudaEvent_t prof_event(ebic_ctx *ctx);
 void prof_push(ebic_ctx *ctx, cudaEvent_t a, cudaEvent_t b, int kernel, double bytes, double ops,
-               double units);
+               double units, bool own_a = true, bool own_b = true);
 // Records an event on the context stream before a timed launch (nullptr when not profiling).
 cudaEvent_t prof_begin(ebic_ctx *ctx);
 // Records the closing event and queues the pair with its algorithmic work.

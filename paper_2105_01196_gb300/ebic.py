@@ -282,7 +282,7 @@ def ebic_load_state(ctx, params, blob):
     _check(ctx, _lib.ebic_load_state(ctx, ctypes.byref(params), ptr(blob), int(blob.size)))
 
 
-KERNEL_EVAL, KERNEL_BITMAP_BUILD, KERNEL_ALL = 0, 1, 2
+KERNEL_EVAL, KERNEL_BITMAP_BUILD, KERNEL_ALL, KERNEL_EVOLVE, KERNEL_FINISH = 0, 1, 2, 3, 4
 
 
 class KernelStats(ctypes.Structure):
