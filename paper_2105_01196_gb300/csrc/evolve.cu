@@ -843,17 +843,22 @@ struct GenState {
   int32_t sort_cap = 0;
   int finish_blocks = 1;
   size_t top_smem = 0;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // [parity][0]: the plain generation graph; [parity][1]: the same with event-record nodes
+  // between the kernels, used while kernel statistics are on (its source graph is kept alive,
+  // because the event nodes are re-pointed at fresh events before each replay)
+  cudaGraphExec_t graph[2][2] = {};
+  cudaGraph_t graph_src[2][2] = {};
   cudaGraphNode_t mark_node[2][4] = {};
-  bool marks_moved[2] = {false, false};
   cudaEvent_t cap_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaStream_t cap_stream = nullptr;
 
   void drop_graphs() {
-    for (auto &g : graph)
-      if (g) {
-        cudaGraphExecDestroy(g);
-        g = nullptr;
+    for (int k = 0; k < 2; ++k)
+      for (int v = 0; v < 2; ++v) {
+        if (graph[k][v]) cudaGraphExecDestroy(graph[k][v]);
+        if (graph_src[k][v]) cudaGraphDestroy(graph_src[k][v]);
+        graph[k][v] = nullptr;
+        graph_src[k][v] = nullptr;
       }
   }
   ~GenState() {
@@ -981,14 +986,28 @@ struct Marks {
 cudaError_t mark(cudaStream_t s, Marks *m, int i) {
   if (!m || !m->ev[i]) return cudaSuccess;
   if (!m->capture) return cudaEventRecord(m->ev[i], s);
-  cudaError_t e = cudaEventRecordWithFlags(m->ev[i], s, cudaEventRecordExternal);
+  return cudaEventRecordWithFlags(m->ev[i], s, cudaEventRecordExternal);
+}
+
+// The event-record nodes of a captured generation, matched to marks by the event they record.
+cudaError_t find_mark_nodes(cudaGraph_t graph, const cudaEvent_t ev[4], cudaGraphNode_t node[4]) {
+  size_t n = 0;
+  cudaError_t e = cudaGraphGetNodes(graph, nullptr, &n);
   if (e != cudaSuccess) return e;
-  cudaStreamCaptureStatus st;
-  const cudaGraphNode_t *deps = nullptr;
-  size_t nd = 0;
-  e = cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &nd);
-  if (e == cudaSuccess && nd == 1) m->node[i] = deps[0];
-  return e;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if ((e = cudaGraphGetNodes(graph, nodes.data(), &n)) != cudaSuccess) return e;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    if ((e = cudaGraphNodeGetType(nd, &t)) != cudaSuccess) return e;
+    if (t != cudaGraphNodeTypeEventRecord) continue;
+    cudaEvent_t ev_n = nullptr;
+    if ((e = cudaGraphEventRecordNodeGetEvent(nd, &ev_n)) != cudaSuccess) return e;
+    for (int i = 0; i < 4; ++i)
+      if (ev[i] == ev_n) node[i] = nd;
+  }
+  for (int i = 0; i < 4; ++i)
+    if (!node[i]) return cudaErrorInvalidValue;
+  return cudaSuccess;
 }
 
 // Scoring kernels shared by initialisation and every generation (buffer k was just built).
@@ -1165,24 +1184,37 @@ int ensure_eval_ready(ebic_ctx *ctx, GenState *g, const ebic_params *p, int n_ge
   return EBIC_OK;
 }
 
-int capture_graph(ebic_ctx *ctx, GenState *g, int parity) {
+int capture_graph(ebic_ctx *ctx, GenState *g, int parity, int profiled) {
   cudaGraph_t graph = nullptr;
   EBIC_CHECK_CUDA(ctx, cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
   Marks m;
   m.capture = true;
-  for (int i = 0; i < 4; ++i) m.ev[i] = g->cap_ev[i];
-  cudaError_t e = launch_generation(ctx, g, parity, g->cap_stream, &m);
-  for (int i = 0; i < 4; ++i) g->mark_node[parity][i] = m.node[i];
-  g->marks_moved[parity] = false;
+  if (profiled)
+    for (int i = 0; i < 4; ++i) m.ev[i] = g->cap_ev[i];
+  cudaError_t e = launch_generation(ctx, g, parity, g->cap_stream, profiled ? &m : nullptr);
   cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
   if (e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
     return ebic_fail_cuda(ctx, e, "generation capture", __FILE__, __LINE__);
   }
   EBIC_CHECK_CUDA(ctx, e2);
-  e = cudaGraphInstantiate(&g->graph[parity], graph, 0);
-  cudaGraphDestroy(graph);
-  EBIC_CHECK_CUDA(ctx, e);
+  if (profiled) {
+    for (int i = 0; i < 4; ++i) g->mark_node[parity][i] = nullptr;
+    e = find_mark_nodes(graph, g->cap_ev, g->mark_node[parity]);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return ebic_fail_cuda(ctx, e, "event nodes of the generation graph", __FILE__, __LINE__);
+    }
+  }
+  e = cudaGraphInstantiate(&g->graph[parity][profiled], graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return ebic_fail_cuda(ctx, e, "cudaGraphInstantiate", __FILE__, __LINE__);
+  }
+  if (profiled)
+    g->graph_src[parity][profiled] = graph;
+  else
+    cudaGraphDestroy(graph);
   return EBIC_OK;
 }
 
@@ -1241,16 +1273,15 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
       Marks m;
       const bool timed = ctx->prof && take_marks(ctx, &m, true);
       if (p->use_graph) {
-        if (!g->graph[parity]) EBIC_TRY(capture_graph(ctx, g, parity));
-        if (timed || g->marks_moved[parity]) {
-          // point the graph's event nodes at this replay's events (or back at the placeholders)
+        const int v = timed ? 1 : 0;
+        if (!g->graph[parity][v]) EBIC_TRY(capture_graph(ctx, g, parity, v));
+        if (timed) {
+          // point the graph's event nodes at this replay's events
           for (int k = 0; k < 4; ++k)
             EBIC_CHECK_CUDA(ctx, cudaGraphExecEventRecordNodeSetEvent(
-                                     g->graph[parity], g->mark_node[parity][k],
-                                     timed ? m.ev[k] : g->cap_ev[k]));
-          g->marks_moved[parity] = timed;
+                                     g->graph[parity][1], g->mark_node[parity][k], m.ev[k]));
         }
-        EBIC_CHECK_CUDA(ctx, cudaGraphLaunch(g->graph[parity], s));
+        EBIC_CHECK_CUDA(ctx, cudaGraphLaunch(g->graph[parity][v], s));
       } else {
         EBIC_CHECK_CUDA(ctx, launch_generation(ctx, g, parity, s, timed ? &m : nullptr));
       }
