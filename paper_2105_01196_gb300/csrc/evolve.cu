@@ -160,54 +160,6 @@ __device__ __forceinline__ int cmp_penalised(uint64_t fa, int ua, uint64_t fb, i
   return ub >= ua ? cmp_shifted(fa, ub - ua, fb) : -cmp_shifted(fb, ua - ub, fa);
 }
 
-// T uniform candidates of the previous population; the best penalised score f * 2^-U wins,
-// ties to the lower slot.  U = sum over the candidate's columns of their top-list usage, computed
-// here from the usage table.  Candidates are drawn four at a time and their loads issued together.
-__device__ int tournament(WordStream &st, const GenArgs &ga, const Buf &pb) {
-  int best = -1, ub = 0;
-  uint64_t fb = 0ull;
-  for (int t0 = 0; t0 < ga.T; t0 += 4) {
-    int idx[4], Lc[4], u[4];
-    uint64_t f[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) idx[j] = (t0 + j < ga.T) ? (int)st.below((uint32_t)ga.P) : -1;
-    int maxL = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      f[j] = idx[j] >= 0 ? pb.fit[idx[j]] : 0ull;
-      Lc[j] = idx[j] >= 0 ? pb.len[idx[j]] : 0;
-      u[j] = 0;
-      maxL = max(maxL, Lc[j]);
-    }
-    for (int k = 0; k < maxL; k += 4) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (k >= Lc[j]) continue;
-        const int4 v = reinterpret_cast<const int4 *>(pb.cols + (size_t)idx[j] * kS)[k >> 2];
-        const int u0 = ga.usage[v.x], u1 = ga.usage[v.y], u2 = ga.usage[v.z], u3 = ga.usage[v.w];
-        u[j] += u0 + (k + 1 < Lc[j] ? u1 : 0) + (k + 2 < Lc[j] ? u2 : 0) + (k + 3 < Lc[j] ? u3 : 0);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (idx[j] < 0) continue;
-      if (best < 0) {
-        best = idx[j];
-        fb = f[j];
-        ub = u[j];
-        continue;
-      }
-      const int c = cmp_penalised(f[j], u[j], fb, ub);
-      if (c > 0 || (c == 0 && idx[j] < best)) {
-        best = idx[j];
-        fb = f[j];
-        ub = u[j];
-      }
-    }
-  }
-  return best;
-}
-
 // ------------------------------------------------------------------ variation
 
 __device__ __forceinline__ bool contains(const int32_t *c, int L, int v) {
@@ -223,78 +175,6 @@ __device__ int draw_free(WordStream &st, int C, const int32_t *c, int L) {
     if (!contains(c, L, v)) return v;
   }
   return -1;
-}
-
-__device__ void swap_op(WordStream &st, int32_t *c, int L) {
-  if (L < 2) return;  // never reached: every live chromosome has at least two columns
-  const int p = (int)st.below((uint32_t)L);
-  int q = (int)st.below((uint32_t)(L - 1));
-  if (q >= p) ++q;
-  const int t = c[p];
-  c[p] = c[q];
-  c[q] = t;
-}
-
-__device__ void mutate(WordStream &st, int32_t *c, int &L, int C, int max_len) {
-  for (int tries = 0; tries < 8; ++tries) {
-    const uint32_t op = st.next() >> 30;
-    if (op == 0u) {  // insertion
-      if (L >= max_len || L >= C) continue;
-      const int pos = (int)st.below((uint32_t)(L + 1));
-      const int v = draw_free(st, C, c, L);
-      if (v < 0) continue;
-      for (int k = L; k > pos; --k) c[k] = c[k - 1];
-      c[pos] = v;
-      ++L;
-      return;
-    }
-    if (op == 1u) {  // deletion
-      if (L <= 2) continue;
-      const int pos = (int)st.below((uint32_t)L);
-      for (int k = pos; k < L - 1; ++k) c[k] = c[k + 1];
-      --L;
-      return;
-    }
-    if (op == 2u) {  // substitution
-      if (L >= C) continue;
-      const int pos = (int)st.below((uint32_t)L);
-      const int v = draw_free(st, C, c, L);
-      if (v < 0) continue;
-      c[pos] = v;
-      return;
-    }
-    swap_op(st, c, L);
-    return;
-  }
-  swap_op(st, c, L);
-}
-
-__device__ void make_child(const GenArgs &ga, const Buf &pb, int g, int s, int a, int32_t *c,
-                           int &L) {
-  WordStream st(ga.seed, (uint32_t)g, (uint32_t)s, (uint32_t)a);
-  const int p1 = tournament(st, ga, pb);
-  const int32_t *A = pb.cols + (size_t)p1 * kS;
-  const int LA = pb.len[p1];
-  if (st.next() < (1u << 30)) {  // one-point crossover, probability 1/4
-    const int p2 = tournament(st, ga, pb);
-    const int32_t *B = pb.cols + (size_t)p2 * kS;
-    const int LB = pb.len[p2];
-    // (the min() guards only matter for a chromosome shorter than 2, which is never built)
-    const int cut1 = min(1 + (int)st.below((uint32_t)(LA - 1)), max(LA, 1));
-    const int cut2 = min(1 + (int)st.below((uint32_t)(LB - 1)), LB);
-    L = 0;
-    for (int k = 0; k < cut1; ++k) c[L++] = A[k];
-    for (int k = cut2; k < LB && L < ga.max_len; ++k)
-      if (!contains(c, cut1, B[k])) c[L++] = B[k];
-    if (L < 2) {
-      for (int k = 0; k < LA; ++k) c[k] = A[k];
-      L = LA;
-    }
-  } else {
-    for (int k = 0; k < LA; ++k) c[k] = A[k];
-    L = LA;
-  }
-  mutate(st, c, L, ga.C, ga.max_len);
 }
 
 // ------------------------------------------------------------------ kernels
@@ -322,58 +202,242 @@ __global__ void __launch_bounds__(kSlotThreads) k_init(GenArgs ga, Buf nb) {
   if (!dead) dedup_insert(ga.dkeys[0], ga.dslot[0], ga.dmask, h, s);
 }
 
-// One lane per (slot, attempt): the attempts of a slot run side by side in a group of G lanes
-// (G = the power of two >= max_attempts) and the lowest attempt whose key misses the tabu list
-// wins, which is exactly the sequential retry rule; when every attempt hits, the slot is dead
-// and keeps the last attempt's child.  Children are built in shared memory.
-constexpr int kEvolveThreads = 128;
+// ------------------------------------------------------------------ warp-cooperative children
+// One warp builds one child.  The word stream and every decision are uniform across the warp (all
+// lanes compute the same Philox words), and the lanes share the data-parallel work: parent
+// copies, membership tests by ballot, shifts, the crossover's compaction and the tournament's
+// penalty sums.  The child lives in shared memory (kS + 1 ints per warp).
 
-__global__ void __launch_bounds__(kEvolveThreads) k_evolve(GenArgs ga, Buf pb, Buf nb, int G,
-                                                           int par) {
-  __shared__ int32_t s_child[kEvolveThreads][kS + 1];
+__device__ __forceinline__ unsigned lanes_below(int lane) { return (1u << lane) - 1u; }
+
+// Whether v occurs in c[0..L) (L <= 64).
+__device__ __forceinline__ bool w_contains(const int32_t *c, int L, int v, int lane) {
+  const bool hit = (lane < L && c[lane] == v) || (lane + 32 < L && c[lane + 32] == v);
+  return __any_sync(kFull, hit);
+}
+
+__device__ int w_draw_free(WordStream &st, int C, const int32_t *c, int L, int lane) {
+  for (int t = 0; t < 64; ++t) {
+    const int v = (int)st.below((uint32_t)C);
+    if (!w_contains(c, L, v, lane)) return v;
+  }
+  return -1;
+}
+
+// Tournament of T candidates drawn in stream order, up to eight at a time; four lanes sum the
+// column usage of each candidate.  Same winner as the sequential rule (exact penalised
+// comparison, ties to the lower slot).
+__device__ int w_tournament(WordStream &st, const GenArgs &ga, const Buf &pb, int lane) {
+  int best = -1, ub = 0;
+  uint64_t fb = 0ull;
+  const int mine = lane >> 2, sub = lane & 3;
+  for (int t0 = 0; t0 < ga.T; t0 += 8) {
+    int ids[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ids[q] = (t0 + q < ga.T) ? (int)st.below((uint32_t)ga.P) : -1;
+    int my = -1;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q == mine) my = ids[q];
+    uint64_t f = 0ull;
+    int u = 0;
+    if (my >= 0) {
+      const int L = pb.len[my];
+      f = pb.fit[my];
+      const int32_t *cc = pb.cols + (size_t)my * kS;
+#pragma unroll 4
+      for (int k = sub; k < L; k += 4) u += ga.usage[cc[k]];
+    }
+    u += __shfl_xor_sync(kFull, u, 1);
+    u += __shfl_xor_sync(kFull, u, 2);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint64_t fq = __shfl_sync(kFull, f, q * 4);
+      const int uq = __shfl_sync(kFull, u, q * 4);
+      const int iq = ids[q];
+      if (iq < 0) continue;
+      if (best < 0) {
+        best = iq;
+        fb = fq;
+        ub = uq;
+        continue;
+      }
+      const int c = cmp_penalised(fq, uq, fb, ub);
+      if (c > 0 || (c == 0 && iq < best)) {
+        best = iq;
+        fb = fq;
+        ub = uq;
+      }
+    }
+  }
+  return best;
+}
+
+__device__ void w_copy(int32_t *c, const int32_t *src, int L, int lane) {
+  if (lane < L) c[lane] = src[lane];
+  if (lane + 32 < L) c[lane + 32] = src[lane + 32];
+  __syncwarp();
+}
+
+__device__ void w_swap(WordStream &st, int32_t *c, int L, int lane) {
+  if (L < 2) return;  // never reached: every live chromosome has at least two columns
+  const int p = (int)st.below((uint32_t)L);
+  int q = (int)st.below((uint32_t)(L - 1));
+  if (q >= p) ++q;
+  if (lane == 0) {
+    const int t = c[p];
+    c[p] = c[q];
+    c[q] = t;
+  }
+  __syncwarp();
+}
+
+__device__ void w_mutate(WordStream &st, int32_t *c, int &L, int C, int max_len, int lane) {
+  for (int tries = 0; tries < 8; ++tries) {
+    const uint32_t op = st.next() >> 30;
+    if (op == 0u) {  // insertion
+      if (L >= max_len || L >= C) continue;
+      const int pos = (int)st.below((uint32_t)(L + 1));
+      const int v = w_draw_free(st, C, c, L, lane);
+      if (v < 0) continue;
+      const bool m0 = lane >= pos && lane < L, m1 = lane + 32 >= pos && lane + 32 < L;
+      const int x0 = m0 ? c[lane] : 0, x1 = m1 ? c[lane + 32] : 0;
+      __syncwarp();
+      if (m0) c[lane + 1] = x0;
+      if (m1) c[lane + 33] = x1;
+      if (lane == 0) c[pos] = v;
+      __syncwarp();
+      ++L;
+      return;
+    }
+    if (op == 1u) {  // deletion
+      if (L <= 2) continue;
+      const int pos = (int)st.below((uint32_t)L);
+      const bool m0 = lane >= pos && lane < L - 1, m1 = lane + 32 >= pos && lane + 32 < L - 1;
+      const int x0 = m0 ? c[lane + 1] : 0, x1 = m1 ? c[lane + 33] : 0;
+      __syncwarp();
+      if (m0) c[lane] = x0;
+      if (m1) c[lane + 32] = x1;
+      __syncwarp();
+      --L;
+      return;
+    }
+    if (op == 2u) {  // substitution
+      if (L >= C) continue;
+      const int pos = (int)st.below((uint32_t)L);
+      const int v = w_draw_free(st, C, c, L, lane);
+      if (v < 0) continue;
+      if (lane == 0) c[pos] = v;
+      __syncwarp();
+      return;
+    }
+    w_swap(st, c, L, lane);
+    return;
+  }
+  w_swap(st, c, L, lane);
+}
+
+__device__ void w_make_child(const GenArgs &ga, const Buf &pb, int g, int s, int a, int32_t *c,
+                             int &L, int lane) {
+  WordStream st(ga.seed, (uint32_t)g, (uint32_t)s, (uint32_t)a);
+  const int p1 = w_tournament(st, ga, pb, lane);
+  const int32_t *A = pb.cols + (size_t)p1 * kS;
+  const int LA = pb.len[p1];
+  if (st.next() < (1u << 30)) {  // one-point crossover, probability 1/4
+    const int p2 = w_tournament(st, ga, pb, lane);
+    const int32_t *B = pb.cols + (size_t)p2 * kS;
+    const int LB = pb.len[p2];
+    // (the min() guards only matter for a chromosome shorter than 2, which is never built)
+    const int cut1 = min(1 + (int)st.below((uint32_t)(LA - 1)), max(LA, 1));
+    const int cut2 = min(1 + (int)st.below((uint32_t)(LB - 1)), LB);
+    w_copy(c, A, cut1, lane);
+    const int k0 = cut2 + lane, k1 = cut2 + lane + 32;
+    const int b0 = k0 < LB ? B[k0] : -1, b1 = k1 < LB ? B[k1] : -1;
+    bool in0 = false, in1 = false;
+    for (int q = 0; q < cut1; ++q) {
+      const int hq = c[q];
+      in0 |= b0 == hq;
+      in1 |= b1 == hq;
+    }
+    const bool keep0 = b0 >= 0 && !in0, keep1 = b1 >= 0 && !in1;
+    const unsigned m0 = __ballot_sync(kFull, keep0), m1 = __ballot_sync(kFull, keep1);
+    const int pos0 = cut1 + __popc(m0 & lanes_below(lane));
+    const int pos1 = cut1 + __popc(m0) + __popc(m1 & lanes_below(lane));
+    if (keep0 && pos0 < ga.max_len) c[pos0] = b0;
+    if (keep1 && pos1 < ga.max_len) c[pos1] = b1;
+    __syncwarp();
+    L = min(cut1 + __popc(m0) + __popc(m1), ga.max_len);
+    if (L < 2) {
+      w_copy(c, A, LA, lane);
+      L = LA;
+    }
+  } else {
+    w_copy(c, A, LA, lane);
+    L = LA;
+  }
+  w_mutate(st, c, L, ga.C, ga.max_len, lane);
+}
+
+// One block per slot, one warp per attempt (G warps, G = the power of two >= max_attempts): the
+// lowest attempt whose key misses the tabu list wins, which is exactly the sequential retry
+// rule; when every attempt hits, the slot is dead and keeps the last attempt's child.
+constexpr int kMaxAttemptWarps = 16;
+
+__global__ void __launch_bounds__(kMaxAttemptWarps * 32) k_evolve(GenArgs ga, Buf pb, Buf nb,
+                                                                  int par) {
+  __shared__ int32_t s_child[kMaxAttemptWarps][kS + 1];
+  __shared__ int s_ok[kMaxAttemptWarps];
   if (ga.ctl->stopped) return;
-  const int lane = threadIdx.x & 31;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = gtid / G, a = gtid - (gtid / G) * G;
-  const bool valid = s < ga.P;
+  const int lane = threadIdx.x & 31, a = threadIdx.x >> 5;
+  const int s = blockIdx.x;
   const int g = ga.ctl->gen + 1;
   const int n_el = min(ga.E, ga.ctl->n_top);
-  const bool elite = valid && s < n_el;
-  int32_t *c = s_child[threadIdx.x];
-  int L = 0;
-  uint64_t h = 0ull;
-  bool ok = false;
-  if (valid && !elite && a < ga.A) {
-    make_child(ga, pb, g, s, a, c, L);
-    h = chromosome_key(c, L);
-    ok = !tabu_contains(ga.tabu, ga.tmask, h) &&
-         !tabu_contains(ga.dkeys[par ^ 1], ga.dmask, h);  // generation g-1's live keys
-  }
-  const unsigned m = __ballot_sync(kFull, ok);
-  if (!valid) return;
   int32_t *out = nb.cols + (size_t)s * kS;
-  if (elite) {  // elitism: copy top-list entry s (its key is already in the tabu list)
+  if (s < n_el) {  // elitism: copy top-list entry s (its key is already in the tabu list)
     if (a == 0) {
       const TopEntry &e = ga.top[s];
-      for (int k = 0; k < kS; ++k) out[k] = k < e.len ? e.cols[k] : 0;
-      nb.len[s] = e.len;
-      nb.hash[s] = e.h;
-      nb.att_dead[s] = 0;
-      nb.att_hits[s] = 0;
+      out[lane] = lane < e.len ? e.cols[lane] : 0;
+      out[lane + 32] = lane + 32 < e.len ? e.cols[lane + 32] : 0;
+      if (lane == 0) {
+        nb.len[s] = e.len;
+        nb.hash[s] = e.h;
+        nb.att_dead[s] = 0;
+        nb.att_hits[s] = 0;
+      }
     }
     return;
   }
-  const int gbase = lane - (lane % G);
-  const unsigned gm = (m >> gbase) & (G >= 32 ? kFull : ((1u << G) - 1u));
-  const bool dead = gm == 0u;
-  const int win = dead ? ga.A - 1 : __ffs(gm) - 1;
+  int32_t *c = s_child[a];
+  int L = 0;
+  uint64_t h = 0ull;
+  int ok = 0;
+  if (a < ga.A) {
+    w_make_child(ga, pb, g, s, a, c, L, lane);
+    h = chromosome_key(c, L);
+    if (lane == 0)
+      ok = !tabu_contains(ga.tabu, ga.tmask, h) &&
+           !tabu_contains(ga.dkeys[par ^ 1], ga.dmask, h);  // generation g-1's live keys
+  }
+  if (lane == 0) s_ok[a] = ok;
+  __syncthreads();
+  int win = -1;
+  for (int q = 0; q < ga.A; ++q)
+    if (s_ok[q]) {
+      win = q;
+      break;
+    }
+  const bool dead = win < 0;
+  if (dead) win = ga.A - 1;
   if (a != win) return;
-  for (int k = 0; k < kS; ++k) out[k] = k < L ? c[k] : 0;
-  nb.len[s] = L;
-  nb.hash[s] = h;
-  nb.att_dead[s] = dead;
-  nb.att_hits[s] = dead ? ga.A : win;
-  if (!dead) dedup_insert(ga.dkeys[par], ga.dslot[par], ga.dmask, h, s);
+  out[lane] = lane < L ? c[lane] : 0;
+  out[lane + 32] = lane + 32 < L ? c[lane + 32] : 0;
+  if (lane == 0) {
+    nb.len[s] = L;
+    nb.hash[s] = h;
+    nb.att_dead[s] = dead;
+    nb.att_hits[s] = dead ? ga.A : win;
+    if (!dead) dedup_insert(ga.dkeys[par], ga.dslot[par], ga.dmask, h, s);
+  }
 }
 
 __device__ __forceinline__ bool key_before(uint64_t fa, uint64_t ha, uint64_t fb, uint64_t hb) {
@@ -527,9 +591,10 @@ __device__ int process_chunk(const GenArgs &ga, const TopSmem &sm, int n, const 
 // a sentinel that sorts last); results land in sf/sh/ss[0..count).
 __device__ void warp_sort(const uint64_t *gf, const uint64_t *gh, const int32_t *gs, int count,
                           uint64_t *sf, uint64_t *sh, int32_t *ss, int lane) {
-  uint64_t f = lane < count ? __ldcg(gf + lane) : 0ull;
-  uint64_t h = lane < count ? __ldcg(gh + lane) : ~0ull;
-  int32_t sl = lane < count ? __ldcg(gs + lane) : 0x7FFFFFFF;
+  uint64_t f = lane < count ? gf[lane] : 0ull;
+  uint64_t h = lane < count ? gh[lane] : ~0ull;
+  int32_t sl = lane < count ? gs[lane] : 0x7FFFFFFF;
+  __syncwarp();
   for (int k = 2; k <= 32; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       const uint64_t pf = __shfl_xor_sync(kFull, f, j), ph = __shfl_xor_sync(kFull, h, j);
@@ -556,15 +621,36 @@ __device__ void warp_sort(const uint64_t *gf, const uint64_t *gh, const int32_t 
 // in global memory, by size), then stages them kChunk at a time in shared memory and lets warp 0
 // process each chunk.  Returns the new list length (valid in every thread).
 __device__ int sort_and_process(const GenArgs &ga, const Buf &nb, const TopSmem &sm, int n,
-                                int count, int *s_n, int *s_stop) {
+                                int count, bool in_smem, int *s_n, int *s_stop) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int N = 1;
   while (N < count) N <<= 1;
   const uint64_t *cf;
   const uint64_t *ch;
   const int32_t *cs;
-  if (count <= 32) {
-    if (warp == 0) warp_sort(ga.cand_f, ga.cand_h, ga.cand_s, count, sm.sf, sm.sh, sm.ss, lane);
+  if (in_smem) {  // already in sm.sf / sh / ss (count <= sort_cap)
+    if (count <= 32) {
+      if (warp == 0) warp_sort(sm.sf, sm.sh, sm.ss, count, sm.sf, sm.sh, sm.ss, lane);
+    } else {
+      block_sort(sm.sf, sm.sh, sm.ss, count);
+    }
+    __syncthreads();
+    cf = sm.sf;
+    ch = sm.sh;
+    cs = sm.ss;
+  } else if (count <= 32) {
+    // written by other blocks: read from L2
+    if (warp == 0) {
+      const uint64_t *gf = ga.cand_f, *gh = ga.cand_h;
+      const int32_t *gs = ga.cand_s;
+      for (int i = lane; i < count; i += 32) {
+        sm.sf[i] = __ldcg(gf + i);
+        sm.sh[i] = __ldcg(gh + i);
+        sm.ss[i] = __ldcg(gs + i);
+      }
+      __syncwarp();
+      warp_sort(sm.sf, sm.sh, sm.ss, count, sm.sf, sm.sh, sm.ss, lane);
+    }
     __syncthreads();
     cf = sm.sf;
     ch = sm.sh;
@@ -624,13 +710,29 @@ __device__ int sort_and_process(const GenArgs &ga, const Buf &nb, const TopSmem 
 // list (clearing it for generation g+1); the last block to finish then runs the single-block part.
 __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, int par) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_hits, s_live, s_lsum, s_last, s_n, s_cnt, s_stop;
+  __shared__ int s_hits, s_live, s_lsum, s_last, s_n, s_cnt, s_stop, s_nc;
   GenCtl *ctl = ga.ctl;
   if (ctl->stopped) return;
+  // A single block keeps the candidates and counters in shared memory; several blocks use the
+  // global arrays and counters and hand over to the last block to finish.
+  const bool single = gridDim.x == 1 && ga.P <= ga.sort_cap;
+  TopSmem sm;
+  const int cw = (ga.C + 31) / 32;
+  sm.pool = reinterpret_cast<TopEntry *>(smem);
+  sm.sf = reinterpret_cast<uint64_t *>(sm.pool + ga.K + 1);
+  sm.sh = sm.sf + ga.sort_cap;
+  sm.colbits = reinterpret_cast<uint32_t *>(sm.sh + ga.sort_cap);
+  sm.ss = reinterpret_cast<int32_t *>(sm.colbits + cw);
+  sm.idx = sm.ss + ga.sort_cap;
+  sm.idx2 = sm.idx + ga.K + 1;
+  sm.ccols = sm.idx2 + ga.K + 1;
+  sm.cmeta = sm.ccols + kChunk * kS;
+  sm.used = reinterpret_cast<uint8_t *>(sm.cmeta + kChunk * 4);
   if (threadIdx.x == 0) {
     s_hits = 0;
     s_live = 0;
     s_lsum = 0;
+    s_nc = 0;
   }
   __syncthreads();
   const int n0 = ctl->n_top;
@@ -640,30 +742,38 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   int hits = 0, live = 0, lsum = 0;
   for (int s = tid; s < ga.P; s += stride) {
+    // every load of the slot first, then the duplicate lookup, then the stores
     const bool att_dead = nb.att_dead[s] != 0;
     const uint64_t h = nb.hash[s];
+    const int L = nb.len[s], ah = nb.att_hits[s];
+    const int rp = ga.rows_scr[s], rn = ga.rows_scr[ga.P + s], ra = ga.rows_scr[2 * ga.P + s];
     const bool dup = !att_dead && dedup_is_dup(ga.dkeys[par], ga.dslot[par], ga.dmask, h, s);
     const bool dead = att_dead || dup;
+    const uint64_t f =
+        (dead || ra < ga.min_rows) ? 0ull : ((uint64_t)ra << (L < ga.col_cap ? L : ga.col_cap));
     nb.dead[s] = dead;
-    const int rp = ga.rows_scr[s], rn = ga.rows_scr[ga.P + s], ra = ga.rows_scr[2 * ga.P + s];
     ga.rows_scr[s] = 0;
     ga.rows_scr[ga.P + s] = 0;
     ga.rows_scr[2 * ga.P + s] = 0;
     nb.rows[s] = rp;
     nb.rows[ga.P + s] = rn;
     nb.rows[2 * ga.P + s] = ra;
-    const int L = nb.len[s];
-    const uint64_t f =
-        (dead || ra < ga.min_rows) ? 0ull : ((uint64_t)ra << (L < ga.col_cap ? L : ga.col_cap));
     nb.fit[s] = f;
-    hits += nb.att_hits[s] + (dup ? 1 : 0);
+    hits += ah + (dup ? 1 : 0);
     live += !dead;
     lsum += dead ? 0 : L;
     if (!dead && f > 0ull && (!had_threshold || key_before(f, h, tf, th))) {
-      const int q = atomicAdd(&ctl->n_cand, 1);
-      ga.cand_f[q] = f;
-      ga.cand_h[q] = h;
-      ga.cand_s[q] = s;
+      if (single) {  // at most P <= sort_cap candidates
+        const int q = atomicAdd(&s_nc, 1);
+        sm.sf[q] = f;
+        sm.sh[q] = h;
+        sm.ss[q] = s;
+      } else {
+        const int q = atomicAdd(&ctl->n_cand, 1);
+        ga.cand_f[q] = f;
+        ga.cand_h[q] = h;
+        ga.cand_s[q] = s;
+      }
     }
   }
   // generation g-1's live keys join the tabu list; its duplicate table is cleared for g+1
@@ -688,43 +798,43 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
   }
   if (added) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->tabu_count), added);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    if (s_hits) atomicAdd(&ctl->hits_cur, s_hits);
-    if (s_live) atomicAdd(&ctl->live_cur, s_live);
-    if (s_lsum) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->len_cur), (unsigned long long)s_lsum);
+  int hits_g, live_g, nc;
+  long long len_g;
+  if (single) {
+    hits_g = s_hits;
+    live_g = s_live;
+    len_g = s_lsum;
+    nc = s_nc;
+  } else {
+    if (threadIdx.x == 0) {
+      if (s_hits) atomicAdd(&ctl->hits_cur, s_hits);
+      if (s_live) atomicAdd(&ctl->live_cur, s_live);
+      if (s_lsum)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->len_cur),
+                  (unsigned long long)s_lsum);
+      __threadfence();
+      s_last = atomicAdd(&ctl->done, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
     __threadfence();
-    s_last = atomicAdd(&ctl->done, 1) == (int)gridDim.x - 1;
+    hits_g = __ldcg(&ctl->hits_cur);
+    live_g = __ldcg(&ctl->live_cur);
+    len_g = __ldcg(&ctl->len_cur);
+    nc = __ldcg(&ctl->n_cand);
   }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
 
   // ---- last block: step 6, then the top rank list (step 7)
   const bool init = ctl->gen < 0;
-  const int hits_g = __ldcg(&ctl->hits_cur);
-  const int live_g = __ldcg(&ctl->live_cur);
-  const int nc = __ldcg(&ctl->n_cand);
   if (!init && ga.tabu_limit > 0 && hits_g >= ga.tabu_limit) {
     if (threadIdx.x == 0) {
       ctl->hits_last = hits_g;
       ctl->stopped = 1;
       ctl->n_evaluated += live_g;          // the generation was evaluated, then discarded
-      ctl->sum_len += __ldcg(&ctl->len_cur);
+      ctl->sum_len += len_g;
     }
     return;
   }
-  TopSmem sm;
-  const int cw = (ga.C + 31) / 32;
-  sm.pool = reinterpret_cast<TopEntry *>(smem);
-  sm.sf = reinterpret_cast<uint64_t *>(sm.pool + ga.K + 1);
-  sm.sh = sm.sf + ga.sort_cap;
-  sm.colbits = reinterpret_cast<uint32_t *>(sm.sh + ga.sort_cap);
-  sm.ss = reinterpret_cast<int32_t *>(sm.colbits + cw);
-  sm.idx = sm.ss + ga.sort_cap;
-  sm.idx2 = sm.idx + ga.K + 1;
-  sm.ccols = sm.idx2 + ga.K + 1;
-  sm.cmeta = sm.ccols + kChunk * kS;
-  sm.used = reinterpret_cast<uint8_t *>(sm.cmeta + kChunk * 4);
   for (int i = threadIdx.x; i < cw; i += blockDim.x) sm.colbits[i] = 0u;
   for (int e = threadIdx.x; e <= ga.K; e += blockDim.x) {
     sm.used[e] = e < n0;
@@ -734,7 +844,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
     reinterpret_cast<int32_t *>(sm.pool)[q] = reinterpret_cast<const int32_t *>(ga.top)[q];
   __syncthreads();
   int n = n0;
-  if (nc > 0) n = sort_and_process(ga, nb, sm, n, nc, &s_n, &s_stop);
+  if (nc > 0) n = sort_and_process(ga, nb, sm, n, nc, single, &s_n, &s_stop);
   if (had_threshold && n < ga.K) {
     // Evictions left room: the candidates ranking after the old threshold come next.
     if (threadIdx.x == 0) s_cnt = 0;
@@ -751,7 +861,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
     __syncthreads();
     const int cnt = s_cnt;
     __syncthreads();
-    if (cnt > 0) n = sort_and_process(ga, nb, sm, n, cnt, &s_n, &s_stop);
+    if (cnt > 0) n = sort_and_process(ga, nb, sm, n, cnt, false, &s_n, &s_stop);
   }
   const int words = (int)(sizeof(TopEntry) / 4);
   for (int q = threadIdx.x; q < n * words; q += blockDim.x) {
@@ -771,7 +881,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
     ctl->n_top = n;
     ctl->gen += 1;
     ctl->n_evaluated += live_g;
-    ctl->sum_len += __ldcg(&ctl->len_cur);
+    ctl->sum_len += len_g;
     ctl->len_cur = 0;
     ctl->hits_cur = 0;
     ctl->live_cur = 0;
@@ -1026,11 +1136,10 @@ cudaError_t launch_scoring(ebic_ctx *ctx, GenState *g, int k, cudaStream_t s, Ma
 cudaError_t launch_generation(ebic_ctx *ctx, GenState *g, int parity, cudaStream_t s, Marks *m) {
   int G = 1;
   while (G < g->p.max_attempts) G <<= 1;
-  const int64_t threads = (int64_t)g->P * G;
   cudaError_t e = mark(s, m, 0);
   if (e != cudaSuccess) return e;
-  k_evolve<<<(unsigned)((threads + kEvolveThreads - 1) / kEvolveThreads), kEvolveThreads, 0, s>>>(
-      gen_args(ctx, g), g->buf(parity ^ 1), g->buf(parity), G, parity);
+  k_evolve<<<(unsigned)g->P, G * 32, 0, s>>>(gen_args(ctx, g), g->buf(parity ^ 1),
+                                            g->buf(parity), parity);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return launch_scoring(ctx, g, parity, s, m);
 }
@@ -1133,6 +1242,7 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
                 (size_t)kChunk * (kS + 4) * 4 + (size_t)(g->K + 1) + 16;
   EBIC_CHECK_CUDA(ctx, cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)g->top_smem));
+
   // enough blocks to spread the slot and table loops, few enough to be co-resident quickly
   const int64_t work = std::max<int64_t>(g->P, g->dcap);
   g->finish_blocks = (int)std::max<int64_t>(
