@@ -72,44 +72,90 @@ __global__ void k_upload_colmajor(const float *__restrict__ x, int64_t R, int32_
 }
 
 // Pair bitmap: G[(a*C + b)*Wst + w] bit j = [key(32w+j, b) > key(32w+j, a)].
-// Block = 8 warps, one column a per warp; a block covers 32 words (1024 rows) of rows.  The
-// b-columns of the chunk are staged in shared memory in groups of kBStage columns and shared by
-// the 8 warps; each warp keeps its a-column chunk in registers and forms one word per ballot.
-constexpr int kBStage = 8;
+// A block covers 32 words (1024 rows) of kBW columns a (one per warp, its 1024 keys held in
+// registers).  Each unordered pair a < b is compared once: the ballot of kb > ka gives G[a][b]
+// and the ballot of kb < ka gives G[b][a] (ties set neither).  The b-columns of the chunk stream
+// through a double-buffered shared-memory stage filled with cp.async, so their loads overlap
+// the ballots; lane 0 parks the 32 ballots of a pair in shared memory and the warp then writes
+// them as two coalesced 128-byte rows.
+constexpr int kBW = 8;  // warps (a-columns) per block
+constexpr int kBS = 4;  // b-columns per stage
 
-__global__ void __launch_bounds__(256) k_build_bitmap(const uint32_t *__restrict__ keys,
-                                                      int64_t R_pad, int32_t C, int64_t Wst,
-                                                      uint32_t *__restrict__ G) {
-  __shared__ uint32_t sb[kBStage][1024];
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gmem));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+__global__ void __launch_bounds__(kBW * 32, 4) k_build_bitmap(const uint32_t *__restrict__ keys,
+                                                              int64_t R_pad, int32_t C,
+                                                              int64_t Wst,
+                                                              uint32_t *__restrict__ G) {
+  __shared__ __align__(16) uint32_t sb[2][kBS][1024];
+  __shared__ uint32_t s_out[kBW][2][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t w0 = (int64_t)blockIdx.x * 32;
-  const int64_t nw = (Wst - w0 < 32) ? (Wst - w0) : 32;  // words of this chunk
-  const int32_t a = blockIdx.y * 8 + warp;
+  const int nw = (int)((Wst - w0 < 32) ? (Wst - w0) : 32);  // words of this chunk
+  const int a0 = blockIdx.y * kBW;
+  const int a = a0 + warp;
   const bool a_ok = a < C;
   uint32_t ka[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j)
     ka[j] = (a_ok && j < nw) ? __ldg(keys + (int64_t)a * R_pad + (w0 + j) * 32 + lane) : 0u;
-
-  for (int32_t b0 = 0; b0 < C; b0 += kBStage) {
-    const int nb = (C - b0 < kBStage) ? (C - b0) : kBStage;
-    __syncthreads();
-    for (int q = threadIdx.x; q < nb * 1024; q += blockDim.x) {
-      const int bb = q >> 10, rr = q & 1023;
-      const int64_t row = w0 * 32 + rr;
-      sb[bb][rr] = (row < R_pad) ? __ldg(keys + (int64_t)(b0 + bb) * R_pad + row) : 0u;
+  if (a_ok && lane < nw) G[((int64_t)a * C + a) * Wst + w0 + lane] = 0u;  // diagonal
+  const int bstart = a0 + 1;
+  const int nstages = bstart < C ? (C - bstart + kBS - 1) / kBS : 0;
+  const int pieces = nw * 8;  // 16-byte pieces of one column's chunk
+  auto issue = [&](int st, int buf) {
+    const int b0 = bstart + st * kBS;
+    for (int i = threadIdx.x; i < kBS * pieces; i += blockDim.x) {
+      const int bb = i / pieces, piece = i - bb * pieces;
+      const int b = b0 + bb;
+      if (b < C)
+        cp_async16(&sb[buf][bb][piece * 4], keys + (int64_t)b * R_pad + w0 * 32 + piece * 4);
+    }
+    cp_commit();
+  };
+  if (nstages > 0) issue(0, 0);
+  for (int st = 0; st < nstages; ++st) {
+    if (st + 1 < nstages) {
+      issue(st + 1, (st + 1) & 1);
+      cp_wait<1>();
+    } else {
+      cp_wait<0>();
     }
     __syncthreads();
-    if (!a_ok) continue;
-    for (int bb = 0; bb < nb; ++bb) {
-      uint32_t word = 0u;
+    const int buf = st & 1, b0 = bstart + st * kBS;
+    if (a_ok) {
+      for (int bb = 0; bb < kBS; ++bb) {
+        const int b = b0 + bb;
+        if (b >= C) break;
+        if (b <= a) continue;
+        const uint32_t *col = sb[buf][bb];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const uint32_t m = __ballot_sync(0xFFFFFFFFu, sb[bb][j * 32 + lane] > ka[j]);
-        if (lane == j) word = m;
+        for (int j = 0; j < 32; ++j) {
+          const uint32_t kb = col[j * 32 + lane];
+          const uint32_t gt = __ballot_sync(0xFFFFFFFFu, kb > ka[j]);
+          const uint32_t lt = __ballot_sync(0xFFFFFFFFu, kb < ka[j]);
+          if (lane == 0) {
+            s_out[warp][0][j] = gt;
+            s_out[warp][1][j] = lt;
+          }
+        }
+        __syncwarp();
+        if (lane < nw) {
+          G[((int64_t)a * C + b) * Wst + w0 + lane] = s_out[warp][0][lane];
+          G[((int64_t)b * C + a) * Wst + w0 + lane] = s_out[warp][1][lane];
+        }
+        __syncwarp();
       }
-      if (lane < nw) G[((int64_t)a * C + (b0 + bb)) * Wst + w0 + lane] = word;
     }
+    __syncthreads();  // this buffer is consumed before it is refilled
   }
 }
 
@@ -131,7 +177,7 @@ cudaError_t launch_upload(const float *x, int64_t R, int32_t C, int64_t R_pad, i
 
 cudaError_t launch_build_bitmap(const uint32_t *keys, int64_t R_pad, int32_t C, int64_t Wst,
                                 uint32_t *bitmap, cudaStream_t s) {
-  dim3 grid((unsigned)((Wst + 31) / 32), (unsigned)((C + 7) / 8));
-  k_build_bitmap<<<grid, 256, 0, s>>>(keys, R_pad, C, Wst, bitmap);
+  dim3 grid((unsigned)((Wst + 31) / 32), (unsigned)((C + kBW - 1) / kBW));
+  k_build_bitmap<<<grid, kBW * 32, 0, s>>>(keys, R_pad, C, Wst, bitmap);
   return cudaGetLastError();
 }
