@@ -40,6 +40,25 @@ __device__ __forceinline__ bool pv_dead(const PopView &v, int i) {
   return false;
 }
 
+// The generation loop's side task (see EvalArgs): move a duplicate table into the tabu list.
+__device__ __noinline__ void move_keys(const EvalArgs &a) {
+  if (!a.mv_keys) return;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  unsigned long long added = 0ull;
+  for (uint32_t i = tid; i < a.mv_n; i += stride) {
+    const uint64_t k = a.mv_keys[i];
+    if (k) {
+      added += tabu_insert(a.mv_table, a.mv_tmask, k) ? 1ull : 0ull;
+      a.mv_keys[i] = 0ull;
+      a.mv_slots[i] = 0u;
+    }
+  }
+  if (added) atomicAdd(a.mv_count, added);
+}
+
+// Waits for the preceding kernel of a programmatic launch (no-op otherwise).
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ uint4 ldg4(const uint32_t *p) {
   return __ldg(reinterpret_cast<const uint4 *>(p));
 }
@@ -67,7 +86,9 @@ __global__ void k_validate_csr(const int32_t *__restrict__ cols, const int32_t *
 template <bool NEG>
 __global__ void __launch_bounds__(kThreads) k_eval_direct(EvalArgs a, PopView pv) {
   __shared__ int64_t s_base[kWarps][EBIC_MAX_LEN];
+  wait_prior_grid();
   if (pv.stop && *pv.stop) return;
+  move_keys(a);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t passes_total = a.R_pad / 128;
   const int32_t n_items = pv.n * a.n_seg;
@@ -196,10 +217,12 @@ __device__ __forceinline__ int popc4(uint4 v) {
 }
 
 template <bool NEG>
-__global__ void __launch_bounds__(kThreads) k_eval_bitmap(EvalArgs a, PopView pv) {
+__global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView pv) {
   __shared__ int64_t s_pos[kWarps][EBIC_MAX_LEN];
   __shared__ int64_t s_neg[kWarps][EBIC_MAX_LEN];
+  wait_prior_grid();
   if (pv.stop && *pv.stop) return;
+  move_keys(a);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t Wst = a.Wst;
   const int64_t passes_total = (Wst + 127) / 128;
@@ -385,8 +408,30 @@ cudaError_t launch_fitness(const EvalArgs &a, const PopView &pv, cudaStream_t s)
   return cudaGetLastError();
 }
 
+// Launches `kern` with programmatic stream serialisation when `pdl` is set (the kernel calls
+// griddepcontrol.wait before it reads what the previous kernel wrote).
+template <class... Args>
+cudaError_t launch_maybe_pdl(void (*kern)(Args...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t s, bool pdl, Args... args) {
+  if (!pdl) {
+    kern<<<grid, block, smem, s>>>(args...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 cudaError_t launch_eval_kernel(int mode, const EvalArgs &a0, const PopView &pv, int num_sms,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool pdl) {
   if (pv.n <= 0) return cudaSuccess;
   EvalArgs a = a0;
   const bool bitmap = (mode == EBIC_MODE_BITMAP);
@@ -412,18 +457,12 @@ cudaError_t launch_eval_kernel(int mode, const EvalArgs &a0, const PopView &pv, 
   int64_t grid = (int64_t)num_sms * bps;
   const int64_t need = (items + kWarps - 1) / kWarps;
   if (grid > need) grid = need;
-  if (bitmap) {
-    if (a.neg)
-      k_eval_bitmap<true><<<(unsigned)grid, kThreads, 0, s>>>(a, pv);
-    else
-      k_eval_bitmap<false><<<(unsigned)grid, kThreads, 0, s>>>(a, pv);
-  } else {
-    if (a.neg)
-      k_eval_direct<true><<<(unsigned)grid, kThreads, 0, s>>>(a, pv);
-    else
-      k_eval_direct<false><<<(unsigned)grid, kThreads, 0, s>>>(a, pv);
-  }
-  return cudaGetLastError();
+  const dim3 g3((unsigned)grid), b3(kThreads);
+  if (bitmap)
+    return a.neg ? launch_maybe_pdl(k_eval_bitmap<true>, g3, b3, 0, s, pdl, a, pv)
+                 : launch_maybe_pdl(k_eval_bitmap<false>, g3, b3, 0, s, pdl, a, pv);
+  return a.neg ? launch_maybe_pdl(k_eval_direct<true>, g3, b3, 0, s, pdl, a, pv)
+               : launch_maybe_pdl(k_eval_direct<false>, g3, b3, 0, s, pdl, a, pv);
 }
 
 cudaError_t launch_eval(int mode, const EvalArgs &a, const PopView &pv, int num_sms,

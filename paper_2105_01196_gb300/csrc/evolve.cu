@@ -83,6 +83,9 @@ struct GenArgs {
   int32_t min_rows, col_cap, ov_num, ov_den, tabu_limit;
 };
 
+// Waits for the preceding kernel of a programmatic launch (no-op otherwise).
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ------------------------------------------------------------------ Philox4x32-10 word stream
 
 constexpr uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
@@ -224,11 +227,14 @@ __device__ int w_draw_free(WordStream &st, int C, const int32_t *c, int L, int l
   return -1;
 }
 
-// Tournament of T candidates drawn in stream order, up to eight at a time; four lanes sum the
-// column usage of each candidate.  Same winner as the sequential rule (exact penalised
-// comparison, ties to the lower slot).
-__device__ int w_tournament(WordStream &st, const GenArgs &ga, const Buf &pb, int lane) {
-  int best = -1, ub = 0;
+// Tournament of T candidates drawn in stream order, up to eight at a time.  Four lanes serve each
+// candidate: one round of loads brings its fitness, length and all 64 column words (the tail past
+// the length is zero), a second its column usage.  The columns go to the warp's scratch rows so
+// that the winner's chromosome is copied to `win` without another trip to global memory.  Same
+// winner as the sequential rule (exact penalised comparison, ties to the lower slot).
+__device__ int w_tournament(WordStream &st, const GenArgs &ga, const Buf &pb, int32_t *scratch,
+                            int32_t *win, int *win_len, int lane) {
+  int best = -1, ub = 0, bl = 0;
   uint64_t fb = 0ull;
   const int mine = lane >> 2, sub = lane & 3;
   for (int t0 = 0; t0 < ga.T; t0 += 8) {
@@ -240,36 +246,53 @@ __device__ int w_tournament(WordStream &st, const GenArgs &ga, const Buf &pb, in
     for (int q = 0; q < 8; ++q)
       if (q == mine) my = ids[q];
     uint64_t f = 0ull;
-    int u = 0;
+    int u = 0, L = 0;
     if (my >= 0) {
-      const int L = pb.len[my];
+      // lane `sub` of the candidate holds the 16-byte chunks sub, sub + 4, sub + 8, sub + 12
+      const int4 *cc4 = reinterpret_cast<const int4 *>(pb.cols + (size_t)my * kS);
+      L = pb.len[my];
       f = pb.fit[my];
-      const int32_t *cc = pb.cols + (size_t)my * kS;
-#pragma unroll 4
-      for (int k = sub; k < L; k += 4) u += ga.usage[cc[k]];
+      int4 v[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) v[r] = cc4[sub + 4 * r];
+      int4 *row4 = reinterpret_cast<int4 *>(scratch + mine * kS);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int k = 4 * (sub + 4 * r);
+        const int u0 = k < L ? ga.usage[v[r].x] : 0, u1 = k + 1 < L ? ga.usage[v[r].y] : 0;
+        const int u2 = k + 2 < L ? ga.usage[v[r].z] : 0, u3 = k + 3 < L ? ga.usage[v[r].w] : 0;
+        u += u0 + u1 + u2 + u3;
+        row4[sub + 4 * r] = v[r];
+      }
     }
     u += __shfl_xor_sync(kFull, u, 1);
     u += __shfl_xor_sync(kFull, u, 2);
+    __syncwarp();
+    int take = -1;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const uint64_t fq = __shfl_sync(kFull, f, q * 4);
       const int uq = __shfl_sync(kFull, u, q * 4);
+      const int lq = __shfl_sync(kFull, L, q * 4);
       const int iq = ids[q];
       if (iq < 0) continue;
-      if (best < 0) {
-        best = iq;
-        fb = fq;
-        ub = uq;
-        continue;
-      }
-      const int c = cmp_penalised(fq, uq, fb, ub);
+      const int c = best < 0 ? 1 : cmp_penalised(fq, uq, fb, ub);
       if (c > 0 || (c == 0 && iq < best)) {
         best = iq;
         fb = fq;
         ub = uq;
+        bl = lq;
+        take = q;
       }
     }
+    if (take >= 0) {  // the winner so far is in this group: keep its columns
+      const int32_t *row = scratch + take * kS;
+      win[lane] = row[lane];
+      win[lane + 32] = row[lane + 32];
+    }
+    __syncwarp();
   }
+  *win_len = bl;
   return best;
 }
 
@@ -338,15 +361,12 @@ __device__ void w_mutate(WordStream &st, int32_t *c, int &L, int C, int max_len,
 }
 
 __device__ void w_make_child(const GenArgs &ga, const Buf &pb, int g, int s, int a, int32_t *c,
-                             int &L, int lane) {
+                             int32_t *scratch, int32_t *A, int32_t *B, int &L, int lane) {
   WordStream st(ga.seed, (uint32_t)g, (uint32_t)s, (uint32_t)a);
-  const int p1 = w_tournament(st, ga, pb, lane);
-  const int32_t *A = pb.cols + (size_t)p1 * kS;
-  const int LA = pb.len[p1];
+  int LA = 0, LB = 0;
+  w_tournament(st, ga, pb, scratch, A, &LA, lane);
   if (st.next() < (1u << 30)) {  // one-point crossover, probability 1/4
-    const int p2 = w_tournament(st, ga, pb, lane);
-    const int32_t *B = pb.cols + (size_t)p2 * kS;
-    const int LB = pb.len[p2];
+    w_tournament(st, ga, pb, scratch, B, &LB, lane);
     // (the min() guards only matter for a chromosome shorter than 2, which is never built)
     const int cut1 = min(1 + (int)st.below((uint32_t)(LA - 1)), max(LA, 1));
     const int cut2 = min(1 + (int)st.below((uint32_t)(LB - 1)), LB);
@@ -382,11 +402,18 @@ __device__ void w_make_child(const GenArgs &ga, const Buf &pb, int g, int s, int
 // lowest attempt whose key misses the tabu list wins, which is exactly the sequential retry
 // rule; when every attempt hits, the slot is dead and keeps the last attempt's child.
 constexpr int kMaxAttemptWarps = 16;
+// Per-warp shared memory of k_evolve, in ints: 8 tournament scratch rows, the two parents and the
+// child (kS + 1 used).  Every part starts on a 16-byte boundary (the scratch rows are written with
+// 16-byte stores), and the total is a multiple of 16 bytes.
+constexpr int kEvoScratch = 0, kEvoA = 8 * kS, kEvoB = 9 * kS, kEvoChild = 10 * kS;
+constexpr int kEvolveWarpInts = 10 * kS + kS + 4;
+static_assert(kEvolveWarpInts % 4 == 0, "per-warp region must keep 16-byte alignment");
 
 __global__ void __launch_bounds__(kMaxAttemptWarps * 32) k_evolve(GenArgs ga, Buf pb, Buf nb,
                                                                   int par) {
-  __shared__ int32_t s_child[kMaxAttemptWarps][kS + 1];
+  extern __shared__ __align__(16) int32_t s_evo[];  // kEvolveWarpInts per warp
   __shared__ int s_ok[kMaxAttemptWarps];
+  wait_prior_grid();
   if (ga.ctl->stopped) return;
   const int lane = threadIdx.x & 31, a = threadIdx.x >> 5;
   const int s = blockIdx.x;
@@ -407,16 +434,19 @@ __global__ void __launch_bounds__(kMaxAttemptWarps * 32) k_evolve(GenArgs ga, Bu
     }
     return;
   }
-  int32_t *c = s_child[a];
+  int32_t *base = s_evo + a * kEvolveWarpInts;
+  int32_t *scratch = base + kEvoScratch, *A = base + kEvoA, *B = base + kEvoB;
+  int32_t *c = base + kEvoChild;
   int L = 0;
   uint64_t h = 0ull;
   int ok = 0;
   if (a < ga.A) {
-    w_make_child(ga, pb, g, s, a, c, L, lane);
+    w_make_child(ga, pb, g, s, a, c, scratch, A, B, L, lane);
     h = chromosome_key(c, L);
-    if (lane == 0)
-      ok = !tabu_contains(ga.tabu, ga.tmask, h) &&
-           !tabu_contains(ga.dkeys[par ^ 1], ga.dmask, h);  // generation g-1's live keys
+    // lane 0 probes the hashed tabu list, lane 1 generation g-1's live keys
+    const bool hit = (lane == 0 && tabu_contains(ga.tabu, ga.tmask, h)) ||
+                     (lane == 1 && tabu_contains(ga.dkeys[par ^ 1], ga.dmask, h));
+    ok = !__any_sync(kFull, hit);
   }
   if (lane == 0) s_ok[a] = ok;
   __syncthreads();
@@ -712,6 +742,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_hits, s_live, s_lsum, s_last, s_n, s_cnt, s_stop, s_nc;
   GenCtl *ctl = ga.ctl;
+  wait_prior_grid();
   if (ctl->stopped) return;
   // A single block keeps the candidates and counters in shared memory; several blocks use the
   // global arrays and counters and hand over to the last block to finish.
@@ -739,6 +770,10 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
   const bool had_threshold = n0 >= ga.K;
   const uint64_t tf = had_threshold ? ga.top[ga.K - 1].f : 0ull;
   const uint64_t th = had_threshold ? ga.top[ga.K - 1].h : 0ull;
+  // Elites (copies of the first n_el entries) are no candidates: while their entry is in the
+  // list they are skipped as duplicates, and an entry evicted by a better candidate fails the
+  // same overlap test as its copy would, so leaving them out changes nothing.
+  const int n_el = ctl->gen < 0 ? 0 : min(ga.E, n0);
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
   int hits = 0, live = 0, lsum = 0;
   for (int s = tid; s < ga.P; s += stride) {
@@ -762,7 +797,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
     hits += ah + (dup ? 1 : 0);
     live += !dead;
     lsum += dead ? 0 : L;
-    if (!dead && f > 0ull && (!had_threshold || key_before(f, h, tf, th))) {
+    if (s >= n_el && !dead && f > 0ull && (!had_threshold || key_before(f, h, tf, th))) {
       if (single) {  // at most P <= sort_cap candidates
         const int q = atomicAdd(&s_nc, 1);
         sm.sf[q] = f;
@@ -776,18 +811,6 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
       }
     }
   }
-  // generation g-1's live keys join the tabu list; its duplicate table is cleared for g+1
-  uint64_t *pk = ga.dkeys[par ^ 1];
-  uint32_t *ps = ga.dslot[par ^ 1];
-  unsigned long long added = 0ull;
-  for (int i = tid; i <= (int)ga.dmask; i += stride) {
-    const uint64_t k = pk[i];
-    if (k) {
-      added += tabu_insert(ga.tabu, ga.tmask, k) ? 1ull : 0ull;
-      pk[i] = 0ull;
-      ps[i] = 0u;
-    }
-  }
   hits = __reduce_add_sync(kFull, hits);
   live = __reduce_add_sync(kFull, live);
   lsum = __reduce_add_sync(kFull, lsum);
@@ -796,7 +819,6 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
     if (live) atomicAdd(&s_live, live);
     if (lsum) atomicAdd(&s_lsum, lsum);
   }
-  if (added) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->tabu_count), added);
   __syncthreads();
   int hits_g, live_g, nc;
   long long len_g;
@@ -832,6 +854,21 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
       ctl->stopped = 1;
       ctl->n_evaluated += live_g;          // the generation was evaluated, then discarded
       ctl->sum_len += len_g;
+    }
+    return;
+  }
+  if (nc == 0) {  // no candidate ranks before the list's last entry: the list stays as it is
+    if (threadIdx.x == 0) {
+      ctl->hits_last = hits_g;
+      ctl->gen += 1;
+      ctl->n_evaluated += live_g;
+      ctl->sum_len += len_g;
+      ctl->len_cur = 0;
+      ctl->hits_cur = 0;
+      ctl->live_cur = 0;
+      ctl->n_cand = 0;
+      ctl->done = 0;
+      *ga.work = 0;
     }
     return;
   }
@@ -1048,8 +1085,15 @@ GenArgs gen_args(ebic_ctx *ctx, GenState *g) {
   return ga;
 }
 
-EvalArgs gen_eval_args(ebic_ctx *ctx, GenState *g) {
+EvalArgs gen_eval_args(ebic_ctx *ctx, GenState *g, int k) {
   EvalArgs a{};
+  // generation g-1's live keys (duplicate table k ^ 1) join the hashed tabu list meanwhile
+  a.mv_keys = g->dkeys[k ^ 1].as<uint64_t>();
+  a.mv_slots = g->dslot[k ^ 1].as<uint32_t>();
+  a.mv_n = g->dcap;
+  a.mv_table = g->tabu.as<uint64_t>();
+  a.mv_tmask = g->tcap - 1;
+  a.mv_count = reinterpret_cast<unsigned long long *>(&g->ctl.as<GenCtl>()->tabu_count);
   a.keys = ctx->keys.as<uint32_t>();
   a.bitmap = ctx->bitmap_ok ? ctx->bitmap.as<uint32_t>() : nullptr;
   a.R = ctx->R;
@@ -1082,6 +1126,24 @@ PopView gen_view(GenState *g, int k) {
   v.dslot = g->dslot[k].as<uint32_t>();
   v.dmask = g->dcap - 1;
   return v;
+}
+
+// Launch with programmatic stream serialisation: the kernel may be scheduled while the previous
+// kernel of the stream drains; it waits (griddepcontrol.wait) before reading that kernel's results.
+template <class... Args>
+cudaError_t launch_pdl(void (*kern)(Args...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 // Event marks between the kernels of one generation: 0 before k_evolve, 1 before the evaluation,
@@ -1124,12 +1186,13 @@ cudaError_t find_mark_nodes(cudaGraph_t graph, const cudaEvent_t ev[4], cudaGrap
 cudaError_t launch_scoring(ebic_ctx *ctx, GenState *g, int k, cudaStream_t s, Marks *m) {
   cudaError_t e;
   if ((e = mark(s, m, 1)) != cudaSuccess) return e;
-  if ((e = launch_eval_kernel(g->eval_mode, gen_eval_args(ctx, g), gen_view(g, k), ctx->num_sms,
-                              s)) != cudaSuccess)
+  if ((e = launch_eval_kernel(g->eval_mode, gen_eval_args(ctx, g, k), gen_view(g, k),
+                              ctx->num_sms, s, true)) != cudaSuccess)
     return e;
   if ((e = mark(s, m, 2)) != cudaSuccess) return e;
-  k_finish<<<g->finish_blocks, kTopThreads, g->top_smem, s>>>(gen_args(ctx, g), g->buf(k), k);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_pdl(k_finish, dim3(g->finish_blocks), dim3(kTopThreads), g->top_smem, s,
+                      gen_args(ctx, g), g->buf(k), k)) != cudaSuccess)
+    return e;
   return mark(s, m, 3);
 }
 
@@ -1138,9 +1201,10 @@ cudaError_t launch_generation(ebic_ctx *ctx, GenState *g, int parity, cudaStream
   while (G < g->p.max_attempts) G <<= 1;
   cudaError_t e = mark(s, m, 0);
   if (e != cudaSuccess) return e;
-  k_evolve<<<(unsigned)g->P, G * 32, 0, s>>>(gen_args(ctx, g), g->buf(parity ^ 1),
-                                            g->buf(parity), parity);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_pdl(k_evolve, dim3((unsigned)g->P), dim3(G * 32),
+                      (size_t)G * kEvolveWarpInts * 4, s, gen_args(ctx, g), g->buf(parity ^ 1),
+                      g->buf(parity), parity)) != cudaSuccess)
+    return e;
   return launch_scoring(ctx, g, parity, s, m);
 }
 
@@ -1242,6 +1306,8 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
                 (size_t)kChunk * (kS + 4) * 4 + (size_t)(g->K + 1) + 16;
   EBIC_CHECK_CUDA(ctx, cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)g->top_smem));
+  EBIC_CHECK_CUDA(ctx, cudaFuncSetAttribute(k_evolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kMaxAttemptWarps * kEvolveWarpInts * 4));
 
   // enough blocks to spread the slot and table loops, few enough to be co-resident quickly
   const int64_t work = std::max<int64_t>(g->P, g->dcap);

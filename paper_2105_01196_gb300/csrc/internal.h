@@ -78,6 +78,15 @@ struct EvalArgs {
   int32_t *work;            // dynamic work counter (zeroed first)
   int32_t seg_passes;       // passes (of 128 words or 128 rows) per work item
   int32_t n_seg;            // segments per individual
+  // Optional side task of the generation loop, done by the launch's threads before their
+  // evaluation work: the keys of table mv_keys (mv_n slots, cleared afterwards, slot words
+  // mv_slots) join the hashed tabu list mv_table; new keys are counted in *mv_count.
+  uint64_t *mv_keys;
+  uint32_t *mv_slots;
+  uint32_t mv_n;
+  uint64_t *mv_table;
+  uint32_t mv_tmask;
+  unsigned long long *mv_count;
 };
 
 // Kernel statistics (ebic_profile_*): launches counted always, event pairs while enabled.
@@ -160,8 +169,10 @@ cudaError_t launch_eval(int mode, const EvalArgs &a, const PopView &pv, int num_
 cudaError_t launch_eval_plain(const EvalArgs &a, const int32_t *d_cols, int32_t L, int32_t i,
                               cudaStream_t s);
 // The evaluation kernel alone (outputs and a.work must be zero): work split, grid, launch.
+// With pdl, the launch may overlap the tail of the previous kernel in the stream (programmatic
+// dependent launch); the kernel waits for that kernel's results before reading them.
 cudaError_t launch_eval_kernel(int mode, const EvalArgs &a, const PopView &pv, int num_sms,
-                               cudaStream_t s);
+                               cudaStream_t s, bool pdl = false);
 cudaError_t launch_fitness(const EvalArgs &a, const PopView &pv, cudaStream_t s);
 int choose_mode(const ebic_ctx *ctx, int requested, int64_t n_ind, double mean_len,
                 int expected_sweeps);
