@@ -274,6 +274,80 @@ EBIC_API int ebic_profile_enable(ebic_ctx *ctx, int32_t on);
 EBIC_API int ebic_profile_read(ebic_ctx *ctx, int32_t kernel, ebic_kernel_stats *out);
 
 /*
+ * Autotuner (no counterpart in the paper; the paper's kernel has a single form).  Measures, with
+ * CUDA events, one evaluation sweep of the population (CSR as in ebic_eval_population, host or
+ * device) in the direct form and, when the pair bitmap fits in half of the free device memory,
+ * in the bitmap form (building it), each for several work-item sizes.  It then records for the
+ * loaded matrix the form and sizes minimising build + expected_sweeps * sweep time;
+ * EBIC_MODE_AUTO follows them in ebic_eval_population and ebic_run_generations until another
+ * matrix is loaded.  Results never depend on the choice.  *rep (may be NULL) receives the
+ * measurements.  Errors: EBIC_ESTATE (no matrix), EBIC_EINVAL (bad population or parameter,
+ * n_ind < 1, expected_sweeps < 1), EBIC_ENOMEM, EBIC_ECUDA.
+ */
+typedef struct ebic_tune_report {
+  int32_t mode;       /* chosen form: EBIC_MODE_DIRECT or EBIC_MODE_BITMAP                  */
+  int32_t seg_direct; /* chosen work-item size of the direct form, passes of 128 rows (0 = default split) */
+  int32_t seg_bitmap; /* the same for the bitmap form, passes of 128 words                  */
+  int32_t reserved;
+  double direct_ms;   /* best measured sweep of the direct form                               */
+  double bitmap_ms;   /* best measured sweep of the bitmap form (-1 when not measured)        */
+  double build_ms;    /* measured bitmap build (0 when the bitmap already existed)            */
+} ebic_tune_report;
+
+EBIC_API int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *offsets,
+                           int32_t n_ind, const ebic_params *p, int32_t expected_sweeps,
+                           ebic_tune_report *rep);
+
+/*
+ * Job server: continuous batching of independent EBIC runs on one GPU (no counterpart in the
+ * paper, which runs one job at a time).  Jobs are admitted in arrival order, a later job that
+ * fits going ahead of a head job that does not, while the admitted jobs' device-memory
+ * footprints (ebic_job_footprint) stay within hbm_budget_bytes and at most max_running (1..64)
+ * jobs run.  Every admitted job runs on its own worker thread, context and stream; kernels of
+ * different jobs overlap on the device, and each job's results are the same as when it runs alone.
+ *   ebic_server_submit copies the matrix (host or device memory; layout EBIC_LAYOUT_*) and queues
+ *     the job (initialisation + n_gen generations, as ebic_run_generations); *job_id receives its
+ *     id.  EBIC_ENOMEM: its footprint exceeds the whole budget.  EBIC_ESTATE: server stopping.
+ *   ebic_server_wait waits up to timeout_ms (< 0: no limit; EBIC_ETIMEOUT when it expires) for the
+ *     job, fills *res and, when capacity >= n_top, the top list (layout of ebic_get_toplist), and
+ *     forgets the job.  res->status is the job's own status code.
+ *   ebic_server_destroy lets running and admitted jobs finish and drops the queued ones.
+ * ebic_job_footprint: device bytes one job holds at most (matrix keys, staging, the pair bitmap
+ * when the cost model picks it, population, tabu list, tables), or -1 for bad arguments.
+ */
+typedef struct ebic_server ebic_server;
+
+typedef struct ebic_job_result {
+  int64_t job_id;
+  int32_t status;      /* EBIC_OK or the job's error code                                    */
+  int32_t gens_done;   /* as ebic_run_report                                                 */
+  int32_t stopped;
+  int32_t n_top;
+  int64_t n_evaluated;
+  int32_t eval_mode;   /* the evaluation form the job used                                   */
+  int32_t reserved;
+  int64_t footprint_bytes;
+  double queued_ms;    /* submission to admission                                            */
+  double run_ms;       /* admission to completion                                            */
+} ebic_job_result;
+
+EBIC_API int64_t ebic_job_footprint(int64_t rows, int32_t cols, const ebic_params *p,
+                                    int32_t n_gen);
+EBIC_API int ebic_server_create(ebic_server **out, int32_t device, int64_t hbm_budget_bytes,
+                                int32_t max_running);
+EBIC_API int ebic_server_destroy(ebic_server *srv);
+EBIC_API int ebic_server_submit(ebic_server *srv, const float *x, int64_t rows, int32_t cols,
+                                int32_t layout, const ebic_params *p, int32_t n_gen,
+                                int64_t *job_id);
+EBIC_API int ebic_server_wait(ebic_server *srv, int64_t job_id, int32_t timeout_ms,
+                              ebic_job_result *res, int32_t capacity, int32_t *top_cols,
+                              int32_t *top_lens, uint64_t *top_fit, uint64_t *top_keys,
+                              int32_t *top_rows);
+/* Queue length, running jobs and reserved device bytes at this moment. */
+EBIC_API int ebic_server_stats(ebic_server *srv, int32_t *queued, int32_t *running,
+                               int64_t *reserved);
+
+/*
  * Population evaluation that allocates no memory.  The paper has no counterpart: this entry
  * point exists for callers that cannot let a library allocate GPU memory.  One case is a
  * serving process whose framework has already reserved the device memory in its own pool, so

@@ -31,7 +31,8 @@ def sources():
 
 def compile_one(src, verbose):
     obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
+           "-pthread",
            "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr",
            "-I", os.path.join(HERE, "..", "include"), "-c", src, "-o", obj]
     if verbose:
@@ -52,7 +53,7 @@ def build(verbose=False):
             sys.stderr.write(err)
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), ARCH, "-shared", "-cudart", "static", "-o", tmp] + objs
+    cmd = [nvcc(), ARCH, "-shared", "-cudart", "static", "-Xcompiler", "-pthread", "-o", tmp] + objs
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")

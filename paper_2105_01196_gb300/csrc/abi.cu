@@ -156,6 +156,77 @@ void prof_collect(ebic_ctx *ctx) {
   ctx->pending.clear();
 }
 
+// Validates a CSR population (on the host for host arrays, on the device for device arrays)
+// and makes it available on the device.  Host arrays are copied into the context's buffers.
+int stage_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *offsets, int32_t n_ind,
+                     bool want_host_offsets, StagedPop *out) {
+  const bool dev_cols = ebic_is_device_ptr(col_idx), dev_off = ebic_is_device_ptr(offsets);
+  if (dev_cols != dev_off)
+    return ebic_fail(ctx, EBIC_EINVAL, "col_idx and offsets must both be host or both device");
+  cudaStream_t s = ctx->stream;
+  const int32_t *d_cols = col_idx, *d_off = offsets;
+  std::vector<int32_t> &h_off = out->h_off;
+  double mean_len = 0.0;
+  int64_t total = 0;
+  if (!dev_cols) {
+    // Host CSR: validate here, then copy.
+    const int64_t base = offsets[0];
+    for (int32_t i = 0; i < n_ind; ++i) {
+      const int64_t L = (int64_t)offsets[i + 1] - offsets[i];
+      if (offsets[i] < 0 || L < 2 || L > EBIC_MAX_LEN)
+        return ebic_fail(ctx, EBIC_EINVAL, "individual " + std::to_string(i) +
+                                               ": length must be in [2, 64]");
+      const int32_t *c = col_idx + offsets[i];
+      for (int64_t k = 0; k < L; ++k) {
+        if (c[k] < 0 || c[k] >= ctx->C)
+          return ebic_fail(ctx, EBIC_EINVAL,
+                           "individual " + std::to_string(i) + ": column out of range");
+        for (int64_t j = 0; j < k; ++j)
+          if (c[j] == c[k])
+            return ebic_fail(ctx, EBIC_EINVAL,
+                             "individual " + std::to_string(i) + ": repeated column");
+      }
+    }
+    total = (int64_t)offsets[n_ind] - base;
+    mean_len = (double)total / n_ind;
+    EBIC_CHECK_CUDA(ctx, ctx->ev_cols.ensure((size_t)(offsets[n_ind]) * 4 + 16));
+    EBIC_CHECK_CUDA(ctx, ctx->ev_off.ensure((size_t)(n_ind + 1) * 4));
+    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(ctx->ev_cols.p, col_idx, (size_t)offsets[n_ind] * 4,
+                                         cudaMemcpyHostToDevice, s));
+    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(ctx->ev_off.p, offsets, (size_t)(n_ind + 1) * 4,
+                                         cudaMemcpyHostToDevice, s));
+    d_cols = ctx->ev_cols.as<int32_t>();
+    d_off = ctx->ev_off.as<int32_t>();
+    if (want_host_offsets) h_off.assign(offsets, offsets + n_ind + 1);
+  } else {
+    // Device CSR: validate on the device before any kernel indexes the matrix with it.
+    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(ctx->d_err.p, 0, sizeof(int32_t), s));
+    EBIC_CHECK_CUDA(ctx, launch_validate_csr(col_idx, offsets, n_ind, ctx->C,
+                                             ctx->d_err.as<int32_t>(), s));
+    prof_count(ctx, -1, 1);
+    int32_t herr = 0;
+    int32_t ends[2] = {0, 0};
+    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&herr, ctx->d_err.p, 4, cudaMemcpyDeviceToHost, s));
+    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&ends[0], offsets, 4, cudaMemcpyDeviceToHost, s));
+    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&ends[1], offsets + n_ind, 4, cudaMemcpyDeviceToHost, s));
+    if (want_host_offsets) {
+      h_off.resize(n_ind + 1);
+      EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(h_off.data(), offsets, (size_t)(n_ind + 1) * 4,
+                                           cudaMemcpyDeviceToHost, s));
+    }
+    EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(s));
+    if (herr) return ebic_fail(ctx, EBIC_EINVAL, "invalid chromosome in the population");
+    total = (int64_t)ends[1] - ends[0];
+    mean_len = (double)total / n_ind;
+  }
+
+  out->d_cols = d_cols;
+  out->d_off = d_off;
+  out->total = total;
+  out->mean_len = mean_len;
+  return EBIC_OK;
+}
+
 extern "C" {
 
 int ebic_profile_enable(ebic_ctx *ctx, int32_t on) {
@@ -287,6 +358,7 @@ int ebic_load_matrix(ebic_ctx *ctx, const float *x, int64_t rows, int32_t cols, 
   EBIC_TRY(check_device_ptr(ctx, x, "x"));
   ctx->have_matrix = false;
   ctx->bitmap_ok = false;
+  ctx->tuned = false;
   gen_state_free(ctx->gen);
   ctx->gen = nullptr;
   const int64_t R_pad = round_up(rows, 128);
@@ -363,66 +435,13 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
   void *outs[4] = {rows_pos, rows_neg, rows_any, fitness};
   for (void *o : outs)
     if (o) EBIC_TRY(check_device_ptr(ctx, o, "output"));
-  const bool dev_cols = ebic_is_device_ptr(col_idx), dev_off = ebic_is_device_ptr(offsets);
-  if (dev_cols != dev_off)
-    return ebic_fail(ctx, EBIC_EINVAL, "col_idx and offsets must both be host or both device");
   cudaStream_t s = ctx->stream;
-
-  const int32_t *d_cols = col_idx, *d_off = offsets;
-  std::vector<int32_t> h_off;
-  double mean_len = 0.0;
-  int64_t total = 0;
-  if (!dev_cols) {
-    // Host CSR: validate here, then copy.
-    const int64_t base = offsets[0];
-    for (int32_t i = 0; i < n_ind; ++i) {
-      const int64_t L = (int64_t)offsets[i + 1] - offsets[i];
-      if (offsets[i] < 0 || L < 2 || L > EBIC_MAX_LEN)
-        return ebic_fail(ctx, EBIC_EINVAL, "individual " + std::to_string(i) +
-                                               ": length must be in [2, 64]");
-      const int32_t *c = col_idx + offsets[i];
-      for (int64_t k = 0; k < L; ++k) {
-        if (c[k] < 0 || c[k] >= ctx->C)
-          return ebic_fail(ctx, EBIC_EINVAL,
-                           "individual " + std::to_string(i) + ": column out of range");
-        for (int64_t j = 0; j < k; ++j)
-          if (c[j] == c[k])
-            return ebic_fail(ctx, EBIC_EINVAL,
-                             "individual " + std::to_string(i) + ": repeated column");
-      }
-    }
-    total = (int64_t)offsets[n_ind] - base;
-    mean_len = (double)total / n_ind;
-    EBIC_CHECK_CUDA(ctx, ctx->ev_cols.ensure((size_t)(offsets[n_ind]) * 4 + 16));
-    EBIC_CHECK_CUDA(ctx, ctx->ev_off.ensure((size_t)(n_ind + 1) * 4));
-    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(ctx->ev_cols.p, col_idx, (size_t)offsets[n_ind] * 4,
-                                         cudaMemcpyHostToDevice, s));
-    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(ctx->ev_off.p, offsets, (size_t)(n_ind + 1) * 4,
-                                         cudaMemcpyHostToDevice, s));
-    d_cols = ctx->ev_cols.as<int32_t>();
-    d_off = ctx->ev_off.as<int32_t>();
-    if (p->mode == EBIC_MODE_PLAIN) h_off.assign(offsets, offsets + n_ind + 1);
-  } else {
-    // Device CSR: validate on the device before any kernel indexes the matrix with it.
-    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(ctx->d_err.p, 0, sizeof(int32_t), s));
-    EBIC_CHECK_CUDA(ctx, launch_validate_csr(col_idx, offsets, n_ind, ctx->C,
-                                             ctx->d_err.as<int32_t>(), s));
-    prof_count(ctx, -1, 1);
-    int32_t herr = 0;
-    int32_t ends[2] = {0, 0};
-    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&herr, ctx->d_err.p, 4, cudaMemcpyDeviceToHost, s));
-    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&ends[0], offsets, 4, cudaMemcpyDeviceToHost, s));
-    EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&ends[1], offsets + n_ind, 4, cudaMemcpyDeviceToHost, s));
-    if (p->mode == EBIC_MODE_PLAIN) {
-      h_off.resize(n_ind + 1);
-      EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(h_off.data(), offsets, (size_t)(n_ind + 1) * 4,
-                                           cudaMemcpyDeviceToHost, s));
-    }
-    EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(s));
-    if (herr) return ebic_fail(ctx, EBIC_EINVAL, "invalid chromosome in the population");
-    total = (int64_t)ends[1] - ends[0];
-    mean_len = (double)total / n_ind;
-  }
+  StagedPop sp;
+  EBIC_TRY(stage_population(ctx, col_idx, offsets, n_ind, p->mode == EBIC_MODE_PLAIN, &sp));
+  const int32_t *d_cols = sp.d_cols, *d_off = sp.d_off;
+  const std::vector<int32_t> &h_off = sp.h_off;
+  const double mean_len = sp.mean_len;
+  const int64_t total = sp.total;
 
   int mode = choose_mode(ctx, p->mode, n_ind, mean_len, 1);
   if (mode == EBIC_MODE_BITMAP && !ctx->bitmap_ok) EBIC_TRY(ebic_build_bitmap(ctx));
@@ -446,6 +465,7 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
   a.rows_any = a.rows_neg + n_ind;
   a.fitness = ctx->ev_fit.as<uint64_t>();
   a.work = ctx->d_work.as<int32_t>();
+  a.seg_passes = ctx->tuned ? (mode == EBIC_MODE_BITMAP ? ctx->seg_bitmap : ctx->seg_direct) : 0;
   PopView pv{};
   pv.cols = d_cols;
   pv.off = d_off;
@@ -494,6 +514,7 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
 int choose_mode(const ebic_ctx *ctx, int requested, int64_t n_ind, double mean_len,
                 int expected_sweeps) {
   if (requested != EBIC_MODE_AUTO) return requested;
+  if (ctx->tuned) return ctx->tuned_mode;
   if (ctx->bitmap_ok) return EBIC_MODE_BITMAP;
   const double Wst = (double)ctx->Wst, C = (double)ctx->C;
   const double bitmap_bytes = C * C * Wst * 4.0;

@@ -442,8 +442,9 @@ cudaError_t launch_eval_kernel(int mode, const EvalArgs &a0, const PopView &pv, 
                                      : (const void *)k_eval_direct<false>);
   const int bps = blocks_per_sm_for(kern);
   const int64_t warps = (int64_t)num_sms * bps * kWarps;
-  // Segments: enough work items for ~8 per resident warp, at most 2^30 items in total.
-  int64_t seg = ((int64_t)pv.n * passes_total) / (8 * warps);
+  // Segments: the autotuner's size when it set one, else enough work items for ~8 per
+  // resident warp; at most 2^30 items in total.
+  int64_t seg = a0.seg_passes > 0 ? a0.seg_passes : ((int64_t)pv.n * passes_total) / (8 * warps);
   if (seg < 1) seg = 1;
   if (seg > passes_total) seg = passes_total;
   int64_t n_seg = (passes_total + seg - 1) / seg;

@@ -34,6 +34,7 @@ constexpr int kS = EBIC_MAX_LEN;  // population slot stride (columns)
 constexpr int kSlotThreads = 64;
 constexpr int kTopThreads = 1024;
 constexpr int kSortSmemMax = 4096;  // most candidates sorted in shared memory
+constexpr size_t kFinishSmemMax = 180 * 1024;  // dynamic shared memory limit set for k_finish
 
 struct TopEntry {
   uint64_t f, h;
@@ -1110,6 +1111,8 @@ EvalArgs gen_eval_args(ebic_ctx *ctx, GenState *g, int k) {
   a.rows_any = a.rows_neg + g->P;
   a.fitness = nullptr;
   a.work = g->work.as<int32_t>();
+  a.seg_passes =
+      ctx->tuned ? (g->eval_mode == EBIC_MODE_BITMAP ? ctx->seg_bitmap : ctx->seg_direct) : 0;
   return a;
 }
 
@@ -1304,8 +1307,15 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
   g->top_smem = (size_t)(g->K + 1) * sizeof(TopEntry) + (size_t)g->sort_cap * 16 +
                 (size_t)cw * 4 + (size_t)g->sort_cap * 4 + (size_t)(g->K + 1) * 8 +
                 (size_t)kChunk * (kS + 4) * 4 + (size_t)(g->K + 1) + 16;
+  // One fixed upper bound for every context (contexts on other threads set the same value, so no
+  // context can lower another's limit): K = 256, 65,535 columns, the largest sort buffer.
+  static_assert((size_t)(EBIC_MAX_BICLUSTERS + 1) * sizeof(TopEntry) + kSortSmemMax * 20 +
+                        2048 * 4 + (EBIC_MAX_BICLUSTERS + 1) * 9 + kChunk * (kS + 4) * 4 + 16 <=
+                    kFinishSmemMax,
+                "k_finish shared memory bound");
+  if (g->top_smem > kFinishSmemMax) return ebic_fail(ctx, EBIC_EINVAL, "top-list workspace too large");
   EBIC_CHECK_CUDA(ctx, cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)g->top_smem));
+                                            (int)kFinishSmemMax));
   EBIC_CHECK_CUDA(ctx, cudaFuncSetAttribute(k_evolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             kMaxAttemptWarps * kEvolveWarpInts * 4));
 

@@ -119,6 +119,11 @@ struct ebic_ctx {
   // scratch for single evaluations
   DevBuf d_err, d_work, ev_cols, ev_off, ev_out, ev_fit;
 
+  // autotuner decisions for the loaded matrix (tune.cu)
+  bool tuned = false;
+  int tuned_mode = EBIC_MODE_DIRECT;
+  int seg_direct = 0, seg_bitmap = 0;  // work-item sizes in passes; 0 = the built-in split
+
   // generation loop state (evolve.cu)
   struct GenState *gen = nullptr;
 
@@ -146,6 +151,16 @@ int ebic_fail(ebic_ctx *ctx, int code, const std::string &msg);
 int ebic_fail_cuda(ebic_ctx *ctx, cudaError_t e, const char *what, const char *file, int line);
 
 bool ebic_is_device_ptr(const void *p);
+
+// A validated population on the device (abi.cu).
+struct StagedPop {
+  const int32_t *d_cols = nullptr, *d_off = nullptr;
+  std::vector<int32_t> h_off;  // host copy of the offsets when requested
+  int64_t total = 0;           // sum of lengths
+  double mean_len = 0.0;
+};
+int stage_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *offsets, int32_t n_ind,
+                     bool want_host_offsets, StagedPop *out);
 
 // params helpers (abi.cu)
 int ebic_check_eval_params(ebic_ctx *ctx, const ebic_params *p);

@@ -1,0 +1,160 @@
+// Autotuner: measures the evaluation kernels on a representative population of the loaded matrix
+// and records, for this matrix, the evaluation form (direct comparison or pair bitmap) and the
+// work-item size (passes of 128 rows or 128 words per item) that minimise the expected time of
+// `expected_sweeps` evaluations, the bitmap build included when the bitmap does not exist yet.
+// EBIC_MODE_AUTO then follows the recorded choice, both in ebic_eval_population and in the
+// generation loop, until another matrix is loaded.
+#include <float.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+const int kSegCandidates[] = {0, 1, 2, 4, 8, 16, 32};  // 0 = the built-in split
+const int kReps = 3;
+
+// Minimum over kReps of one evaluation sweep (kernel only, CUDA events on the context stream).
+int time_eval(ebic_ctx *ctx, int mode, EvalArgs a, const PopView &pv, int seg, double *ms_out) {
+  cudaEvent_t e0, e1;
+  EBIC_CHECK_CUDA(ctx, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return ebic_fail(ctx, EBIC_ECUDA, "cudaEventCreate failed");
+  }
+  a.seg_passes = seg;
+  double best = DBL_MAX;
+  int status = EBIC_OK;
+  for (int r = 0; r < kReps && status == EBIC_OK; ++r) {
+    cudaError_t e = launch_eval(mode, a, pv, ctx->num_sms, ctx->stream, e0, e1);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      status = ebic_fail_cuda(ctx, e, "autotune sweep", __FILE__, __LINE__);
+      break;
+    }
+    prof_count(ctx, EBIC_KERNEL_EVAL, 1);
+    prof_count(ctx, -1, 1);
+    best = std::min(best, (double)ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = best;
+  return status;
+}
+
+}  // namespace
+
+extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *offsets,
+                             int32_t n_ind, const ebic_params *p, int32_t expected_sweeps,
+                             ebic_tune_report *rep) {
+  if (!ctx) return EBIC_EINVAL;
+  if (!ctx->have_matrix) return ebic_fail(ctx, EBIC_ESTATE, "no matrix loaded");
+  EBIC_TRY(ebic_check_eval_params(ctx, p));
+  if (n_ind < 1 || n_ind > (1 << 24) || expected_sweeps < 1)
+    return ebic_fail(ctx, EBIC_EINVAL, "need 1 <= n_ind <= 2^24 and expected_sweeps >= 1");
+  if (!col_idx || !offsets) return ebic_fail(ctx, EBIC_EINVAL, "col_idx/offsets NULL");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  struct Restore {
+    int d;
+    ~Restore() {
+      if (d >= 0) cudaSetDevice(d);
+    }
+  } restore{prev};
+  StagedPop sp;
+  EBIC_TRY(stage_population(ctx, col_idx, offsets, n_ind, false, &sp));
+  EBIC_CHECK_CUDA(ctx, ctx->ev_out.ensure((size_t)n_ind * 3 * sizeof(int32_t)));
+  EBIC_CHECK_CUDA(ctx, ctx->ev_fit.ensure((size_t)n_ind * sizeof(uint64_t)));
+  EvalArgs a{};
+  a.keys = ctx->keys.as<uint32_t>();
+  a.R = ctx->R;
+  a.R_pad = ctx->R_pad;
+  a.Wst = ctx->Wst;
+  a.C = ctx->C;
+  a.neg = p->neg_trends;
+  a.rnum = p->ratio_num;
+  a.rden = p->ratio_den;
+  a.min_rows = p->min_rows;
+  a.col_cap = p->col_cap;
+  a.rows_pos = ctx->ev_out.as<int32_t>();
+  a.rows_neg = a.rows_pos + n_ind;
+  a.rows_any = a.rows_neg + n_ind;
+  a.fitness = ctx->ev_fit.as<uint64_t>();
+  a.work = ctx->d_work.as<int32_t>();
+  PopView pv{};
+  pv.cols = sp.d_cols;
+  pv.off = sp.d_off;
+  pv.n = n_ind;
+
+  ebic_tune_report r{};
+  const int64_t passes_direct = ctx->R_pad / 128, passes_bitmap = (ctx->Wst + 127) / 128;
+  double best_direct = DBL_MAX, best_bitmap = DBL_MAX;
+  int seg_direct = 0, seg_bitmap = 0;
+  for (int seg : kSegCandidates) {
+    if (seg > passes_direct) break;
+    double ms = 0;
+    EBIC_TRY(time_eval(ctx, EBIC_MODE_DIRECT, a, pv, seg, &ms));
+    if (ms < best_direct) {
+      best_direct = ms;
+      seg_direct = seg;
+    }
+  }
+  // the bitmap form, when its C^2 * R / 8 bytes fit comfortably
+  double build_ms = 0.0;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    free_b = 0;
+  }
+  const bool had_bitmap = ctx->bitmap_ok;
+  if (had_bitmap || (double)ebic_bitmap_bytes(ctx->R, ctx->C) < 0.5 * (double)free_b) {
+    if (!had_bitmap) {
+      cudaEvent_t e0, e1;
+      EBIC_CHECK_CUDA(ctx, cudaEventCreate(&e0));
+      EBIC_CHECK_CUDA(ctx, cudaEventCreate(&e1));
+      EBIC_CHECK_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+      const int st = ebic_build_bitmap(ctx);
+      cudaEventRecord(e1, ctx->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (st != EBIC_OK) return st;
+      build_ms = ms;
+    }
+    a.bitmap = ctx->bitmap.as<uint32_t>();
+    for (int seg : kSegCandidates) {
+      if (seg > passes_bitmap) break;
+      double ms = 0;
+      EBIC_TRY(time_eval(ctx, EBIC_MODE_BITMAP, a, pv, seg, &ms));
+      if (ms < best_bitmap) {
+        best_bitmap = ms;
+        seg_bitmap = seg;
+      }
+    }
+  }
+  const double cost_direct = (double)expected_sweeps * best_direct;
+  const double cost_bitmap = best_bitmap == DBL_MAX
+                                 ? DBL_MAX
+                                 : build_ms + (double)expected_sweeps * best_bitmap;
+  ctx->tuned = true;
+  ctx->tuned_mode = cost_bitmap < cost_direct ? EBIC_MODE_BITMAP : EBIC_MODE_DIRECT;
+  ctx->seg_direct = seg_direct;
+  ctx->seg_bitmap = seg_bitmap;
+  if (rep) {
+    r.mode = ctx->tuned_mode;
+    r.seg_direct = seg_direct;
+    r.seg_bitmap = seg_bitmap;
+    r.direct_ms = best_direct;
+    r.bitmap_ms = best_bitmap == DBL_MAX ? -1.0 : best_bitmap;
+    r.build_ms = build_ms;
+    *rep = r;
+  }
+  return EBIC_OK;
+}

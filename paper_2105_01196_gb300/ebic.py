@@ -97,6 +97,13 @@ SIGNATURES = {
     "ebic_load_state": (ctypes.c_int, [_VP, _VP, _VP, _I64]),
     "ebic_profile_enable": (ctypes.c_int, [_VP, _I32]),
     "ebic_profile_read": (ctypes.c_int, [_VP, _I32, _VP]),
+    "ebic_autotune": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP, _I32, _VP]),
+    "ebic_job_footprint": (ctypes.c_int64, [_I64, _I32, _VP, _I32]),
+    "ebic_server_create": (ctypes.c_int, [_VP, _I32, _I64, _I32]),
+    "ebic_server_destroy": (ctypes.c_int, [_VP]),
+    "ebic_server_submit": (ctypes.c_int, [_VP, _VP, _I64, _I32, _I32, _VP, _I32, _VP]),
+    "ebic_server_wait": (ctypes.c_int, [_VP, _I64, _I32, _VP, _I32, _VP, _VP, _VP, _VP, _VP]),
+    "ebic_server_stats": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "ebic_eval_population_noalloc": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _I32, _VP, _VP,
                                                     _VP, _VP, _VP, _I32, _VP, _VP, _I32]),
 }
@@ -304,6 +311,112 @@ def ebic_profile_read(ctx, kernel):
     return st.as_dict()
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("seg_direct", ctypes.c_int32),
+                ("seg_bitmap", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("direct_ms", ctypes.c_double), ("bitmap_ms", ctypes.c_double),
+                ("build_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
+def ebic_autotune(ctx, col_idx, offsets, params, expected_sweeps=1):
+    col_idx = _as_dtype(col_idx, np.int32, "int32")
+    offsets = _as_dtype(offsets, np.int32, "int32")
+    n = (offsets.numel() if _is_torch(offsets) else offsets.size) - 1
+    rep = TuneReport()
+    _check(ctx, _lib.ebic_autotune(ctx, ptr(col_idx), ptr(offsets), int(n), ctypes.byref(params),
+                                   int(expected_sweeps), ctypes.byref(rep)))
+    return rep.as_dict()
+
+
+class JobResult(ctypes.Structure):
+    _fields_ = [("job_id", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("gens_done", ctypes.c_int32), ("stopped", ctypes.c_int32),
+                ("n_top", ctypes.c_int32), ("n_evaluated", ctypes.c_int64),
+                ("eval_mode", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("footprint_bytes", ctypes.c_int64), ("queued_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
+def ebic_job_footprint(rows, cols, params, n_gen):
+    return int(_lib.ebic_job_footprint(int(rows), int(cols), ctypes.byref(params), int(n_gen)))
+
+
+def ebic_server_create(device=0, hbm_budget_bytes=16 << 30, max_running=8):
+    out = ctypes.c_void_p()
+    _check(None, _lib.ebic_server_create(ctypes.byref(out), int(device), int(hbm_budget_bytes),
+                                         int(max_running)))
+    return out.value
+
+
+def ebic_server_destroy(srv):
+    return _lib.ebic_server_destroy(srv)
+
+
+def ebic_server_submit(srv, x, params, n_gen, layout=ROW_MAJOR):
+    x = _as_dtype(x, np.float32, "float32")
+    rows, cols = x.shape if layout == ROW_MAJOR else x.shape[::-1]
+    jid = ctypes.c_int64()
+    _check(None, _lib.ebic_server_submit(srv, ptr(x), int(rows), int(cols), int(layout),
+                                         ctypes.byref(params), int(n_gen), ctypes.byref(jid)))
+    return jid.value
+
+
+def ebic_server_wait(srv, job_id, timeout_ms=-1, capacity=256):
+    res = JobResult()
+    cols = np.zeros((capacity, MAX_LEN), np.int32)
+    lens = np.zeros(capacity, np.int32)
+    fit = np.zeros(capacity, np.uint64)
+    keys = np.zeros(capacity, np.uint64)
+    rows = np.zeros((capacity, 3), np.int32)
+    _check(None, _lib.ebic_server_wait(srv, int(job_id), int(timeout_ms), ctypes.byref(res),
+                                       capacity, ptr(cols), ptr(lens), ptr(fit), ptr(keys),
+                                       ptr(rows)))
+    out = res.as_dict()
+    out["top"] = [dict(cols=tuple(int(c) for c in cols[e, :lens[e]]), f=int(fit[e]),
+                       h=int(keys[e]), rows_pos=int(rows[e, 0]), rows_neg=int(rows[e, 1]),
+                       rows_any=int(rows[e, 2])) for e in range(res.n_top)]
+    return out
+
+
+def ebic_server_stats(srv):
+    q, r, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(None, _lib.ebic_server_stats(srv, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b)))
+    return {"queued": q.value, "running": r.value, "reserved": b.value}
+
+
+class Server:
+    """Continuous-batching job server on one GPU (see ebic_server_create)."""
+
+    def __init__(self, device=0, hbm_budget_bytes=16 << 30, max_running=8):
+        self.handle = ebic_server_create(device, hbm_budget_bytes, max_running)
+
+    def submit(self, x, params, n_gen, layout=ROW_MAJOR):
+        return ebic_server_submit(self.handle, x, params, n_gen, layout)
+
+    def wait(self, job_id, timeout_ms=-1):
+        return ebic_server_wait(self.handle, job_id, timeout_ms)
+
+    def stats(self):
+        return ebic_server_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            ebic_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 NOALLOC_MAX_IND = 65536
 
 
@@ -381,6 +494,9 @@ class Context:
 
     def last_error(self):
         return ebic_last_error(self.handle)
+
+    def autotune(self, col_idx, offsets, params, expected_sweeps=1):
+        return ebic_autotune(self.handle, col_idx, offsets, params, expected_sweeps)
 
     def profile_enable(self, on=True):
         ebic_profile_enable(self.handle, on)

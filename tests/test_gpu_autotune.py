@@ -1,0 +1,47 @@
+"""The autotuner's choices never change results: after tuning, EBIC_MODE_AUTO evaluations and
+generations equal the oracle's."""
+
+import numpy as np
+import pytest
+
+from oracle import counts as ocounts
+from oracle import ebic as oebic
+from oracle.params import Params as OParams
+from paper_2105_01196_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("sweeps", [1, 101])
+def test_autotune_then_auto_matches_oracle(sweeps):
+    from paper_2105_01196_gb300 import ebic
+    w = synth.WORKLOADS["default"]
+    x, _, ci, off = synth.workload_inputs(w)
+    p = ebic.Params.make(neg_trends=1, ratio_num=85, ratio_den=100, mode=ebic.MODE_AUTO)
+    op = OParams(neg_trends=1, ratio_num=85, ratio_den=100, min_rows=p.min_rows, col_cap=p.col_cap)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        rep = ctx.autotune(ci, off, p, sweeps)
+        assert rep["mode"] in (ebic.MODE_DIRECT, ebic.MODE_BITMAP)
+        assert rep["direct_ms"] > 0 and rep["seg_direct"] >= 0 and rep["seg_bitmap"] >= 0
+        got = ctx.eval_population(ci, off, p)
+    want = ocounts.eval_population(x, ci, off, op)
+    for g_, w_ in zip(got, want):
+        assert np.array_equal(np.asarray(g_, np.int64), np.asarray(w_, np.int64))
+
+
+def test_autotuned_generations_match_oracle():
+    from paper_2105_01196_gb300 import ebic
+    x, _, ci, off = synth.workload_inputs(synth.WORKLOADS["tiny"])
+    base = dict(neg_trends=1, ratio_num=85, ratio_den=100, max_len=6, init_min_len=2,
+                init_max_len=6, pop_size=64, elite=4, n_biclusters=4, tabu_hit_limit=0, seed=13)
+    gp = ebic.Params.make(mode=ebic.MODE_AUTO, **base)
+    op = OParams(**base)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        ctx.autotune(ci, off, gp, 20)
+        rep = ctx.run_generations(gp, 20)
+        top = ctx.toplist()
+    st = oebic.run(x, op, 20)
+    assert rep.gens_done == st.gen
+    assert [(e["cols"], e["f"]) for e in top] == [(tuple(e.cols), e.f) for e in st.top]
