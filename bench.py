@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--jobs", type=int, default=0, help="serving: number of jobs (0 = 256)")
+    ap.add_argument("--max-running", type=int, default=8, help="serving: concurrent jobs")
     return ap.parse_args()
 
 
@@ -173,11 +175,69 @@ def run_reference(args, w, world, rank, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, world, rank, local, dist):
+    """Serving workload: a Poisson stream of EBIC jobs through the continuous-batching server;
+    p50/p99 job latency (arrival to completion) and jobs/s, plus the saturated throughput with
+    every job queued at once."""
+    import threading
+    import torch
+    from paper_2105_01196_gb300 import ebic, synth
+    torch.cuda.set_device(local)
+    cfg = synth.SERVING
+    n_jobs = args.jobs if args.jobs else cfg["n_jobs"]
+    jobs, mats = synth.serving_jobs(n_jobs, seed=cfg["seed"] + 7919 * rank)
+
+    def params(seed):
+        return ebic.Params.make(neg_trends=1, ratio_num=cfg["ratio"][0], ratio_den=cfg["ratio"][1],
+                                pop_size=cfg["pop"], max_len=20, init_min_len=2, init_max_len=20,
+                                n_biclusters=10, elite=10, tabu_hit_limit=0, seed=seed)
+    free, total = torch.cuda.mem_get_info(local)
+    budget = int(0.6 * free)
+    out = {}
+    for phase in ("poisson", "saturated"):
+        lat = []
+        evals = 0
+        with ebic.Server(local, hbm_budget_bytes=budget, max_running=args.max_running) as srv:
+            t0 = time.perf_counter()
+            ids = []
+            for at, m, seed in jobs:
+                if phase == "poisson":
+                    delay = t0 + at - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                ids.append((time.perf_counter(), srv.submit(mats[m], params(seed), cfg["generations"]), m))
+            for t_sub, jid, m in ids:
+                r = srv.wait(jid)
+                assert r["status"] == 0, r
+                lat.append(r["queued_ms"] + r["run_ms"])
+                evals += r["n_evaluated"] * mats[m].shape[0]
+            wall = time.perf_counter() - t0
+        out[phase] = {"jobs_per_s": len(jobs) / wall, "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)), "wall_s": wall,
+                      "evals_per_s": evals / wall}
+    if rank == 0:
+        line = {"metric": "EBIC jobs/sec and p50/p99 job latency (continuous batching)",
+                "value": out["saturated"]["jobs_per_s"], "unit": "jobs/s", "n_gpus": world,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32-compare/int32", "data": "synthetic",
+                "config": {"workload": "serving", "jobs": len(jobs), "rate_per_s": cfg["rate_per_s"],
+                           "rows": list(cfg["rows"]), "cols": list(cfg["cols"]), "pop": cfg["pop"],
+                           "generations": cfg["generations"], "distinct_matrices": len(mats),
+                           "max_running": args.max_running, "hbm_budget_bytes": budget},
+                "poisson": out["poisson"], "saturated": out["saturated"]}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local, dist = dist_setup(args)
     from paper_2105_01196_gb300 import synth
     import dataclasses
+    if args.workload == "serving":
+        run_serving(args, world, rank, local, dist)
+        if dist:
+            dist.destroy_process_group()
+        return
     w = dataclasses.replace(synth.WORKLOADS[args.workload])
     if args.impl == "reference":
         run_reference(args, w, world, rank, dist)

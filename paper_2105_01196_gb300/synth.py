@@ -56,6 +56,37 @@ WORKLOADS = {
 }
 
 
+# The job stream of the serving workload: 256 jobs, Poisson arrivals at 20 jobs/s, matrices of
+# 1,000-50,000 rows x 20-500 columns with 3-10 planted biclusters, population 800, ratio 0.85,
+# 50 generations.
+SERVING = dict(n_jobs=256, rate_per_s=20.0, rows=(1_000, 50_000), cols=(20, 500), n_bic=(3, 10),
+               pop=800, ratio=(85, 100), generations=50, seed=SEED_BASE + 4)
+
+
+def serving_jobs(n_jobs=None, n_matrices=16, seed=None):
+    """Arrival times (s) and (matrix index, run seed) of the serving stream, and its matrices.
+
+    Generating a new 50,000 x 500 matrix per job would take longer than the arrivals leave, so
+    the stream draws its jobs' matrices from `n_matrices` pre-generated ones of random shape; each
+    job has its own EBIC seed."""
+    cfg = SERVING
+    n_jobs = cfg["n_jobs"] if n_jobs is None else n_jobs
+    g = rng(cfg["seed"] if seed is None else seed)
+    mats = []
+    for m in range(n_matrices):
+        R = int(g.integers(cfg["rows"][0], cfg["rows"][1] + 1))
+        C = int(g.integers(cfg["cols"][0], cfg["cols"][1] + 1))
+        nb = int(g.integers(cfg["n_bic"][0], cfg["n_bic"][1] + 1))
+        x, _ = planted_matrix(R, C, nb, (max(10, R // 100), max(20, R // 20)),
+                              (4, min(20, C // 2)), seed=int(g.integers(1 << 31)))
+        mats.append(x)
+    gaps = g.exponential(1.0 / cfg["rate_per_s"], size=n_jobs)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    jobs = [(float(arrivals[k]), int(g.integers(n_matrices)), int(g.integers(1 << 31)))
+            for k in range(n_jobs)]
+    return jobs, mats
+
+
 def rng(seed):
     return np.random.Generator(np.random.Philox(int(seed)))
 
