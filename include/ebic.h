@@ -53,6 +53,8 @@ extern "C" {
 #define EBIC_MODE_DIRECT 1 /* direct comparison of the matrix's order keys                     */
 #define EBIC_MODE_BITMAP 2 /* column-pair comparison bitmap (built on first use)               */
 #define EBIC_MODE_PLAIN 3  /* one kernel launch per individual (reference GPU form)            */
+#define EBIC_MODE_STAGED 4 /* direct comparison over TMA-staged row tiles in shared memory;
+                              the direct form is used where the tile does not fit (> 1536 columns) */
 
 #define EBIC_LAYOUT_ROW_MAJOR 0 /* x[r * cols + c] */
 #define EBIC_LAYOUT_COL_MAJOR 1 /* x[c * rows + r] */
@@ -244,12 +246,15 @@ EBIC_API int ebic_load_state(ebic_ctx *ctx, const ebic_params *p, const void *bl
  * nodes re-pointed at fresh events before each replay), and it counts every kernel it launches.
  *   kernel  EBIC_KERNEL_EVAL (direct or bitmap evaluation, single sweeps and generations),
  *           EBIC_KERNEL_BITMAP_BUILD, EBIC_KERNEL_EVOLVE (children of one generation),
- *           EBIC_KERNEL_FINISH (scoring, tabu list and top-list update of one generation), or
- *           EBIC_KERNEL_ALL (launch count only).
+ *           EBIC_KERNEL_FINISH (scoring, tabu list and top-list update of one generation),
+ *           EBIC_KERNEL_RANK_CODES (per-row rank codes, built by ebic_load_matrix when cols
+ *           <= 1,024), or EBIC_KERNEL_ALL (launch count only).
  *   ms         summed event time of the timed launches;
  *   alg_bytes  algorithmic bytes of those launches: the bitmap form reads sum_i (L_i - 1) pair
- *              words per 32 rows and direction, the direct form gathers sum_i L_i keys per row,
- *              the build writes cols^2 words per 32 rows;
+ *              words per 32 rows and direction, the direct form gathers sum_i L_i codes (1 or 2
+ *              bytes; keys, 4 bytes, when cols > 1,024 and in the staged form) per row, the
+ *              build writes cols^2 words per 32 rows, the rank-code kernel reads the keys and
+ *              writes the codes;
  *   alg_ops    algorithmic comparisons: sum_i (L_i - 1) * rows per direction;
  *   units      (individual, row) evaluations.
  * ebic_profile_enable(ctx, 1) resets the counters; 0 stops recording.
@@ -259,7 +264,8 @@ EBIC_API int ebic_load_state(ebic_ctx *ctx, const ebic_params *p, const void *bl
 #define EBIC_KERNEL_ALL 2
 #define EBIC_KERNEL_EVOLVE 3
 #define EBIC_KERNEL_FINISH 4
-#define EBIC_KERNEL_COUNT 5
+#define EBIC_KERNEL_RANK_CODES 5
+#define EBIC_KERNEL_COUNT 6
 
 typedef struct ebic_kernel_stats {
   int64_t launches;
@@ -276,8 +282,9 @@ EBIC_API int ebic_profile_read(ebic_ctx *ctx, int32_t kernel, ebic_kernel_stats 
 /*
  * Autotuner (no counterpart in the paper; the paper's kernel has a single form).  Measures, with
  * CUDA events, one evaluation sweep of the population (CSR as in ebic_eval_population, host or
- * device) in the direct form and, when the pair bitmap fits in half of the free device memory,
- * in the bitmap form (building it), each for several work-item sizes.  It then records for the
+ * device) in the direct form (several work-item sizes), the staged direct form (when its tiles
+ * fit) and, when the pair bitmap fits in half of the free device memory, the bitmap form
+ * (building it; several work-item sizes).  It then records for the
  * loaded matrix the form and sizes minimising build + expected_sweeps * sweep time;
  * EBIC_MODE_AUTO follows them in ebic_eval_population and ebic_run_generations until another
  * matrix is loaded.  Results never depend on the choice.  *rep (may be NULL) receives the
@@ -285,13 +292,14 @@ EBIC_API int ebic_profile_read(ebic_ctx *ctx, int32_t kernel, ebic_kernel_stats 
  * n_ind < 1, expected_sweeps < 1), EBIC_ENOMEM, EBIC_ECUDA.
  */
 typedef struct ebic_tune_report {
-  int32_t mode;       /* chosen form: EBIC_MODE_DIRECT or EBIC_MODE_BITMAP                  */
+  int32_t mode;       /* chosen form: EBIC_MODE_DIRECT, EBIC_MODE_STAGED or EBIC_MODE_BITMAP */
   int32_t seg_direct; /* chosen work-item size of the direct form, passes of 128 rows (0 = default split) */
   int32_t seg_bitmap; /* the same for the bitmap form, passes of 128 words                  */
   int32_t reserved;
   double direct_ms;   /* best measured sweep of the direct form                               */
   double bitmap_ms;   /* best measured sweep of the bitmap form (-1 when not measured)        */
   double build_ms;    /* measured bitmap build (0 when the bitmap already existed)            */
+  double staged_ms;   /* best measured sweep of the staged direct form (-1 when not measured) */
 } ebic_tune_report;
 
 EBIC_API int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *offsets,

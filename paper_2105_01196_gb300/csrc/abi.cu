@@ -74,7 +74,7 @@ int ebic_check_eval_params(ebic_ctx *ctx, const ebic_params *p) {
     return ebic_fail(ctx, EBIC_EINVAL, "neg_trends must be 0 or 1");
   if (p->col_cap < 0 || p->col_cap > 16 || p->min_rows < 0)
     return ebic_fail(ctx, EBIC_EINVAL, "need 0 <= col_cap <= 16 and min_rows >= 0");
-  if (p->mode < EBIC_MODE_AUTO || p->mode > EBIC_MODE_PLAIN)
+  if (p->mode < EBIC_MODE_AUTO || p->mode > EBIC_MODE_STAGED)
     return ebic_fail(ctx, EBIC_EINVAL, "unknown mode");
   return EBIC_OK;
 }
@@ -313,7 +313,9 @@ int ebic_create(ebic_ctx **out, int32_t device, void *cuda_stream) {
     }
     ctx->own_stream = true;
   }
-  if (ctx->d_err.ensure(64) != cudaSuccess || ctx->d_work.ensure(64) != cudaSuccess) {
+  if (ctx->d_err.ensure(64) != cudaSuccess || ctx->d_work.ensure(64) != cudaSuccess ||
+      ctx->d_kerr.ensure(64) != cudaSuccess ||
+      cudaMemset(ctx->d_kerr.p, 0, 64) != cudaSuccess) {
     ebic_destroy(ctx);
     return EBIC_ENOMEM;
   }
@@ -329,7 +331,7 @@ int ebic_destroy(ebic_ctx *ctx) {
   gen_state_free(ctx->gen);
   ctx->gen = nullptr;
   DevBuf *bufs[] = {&ctx->keys, &ctx->bitmap, &ctx->stage_x, &ctx->d_err, &ctx->d_work,
-                    &ctx->ev_cols, &ctx->ev_off, &ctx->ev_out, &ctx->ev_fit};
+                    &ctx->ev_cols, &ctx->ev_off, &ctx->ev_out, &ctx->ev_fit, &ctx->d_kerr};
   for (DevBuf *b : bufs) b->release();
   prof_collect(ctx);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -383,6 +385,24 @@ int ebic_load_matrix(ebic_ctx *ctx, const float *x, int64_t rows, int32_t cols, 
   ctx->C = cols;
   ctx->R_pad = R_pad;
   ctx->Wst = R_pad / 32;
+  direct_tma_prepare(&ctx->dtma, ctx->keys.as<uint32_t>(), R_pad, cols);
+  // per-row rank codes for the direct form (C <= 1,024)
+  ctx->code_bytes = code_bytes_for(cols);
+  ctx->code_stride = 0;
+  if (ctx->code_bytes) {
+    const int64_t S = code_stride_for(rows, ctx->code_bytes);
+    EBIC_CHECK_CUDA(ctx, ctx->codes.ensure((size_t)cols * S * ctx->code_bytes));
+    cudaEvent_t ev = prof_begin(ctx);
+    EBIC_CHECK_CUDA(ctx, launch_rank_codes(ctx->keys.as<uint32_t>(), R_pad, cols, ctx->codes.p,
+                                           ctx->code_bytes, S, ctx->num_sms, ctx->stream));
+    prof_end(ctx, ev, EBIC_KERNEL_RANK_CODES,
+             (double)cols * R_pad * 4.0 + (double)cols * S * ctx->code_bytes,
+             (double)cols * cols * (double)R_pad, (double)R_pad);
+    prof_count(ctx, EBIC_KERNEL_RANK_CODES, 1);
+    EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    prof_collect(ctx);
+    ctx->code_stride = S;
+  }
   ctx->have_matrix = true;
   ctx->err.clear();
   return EBIC_OK;
@@ -448,13 +468,7 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
 
   EBIC_CHECK_CUDA(ctx, ctx->ev_out.ensure((size_t)n_ind * 3 * sizeof(int32_t)));
   EBIC_CHECK_CUDA(ctx, ctx->ev_fit.ensure((size_t)n_ind * sizeof(uint64_t)));
-  EvalArgs a{};
-  a.keys = ctx->keys.as<uint32_t>();
-  a.bitmap = ctx->bitmap_ok ? ctx->bitmap.as<uint32_t>() : nullptr;
-  a.R = ctx->R;
-  a.R_pad = ctx->R_pad;
-  a.Wst = ctx->Wst;
-  a.C = ctx->C;
+  EvalArgs a = eval_args_for(ctx);
   a.neg = p->neg_trends;
   a.rnum = p->ratio_num;
   a.rden = p->ratio_den;
@@ -465,15 +479,16 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
   a.rows_any = a.rows_neg + n_ind;
   a.fitness = ctx->ev_fit.as<uint64_t>();
   a.work = ctx->d_work.as<int32_t>();
-  a.seg_passes = ctx->tuned ? (mode == EBIC_MODE_BITMAP ? ctx->seg_bitmap : ctx->seg_direct) : 0;
+  a.seg_passes = ctx->tuned ? (mode == EBIC_MODE_BITMAP ? ctx->seg_bitmap
+                                                      : (mode == EBIC_MODE_DIRECT ? ctx->seg_direct : 0))
+                            : 0;
   PopView pv{};
   pv.cols = d_cols;
   pv.off = d_off;
   pv.n = n_ind;
 
   const double pairs = (double)(total - n_ind), nd = a.neg ? 2.0 : 1.0;
-  const double ev_bytes = (mode == EBIC_MODE_BITMAP) ? pairs * (double)ctx->Wst * 4.0 * nd
-                                                     : (double)total * (double)ctx->R_pad * 4.0;
+  const double ev_bytes = eval_bytes(ctx, mode, total, n_ind, a.neg);
   const double ev_ops = pairs * (double)ctx->R * nd, ev_units = (double)n_ind * (double)ctx->R;
   if (mode == EBIC_MODE_PLAIN) {
     EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(a.rows_pos, 0, (size_t)n_ind * 3 * 4, s));
@@ -500,8 +515,14 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
   if (fitness)
     EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(fitness, a.fitness, (size_t)n_ind * 8,
                                          cudaMemcpyDefault, s));
+  int32_t kerr = 0;
+  EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&kerr, ctx->d_kerr.p, 4, cudaMemcpyDeviceToHost, s));
   EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(s));
   prof_collect(ctx);
+  if (kerr) {
+    cudaMemset(ctx->d_kerr.p, 0, 4);
+    return ebic_fail(ctx, EBIC_ETIMEOUT, "a bounded device wait expired in the evaluation");
+  }
   return EBIC_OK;
 }
 
@@ -511,6 +532,39 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
 // autotuner when it has measured this matrix.  The bitmap costs a one-off build of C^2 * Wst
 // words and then (L-1) * Wst words per individual and direction; the direct form gathers
 // L * R_pad keys per individual.
+EvalArgs eval_args_for(const ebic_ctx *ctx) {
+  EvalArgs a{};
+  a.keys = ctx->keys.as<uint32_t>();
+  a.bitmap = ctx->bitmap_ok ? ctx->bitmap.as<uint32_t>() : nullptr;
+  a.R = ctx->R;
+  a.R_pad = ctx->R_pad;
+  a.Wst = ctx->Wst;
+  a.C = ctx->C;
+  a.err = ctx->d_kerr.as<int32_t>();
+  a.dtma = ctx->dtma.ok ? &ctx->dtma : nullptr;
+  a.codes = ctx->code_bytes ? ctx->codes.as<uint8_t>() : nullptr;
+  a.code_bytes = ctx->code_bytes;
+  a.S = ctx->code_stride;
+  return a;
+}
+
+int64_t eval_passes(const ebic_ctx *ctx, int mode) {
+  if (mode == EBIC_MODE_BITMAP) return (ctx->Wst + 127) / 128;
+  if (ctx->code_bytes) return ctx->code_stride / code_rows_per_pass(ctx->code_bytes);
+  return ctx->R_pad / 128;
+}
+
+double eval_bytes(const ebic_ctx *ctx, int mode, int64_t total_len, int64_t n_ind, int neg) {
+  // algorithmic bytes of one sweep: the pair words (bitmap), else one code or key per row and
+  // chromosome column (the staged form reads each tile of keys once per group of individuals;
+  // its algorithmic gathers are counted like the key form's)
+  if (mode == EBIC_MODE_BITMAP)
+    return (double)(total_len - n_ind) * (double)ctx->Wst * 4.0 * (neg ? 2.0 : 1.0);
+  if (mode == EBIC_MODE_DIRECT && ctx->code_bytes)
+    return (double)total_len * (double)ctx->code_stride * ctx->code_bytes;
+  return (double)total_len * (double)ctx->R_pad * 4.0;
+}
+
 int choose_mode(const ebic_ctx *ctx, int requested, int64_t n_ind, double mean_len,
                 int expected_sweeps) {
   if (requested != EBIC_MODE_AUTO) return requested;
@@ -524,9 +578,11 @@ int choose_mode(const ebic_ctx *ctx, int requested, int64_t n_ind, double mean_l
     free_b = 0;
   }
   if (bitmap_bytes > 0.5 * (double)free_b) return EBIC_MODE_DIRECT;
-  // Relative per-unit costs (direct key gathers are ~4x cheaper per byte than a bitmap build
-  // word, bitmap eval words stream from HBM): time in units of one 32-bit access.
-  const double direct = (double)n_ind * mean_len * (double)ctx->R_pad / 4.0;
+  // Relative per-unit costs (direct gathers are ~4x cheaper per byte than a bitmap build word,
+  // bitmap eval words stream from HBM): time in units of one 32-bit access.  Codes of W bytes
+  // read W bytes per row and column, keys four.
+  const double row_bytes = ctx->code_bytes ? (double)ctx->code_bytes : 4.0;
+  const double direct = (double)n_ind * mean_len * (double)ctx->R_pad * row_bytes / 16.0;
   const double build = C * C * Wst * 4.0;
   const double eval_bm = (double)n_ind * (mean_len - 1.0) * Wst * 2.0;
   return (build + expected_sweeps * eval_bm < expected_sweeps * direct) ? EBIC_MODE_BITMAP

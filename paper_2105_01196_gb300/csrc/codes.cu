@@ -1,0 +1,288 @@
+// Per-row rank codes and the direct-comparison evaluation over them (the trend counts of
+// Sec. 2.3 / Sec. 2.4 steps 2-3, as in eval.cu).
+//
+// Every comparison the trend counts make is between two entries of the same row.  Replacing the
+// entry of row r, column c by its rank within the row,
+//   code(r, c) = #{k : key(r, k) < key(r, c)},
+// preserves each such comparison exactly: key(r, a) > key(r, b) implies that every k counted
+// for b is also counted for a, and so is b itself, hence code(r, a) > code(r, b); equal keys
+// count the same set.  Codes lie in [0, C-1], so for C <= 128 they fit in 7 bits of a byte and
+// for C <= 1,024 in 15 bits of a 16-bit half-word (column-major [C][S], rows padded to one pass
+// of the kernel with code 0, which never forms a trend).
+//
+// The evaluation kernel then reads one byte (or two) per row and column instead of four, and
+// compares 4 (or 2) rows per 32-bit word with SIMD-within-a-register arithmetic: with the top bit
+// of each field free,
+//   ((cur | H) - (prev + ONE)) & H  has the top bit of a field set exactly where cur > prev
+// (no field borrows: every field difference stays in [0, 2^b - 1]).  Per-row counts (at most
+// 63) accumulate in the fields, and a field's count is >= t exactly where
+// (count + 2^(b-1) - t) has its top bit set.
+#include <algorithm>
+#include <mutex>
+
+#include "internal.h"
+#include "tables.cuh"
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kRankRows = 32;                        // rows per rank-code tile
+constexpr size_t kRankSmemMax = 1024 * kRankRows * 4;  // C <= 1,024
+constexpr int kMaxDevices = 64;
+constexpr int kVec = 1;  // 16-byte loads per lane and column in one pass
+
+__device__ __forceinline__ int threshold(int L, int num, int den) {
+  return (num * (L - 1) + den - 1) / den;
+}
+
+__device__ __forceinline__ void wait_prior_grid() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// ------------------------------------------------------------------------------- rank codes
+
+// A block ranks 32 rows at a time: the rows' keys of every column are staged in shared memory
+// as [C][32] (lane = row, so a warp's loads are conflict-free), and each thread ranks four
+// columns of its row per sweep over the C keys.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_rank_codes(const uint32_t *__restrict__ keys,
+                                                         int64_t R_pad, int32_t C, int64_t S,
+                                                         T *__restrict__ codes) {
+  extern __shared__ uint32_t s_k[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n_tiles = R_pad / kRankRows;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t r0 = tile * kRankRows;
+    __syncthreads();  // the previous tile's keys are no longer read
+    for (int c = warp; c < C; c += kWarps) s_k[c * kRankRows + lane] = keys[(int64_t)c * R_pad + r0 + lane];
+    __syncthreads();
+    for (int c0 = warp; c0 < C; c0 += 4 * kWarps) {
+      uint32_t x[4];
+      int n[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = c0 + j * kWarps;
+        x[j] = c < C ? s_k[c * kRankRows + lane] : 0u;
+      }
+#pragma unroll 4
+      for (int k = 0; k < C; ++k) {
+        const uint32_t v = s_k[k * kRankRows + lane];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) n[j] += v < x[j];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = c0 + j * kWarps;
+        if (c < C) codes[(int64_t)c * S + r0 + lane] = (T)n[j];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------- evaluation
+
+// W = bytes per code.  A pass covers 32 lanes x kVec 16-byte loads (16 / W rows each) per column.
+template <int W, bool NEG>
+__global__ void __launch_bounds__(kThreads) k_eval_codes(EvalArgs a, PopView pv) {
+  constexpr uint32_t H = W == 1 ? 0x80808080u : 0x80008000u;    // top bit of every field
+  constexpr uint32_t ONE = W == 1 ? 0x01010101u : 0x00010001u;  // 1 in every field
+  constexpr int SH = W == 1 ? 7 : 15;
+  constexpr int kRowsPerPass = 32 * 16 * kVec / W;
+  constexpr int NW = 4 * kVec;  // 32-bit words per lane
+  __shared__ int64_t s_base[kWarps][EBIC_MAX_LEN];
+  wait_prior_grid();
+  if (pv.stop && *pv.stop) return;
+  // the generation loop's side task: the previous generation's keys join the tabu list
+  if (a.mv_keys) move_table_keys(a.mv_keys, a.mv_slots, a.mv_n, a.mv_table, a.mv_tmask, a.mv_count);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t passes_total = a.S / kRowsPerPass;
+  const int32_t n_items = pv.n * a.n_seg;
+  // Items are taken segment-major (all individuals of a row segment before the next segment),
+  // so the codes of the segment stay in L2 while every individual reads them.  (Fetching the
+  // next item's index ahead of the current item's work measured slower.)
+  for (;;) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(a.work, 1);
+    q = __shfl_sync(kFull, q, 0);
+    if (q >= n_items) break;
+    const int seg = q / pv.n, i = q - seg * pv.n;
+    int L = 0;
+    bool live = !(pv.dead && pv.dead[i]);
+    if (live && pv.dkeys) live = !dedup_is_dup(pv.dkeys, pv.dslot, pv.dmask, pv.hash[i], i);
+    const int st = live ? (pv.off ? pv.off[i] : i * pv.stride) : 0;
+    if (live) L = pv.off ? pv.off[i + 1] - st : pv.len[i];
+    if (L >= 2) {
+      __syncwarp();
+      for (int k = lane; k < L; k += 32) s_base[warp][k] = (int64_t)pv.cols[st + k] * a.S * W;
+      __syncwarp();
+      const int t = threshold(L, a.rnum, a.rden);
+      const uint32_t tadd = (uint32_t)((1 << SH) - t) * ONE;
+      const int64_t p0 = (int64_t)seg * a.seg_passes;
+      const int64_t p1 = min(p0 + a.seg_passes, passes_total);
+      int cp = 0, cn = 0, ca = 0;
+      for (int64_t pass = p0; pass < p1; ++pass) {
+        // lane's 16-byte chunks: lane + 32 v for v < kVec (each warp load is contiguous)
+        const uint8_t *base = a.codes + pass * (kRowsPerPass * W) + lane * 16;
+        uint32_t pH[NW], p1w[NW], inc[NW], dec[NW];
+#pragma unroll
+        for (int v = 0; v < kVec; ++v) {
+          const uint4 v0 = __ldg(reinterpret_cast<const uint4 *>(base + v * 512 + s_base[warp][0]));
+          const uint32_t w0[4] = {v0.x, v0.y, v0.z, v0.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            pH[4 * v + j] = w0[j] | H;
+            p1w[4 * v + j] = w0[j] + ONE;
+            inc[4 * v + j] = 0u;
+            dec[4 * v + j] = 0u;
+          }
+        }
+#pragma unroll 8
+        for (int k = 1; k < L; ++k) {
+          uint32_t cur[NW];
+#pragma unroll
+          for (int v = 0; v < kVec; ++v) {
+            const uint4 x = __ldg(reinterpret_cast<const uint4 *>(base + v * 512 + s_base[warp][k]));
+            cur[4 * v] = x.x;
+            cur[4 * v + 1] = x.y;
+            cur[4 * v + 2] = x.z;
+            cur[4 * v + 3] = x.w;
+          }
+#pragma unroll
+          for (int j = 0; j < NW; ++j) {
+            const uint32_t cH = cur[j] | H, c1 = cur[j] + ONE;
+            inc[j] += ((cH - p1w[j]) & H) >> SH;
+            if (NEG) dec[j] += ((pH[j] - c1) & H) >> SH;
+            pH[j] = cH;
+            p1w[j] = c1;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NW; ++j) {
+          const uint32_t po = (inc[j] + tadd) & H;
+          const uint32_t ne = NEG ? ((dec[j] + tadd) & H) : 0u;
+          cp += __popc(po);
+          if (NEG) {
+            cn += __popc(ne);
+            ca += __popc(po | ne);
+          }
+        }
+      }
+      if (!NEG) ca = cp;
+      cp = __reduce_add_sync(kFull, cp);
+      cn = __reduce_add_sync(kFull, cn);
+      ca = __reduce_add_sync(kFull, ca);
+      if (lane == 0) {
+        if (cp) atomicAdd(a.rows_pos + i, cp);
+        if (cn) atomicAdd(a.rows_neg + i, cn);
+        if (ca) atomicAdd(a.rows_any + i, ca);
+      }
+    }
+  }
+}
+
+template <class K>
+int blocks_per_sm(K kern, size_t smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  return nb < 1 ? 1 : nb;
+}
+
+template <class... Args>
+cudaError_t launch_pdl_opt(void (*kern)(Args...), dim3 grid, dim3 block, cudaStream_t s,
+                           bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+}  // namespace
+
+int code_bytes_for(int32_t C) { return C <= 128 ? 1 : (C <= 1024 ? 2 : 0); }
+
+int64_t code_rows_per_pass(int code_bytes) { return 32 * 16 * kVec / code_bytes; }
+
+int64_t code_stride_for(int64_t R, int code_bytes) {
+  const int64_t q = code_rows_per_pass(code_bytes);
+  return (R + q - 1) / q * q;
+}
+
+cudaError_t launch_rank_codes(const uint32_t *keys, int64_t R_pad, int32_t C, void *codes,
+                              int code_bytes, int64_t S, int num_sms, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(codes, 0, (size_t)C * S * code_bytes, s);
+  if (e != cudaSuccess) return e;
+  const size_t smem = (size_t)C * kRankRows * 4;
+  if (smem > kRankSmemMax) return cudaErrorInvalidValue;
+  // one fixed limit for every context (no call lowers another's), set once per device
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  static std::mutex mu;
+  static bool attr_set[kMaxDevices] = {};
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
+      if ((e = cudaFuncSetAttribute(k_rank_codes<uint8_t>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kRankSmemMax)) != cudaSuccess)
+        return e;
+      if ((e = cudaFuncSetAttribute(k_rank_codes<uint16_t>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kRankSmemMax)) != cudaSuccess)
+        return e;
+      attr_set[dev] = true;
+    }
+  }
+  const int64_t n_tiles = R_pad / kRankRows;
+  if (code_bytes == 1) {
+    const int64_t grid = std::min<int64_t>(n_tiles, (int64_t)num_sms * blocks_per_sm(k_rank_codes<uint8_t>, smem));
+    k_rank_codes<uint8_t><<<(unsigned)grid, kThreads, smem, s>>>(keys, R_pad, C, S,
+                                                                 static_cast<uint8_t *>(codes));
+  } else {
+    const int64_t grid = std::min<int64_t>(n_tiles, (int64_t)num_sms * blocks_per_sm(k_rank_codes<uint16_t>, smem));
+    k_rank_codes<uint16_t><<<(unsigned)grid, kThreads, smem, s>>>(keys, R_pad, C, S,
+                                                                  static_cast<uint16_t *>(codes));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval_codes(const EvalArgs &a0, const PopView &pv, int num_sms, cudaStream_t s,
+                              bool pdl) {
+  if (pv.n <= 0) return cudaSuccess;
+  EvalArgs a = a0;
+  const int W = a.code_bytes;
+  const int64_t passes_total = a.S / code_rows_per_pass(W);
+  void (*kern)(EvalArgs, PopView) =
+      W == 1 ? (a.neg ? k_eval_codes<1, true> : k_eval_codes<1, false>)
+             : (a.neg ? k_eval_codes<2, true> : k_eval_codes<2, false>);
+  const int bps = blocks_per_sm(kern, 0);
+  const int64_t warps = (int64_t)num_sms * bps * kWarps;
+  // Segments: the autotuner's size when it set one, else enough work items for ~8 per
+  // resident warp; at most 2^30 items in total.
+  int64_t seg = a0.seg_passes > 0 ? a0.seg_passes : ((int64_t)pv.n * passes_total) / (8 * warps);
+  if (seg < 1) seg = 1;
+  if (seg > passes_total) seg = passes_total;
+  int64_t n_seg = (passes_total + seg - 1) / seg;
+  while ((int64_t)pv.n * n_seg > (1LL << 30)) {
+    seg *= 2;
+    n_seg = (passes_total + seg - 1) / seg;
+  }
+  a.seg_passes = (int32_t)seg;
+  a.n_seg = (int32_t)n_seg;
+  const int64_t items = (int64_t)pv.n * n_seg;
+  int64_t grid = (int64_t)num_sms * bps;
+  const int64_t need = (items + kWarps - 1) / kWarps;
+  if (grid > need) grid = need;
+  return launch_pdl_opt(kern, dim3((unsigned)grid), dim3(kThreads), s, pdl, a, pv);
+}

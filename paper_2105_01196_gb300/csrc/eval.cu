@@ -8,11 +8,14 @@
 //
 // Three forms compute the same counts:
 //   direct  keys gathered per row (4 rows per lane, 16-byte loads of the column-major keys);
+//           with up to 1,024 columns the per-row rank codes of codes.cu stand in for the keys;
 //   bitmap  32 rows per word from the pair bitmap: an AND of the L-1 pair words for the exact
 //           trend, a bit-sliced carry-save counter compared with t(L) for approximate trends;
 //   plain   one kernel launch per individual, one row per thread (the reference GPU form).
 // The direct and bitmap kernels are persistent: warps pull (individual, row segment) work items
-// from an atomic counter and add their partial counts with one atomic per item.
+// from an atomic counter, segment-major (every individual of a row segment before the next
+// segment, so the segment's data stays in L2 while all individuals read it), and add their
+// partial counts with one atomic per item.
 #include "internal.h"
 #include "tables.cuh"
 
@@ -41,23 +44,19 @@ __device__ __forceinline__ bool pv_dead(const PopView &v, int i) {
 }
 
 // The generation loop's side task (see EvalArgs): move a duplicate table into the tabu list.
-__device__ __noinline__ void move_keys(const EvalArgs &a) {
-  if (!a.mv_keys) return;
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  unsigned long long added = 0ull;
-  for (uint32_t i = tid; i < a.mv_n; i += stride) {
-    const uint64_t k = a.mv_keys[i];
-    if (k) {
-      added += tabu_insert(a.mv_table, a.mv_tmask, k) ? 1ull : 0ull;
-      a.mv_keys[i] = 0ull;
-      a.mv_slots[i] = 0u;
-    }
-  }
-  if (added) atomicAdd(a.mv_count, added);
+__device__ __forceinline__ void move_keys(const EvalArgs &a) {
+  if (a.mv_keys) move_table_keys(a.mv_keys, a.mv_slots, a.mv_n, a.mv_table, a.mv_tmask, a.mv_count);
 }
 
 // Waits for the preceding kernel of a programmatic launch (no-op otherwise).
 __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Next work item of a warp (lane 0 takes it from the counter).
+__device__ __forceinline__ int next_item(int32_t *work, int lane) {
+  int q = 0;
+  if (lane == 0) q = atomicAdd(work, 1);
+  return __shfl_sync(kFull, q, 0);
+}
 
 __device__ __forceinline__ uint4 ldg4(const uint32_t *p) {
   return __ldg(reinterpret_cast<const uint4 *>(p));
@@ -93,11 +92,9 @@ __global__ void __launch_bounds__(kThreads) k_eval_direct(EvalArgs a, PopView pv
   const int64_t passes_total = a.R_pad / 128;
   const int32_t n_items = pv.n * a.n_seg;
   for (;;) {
-    int q = 0;
-    if (lane == 0) q = atomicAdd(a.work, 1);
-    q = __shfl_sync(kFull, q, 0);
+    const int q = next_item(a.work, lane);
     if (q >= n_items) break;
-    const int i = q / a.n_seg, seg = q - i * a.n_seg;
+    const int seg = q / pv.n, i = q - seg * pv.n;  // segment-major
     if (pv_dead(pv, i)) continue;
     const int L = pv_len(pv, i), st = pv_start(pv, i);
     if (L < 2) continue;
@@ -229,11 +226,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
   const int32_t n_items = pv.n * a.n_seg;
   const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
   for (;;) {
-    int q = 0;
-    if (lane == 0) q = atomicAdd(a.work, 1);
-    q = __shfl_sync(kFull, q, 0);
+    const int q = next_item(a.work, lane);
     if (q >= n_items) break;
-    const int i = q / a.n_seg, seg = q - i * a.n_seg;
+    const int seg = q / pv.n, i = q - seg * pv.n;  // segment-major
     if (pv_dead(pv, i)) continue;
     const int L = pv_len(pv, i), st = pv_start(pv, i);
     if (L < 2) continue;
@@ -433,6 +428,11 @@ cudaError_t launch_maybe_pdl(void (*kern)(Args...), dim3 grid, dim3 block, size_
 cudaError_t launch_eval_kernel(int mode, const EvalArgs &a0, const PopView &pv, int num_sms,
                                cudaStream_t s, bool pdl) {
   if (pv.n <= 0) return cudaSuccess;
+  if (mode == EBIC_MODE_STAGED) {
+    if (a0.dtma && a0.dtma->ok) return launch_eval_direct_tma(*a0.dtma, a0, pv, num_sms, s, pdl);
+    mode = EBIC_MODE_DIRECT;  // the tile does not fit in shared memory
+  }
+  if (mode == EBIC_MODE_DIRECT && a0.codes) return launch_eval_codes(a0, pv, num_sms, s, pdl);
   EvalArgs a = a0;
   const bool bitmap = (mode == EBIC_MODE_BITMAP);
   const int64_t passes_total = bitmap ? (a.Wst + 127) / 128 : a.R_pad / 128;

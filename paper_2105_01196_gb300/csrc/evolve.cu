@@ -1087,7 +1087,7 @@ GenArgs gen_args(ebic_ctx *ctx, GenState *g) {
 }
 
 EvalArgs gen_eval_args(ebic_ctx *ctx, GenState *g, int k) {
-  EvalArgs a{};
+  EvalArgs a = eval_args_for(ctx);
   // generation g-1's live keys (duplicate table k ^ 1) join the hashed tabu list meanwhile
   a.mv_keys = g->dkeys[k ^ 1].as<uint64_t>();
   a.mv_slots = g->dslot[k ^ 1].as<uint32_t>();
@@ -1095,12 +1095,6 @@ EvalArgs gen_eval_args(ebic_ctx *ctx, GenState *g, int k) {
   a.mv_table = g->tabu.as<uint64_t>();
   a.mv_tmask = g->tcap - 1;
   a.mv_count = reinterpret_cast<unsigned long long *>(&g->ctl.as<GenCtl>()->tabu_count);
-  a.keys = ctx->keys.as<uint32_t>();
-  a.bitmap = ctx->bitmap_ok ? ctx->bitmap.as<uint32_t>() : nullptr;
-  a.R = ctx->R;
-  a.R_pad = ctx->R_pad;
-  a.Wst = ctx->Wst;
-  a.C = ctx->C;
   a.neg = g->p.neg_trends;
   a.rnum = g->p.ratio_num;
   a.rden = g->p.ratio_den;
@@ -1111,8 +1105,10 @@ EvalArgs gen_eval_args(ebic_ctx *ctx, GenState *g, int k) {
   a.rows_any = a.rows_neg + g->P;
   a.fitness = nullptr;
   a.work = g->work.as<int32_t>();
-  a.seg_passes =
-      ctx->tuned ? (g->eval_mode == EBIC_MODE_BITMAP ? ctx->seg_bitmap : ctx->seg_direct) : 0;
+  a.seg_passes = ctx->tuned ? (g->eval_mode == EBIC_MODE_BITMAP
+                                    ? ctx->seg_bitmap
+                                    : (g->eval_mode == EBIC_MODE_DIRECT ? ctx->seg_direct : 0))
+                             : 0;
   return a;
 }
 
@@ -1248,7 +1244,8 @@ int check_run_params(ebic_ctx *ctx, const ebic_params *p) {
   if (p->tournament < 1 || p->tournament > 16 || p->max_attempts < 1 || p->max_attempts > 16)
     return ebic_fail(ctx, EBIC_EINVAL, "tournament and max_attempts must be in [1, 16]");
   if (p->mode == EBIC_MODE_PLAIN)
-    return ebic_fail(ctx, EBIC_EINVAL, "the generation loop evaluates with DIRECT or BITMAP");
+    return ebic_fail(ctx, EBIC_EINVAL,
+                     "the generation loop evaluates with the DIRECT, STAGED or BITMAP form");
   return EBIC_OK;
 }
 
@@ -1483,14 +1480,19 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
     }
   }
   EBIC_TRY(read_ctl(ctx, g, &c));
+  int32_t kerr = 0;
+  EBIC_CHECK_CUDA(ctx, cudaMemcpy(&kerr, ctx->d_kerr.p, 4, cudaMemcpyDeviceToHost));
+  if (kerr) {
+    cudaMemset(ctx->d_kerr.p, 0, 4);
+    return ebic_fail(ctx, EBIC_ETIMEOUT, "a bounded device wait expired in the generation loop");
+  }
   if (ctx->prof) {
     // algorithmic work of the evaluations run by this call (live slots only)
     const double dlen = (double)(c.sum_len - c_start.sum_len);
     const double dlive = (double)(c.n_evaluated - c_start.n_evaluated);
     const double nd = g->p.neg_trends ? 2.0 : 1.0;
     KStats &k = ctx->kst[EBIC_KERNEL_EVAL];
-    k.bytes += g->eval_mode == EBIC_MODE_BITMAP ? (dlen - dlive) * (double)ctx->Wst * 4.0 * nd
-                                                : dlen * (double)ctx->R_pad * 4.0;
+    k.bytes += eval_bytes(ctx, g->eval_mode, (int64_t)dlen, (int64_t)dlive, g->p.neg_trends);
     k.ops += (dlen - dlive) * (double)ctx->R * nd;
     k.units += dlive * (double)ctx->R;
     prof_collect(ctx);

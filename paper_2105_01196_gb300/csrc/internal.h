@@ -87,7 +87,34 @@ struct EvalArgs {
   uint64_t *mv_table;
   uint32_t mv_tmask;
   unsigned long long *mv_count;
+  int32_t *err;                   // kernels OR error bits in (4: a bounded wait expired)
+  const struct DirectTma *dtma;   // host-side: staged direct form, when prepared
+  const uint8_t *codes;           // [C][S] per-row rank codes (codes.cu), or nullptr
+  int32_t code_bytes;             // bytes per code: 1 or 2 (0: the direct form reads keys)
+  int64_t S;                      // rows per code column (a multiple of one pass)
 };
+
+// Per-row rank codes (codes.cu): code width for C columns (1 for C <= 128, 2 for C <= 1024,
+// else 0 = none), rows per pass of the code kernel, padded rows per code column, the rank
+// kernel (zero-fills the padding) and the direct evaluation over codes.
+int code_bytes_for(int32_t C);
+int64_t code_rows_per_pass(int code_bytes);
+int64_t code_stride_for(int64_t R, int code_bytes);
+cudaError_t launch_rank_codes(const uint32_t *keys, int64_t R_pad, int32_t C, void *codes,
+                              int code_bytes, int64_t S, int num_sms, cudaStream_t s);
+cudaError_t launch_eval_codes(const EvalArgs &a, const PopView &pv, int num_sms, cudaStream_t s,
+                              bool pdl);
+
+// Tensor map and tile geometry of the TMA-staged direct form (direct_tma.cu).
+struct DirectTma {
+  alignas(64) unsigned char map[128];  // CUtensorMap of the keys [C][R_pad]
+  int TR = 0, CB = 0, nbox = 0, stages = 0;
+  int64_t stage_words = 0;
+  bool ok = false;
+};
+void direct_tma_prepare(DirectTma *d, const uint32_t *keys, int64_t R_pad, int32_t C);
+cudaError_t launch_eval_direct_tma(const DirectTma &d, const EvalArgs &a, const PopView &pv,
+                                   int num_sms, cudaStream_t s, bool pdl);
 
 // Kernel statistics (ebic_profile_*): launches counted always, event pairs while enabled.
 struct KStats {
@@ -119,6 +146,15 @@ struct ebic_ctx {
   // scratch for single evaluations
   DevBuf d_err, d_work, ev_cols, ev_off, ev_out, ev_fit;
 
+  // staged direct form of the loaded matrix, and the kernels' error word
+  DirectTma dtma;
+  DevBuf d_kerr;
+
+  // per-row rank codes of the loaded matrix (code_bytes 0: none)
+  DevBuf codes;
+  int code_bytes = 0;
+  int64_t code_stride = 0;
+
   // autotuner decisions for the loaded matrix (tune.cu)
   bool tuned = false;
   int tuned_mode = EBIC_MODE_DIRECT;
@@ -148,6 +184,14 @@ void prof_count(ebic_ctx *ctx, int kernel, int64_t n);
 void prof_collect(ebic_ctx *ctx);
 
 int ebic_fail(ebic_ctx *ctx, int code, const std::string &msg);
+
+// Evaluation arguments with the loaded matrix's fields set (keys, bitmap, codes, sizes, error
+// word, staged form); the caller sets the trend parameters, outputs and work counter.
+EvalArgs eval_args_for(const ebic_ctx *ctx);
+// Passes of 128 rows (keys), of one code load (codes) or of 128 bitmap words per individual.
+int64_t eval_passes(const ebic_ctx *ctx, int mode);
+// Algorithmic bytes of one evaluation sweep in `mode` (sum of lengths total_len).
+double eval_bytes(const ebic_ctx *ctx, int mode, int64_t total_len, int64_t n_ind, int neg);
 int ebic_fail_cuda(ebic_ctx *ctx, cudaError_t e, const char *what, const char *file, int line);
 
 bool ebic_is_device_ptr(const void *p);

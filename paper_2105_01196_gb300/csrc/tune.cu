@@ -1,5 +1,6 @@
 // Autotuner: measures the evaluation kernels on a representative population of the loaded matrix
-// and records, for this matrix, the evaluation form (direct comparison or pair bitmap) and the
+// and records, for this matrix, the evaluation form (direct comparison from L2, direct comparison
+// over TMA-staged tiles, or pair bitmap) and the
 // work-item size (passes of 128 rows or 128 words per item) that minimise the expected time of
 // `expected_sweeps` evaluations, the bitmap build included when the bitmap does not exist yet.
 // EBIC_MODE_AUTO then follows the recorded choice, both in ebic_eval_population and in the
@@ -70,12 +71,8 @@ extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_
   EBIC_TRY(stage_population(ctx, col_idx, offsets, n_ind, false, &sp));
   EBIC_CHECK_CUDA(ctx, ctx->ev_out.ensure((size_t)n_ind * 3 * sizeof(int32_t)));
   EBIC_CHECK_CUDA(ctx, ctx->ev_fit.ensure((size_t)n_ind * sizeof(uint64_t)));
-  EvalArgs a{};
-  a.keys = ctx->keys.as<uint32_t>();
-  a.R = ctx->R;
-  a.R_pad = ctx->R_pad;
-  a.Wst = ctx->Wst;
-  a.C = ctx->C;
+  EvalArgs a = eval_args_for(ctx);
+  a.bitmap = nullptr;
   a.neg = p->neg_trends;
   a.rnum = p->ratio_num;
   a.rden = p->ratio_den;
@@ -92,7 +89,8 @@ extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_
   pv.n = n_ind;
 
   ebic_tune_report r{};
-  const int64_t passes_direct = ctx->R_pad / 128, passes_bitmap = (ctx->Wst + 127) / 128;
+  const int64_t passes_direct = eval_passes(ctx, EBIC_MODE_DIRECT),
+                passes_bitmap = eval_passes(ctx, EBIC_MODE_BITMAP);
   double best_direct = DBL_MAX, best_bitmap = DBL_MAX;
   int seg_direct = 0, seg_bitmap = 0;
   for (int seg : kSegCandidates) {
@@ -139,12 +137,19 @@ extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_
       }
     }
   }
-  const double cost_direct = (double)expected_sweeps * best_direct;
+  // the staged direct form, when its tiles fit in shared memory
+  double best_staged = DBL_MAX;
+  if (ctx->dtma.ok) {
+    EBIC_TRY(time_eval(ctx, EBIC_MODE_STAGED, a, pv, 0, &best_staged));
+  }
+  const int direct_mode = best_staged < best_direct ? EBIC_MODE_STAGED : EBIC_MODE_DIRECT;
+  const double cost_direct = (double)expected_sweeps * (best_staged < best_direct ? best_staged
+                                                                                    : best_direct);
   const double cost_bitmap = best_bitmap == DBL_MAX
                                  ? DBL_MAX
                                  : build_ms + (double)expected_sweeps * best_bitmap;
   ctx->tuned = true;
-  ctx->tuned_mode = cost_bitmap < cost_direct ? EBIC_MODE_BITMAP : EBIC_MODE_DIRECT;
+  ctx->tuned_mode = cost_bitmap < cost_direct ? EBIC_MODE_BITMAP : direct_mode;
   ctx->seg_direct = seg_direct;
   ctx->seg_bitmap = seg_bitmap;
   if (rep) {
@@ -152,6 +157,7 @@ extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_
     r.seg_direct = seg_direct;
     r.seg_bitmap = seg_bitmap;
     r.direct_ms = best_direct;
+    r.staged_ms = best_staged == DBL_MAX ? -1.0 : best_staged;
     r.bitmap_ms = best_bitmap == DBL_MAX ? -1.0 : best_bitmap;
     r.build_ms = build_ms;
     *rep = r;

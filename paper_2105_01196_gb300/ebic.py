@@ -23,7 +23,7 @@ EBIC_ECUDA = -4
 EBIC_ETIMEOUT = -5
 EBIC_ESTATE = -6
 
-MODE_AUTO, MODE_DIRECT, MODE_BITMAP, MODE_PLAIN = 0, 1, 2, 3
+MODE_AUTO, MODE_DIRECT, MODE_BITMAP, MODE_PLAIN, MODE_STAGED = 0, 1, 2, 3, 4
 ROW_MAJOR, COL_MAJOR = 0, 1
 MAX_LEN = 64
 
@@ -290,6 +290,7 @@ def ebic_load_state(ctx, params, blob):
 
 
 KERNEL_EVAL, KERNEL_BITMAP_BUILD, KERNEL_ALL, KERNEL_EVOLVE, KERNEL_FINISH = 0, 1, 2, 3, 4
+KERNEL_RANK_CODES = 5
 
 
 class KernelStats(ctypes.Structure):
@@ -315,7 +316,7 @@ class TuneReport(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("seg_direct", ctypes.c_int32),
                 ("seg_bitmap", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("direct_ms", ctypes.c_double), ("bitmap_ms", ctypes.c_double),
-                ("build_ms", ctypes.c_double)]
+                ("build_ms", ctypes.c_double), ("staged_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}

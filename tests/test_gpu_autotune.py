@@ -22,8 +22,9 @@ def test_autotune_then_auto_matches_oracle(sweeps):
     with ebic.Context(0) as ctx:
         ctx.load_matrix(x)
         rep = ctx.autotune(ci, off, p, sweeps)
-        assert rep["mode"] in (ebic.MODE_DIRECT, ebic.MODE_BITMAP)
+        assert rep["mode"] in (ebic.MODE_DIRECT, ebic.MODE_BITMAP, ebic.MODE_STAGED)
         assert rep["direct_ms"] > 0 and rep["seg_direct"] >= 0 and rep["seg_bitmap"] >= 0
+        assert rep["staged_ms"] > 0                  # 100 columns: the staged tiles fit
         got = ctx.eval_population(ci, off, p)
     want = ocounts.eval_population(x, ci, off, op)
     for g_, w_ in zip(got, want):

@@ -13,7 +13,7 @@ from paper_2105_01196_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-MODES = (1, 2, 3, 0)  # direct, bitmap, plain, auto
+MODES = (1, 2, 3, 4, 0)  # direct, bitmap, plain, staged, auto
 
 
 @pytest.fixture(scope="module")
@@ -117,7 +117,7 @@ def test_large_workloads_sampled(ebic, name, n_sample):
         ctx.load_matrix(x)
         for neg, num, den in ((1, 85, 100), (1, 1, 1)):
             want = oracle_eval(x, ci, off, neg, num, den, sample=sample)
-            for mode in (1, 2):
+            for mode in (1, 2, 4):
                 p = ebic.Params.make(neg_trends=neg, ratio_num=num, ratio_den=den, mode=mode)
                 assert_parity(ctx.eval_population(ci, off, p), want)
 
@@ -134,7 +134,7 @@ def test_device_pointers_and_col_major(ebic, torch_cuda):
                             (ebic.COL_MAJOR, torch.from_numpy(np.ascontiguousarray(x.T)).to(dev)),
                             (ebic.COL_MAJOR, np.ascontiguousarray(x.T))):
             ctx.load_matrix(xin, layout)
-            for mode in (1, 2, 3):
+            for mode in (1, 2, 3, 4):
                 p = ebic.Params.make(neg_trends=1, ratio_num=85, ratio_den=100, mode=mode)
                 outs = [torch.zeros(300, dtype=torch.int32, device=dev) for _ in range(3)]
                 outs.append(torch.zeros(300, dtype=torch.int64, device=dev))
@@ -196,3 +196,28 @@ def test_errors_are_reported(ebic, torch_cuda):
         # the context stays usable after every error
         r = ctx.eval_population(np.array([0, 1], np.int32), np.array([0, 2], np.int32), p)
         assert int(r[2][0]) == 0
+
+
+@pytest.mark.parametrize("R,C", [(700, 128), (700, 129), (520, 1024), (300, 1025)])
+def test_code_width_boundaries(ebic, R, C):
+    """The direct form reads 8-bit per-row rank codes up to 128 columns, 16-bit ones up to 1,024
+    and the 32-bit order keys beyond; each width against the oracle, on tie-heavy values with
+    signed zeros and extreme magnitudes, rows not a multiple of the kernel's pass."""
+    g = np.random.default_rng(R * 7 + C)
+    x = g.integers(-3, 4, size=(R, C)).astype(np.float32)
+    x[g.random((R, C)) < 0.05] = -0.0
+    x[g.random((R, C)) < 0.01] = np.finfo(np.float32).max
+    x[g.random((R, C)) < 0.01] = -np.finfo(np.float32).max
+    x[g.random((R, C)) < 0.01] = np.float32(1e-45)
+    x[: R // 10] = 1.5                              # rows of one value: no trend at all
+    ci, off = ragged_population(g, 48, C)
+    with ebic.Context(0) as ctx:
+        ctx.profile_enable(True)
+        ctx.load_matrix(x)
+        st = ctx.profile_read(ebic.KERNEL_RANK_CODES)
+        assert st["launches"] == (1 if C <= 1024 else 0)
+        for neg, num, den in ((1, 85, 100), (0, 1, 1), (1, 1, 2)):
+            want = oracle_eval(x, ci, off, neg, num, den)
+            for mode in (1, 2, 4):
+                p = ebic.Params.make(neg_trends=neg, ratio_num=num, ratio_den=den, mode=mode)
+                assert_parity(ctx.eval_population(ci, off, p), want)

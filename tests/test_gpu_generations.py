@@ -56,7 +56,7 @@ def tiny_matrix():
     return x
 
 
-@pytest.mark.parametrize("mode,use_graph", [(1, 1), (2, 1), (2, 0)])
+@pytest.mark.parametrize("mode,use_graph", [(1, 1), (2, 1), (2, 0), (4, 1)])
 def test_generation_by_generation(ebic, mode, use_graph):
     x = tiny_matrix()
     gp, op = both_params(ebic, mode=mode, use_graph=use_graph)
