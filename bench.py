@@ -30,7 +30,7 @@ if ROOT not in sys.path:
 
 METRIC = "individual·row trend evaluations/sec and EBIC generations/sec vs plain GPU form"
 UNIT = "evals/s"
-MODES = {"auto": 0, "direct": 1, "bitmap": 2, "plain": 3}
+MODES = {"auto": 0, "direct": 1, "bitmap": 2, "plain": 3, "staged": 4}
 
 
 def parse():
@@ -61,6 +61,19 @@ def dist_setup(args):
         backend = "nccl" if torch.cuda.is_available() else "gloo"
         dist.init_process_group(backend)
     return world, rank, local, dist
+
+
+def eval_kernel_name(mode, cols):
+    """The evaluation kernel a form runs (the direct form reads rank codes up to 1,024 columns)."""
+    if mode == 2:
+        return "k_eval_bitmap"
+    if mode == 4:
+        return "k_eval_direct_tma"
+    if mode == 3:
+        return "k_eval_plain"
+    if mode == 1:
+        return "k_eval_codes" if cols <= 1024 else "k_eval_direct"
+    return "k_eval_bitmap|k_eval_codes"
 
 
 def load_peaks():
@@ -271,6 +284,7 @@ def main():
                               n_biclusters=max(10, w.n_bic), elite=max(10, w.n_bic),
                               tabu_hit_limit=0, seed=w.seed, mode=MODES[args.mode])
     ctx = ebic.Context(local, stream.cuda_stream)
+    used_mode = [0]                     # evaluation form the generation loop used
 
     def step(host):
         """One pass of the hot path; returns (individual,row) evaluations done."""
@@ -284,6 +298,7 @@ def main():
         units += P * R
         if gens > 0:
             rep = ctx.run_generations(params, gens)
+            used_mode[0] = int(rep.eval_mode)
             units += int(rep.n_evaluated) * R
             masks = ctx.extract_biclusters(R)
             units += len(masks) * R
@@ -360,7 +375,8 @@ def main():
         v["avg_us"] = 1e3 * v["ms"] / v["timed_launches"] if v["timed_launches"] else None
         v["share_of_kernel_time"] = v["ms"] / timed_ms if timed_ms else None
     dominant = max(stats, key=lambda k: stats[k]["ms"])
-    kernel_names = {"eval": "k_eval_bitmap" if args.mode != "direct" else "k_eval_direct",
+    kernel_names = {"eval": eval_kernel_name(used_mode[0] if used_mode[0] else MODES[args.mode],
+                                             w.cols),
                     "evolve": "k_evolve", "finish": "k_finish", "bitmap_build": "k_build_bitmap"}
     roof = None
     se = stats["eval"]

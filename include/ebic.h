@@ -116,7 +116,7 @@ typedef struct ebic_run_report {
   int32_t last_hits;   /* tabu hits of the last generation built                             */
   int32_t n_top;       /* entries in the top rank list                                       */
   int64_t n_evaluated; /* individuals scored since the run was initialised                   */
-  int32_t eval_mode;   /* the evaluation kernel used (EBIC_MODE_DIRECT or EBIC_MODE_BITMAP)  */
+  int32_t eval_mode;   /* evaluation form used: EBIC_MODE_DIRECT, _STAGED or _BITMAP         */
   int32_t reserved;
 } ebic_run_report;
 

@@ -152,8 +152,11 @@ __global__ void __launch_bounds__(kThreads) k_eval_codes(EvalArgs a, PopView pv)
 #pragma unroll
           for (int j = 0; j < NW; ++j) {
             const uint32_t cH = cur[j] | H, c1 = cur[j] + ONE;
-            inc[j] += ((cH - p1w[j]) & H) >> SH;
-            if (NEG) dec[j] += ((pH[j] - c1) & H) >> SH;
+            // (m >> SH) + acc as the high word of m * 2^(32-SH) plus acc: one multiply-add on
+            // the FMA pipe instead of a shift and an add on the integer ALU pipe, which this
+            // loop otherwise saturates
+            inc[j] = __umulhi((cH - p1w[j]) & H, 1u << (32 - SH)) + inc[j];
+            if (NEG) dec[j] = __umulhi((pH[j] - c1) & H, 1u << (32 - SH)) + dec[j];
             pH[j] = cH;
             p1w[j] = c1;
           }
