@@ -63,6 +63,25 @@ def dist_setup(args):
     return world, rank, local, dist
 
 
+def search_quality(ctx, truth, R, C, gens):
+    """CE (Eq. 1) of the last run's top list, with the rows that follow each entry, against the
+    planted biclusters (measured after the timed region)."""
+    from paper_2105_01196_gb300.quality import clustering_error, rows_from_mask
+    top = ctx.toplist()
+    masks = ctx.extract_biclusters(R)
+    found = [(rows_from_mask(masks[k], R), list(e["cols"])) for k, e in enumerate(top)]
+    ref = [(rows, order) for rows, order, _ in truth]
+    ce = clustering_error(found, ref, R, C)
+    # for each planted bicluster, the best pairwise CE score over the found entries
+    best = [max((clustering_error([f], [t], R, C)["score"] for f in found), default=0.0)
+            for t in ref]
+    return {"ce_score": ce["score"], "ce_error": ce["error"], "d_max": ce["d_max"],
+            "union": ce["union"], "found": len(found), "planted": len(ref),
+            "best_pair_score_per_planted": [round(b, 4) for b in best],
+            "generations": gens, "measure": "clustering error, Eq. 1 (Munkres assignment); "
+            "score = D_max/|U|, 1 = perfect"}
+
+
 def eval_kernel_name(mode, cols):
     """The evaluation kernel a form runs (the direct form reads rank codes up to 1,024 columns)."""
     if mode == 2:
@@ -409,6 +428,7 @@ def main():
             "e2e": e2e}
     if gens > 0:
         line["generations_per_s"] = gens * args.steps / (total_ms / 1e3)
+        line["quality"] = search_quality(ctx, truth, R, w.cols, gens)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, x, ci, off, args.cpu_seconds)
     print(json.dumps(line), flush=True)
