@@ -16,6 +16,14 @@ Readings where the paper is silent:
   * fitness f = 0 when fewer than ``min_rows`` rows are accepted or the individual is dead, else
     rows_any * 2**min(L, col_cap), an exact integer.
 
+Two variants of the pair test, each a flag (both off by default):
+  * ``non_strict``: a positive pair holds when x[r, c_{k+1}] >= x[r, c_k] and a negative pair when
+    x[r, c_{k+1}] <= x[r, c_k], so a tie counts for both directions;
+  * ``last_kept``: each direction compares a value with the last value that kept the trend rather
+    than with its predecessor: last = x[r, c_0]; for k = 1..L-1, when the pair (last, x[r, c_k])
+    holds the count grows and last becomes x[r, c_k]; a value that breaks the trend is skipped.
+    With the exact threshold (every pair) both ways of counting accept the same rows.
+
 Test infrastructure only (see the package docstring).
 """
 
@@ -46,12 +54,31 @@ def check_chromosome(cols, n_cols):
     return cols
 
 
-def row_trend_masks(x, cols, neg_trends, ratio_num, ratio_den):
+def pair_holds(nxt, prev, positive, non_strict):
+    """The pair test of one direction (element-wise over rows)."""
+    if positive:
+        return nxt >= prev if non_strict else nxt > prev
+    return nxt <= prev if non_strict else nxt < prev
+
+
+def trend_count(sub, positive, non_strict, last_kept):
+    """Per-row count of the series' pairs that follow the direction (sub = R x L values)."""
+    if not last_kept:
+        return pair_holds(sub[:, 1:], sub[:, :-1], positive, non_strict).sum(axis=1)
+    last = sub[:, 0].copy()
+    count = np.zeros(sub.shape[0], dtype=np.int64)
+    for k in range(1, sub.shape[1]):
+        hit = pair_holds(sub[:, k], last, positive, non_strict)
+        count += hit
+        last = np.where(hit, sub[:, k], last)
+    return count
+
+
+def row_trend_masks(x, cols, neg_trends, ratio_num, ratio_den, non_strict=0, last_kept=0):
     """Boolean masks over rows: (pos_ok, neg_ok) for one individual, from the plain definition."""
     sub = x[:, cols]                       # R x L, float32
-    nxt, cur = sub[:, 1:], sub[:, :-1]
-    inc = (nxt > cur).sum(axis=1)
-    dec = (nxt < cur).sum(axis=1)
+    inc = trend_count(sub, True, non_strict, last_kept)
+    dec = trend_count(sub, False, non_strict, last_kept)
     t = threshold(len(cols), ratio_num, ratio_den)
     pos_ok = inc >= t
     neg_ok = (dec >= t) if neg_trends else np.zeros_like(pos_ok)
@@ -65,7 +92,8 @@ def fitness(rows_any, L, min_rows, col_cap, dead=False):
 
 
 def eval_individual(x, cols, p):
-    pos_ok, neg_ok = row_trend_masks(x, cols, p.neg_trends, p.ratio_num, p.ratio_den)
+    pos_ok, neg_ok = row_trend_masks(x, cols, p.neg_trends, p.ratio_num, p.ratio_den,
+                                     p.non_strict, p.last_kept)
     rp = int(pos_ok.sum())
     rn = int(neg_ok.sum())
     ra = int((pos_ok | neg_ok).sum())

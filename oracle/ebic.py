@@ -243,7 +243,8 @@ def score(x, st, p):
         if st.dead[s]:
             continue
         cols = st.pop[s]
-        pos_ok, neg_ok = row_trend_masks(x, cols, p.neg_trends, p.ratio_num, p.ratio_den)
+        pos_ok, neg_ok = row_trend_masks(x, cols, p.neg_trends, p.ratio_num, p.ratio_den,
+                                         p.non_strict, p.last_kept)
         rp, rn, ra = int(pos_ok.sum()), int(neg_ok.sum()), int((pos_ok | neg_ok).sum())
         st.rows[s] = (rp, rn, ra)
         st.fit[s] = fitness(ra, len(cols), p.min_rows, p.col_cap)
@@ -332,7 +333,8 @@ def extract(x, st, p):
     masks = np.zeros((len(st.top), W), dtype=np.uint32)
     weights = (np.uint64(1) << np.arange(32, dtype=np.uint64))
     for k, e in enumerate(st.top):
-        pos_ok, neg_ok = row_trend_masks(x, list(e.cols), p.neg_trends, p.ratio_num, p.ratio_den)
+        pos_ok, neg_ok = row_trend_masks(x, list(e.cols), p.neg_trends, p.ratio_num, p.ratio_den,
+                                         p.non_strict, p.last_kept)
         bits = np.zeros(W * 32, dtype=np.uint64)
         bits[:R] = pos_ok | neg_ok
         masks[k] = (bits.reshape(W, 32) * weights).sum(axis=1).astype(np.uint32)

@@ -12,6 +12,8 @@ below are readings, documented with the design notes:
   tournament           tournament size (step 5).
   max_attempts         children tried per slot before the slot is declared dead (tabu, step 5).
   tabu_hit_limit       per-generation tabu hits that stop the run (step 6); <= 0 disables.
+  non_strict           1: ties count as following both directions (pair test >= / <=).
+  last_kept            1: compare each value with the last value that kept the trend.
 
 Test infrastructure only (see the package docstring).
 """
@@ -40,6 +42,8 @@ class Params:
     max_attempts: int = 4
     tabu_hit_limit: int = 800
     seed: int = 20210710
+    non_strict: int = 0
+    last_kept: int = 0
 
     def as_dict(self):
         return asdict(self)
@@ -63,3 +67,5 @@ def validate(p, n_cols):
         raise ValueError("tournament and max_attempts must be in [1, 16]")
     if not (0 <= p.col_cap <= 16 and p.min_rows >= 0):
         raise ValueError("col_cap must be in [0, 16] and min_rows >= 0")
+    if p.non_strict not in (0, 1) or p.last_kept not in (0, 1):
+        raise ValueError("non_strict and last_kept are 0 or 1")
