@@ -107,6 +107,10 @@ typedef struct ebic_params {
   uint64_t seed;
   int32_t mode;
   int32_t use_graph;
+  int32_t non_strict;  /* 1: ties hold for both directions (pair test >= / <=); default 0      */
+  int32_t last_kept;   /* 1: each value is compared with the last value that kept the
+                          direction instead of with its predecessor; no bitmap form (mode
+                          EBIC_MODE_BITMAP is rejected, AUTO takes the direct form); default 0 */
 } ebic_params;
 
 /* Progress of a run (Sec. 2.4, steps 6 and 8). */

@@ -76,6 +76,10 @@ int ebic_check_eval_params(ebic_ctx *ctx, const ebic_params *p) {
     return ebic_fail(ctx, EBIC_EINVAL, "need 0 <= col_cap <= 16 and min_rows >= 0");
   if (p->mode < EBIC_MODE_AUTO || p->mode > EBIC_MODE_STAGED)
     return ebic_fail(ctx, EBIC_EINVAL, "unknown mode");
+  if ((p->non_strict != 0 && p->non_strict != 1) || (p->last_kept != 0 && p->last_kept != 1))
+    return ebic_fail(ctx, EBIC_EINVAL, "non_strict and last_kept must be 0 or 1");
+  if (p->last_kept && p->mode == EBIC_MODE_BITMAP)
+    return ebic_fail(ctx, EBIC_EINVAL, "the last-kept pair test has no bitmap form");
   return EBIC_OK;
 }
 
@@ -463,13 +467,15 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
   const double mean_len = sp.mean_len;
   const int64_t total = sp.total;
 
-  int mode = choose_mode(ctx, p->mode, n_ind, mean_len, 1);
+  int mode = choose_mode(ctx, p->mode, n_ind, mean_len, 1, p->last_kept);
   if (mode == EBIC_MODE_BITMAP && !ctx->bitmap_ok) EBIC_TRY(ebic_build_bitmap(ctx));
 
   EBIC_CHECK_CUDA(ctx, ctx->ev_out.ensure((size_t)n_ind * 3 * sizeof(int32_t)));
   EBIC_CHECK_CUDA(ctx, ctx->ev_fit.ensure((size_t)n_ind * sizeof(uint64_t)));
   EvalArgs a = eval_args_for(ctx);
   a.neg = p->neg_trends;
+  a.non_strict = p->non_strict;
+  a.last_kept = p->last_kept;
   a.rnum = p->ratio_num;
   a.rden = p->ratio_den;
   a.min_rows = p->min_rows;
@@ -566,8 +572,11 @@ double eval_bytes(const ebic_ctx *ctx, int mode, int64_t total_len, int64_t n_in
 }
 
 int choose_mode(const ebic_ctx *ctx, int requested, int64_t n_ind, double mean_len,
-                int expected_sweeps) {
+                int expected_sweeps, int last_kept) {
   if (requested != EBIC_MODE_AUTO) return requested;
+  if (last_kept) {  // no bitmap form
+    return ctx->tuned && ctx->tuned_mode != EBIC_MODE_BITMAP ? ctx->tuned_mode : EBIC_MODE_DIRECT;
+  }
   if (ctx->tuned) return ctx->tuned_mode;
   if (ctx->bitmap_ok) return EBIC_MODE_BITMAP;
   const double Wst = (double)ctx->Wst, C = (double)ctx->C;

@@ -84,11 +84,21 @@ __global__ void __launch_bounds__(kThreads) k_rank_codes(const uint32_t *__restr
 // ------------------------------------------------------------------------------- evaluation
 
 // W = bytes per code.  A pass covers 32 lanes x kVec 16-byte loads (16 / W rows each) per column.
-template <int W, bool NEG>
+// NS / LK: the pair-test variants of trend.cuh.  Each direction keeps a reference word: its
+// fields hold the predecessor (or, with LK, the last value the direction kept) plus OFF for the
+// upward test and with the top bit set for the downward one, so that
+//   up:   ((cur | H) - up_ref) & H      down: (down_ref - (cur + OFF)) & H
+// set a field's top bit where the pair holds (OFF = 1 per field for the strict tests, 0 for
+// greater-or-equal / smaller-or-equal).  With LK a field's reference is replaced only where its
+// test held.  With ties counting, the pad rows past R (code 0) would pass and are masked out.
+template <int W, bool NEG, bool NS, bool LK>
 __global__ void __launch_bounds__(kThreads) k_eval_codes(EvalArgs a, PopView pv) {
   constexpr uint32_t H = W == 1 ? 0x80808080u : 0x80008000u;    // top bit of every field
   constexpr uint32_t ONE = W == 1 ? 0x01010101u : 0x00010001u;  // 1 in every field
+  constexpr uint32_t OFF = NS ? 0u : ONE;
+  constexpr uint32_t FMAX = W == 1 ? 0xFFu : 0xFFFFu;           // a full field
   constexpr int SH = W == 1 ? 7 : 15;
+  constexpr int FW = 4 / W;                                     // fields per word
   constexpr int kRowsPerPass = 32 * 16 * kVec / W;
   constexpr int NW = 4 * kVec;  // 32-bit words per lane
   __shared__ int64_t s_base[kWarps][EBIC_MAX_LEN];
@@ -125,15 +135,15 @@ __global__ void __launch_bounds__(kThreads) k_eval_codes(EvalArgs a, PopView pv)
       for (int64_t pass = p0; pass < p1; ++pass) {
         // lane's 16-byte chunks: lane + 32 v for v < kVec (each warp load is contiguous)
         const uint8_t *base = a.codes + pass * (kRowsPerPass * W) + lane * 16;
-        uint32_t pH[NW], p1w[NW], inc[NW], dec[NW];
+        uint32_t dn_ref[NW], up_ref[NW], inc[NW], dec[NW];
 #pragma unroll
         for (int v = 0; v < kVec; ++v) {
           const uint4 v0 = __ldg(reinterpret_cast<const uint4 *>(base + v * 512 + s_base[warp][0]));
           const uint32_t w0[4] = {v0.x, v0.y, v0.z, v0.w};
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            pH[4 * v + j] = w0[j] | H;
-            p1w[4 * v + j] = w0[j] + ONE;
+            dn_ref[4 * v + j] = w0[j] | H;
+            up_ref[4 * v + j] = w0[j] + OFF;
             inc[4 * v + j] = 0u;
             dec[4 * v + j] = 0u;
           }
@@ -151,20 +161,44 @@ __global__ void __launch_bounds__(kThreads) k_eval_codes(EvalArgs a, PopView pv)
           }
 #pragma unroll
           for (int j = 0; j < NW; ++j) {
-            const uint32_t cH = cur[j] | H, c1 = cur[j] + ONE;
-            // (m >> SH) + acc as the high word of m * 2^(32-SH) plus acc: one multiply-add on
-            // the FMA pipe instead of a shift and an add on the integer ALU pipe, which this
+            const uint32_t cH = cur[j] | H, cO = cur[j] + OFF;
+            // (m >> SH) as the high word of m * 2^(32-SH): with the accumulate, one multiply-add
+            // on the FMA pipe instead of a shift and an add on the integer ALU pipe, which this
             // loop otherwise saturates
-            inc[j] = __umulhi((cH - p1w[j]) & H, 1u << (32 - SH)) + inc[j];
-            if (NEG) dec[j] = __umulhi((pH[j] - c1) & H, 1u << (32 - SH)) + dec[j];
-            pH[j] = cH;
-            p1w[j] = c1;
+            const uint32_t u1 = __umulhi((cH - up_ref[j]) & H, 1u << (32 - SH));
+            inc[j] += u1;
+            uint32_t d1 = 0u;
+            if (NEG) {
+              d1 = __umulhi((dn_ref[j] - cO) & H, 1u << (32 - SH));
+              dec[j] += d1;
+            }
+            if (LK) {  // replace the reference only in the fields whose pair held
+              const uint32_t fu = u1 * FMAX;
+              up_ref[j] = (cO & fu) | (up_ref[j] & ~fu);
+              if (NEG) {
+                const uint32_t fd = d1 * FMAX;
+                dn_ref[j] = (cH & fd) | (dn_ref[j] & ~fd);
+              }
+            } else {
+              up_ref[j] = cO;
+              dn_ref[j] = cH;
+            }
           }
         }
+        const bool tail = NS && (pass + 1) * kRowsPerPass > a.R;  // pass holds pad rows
 #pragma unroll
         for (int j = 0; j < NW; ++j) {
-          const uint32_t po = (inc[j] + tadd) & H;
-          const uint32_t ne = NEG ? ((dec[j] + tadd) & H) : 0u;
+          uint32_t po = (inc[j] + tadd) & H;
+          uint32_t ne = NEG ? ((dec[j] + tadd) & H) : 0u;
+          if (tail) {
+            const int64_t row0 = pass * kRowsPerPass + ((j >> 2) * 512 + lane * 16 + 4 * (j & 3)) / W;
+            uint32_t vm = 0u;
+#pragma unroll
+            for (int f = 0; f < FW; ++f)
+              if (row0 + f < a.R) vm |= 1u << (8 * W * (f + 1) - 1);
+            po &= vm;
+            ne &= vm;
+          }
           cp += __popc(po);
           if (NEG) {
             cn += __popc(ne);
@@ -266,9 +300,18 @@ cudaError_t launch_eval_codes(const EvalArgs &a0, const PopView &pv, int num_sms
   EvalArgs a = a0;
   const int W = a.code_bytes;
   const int64_t passes_total = a.S / code_rows_per_pass(W);
-  void (*kern)(EvalArgs, PopView) =
-      W == 1 ? (a.neg ? k_eval_codes<1, true> : k_eval_codes<1, false>)
-             : (a.neg ? k_eval_codes<2, true> : k_eval_codes<2, false>);
+  using Kernel = void (*)(EvalArgs, PopView);
+  static const Kernel table[16] = {
+      k_eval_codes<1, false, false, false>, k_eval_codes<1, false, false, true>,
+      k_eval_codes<1, false, true, false>,  k_eval_codes<1, false, true, true>,
+      k_eval_codes<1, true, false, false>,  k_eval_codes<1, true, false, true>,
+      k_eval_codes<1, true, true, false>,   k_eval_codes<1, true, true, true>,
+      k_eval_codes<2, false, false, false>, k_eval_codes<2, false, false, true>,
+      k_eval_codes<2, false, true, false>,  k_eval_codes<2, false, true, true>,
+      k_eval_codes<2, true, false, false>,  k_eval_codes<2, true, false, true>,
+      k_eval_codes<2, true, true, false>,   k_eval_codes<2, true, true, true>};
+  const Kernel kern = table[(W == 2 ? 8 : 0) + (a.neg ? 4 : 0) + (a.non_strict ? 2 : 0) +
+                            (a.last_kept ? 1 : 0)];
   const int bps = blocks_per_sm(kern, 0);
   const int64_t warps = (int64_t)num_sms * bps * kWarps;
   // Segments: the autotuner's size when it set one, else enough work items for ~8 per

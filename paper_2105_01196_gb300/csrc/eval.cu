@@ -18,6 +18,7 @@
 // partial counts with one atomic per item.
 #include "internal.h"
 #include "tables.cuh"
+#include "trend.cuh"
 
 namespace {
 
@@ -82,7 +83,10 @@ __global__ void k_validate_csr(const int32_t *__restrict__ cols, const int32_t *
 
 // ------------------------------------------------------------------------------- direct form
 
-template <bool NEG>
+// NS / LK: the pair-test variants of trend.cuh (ties count for both directions / compare with
+// the last value kept).  With ties counting, the pad rows past R (key 0 everywhere) would pass,
+// so they are masked out.
+template <bool NEG, bool NS, bool LK>
 __global__ void __launch_bounds__(kThreads) k_eval_direct(EvalArgs a, PopView pv) {
   __shared__ int64_t s_base[kWarps][EBIC_MAX_LEN];
   wait_prior_grid();
@@ -107,29 +111,28 @@ __global__ void __launch_bounds__(kThreads) k_eval_direct(EvalArgs a, PopView pv
     int cp = 0, cn = 0, ca = 0;
     for (int64_t pass = p0; pass < p1; ++pass) {
       const int64_t r = pass * 128 + lane * 4;
-      uint4 prev = ldg4(a.keys + s_base[warp][0] + r);
-      int i0 = 0, i1 = 0, i2 = 0, i3 = 0, d0 = 0, d1 = 0, d2 = 0, d3 = 0;
+      const uint4 v0 = ldg4(a.keys + s_base[warp][0] + r);
+      RowTrend<uint32_t, NEG, NS, LK> tr[4];
+      tr[0].start(v0.x);
+      tr[1].start(v0.y);
+      tr[2].start(v0.z);
+      tr[3].start(v0.w);
 #pragma unroll 4
       for (int k = 1; k < L; ++k) {
         const uint4 cur = ldg4(a.keys + s_base[warp][k] + r);
-        i0 += cur.x > prev.x;
-        i1 += cur.y > prev.y;
-        i2 += cur.z > prev.z;
-        i3 += cur.w > prev.w;
-        if (NEG) {
-          d0 += cur.x < prev.x;
-          d1 += cur.y < prev.y;
-          d2 += cur.z < prev.z;
-          d3 += cur.w < prev.w;
-        }
-        prev = cur;
+        tr[0].step(cur.x);
+        tr[1].step(cur.y);
+        tr[2].step(cur.z);
+        tr[3].step(cur.w);
       }
-      const bool p_0 = i0 >= t, p_1 = i1 >= t, p_2 = i2 >= t, p_3 = i3 >= t;
-      const bool n_0 = NEG && d0 >= t, n_1 = NEG && d1 >= t, n_2 = NEG && d2 >= t,
-                 n_3 = NEG && d3 >= t;
-      cp += p_0 + p_1 + p_2 + p_3;
-      cn += n_0 + n_1 + n_2 + n_3;
-      ca += (p_0 | n_0) + (p_1 | n_1) + (p_2 | n_2) + (p_3 | n_3);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool valid = !NS || r + j < a.R;
+        const bool po = valid && tr[j].inc >= t, ne = valid && NEG && tr[j].dec >= t;
+        cp += po;
+        cn += ne;
+        ca += po | ne;
+      }
     }
     cp = __reduce_add_sync(kFull, cp);
     cn = __reduce_add_sync(kFull, cn);
@@ -213,7 +216,24 @@ __device__ __forceinline__ int popc4(uint4 v) {
   return __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
 }
 
-template <bool NEG>
+// A pair word of the bitmap for lane-active words (zero otherwise); with ties counting (NS) the
+// word is the complement of the opposite direction's word: key(d) >= key(c) = not key(c) > key(d).
+template <bool NS>
+__device__ __forceinline__ uint4 ldb(bool act, const uint32_t *p) {
+  if (!act) return make_uint4(0u, 0u, 0u, 0u);
+  const uint4 v = ldg4(p);
+  return NS ? make_uint4(~v.x, ~v.y, ~v.z, ~v.w) : v;
+}
+
+// Rows of word w that exist (bit j = row 32 w + j < R).
+__device__ __forceinline__ uint32_t valid_bits(int64_t w, int64_t R) {
+  const int64_t n = R - 32 * w;
+  return n >= 32 ? kFull : (n <= 0 ? 0u : ((1u << n) - 1u));
+}
+
+// NS: ties count for both directions (complemented opposite words; pad rows masked out).  The
+// last-kept variant has no pair-word form (its reference value differs from row to row).
+template <bool NEG, bool NS>
 __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView pv) {
   __shared__ int64_t s_pos[kWarps][EBIC_MAX_LEN];
   __shared__ int64_t s_neg[kWarps][EBIC_MAX_LEN];
@@ -236,8 +256,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
     __syncwarp();
     for (int k = lane; k < np; k += 32) {
       const int64_t c = pv.cols[st + k], d = pv.cols[st + k + 1];
-      s_pos[warp][k] = (c * a.C + d) * Wst;
-      s_neg[warp][k] = (d * a.C + c) * Wst;
+      s_pos[warp][k] = NS ? (d * a.C + c) * Wst : (c * a.C + d) * Wst;
+      s_neg[warp][k] = NS ? (c * a.C + d) * Wst : (d * a.C + c) * Wst;
     }
     __syncwarp();
     const int t = threshold(L, a.rnum, a.rden);
@@ -257,8 +277,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
           uint4 v[4], u[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            v[j] = act ? ldg4(G + s_pos[warp][k + j]) : zero4;
-            if (NEG) u[j] = act ? ldg4(G + s_neg[warp][k + j]) : zero4;
+            v[j] = ldb<NS>(act, G + s_pos[warp][k + j]);
+            if (NEG) u[j] = ldb<NS>(act, G + s_neg[warp][k + j]);
           }
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
@@ -267,8 +287,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
           }
         }
         for (; k < np; ++k) {
-          ap = and4(ap, act ? ldg4(G + s_pos[warp][k]) : zero4);
-          if (NEG) an = and4(an, act ? ldg4(G + s_neg[warp][k]) : zero4);
+          ap = and4(ap, ldb<NS>(act, G + s_pos[warp][k]));
+          if (NEG) an = and4(an, ldb<NS>(act, G + s_neg[warp][k]));
         }
         pos = act ? ap : zero4;
         if (NEG) neg = act ? an : zero4;
@@ -284,8 +304,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
           uint4 v[4], u[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            v[j] = act ? ldg4(G + s_pos[warp][k + j]) : zero4;
-            if (NEG) u[j] = act ? ldg4(G + s_neg[warp][k + j]) : zero4;
+            v[j] = ldb<NS>(act, G + s_pos[warp][k + j]);
+            if (NEG) u[j] = ldb<NS>(act, G + s_neg[warp][k + j]);
           }
           cnt_add4(P[0], v[0].x, v[1].x, v[2].x, v[3].x);
           cnt_add4(P[1], v[0].y, v[1].y, v[2].y, v[3].y);
@@ -299,13 +319,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
           }
         }
         for (; k < np; ++k) {
-          const uint4 v = act ? ldg4(G + s_pos[warp][k]) : zero4;
+          const uint4 v = ldb<NS>(act, G + s_pos[warp][k]);
           cnt_add1(P[0], v.x);
           cnt_add1(P[1], v.y);
           cnt_add1(P[2], v.z);
           cnt_add1(P[3], v.w);
           if (NEG) {
-            const uint4 u = act ? ldg4(G + s_neg[warp][k]) : zero4;
+            const uint4 u = ldb<NS>(act, G + s_neg[warp][k]);
             cnt_add1(N[0], u.x);
             cnt_add1(N[1], u.y);
             cnt_add1(N[2], u.z);
@@ -315,6 +335,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
         pos = make_uint4(cnt_ge(P[0], t), cnt_ge(P[1], t), cnt_ge(P[2], t), cnt_ge(P[3], t));
         if (NEG)
           neg = make_uint4(cnt_ge(N[0], t), cnt_ge(N[1], t), cnt_ge(N[2], t), cnt_ge(N[3], t));
+      }
+      if (NS) {  // pad rows (and inactive lanes) hold complemented zeros: mask them out
+        const uint4 vm = act ? make_uint4(valid_bits(w, a.R), valid_bits(w + 1, a.R),
+                                          valid_bits(w + 2, a.R), valid_bits(w + 3, a.R))
+                             : zero4;
+        pos = and4(pos, vm);
+        if (NEG) neg = and4(neg, vm);
       }
       cp += popc4(pos);
       if (NEG) {
@@ -339,22 +366,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
 
 // One launch per individual; one row per thread; block counts by __syncthreads_count and one
 // atomic per block and output (the paper's Sec. 2.4 kernel: atomics, no intermediate buffer).
-template <bool NEG>
+template <bool NEG, bool NS, bool LK>
 __global__ void k_eval_plain(EvalArgs a, const int32_t *__restrict__ cols, int L, int i) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool po = false, ne = false;
   if (r < a.R) {
     const int t = threshold(L, a.rnum, a.rden);
-    uint32_t prev = a.keys[(int64_t)cols[0] * a.R_pad + r];
-    int inc = 0, dec = 0;
-    for (int k = 1; k < L; ++k) {
-      const uint32_t cur = a.keys[(int64_t)cols[k] * a.R_pad + r];
-      inc += cur > prev;
-      dec += cur < prev;
-      prev = cur;
-    }
-    po = inc >= t;
-    ne = NEG && dec >= t;
+    RowTrend<uint32_t, NEG, NS, LK> tr;
+    tr.start(a.keys[(int64_t)cols[0] * a.R_pad + r]);
+    for (int k = 1; k < L; ++k) tr.step(a.keys[(int64_t)cols[k] * a.R_pad + r]);
+    po = tr.inc >= t;
+    ne = NEG && tr.dec >= t;
   }
   const int np = __syncthreads_count(po);
   const int nn = __syncthreads_count(ne);
@@ -425,22 +447,41 @@ cudaError_t launch_maybe_pdl(void (*kern)(Args...), dim3 grid, dim3 block, size_
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+using EvalKernel = void (*)(EvalArgs, PopView);
+
+// The instantiation for (negative trends, ties counting, last kept).
+static EvalKernel direct_kernel(bool neg, bool ns, bool lk) {
+  static const EvalKernel t[8] = {
+      k_eval_direct<false, false, false>, k_eval_direct<false, false, true>,
+      k_eval_direct<false, true, false>,  k_eval_direct<false, true, true>,
+      k_eval_direct<true, false, false>,  k_eval_direct<true, false, true>,
+      k_eval_direct<true, true, false>,   k_eval_direct<true, true, true>};
+  return t[(neg ? 4 : 0) + (ns ? 2 : 0) + (lk ? 1 : 0)];
+}
+
+static EvalKernel bitmap_kernel(bool neg, bool ns) {
+  static const EvalKernel t[4] = {k_eval_bitmap<false, false>, k_eval_bitmap<false, true>,
+                                  k_eval_bitmap<true, false>, k_eval_bitmap<true, true>};
+  return t[(neg ? 2 : 0) + (ns ? 1 : 0)];
+}
+
 cudaError_t launch_eval_kernel(int mode, const EvalArgs &a0, const PopView &pv, int num_sms,
                                cudaStream_t s, bool pdl) {
   if (pv.n <= 0) return cudaSuccess;
   if (mode == EBIC_MODE_STAGED) {
-    if (a0.dtma && a0.dtma->ok) return launch_eval_direct_tma(*a0.dtma, a0, pv, num_sms, s, pdl);
-    mode = EBIC_MODE_DIRECT;  // the tile does not fit in shared memory
+    // the staged kernel implements the default pair test and needs its tiles to fit
+    if (a0.dtma && a0.dtma->ok && !a0.non_strict && !a0.last_kept)
+      return launch_eval_direct_tma(*a0.dtma, a0, pv, num_sms, s, pdl);
+    mode = EBIC_MODE_DIRECT;
   }
+  if (mode == EBIC_MODE_BITMAP && a0.last_kept) return cudaErrorInvalidValue;  // no word form
   if (mode == EBIC_MODE_DIRECT && a0.codes) return launch_eval_codes(a0, pv, num_sms, s, pdl);
   EvalArgs a = a0;
   const bool bitmap = (mode == EBIC_MODE_BITMAP);
   const int64_t passes_total = bitmap ? (a.Wst + 127) / 128 : a.R_pad / 128;
-  const void *kern = bitmap ? (a.neg ? (const void *)k_eval_bitmap<true>
-                                     : (const void *)k_eval_bitmap<false>)
-                            : (a.neg ? (const void *)k_eval_direct<true>
-                                     : (const void *)k_eval_direct<false>);
-  const int bps = blocks_per_sm_for(kern);
+  const EvalKernel kern = bitmap ? bitmap_kernel(a.neg, a.non_strict)
+                                 : direct_kernel(a.neg, a.non_strict, a.last_kept);
+  const int bps = blocks_per_sm_for((const void *)kern);
   const int64_t warps = (int64_t)num_sms * bps * kWarps;
   // Segments: the autotuner's size when it set one, else enough work items for ~8 per
   // resident warp; at most 2^30 items in total.
@@ -458,12 +499,7 @@ cudaError_t launch_eval_kernel(int mode, const EvalArgs &a0, const PopView &pv, 
   int64_t grid = (int64_t)num_sms * bps;
   const int64_t need = (items + kWarps - 1) / kWarps;
   if (grid > need) grid = need;
-  const dim3 g3((unsigned)grid), b3(kThreads);
-  if (bitmap)
-    return a.neg ? launch_maybe_pdl(k_eval_bitmap<true>, g3, b3, 0, s, pdl, a, pv)
-                 : launch_maybe_pdl(k_eval_bitmap<false>, g3, b3, 0, s, pdl, a, pv);
-  return a.neg ? launch_maybe_pdl(k_eval_direct<true>, g3, b3, 0, s, pdl, a, pv)
-               : launch_maybe_pdl(k_eval_direct<false>, g3, b3, 0, s, pdl, a, pv);
+  return launch_maybe_pdl(kern, dim3((unsigned)grid), dim3(kThreads), 0, s, pdl, a, pv);
 }
 
 cudaError_t launch_eval(int mode, const EvalArgs &a, const PopView &pv, int num_sms,
@@ -482,10 +518,14 @@ cudaError_t launch_eval(int mode, const EvalArgs &a, const PopView &pv, int num_
 
 cudaError_t launch_eval_plain(const EvalArgs &a, const int32_t *d_cols, int32_t L, int32_t i,
                               cudaStream_t s) {
+  using PlainKernel = void (*)(EvalArgs, const int32_t *, int, int);
+  static const PlainKernel t[8] = {
+      k_eval_plain<false, false, false>, k_eval_plain<false, false, true>,
+      k_eval_plain<false, true, false>,  k_eval_plain<false, true, true>,
+      k_eval_plain<true, false, false>,  k_eval_plain<true, false, true>,
+      k_eval_plain<true, true, false>,   k_eval_plain<true, true, true>};
+  const PlainKernel k = t[(a.neg ? 4 : 0) + (a.non_strict ? 2 : 0) + (a.last_kept ? 1 : 0)];
   const unsigned grid = (unsigned)((a.R + 255) / 256);
-  if (a.neg)
-    k_eval_plain<true><<<grid, 256, 0, s>>>(a, d_cols, L, i);
-  else
-    k_eval_plain<false><<<grid, 256, 0, s>>>(a, d_cols, L, i);
+  k<<<grid, 256, 0, s>>>(a, d_cols, L, i);
   return cudaGetLastError();
 }

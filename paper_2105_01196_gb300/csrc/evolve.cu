@@ -1096,6 +1096,8 @@ EvalArgs gen_eval_args(ebic_ctx *ctx, GenState *g, int k) {
   a.mv_tmask = g->tcap - 1;
   a.mv_count = reinterpret_cast<unsigned long long *>(&g->ctl.as<GenCtl>()->tabu_count);
   a.neg = g->p.neg_trends;
+  a.non_strict = g->p.non_strict;
+  a.last_kept = g->p.last_kept;
   a.rnum = g->p.ratio_num;
   a.rden = g->p.ratio_den;
   a.min_rows = g->p.min_rows;
@@ -1359,7 +1361,8 @@ int ensure_tabu(ebic_ctx *ctx, GenState *g, int64_t need) {
 }
 
 int ensure_eval_ready(ebic_ctx *ctx, GenState *g, const ebic_params *p, int n_gen) {
-  int mode = choose_mode(ctx, p->mode, g->P, 0.5 * (p->init_min_len + p->max_len), n_gen + 1);
+  int mode = choose_mode(ctx, p->mode, g->P, 0.5 * (p->init_min_len + p->max_len), n_gen + 1,
+                         p->last_kept);
   if (mode == EBIC_MODE_PLAIN) mode = EBIC_MODE_DIRECT;
   if (mode == EBIC_MODE_BITMAP && !ctx->bitmap_ok) EBIC_TRY(ebic_build_bitmap(ctx));
   if (mode != g->eval_mode) g->drop_graphs();

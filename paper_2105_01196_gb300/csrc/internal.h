@@ -73,6 +73,7 @@ struct EvalArgs {
   int64_t R, R_pad, Wst;   // rows, padded rows, words per column pair (R_pad / 32)
   int32_t C;
   int32_t neg, rnum, rden, min_rows, col_cap;
+  int32_t non_strict, last_kept;  // pair-test variants (trend.cuh)
   int32_t *rows_pos, *rows_neg, *rows_any;  // accumulated with atomics (zeroed first)
   uint64_t *fitness;
   int32_t *work;            // dynamic work counter (zeroed first)
@@ -234,7 +235,7 @@ cudaError_t launch_eval_kernel(int mode, const EvalArgs &a, const PopView &pv, i
                                cudaStream_t s, bool pdl = false);
 cudaError_t launch_fitness(const EvalArgs &a, const PopView &pv, cudaStream_t s);
 int choose_mode(const ebic_ctx *ctx, int requested, int64_t n_ind, double mean_len,
-                int expected_sweeps);
+                int expected_sweeps, int last_kept);
 
 // evolve.cu
 void gen_state_free(struct GenState *g);

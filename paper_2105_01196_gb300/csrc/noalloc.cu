@@ -18,6 +18,7 @@
 #include <mutex>
 
 #include "internal.h"
+#include "trend.cuh"
 
 namespace {
 
@@ -84,9 +85,10 @@ __global__ void k_na_validate(const float *__restrict__ x, int64_t total,
   }
 }
 
-// Direct float32 comparisons (strict; -0 equals +0; no FTZ in this file's compilation), one row
-// per lane, warps pulling (individual, segment of 32-row passes) items from sc->work.
-template <bool NEG>
+// Direct float32 comparisons (-0 equals +0; no FTZ in this file's compilation), one row per
+// lane, warps pulling (individual, segment of 32-row passes) items from sc->work.  NS / LK are
+// the pair-test variants of trend.cuh.
+template <bool NEG, bool NS, bool LK>
 __global__ void __launch_bounds__(kNaThreads) k_na_eval(const float *__restrict__ x, int64_t R,
                                                         const int32_t *__restrict__ cols,
                                                         const int32_t *__restrict__ off,
@@ -114,15 +116,10 @@ __global__ void __launch_bounds__(kNaThreads) k_na_eval(const float *__restrict_
     for (int64_t pass = p0; pass < p1; ++pass) {
       const int64_t r = pass * 32 + lane;
       if (r < R) {
-        float prev = __ldg(x + s_base[warp][0] + r);
-        int inc = 0, dec = 0;
-        for (int k = 1; k < L; ++k) {
-          const float cur = __ldg(x + s_base[warp][k] + r);
-          inc += cur > prev;
-          if (NEG) dec += cur < prev;
-          prev = cur;
-        }
-        const bool po = inc >= t, ne = NEG && dec >= t;
+        RowTrend<float, NEG, NS, LK> tr;
+        tr.start(__ldg(x + s_base[warp][0] + r));
+        for (int k = 1; k < L; ++k) tr.step(__ldg(x + s_base[warp][k] + r));
+        const bool po = tr.inc >= t, ne = NEG && tr.dec >= t;
         cp += po;
         cn += ne;
         ca += po || ne;
@@ -186,6 +183,8 @@ extern "C" int ebic_eval_population_noalloc(const float *x, int64_t rows, int32_
   if ((p->neg_trends != 0 && p->neg_trends != 1) || p->col_cap < 0 || p->col_cap > 16 ||
       p->min_rows < 0)
     return fail(msg, msg_len, EBIC_EINVAL, "bad neg_trends, col_cap or min_rows");
+  if ((p->non_strict != 0 && p->non_strict != 1) || (p->last_kept != 0 && p->last_kept != 1))
+    return fail(msg, msg_len, EBIC_EINVAL, "non_strict and last_kept must be 0 or 1");
   if (rows < 1 || rows > (int64_t(1) << 31) - 32 || cols < 2 || cols > 65535)
     return fail(msg, msg_len, EBIC_EINVAL, "need 1 <= rows < 2^31 - 32 and 2 <= cols <= 65535");
   if (n_ind < 0 || n_ind > EBIC_NOALLOC_MAX_IND)
@@ -255,14 +254,17 @@ extern "C" int ebic_eval_population_noalloc(const float *x, int64_t rows, int32_
     }
     int64_t grid = ((int64_t)n_ind * n_seg + kNaWarps - 1) / kNaWarps;
     if (grid > (int64_t)num_sms * 2) grid = (int64_t)num_sms * 2;
-    if (p->neg_trends)
-      k_na_eval<true><<<(unsigned)grid, kNaThreads, 0, s>>>(
-          x, rows, col_idx, offsets, n_ind, (int32_t)n_seg, (int32_t)seg, p->ratio_num,
-          p->ratio_den, sc);
-    else
-      k_na_eval<false><<<(unsigned)grid, kNaThreads, 0, s>>>(
-          x, rows, col_idx, offsets, n_ind, (int32_t)n_seg, (int32_t)seg, p->ratio_num,
-          p->ratio_den, sc);
+    using NaKernel = void (*)(const float *, int64_t, const int32_t *, const int32_t *, int32_t,
+                              int32_t, int32_t, int32_t, int32_t, NoAllocScratch *);
+    static const NaKernel table[8] = {
+        k_na_eval<false, false, false>, k_na_eval<false, false, true>,
+        k_na_eval<false, true, false>,  k_na_eval<false, true, true>,
+        k_na_eval<true, false, false>,  k_na_eval<true, false, true>,
+        k_na_eval<true, true, false>,   k_na_eval<true, true, true>};
+    const NaKernel kern =
+        table[(p->neg_trends ? 4 : 0) + (p->non_strict ? 2 : 0) + (p->last_kept ? 1 : 0)];
+    kern<<<(unsigned)grid, kNaThreads, 0, s>>>(x, rows, col_idx, offsets, n_ind, (int32_t)n_seg,
+                                               (int32_t)seg, p->ratio_num, p->ratio_den, sc);
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     k_na_finish<<<(n_ind + 255) / 256, 256, 0, s>>>(offsets, n_ind, p->min_rows, p->col_cap, sc,
                                                     rows_pos, rows_neg, rows_any, fitness);

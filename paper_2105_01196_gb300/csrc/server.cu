@@ -37,11 +37,13 @@ uint64_t next_pow2(uint64_t v) {
 
 // The evaluation form a job will use: the cost model of ebic_eval_population's AUTO mode.
 int job_mode(int64_t rows, int32_t cols, const ebic_params &p, int32_t n_gen) {
-  if (p.mode == EBIC_MODE_DIRECT || p.mode == EBIC_MODE_BITMAP) return p.mode;
+  if (p.mode != EBIC_MODE_AUTO) return p.mode;
+  if (p.last_kept) return EBIC_MODE_DIRECT;  // no bitmap form
   const double R_pad = (double)round_up(rows, 128), Wst = R_pad / 32.0, C = cols;
   const double mean_len = 0.5 * (p.init_min_len + p.max_len);
   const double sweeps = (double)n_gen + 1.0;
-  const double direct = (double)p.pop_size * mean_len * R_pad / 4.0;
+  const int w = code_bytes_for(cols);
+  const double direct = (double)p.pop_size * mean_len * R_pad * (w ? w : 4) / 16.0;
   const double build = C * C * Wst * 4.0;
   const double eval_bm = (double)p.pop_size * (mean_len - 1.0) * Wst * 2.0;
   return build + sweeps * eval_bm < sweeps * direct ? EBIC_MODE_BITMAP : EBIC_MODE_DIRECT;

@@ -74,6 +74,8 @@ extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_
   EvalArgs a = eval_args_for(ctx);
   a.bitmap = nullptr;
   a.neg = p->neg_trends;
+  a.non_strict = p->non_strict;
+  a.last_kept = p->last_kept;
   a.rnum = p->ratio_num;
   a.rden = p->ratio_den;
   a.min_rows = p->min_rows;
@@ -110,7 +112,9 @@ extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_
     free_b = 0;
   }
   const bool had_bitmap = ctx->bitmap_ok;
-  if (had_bitmap || (double)ebic_bitmap_bytes(ctx->R, ctx->C) < 0.5 * (double)free_b) {
+  // (the last-kept pair test has no bitmap form)
+  if (!p->last_kept &&
+      (had_bitmap || (double)ebic_bitmap_bytes(ctx->R, ctx->C) < 0.5 * (double)free_b)) {
     if (!had_bitmap) {
       cudaEvent_t e0, e1;
       EBIC_CHECK_CUDA(ctx, cudaEventCreate(&e0));
@@ -139,7 +143,7 @@ extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_
   }
   // the staged direct form, when its tiles fit in shared memory
   double best_staged = DBL_MAX;
-  if (ctx->dtma.ok) {
+  if (ctx->dtma.ok && !p->non_strict && !p->last_kept) {  // the staged kernel's pair test
     EBIC_TRY(time_eval(ctx, EBIC_MODE_STAGED, a, pv, 0, &best_staged));
   }
   const int direct_mode = best_staged < best_direct ? EBIC_MODE_STAGED : EBIC_MODE_DIRECT;

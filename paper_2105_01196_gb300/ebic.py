@@ -47,7 +47,8 @@ class Params(ctypes.Structure):
                 ("elite", ctypes.c_int32), ("tournament", ctypes.c_int32),
                 ("max_attempts", ctypes.c_int32), ("tabu_hit_limit", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("mode", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("non_strict", ctypes.c_int32),
+                ("last_kept", ctypes.c_int32)]
 
     @classmethod
     def make(cls, **kw):

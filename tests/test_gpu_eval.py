@@ -29,13 +29,14 @@ def torch_cuda():
     return torch
 
 
-def oparams(neg, num, den, min_rows=2, col_cap=10):
+def oparams(neg, num, den, min_rows=2, col_cap=10, ns=0, lk=0):
     return OParams(neg_trends=neg, ratio_num=num, ratio_den=den, min_rows=min_rows,
-                   col_cap=col_cap)
+                   col_cap=col_cap, non_strict=ns, last_kept=lk)
 
 
-def oracle_eval(x, col_idx, offsets, neg, num, den, sample=None, min_rows=2, col_cap=10):
-    p = oparams(neg, num, den, min_rows, col_cap)
+def oracle_eval(x, col_idx, offsets, neg, num, den, sample=None, min_rows=2, col_cap=10, ns=0,
+                lk=0):
+    p = oparams(neg, num, den, min_rows, col_cap, ns, lk)
     n = len(offsets) - 1
     idx = range(n) if sample is None else sample
     out = {}
@@ -220,4 +221,50 @@ def test_code_width_boundaries(ebic, R, C):
             want = oracle_eval(x, ci, off, neg, num, den)
             for mode in (1, 2, 4):
                 p = ebic.Params.make(neg_trends=neg, ratio_num=num, ratio_den=den, mode=mode)
+                assert_parity(ctx.eval_population(ci, off, p), want)
+
+
+def tie_matrix(g, R, C):
+    x = g.integers(-3, 4, size=(R, C)).astype(np.float32)
+    x[g.random((R, C)) < 0.05] = -0.0
+    x[: R // 10] = 1.5                              # rows of one value
+    return x
+
+
+@pytest.mark.parametrize("R,C", [(200, 20), (700, 129), (300, 1025)])
+def test_trend_variants_all_forms(ebic, R, C):
+    """Ties counting for both directions (non_strict) and counting against the last kept value
+    (last_kept), each form against the oracle: 8-bit codes, 16-bit codes and order keys for the
+    direct form, the bitmap (non_strict only), the plain form; rows not a multiple of 32."""
+    g = np.random.default_rng(R + C)
+    x = tie_matrix(g, R, C)
+    ci, off = ragged_population(g, 40, C)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        for ns, lk in ((1, 0), (0, 1), (1, 1)):
+            for neg, num, den in ((1, 1, 1), (1, 85, 100), (0, 1, 2)):
+                want = oracle_eval(x, ci, off, neg, num, den, ns=ns, lk=lk)
+                for mode in (1, 2, 3, 4, 0):
+                    p = ebic.Params.make(neg_trends=neg, ratio_num=num, ratio_den=den, mode=mode,
+                                         non_strict=ns, last_kept=lk)
+                    if mode == 2 and lk:
+                        with pytest.raises(ebic.EbicError) as e:
+                            ctx.eval_population(ci, off, p)
+                        assert e.value.code == ebic.EBIC_EINVAL
+                        continue
+                    assert_parity(ctx.eval_population(ci, off, p), want)
+
+
+def test_trend_variants_default_workload(ebic):
+    w = synth.WORKLOADS["default"]
+    x, _, ci, off = synth.workload_inputs(w)
+    g = np.random.default_rng(4)
+    sample = sorted(g.choice(len(off) - 1, size=120, replace=False).tolist())
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        for ns, lk in ((1, 0), (0, 1)):
+            want = oracle_eval(x, ci, off, 1, 85, 100, sample=sample, ns=ns, lk=lk)
+            for mode in ((1, 2, 0) if not lk else (1, 0)):
+                p = ebic.Params.make(neg_trends=1, ratio_num=85, ratio_den=100, mode=mode,
+                                     non_strict=ns, last_kept=lk)
                 assert_parity(ctx.eval_population(ci, off, p), want)

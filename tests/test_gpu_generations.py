@@ -56,10 +56,12 @@ def tiny_matrix():
     return x
 
 
-@pytest.mark.parametrize("mode,use_graph", [(1, 1), (2, 1), (2, 0), (4, 1)])
-def test_generation_by_generation(ebic, mode, use_graph):
+@pytest.mark.parametrize("mode,use_graph,ns,lk", [(1, 1, 0, 0), (2, 1, 0, 0), (2, 0, 0, 0),
+                                                  (4, 1, 0, 0), (1, 1, 1, 1), (2, 1, 1, 0),
+                                                  (0, 1, 0, 1)])
+def test_generation_by_generation(ebic, mode, use_graph, ns, lk):
     x = tiny_matrix()
-    gp, op = both_params(ebic, mode=mode, use_graph=use_graph)
+    gp, op = both_params(ebic, mode=mode, use_graph=use_graph, non_strict=ns, last_kept=lk)
     with ebic.Context(0) as ctx:
         ctx.load_matrix(x)
         rep = ctx.run_generations(gp, 0)

@@ -35,8 +35,10 @@ def test_noalloc_matches_regular_entry_point_twice(ebic):
     dev = torch.device("cuda:0")
     stream = torch.cuda.current_stream()
     cases = [make_inputs(1, 3001, 40, 700), make_inputs(2, 130, 70, 3000)]
-    for neg, num, den in ((1, 85, 100), (0, 1, 1)):
-        p = ebic.Params.make(neg_trends=neg, ratio_num=num, ratio_den=den, mode=ebic.MODE_DIRECT)
+    for neg, num, den, ns, lk in ((1, 85, 100, 0, 0), (0, 1, 1, 0, 0), (1, 85, 100, 1, 1),
+                                  (1, 2, 3, 1, 0), (0, 2, 3, 0, 1)):
+        p = ebic.Params.make(neg_trends=neg, ratio_num=num, ratio_den=den, mode=ebic.MODE_DIRECT,
+                             non_strict=ns, last_kept=lk)
         for x, ci, off in cases:
             n = len(off) - 1
             with ebic.Context(0) as ctx:
