@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--workload", default="default")
     ap.add_argument("--gens", type=int, default=None, help="generations per step")
     ap.add_argument("--mode", default="auto", choices=list(MODES))
+    ap.add_argument("--trend", default="strict",
+                    choices=["strict", "ties", "last-kept", "ties-last-kept"],
+                    help="pair test: strict (default), ties holding for both directions, "
+                         "comparison with the last kept value, or both")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -61,6 +65,22 @@ def dist_setup(args):
         backend = "nccl" if torch.cuda.is_available() else "gloo"
         dist.init_process_group(backend)
     return world, rank, local, dist
+
+
+def gens_of(args, w):
+    return w.generations if args.gens is None else args.gens
+
+
+def reduce_over_ranks(dist, total_ms, units, device):
+    """Whole-job timing over the ranks: the slowest rank's time and the sum of all ranks' units
+    (each rank runs an independent job, so nothing else is exchanged)."""
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.barrier()
+    return float(t.item()), float(u.item())
 
 
 def search_quality(ctx, truth, R, C, gens):
@@ -159,12 +179,13 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def cpu_baseline(w, x, ci, off, seconds):
+def cpu_baseline(w, x, ci, off, seconds, trend="strict"):
     """The CPU oracle as it stands, single-threaded, on a bounded sample of the workload: full
     trend counts of the first individuals of the workload's population until `seconds` pass."""
     from oracle import counts as ocounts
     from oracle.params import Params as OParams
-    p = OParams(neg_trends=w.neg_trends, ratio_num=w.ratio[0], ratio_den=w.ratio[1])
+    p = OParams(neg_trends=w.neg_trends, ratio_num=w.ratio[0], ratio_den=w.ratio[1],
+                non_strict=int("ties" in trend), last_kept=int("last-kept" in trend))
     n = len(off) - 1
     t0 = time.perf_counter()
     done = 0
@@ -186,12 +207,12 @@ def run_reference(args, w, world, rank, dist):
     x, _, ci, off = synth.workload_inputs(w)
     per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        cpu_baseline(w, x, ci, off, per_step / 4)
+        cpu_baseline(w, x, ci, off, per_step / 4, args.trend)
     vals = []
     t0 = time.perf_counter()
     last = None
     for _ in range(args.steps):
-        last = cpu_baseline(w, x, ci, off, per_step)
+        last = cpu_baseline(w, x, ci, off, per_step, args.trend)
         vals.append(last["value"])
     total = time.perf_counter() - t0
     v = float(np.median(vals))
@@ -201,7 +222,9 @@ def run_reference(args, w, world, rank, dist):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32-compare/int32",
             "data": "synthetic", "config": {"workload": w.name, "rows": w.rows, "cols": w.cols,
                                              "pop": w.pop, "len": [w.len_lo, w.len_hi],
-                                             "ratio": list(w.ratio), "neg_trends": w.neg_trends},
+                                             "ratio": list(w.ratio), "neg_trends": w.neg_trends,
+                                             "generations": gens_of(args, w), "mode": args.mode,
+                                             "trend": args.trend},
             "cpu_baseline": dict(last, value=v),
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -283,7 +306,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     w = dataclasses.replace(w, seed=w.seed + 7919 * rank)
-    gens = w.generations if args.gens is None else args.gens
+    gens = gens_of(args, w)
     x, truth, ci, off = synth.workload_inputs(w)
     R = w.rows
     x_d = torch.from_numpy(x).to(dev)
@@ -301,7 +324,9 @@ def main():
                               ratio_den=w.ratio[1], pop_size=w.pop, max_len=min(w.len_hi, 64),
                               init_min_len=w.len_lo, init_max_len=min(w.len_hi, 64),
                               n_biclusters=max(10, w.n_bic), elite=max(10, w.n_bic),
-                              tabu_hit_limit=0, seed=w.seed, mode=MODES[args.mode])
+                              tabu_hit_limit=0, seed=w.seed, mode=MODES[args.mode],
+                              non_strict=int("ties" in args.trend),
+                              last_kept=int("last-kept" in args.trend))
     ctx = ebic.Context(local, stream.cuda_stream)
     used_mode = [0]                     # evaluation form the generation loop used
 
@@ -358,13 +383,7 @@ def main():
               ("finish", ebic.KERNEL_FINISH), ("bitmap_build", ebic.KERNEL_BITMAP_BUILD))}
     ctx.profile_enable(False)
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        u = torch.tensor([float(units)], device=dev)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        units = float(u.item())
-        dist.barrier()
+        total_ms, units = reduce_over_ranks(dist, total_ms, units, dev)
 
     e2e = None
     if not args.no_e2e:
@@ -417,6 +436,7 @@ def main():
             "config": {"workload": w.name, "rows": w.rows, "cols": w.cols, "pop": w.pop,
                        "len": [w.len_lo, w.len_hi], "ratio": list(w.ratio),
                        "neg_trends": w.neg_trends, "generations": gens, "mode": args.mode,
+                       "trend": args.trend,
                        "l2": "flushed between steps (512 MB write)",
                        "kernel_stats": "CUDA events around every kernel, on the library's "
                                        "stream, over a second pass of the same K steps",
@@ -430,7 +450,7 @@ def main():
         line["generations_per_s"] = gens * args.steps / (total_ms / 1e3)
         line["quality"] = search_quality(ctx, truth, R, w.cols, gens)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, x, ci, off, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(w, x, ci, off, args.cpu_seconds, args.trend)
     print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
