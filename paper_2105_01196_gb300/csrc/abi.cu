@@ -390,23 +390,10 @@ int ebic_load_matrix(ebic_ctx *ctx, const float *x, int64_t rows, int32_t cols, 
   ctx->R_pad = R_pad;
   ctx->Wst = R_pad / 32;
   direct_tma_prepare(&ctx->dtma, ctx->keys.as<uint32_t>(), R_pad, cols);
-  // per-row rank codes for the direct form (C <= 1,024)
+  // per-row rank codes for the direct form (C <= 1,024), built on the direct form's first use
   ctx->code_bytes = code_bytes_for(cols);
-  ctx->code_stride = 0;
-  if (ctx->code_bytes) {
-    const int64_t S = code_stride_for(rows, ctx->code_bytes);
-    EBIC_CHECK_CUDA(ctx, ctx->codes.ensure((size_t)cols * S * ctx->code_bytes));
-    cudaEvent_t ev = prof_begin(ctx);
-    EBIC_CHECK_CUDA(ctx, launch_rank_codes(ctx->keys.as<uint32_t>(), R_pad, cols, ctx->codes.p,
-                                           ctx->code_bytes, S, ctx->num_sms, ctx->stream));
-    prof_end(ctx, ev, EBIC_KERNEL_RANK_CODES,
-             (double)cols * R_pad * 4.0 + (double)cols * S * ctx->code_bytes,
-             (double)cols * cols * (double)R_pad, (double)R_pad);
-    prof_count(ctx, EBIC_KERNEL_RANK_CODES, 1);
-    EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    prof_collect(ctx);
-    ctx->code_stride = S;
-  }
+  ctx->code_stride = ctx->code_bytes ? code_stride_for(rows, ctx->code_bytes) : 0;
+  ctx->codes_ready = false;
   ctx->have_matrix = true;
   ctx->err.clear();
   return EBIC_OK;
@@ -469,6 +456,7 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
 
   int mode = choose_mode(ctx, p->mode, n_ind, mean_len, 1, p->last_kept);
   if (mode == EBIC_MODE_BITMAP && !ctx->bitmap_ok) EBIC_TRY(ebic_build_bitmap(ctx));
+  if (direct_form_used(ctx, mode, p)) EBIC_TRY(ensure_codes(ctx));
 
   EBIC_CHECK_CUDA(ctx, ctx->ev_out.ensure((size_t)n_ind * 3 * sizeof(int32_t)));
   EBIC_CHECK_CUDA(ctx, ctx->ev_fit.ensure((size_t)n_ind * sizeof(uint64_t)));
@@ -534,6 +522,30 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
 
 }  // extern "C"
 
+int ensure_codes(ebic_ctx *ctx) {
+  if (!ctx->code_bytes || ctx->codes_ready) return EBIC_OK;
+  const int64_t S = ctx->code_stride, C = ctx->C;
+  EBIC_CHECK_CUDA(ctx, ctx->codes.ensure((size_t)C * S * ctx->code_bytes));
+  cudaEvent_t ev = prof_begin(ctx);
+  EBIC_CHECK_CUDA(ctx, launch_rank_codes(ctx->keys.as<uint32_t>(), ctx->R_pad, ctx->C,
+                                         ctx->codes.p, ctx->code_bytes, S, ctx->num_sms,
+                                         ctx->stream));
+  prof_end(ctx, ev, EBIC_KERNEL_RANK_CODES,
+           (double)C * ctx->R_pad * 4.0 + (double)C * S * ctx->code_bytes,
+           (double)C * C * (double)ctx->R_pad, (double)ctx->R_pad);
+  prof_count(ctx, EBIC_KERNEL_RANK_CODES, 1);
+  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  prof_collect(ctx);
+  ctx->codes_ready = true;
+  return EBIC_OK;
+}
+
+int direct_form_used(const ebic_ctx *ctx, int mode, const ebic_params *p) {
+  if (mode == EBIC_MODE_DIRECT) return 1;
+  return mode == EBIC_MODE_STAGED && (!ctx->dtma.ok || p->non_strict || p->last_kept);
+}
+
+
 // Evaluation-kernel choice for EBIC_MODE_AUTO: a cost model in row-words, refined by the
 // autotuner when it has measured this matrix.  The bitmap costs a one-off build of C^2 * Wst
 // words and then (L-1) * Wst words per individual and direction; the direct form gathers
@@ -548,15 +560,15 @@ EvalArgs eval_args_for(const ebic_ctx *ctx) {
   a.C = ctx->C;
   a.err = ctx->d_kerr.as<int32_t>();
   a.dtma = ctx->dtma.ok ? &ctx->dtma : nullptr;
-  a.codes = ctx->code_bytes ? ctx->codes.as<uint8_t>() : nullptr;
-  a.code_bytes = ctx->code_bytes;
-  a.S = ctx->code_stride;
+  a.codes = ctx->codes_ready ? ctx->codes.as<uint8_t>() : nullptr;
+  a.code_bytes = ctx->codes_ready ? ctx->code_bytes : 0;
+  a.S = ctx->codes_ready ? ctx->code_stride : 0;
   return a;
 }
 
 int64_t eval_passes(const ebic_ctx *ctx, int mode) {
   if (mode == EBIC_MODE_BITMAP) return (ctx->Wst + 127) / 128;
-  if (ctx->code_bytes) return ctx->code_stride / code_rows_per_pass(ctx->code_bytes);
+  if (ctx->codes_ready) return ctx->code_stride / code_rows_per_pass(ctx->code_bytes);
   return ctx->R_pad / 128;
 }
 
@@ -566,7 +578,7 @@ double eval_bytes(const ebic_ctx *ctx, int mode, int64_t total_len, int64_t n_in
   // its algorithmic gathers are counted like the key form's)
   if (mode == EBIC_MODE_BITMAP)
     return (double)(total_len - n_ind) * (double)ctx->Wst * 4.0 * (neg ? 2.0 : 1.0);
-  if (mode == EBIC_MODE_DIRECT && ctx->code_bytes)
+  if (mode == EBIC_MODE_DIRECT && ctx->codes_ready)
     return (double)total_len * (double)ctx->code_stride * ctx->code_bytes;
   return (double)total_len * (double)ctx->R_pad * 4.0;
 }

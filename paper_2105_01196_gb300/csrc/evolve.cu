@@ -1365,6 +1365,10 @@ int ensure_eval_ready(ebic_ctx *ctx, GenState *g, const ebic_params *p, int n_ge
                          p->last_kept);
   if (mode == EBIC_MODE_PLAIN) mode = EBIC_MODE_DIRECT;
   if (mode == EBIC_MODE_BITMAP && !ctx->bitmap_ok) EBIC_TRY(ebic_build_bitmap(ctx));
+  if (direct_form_used(ctx, mode, p) && !ctx->codes_ready) {
+    EBIC_TRY(ensure_codes(ctx));
+    g->drop_graphs();  // graphs captured before read the keys
+  }
   if (mode != g->eval_mode) g->drop_graphs();
   g->eval_mode = mode;
   return EBIC_OK;

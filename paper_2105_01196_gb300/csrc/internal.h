@@ -151,10 +151,11 @@ struct ebic_ctx {
   DirectTma dtma;
   DevBuf d_kerr;
 
-  // per-row rank codes of the loaded matrix (code_bytes 0: none)
+  // per-row rank codes of the loaded matrix (code_bytes 0: none), built on first use
   DevBuf codes;
   int code_bytes = 0;
   int64_t code_stride = 0;
+  bool codes_ready = false;
 
   // autotuner decisions for the loaded matrix (tune.cu)
   bool tuned = false;
@@ -186,6 +187,10 @@ void prof_collect(ebic_ctx *ctx);
 
 int ebic_fail(ebic_ctx *ctx, int code, const std::string &msg);
 
+// Builds the rank codes of the loaded matrix if it has some and they are not built yet.
+int ensure_codes(ebic_ctx *ctx);
+// Whether evaluation form `mode` runs the direct kernel (the staged form falls back to it).
+int direct_form_used(const ebic_ctx *ctx, int mode, const ebic_params *p);
 // Evaluation arguments with the loaded matrix's fields set (keys, bitmap, codes, sizes, error
 // word, staged form); the caller sets the trend parameters, outputs and work counter.
 EvalArgs eval_args_for(const ebic_ctx *ctx);

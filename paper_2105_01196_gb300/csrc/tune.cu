@@ -71,6 +71,7 @@ extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_
   EBIC_TRY(stage_population(ctx, col_idx, offsets, n_ind, false, &sp));
   EBIC_CHECK_CUDA(ctx, ctx->ev_out.ensure((size_t)n_ind * 3 * sizeof(int32_t)));
   EBIC_CHECK_CUDA(ctx, ctx->ev_fit.ensure((size_t)n_ind * sizeof(uint64_t)));
+  EBIC_TRY(ensure_codes(ctx));  // the direct form is always measured
   EvalArgs a = eval_args_for(ctx);
   a.bitmap = nullptr;
   a.neg = p->neg_trends;
