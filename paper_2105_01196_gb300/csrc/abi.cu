@@ -335,7 +335,8 @@ int ebic_destroy(ebic_ctx *ctx) {
   gen_state_free(ctx->gen);
   ctx->gen = nullptr;
   DevBuf *bufs[] = {&ctx->keys, &ctx->bitmap, &ctx->stage_x, &ctx->d_err, &ctx->d_work,
-                    &ctx->ev_cols, &ctx->ev_off, &ctx->ev_out, &ctx->ev_fit, &ctx->d_kerr};
+                    &ctx->ev_cols, &ctx->ev_off, &ctx->ev_out, &ctx->ev_fit, &ctx->d_kerr,
+                    &ctx->codes};
   for (DevBuf *b : bufs) b->release();
   prof_collect(ctx);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -365,8 +366,14 @@ int ebic_load_matrix(ebic_ctx *ctx, const float *x, int64_t rows, int32_t cols, 
   ctx->have_matrix = false;
   ctx->bitmap_ok = false;
   ctx->tuned = false;
-  gen_state_free(ctx->gen);
-  ctx->gen = nullptr;
+  // A matrix of the same shape keeps the generation loop's buffers and captured graphs (their
+  // device addresses and sizes stay valid); the run state is cleared before the next run.
+  if (ctx->gen && rows == ctx->R && cols == ctx->C) {
+    gen_mark_reset(ctx->gen);
+  } else {
+    gen_state_free(ctx->gen);
+    ctx->gen = nullptr;
+  }
   const int64_t R_pad = round_up(rows, 128);
   EBIC_CHECK_CUDA(ctx, ctx->keys.ensure((size_t)cols * R_pad * sizeof(uint32_t)));
   const float *src = x;

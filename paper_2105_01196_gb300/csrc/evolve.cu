@@ -984,6 +984,8 @@ struct GenState {
   ebic_params p{};
   int P = 0, K = 0, C = 0, eval_mode = EBIC_MODE_DIRECT;
   bool initialised = false;
+  bool reset_pending = false;          // the run state must be cleared before the next run
+  const void *graph_buf = nullptr;  // codes or bitmap the captured graphs read (null: keys)
   DevBuf cols[2], len[2], att_hits[2], rows[2], att_dead[2], dead[2], hash[2], fit[2];
   DevBuf dkeys[2], dslot[2];
   DevBuf rows_scr, work, tabu, top, ctl, usage, cand_f, cand_h, cand_s, extract;
@@ -1038,6 +1040,11 @@ struct GenState {
 };
 
 void gen_state_free(GenState *g) { delete g; }
+
+void gen_mark_reset(GenState *g) {
+  g->initialised = false;
+  g->reset_pending = true;
+}
 
 namespace {
 
@@ -1253,6 +1260,32 @@ int check_run_params(ebic_ctx *ctx, const ebic_params *p) {
 
 #define GEN_ALLOC(buf, bytes) EBIC_CHECK_CUDA(ctx, (buf).ensure(bytes))
 
+// Clears the run state of g (population, duplicate tables, tabu list, top list, column usage,
+// counters) on the context stream; buffers and graphs stay.
+int gen_reset(ebic_ctx *ctx, GenState *g) {
+  const size_t P = (size_t)g->P;
+  for (int k = 0; k < 2; ++k) {
+    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->cols[k].p, 0, P * kS * 4, ctx->stream));
+    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->len[k].p, 0, P * 4, ctx->stream));
+    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->fit[k].p, 0, P * 8, ctx->stream));
+    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->dkeys[k].p, 0, (size_t)g->dcap * 8, ctx->stream));
+    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->dslot[k].p, 0, (size_t)g->dcap * 4, ctx->stream));
+  }
+  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->rows_scr.p, 0, P * 3 * 4, ctx->stream));
+  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->work.p, 0, 64, ctx->stream));
+  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->usage.p, 0, (size_t)g->C * 4, ctx->stream));
+  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->top.p, 0, (size_t)g->K * sizeof(TopEntry), ctx->stream));
+  if (g->tcap) EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->tabu.p, 0, (size_t)g->tcap * 8, ctx->stream));
+  GenCtl c0{};
+  c0.gen = -1;
+  EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(g->ctl.p, &c0, sizeof(c0), cudaMemcpyHostToDevice,
+                                       ctx->stream));
+  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  g->initialised = false;
+  g->reset_pending = false;
+  return EBIC_OK;
+}
+
 int gen_create(ebic_ctx *ctx, const ebic_params *p) {
   gen_state_free(ctx->gen);
   ctx->gen = nullptr;
@@ -1273,9 +1306,6 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
     GEN_ALLOC(g->dead[k], P);
     GEN_ALLOC(g->hash[k], P * 8);
     GEN_ALLOC(g->fit[k], P * 8);
-    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->cols[k].p, 0, P * kS * 4, ctx->stream));
-    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->len[k].p, 0, P * 4, ctx->stream));
-    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->fit[k].p, 0, P * 8, ctx->stream));
   }
   GEN_ALLOC(g->rows_scr, P * 3 * 4);
   GEN_ALLOC(g->work, 64);
@@ -1283,8 +1313,6 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
   for (int k = 0; k < 2; ++k) {
     GEN_ALLOC(g->dkeys[k], (size_t)g->dcap * 8);
     GEN_ALLOC(g->dslot[k], (size_t)g->dcap * 4);
-    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->dkeys[k].p, 0, (size_t)g->dcap * 8, ctx->stream));
-    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->dslot[k].p, 0, (size_t)g->dcap * 4, ctx->stream));
   }
   g->ccap = next_pow2(P);
   GEN_ALLOC(g->cand_f, (size_t)g->ccap * 8);
@@ -1293,14 +1321,6 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
   GEN_ALLOC(g->top, (size_t)g->K * sizeof(TopEntry));
   GEN_ALLOC(g->ctl, sizeof(GenCtl));
   GEN_ALLOC(g->usage, (size_t)ctx->C * 4);
-  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->rows_scr.p, 0, P * 3 * 4, ctx->stream));
-  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->work.p, 0, 64, ctx->stream));
-  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->usage.p, 0, (size_t)ctx->C * 4, ctx->stream));
-  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->top.p, 0, (size_t)g->K * sizeof(TopEntry), ctx->stream));
-  GenCtl c0{};
-  c0.gen = -1;
-  EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(g->ctl.p, &c0, sizeof(c0), cudaMemcpyHostToDevice,
-                                       ctx->stream));
   const int cw = (ctx->C + 31) / 32;
   g->sort_cap = (int32_t)std::min<uint32_t>(kSortSmemMax, next_pow2(P));
   g->top_smem = (size_t)(g->K + 1) * sizeof(TopEntry) + (size_t)g->sort_cap * 16 +
@@ -1324,8 +1344,7 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
       1, std::min<int64_t>((work + 4 * kTopThreads - 1) / (4 * kTopThreads), ctx->num_sms));
   EBIC_CHECK_CUDA(ctx, cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
   for (cudaEvent_t &e : g->cap_ev) EBIC_CHECK_CUDA(ctx, cudaEventCreate(&e));
-  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  return EBIC_OK;
+  return gen_reset(ctx, g);
 }
 
 int read_ctl(ebic_ctx *ctx, GenState *g, GenCtl *out) {
@@ -1365,11 +1384,15 @@ int ensure_eval_ready(ebic_ctx *ctx, GenState *g, const ebic_params *p, int n_ge
                          p->last_kept);
   if (mode == EBIC_MODE_PLAIN) mode = EBIC_MODE_DIRECT;
   if (mode == EBIC_MODE_BITMAP && !ctx->bitmap_ok) EBIC_TRY(ebic_build_bitmap(ctx));
-  if (direct_form_used(ctx, mode, p) && !ctx->codes_ready) {
-    EBIC_TRY(ensure_codes(ctx));
-    g->drop_graphs();  // graphs captured before read the keys
+  const bool direct = direct_form_used(ctx, mode, p);
+  if (direct) EBIC_TRY(ensure_codes(ctx));
+  // the captured graphs hold the evaluation kernel's data buffer: recapture when it changed
+  const void *buf = mode == EBIC_MODE_BITMAP ? ctx->bitmap.p
+                    : (direct && ctx->codes_ready ? ctx->codes.p : nullptr);
+  if (mode != g->eval_mode || buf != g->graph_buf) {
+    g->drop_graphs();
+    g->graph_buf = buf;
   }
-  if (mode != g->eval_mode) g->drop_graphs();
   g->eval_mode = mode;
   return EBIC_OK;
 }
@@ -1433,6 +1456,8 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
   if (!g || !same_run_params(g->p, *p)) {
     EBIC_TRY(gen_create(ctx, p));
     g = ctx->gen;
+  } else if (g->reset_pending) {
+    EBIC_TRY(gen_reset(ctx, g));
   }
   g->p.mode = p->mode;
   g->p.use_graph = p->use_graph;

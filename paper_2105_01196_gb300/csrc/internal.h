@@ -244,3 +244,5 @@ int choose_mode(const ebic_ctx *ctx, int requested, int64_t n_ind, double mean_l
 
 // evolve.cu
 void gen_state_free(struct GenState *g);
+// Ends the current run: the state is cleared before the next run, buffers and graphs stay.
+void gen_mark_reset(struct GenState *g);

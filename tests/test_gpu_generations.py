@@ -158,3 +158,24 @@ def test_run_parameter_errors(ebic):
             with pytest.raises(ebic.EbicError) as e:
                 ctx.run_generations(gp, 1)
             assert e.value.code == ebic.EBIC_EINVAL
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_same_shape_reload_starts_a_fresh_run(ebic, mode):
+    """Loading a matrix of the same shape keeps the loop's buffers and graphs but starts a new run:
+    each run equals the oracle's run on its own matrix, and nothing of the previous run is left."""
+    x1 = tiny_matrix()
+    x2, _ = synth.planted_matrix(x1.shape[0], x1.shape[1], 2, (30, 30), (5, 5), seed=99,
+                                 neg_fraction=0.5)
+    gp, op = both_params(ebic, mode=mode)
+    with ebic.Context(0) as ctx:
+        for x in (x1, x2, x1):
+            ctx.load_matrix(x)
+            with pytest.raises(ebic.EbicError) as e:
+                ctx.toplist()                        # no run on this matrix yet
+            assert e.value.code == ebic.EBIC_ESTATE
+            rep = ctx.run_generations(gp, 8)
+            st = oebic.run(x, op, 8)
+            assert rep.gens_done == st.gen == 8
+            assert rep.n_evaluated == st.n_evaluated
+            assert_same_state(ctx, st, gp)
