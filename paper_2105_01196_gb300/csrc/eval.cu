@@ -14,10 +14,12 @@
 //   plain   one kernel launch per individual, one row per thread (the reference GPU form).
 // The direct and bitmap kernels are persistent: warps pull (individual, row segment) work items
 // from an atomic counter, segment-major (every individual of a row segment before the next
-// segment, so the segment's data stays in L2 while all individuals read it), and add their
-// partial counts with one atomic per item.
+// segment, so the segment's data stays in L2 while all individuals read it), then the chunks of
+// the generation loop's side task (items.cuh), and add their partial counts with one atomic per
+// item.
 #include "internal.h"
 #include "tables.cuh"
+#include "items.cuh"
 #include "trend.cuh"
 
 namespace {
@@ -30,10 +32,6 @@ __device__ __forceinline__ int threshold(int L, int num, int den) {
   return (num * (L - 1) + den - 1) / den;
 }
 
-__device__ __forceinline__ int pv_start(const PopView &v, int i) {
-  return v.off ? v.off[i] : i * v.stride;
-}
-
 __device__ __forceinline__ int pv_len(const PopView &v, int i) {
   return v.off ? (v.off[i + 1] - v.off[i]) : v.len[i];
 }
@@ -44,20 +42,8 @@ __device__ __forceinline__ bool pv_dead(const PopView &v, int i) {
   return false;
 }
 
-// The generation loop's side task (see EvalArgs): move a duplicate table into the tabu list.
-__device__ __forceinline__ void move_keys(const EvalArgs &a) {
-  if (a.mv_keys) move_table_keys(a.mv_keys, a.mv_slots, a.mv_n, a.mv_table, a.mv_tmask, a.mv_count);
-}
-
 // Waits for the preceding kernel of a programmatic launch (no-op otherwise).
 __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-// Next work item of a warp (lane 0 takes it from the counter).
-__device__ __forceinline__ int next_item(int32_t *work, int lane) {
-  int q = 0;
-  if (lane == 0) q = atomicAdd(work, 1);
-  return __shfl_sync(kFull, q, 0);
-}
 
 __device__ __forceinline__ uint4 ldg4(const uint32_t *p) {
   return __ldg(reinterpret_cast<const uint4 *>(p));
@@ -87,23 +73,27 @@ __global__ void k_validate_csr(const int32_t *__restrict__ cols, const int32_t *
 // the last value kept).  With ties counting, the pad rows past R (key 0 everywhere) would pass,
 // so they are masked out.
 template <bool NEG, bool NS, bool LK>
-__global__ void __launch_bounds__(kThreads) k_eval_direct(EvalArgs a, PopView pv) {
+__global__ void __launch_bounds__(kThreads, 4) k_eval_direct(EvalArgs a, PopView pv) {
   __shared__ int64_t s_base[kWarps][EBIC_MAX_LEN];
   wait_prior_grid();
-  if (pv.stop && *pv.stop) return;
-  move_keys(a);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t passes_total = a.R_pad / 128;
-  const int32_t n_items = pv.n * a.n_seg;
-  for (;;) {
-    const int q = next_item(a.work, lane);
-    if (q >= n_items) break;
+  const int32_t n_items = pv.n * a.n_seg, n_all = n_items + items::move_chunks(a);
+  int q = items::first(a.work, pv, lane);
+  if (q < 0) return;  // the run has stopped
+  for (; q < n_all; q = items::next(a.work, lane)) {
+    if (q >= n_items) {
+      items::move_chunk(a, q - n_items, lane);
+      continue;
+    }
     const int seg = q / pv.n, i = q - seg * pv.n;  // segment-major
-    if (pv_dead(pv, i)) continue;
-    const int L = pv_len(pv, i), st = pv_start(pv, i);
-    if (L < 2) continue;
+    const items::Meta m = items::load_meta(pv, i, lane);
+    if (m.dead || m.L < 2) continue;
+    const items::Probe pr = items::probe_start(pv, m.h);
+    const int L = m.L;
     __syncwarp();
-    for (int k = lane; k < L; k += 32) s_base[warp][k] = (int64_t)pv.cols[st + k] * a.R_pad;
+    s_base[warp][lane] = (int64_t)m.c0 * a.R_pad;
+    s_base[warp][lane + 32] = (int64_t)m.c1 * a.R_pad;
     __syncwarp();
     const int t = threshold(L, a.rnum, a.rden);
     const int64_t p0 = (int64_t)seg * a.seg_passes;
@@ -134,6 +124,7 @@ __global__ void __launch_bounds__(kThreads) k_eval_direct(EvalArgs a, PopView pv
         ca += po | ne;
       }
     }
+    if (items::is_dup(pv, pr, m.h, i)) continue;  // a lower slot scores this key
     cp = __reduce_add_sync(kFull, cp);
     cn = __reduce_add_sync(kFull, cn);
     ca = __reduce_add_sync(kFull, ca);
@@ -237,25 +228,31 @@ template <bool NEG, bool NS>
 __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView pv) {
   __shared__ int64_t s_pos[kWarps][EBIC_MAX_LEN];
   __shared__ int64_t s_neg[kWarps][EBIC_MAX_LEN];
+  __shared__ int32_t s_col[kWarps][EBIC_MAX_LEN];
   wait_prior_grid();
-  if (pv.stop && *pv.stop) return;
-  move_keys(a);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t Wst = a.Wst;
   const int64_t passes_total = (Wst + 127) / 128;
-  const int32_t n_items = pv.n * a.n_seg;
+  const int32_t n_items = pv.n * a.n_seg, n_all = n_items + items::move_chunks(a);
   const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-  for (;;) {
-    const int q = next_item(a.work, lane);
-    if (q >= n_items) break;
+  int q = items::first(a.work, pv, lane);
+  if (q < 0) return;  // the run has stopped
+  for (; q < n_all; q = items::next(a.work, lane)) {
+    if (q >= n_items) {
+      items::move_chunk(a, q - n_items, lane);
+      continue;
+    }
     const int seg = q / pv.n, i = q - seg * pv.n;  // segment-major
-    if (pv_dead(pv, i)) continue;
-    const int L = pv_len(pv, i), st = pv_start(pv, i);
-    if (L < 2) continue;
-    const int np = L - 1;
+    const items::Meta m = items::load_meta(pv, i, lane);
+    if (m.dead || m.L < 2) continue;
+    const items::Probe pr = items::probe_start(pv, m.h);
+    const int L = m.L, np = L - 1;
+    __syncwarp();
+    s_col[warp][lane] = m.c0;
+    s_col[warp][lane + 32] = m.c1;
     __syncwarp();
     for (int k = lane; k < np; k += 32) {
-      const int64_t c = pv.cols[st + k], d = pv.cols[st + k + 1];
+      const int64_t c = s_col[warp][k], d = s_col[warp][k + 1];
       s_pos[warp][k] = NS ? (d * a.C + c) * Wst : (c * a.C + d) * Wst;
       s_neg[warp][k] = NS ? (c * a.C + d) * Wst : (d * a.C + c) * Wst;
     }
@@ -351,6 +348,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
         ca += popc4(pos);
       }
     }
+    if (items::is_dup(pv, pr, m.h, i)) continue;  // a lower slot scores this key
     cp = __reduce_add_sync(kFull, cp);
     cn = __reduce_add_sync(kFull, cn);
     ca = __reduce_add_sync(kFull, ca);

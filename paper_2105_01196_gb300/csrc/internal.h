@@ -79,9 +79,10 @@ struct EvalArgs {
   int32_t *work;            // dynamic work counter (zeroed first)
   int32_t seg_passes;       // passes (of 128 words or 128 rows) per work item
   int32_t n_seg;            // segments per individual
-  // Optional side task of the generation loop, done by the launch's threads before their
-  // evaluation work: the keys of table mv_keys (mv_n slots, cleared afterwards, slot words
-  // mv_slots) join the hashed tabu list mv_table; new keys are counted in *mv_count.
+  // Optional side task of the generation loop, done by the launch's warps after the evaluation
+  // items (the staged kernel: before them): the keys of table mv_keys (mv_n slots, cleared
+  // afterwards, slot words mv_slots) join the hashed tabu list mv_table; new keys are counted
+  // in *mv_count.
   uint64_t *mv_keys;
   uint32_t *mv_slots;
   uint32_t mv_n;

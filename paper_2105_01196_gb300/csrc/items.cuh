@@ -1,0 +1,121 @@
+// Work items of the persistent evaluation kernels (eval.cu, codes.cu).
+//
+// Warps take items from one atomic counter: first the (individual, row segment) evaluation items,
+// segment-major, then - in the generation loop - the chunks of its side task, the move of the
+// previous generation's duplicate table into the tabu list.  Taking the side task last lets it
+// run in the shadow of the warps still evaluating instead of delaying every warp's first item.
+//
+// The per-item bookkeeping is arranged so that its loads leave in as few dependent round trips as
+// possible: length, start, dead flag, hash and (for the generation loop's fixed-stride rows) the
+// 64 column words are loaded together, and the first probe of the duplicate table is issued
+// before the evaluation loads and checked after them.
+#pragma once
+
+#include "internal.h"
+#include "tables.cuh"
+
+namespace items {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Number of side-task chunks (32 table slots each).
+__device__ __forceinline__ int move_chunks(const EvalArgs &a) {
+  return a.mv_keys ? (int)((a.mv_n + 31u) / 32u) : 0;
+}
+
+// One side-task chunk: slot 32 m + lane of table mv_keys joins the tabu list and is cleared.
+__device__ __forceinline__ void move_chunk(const EvalArgs &a, int m, int lane) {
+  const uint32_t idx = (uint32_t)m * 32u + (uint32_t)lane;
+  unsigned added = 0u;
+  if (idx < a.mv_n) {
+    const uint64_t k = a.mv_keys[idx];
+    if (k) {
+      added = tabu_insert(a.mv_table, a.mv_tmask, k) ? 1u : 0u;
+      a.mv_keys[idx] = 0ull;
+      a.mv_slots[idx] = 0u;
+    }
+  }
+  added = __reduce_add_sync(kFull, added);
+  if (lane == 0 && added) atomicAdd(a.mv_count, (unsigned long long)added);
+}
+
+// The next item of the warp (lane 0 takes it from the counter).
+__device__ __forceinline__ int next(int32_t *work, int lane) {
+  int q = 0;
+  if (lane == 0) q = atomicAdd(work, 1);
+  return __shfl_sync(kFull, q, 0);
+}
+
+// First item, fetched together with the stop flag; returns -1 when the run has stopped.
+__device__ __forceinline__ int first(int32_t *work, const PopView &pv, int lane) {
+  int q = 0;
+  if (lane == 0) q = atomicAdd(work, 1);
+  const bool stopped = pv.stop && *pv.stop;
+  q = __shfl_sync(kFull, q, 0);
+  return stopped ? -1 : q;
+}
+
+struct Meta {
+  int st, L;     // start in cols, length
+  bool dead;     // tabu-dead slot (never scored)
+  uint64_t h;    // key (duplicate check), 0 when there is no duplicate table
+  int c0, c1;    // columns k = lane and k = lane + 32 (0 past the length)
+};
+
+// One individual's bookkeeping.  The generation loop's rows have a fixed stride of 64 columns,
+// so their column words load in the same round trip as the length.
+__device__ __forceinline__ Meta load_meta(const PopView &pv, int i, int lane) {
+  Meta m;
+  if (pv.off) {
+    m.st = pv.off[i];
+    m.L = pv.off[i + 1] - m.st;
+  } else {
+    m.st = i * pv.stride;
+    m.L = pv.len[i];
+  }
+  m.dead = pv.dead && pv.dead[i];
+  m.h = pv.dkeys ? pv.hash[i] : 0ull;
+  if (!pv.off) {
+    m.c0 = pv.cols[m.st + lane];
+    m.c1 = pv.cols[m.st + 32 + lane];
+    if (lane >= m.L) m.c0 = 0;
+    if (lane + 32 >= m.L) m.c1 = 0;
+  } else {
+    m.c0 = lane < m.L ? pv.cols[m.st + lane] : 0;
+    m.c1 = lane + 32 < m.L ? pv.cols[m.st + 32 + lane] : 0;
+  }
+  return m;
+}
+
+// First probe of the duplicate table for key h (loaded ahead, finished by is_dup).
+struct Probe {
+  uint64_t k0;
+  uint32_t s0, idx0;
+};
+
+__device__ __forceinline__ Probe probe_start(const PopView &pv, uint64_t h) {
+  Probe p{0ull, 0u, 0u};
+  if (pv.dkeys) {
+    p.idx0 = table_index(h, pv.dmask);
+    p.k0 = pv.dkeys[p.idx0];
+    p.s0 = pv.dslot[p.idx0];
+  }
+  return p;
+}
+
+// True when a lower slot than s produced key h this generation (same rule as dedup_is_dup).
+__device__ __forceinline__ bool is_dup(const PopView &pv, const Probe &p, uint64_t h, int s) {
+  if (!pv.dkeys) return false;
+  if (p.k0 == h) return p.s0 != 0xFFFFFFFFu - (uint32_t)s;
+  if (p.k0 == 0ull) return false;
+  uint32_t i = (p.idx0 + 1u) & pv.dmask;
+  for (uint32_t n = 1; n <= pv.dmask; ++n) {
+    const uint64_t k = pv.dkeys[i];
+    if (k == h) return pv.dslot[i] != 0xFFFFFFFFu - (uint32_t)s;
+    if (k == 0ull) return false;
+    i = (i + 1u) & pv.dmask;
+  }
+  return false;
+}
+
+}  // namespace items
