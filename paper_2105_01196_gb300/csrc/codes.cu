@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_eval_codes(EvalArgs a, PopView 
     const items::Meta m = items::load_meta(pv, i, lane);
     const int L = m.dead ? 0 : m.L;
     if (L >= 2) {
-      const items::Probe pr = items::probe_start(pv, m.h);
+      const items::Insert ins = items::insert_start(pv, seg, m.h, lane);
       __syncwarp();
       s_base[warp][lane] = (int64_t)m.c0 * a.S * W;
       s_base[warp][lane + 32] = (int64_t)m.c1 * a.S * W;
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_eval_codes(EvalArgs a, PopView 
         }
       }
       if (!NEG) ca = cp;
-      if (items::is_dup(pv, pr, m.h, i)) continue;  // a lower slot scores this key
+      items::insert_finish(pv, ins, m.h, i);
       cp = __reduce_add_sync(kFull, cp);
       cn = __reduce_add_sync(kFull, cn);
       ca = __reduce_add_sync(kFull, ca);

@@ -84,8 +84,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ int32_t s_base[kWarps][EBIC_MAX_LEN];
   asm volatile("griddepcontrol.wait;" ::: "memory");
   if (pv.stop && *pv.stop) return;
-  // the generation loop's side task: the previous generation's keys join the tabu list
+  // the generation loop's side tasks: the previous generation's keys join the tabu list, and
+  // this generation's live keys enter its duplicate table (tested after the launch)
   if (a.mv_keys) move_table_keys(a.mv_keys, a.mv_slots, a.mv_n, a.mv_table, a.mv_tmask, a.mv_count);
+  if (pv.dkeys)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < pv.n; i += gridDim.x * blockDim.x)
+      if (!(pv.dead && pv.dead[i])) dedup_insert(pv.dkeys, pv.dslot, pv.dmask, pv.hash[i], i);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n_items = sa.n_tiles * sa.n_groups;
   const uint32_t stage_bytes = (uint32_t)sa.stage_words * 4u;
@@ -130,7 +134,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int i0 = grp * sa.group_size, i1 = min(pv.n, i0 + sa.group_size);
     for (int i = i0 + warp; i < i1; i += kWarps) {
       if (pv.dead && pv.dead[i]) continue;
-      if (pv.dkeys && dedup_is_dup(pv.dkeys, pv.dslot, pv.dmask, pv.hash[i], i)) continue;
       const int st = pv.off ? pv.off[i] : i * pv.stride;
       const int L = pv.off ? pv.off[i + 1] - st : pv.len[i];
       if (L < 2) continue;

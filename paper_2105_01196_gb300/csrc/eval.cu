@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_eval_direct(EvalArgs a, PopView
     const int seg = q / pv.n, i = q - seg * pv.n;  // segment-major
     const items::Meta m = items::load_meta(pv, i, lane);
     if (m.dead || m.L < 2) continue;
-    const items::Probe pr = items::probe_start(pv, m.h);
+    const items::Insert ins = items::insert_start(pv, seg, m.h, lane);
     const int L = m.L;
     __syncwarp();
     s_base[warp][lane] = (int64_t)m.c0 * a.R_pad;
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_eval_direct(EvalArgs a, PopView
         ca += po | ne;
       }
     }
-    if (items::is_dup(pv, pr, m.h, i)) continue;  // a lower slot scores this key
+    items::insert_finish(pv, ins, m.h, i);
     cp = __reduce_add_sync(kFull, cp);
     cn = __reduce_add_sync(kFull, cn);
     ca = __reduce_add_sync(kFull, ca);
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
     const int seg = q / pv.n, i = q - seg * pv.n;  // segment-major
     const items::Meta m = items::load_meta(pv, i, lane);
     if (m.dead || m.L < 2) continue;
-    const items::Probe pr = items::probe_start(pv, m.h);
+    const items::Insert ins = items::insert_start(pv, seg, m.h, lane);
     const int L = m.L, np = L - 1;
     __syncwarp();
     s_col[warp][lane] = m.c0;
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
         ca += popc4(pos);
       }
     }
-    if (items::is_dup(pv, pr, m.h, i)) continue;  // a lower slot scores this key
+    items::insert_finish(pv, ins, m.h, i);
     cp = __reduce_add_sync(kFull, cp);
     cn = __reduce_add_sync(kFull, cn);
     ca = __reduce_add_sync(kFull, ca);

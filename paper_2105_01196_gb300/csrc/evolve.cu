@@ -201,9 +201,7 @@ __global__ void __launch_bounds__(kSlotThreads) k_init(GenArgs ga, Buf nb) {
   const bool dead = L < 2;
   nb.att_dead[s] = dead;
   nb.att_hits[s] = 0;
-  const uint64_t h = chromosome_key(c, L);
-  nb.hash[s] = h;
-  if (!dead) dedup_insert(ga.dkeys[0], ga.dslot[0], ga.dmask, h, s);
+  nb.hash[s] = chromosome_key(c, L);  // (the scoring launch enters live keys in the table)
 }
 
 // ------------------------------------------------------------------ warp-cooperative children
@@ -234,7 +232,7 @@ __device__ int w_draw_free(WordStream &st, int C, const int32_t *c, int L, int l
 // that the winner's chromosome is copied to `win` without another trip to global memory.  Same
 // winner as the sequential rule (exact penalised comparison, ties to the lower slot).
 __device__ int w_tournament(WordStream &st, const GenArgs &ga, const Buf &pb, int32_t *scratch,
-                            int32_t *win, int *win_len, int lane) {
+                            int32_t *win, int *win_len, int lane, const int32_t *usage) {
   int best = -1, ub = 0, bl = 0;
   uint64_t fb = 0ull;
   const int mine = lane >> 2, sub = lane & 3;
@@ -260,8 +258,8 @@ __device__ int w_tournament(WordStream &st, const GenArgs &ga, const Buf &pb, in
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const int k = 4 * (sub + 4 * r);
-        const int u0 = k < L ? ga.usage[v[r].x] : 0, u1 = k + 1 < L ? ga.usage[v[r].y] : 0;
-        const int u2 = k + 2 < L ? ga.usage[v[r].z] : 0, u3 = k + 3 < L ? ga.usage[v[r].w] : 0;
+        const int u0 = k < L ? usage[v[r].x] : 0, u1 = k + 1 < L ? usage[v[r].y] : 0;
+        const int u2 = k + 2 < L ? usage[v[r].z] : 0, u3 = k + 3 < L ? usage[v[r].w] : 0;
         u += u0 + u1 + u2 + u3;
         row4[sub + 4 * r] = v[r];
       }
@@ -295,6 +293,98 @@ __device__ int w_tournament(WordStream &st, const GenArgs &ga, const Buf &pb, in
   }
   *win_len = bl;
   return best;
+}
+
+// Both tournaments of a child when 2 T <= 8: the first one's T candidates, the crossover word and
+// the second one's T candidates are drawn in stream order (the second set from a copy of the
+// stream, adopted only when the crossover happens), and all candidates' data arrive in one round
+// of loads.  Same winners as two calls of w_tournament.  Returns whether the crossover happens.
+__device__ bool w_tournament_pair(WordStream &st, const GenArgs &ga, const Buf &pb,
+                                  int32_t *scratch, int32_t *A, int *LA, int32_t *B, int *LB,
+                                  int lane, const int32_t *usage) {
+  const int T = ga.T;
+  int ids[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) ids[q] = -1;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (q < T) ids[q] = (int)st.below((uint32_t)ga.P);
+  const bool cross = st.next() < (1u << 30);  // one-point crossover, probability 1/4
+  WordStream st2 = st;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (q >= T && q < 2 * T) ids[q] = (int)st2.below((uint32_t)ga.P);
+  if (cross) st = st2;
+  const int mine = lane >> 2, sub = lane & 3;
+  int my = -1;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (q == mine) my = ids[q];
+  if (!cross && mine >= T) my = -1;  // the second set is not needed
+  uint64_t f = 0ull;
+  int u = 0, L = 0;
+  if (my >= 0) {
+    const int4 *cc4 = reinterpret_cast<const int4 *>(pb.cols + (size_t)my * kS);
+    L = pb.len[my];
+    f = pb.fit[my];
+    int4 v[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) v[r] = cc4[sub + 4 * r];
+    int4 *row4 = reinterpret_cast<int4 *>(scratch + mine * kS);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int k = 4 * (sub + 4 * r);
+      const int u0 = k < L ? usage[v[r].x] : 0, u1 = k + 1 < L ? usage[v[r].y] : 0;
+      const int u2 = k + 2 < L ? usage[v[r].z] : 0, u3 = k + 3 < L ? usage[v[r].w] : 0;
+      u += u0 + u1 + u2 + u3;
+      row4[sub + 4 * r] = v[r];
+    }
+  }
+  u += __shfl_xor_sync(kFull, u, 1);
+  u += __shfl_xor_sync(kFull, u, 2);
+  __syncwarp();
+  // the winner of each set, as in w_tournament (exact penalised comparison, ties to the lower slot)
+  int best0 = -1, take0 = 0, bl0 = 0, ub0 = 0, best1 = -1, take1 = 0, bl1 = 0, ub1 = 0;
+  uint64_t fb0 = 0ull, fb1 = 0ull;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const uint64_t fq = __shfl_sync(kFull, f, q * 4);
+    const int uq = __shfl_sync(kFull, u, q * 4);
+    const int lq = __shfl_sync(kFull, L, q * 4);
+    const int iq = ids[q];
+    if (iq < 0) continue;
+    if (q < T) {
+      const int c = best0 < 0 ? 1 : cmp_penalised(fq, uq, fb0, ub0);
+      if (c > 0 || (c == 0 && iq < best0)) {
+        best0 = iq;
+        fb0 = fq;
+        ub0 = uq;
+        bl0 = lq;
+        take0 = q;
+      }
+    } else if (cross) {
+      const int c = best1 < 0 ? 1 : cmp_penalised(fq, uq, fb1, ub1);
+      if (c > 0 || (c == 0 && iq < best1)) {
+        best1 = iq;
+        fb1 = fq;
+        ub1 = uq;
+        bl1 = lq;
+        take1 = q;
+      }
+    }
+  }
+  const int32_t *ra = scratch + take0 * kS;
+  A[lane] = ra[lane];
+  A[lane + 32] = ra[lane + 32];
+  *LA = bl0;
+  if (cross) {
+    const int32_t *rb = scratch + take1 * kS;
+    B[lane] = rb[lane];
+    B[lane + 32] = rb[lane + 32];
+    *LB = bl1;
+  }
+  __syncwarp();
+  return cross;
 }
 
 __device__ void w_copy(int32_t *c, const int32_t *src, int L, int lane) {
@@ -362,12 +452,19 @@ __device__ void w_mutate(WordStream &st, int32_t *c, int &L, int C, int max_len,
 }
 
 __device__ void w_make_child(const GenArgs &ga, const Buf &pb, int g, int s, int a, int32_t *c,
-                             int32_t *scratch, int32_t *A, int32_t *B, int &L, int lane) {
+                             int32_t *scratch, int32_t *A, int32_t *B, int &L, int lane,
+                             const int32_t *usage) {
   WordStream st(ga.seed, (uint32_t)g, (uint32_t)s, (uint32_t)a);
   int LA = 0, LB = 0;
-  w_tournament(st, ga, pb, scratch, A, &LA, lane);
-  if (st.next() < (1u << 30)) {  // one-point crossover, probability 1/4
-    w_tournament(st, ga, pb, scratch, B, &LB, lane);
+  bool cross;
+  if (2 * ga.T <= 8) {
+    cross = w_tournament_pair(st, ga, pb, scratch, A, &LA, B, &LB, lane, usage);
+  } else {
+    w_tournament(st, ga, pb, scratch, A, &LA, lane, usage);
+    cross = st.next() < (1u << 30);  // one-point crossover, probability 1/4
+    if (cross) w_tournament(st, ga, pb, scratch, B, &LB, lane, usage);
+  }
+  if (cross) {
     // (the min() guards only matter for a chromosome shorter than 2, which is never built)
     const int cut1 = min(1 + (int)st.below((uint32_t)(LA - 1)), max(LA, 1));
     const int cut2 = min(1 + (int)st.below((uint32_t)(LB - 1)), LB);
@@ -408,18 +505,34 @@ constexpr int kMaxAttemptWarps = 16;
 // 16-byte stores), and the total is a multiple of 16 bytes.
 constexpr int kEvoScratch = 0, kEvoA = 8 * kS, kEvoB = 9 * kS, kEvoChild = 10 * kS;
 constexpr int kEvolveWarpInts = 10 * kS + kS + 4;
+// Matrices of up to this many columns have k_evolve's column-usage table in shared memory.
+constexpr int kUsageSmemMax = 4096;
+
+// Dynamic shared memory of a k_evolve launch with G warps.
+size_t evolve_smem(int G, int C) {
+  return (size_t)G * kEvolveWarpInts * 4 + (C <= kUsageSmemMax ? (size_t)(C + 3) / 4 * 16 : 0);
+}
 static_assert(kEvolveWarpInts % 4 == 0, "per-warp region must keep 16-byte alignment");
 
 __global__ void __launch_bounds__(kMaxAttemptWarps * 32) k_evolve(GenArgs ga, Buf pb, Buf nb,
                                                                   int par) {
-  extern __shared__ __align__(16) int32_t s_evo[];  // kEvolveWarpInts per warp
+  extern __shared__ __align__(16) int32_t s_evo[];  // kEvolveWarpInts per warp, then usage
   __shared__ int s_ok[kMaxAttemptWarps];
   wait_prior_grid();
-  if (ga.ctl->stopped) return;
+  const int stopped = ga.ctl->stopped, gen = ga.ctl->gen, n_top = ga.ctl->n_top;
+  // the column-usage table goes to shared memory (its loads leave with the counters' loads)
+  const int32_t *usage = ga.usage;
+  if (ga.C <= kUsageSmemMax) {
+    int32_t *s_usage = s_evo + (blockDim.x >> 5) * kEvolveWarpInts;
+    for (int c = threadIdx.x; c < ga.C; c += blockDim.x) s_usage[c] = ga.usage[c];
+    usage = s_usage;
+  }
+  if (stopped) return;
+  __syncthreads();
   const int lane = threadIdx.x & 31, a = threadIdx.x >> 5;
   const int s = blockIdx.x;
-  const int g = ga.ctl->gen + 1;
-  const int n_el = min(ga.E, ga.ctl->n_top);
+  const int g = gen + 1;
+  const int n_el = min(ga.E, n_top);
   int32_t *out = nb.cols + (size_t)s * kS;
   if (s < n_el) {  // elitism: copy top-list entry s (its key is already in the tabu list)
     if (a == 0) {
@@ -442,7 +555,7 @@ __global__ void __launch_bounds__(kMaxAttemptWarps * 32) k_evolve(GenArgs ga, Bu
   uint64_t h = 0ull;
   int ok = 0;
   if (a < ga.A) {
-    w_make_child(ga, pb, g, s, a, c, scratch, A, B, L, lane);
+    w_make_child(ga, pb, g, s, a, c, scratch, A, B, L, lane, usage);
     h = chromosome_key(c, L);
     // lane 0 probes the hashed tabu list, lane 1 generation g-1's live keys
     const bool hit = (lane == 0 && tabu_contains(ga.tabu, ga.tmask, h)) ||
@@ -466,8 +579,7 @@ __global__ void __launch_bounds__(kMaxAttemptWarps * 32) k_evolve(GenArgs ga, Bu
     nb.len[s] = L;
     nb.hash[s] = h;
     nb.att_dead[s] = dead;
-    nb.att_hits[s] = dead ? ga.A : win;
-    if (!dead) dedup_insert(ga.dkeys[par], ga.dslot[par], ga.dmask, h, s);
+    nb.att_hits[s] = dead ? ga.A : win;  // (the evaluation launch enters live keys in D[par])
   }
 }
 
@@ -791,9 +903,9 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
     ga.rows_scr[s] = 0;
     ga.rows_scr[ga.P + s] = 0;
     ga.rows_scr[2 * ga.P + s] = 0;
-    nb.rows[s] = rp;
-    nb.rows[ga.P + s] = rn;
-    nb.rows[2 * ga.P + s] = ra;
+    nb.rows[s] = dead ? 0 : rp;  // (a duplicate was evaluated, and is not scored)
+    nb.rows[ga.P + s] = dead ? 0 : rn;
+    nb.rows[2 * ga.P + s] = dead ? 0 : ra;
     nb.fit[s] = f;
     hits += ah + (dup ? 1 : 0);
     live += !dead;
@@ -1209,9 +1321,9 @@ cudaError_t launch_generation(ebic_ctx *ctx, GenState *g, int parity, cudaStream
   while (G < g->p.max_attempts) G <<= 1;
   cudaError_t e = mark(s, m, 0);
   if (e != cudaSuccess) return e;
-  if ((e = launch_pdl(k_evolve, dim3((unsigned)g->P), dim3(G * 32),
-                      (size_t)G * kEvolveWarpInts * 4, s, gen_args(ctx, g), g->buf(parity ^ 1),
-                      g->buf(parity), parity)) != cudaSuccess)
+  if ((e = launch_pdl(k_evolve, dim3((unsigned)g->P), dim3(G * 32), evolve_smem(G, g->C), s,
+                      gen_args(ctx, g), g->buf(parity ^ 1), g->buf(parity), parity)) !=
+      cudaSuccess)
     return e;
   return launch_scoring(ctx, g, parity, s, m);
 }
@@ -1336,7 +1448,7 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
   EBIC_CHECK_CUDA(ctx, cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)kFinishSmemMax));
   EBIC_CHECK_CUDA(ctx, cudaFuncSetAttribute(k_evolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            kMaxAttemptWarps * kEvolveWarpInts * 4));
+                                            (int)evolve_smem(kMaxAttemptWarps, kUsageSmemMax)));
 
   // enough blocks to spread the slot and table loops, few enough to be co-resident quickly
   const int64_t work = std::max<int64_t>(g->P, g->dcap);

@@ -61,8 +61,8 @@ struct PopView {
   int32_t n;
   const int32_t *stop;
   const uint64_t *hash;
-  const uint64_t *dkeys;
-  const uint32_t *dslot;
+  uint64_t *dkeys;
+  uint32_t *dslot;
   uint32_t dmask;
 };
 

@@ -7,8 +7,8 @@
 //
 // The per-item bookkeeping is arranged so that its loads leave in as few dependent round trips as
 // possible: length, start, dead flag, hash and (for the generation loop's fixed-stride rows) the
-// 64 column words are loaded together, and the first probe of the duplicate table is issued
-// before the evaluation loads and checked after them.
+// 64 column words are loaded together, and the entry of the slot's key into the generation's
+// duplicate table is started before the evaluation loads and finished after them.
 #pragma once
 
 #include "internal.h"
@@ -58,7 +58,7 @@ __device__ __forceinline__ int first(int32_t *work, const PopView &pv, int lane)
 struct Meta {
   int st, L;     // start in cols, length
   bool dead;     // tabu-dead slot (never scored)
-  uint64_t h;    // key (duplicate check), 0 when there is no duplicate table
+  uint64_t h;    // key (duplicate table), 0 when there is none
   int c0, c1;    // columns k = lane and k = lane + 32 (0 past the length)
 };
 
@@ -87,35 +87,45 @@ __device__ __forceinline__ Meta load_meta(const PopView &pv, int i, int lane) {
   return m;
 }
 
-// First probe of the duplicate table for key h (loaded ahead, finished by is_dup).
-struct Probe {
-  uint64_t k0;
-  uint32_t s0, idx0;
+// The generation loop's duplicate table: each live slot's key enters it once, from the item of
+// the slot's first row segment (the duplicate test itself runs after this launch, in k_finish).
+// The compare-and-swap leaves before the evaluation loads and its result is used after them.
+struct Insert {
+  uint64_t prev;  // what the first probe position held
+  uint32_t idx;   // first probe position
+  bool on;        // lane 0 of the slot's first item, with a duplicate table
 };
 
-__device__ __forceinline__ Probe probe_start(const PopView &pv, uint64_t h) {
-  Probe p{0ull, 0u, 0u};
-  if (pv.dkeys) {
-    p.idx0 = table_index(h, pv.dmask);
-    p.k0 = pv.dkeys[p.idx0];
-    p.s0 = pv.dslot[p.idx0];
+__device__ __forceinline__ Insert insert_start(const PopView &pv, int seg, uint64_t h, int lane) {
+  Insert in{0ull, 0u, pv.dkeys != nullptr && seg == 0 && lane == 0};
+  if (in.on) {
+    in.idx = table_index(h, pv.dmask);
+    in.prev = atomicCAS(reinterpret_cast<unsigned long long *>(pv.dkeys + in.idx), 0ull,
+                        (unsigned long long)h);
   }
-  return p;
+  return in;
 }
 
-// True when a lower slot than s produced key h this generation (same rule as dedup_is_dup).
-__device__ __forceinline__ bool is_dup(const PopView &pv, const Probe &p, uint64_t h, int s) {
-  if (!pv.dkeys) return false;
-  if (p.k0 == h) return p.s0 != 0xFFFFFFFFu - (uint32_t)s;
-  if (p.k0 == 0ull) return false;
-  uint32_t i = (p.idx0 + 1u) & pv.dmask;
+// Completes the insertion: the slot word keeps the lowest slot (see dedup_insert).
+__device__ __forceinline__ void insert_finish(const PopView &pv, const Insert &in, uint64_t h,
+                                              int s) {
+  if (!in.on) return;
+  if (in.prev == 0ull || in.prev == h) {
+    atomicMax(pv.dslot + in.idx, 0xFFFFFFFFu - (uint32_t)s);
+    return;
+  }
+  // the first position holds another key: continue the linear probe from the next one
+  uint32_t i = (in.idx + 1u) & pv.dmask;
   for (uint32_t n = 1; n <= pv.dmask; ++n) {
-    const uint64_t k = pv.dkeys[i];
-    if (k == h) return pv.dslot[i] != 0xFFFFFFFFu - (uint32_t)s;
-    if (k == 0ull) return false;
+    const unsigned long long prev =
+        atomicCAS(reinterpret_cast<unsigned long long *>(pv.dkeys + i), 0ull,
+                  (unsigned long long)h);
+    if (prev == 0ull || prev == h) {
+      atomicMax(pv.dslot + i, 0xFFFFFFFFu - (uint32_t)s);
+      return;
+    }
     i = (i + 1u) & pv.dmask;
   }
-  return false;
 }
 
 }  // namespace items
