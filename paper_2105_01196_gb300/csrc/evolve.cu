@@ -1110,11 +1110,19 @@ struct GenState {
   // because the event nodes are re-pointed at fresh events before each replay)
   cudaGraphExec_t graph[2][2] = {};
   cudaGraph_t graph_src[2][2] = {};
+  // kGraphGenerations consecutive generations in one graph, by the parity of the first one (the
+  // kernels of successive generations then overlap through programmatic launches, which a graph
+  // launch per generation would not allow)
+  cudaGraphExec_t multi[2] = {};
   cudaGraphNode_t mark_node[2][4] = {};
   cudaEvent_t cap_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaStream_t cap_stream = nullptr;
 
   void drop_graphs() {
+    for (int k = 0; k < 2; ++k) {
+      if (multi[k]) cudaGraphExecDestroy(multi[k]);
+      multi[k] = nullptr;
+    }
     for (int k = 0; k < 2; ++k)
       for (int v = 0; v < 2; ++v) {
         if (graph[k][v]) cudaGraphExecDestroy(graph[k][v]);
@@ -1544,6 +1552,26 @@ int capture_graph(ebic_ctx *ctx, GenState *g, int parity, int profiled) {
 }
 
 constexpr int kKernelsPerGeneration = 3;
+constexpr int kGraphGenerations = 8;  // even: a chunk ends on the parity it started with
+
+// The graph of kGraphGenerations generations starting at `parity` (no event marks).
+int capture_multi(ebic_ctx *ctx, GenState *g, int parity) {
+  cudaGraph_t graph = nullptr;
+  EBIC_CHECK_CUDA(ctx, cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < kGraphGenerations && e == cudaSuccess; ++j)
+    e = launch_generation(ctx, g, parity ^ (j & 1), g->cap_stream, nullptr);
+  cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return ebic_fail_cuda(ctx, e, "generation capture", __FILE__, __LINE__);
+  }
+  EBIC_CHECK_CUDA(ctx, e2);
+  e = cudaGraphInstantiate(&g->multi[parity], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return ebic_fail_cuda(ctx, e, "cudaGraphInstantiate", __FILE__, __LINE__);
+  return EBIC_OK;
+}
 
 }  // namespace
 
@@ -1597,6 +1625,15 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
     for (int i = 0; i < n_gen; ++i) {
       const int gnext = c.gen + 1 + i;
       const int parity = gnext & 1;
+      if (p->use_graph && !ctx->prof && n_gen - i >= kGraphGenerations) {
+        if (!g->multi[parity]) EBIC_TRY(capture_multi(ctx, g, parity));
+        EBIC_CHECK_CUDA(ctx, cudaGraphLaunch(g->multi[parity], s));
+        prof_count(ctx, EBIC_KERNEL_EVOLVE, kGraphGenerations);
+        prof_count(ctx, EBIC_KERNEL_EVAL, kGraphGenerations);
+        prof_count(ctx, EBIC_KERNEL_FINISH, kGraphGenerations);
+        i += kGraphGenerations - 1;
+        continue;
+      }
       Marks m;
       const bool timed = ctx->prof && take_marks(ctx, &m, true);
       if (p->use_graph) {
