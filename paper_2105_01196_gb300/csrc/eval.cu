@@ -162,15 +162,6 @@ __device__ __forceinline__ void cnt_ripple2(Cnt6 &c, uint32_t k) {
   c.b5 ^= k;
 }
 
-__device__ __forceinline__ void cnt_add1(Cnt6 &c, uint32_t x) {
-  uint32_t t = c.b0 & x;
-  c.b0 ^= x;
-  x = t;
-  t = c.b1 & x;
-  c.b1 ^= x;
-  cnt_ripple2(c, t);
-}
-
 // Adds four inputs: two full adders into the ones, one into the twos, ripple from the fours.
 __device__ __forceinline__ void cnt_add4(Cnt6 &c, uint32_t x0, uint32_t x1, uint32_t x2,
                                          uint32_t x3) {
@@ -267,25 +258,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
       const bool act = w < Wst;
       const uint32_t *G = a.bitmap + w;
       uint4 pos, neg = zero4;
+      // The pair words of a round of pairs are loaded together, the last round padded with the
+      // operation's identity (all ones for the AND, zero for the counters), so an individual
+      // of np pairs costs ceil(np / round) dependent load rounds.
       if (exact) {
-        uint4 ap = make_uint4(kFull, kFull, kFull, kFull), an = ap;
-        int k = 0;
-        for (; k + 4 <= np; k += 4) {
-          uint4 v[4], u[4];
+        const uint4 ones = make_uint4(kFull, kFull, kFull, kFull);
+        uint4 ap = ones, an = ones;
+        for (int k = 0; k < np; k += 8) {
+          uint4 v[8], u[8];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            v[j] = ldb<NS>(act, G + s_pos[warp][k + j]);
-            if (NEG) u[j] = ldb<NS>(act, G + s_neg[warp][k + j]);
+          for (int j = 0; j < 8; ++j) {
+            const bool in = k + j < np;
+            v[j] = in ? ldb<NS>(act, G + s_pos[warp][k + j]) : ones;
+            if (NEG) u[j] = in ? ldb<NS>(act, G + s_neg[warp][k + j]) : ones;
           }
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
+          for (int j = 0; j < 8; ++j) {
             ap = and4(ap, v[j]);
             if (NEG) an = and4(an, u[j]);
           }
-        }
-        for (; k < np; ++k) {
-          ap = and4(ap, ldb<NS>(act, G + s_pos[warp][k]));
-          if (NEG) an = and4(an, ldb<NS>(act, G + s_neg[warp][k]));
         }
         pos = act ? ap : zero4;
         if (NEG) neg = act ? an : zero4;
@@ -296,13 +287,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
           cnt_zero(P[j]);
           cnt_zero(N[j]);
         }
-        int k = 0;
-        for (; k + 4 <= np; k += 4) {
+        for (int k = 0; k < np; k += 4) {
           uint4 v[4], u[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            v[j] = ldb<NS>(act, G + s_pos[warp][k + j]);
-            if (NEG) u[j] = ldb<NS>(act, G + s_neg[warp][k + j]);
+            const bool in = k + j < np;
+            v[j] = in ? ldb<NS>(act, G + s_pos[warp][k + j]) : zero4;
+            if (NEG) u[j] = in ? ldb<NS>(act, G + s_neg[warp][k + j]) : zero4;
           }
           cnt_add4(P[0], v[0].x, v[1].x, v[2].x, v[3].x);
           cnt_add4(P[1], v[0].y, v[1].y, v[2].y, v[3].y);
@@ -313,20 +304,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
             cnt_add4(N[1], u[0].y, u[1].y, u[2].y, u[3].y);
             cnt_add4(N[2], u[0].z, u[1].z, u[2].z, u[3].z);
             cnt_add4(N[3], u[0].w, u[1].w, u[2].w, u[3].w);
-          }
-        }
-        for (; k < np; ++k) {
-          const uint4 v = ldb<NS>(act, G + s_pos[warp][k]);
-          cnt_add1(P[0], v.x);
-          cnt_add1(P[1], v.y);
-          cnt_add1(P[2], v.z);
-          cnt_add1(P[3], v.w);
-          if (NEG) {
-            const uint4 u = ldb<NS>(act, G + s_neg[warp][k]);
-            cnt_add1(N[0], u.x);
-            cnt_add1(N[1], u.y);
-            cnt_add1(N[2], u.z);
-            cnt_add1(N[3], u.w);
           }
         }
         pos = make_uint4(cnt_ge(P[0], t), cnt_ge(P[1], t), cnt_ge(P[2], t), cnt_ge(P[3], t));
