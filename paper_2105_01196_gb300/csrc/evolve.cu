@@ -92,43 +92,87 @@ __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol
 constexpr uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
 constexpr uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
 
+// One Philox4x32-10 block: counter (c0, c1, c2, c3), key (k0, k1).
+__device__ __forceinline__ void philox_block(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1,
+                                             uint32_t c2, uint32_t c3, uint32_t w[4]) {
+  uint32_t x0 = c0, x1 = c1, x2 = c2, x3 = c3, a0 = k0, a1 = k1;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      a0 += kWeyl0;
+      a1 += kWeyl1;
+    }
+    const uint32_t lo0 = kMul0 * x0, hi0 = __umulhi(kMul0, x0);
+    const uint32_t lo1 = kMul1 * x2, hi1 = __umulhi(kMul1, x2);
+    const uint32_t y0 = hi1 ^ x1 ^ a0, y2 = hi0 ^ x3 ^ a1;
+    x0 = y0;
+    x1 = lo1;
+    x2 = y2;
+    x3 = lo0;
+  }
+  w[0] = x0;
+  w[1] = x1;
+  w[2] = x2;
+  w[3] = x3;
+}
+
+// The same as a call (for the rare refills of WarpStream, which would otherwise be inlined at
+// every draw).
+__device__ __noinline__ uint4 philox_block_call(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1,
+                                                uint32_t c2, uint32_t c3) {
+  uint32_t w[4];
+  philox_block(k0, k1, c0, c1, c2, c3, w);
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// The word stream of counter (g, s, a): the words of blocks 0, 1, 2, ... in order, one thread.
 struct WordStream {
   uint32_t k0, k1, c0, c1, c2, blk;
-  uint32_t w0, w1, w2, w3;
+  uint32_t w[4];
   int pos;
   __device__ WordStream(uint64_t seed, uint32_t g, uint32_t s, uint32_t a)
       : k0((uint32_t)seed), k1((uint32_t)(seed >> 32)), c0(g), c1(s), c2(a), blk(0), pos(4) {}
-  __device__ void refill() {
-    uint32_t x0 = c0, x1 = c1, x2 = c2, x3 = blk, a0 = k0, a1 = k1;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-      if (r) {
-        a0 += kWeyl0;
-        a1 += kWeyl1;
-      }
-      const uint32_t lo0 = kMul0 * x0, hi0 = __umulhi(kMul0, x0);
-      const uint32_t lo1 = kMul1 * x2, hi1 = __umulhi(kMul1, x2);
-      const uint32_t y0 = hi1 ^ x1 ^ a0, y2 = hi0 ^ x3 ^ a1;
-      x0 = y0;
-      x1 = lo1;
-      x2 = y2;
-      x3 = lo0;
-    }
-    w0 = x0;
-    w1 = x1;
-    w2 = x2;
-    w3 = x3;
-    ++blk;
-    pos = 0;
-  }
-  // Next word of the stream (the four words of a block in order; kept in registers).
   __device__ uint32_t next() {
-    if (pos == 4) refill();
-    const uint32_t w = pos == 0 ? w0 : (pos == 1 ? w1 : (pos == 2 ? w2 : w3));
+    if (pos == 4) {
+      philox_block(k0, k1, c0, c1, c2, blk++, w);
+      pos = 0;
+    }
+    const uint32_t v = pos == 0 ? w[0] : (pos == 1 ? w[1] : (pos == 2 ? w[2] : w[3]));
     ++pos;
-    return w;
+    return v;
   }
   // Uniform integer in [0, n): high word of word * n.
+  __device__ uint32_t below(uint32_t n) { return __umulhi(next(), n); }
+};
+
+// The same word stream for a whole warp: lane j holds block base + j, so one round of Philox
+// in all lanes yields 128 words, and word i comes from lane i / 4 - base by a shuffle (every
+// lane calls next() together and gets the same word).  The sequence is that of WordStream.
+struct WarpStream {
+  uint32_t k0, k1, c0, c1, c2;
+  uint32_t w[4];
+  uint32_t base, pos;  // first block held; next word index
+  int lane;
+  __device__ WarpStream(uint64_t seed, uint32_t g, uint32_t s, uint32_t a, int lane_)
+      : k0((uint32_t)seed), k1((uint32_t)(seed >> 32)), c0(g), c1(s), c2(a), base(0), pos(0),
+        lane(lane_) {
+    philox_block(k0, k1, c0, c1, c2, base + (uint32_t)lane, w);
+  }
+  __device__ uint32_t next() {
+    const uint32_t b = pos >> 2;
+    if (b >= base + 32u) {  // (warp-uniform) the next 32 blocks
+      base += 32u;
+      const uint4 v = philox_block_call(k0, k1, c0, c1, c2, base + (uint32_t)lane);
+      w[0] = v.x;
+      w[1] = v.y;
+      w[2] = v.z;
+      w[3] = v.w;
+    }
+    const uint32_t k = pos & 3u;
+    const uint32_t mine = k == 0 ? w[0] : (k == 1 ? w[1] : (k == 2 ? w[2] : w[3]));
+    ++pos;
+    return __shfl_sync(0xFFFFFFFFu, mine, (int)(b - base));
+  }
   __device__ uint32_t below(uint32_t n) { return __umulhi(next(), n); }
 };
 
@@ -218,7 +262,7 @@ __device__ __forceinline__ bool w_contains(const int32_t *c, int L, int v, int l
   return __any_sync(kFull, hit);
 }
 
-__device__ int w_draw_free(WordStream &st, int C, const int32_t *c, int L, int lane) {
+__device__ int w_draw_free(WarpStream &st, int C, const int32_t *c, int L, int lane) {
   for (int t = 0; t < 64; ++t) {
     const int v = (int)st.below((uint32_t)C);
     if (!w_contains(c, L, v, lane)) return v;
@@ -231,7 +275,7 @@ __device__ int w_draw_free(WordStream &st, int C, const int32_t *c, int L, int l
 // the length is zero), a second its column usage.  The columns go to the warp's scratch rows so
 // that the winner's chromosome is copied to `win` without another trip to global memory.  Same
 // winner as the sequential rule (exact penalised comparison, ties to the lower slot).
-__device__ int w_tournament(WordStream &st, const GenArgs &ga, const Buf &pb, int32_t *scratch,
+__device__ int w_tournament(WarpStream &st, const GenArgs &ga, const Buf &pb, int32_t *scratch,
                             int32_t *win, int *win_len, int lane, const int32_t *usage) {
   int best = -1, ub = 0, bl = 0;
   uint64_t fb = 0ull;
@@ -295,11 +339,23 @@ __device__ int w_tournament(WordStream &st, const GenArgs &ga, const Buf &pb, in
   return best;
 }
 
-// Both tournaments of a child when 2 T <= 8: the first one's T candidates, the crossover word and
+// Whether candidate (fa, ua, ia) beats (fb, ub, ib): exact penalised comparison, ties to the
+// lower slot; a missing candidate (slot < 0) never wins.
+__device__ __forceinline__ bool beats(uint64_t fa, int ua, int ia, uint64_t fb, int ub, int ib) {
+  if (ia < 0) return false;
+  if (ib < 0) return true;
+  const int c = cmp_penalised(fa, ua, fb, ub);
+  return c > 0 || (c == 0 && ia < ib);
+}
+
+// Both tournaments of a child when T <= 4: the first one's T candidates, the crossover word and
 // the second one's T candidates are drawn in stream order (the second set from a copy of the
-// stream, adopted only when the crossover happens), and all candidates' data arrive in one round
-// of loads.  Same winners as two calls of w_tournament.  Returns whether the crossover happens.
-__device__ bool w_tournament_pair(WordStream &st, const GenArgs &ga, const Buf &pb,
+// stream, adopted only when the crossover happens).  The sets take candidate places 0..T-1 and
+// 4..4+T-1, four lanes each, so all candidates' data arrive in one round of loads and each set's
+// winner comes out of a two-step butterfly over its places.  The winner is the one w_tournament
+// picks (the maximum of one total order: penalised score, then the lower slot).  Returns whether
+// the crossover happens.
+__device__ bool w_tournament_pair(WarpStream &st, const GenArgs &ga, const Buf &pb,
                                   int32_t *scratch, int32_t *A, int *LA, int32_t *B, int *LB,
                                   int lane, const int32_t *usage) {
   const int T = ga.T;
@@ -307,20 +363,20 @@ __device__ bool w_tournament_pair(WordStream &st, const GenArgs &ga, const Buf &
 #pragma unroll
   for (int q = 0; q < 8; ++q) ids[q] = -1;
 #pragma unroll
-  for (int q = 0; q < 8; ++q)
+  for (int q = 0; q < 4; ++q)
     if (q < T) ids[q] = (int)st.below((uint32_t)ga.P);
   const bool cross = st.next() < (1u << 30);  // one-point crossover, probability 1/4
-  WordStream st2 = st;
+  WarpStream st2 = st;
 #pragma unroll
-  for (int q = 0; q < 8; ++q)
-    if (q >= T && q < 2 * T) ids[q] = (int)st2.below((uint32_t)ga.P);
+  for (int q = 0; q < 4; ++q)
+    if (q < T) ids[4 + q] = (int)st2.below((uint32_t)ga.P);
   if (cross) st = st2;
   const int mine = lane >> 2, sub = lane & 3;
   int my = -1;
 #pragma unroll
   for (int q = 0; q < 8; ++q)
     if (q == mine) my = ids[q];
-  if (!cross && mine >= T) my = -1;  // the second set is not needed
+  if (!cross && mine >= 4) my = -1;  // the second set is not needed
   uint64_t f = 0ull;
   int u = 0, L = 0;
   if (my >= 0) {
@@ -342,37 +398,25 @@ __device__ bool w_tournament_pair(WordStream &st, const GenArgs &ga, const Buf &
   }
   u += __shfl_xor_sync(kFull, u, 1);
   u += __shfl_xor_sync(kFull, u, 2);
-  __syncwarp();
-  // the winner of each set, as in w_tournament (exact penalised comparison, ties to the lower slot)
-  int best0 = -1, take0 = 0, bl0 = 0, ub0 = 0, best1 = -1, take1 = 0, bl1 = 0, ub1 = 0;
-  uint64_t fb0 = 0ull, fb1 = 0ull;
+  // butterfly over the places of each set (lanes 0-15: first set, 16-31: second set)
+  int wi = my, wq = mine, wl = L, wu = u;
+  uint64_t wf = f;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const uint64_t fq = __shfl_sync(kFull, f, q * 4);
-    const int uq = __shfl_sync(kFull, u, q * 4);
-    const int lq = __shfl_sync(kFull, L, q * 4);
-    const int iq = ids[q];
-    if (iq < 0) continue;
-    if (q < T) {
-      const int c = best0 < 0 ? 1 : cmp_penalised(fq, uq, fb0, ub0);
-      if (c > 0 || (c == 0 && iq < best0)) {
-        best0 = iq;
-        fb0 = fq;
-        ub0 = uq;
-        bl0 = lq;
-        take0 = q;
-      }
-    } else if (cross) {
-      const int c = best1 < 0 ? 1 : cmp_penalised(fq, uq, fb1, ub1);
-      if (c > 0 || (c == 0 && iq < best1)) {
-        best1 = iq;
-        fb1 = fq;
-        ub1 = uq;
-        bl1 = lq;
-        take1 = q;
-      }
+  for (int off = 4; off <= 8; off <<= 1) {
+    const uint64_t of = __shfl_xor_sync(kFull, wf, off);
+    const int ou = __shfl_xor_sync(kFull, wu, off), oi = __shfl_xor_sync(kFull, wi, off);
+    const int ol = __shfl_xor_sync(kFull, wl, off), oq = __shfl_xor_sync(kFull, wq, off);
+    if (beats(of, ou, oi, wf, wu, wi)) {
+      wf = of;
+      wu = ou;
+      wi = oi;
+      wl = ol;
+      wq = oq;
     }
   }
+  const int take0 = __shfl_sync(kFull, wq, 0), take1 = __shfl_sync(kFull, wq, 16);
+  const int bl0 = __shfl_sync(kFull, wl, 0), bl1 = __shfl_sync(kFull, wl, 16);
+  __syncwarp();  // the scratch rows are written
   const int32_t *ra = scratch + take0 * kS;
   A[lane] = ra[lane];
   A[lane + 32] = ra[lane + 32];
@@ -393,7 +437,7 @@ __device__ void w_copy(int32_t *c, const int32_t *src, int L, int lane) {
   __syncwarp();
 }
 
-__device__ void w_swap(WordStream &st, int32_t *c, int L, int lane) {
+__device__ void w_swap(WarpStream &st, int32_t *c, int L, int lane) {
   if (L < 2) return;  // never reached: every live chromosome has at least two columns
   const int p = (int)st.below((uint32_t)L);
   int q = (int)st.below((uint32_t)(L - 1));
@@ -406,7 +450,7 @@ __device__ void w_swap(WordStream &st, int32_t *c, int L, int lane) {
   __syncwarp();
 }
 
-__device__ void w_mutate(WordStream &st, int32_t *c, int &L, int C, int max_len, int lane) {
+__device__ void w_mutate(WarpStream &st, int32_t *c, int &L, int C, int max_len, int lane) {
   for (int tries = 0; tries < 8; ++tries) {
     const uint32_t op = st.next() >> 30;
     if (op == 0u) {  // insertion
@@ -454,10 +498,10 @@ __device__ void w_mutate(WordStream &st, int32_t *c, int &L, int C, int max_len,
 __device__ void w_make_child(const GenArgs &ga, const Buf &pb, int g, int s, int a, int32_t *c,
                              int32_t *scratch, int32_t *A, int32_t *B, int &L, int lane,
                              const int32_t *usage) {
-  WordStream st(ga.seed, (uint32_t)g, (uint32_t)s, (uint32_t)a);
+  WarpStream st(ga.seed, (uint32_t)g, (uint32_t)s, (uint32_t)a, lane);
   int LA = 0, LB = 0;
   bool cross;
-  if (2 * ga.T <= 8) {
+  if (ga.T <= 4) {
     cross = w_tournament_pair(st, ga, pb, scratch, A, &LA, B, &LB, lane, usage);
   } else {
     w_tournament(st, ga, pb, scratch, A, &LA, lane, usage);
