@@ -513,22 +513,38 @@ __device__ void w_make_child(const GenArgs &ga, const Buf &pb, int g, int s, int
     const int cut1 = min(1 + (int)st.below((uint32_t)(LA - 1)), max(LA, 1));
     const int cut2 = min(1 + (int)st.below((uint32_t)(LB - 1)), LB);
     w_copy(c, A, cut1, lane);
-    const int k0 = cut2 + lane, k1 = cut2 + lane + 32;
-    const int b0 = k0 < LB ? B[k0] : -1, b1 = k1 < LB ? B[k1] : -1;
-    bool in0 = false, in1 = false;
-    for (int q = 0; q < cut1; ++q) {
-      const int hq = c[q];
-      in0 |= b0 == hq;
-      in1 |= b1 == hq;
+    const int ns = LB - cut2;  // suffix length
+    if (cut1 + ns <= 32) {
+      // prefix in lanes [0, cut1), suffix in lanes [cut1, cut1 + ns): one match finds the
+      // suffix columns present in the prefix (other lanes hold values no column has)
+      const bool suf = lane >= cut1 && lane < cut1 + ns;
+      const int v = lane < cut1 ? A[lane] : (suf ? B[cut2 + lane - cut1] : -1 - lane);
+      const unsigned eq = __match_any_sync(kFull, v);
+      const unsigned pre = cut1 >= 32 ? kFull : ((1u << cut1) - 1u);
+      const bool keep = suf && !(eq & pre);
+      const unsigned m = __ballot_sync(kFull, keep);
+      const int pos = cut1 + __popc(m & lanes_below(lane));
+      if (keep && pos < ga.max_len) c[pos] = v;
+      __syncwarp();
+      L = min(cut1 + __popc(m), ga.max_len);
+    } else {
+      const int k0 = cut2 + lane, k1 = cut2 + lane + 32;
+      const int b0 = k0 < LB ? B[k0] : -1, b1 = k1 < LB ? B[k1] : -1;
+      bool in0 = false, in1 = false;
+      for (int q = 0; q < cut1; ++q) {
+        const int hq = c[q];
+        in0 |= b0 == hq;
+        in1 |= b1 == hq;
+      }
+      const bool keep0 = b0 >= 0 && !in0, keep1 = b1 >= 0 && !in1;
+      const unsigned m0 = __ballot_sync(kFull, keep0), m1 = __ballot_sync(kFull, keep1);
+      const int pos0 = cut1 + __popc(m0 & lanes_below(lane));
+      const int pos1 = cut1 + __popc(m0) + __popc(m1 & lanes_below(lane));
+      if (keep0 && pos0 < ga.max_len) c[pos0] = b0;
+      if (keep1 && pos1 < ga.max_len) c[pos1] = b1;
+      __syncwarp();
+      L = min(cut1 + __popc(m0) + __popc(m1), ga.max_len);
     }
-    const bool keep0 = b0 >= 0 && !in0, keep1 = b1 >= 0 && !in1;
-    const unsigned m0 = __ballot_sync(kFull, keep0), m1 = __ballot_sync(kFull, keep1);
-    const int pos0 = cut1 + __popc(m0 & lanes_below(lane));
-    const int pos1 = cut1 + __popc(m0) + __popc(m1 & lanes_below(lane));
-    if (keep0 && pos0 < ga.max_len) c[pos0] = b0;
-    if (keep1 && pos1 < ga.max_len) c[pos1] = b1;
-    __syncwarp();
-    L = min(cut1 + __popc(m0) + __popc(m1), ga.max_len);
     if (L < 2) {
       w_copy(c, A, LA, lane);
       L = LA;
