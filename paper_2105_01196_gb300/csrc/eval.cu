@@ -287,23 +287,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
           cnt_zero(P[j]);
           cnt_zero(N[j]);
         }
-        for (int k = 0; k < np; k += 4) {
-          uint4 v[4], u[4];
+        for (int k = 0; k < np; k += 8) {
+          uint4 v[8], u[8];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
+          for (int j = 0; j < 8; ++j) {
             const bool in = k + j < np;
             v[j] = in ? ldb<NS>(act, G + s_pos[warp][k + j]) : zero4;
             if (NEG) u[j] = in ? ldb<NS>(act, G + s_neg[warp][k + j]) : zero4;
           }
-          cnt_add4(P[0], v[0].x, v[1].x, v[2].x, v[3].x);
-          cnt_add4(P[1], v[0].y, v[1].y, v[2].y, v[3].y);
-          cnt_add4(P[2], v[0].z, v[1].z, v[2].z, v[3].z);
-          cnt_add4(P[3], v[0].w, v[1].w, v[2].w, v[3].w);
-          if (NEG) {
-            cnt_add4(N[0], u[0].x, u[1].x, u[2].x, u[3].x);
-            cnt_add4(N[1], u[0].y, u[1].y, u[2].y, u[3].y);
-            cnt_add4(N[2], u[0].z, u[1].z, u[2].z, u[3].z);
-            cnt_add4(N[3], u[0].w, u[1].w, u[2].w, u[3].w);
+#pragma unroll
+          for (int h = 0; h < 8; h += 4) {
+            cnt_add4(P[0], v[h].x, v[h + 1].x, v[h + 2].x, v[h + 3].x);
+            cnt_add4(P[1], v[h].y, v[h + 1].y, v[h + 2].y, v[h + 3].y);
+            cnt_add4(P[2], v[h].z, v[h + 1].z, v[h + 2].z, v[h + 3].z);
+            cnt_add4(P[3], v[h].w, v[h + 1].w, v[h + 2].w, v[h + 3].w);
+            if (NEG) {
+              cnt_add4(N[0], u[h].x, u[h + 1].x, u[h + 2].x, u[h + 3].x);
+              cnt_add4(N[1], u[h].y, u[h + 1].y, u[h + 2].y, u[h + 3].y);
+              cnt_add4(N[2], u[h].z, u[h + 1].z, u[h + 2].z, u[h + 3].z);
+              cnt_add4(N[3], u[h].w, u[h + 1].w, u[h + 2].w, u[h + 3].w);
+            }
           }
         }
         pos = make_uint4(cnt_ge(P[0], t), cnt_ge(P[1], t), cnt_ge(P[2], t), cnt_ge(P[3], t));
