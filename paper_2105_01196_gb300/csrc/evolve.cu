@@ -689,6 +689,7 @@ struct TopSmem {
   uint32_t *colbits; // ceil(C / 32) words
   int32_t *idx;      // K + 1: pool index of list position
   int32_t *idx2;     // K + 1
+  int32_t *ov;       // K + 1: columns each list entry shares with the candidate
   uint8_t *used;     // K + 1
   uint64_t *sf, *sh; // sort_cap
   int32_t *ss;
@@ -706,88 +707,122 @@ __device__ __forceinline__ int overlap(const TopSmem &sm, const TopEntry &e, int
   return __reduce_add_sync(kFull, cnt);
 }
 
-// Sequential top-list update by one warp over the staged, sorted candidates q0..q1-1 (their data
-// is in sm.ccols / sm.cmeta at q - q0).  Returns the new list length; *stop is set when a
-// candidate ranks at position >= K (every later candidate ranks lower still).
+// Top-list update over the staged, sorted candidates q0..q1-1 (their data is in sm.ccols /
+// sm.cmeta at q - q0), one candidate after the other, by the whole block: warp 0 finds the
+// candidate's rank and marks its columns; every warp then counts, for its share of the list's
+// entries, the columns the entry shares with the candidate (sm.ov); warp 0 applies the
+// admission and eviction rule with those counts.  Returns the new list length; *s_stop is set
+// when a candidate ranks at position >= K (every later candidate ranks lower still).  Called by
+// every thread of the block.
 __device__ int process_chunk(const GenArgs &ga, const TopSmem &sm, int n, const uint64_t *cf,
-                             const uint64_t *ch, int q0, int q1, int lane, bool *stop) {
+                             const uint64_t *ch, int q0, int q1, int *s_stop) {
+  __shared__ int s_pos, s_dup, s_n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  if (threadIdx.x == 0) s_n = n;
   for (int q = q0; q < q1; ++q) {
     const uint64_t f = cf[q], h = ch[q];
-    int pos = 0;
-    bool dup = false;
-    for (int e0 = 0; e0 < n; e0 += 32) {
-      const int e = e0 + lane;
-      bool isdup = false, before = false;
-      if (e < n) {
-        const TopEntry &E = sm.pool[sm.idx[e]];
-        isdup = E.h == h;
-        before = key_before(E.f, E.h, f, h);
-      }
-      dup |= __any_sync(kFull, isdup);
-      pos += __popc(__ballot_sync(kFull, before));
-    }
-    if (dup) continue;
-    if (pos >= ga.K) {  // the list is full and every later candidate ranks after it
-      *stop = true;
-      break;
-    }
     const int32_t *cc = sm.ccols + (q - q0) * kS;
     const int L = sm.cmeta[(q - q0) * 4];
     const int c0 = lane < L ? cc[lane] : 0, c1 = lane + 32 < L ? cc[lane + 32] : 0;
-    if (lane < L) atomicOr(&sm.colbits[c0 >> 5], 1u << (c0 & 31));
-    if (lane + 32 < L) atomicOr(&sm.colbits[c1 >> 5], 1u << (c1 & 31));
-    __syncwarp();
-    bool ok = true;
-    for (int e = 0; e < pos && ok; ++e) {
-      const int inter = overlap(sm, sm.pool[sm.idx[e]], lane);
-      if ((long long)inter * ga.ov_den > (long long)ga.ov_num * L) ok = false;
-    }
-    if (ok) {
-      // a free pool slot: the pool has K + 1 entries and the list at most K
-      int fr = -1;
-      for (int b0 = 0; b0 <= ga.K && fr < 0; b0 += 32) {
-        const int b = b0 + lane;
-        const unsigned m = __ballot_sync(kFull, b <= ga.K && !sm.used[b]);
-        if (m) fr = b0 + __ffs(m) - 1;
-      }
-      TopEntry &ne = sm.pool[fr];
-      ne.cols[lane] = lane < L ? c0 : 0;
-      ne.cols[lane + 32] = lane + 32 < L ? c1 : 0;
-      if (lane == 0) {
-        ne.len = L;
-        ne.f = f;
-        ne.h = h;
-        ne.rp = sm.cmeta[(q - q0) * 4 + 1];
-        ne.rn = sm.cmeta[(q - q0) * 4 + 2];
-        ne.ra = sm.cmeta[(q - q0) * 4 + 3];
-        sm.used[fr] = 1;
-      }
-      for (int e = lane; e < pos; e += 32) sm.idx2[e] = sm.idx[e];
-      int m = pos + 1;
-      for (int e = pos; e < n; ++e) {
-        const int pe = sm.idx[e];
-        const TopEntry &E = sm.pool[pe];
-        const int inter = overlap(sm, E, lane);
-        const bool keep = (long long)inter * ga.ov_den <= (long long)ga.ov_num * E.len;
-        if (keep && m < ga.K) {
-          if (lane == 0) sm.idx2[m] = pe;
-          ++m;
-        } else if (lane == 0) {
-          sm.used[pe] = 0;
+    if (warp == 0) {
+      int pos = 0;
+      bool dup = false;
+      for (int e0 = 0; e0 < n; e0 += 32) {
+        const int e = e0 + lane;
+        bool isdup = false, before = false;
+        if (e < n) {
+          const TopEntry &E = sm.pool[sm.idx[e]];
+          isdup = E.h == h;
+          before = key_before(E.f, E.h, f, h);
         }
+        dup |= __any_sync(kFull, isdup);
+        pos += __popc(__ballot_sync(kFull, before));
+      }
+      if (!dup && pos < ga.K) {  // the candidate's columns, for the overlap counts
+        if (lane < L) atomicOr(&sm.colbits[c0 >> 5], 1u << (c0 & 31));
+        if (lane + 32 < L) atomicOr(&sm.colbits[c1 >> 5], 1u << (c1 & 31));
+      }
+      if (lane == 0) {
+        s_pos = pos;
+        s_dup = dup;
+      }
+    }
+    __syncthreads();
+    const int pos = s_pos;
+    if (s_dup) {  // (uniform) every thread has read s_pos / s_dup before warp 0 rewrites them
+      __syncthreads();
+      continue;
+    }
+    if (pos >= ga.K) {    // the list is full and every later candidate ranks after it
+      if (threadIdx.x == 0) *s_stop = 1;
+      break;
+    }
+    for (int e = warp; e < n; e += nwarps) {
+      const int inter = overlap(sm, sm.pool[sm.idx[e]], lane);
+      if (lane == 0) sm.ov[e] = inter;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      bool ok = true;
+      for (int e = lane; e < pos; e += 32)
+        ok &= (long long)sm.ov[e] * ga.ov_den <= (long long)ga.ov_num * L;
+      ok = __all_sync(kFull, ok);
+      if (ok) {
+        // a free pool slot: the pool has K + 1 entries and the list at most K
+        int fr = -1;
+        for (int b0 = 0; b0 <= ga.K && fr < 0; b0 += 32) {
+          const int b = b0 + lane;
+          const unsigned m = __ballot_sync(kFull, b <= ga.K && !sm.used[b]);
+          if (m) fr = b0 + __ffs(m) - 1;
+        }
+        TopEntry &ne = sm.pool[fr];
+        ne.cols[lane] = lane < L ? c0 : 0;
+        ne.cols[lane + 32] = lane + 32 < L ? c1 : 0;
+        if (lane == 0) {
+          ne.len = L;
+          ne.f = f;
+          ne.h = h;
+          ne.rp = sm.cmeta[(q - q0) * 4 + 1];
+          ne.rn = sm.cmeta[(q - q0) * 4 + 2];
+          ne.ra = sm.cmeta[(q - q0) * 4 + 3];
+          sm.used[fr] = 1;
+        }
+        // entries after the candidate stay when they share at most the allowed fraction of
+        // their own columns with it (in order, the list cut to K)
+        for (int e = lane; e < pos; e += 32) sm.idx2[e] = sm.idx[e];
+        int m = pos + 1;
+        for (int e0 = pos; e0 < n; e0 += 32) {
+          const int e = e0 + lane;
+          bool keep = false;
+          int pe = 0;
+          if (e < n) {
+            pe = sm.idx[e];
+            keep = (long long)sm.ov[e] * ga.ov_den <= (long long)ga.ov_num * sm.pool[pe].len;
+          }
+          const unsigned km = __ballot_sync(kFull, keep);
+          const int dst = m + __popc(km & lanes_below(lane));
+          if (e < n) {
+            if (keep && dst < ga.K) sm.idx2[dst] = pe;
+            else sm.used[pe] = 0;
+          }
+          m += __popc(km);
+        }
+        m = min(m, ga.K);
+        __syncwarp();
+        if (lane == 0) sm.idx2[pos] = fr;
+        __syncwarp();
+        for (int e = lane; e < m; e += 32) sm.idx[e] = sm.idx2[e];
+        if (lane == 0) s_n = m;
       }
       __syncwarp();
-      if (lane == 0) sm.idx2[pos] = fr;
-      __syncwarp();
-      for (int e = lane; e < m; e += 32) sm.idx[e] = sm.idx2[e];
-      n = m;
-      __syncwarp();
+      if (lane < L) atomicAnd(&sm.colbits[c0 >> 5], ~(1u << (c0 & 31)));
+      if (lane + 32 < L) atomicAnd(&sm.colbits[c1 >> 5], ~(1u << (c1 & 31)));
     }
-    if (lane < L) atomicAnd(&sm.colbits[c0 >> 5], ~(1u << (c0 & 31)));
-    if (lane + 32 < L) atomicAnd(&sm.colbits[c1 >> 5], ~(1u << (c1 & 31)));
-    __syncwarp();
+    __syncthreads();
+    n = s_n;
   }
-  return n;
+  __syncthreads();
+  return s_n;
 }
 
 // Bitonic sort of up to 32 candidates across the lanes of one warp (lane i holds candidate i or
@@ -893,15 +928,8 @@ __device__ int sort_and_process(const GenArgs &ga, const Buf &nb, const TopSmem 
       sm.cmeta[i * 4 + 3] = __ldcg(nb.rows + 2 * ga.P + sl);
     }
     __syncthreads();
-    if (warp == 0) {
-      bool stop = false;
-      const int m = process_chunk(ga, sm, *s_n, cf, ch, q0, q1, lane, &stop);
-      __syncwarp();
-      if (lane == 0) {
-        *s_n = m;
-        *s_stop = stop;
-      }
-    }
+    const int m = process_chunk(ga, sm, *s_n, cf, ch, q0, q1, s_stop);
+    if (threadIdx.x == 0) *s_n = m;
     __syncthreads();
     if (*s_stop) break;
   }
@@ -929,7 +957,8 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
   sm.ss = reinterpret_cast<int32_t *>(sm.colbits + cw);
   sm.idx = sm.ss + ga.sort_cap;
   sm.idx2 = sm.idx + ga.K + 1;
-  sm.ccols = sm.idx2 + ga.K + 1;
+  sm.ov = sm.idx2 + ga.K + 1;
+  sm.ccols = sm.ov + ga.K + 1;
   sm.cmeta = sm.ccols + kChunk * kS;
   sm.used = reinterpret_cast<uint8_t *>(sm.cmeta + kChunk * 4);
   if (threadIdx.x == 0) {
@@ -1504,12 +1533,12 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
   const int cw = (ctx->C + 31) / 32;
   g->sort_cap = (int32_t)std::min<uint32_t>(kSortSmemMax, next_pow2(P));
   g->top_smem = (size_t)(g->K + 1) * sizeof(TopEntry) + (size_t)g->sort_cap * 16 +
-                (size_t)cw * 4 + (size_t)g->sort_cap * 4 + (size_t)(g->K + 1) * 8 +
+                (size_t)cw * 4 + (size_t)g->sort_cap * 4 + (size_t)(g->K + 1) * 12 +
                 (size_t)kChunk * (kS + 4) * 4 + (size_t)(g->K + 1) + 16;
   // One fixed upper bound for every context (contexts on other threads set the same value, so no
   // context can lower another's limit): K = 256, 65,535 columns, the largest sort buffer.
   static_assert((size_t)(EBIC_MAX_BICLUSTERS + 1) * sizeof(TopEntry) + kSortSmemMax * 20 +
-                        2048 * 4 + (EBIC_MAX_BICLUSTERS + 1) * 9 + kChunk * (kS + 4) * 4 + 16 <=
+                        2048 * 4 + (EBIC_MAX_BICLUSTERS + 1) * 13 + kChunk * (kS + 4) * 4 + 16 <=
                     kFinishSmemMax,
                 "k_finish shared memory bound");
   if (g->top_smem > kFinishSmemMax) return ebic_fail(ctx, EBIC_EINVAL, "top-list workspace too large");
