@@ -936,6 +936,27 @@ __device__ int sort_and_process(const GenArgs &ga, const Buf &nb, const TopSmem 
   return *s_n;
 }
 
+// A slot's inputs to scoring: every load first, then the duplicate lookup (probed whatever
+// the dead flag says, so that its loads need not wait for it).
+struct SlotIn {
+  bool att_dead, in_dup;
+  uint64_t h;
+  int L, ah, rp, rn, ra;
+};
+
+__device__ __forceinline__ SlotIn load_slot(const GenArgs &ga, const Buf &nb, int par, int s) {
+  SlotIn in;
+  in.att_dead = nb.att_dead[s] != 0;
+  in.h = nb.hash[s];
+  in.L = nb.len[s];
+  in.ah = nb.att_hits[s];
+  in.rp = ga.rows_scr[s];
+  in.rn = ga.rows_scr[ga.P + s];
+  in.ra = ga.rows_scr[2 * ga.P + s];
+  in.in_dup = dedup_is_dup(ga.dkeys[par], ga.dslot[par], ga.dmask, in.h, s);
+  return in;
+}
+
 // Scoring, tabu bookkeeping and the top-list update of generation g (parity par).  Every block
 // scores a share of the slots and moves a share of generation g-1's duplicate table into the tabu
 // list (clearing it for generation g+1); the last block to finish then runs the single-block part.
@@ -944,7 +965,14 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
   __shared__ int s_hits, s_live, s_lsum, s_last, s_n, s_cnt, s_stop, s_nc;
   GenCtl *ctl = ga.ctl;
   wait_prior_grid();
-  if (ctl->stopped) return;
+  // The counters, the list's last entry and this thread's first slot are loaded in one round,
+  // ahead of the stop test (which must still come before any store).
+  const int stopped = ctl->stopped, n0 = ctl->n_top, gen0 = ctl->gen;
+  const uint64_t last_f = ga.top[ga.K - 1].f, last_h = ga.top[ga.K - 1].h;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  SlotIn first;
+  if (tid < ga.P) first = load_slot(ga, nb, par, tid);
+  if (stopped) return;
   // A single block keeps the candidates and counters in shared memory; several blocks use the
   // global arrays and counters and hand over to the last block to finish.
   const bool single = gridDim.x == 1 && ga.P <= ga.sort_cap;
@@ -968,23 +996,20 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
     s_nc = 0;
   }
   __syncthreads();
-  const int n0 = ctl->n_top;
   const bool had_threshold = n0 >= ga.K;
-  const uint64_t tf = had_threshold ? ga.top[ga.K - 1].f : 0ull;
-  const uint64_t th = had_threshold ? ga.top[ga.K - 1].h : 0ull;
+  const uint64_t tf = had_threshold ? last_f : 0ull;
+  const uint64_t th = had_threshold ? last_h : 0ull;
   // Elites (copies of the first n_el entries) are no candidates: while their entry is in the
   // list they are skipped as duplicates, and an entry evicted by a better candidate fails the
   // same overlap test as its copy would, so leaving them out changes nothing.
-  const int n_el = ctl->gen < 0 ? 0 : min(ga.E, n0);
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  const int n_el = gen0 < 0 ? 0 : min(ga.E, n0);
   int hits = 0, live = 0, lsum = 0;
   for (int s = tid; s < ga.P; s += stride) {
-    // every load of the slot first, then the duplicate lookup, then the stores
-    const bool att_dead = nb.att_dead[s] != 0;
-    const uint64_t h = nb.hash[s];
-    const int L = nb.len[s], ah = nb.att_hits[s];
-    const int rp = ga.rows_scr[s], rn = ga.rows_scr[ga.P + s], ra = ga.rows_scr[2 * ga.P + s];
-    const bool dup = !att_dead && dedup_is_dup(ga.dkeys[par], ga.dslot[par], ga.dmask, h, s);
+    const SlotIn in = s == tid ? first : load_slot(ga, nb, par, s);
+    const bool att_dead = in.att_dead;
+    const uint64_t h = in.h;
+    const int L = in.L, ah = in.ah, rp = in.rp, rn = in.rn, ra = in.ra;
+    const bool dup = !att_dead && in.in_dup;
     const bool dead = att_dead || dup;
     const uint64_t f =
         (dead || ra < ga.min_rows) ? 0ull : ((uint64_t)ra << (L < ga.col_cap ? L : ga.col_cap));

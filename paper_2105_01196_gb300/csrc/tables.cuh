@@ -51,13 +51,15 @@ __device__ __forceinline__ void dedup_insert(uint64_t *keys, uint32_t *slot, uin
   }
 }
 
-// True when h was inserted by a lower slot than s.
+// True when h was inserted by a lower slot than s.  (A position's key and slot word are loaded
+// together, so each probe step is one round trip.)
 __device__ __forceinline__ bool dedup_is_dup(const uint64_t *keys, const uint32_t *slot,
                                              uint32_t mask, uint64_t h, int s) {
   uint32_t i = table_index(h, mask);
   for (uint32_t n = 0; n <= mask; ++n) {
     const uint64_t k = keys[i];
-    if (k == h) return slot[i] != 0xFFFFFFFFu - (uint32_t)s;
+    const uint32_t w = slot[i];
+    if (k == h) return w != 0xFFFFFFFFu - (uint32_t)s;
     if (k == 0ull) return false;
     i = (i + 1) & mask;
   }
