@@ -179,3 +179,34 @@ def test_same_shape_reload_starts_a_fresh_run(ebic, mode):
             assert rep.gens_done == st.gen == 8
             assert rep.n_evaluated == st.n_evaluated
             assert_same_state(ctx, st, gp)
+
+
+@pytest.mark.parametrize("tournament,max_attempts", [(1, 1), (3, 2), (6, 5), (8, 16)])
+def test_tournament_and_attempt_shapes(ebic, tournament, max_attempts):
+    """Tournament sizes on both sides of the paired-load path (T <= 4) and attempt counts that
+    give 1, 2, 8 and 16 warps per slot, generation by generation against the oracle."""
+    x = tiny_matrix()
+    gp, op = both_params(ebic, mode=2, tournament=tournament, max_attempts=max_attempts, seed=21)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        ctx.run_generations(gp, 0)
+        st = oebic.initialise(x, op)
+        for g in range(1, 7):
+            rep = ctx.run_generations(gp, 1)
+            assert oebic.next_generation(x, st, op)
+            assert rep.gens_done == g and rep.last_hits == st.hits[-1]
+            assert_same_state(ctx, st, gp)
+
+
+def test_large_population_multi_block_finish(ebic):
+    """A population large enough for several k_finish blocks (their hand-over to the last block)
+    and a candidate count past one warp, against the oracle."""
+    x = tiny_matrix()
+    gp, op = both_params(ebic, mode=1, pop_size=3000, elite=8, n_biclusters=8, seed=17)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        rep = ctx.run_generations(gp, 4)
+        st = oebic.run(x, op, 4)
+        assert rep.gens_done == st.gen == 4
+        assert rep.n_evaluated == st.n_evaluated
+        assert_same_state(ctx, st, gp)
