@@ -1512,9 +1512,9 @@ int gen_reset(ebic_ctx *ctx, GenState *g) {
   if (g->tcap) EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(g->tabu.p, 0, (size_t)g->tcap * 8, ctx->stream));
   GenCtl c0{};
   c0.gen = -1;
+  // (a copy from pageable memory has taken its source before the call returns)
   EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(g->ctl.p, &c0, sizeof(c0), cudaMemcpyHostToDevice,
                                        ctx->stream));
-  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   g->initialised = false;
   g->reset_pending = false;
   return EBIC_OK;
@@ -1774,9 +1774,13 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
       }
     }
   }
-  EBIC_TRY(read_ctl(ctx, g, &c));
+  // the counters and the kernels' error word, in one synchronisation
   int32_t kerr = 0;
-  EBIC_CHECK_CUDA(ctx, cudaMemcpy(&kerr, ctx->d_kerr.p, 4, cudaMemcpyDeviceToHost));
+  EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&c, g->ctl.p, sizeof(GenCtl), cudaMemcpyDeviceToHost,
+                                       ctx->stream));
+  EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&kerr, ctx->d_kerr.p, 4, cudaMemcpyDeviceToHost,
+                                       ctx->stream));
+  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (kerr) {
     cudaMemset(ctx->d_kerr.p, 0, 4);
     return ebic_fail(ctx, EBIC_ETIMEOUT, "a bounded device wait expired in the generation loop");
@@ -1792,7 +1796,6 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
     k.units += dlive * (double)ctx->R;
     prof_collect(ctx);
   }
-  EBIC_TRY(read_ctl(ctx, g, &c));
   if (rep) {
     memset(rep, 0, sizeof(*rep));
     rep->gens_done = c.gen;

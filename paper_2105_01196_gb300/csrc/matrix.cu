@@ -5,6 +5,8 @@
 // an increasing map of the finite floats onto uint32, so `k(a) > k(b)` is exactly `a > b`
 // (ties, including -0 against +0, compare equal) whatever the FTZ/DAZ mode of the arithmetic.
 // The trend definition the keys serve is Sec. 2.3 ("EBIC" paragraph) of the EBIC.jl paper.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace {
@@ -77,7 +79,9 @@ __global__ void k_upload_colmajor(const float *__restrict__ x, int64_t R, int32_
 // and the ballot of kb < ka gives G[b][a] (ties set neither).  The b-columns of the chunk stream
 // through a double-buffered shared-memory stage filled with cp.async, so their loads overlap
 // the ballots; lane 0 parks the 32 ballots of a pair in shared memory and the warp then writes
-// them as two coalesced 128-byte rows.
+// them as two coalesced 128-byte rows.  With few (chunk, a-block) pairs (small matrices), the
+// stages of b-columns are also split across blockIdx.z (stage st goes to z = st mod gridDim.z),
+// so the launch still fills the GPU and the long first a-blocks share their work.
 constexpr int kBW = 8;  // warps (a-columns) per block
 constexpr int kBS = 4;  // b-columns per stage
 
@@ -107,9 +111,11 @@ __global__ void __launch_bounds__(kBW * 32, 4) k_build_bitmap(const uint32_t *__
 #pragma unroll
   for (int j = 0; j < 32; ++j)
     ka[j] = (a_ok && j < nw) ? __ldg(keys + (int64_t)a * R_pad + (w0 + j) * 32 + lane) : 0u;
-  if (a_ok && lane < nw) G[((int64_t)a * C + a) * Wst + w0 + lane] = 0u;  // diagonal
+  if (a_ok && lane < nw && blockIdx.z == 0) G[((int64_t)a * C + a) * Wst + w0 + lane] = 0u;
   const int bstart = a0 + 1;
   const int nstages = bstart < C ? (C - bstart + kBS - 1) / kBS : 0;
+  const int S = (int)gridDim.z, z = (int)blockIdx.z;
+  const int my_stages = nstages > z ? (nstages - z + S - 1) / S : 0;  // stages z, z + S, ...
   const int pieces = nw * 8;  // 16-byte pieces of one column's chunk
   auto issue = [&](int st, int buf) {
     const int b0 = bstart + st * kBS;
@@ -121,16 +127,17 @@ __global__ void __launch_bounds__(kBW * 32, 4) k_build_bitmap(const uint32_t *__
     }
     cp_commit();
   };
-  if (nstages > 0) issue(0, 0);
-  for (int st = 0; st < nstages; ++st) {
-    if (st + 1 < nstages) {
-      issue(st + 1, (st + 1) & 1);
+  if (my_stages > 0) issue(z, 0);
+  for (int k = 0; k < my_stages; ++k) {
+    const int st = z + k * S;
+    if (k + 1 < my_stages) {
+      issue(st + S, (k + 1) & 1);
       cp_wait<1>();
     } else {
       cp_wait<0>();
     }
     __syncthreads();
-    const int buf = st & 1, b0 = bstart + st * kBS;
+    const int buf = k & 1, b0 = bstart + st * kBS;
     if (a_ok) {
       for (int bb = 0; bb < kBS; ++bb) {
         const int b = b0 + bb;
@@ -177,7 +184,18 @@ cudaError_t launch_upload(const float *x, int64_t R, int32_t C, int64_t R_pad, i
 
 cudaError_t launch_build_bitmap(const uint32_t *keys, int64_t R_pad, int32_t C, int64_t Wst,
                                 uint32_t *bitmap, cudaStream_t s) {
-  dim3 grid((unsigned)((Wst + 31) / 32), (unsigned)((C + kBW - 1) / kBW));
+  const int64_t gx = (Wst + 31) / 32, gy = (C + kBW - 1) / kBW;
+  // enough blocks for about four per SM, split over the b-stages of the first a-block at most
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  const int64_t max_split = std::max<int64_t>(1, (C - 1 + kBS - 1) / kBS);
+  const int64_t split =
+      std::min<int64_t>(max_split, std::max<int64_t>(1, (4LL * sms + gx * gy - 1) / (gx * gy)));
+  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)std::min<int64_t>(split, 65535));
   k_build_bitmap<<<grid, kBW * 32, 0, s>>>(keys, R_pad, C, Wst, bitmap);
   return cudaGetLastError();
 }
