@@ -111,15 +111,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_eval_codes(EvalArgs a, PopView 
   // Items are taken segment-major (all individuals of a row segment before the next segment),
   // so the codes of the segment stay in L2 while every individual reads them.  (Fetching the
   // next item's index ahead of the current item's work measured slower.)
-  int q = items::first(a.work, pv, lane);
-  if (q < 0) return;  // the run has stopped
-  for (; q < n_all; q = items::next(a.work, lane)) {
+  for (int q = items::first(); q < n_all; q = items::next(a.work, lane)) {
     if (q >= n_items) {
+      if (items::stopped(pv)) return;  // a stopped run changes nothing
       items::move_chunk(a, q - n_items, lane);
       continue;
     }
     const int seg = q / pv.n, i = q - seg * pv.n;
     const items::Meta m = items::load_meta(pv, i, lane);
+    if (items::stopped(pv)) return;  // (read with the item's loads; before any store)
     const int L = m.dead ? 0 : m.L;
     if (L >= 2) {
       const items::Insert ins = items::insert_start(pv, seg, m.h, lane);

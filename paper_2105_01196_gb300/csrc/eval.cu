@@ -79,15 +79,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_eval_direct(EvalArgs a, PopView
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t passes_total = a.R_pad / 128;
   const int32_t n_items = pv.n * a.n_seg, n_all = n_items + items::move_chunks(a);
-  int q = items::first(a.work, pv, lane);
-  if (q < 0) return;  // the run has stopped
-  for (; q < n_all; q = items::next(a.work, lane)) {
+  for (int q = items::first(); q < n_all; q = items::next(a.work, lane)) {
     if (q >= n_items) {
+      if (items::stopped(pv)) return;  // a stopped run changes nothing
       items::move_chunk(a, q - n_items, lane);
       continue;
     }
     const int seg = q / pv.n, i = q - seg * pv.n;  // segment-major
     const items::Meta m = items::load_meta(pv, i, lane);
+    if (items::stopped(pv)) return;  // (read with the item's loads; before any store)
     if (m.dead || m.L < 2) continue;
     const items::Insert ins = items::insert_start(pv, seg, m.h, lane);
     const int L = m.L;
@@ -226,15 +226,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
   const int64_t passes_total = (Wst + 127) / 128;
   const int32_t n_items = pv.n * a.n_seg, n_all = n_items + items::move_chunks(a);
   const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-  int q = items::first(a.work, pv, lane);
-  if (q < 0) return;  // the run has stopped
-  for (; q < n_all; q = items::next(a.work, lane)) {
+  for (int q = items::first(); q < n_all; q = items::next(a.work, lane)) {
     if (q >= n_items) {
+      if (items::stopped(pv)) return;  // a stopped run changes nothing
       items::move_chunk(a, q - n_items, lane);
       continue;
     }
     const int seg = q / pv.n, i = q - seg * pv.n;  // segment-major
     const items::Meta m = items::load_meta(pv, i, lane);
+    if (items::stopped(pv)) return;  // (read with the item's loads; before any store)
     if (m.dead || m.L < 2) continue;
     const items::Insert ins = items::insert_start(pv, seg, m.h, lane);
     const int L = m.L, np = L - 1;

@@ -39,21 +39,21 @@ __device__ __forceinline__ void move_chunk(const EvalArgs &a, int m, int lane) {
   if (lane == 0 && added) atomicAdd(a.mv_count, (unsigned long long)added);
 }
 
-// The next item of the warp (lane 0 takes it from the counter).
+// A warp's first item is its index in the launch (no round trip to the counter); the later
+// ones come from the counter, after the first items of all the launch's warps.
+__device__ __forceinline__ int first() {
+  return (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+}
+
 __device__ __forceinline__ int next(int32_t *work, int lane) {
   int q = 0;
   if (lane == 0) q = atomicAdd(work, 1);
-  return __shfl_sync(kFull, q, 0);
+  return __shfl_sync(kFull, q, 0) + (int)(gridDim.x * (blockDim.x >> 5));
 }
 
-// First item, fetched together with the stop flag; returns -1 when the run has stopped.
-__device__ __forceinline__ int first(int32_t *work, const PopView &pv, int lane) {
-  int q = 0;
-  if (lane == 0) q = atomicAdd(work, 1);
-  const bool stopped = pv.stop && *pv.stop;
-  q = __shfl_sync(kFull, q, 0);
-  return stopped ? -1 : q;
-}
+// Whether the run has stopped (the flag is read beside an item's first loads, and tested before
+// the item's first store).
+__device__ __forceinline__ bool stopped(const PopView &pv) { return pv.stop && *pv.stop; }
 
 struct Meta {
   int st, L;     // start in cols, length
