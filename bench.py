@@ -146,10 +146,24 @@ def scale_roofline(ebic, dev, stream, peak, peak_kind, sweeps=20):
     achieved = per_launch / avg_s / 1e9
     return {"workload": "batched", "kernel": "k_eval_bitmap", "bound": "hbm",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": ncu_traffic("k_eval_bitmap", "batched"),
             "peak_kind": peak_kind, "alg_bytes_per_launch": per_launch,
             "avg_launch_us": avg_s * 1e6, "launches": st["timed_launches"],
             "note": "bitmap (628 MB) larger than L2, so no flush between sweeps; algorithmic "
                     "bytes count every pair word read, some of which individuals share"}
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", "traffic_" + kernel + ".txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        for line in fh:
+            parts = line.split()
+            if len(parts) == 3 and not line.startswith("#") and parts[:2] == [kernel, workload]:
+                return float(parts[2])
+    return None
 
 
 def load_peaks():
@@ -463,7 +477,9 @@ def main():
         per_launch = se["alg_bytes"] / n_l
         achieved = per_launch / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": kernel_names["eval"],
+                "frac": achieved / peak,
+                "traffic": ncu_traffic(kernel_names["eval"], w.name),
+                "kernel": kernel_names["eval"],
                 "peak_kind": peak_kind, "alg_bytes_per_launch": per_launch,
                 "avg_launch_us": avg_s * 1e6, "launches": n_l,
                 "share_of_kernel_time": se["share_of_kernel_time"],
