@@ -2,23 +2,25 @@
 // elitism, tournament selection with an exponential penalty on overused columns, tabu list of
 // chromosome hashes, tabu-hit termination; parameters of Sec. 2.4's last paragraph).
 //
-// One generation is three kernels, captured once per buffer parity as a CUDA graph and replayed:
-//   k_evolve    one lane per (slot, attempt): elites from the top list (step 4), otherwise
-//               penalised tournament, optional one-point crossover and one mutation, tabu probe;
-//               the lowest attempt that misses the tabu list wins (step 5); live children enter
-//               this generation's duplicate table;
-//   k_eval_*    the persistent evaluation kernel (eval.cu) over the new population, skipping
-//               tabu-dead and duplicate slots (step 7);
-//   k_finish    all blocks: final dead flags, tabu hits, fitness, candidates for the top list,
-//               and the previous generation's keys moved from its duplicate table into the tabu
-//               list; then the last block to finish: tabu-hit stop test (step 6), top rank list
-//               update (step 7), column usage, counters for the next generation.
+// One generation is three kernels, captured as CUDA graphs (one per buffer parity, and one of
+// eight consecutive generations per starting parity) and replayed:
+//   k_evolve    one block per slot, one warp per tabu attempt: elites from the top list (step
+//               4), otherwise penalised tournament, optional one-point crossover and one
+//               mutation, tabu probe; the lowest attempt that misses the tabu list wins (step 5);
+//   k_eval_*    the persistent evaluation kernel (eval.cu, codes.cu) over the new population,
+//               skipping tabu-dead slots (step 7); it also enters the live keys into this
+//               generation's duplicate table and moves the previous generation's table into the
+//               hashed tabu list;
+//   k_finish    all blocks: final dead flags (tabu or duplicate), tabu hits, fitness, candidates
+//               for the top list; then the last block to finish: tabu-hit stop test (step 6),
+//               top rank list update (step 7), column usage, counters for the next generation.
+// k_init builds the initial population (step 1), one warp per slot.
 // Generation g reads population buffer (g-1)&1 and writes g&1, and uses duplicate table g&1.
 // The tabu list a child is probed against is the hashed set of generations <= g-2 plus the
-// duplicate table of generation g-1 (its live non-elite keys), which is the whole tabu list as
-// it stood at the start of generation g.  Once the stop flag is set every kernel returns at once,
-// so further replays are no-ops.  The random words come from
-// Philox4x32-10 (Salmon et al., SC'11) with counter (generation, slot, attempt, block).
+// duplicate table of generation g-1 (its live keys), which is the whole tabu list as it stood at
+// the start of generation g.  Once the stop flag is set every kernel returns before its first
+// store, so further replays are no-ops.  The random words come from Philox4x32-10 (Salmon et
+// al., SC'11) with counter (generation, slot, attempt, block).
 #include <string.h>
 
 #include <algorithm>
@@ -31,7 +33,6 @@ namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kS = EBIC_MAX_LEN;  // population slot stride (columns)
-constexpr int kSlotThreads = 64;
 constexpr int kTopThreads = 1024;
 constexpr int kSortSmemMax = 4096;  // most candidates sorted in shared memory
 constexpr size_t kFinishSmemMax = 180 * 1024;  // dynamic shared memory limit set for k_finish
@@ -125,29 +126,10 @@ __device__ __noinline__ uint4 philox_block_call(uint32_t k0, uint32_t k1, uint32
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// The word stream of counter (g, s, a): the words of blocks 0, 1, 2, ... in order, one thread.
-struct WordStream {
-  uint32_t k0, k1, c0, c1, c2, blk;
-  uint32_t w[4];
-  int pos;
-  __device__ WordStream(uint64_t seed, uint32_t g, uint32_t s, uint32_t a)
-      : k0((uint32_t)seed), k1((uint32_t)(seed >> 32)), c0(g), c1(s), c2(a), blk(0), pos(4) {}
-  __device__ uint32_t next() {
-    if (pos == 4) {
-      philox_block(k0, k1, c0, c1, c2, blk++, w);
-      pos = 0;
-    }
-    const uint32_t v = pos == 0 ? w[0] : (pos == 1 ? w[1] : (pos == 2 ? w[2] : w[3]));
-    ++pos;
-    return v;
-  }
-  // Uniform integer in [0, n): high word of word * n.
-  __device__ uint32_t below(uint32_t n) { return __umulhi(next(), n); }
-};
-
-// The same word stream for a whole warp: lane j holds block base + j, so one round of Philox
-// in all lanes yields 128 words, and word i comes from lane i / 4 - base by a shuffle (every
-// lane calls next() together and gets the same word).  The sequence is that of WordStream.
+// The word stream of counter (g, s, a) - the words of Philox blocks 0, 1, 2, ... in order - for
+// a whole warp: lane j holds block base + j, so one round of Philox in all lanes yields 128
+// words, and word i comes from lane i / 4 - base by a shuffle (every lane calls next() together
+// and gets the same word).
 struct WarpStream {
   uint32_t k0, k1, c0, c1, c2;
   uint32_t w[4];
@@ -210,43 +192,8 @@ __device__ __forceinline__ int cmp_penalised(uint64_t fa, int ua, uint64_t fb, i
 
 // ------------------------------------------------------------------ variation
 
-__device__ __forceinline__ bool contains(const int32_t *c, int L, int v) {
-  for (int k = 0; k < L; ++k)
-    if (c[k] == v) return true;
-  return false;
-}
-
-// A column not in c[0..L), by up to 64 uniform draws; -1 when every draw hit.
-__device__ int draw_free(WordStream &st, int C, const int32_t *c, int L) {
-  for (int t = 0; t < 64; ++t) {
-    const int v = (int)st.below((uint32_t)C);
-    if (!contains(c, L, v)) return v;
-  }
-  return -1;
-}
-
 // ------------------------------------------------------------------ kernels
 
-__global__ void __launch_bounds__(kSlotThreads) k_init(GenArgs ga, Buf nb) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= ga.P) return;
-  WordStream st(ga.seed, 0u, (uint32_t)s, 0u);
-  int32_t c[kS];
-  const int want = ga.init_min + (int)st.below((uint32_t)(ga.init_max - ga.init_min + 1));
-  int L = 0;
-  for (int j = 0; j < want; ++j) {
-    const int v = draw_free(st, ga.C, c, L);
-    if (v < 0) break;
-    c[L++] = v;
-  }
-  int32_t *out = nb.cols + (size_t)s * kS;
-  for (int k = 0; k < kS; ++k) out[k] = k < L ? c[k] : 0;
-  nb.len[s] = L;
-  const bool dead = L < 2;
-  nb.att_dead[s] = dead;
-  nb.att_hits[s] = 0;
-  nb.hash[s] = chromosome_key(c, L);  // (the scoring launch enters live keys in the table)
-}
 
 // ------------------------------------------------------------------ warp-cooperative children
 // One warp builds one child.  The word stream and every decision are uniform across the warp (all
@@ -554,6 +501,38 @@ __device__ void w_make_child(const GenArgs &ga, const Buf &pb, int g, int s, int
     L = LA;
   }
   w_mutate(st, c, L, ga.C, ga.max_len, lane);
+}
+
+// Step 1: the initial population, one warp per slot (generation 0, attempt 0 of the word
+// stream): length init_min + below(init_max - init_min + 1), then that many columns, each by at
+// most 64 draws that avoid the columns already present (the chromosome ends early when all 64
+// hit).
+constexpr int kInitWarps = 8;
+__global__ void __launch_bounds__(kInitWarps * 32) k_init(GenArgs ga, Buf nb) {
+  __shared__ int32_t s_c[kInitWarps][kS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int s = blockIdx.x * kInitWarps + warp;
+  if (s >= ga.P) return;  // (whole warps)
+  int32_t *c = s_c[warp];
+  WarpStream st(ga.seed, 0u, (uint32_t)s, 0u, lane);
+  const int want = ga.init_min + (int)st.below((uint32_t)(ga.init_max - ga.init_min + 1));
+  int L = 0;
+  for (int j = 0; j < want; ++j) {
+    const int v = w_draw_free(st, ga.C, c, L, lane);
+    if (v < 0) break;
+    if (lane == 0) c[L] = v;
+    __syncwarp();
+    ++L;
+  }
+  int32_t *out = nb.cols + (size_t)s * kS;
+  out[lane] = lane < L ? c[lane] : 0;
+  out[lane + 32] = lane + 32 < L ? c[lane + 32] : 0;
+  if (lane == 0) {
+    nb.len[s] = L;
+    nb.att_dead[s] = L < 2;
+    nb.att_hits[s] = 0;
+    nb.hash[s] = chromosome_key(c, L);  // (the scoring launch enters live keys in the table)
+  }
 }
 
 // One block per slot, one warp per attempt (G warps, G = the power of two >= max_attempts): the
@@ -1720,12 +1699,12 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
   EBIC_TRY(read_ctl(ctx, g, &c));
   EBIC_TRY(ensure_tabu(ctx, g, c.tabu_count + (int64_t)g->P * ((int64_t)n_gen + 2)));
   cudaStream_t s = ctx->stream;
-  const unsigned iblocks = (unsigned)((g->P + kSlotThreads - 1) / kSlotThreads);
   const GenCtl c_start = c;
   if (!g->initialised) {
     Marks m;
     const bool timed = ctx->prof && take_marks(ctx, &m, false);
-    k_init<<<iblocks, kSlotThreads, 0, s>>>(gen_args(ctx, g), g->buf(0));
+    k_init<<<(unsigned)((g->P + kInitWarps - 1) / kInitWarps), kInitWarps * 32, 0, s>>>(
+        gen_args(ctx, g), g->buf(0));
     EBIC_CHECK_CUDA(ctx, cudaGetLastError());
     EBIC_CHECK_CUDA(ctx, launch_scoring(ctx, g, 0, s, timed ? &m : nullptr));
     if (timed) push_generation_timing(ctx, m, false);
