@@ -159,7 +159,8 @@ EBIC_API int ebic_load_matrix(ebic_ctx *ctx, const float *x, int64_t rows, int32
  * Builds the column-pair comparison bitmap of the loaded matrix: for every ordered pair of
  * columns (a, b), word w bit j is [x(32w+j, b) > x(32w+j, a)].  Its size is
  * ebic_bitmap_bytes(rows, cols).  EBIC_MODE_BITMAP builds it on first use; this call builds it
- * ahead of time.  Errors: EBIC_ESTATE (no matrix), EBIC_ENOMEM, EBIC_ECUDA.
+ * ahead of time, queued on the context's stream (every later call of the context is ordered
+ * after it).  Errors: EBIC_ESTATE (no matrix), EBIC_ENOMEM, EBIC_ECUDA.
  */
 EBIC_API int ebic_build_bitmap(ebic_ctx *ctx);
 

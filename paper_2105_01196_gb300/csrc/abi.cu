@@ -419,8 +419,10 @@ int ebic_build_bitmap(ebic_ctx *ctx) {
   prof_end(ctx, ev, EBIC_KERNEL_BITMAP_BUILD, (double)bytes,
            (double)ctx->C * ctx->C * (double)ctx->R, 0.0);
   prof_count(ctx, EBIC_KERNEL_BITMAP_BUILD, 1);
-  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  prof_collect(ctx);
+  if (ctx->prof) {  // (later work on the stream is ordered after the build anyway)
+    EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    prof_collect(ctx);
+  }
   ctx->bitmap_ok = true;
   return EBIC_OK;
 }
@@ -541,8 +543,10 @@ int ensure_codes(ebic_ctx *ctx) {
            (double)C * ctx->R_pad * 4.0 + (double)C * S * ctx->code_bytes,
            (double)C * C * (double)ctx->R_pad, (double)ctx->R_pad);
   prof_count(ctx, EBIC_KERNEL_RANK_CODES, 1);
-  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  prof_collect(ctx);
+  if (ctx->prof) {  // (later work on the stream is ordered after the build anyway)
+    EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    prof_collect(ctx);
+  }
   ctx->codes_ready = true;
   return EBIC_OK;
 }
