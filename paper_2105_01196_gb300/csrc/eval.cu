@@ -287,16 +287,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
           cnt_zero(P[j]);
           cnt_zero(N[j]);
         }
-        for (int k = 0; k < np; k += 8) {
-          uint4 v[8], u[8];
+        constexpr int RC = NEG ? 4 : 8;  // pairs per round (the counters of both directions
+                                         // and 8 pairs' words exceed the register budget)
+        for (int k = 0; k < np; k += RC) {
+          uint4 v[RC], u[RC];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
+          for (int j = 0; j < RC; ++j) {
             const bool in = k + j < np;
             v[j] = in ? ldb<NS>(act, G + s_pos[warp][k + j]) : zero4;
             if (NEG) u[j] = in ? ldb<NS>(act, G + s_neg[warp][k + j]) : zero4;
           }
 #pragma unroll
-          for (int h = 0; h < 8; h += 4) {
+          for (int h = 0; h < RC; h += 4) {
             cnt_add4(P[0], v[h].x, v[h + 1].x, v[h + 2].x, v[h + 3].x);
             cnt_add4(P[1], v[h].y, v[h + 1].y, v[h + 2].y, v[h + 3].y);
             cnt_add4(P[2], v[h].z, v[h + 1].z, v[h + 2].z, v[h + 3].z);
