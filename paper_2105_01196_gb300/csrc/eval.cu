@@ -198,13 +198,18 @@ __device__ __forceinline__ int popc4(uint4 v) {
   return __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
 }
 
-// A pair word of the bitmap for lane-active words (zero otherwise); with ties counting (NS) the
-// word is the complement of the opposite direction's word: key(d) >= key(c) = not key(c) > key(d).
+__device__ __forceinline__ uint4 not4(uint4 v) { return make_uint4(~v.x, ~v.y, ~v.z, ~v.w); }
+
+// A pair word of the bitmap where `on`, else `fill` (the identity of the operation it feeds).
+// With ties counting (NS) the word is the complement of the opposite direction's word:
+// key(d) >= key(c) = not key(c) > key(d).  The complement is applied after a load that is the
+// same predicated load as in the strict form (fill complemented beforehand): selecting between a
+// loaded word's complement and a constant instead made the NS forms 1.6-2.8x slower.
 template <bool NS>
-__device__ __forceinline__ uint4 ldb(bool act, const uint32_t *p) {
-  if (!act) return make_uint4(0u, 0u, 0u, 0u);
-  const uint4 v = ldg4(p);
-  return NS ? make_uint4(~v.x, ~v.y, ~v.z, ~v.w) : v;
+__device__ __forceinline__ uint4 ldb(bool on, const uint32_t *p, uint4 fill) {
+  uint4 v = NS ? not4(fill) : fill;
+  if (on) v = ldg4(p);
+  return NS ? not4(v) : v;
 }
 
 // Rows of word w that exist (bit j = row 32 w + j < R).
@@ -269,8 +274,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const bool in = k + j < np;
-            v[j] = in ? ldb<NS>(act, G + s_pos[warp][k + j]) : ones;
-            if (NEG) u[j] = in ? ldb<NS>(act, G + s_neg[warp][k + j]) : ones;
+            v[j] = ldb<NS>(act && in, G + (in ? s_pos[warp][k + j] : 0), ones);
+            if (NEG) u[j] = ldb<NS>(act && in, G + (in ? s_neg[warp][k + j] : 0), ones);
           }
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
@@ -294,8 +299,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
 #pragma unroll
           for (int j = 0; j < RC; ++j) {
             const bool in = k + j < np;
-            v[j] = in ? ldb<NS>(act, G + s_pos[warp][k + j]) : zero4;
-            if (NEG) u[j] = in ? ldb<NS>(act, G + s_neg[warp][k + j]) : zero4;
+            v[j] = ldb<NS>(act && in, G + (in ? s_pos[warp][k + j] : 0), zero4);
+            if (NEG) u[j] = ldb<NS>(act && in, G + (in ? s_neg[warp][k + j] : 0), zero4);
           }
 #pragma unroll
           for (int h = 0; h < RC; h += 4) {
