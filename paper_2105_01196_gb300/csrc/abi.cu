@@ -301,12 +301,15 @@ int ebic_create(ebic_ctx **out, int32_t device, void *cuda_stream) {
   if (!ctx) return EBIC_ENOMEM;
   ctx->device = device;
   DeviceGuard g(device);
+  int l2 = 0;
   if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) !=
-      cudaSuccess) {
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device) != cudaSuccess) {
     cudaGetLastError();
     delete ctx;
     return EBIC_ECUDA;
   }
+  ctx->l2_bytes = l2;
   if (cuda_stream) {
     ctx->stream = (cudaStream_t)cuda_stream;
   } else {
@@ -413,6 +416,7 @@ int ebic_build_bitmap(ebic_ctx *ctx) {
   DeviceGuard g(ctx->device);
   const size_t bytes = (size_t)ebic_bitmap_bytes(ctx->R, ctx->C);
   EBIC_CHECK_CUDA(ctx, ctx->bitmap.ensure(bytes));
+  EBIC_CHECK_CUDA(ctx, prepare_bitmap_eval());
   cudaEvent_t ev = prof_begin(ctx);
   EBIC_CHECK_CUDA(ctx, launch_build_bitmap(ctx->keys.as<uint32_t>(), ctx->R_pad, ctx->C, ctx->Wst,
                                            ctx->bitmap.as<uint32_t>(), ctx->stream));
@@ -574,6 +578,7 @@ EvalArgs eval_args_for(const ebic_ctx *ctx) {
   a.codes = ctx->codes_ready ? ctx->codes.as<uint8_t>() : nullptr;
   a.code_bytes = ctx->codes_ready ? ctx->code_bytes : 0;
   a.S = ctx->codes_ready ? ctx->code_stride : 0;
+  a.stage_bitmap = ctx->bitmap_ok && (double)ebic_bitmap_bytes(ctx->R, ctx->C) > (double)ctx->l2_bytes;
   return a;
 }
 

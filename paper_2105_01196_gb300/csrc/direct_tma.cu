@@ -16,54 +16,18 @@
 
 #include "internal.h"
 #include "tables.cuh"
+#include "tma.cuh"
 
 namespace {
+
+using tma::mbar_expect_tx;
+using tma::mbar_init;
+using tma::mbar_wait;
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-constexpr uint32_t kWaitLimit = 1u << 22;
 constexpr size_t kStagedSmemMax = 192 * 1024;  // stage buffers; the static part comes on top
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-// Bounded wait for phase `parity` of the barrier; false when the limit expired.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  const uint32_t a = smem_addr(bar);
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
-                                            uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
-      : "memory");
-}
 
 __device__ __forceinline__ int threshold(int L, int num, int den) {
   return (num * (L - 1) + den - 1) / den;
@@ -95,7 +59,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t stage_bytes = (uint32_t)sa.stage_words * 4u;
   if (threadIdx.x == 0) {
     for (int s = 0; s < sa.stages; ++s) mbar_init(&s_bar[s], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    tma::fence_mbar_init();
   }
   __syncthreads();
   auto issue = [&](int item, int stage) {  // thread 0: copy the tile of `item` into `stage`
@@ -103,7 +67,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t *dst = s_tile + (size_t)stage * sa.stage_words;
     mbar_expect_tx(&s_bar[stage], stage_bytes);
     for (int b = 0; b < sa.nbox; ++b)
-      tma_load_2d(dst + (size_t)b * sa.CB * sa.TR, &map, tile * sa.TR, b * sa.CB, &s_bar[stage]);
+      tma::tensor_load_2d(dst + (size_t)b * sa.CB * sa.TR, &map, tile * sa.TR, b * sa.CB,
+                          &s_bar[stage]);
   };
   int item = blockIdx.x;
   bool pending[2] = {false, false};  // a copy into the stage is in flight (tracked by thread 0)

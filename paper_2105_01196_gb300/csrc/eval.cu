@@ -17,6 +17,8 @@
 // segment, so the segment's data stays in L2 while all individuals read it), then the chunks of
 // the generation loop's side task (items.cuh), and add their partial counts with one atomic per
 // item.
+#include <mutex>
+
 #include "internal.h"
 #include "tables.cuh"
 #include "items.cuh"
@@ -27,6 +29,7 @@ namespace {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
+constexpr int kMaxDevices = 64;
 
 __device__ __forceinline__ int threshold(int L, int num, int den) {
   return (num * (L - 1) + den - 1) / den;
@@ -198,11 +201,31 @@ __device__ __forceinline__ int popc4(uint4 v) {
   return __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
 }
 
+// Rows of word w that exist (bit j = row 32 w + j < R).
+__device__ __forceinline__ uint32_t valid_bits(int64_t w, int64_t R) {
+  const int64_t n = R - 32 * w;
+  return n >= 32 ? kFull : (n <= 0 ? 0u : ((1u << n) - 1u));
+}
+
+// A pass covers 128 words (4096 rows) of a column pair; lane l holds words 4l..4l+3.
+constexpr int kPassWords = 128;
+
+// Staged form: each warp has kStageBytes of shared memory, one pass of NB pairs per direction.
+// The lanes copy the pair words of up to NB pairs with asynchronous copies (cp.async, 16 bytes
+// each, no registers held while they are in flight) and wait once, so an individual of np pairs
+// costs ceil(np / NB) round trips to memory.  Each lane reads back only the bytes it copied.
+constexpr uint32_t kStageBytes = 12 * 1024;
+template <bool NEG>
+__host__ __device__ constexpr int stage_pairs() {
+  return (int)(kStageBytes / (kPassWords * 4u)) / (NEG ? 2 : 1);  // 12 with NEG, else 24
+}
+constexpr size_t kBitmapSmem = (size_t)kWarps * kStageBytes;
+
 __device__ __forceinline__ uint4 not4(uint4 v) { return make_uint4(~v.x, ~v.y, ~v.z, ~v.w); }
 
-// A pair word of the bitmap where `on`, else `fill` (the identity of the operation it feeds).
-// With ties counting (NS) the word is the complement of the opposite direction's word:
-// key(d) >= key(c) = not key(c) > key(d).  The complement is applied after a load that is the
+// A pair word where `on`, else `fill` (the identity of the operation it feeds), from global
+// (ldb) or staged shared memory (lds).  With ties counting (NS) the word is the complement of the
+// opposite direction's word: key(d) >= key(c) = not key(c) > key(d).  The complement follows the
 // same predicated load as in the strict form (fill complemented beforehand): selecting between a
 // loaded word's complement and a constant instead made the NS forms 1.6-2.8x slower.
 template <bool NS>
@@ -212,25 +235,66 @@ __device__ __forceinline__ uint4 ldb(bool on, const uint32_t *p, uint4 fill) {
   return NS ? not4(v) : v;
 }
 
-// Rows of word w that exist (bit j = row 32 w + j < R).
-__device__ __forceinline__ uint32_t valid_bits(int64_t w, int64_t R) {
-  const int64_t n = R - 32 * w;
-  return n >= 32 ? kFull : (n <= 0 ? 0u : ((1u << n) - 1u));
+template <bool NS>
+__device__ __forceinline__ uint4 lds(bool on, const uint32_t *p, uint4 fill) {
+  uint4 v = NS ? not4(fill) : fill;
+  if (on) v = *reinterpret_cast<const uint4 *>(p);
+  return NS ? not4(v) : v;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t *dst, const uint32_t *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"((uint64_t)__cvta_generic_to_global(src))
+               : "memory");
+}
+
+// Waits for all of this thread's asynchronous copies (a bounded hardware wait).
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
+
+// Adds four pair words per direction to the bit-sliced counters.
+template <bool NEG>
+__device__ __forceinline__ void cnt_add_group(Cnt6 (&P)[4], Cnt6 (&N)[4], const uint4 (&v)[4],
+                                              const uint4 (&u)[4]) {
+  cnt_add4(P[0], v[0].x, v[1].x, v[2].x, v[3].x);
+  cnt_add4(P[1], v[0].y, v[1].y, v[2].y, v[3].y);
+  cnt_add4(P[2], v[0].z, v[1].z, v[2].z, v[3].z);
+  cnt_add4(P[3], v[0].w, v[1].w, v[2].w, v[3].w);
+  if (NEG) {
+    cnt_add4(N[0], u[0].x, u[1].x, u[2].x, u[3].x);
+    cnt_add4(N[1], u[0].y, u[1].y, u[2].y, u[3].y);
+    cnt_add4(N[2], u[0].z, u[1].z, u[2].z, u[3].z);
+    cnt_add4(N[3], u[0].w, u[1].w, u[2].w, u[3].w);
+  }
 }
 
 // NS: ties count for both directions (complemented opposite words; pad rows masked out).  The
 // last-kept variant has no pair-word form (its reference value differs from row to row).
-template <bool NEG, bool NS>
+// STAGE: pair words staged in shared memory, for bitmaps larger than L2 whose words stream from
+// HBM (more bytes in flight per warp), unless every item is exact (ratio 1: the AND needs no
+// counter registers, so rounds of 8 pairs fit in registers).  Otherwise rounds of register loads.
+// Staging measured slower where L2 holds the bitmap and with ratio 1; register loads inside the
+// staged kernel measured slower still (its shared memory leaves the L1 too little room for the
+// loads in flight), so that kernel stages every item.
+template <bool NEG, bool NS, bool STAGE>
 __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView pv) {
+  extern __shared__ __align__(128) uint32_t s_stage[];  // kStageBytes per warp (STAGE)
   __shared__ int64_t s_pos[kWarps][EBIC_MAX_LEN];
   __shared__ int64_t s_neg[kWarps][EBIC_MAX_LEN];
   __shared__ int32_t s_col[kWarps][EBIC_MAX_LEN];
+  constexpr int NB = stage_pairs<NEG>();
+  static_assert(NB % 4 == 0, "staged batches are read in groups of four pairs");
   wait_prior_grid();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t *sp = s_stage + (size_t)warp * (kStageBytes / 4) + lane * 4;  // pair j: sp + 128 j
+  uint32_t *sn = sp + NB * kPassWords;                                    // negative direction
   const int64_t Wst = a.Wst;
-  const int64_t passes_total = (Wst + 127) / 128;
+  const int64_t passes_total = (Wst + kPassWords - 1) / kPassWords;
   const int32_t n_items = pv.n * a.n_seg, n_all = n_items + items::move_chunks(a);
   const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+  const uint4 ones = make_uint4(kFull, kFull, kFull, kFull);
   for (int q = items::first(); q < n_all; q = items::next(a.work, lane)) {
     if (q >= n_items) {
       if (items::stopped(pv)) return;  // a stopped run changes nothing
@@ -259,16 +323,46 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
     const int64_t p1 = min(p0 + a.seg_passes, passes_total);
     int cp = 0, cn = 0, ca = 0;
     for (int64_t pass = p0; pass < p1; ++pass) {
-      const int64_t w = pass * 128 + lane * 4;
-      const bool act = w < Wst;
+      const int64_t w = pass * kPassWords + lane * 4;
+      const bool act = w < Wst;  // (Wst is a multiple of 4: a lane's 4 words all exist or not)
       const uint32_t *G = a.bitmap + w;
-      uint4 pos, neg = zero4;
-      // The pair words of a round of pairs are loaded together, the last round padded with the
-      // operation's identity (all ones for the AND, zero for the counters), so an individual
-      // of np pairs costs ceil(np / round) dependent load rounds.
-      if (exact) {
-        const uint4 ones = make_uint4(kFull, kFull, kFull, kFull);
-        uint4 ap = ones, an = ones;
+      uint4 ap = ones, an = ones;
+      Cnt6 P[4], N[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        cnt_zero(P[j]);
+        cnt_zero(N[j]);
+      }
+      if (STAGE) {
+        for (int k0 = 0; k0 < np; k0 += NB) {
+          const int nb = min(NB, np - k0);
+          if (act)
+            for (int j = 0; j < nb; ++j) {
+              cp_async16(sp + j * kPassWords, G + s_pos[warp][k0 + j]);
+              if (NEG) cp_async16(sn + j * kPassWords, G + s_neg[warp][k0 + j]);
+            }
+          cp_async_wait_all();
+          if (exact) {
+            for (int j = 0; j < nb; ++j) {
+              ap = and4(ap, lds<NS>(act, sp + j * kPassWords, ones));
+              if (NEG) an = and4(an, lds<NS>(act, sn + j * kPassWords, ones));
+            }
+          } else {
+            for (int h = 0; h < nb; h += 4) {  // (the last group padded with zeros)
+              uint4 v[4], u[4];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const bool in = act && h + j < nb;
+                v[j] = lds<NS>(in, sp + (h + j) * kPassWords, zero4);
+                u[j] = NEG ? lds<NS>(in, sn + (h + j) * kPassWords, zero4) : zero4;
+              }
+              cnt_add_group<NEG>(P, N, v, u);
+            }
+          }
+        }
+      } else if (exact) {
+        // The pair words of a round are loaded together, the last round padded with the
+        // operation's identity, so np pairs cost ceil(np / 8) dependent load rounds.
         for (int k = 0; k < np; k += 8) {
           uint4 v[8], u[8];
 #pragma unroll
@@ -283,15 +377,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
             if (NEG) an = and4(an, u[j]);
           }
         }
-        pos = act ? ap : zero4;
-        if (NEG) neg = act ? an : zero4;
       } else {
-        Cnt6 P[4], N[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          cnt_zero(P[j]);
-          cnt_zero(N[j]);
-        }
         constexpr int RC = NEG ? 4 : 8;  // pairs per round (the counters of both directions
                                          // and 8 pairs' words exceed the register budget)
         for (int k = 0; k < np; k += RC) {
@@ -304,18 +390,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
           }
 #pragma unroll
           for (int h = 0; h < RC; h += 4) {
-            cnt_add4(P[0], v[h].x, v[h + 1].x, v[h + 2].x, v[h + 3].x);
-            cnt_add4(P[1], v[h].y, v[h + 1].y, v[h + 2].y, v[h + 3].y);
-            cnt_add4(P[2], v[h].z, v[h + 1].z, v[h + 2].z, v[h + 3].z);
-            cnt_add4(P[3], v[h].w, v[h + 1].w, v[h + 2].w, v[h + 3].w);
-            if (NEG) {
-              cnt_add4(N[0], u[h].x, u[h + 1].x, u[h + 2].x, u[h + 3].x);
-              cnt_add4(N[1], u[h].y, u[h + 1].y, u[h + 2].y, u[h + 3].y);
-              cnt_add4(N[2], u[h].z, u[h + 1].z, u[h + 2].z, u[h + 3].z);
-              cnt_add4(N[3], u[h].w, u[h + 1].w, u[h + 2].w, u[h + 3].w);
-            }
+            const uint4 vv[4] = {v[h], v[h + 1], v[h + 2], v[h + 3]};
+            const uint4 uu[4] = {NEG ? u[h] : zero4, NEG ? u[h + 1] : zero4,
+                                 NEG ? u[h + 2] : zero4, NEG ? u[h + 3] : zero4};
+            cnt_add_group<NEG>(P, N, vv, uu);
           }
         }
+      }
+      uint4 pos, neg = zero4;
+      if (exact) {
+        pos = act ? ap : zero4;
+        if (NEG) neg = act ? an : zero4;
+      } else {
         pos = make_uint4(cnt_ge(P[0], t), cnt_ge(P[1], t), cnt_ge(P[2], t), cnt_ge(P[3], t));
         if (NEG)
           neg = make_uint4(cnt_ge(N[0], t), cnt_ge(N[1], t), cnt_ge(N[2], t), cnt_ge(N[3], t));
@@ -386,9 +472,9 @@ __global__ void k_fitness(EvalArgs a, PopView pv) {
   a.fitness[i] = (dead || ra < a.min_rows) ? 0ull : ((uint64_t)ra << sh);
 }
 
-int blocks_per_sm_for(const void *kernel) {
+int blocks_per_sm_for(const void *kernel, size_t smem) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kThreads, smem) != cudaSuccess) {
     cudaGetLastError();
     nb = 1;
   }
@@ -444,10 +530,32 @@ static EvalKernel direct_kernel(bool neg, bool ns, bool lk) {
   return t[(neg ? 4 : 0) + (ns ? 2 : 0) + (lk ? 1 : 0)];
 }
 
-static EvalKernel bitmap_kernel(bool neg, bool ns) {
-  static const EvalKernel t[4] = {k_eval_bitmap<false, false>, k_eval_bitmap<false, true>,
-                                  k_eval_bitmap<true, false>, k_eval_bitmap<true, true>};
-  return t[(neg ? 2 : 0) + (ns ? 1 : 0)];
+static EvalKernel bitmap_kernel(bool neg, bool ns, bool stage) {
+  static const EvalKernel t[8] = {
+      k_eval_bitmap<false, false, false>, k_eval_bitmap<false, false, true>,
+      k_eval_bitmap<false, true, false>,  k_eval_bitmap<false, true, true>,
+      k_eval_bitmap<true, false, false>,  k_eval_bitmap<true, false, true>,
+      k_eval_bitmap<true, true, false>,   k_eval_bitmap<true, true, true>};
+  return t[(neg ? 4 : 0) + (ns ? 2 : 0) + (stage ? 1 : 0)];
+}
+
+cudaError_t prepare_bitmap_eval() {
+  // one fixed limit for every context (no call lowers another's), set once per device
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static bool attr_set[kMaxDevices] = {};
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (attr_set[dev]) return cudaSuccess;
+  for (int k = 0; k < 4; ++k)
+    if ((e = cudaFuncSetAttribute(bitmap_kernel(k & 2, k & 1, true),
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kBitmapSmem)) != cudaSuccess)
+      return e;
+  attr_set[dev] = true;
+  return cudaSuccess;
 }
 
 cudaError_t launch_eval_kernel(int mode, const EvalArgs &a0, const PopView &pv, int num_sms,
@@ -464,9 +572,15 @@ cudaError_t launch_eval_kernel(int mode, const EvalArgs &a0, const PopView &pv, 
   EvalArgs a = a0;
   const bool bitmap = (mode == EBIC_MODE_BITMAP);
   const int64_t passes_total = bitmap ? (a.Wst + 127) / 128 : a.R_pad / 128;
-  const EvalKernel kern = bitmap ? bitmap_kernel(a.neg, a.non_strict)
+  const bool stage = bitmap && a.stage_bitmap && a.rnum < a.rden;  // (ratio 1: all exact)
+  const EvalKernel kern = bitmap ? bitmap_kernel(a.neg, a.non_strict, stage)
                                  : direct_kernel(a.neg, a.non_strict, a.last_kept);
-  const int bps = blocks_per_sm_for((const void *)kern);
+  const size_t smem = stage ? kBitmapSmem : 0;
+  if (stage) {
+    const cudaError_t e = prepare_bitmap_eval();
+    if (e != cudaSuccess) return e;
+  }
+  const int bps = blocks_per_sm_for((const void *)kern, smem);
   const int64_t warps = (int64_t)num_sms * bps * kWarps;
   // Segments: the autotuner's size when it set one, else enough work items for ~8 per
   // resident warp; at most 2^30 items in total.
@@ -484,7 +598,7 @@ cudaError_t launch_eval_kernel(int mode, const EvalArgs &a0, const PopView &pv, 
   int64_t grid = (int64_t)num_sms * bps;
   const int64_t need = (items + kWarps - 1) / kWarps;
   if (grid > need) grid = need;
-  return launch_maybe_pdl(kern, dim3((unsigned)grid), dim3(kThreads), 0, s, pdl, a, pv);
+  return launch_maybe_pdl(kern, dim3((unsigned)grid), dim3(kThreads), smem, s, pdl, a, pv);
 }
 
 cudaError_t launch_eval(int mode, const EvalArgs &a, const PopView &pv, int num_sms,

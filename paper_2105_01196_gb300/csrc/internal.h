@@ -94,6 +94,8 @@ struct EvalArgs {
   const uint8_t *codes;           // [C][S] per-row rank codes (codes.cu), or nullptr
   int32_t code_bytes;             // bytes per code: 1 or 2 (0: the direct form reads keys)
   int64_t S;                      // rows per code column (a multiple of one pass)
+  int32_t stage_bitmap;           // the bitmap kernel stages pair words in shared memory (set
+                                  // when the bitmap exceeds L2: its words stream from HBM)
 };
 
 // Per-row rank codes (codes.cu): code width for C columns (1 for C <= 128, 2 for C <= 1024,
@@ -136,6 +138,7 @@ struct ebic_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int num_sms = 0;
+  int64_t l2_bytes = 0;  // the device's L2 size
   std::string err;
 
   // matrix
@@ -240,6 +243,9 @@ cudaError_t launch_eval_plain(const EvalArgs &a, const int32_t *d_cols, int32_t 
 cudaError_t launch_eval_kernel(int mode, const EvalArgs &a, const PopView &pv, int num_sms,
                                cudaStream_t s, bool pdl = false);
 cudaError_t launch_fitness(const EvalArgs &a, const PopView &pv, cudaStream_t s);
+// Raises the bitmap kernels' dynamic shared-memory limit on the current device (once per device;
+// done before any graph capture, with the bitmap's build).
+cudaError_t prepare_bitmap_eval();
 int choose_mode(const ebic_ctx *ctx, int requested, int64_t n_ind, double mean_len,
                 int expected_sweeps, int last_kept);
 

@@ -269,3 +269,27 @@ def test_trend_variants_default_workload(ebic):
                 p = ebic.Params.make(neg_trends=1, ratio_num=85, ratio_den=100, mode=mode,
                                      non_strict=ns, last_kept=lk)
                 assert_parity(ctx.eval_population(ci, off, p), want)
+
+
+def test_bitmap_larger_than_l2_all_variants(ebic, torch_cuda):
+    """A pair bitmap larger than the device's L2 (243 MB), which the bitmap kernel reads through
+    its shared-memory staging for ratios below 1 (exact items included: short chromosomes at
+    ratio 0.85) and with register rounds at ratio 1: both directions and one, ties for both
+    directions or not; chromosomes of 2 to 64 columns (one to several staged batches of pairs);
+    4,500 rows (the last pass of 128 words only partly filled, pad rows in the last word)."""
+    R, C = 4500, 650
+    bitmap_bytes = C * C * ((R + 127) // 128 * 128 // 32) * 4
+    l2 = getattr(torch_cuda.cuda.get_device_properties(0), "L2_cache_size", 0)
+    assert l2 == 0 or bitmap_bytes > l2
+    g = np.random.default_rng(77)
+    x = tie_matrix(g, R, C)
+    lens = np.concatenate([[2, 3, 13, 14, 25, 26, 64], g.integers(2, 65, size=33)])
+    ci, off = ragged_population(g, len(lens), C, lens)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        for neg, ns in ((1, 0), (1, 1), (0, 0), (0, 1)):
+            for num, den in ((85, 100), (1, 1), (1, 2)):
+                want = oracle_eval(x, ci, off, neg, num, den, ns=ns)
+                p = ebic.Params.make(neg_trends=neg, ratio_num=num, ratio_den=den, mode=2,
+                                     non_strict=ns)
+                assert_parity(ctx.eval_population(ci, off, p), want)
