@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_eval_codes(EvalArgs a, PopView 
   // Items are taken segment-major (all individuals of a row segment before the next segment),
   // so the codes of the segment stay in L2 while every individual reads them.  (Fetching the
   // next item's index ahead of the current item's work measured slower.)
-  for (int q = items::first(); q < n_all; q = items::next(a.work, lane)) {
+  for (int q = items::first(); q < n_all; q = items::next(a.work, lane, q, n_all)) {
     if (q >= n_items) {
       if (items::stopped(pv)) return;  // a stopped run changes nothing
       items::move_chunk(a, q - n_items, lane);

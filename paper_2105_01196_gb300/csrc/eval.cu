@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_eval_direct(EvalArgs a, PopView
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t passes_total = a.R_pad / 128;
   const int32_t n_items = pv.n * a.n_seg, n_all = n_items + items::move_chunks(a);
-  for (int q = items::first(); q < n_all; q = items::next(a.work, lane)) {
+  for (int q = items::first(); q < n_all; q = items::next(a.work, lane, q, n_all)) {
     if (q >= n_items) {
       if (items::stopped(pv)) return;  // a stopped run changes nothing
       items::move_chunk(a, q - n_items, lane);
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
   const int32_t n_items = pv.n * a.n_seg, n_all = n_items + items::move_chunks(a);
   const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
   const uint4 ones = make_uint4(kFull, kFull, kFull, kFull);
-  for (int q = items::first(); q < n_all; q = items::next(a.work, lane)) {
+  for (int q = items::first(); q < n_all; q = items::next(a.work, lane, q, n_all)) {
     if (q >= n_items) {
       if (items::stopped(pv)) return;  // a stopped run changes nothing
       items::move_chunk(a, q - n_items, lane);

@@ -1175,12 +1175,6 @@ __global__ void k_tabu_load(const uint64_t *list, int64_t n, uint64_t *keys, uin
   if (i < n) tabu_insert(keys, mask, list[i]);
 }
 
-uint32_t next_pow2(uint64_t v) {
-  uint64_t p = 1;
-  while (p < v) p <<= 1;
-  return (uint32_t)p;
-}
-
 }  // namespace
 
 // ------------------------------------------------------------------------------ host state
@@ -1522,12 +1516,12 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
   }
   GEN_ALLOC(g->rows_scr, P * 3 * 4);
   GEN_ALLOC(g->work, 64);
-  g->dcap = next_pow2(2 * P);
+  g->dcap = (uint32_t)dedup_capacity(P);
   for (int k = 0; k < 2; ++k) {
     GEN_ALLOC(g->dkeys[k], (size_t)g->dcap * 8);
     GEN_ALLOC(g->dslot[k], (size_t)g->dcap * 4);
   }
-  g->ccap = next_pow2(P);
+  g->ccap = (uint32_t)pow2_at_least(P);
   GEN_ALLOC(g->cand_f, (size_t)g->ccap * 8);
   GEN_ALLOC(g->cand_h, (size_t)g->ccap * 8);
   GEN_ALLOC(g->cand_s, (size_t)g->ccap * 4);
@@ -1535,7 +1529,7 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
   GEN_ALLOC(g->ctl, sizeof(GenCtl));
   GEN_ALLOC(g->usage, (size_t)ctx->C * 4);
   const int cw = (ctx->C + 31) / 32;
-  g->sort_cap = (int32_t)std::min<uint32_t>(kSortSmemMax, next_pow2(P));
+  g->sort_cap = (int32_t)std::min<uint64_t>(kSortSmemMax, pow2_at_least(P));
   g->top_smem = (size_t)(g->K + 1) * sizeof(TopEntry) + (size_t)g->sort_cap * 16 +
                 (size_t)cw * 4 + (size_t)g->sort_cap * 4 + (size_t)(g->K + 1) * 12 +
                 (size_t)kChunk * (kS + 4) * 4 + (size_t)(g->K + 1) + 16;
@@ -1551,10 +1545,10 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
   EBIC_CHECK_CUDA(ctx, cudaFuncSetAttribute(k_evolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)evolve_smem(kMaxAttemptWarps, kUsageSmemMax)));
 
-  // enough blocks to spread the slot and table loops, few enough to be co-resident quickly
-  const int64_t work = std::max<int64_t>(g->P, g->dcap);
+  // one block per 2,048 slots: the slot loop spread, few blocks to meet at the end (measured:
+  // one block for P = 800, 8.4 against 10.2 us with two; two for P = 4,096, 13.6 against 15.2 us)
   g->finish_blocks = (int)std::max<int64_t>(
-      1, std::min<int64_t>((work + 4 * kTopThreads - 1) / (4 * kTopThreads), ctx->num_sms));
+      1, std::min<int64_t>((g->P + 2 * kTopThreads - 1) / (2 * kTopThreads), ctx->num_sms));
   EBIC_CHECK_CUDA(ctx, cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
   for (cudaEvent_t &e : g->cap_ev) EBIC_CHECK_CUDA(ctx, cudaEventCreate(&e));
   return gen_reset(ctx, g);
@@ -1567,10 +1561,11 @@ int read_ctl(ebic_ctx *ctx, GenState *g, GenCtl *out) {
   return EBIC_OK;
 }
 
-// Grows the tabu table to hold `need` keys at load factor <= 1/2 (rehashing live keys).
+// Grows the tabu table to hold `need` keys at load factor <= 1 / kTableSpread (rehashing live
+// keys).
 int ensure_tabu(ebic_ctx *ctx, GenState *g, int64_t need) {
-  const uint64_t want = next_pow2((uint64_t)std::max<int64_t>(2 * need, 1024));
-  if (want > (1ull << 31)) return ebic_fail(ctx, EBIC_ENOMEM, "tabu list beyond 2^31 keys");
+  const uint64_t want = tabu_capacity(need);
+  if (want > (1ull << 31)) return ebic_fail(ctx, EBIC_ENOMEM, "tabu list beyond 2^31 slots");
   if (g->tcap >= want) return EBIC_OK;
   DevBuf fresh;
   EBIC_CHECK_CUDA(ctx, fresh.ensure(want * 8));

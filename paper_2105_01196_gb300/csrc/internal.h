@@ -249,6 +249,20 @@ cudaError_t prepare_bitmap_eval();
 int choose_mode(const ebic_ctx *ctx, int requested, int64_t n_ind, double mean_len,
                 int expected_sweeps, int last_kept);
 
+// Capacities of the generation loop's hash tables (tables.cuh): powers of two at load factor
+// <= 1 / kTableSpread.  The tabu list is sized for `keys` keys, the duplicate table for P.
+constexpr int64_t kTableSpread = 8;
+inline uint64_t pow2_at_least(uint64_t v) {
+  uint64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+inline uint64_t tabu_capacity(int64_t keys) {
+  const int64_t want = kTableSpread * keys;
+  return pow2_at_least((uint64_t)(want > 1024 ? want : 1024));
+}
+inline uint64_t dedup_capacity(int64_t P) { return pow2_at_least((uint64_t)(kTableSpread * P)); }
+
 // evolve.cu
 void gen_state_free(struct GenState *g);
 // Ends the current run: the state is cleared before the next run, buffers and graphs stay.

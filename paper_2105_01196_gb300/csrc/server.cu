@@ -29,12 +29,6 @@ using Clock = std::chrono::steady_clock;
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
-uint64_t next_pow2(uint64_t v) {
-  uint64_t p = 1;
-  while (p < v) p <<= 1;
-  return p;
-}
-
 // The evaluation form a job will use: the cost model of ebic_eval_population's AUTO mode.
 int job_mode(int64_t rows, int32_t cols, const ebic_params &p, int32_t n_gen) {
   if (p.mode != EBIC_MODE_AUTO) return p.mode;
@@ -168,9 +162,9 @@ int64_t ebic_job_footprint(int64_t rows, int32_t cols, const ebic_params *p, int
     bytes += ebic_bitmap_bytes(rows, cols);               // pair bitmap
   bytes += 2 * P * (EBIC_MAX_LEN * 4 + 4 + 4 + 12 + 1 + 1 + 8 + 8);  // population buffers
   bytes += P * 12 + 64;                                   // evaluation scratch
-  bytes += (int64_t)next_pow2((uint64_t)std::max<int64_t>(2 * P * ((int64_t)n_gen + 2), 1024)) * 8;
-  bytes += 2 * (int64_t)next_pow2((uint64_t)(2 * P)) * 12;  // duplicate tables
-  bytes += (int64_t)next_pow2((uint64_t)P) * 20;           // top-list candidates
+  bytes += (int64_t)tabu_capacity(P * ((int64_t)n_gen + 2)) * 8;  // tabu list
+  bytes += 2 * (int64_t)dedup_capacity(P) * 12;                   // duplicate tables
+  bytes += (int64_t)pow2_at_least((uint64_t)P) * 20;              // top-list candidates
   bytes += (int64_t)p->n_biclusters * 288 + (int64_t)cols * 4 + 4096;
   return bytes + bytes / 16;                               // allocator slack
 }

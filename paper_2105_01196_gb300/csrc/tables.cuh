@@ -1,7 +1,10 @@
 // Device hash tables of the generation loop: the tabu list (set of chromosome keys) and the
 // per-generation duplicate table (key -> lowest slot).  Open addressing with linear probing over a
-// power-of-two capacity that is kept at least twice the number of keys, so every probe sequence
-// meets an empty slot; loops are still bounded by the capacity.  Key 0 marks an empty slot (the
+// power-of-two capacity that is kept at least eight times the number of keys, so every probe
+// sequence meets an empty slot; loops are still bounded by the capacity.  Each probe step is a
+// dependent round trip to L2 (an atomic for insertions), and the slowest of a launch's probes
+// sets the launch's length: at load factor 1/2 the longest runs of linear probing cost several
+// microseconds per generation, at 1/8 they are short.  Key 0 marks an empty slot (the
 // chromosome key never is 0: a zero FNV-1a hash is replaced by a fixed constant).
 #pragma once
 
