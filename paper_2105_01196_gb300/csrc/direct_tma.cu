@@ -15,6 +15,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "items.cuh"
 #include "tables.cuh"
 #include "tma.cuh"
 
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (pv.stop && *pv.stop) return;
   // the generation loop's side tasks: the previous generation's keys join the tabu list, and
   // this generation's live keys enter its duplicate table (tested after the launch)
-  if (a.mv_keys) move_table_keys(a.mv_keys, a.mv_slots, a.mv_n, a.mv_table, a.mv_tmask, a.mv_count);
+  items::move_all(a);
   if (pv.dkeys)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < pv.n; i += gridDim.x * blockDim.x)
       if (!(pv.dead && pv.dead[i])) dedup_insert(pv.dkeys, pv.dslot, pv.dmask, pv.hash[i], i);

@@ -81,14 +81,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_eval_direct(EvalArgs a, PopView
   wait_prior_grid();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t passes_total = a.R_pad / 128;
-  const int32_t n_items = pv.n * a.n_seg, n_all = n_items + items::move_chunks(a);
+  const int32_t n_side = items::move_chunks(a), n_all = n_side + pv.n * a.n_seg;
   for (int q = items::first(); q < n_all; q = items::next(a.work, lane, q, n_all)) {
-    if (q >= n_items) {
+    if (q < n_side) {
       if (items::stopped(pv)) return;  // a stopped run changes nothing
-      items::move_chunk(a, q - n_items, lane);
+      items::move_chunk(a, q, lane);
       continue;
     }
-    const int seg = q / pv.n, i = q - seg * pv.n;  // segment-major
+    const int seg = (q - n_side) / pv.n, i = (q - n_side) - seg * pv.n;  // segment-major
     const items::Meta m = items::load_meta(pv, i, lane);
     if (items::stopped(pv)) return;  // (read with the item's loads; before any store)
     if (m.dead || m.L < 2) continue;
@@ -292,16 +292,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
   uint32_t *sn = sp + NB * kPassWords;                                    // negative direction
   const int64_t Wst = a.Wst;
   const int64_t passes_total = (Wst + kPassWords - 1) / kPassWords;
-  const int32_t n_items = pv.n * a.n_seg, n_all = n_items + items::move_chunks(a);
+  const int32_t n_side = items::move_chunks(a), n_all = n_side + pv.n * a.n_seg;
   const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
   const uint4 ones = make_uint4(kFull, kFull, kFull, kFull);
   for (int q = items::first(); q < n_all; q = items::next(a.work, lane, q, n_all)) {
-    if (q >= n_items) {
+    if (q < n_side) {
       if (items::stopped(pv)) return;  // a stopped run changes nothing
-      items::move_chunk(a, q - n_items, lane);
+      items::move_chunk(a, q, lane);
       continue;
     }
-    const int seg = q / pv.n, i = q - seg * pv.n;  // segment-major
+    const int seg = (q - n_side) / pv.n, i = (q - n_side) - seg * pv.n;  // segment-major
     const items::Meta m = items::load_meta(pv, i, lane);
     if (items::stopped(pv)) return;  // (read with the item's loads; before any store)
     if (m.dead || m.L < 2) continue;
@@ -594,7 +594,8 @@ cudaError_t launch_eval_kernel(int mode, const EvalArgs &a0, const PopView &pv, 
   }
   a.seg_passes = (int32_t)seg;
   a.n_seg = (int32_t)n_seg;
-  const int64_t items = (int64_t)pv.n * n_seg;
+  // (the side task's chunks count too: with a warp for every item they run beside the others)
+  const int64_t items = (int64_t)pv.n * n_seg + (a.mv_table ? (a.mv_n + 31) / 32 : 0);
   int64_t grid = (int64_t)num_sms * bps;
   const int64_t need = (items + kWarps - 1) / kWarps;
   if (grid > need) grid = need;

@@ -1300,15 +1300,22 @@ GenArgs gen_args(ebic_ctx *ctx, GenState *g) {
   return ga;
 }
 
-EvalArgs gen_eval_args(ebic_ctx *ctx, GenState *g, int k) {
+EvalArgs gen_eval_args(ebic_ctx *ctx, GenState *g, int k, bool has_prev) {
   EvalArgs a = eval_args_for(ctx);
-  // generation g-1's live keys (duplicate table k ^ 1) join the hashed tabu list meanwhile
-  a.mv_keys = g->dkeys[k ^ 1].as<uint64_t>();
-  a.mv_slots = g->dslot[k ^ 1].as<uint32_t>();
-  a.mv_n = g->dcap;
-  a.mv_table = g->tabu.as<uint64_t>();
-  a.mv_tmask = g->tcap - 1;
-  a.mv_count = reinterpret_cast<unsigned long long *>(&g->ctl.as<GenCtl>()->tabu_count);
+  // generation g-1's live keys (population buffer k ^ 1) join the hashed tabu list meanwhile,
+  // and its duplicate table is cleared (there is none before the initial population)
+  if (has_prev) {
+    a.mv_hash = g->hash[k ^ 1].as<uint64_t>();
+    a.mv_dead = g->att_dead[k ^ 1].as<uint8_t>();
+    a.mv_len = g->len[k ^ 1].as<int32_t>();
+    a.mv_n = (uint32_t)g->P;
+    a.mv_table = g->tabu.as<uint64_t>();
+    a.mv_tmask = g->tcap - 1;
+    a.mv_count = reinterpret_cast<unsigned long long *>(&g->ctl.as<GenCtl>()->tabu_count);
+    a.clr_keys = g->dkeys[k ^ 1].as<uint64_t>();
+    a.clr_slots = g->dslot[k ^ 1].as<uint32_t>();
+    a.clr_n = g->dcap;
+  }
   a.neg = g->p.neg_trends;
   a.non_strict = g->p.non_strict;
   a.last_kept = g->p.last_kept;
@@ -1397,11 +1404,13 @@ cudaError_t find_mark_nodes(cudaGraph_t graph, const cudaEvent_t ev[4], cudaGrap
   return cudaSuccess;
 }
 
-// Scoring kernels shared by initialisation and every generation (buffer k was just built).
-cudaError_t launch_scoring(ebic_ctx *ctx, GenState *g, int k, cudaStream_t s, Marks *m) {
+// Scoring kernels shared by initialisation and every generation (buffer k was just built;
+// has_prev: a previous generation sits in buffer k ^ 1).
+cudaError_t launch_scoring(ebic_ctx *ctx, GenState *g, int k, bool has_prev, cudaStream_t s,
+                           Marks *m) {
   cudaError_t e;
   if ((e = mark(s, m, 1)) != cudaSuccess) return e;
-  if ((e = launch_eval_kernel(g->eval_mode, gen_eval_args(ctx, g, k), gen_view(g, k),
+  if ((e = launch_eval_kernel(g->eval_mode, gen_eval_args(ctx, g, k, has_prev), gen_view(g, k),
                               ctx->num_sms, s, true)) != cudaSuccess)
     return e;
   if ((e = mark(s, m, 2)) != cudaSuccess) return e;
@@ -1420,7 +1429,7 @@ cudaError_t launch_generation(ebic_ctx *ctx, GenState *g, int parity, cudaStream
                       gen_args(ctx, g), g->buf(parity ^ 1), g->buf(parity), parity)) !=
       cudaSuccess)
     return e;
-  return launch_scoring(ctx, g, parity, s, m);
+  return launch_scoring(ctx, g, parity, true, s, m);
 }
 
 // Queues the event pairs of one profiled generation (evolve, evaluation, finish).
@@ -1701,7 +1710,7 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
     k_init<<<(unsigned)((g->P + kInitWarps - 1) / kInitWarps), kInitWarps * 32, 0, s>>>(
         gen_args(ctx, g), g->buf(0));
     EBIC_CHECK_CUDA(ctx, cudaGetLastError());
-    EBIC_CHECK_CUDA(ctx, launch_scoring(ctx, g, 0, s, timed ? &m : nullptr));
+    EBIC_CHECK_CUDA(ctx, launch_scoring(ctx, g, 0, false, s, timed ? &m : nullptr));
     if (timed) push_generation_timing(ctx, m, false);
     prof_count(ctx, EBIC_KERNEL_EVAL, 1);
     prof_count(ctx, EBIC_KERNEL_FINISH, 1);

@@ -79,16 +79,21 @@ struct EvalArgs {
   int32_t *work;            // dynamic work counter (zeroed first)
   int32_t seg_passes;       // passes (of 128 words or 128 rows) per work item
   int32_t n_seg;            // segments per individual
-  // Optional side task of the generation loop, done by the launch's warps after the evaluation
-  // items (the staged kernel: before them): the keys of table mv_keys (mv_n slots, cleared
-  // afterwards, slot words mv_slots) join the hashed tabu list mv_table; new keys are counted
-  // in *mv_count.
-  uint64_t *mv_keys;
-  uint32_t *mv_slots;
+  // Optional side task of the generation loop, done by the launch's warps beside the evaluation
+  // items (the staged kernel: before them): the previous generation's live keys (mv_hash[s] of
+  // its slots s < mv_n with !mv_dead[s] and mv_len[s] >= 2) join the hashed tabu list
+  // mv_table, new keys counted in *mv_count; and that generation's duplicate table (clr_n
+  // slots of clr_keys / clr_slots) is cleared for the next generation.  mv_n = 0: none.
+  const uint64_t *mv_hash;
+  const uint8_t *mv_dead;
+  const int32_t *mv_len;
   uint32_t mv_n;
   uint64_t *mv_table;
   uint32_t mv_tmask;
   unsigned long long *mv_count;
+  uint64_t *clr_keys;
+  uint32_t *clr_slots;
+  uint32_t clr_n;
   int32_t *err;                   // kernels OR error bits in (4: a bounded wait expired)
   const struct DirectTma *dtma;   // host-side: staged direct form, when prepared
   const uint8_t *codes;           // [C][S] per-row rank codes (codes.cu), or nullptr

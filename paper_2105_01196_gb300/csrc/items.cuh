@@ -1,10 +1,11 @@
 // Work items of the persistent evaluation kernels (eval.cu, codes.cu).
 //
 // Warps take items in one sequence (statically for small launches, else from one atomic counter):
-// first the (individual, row segment) evaluation items, segment-major, then - in the generation
-// loop - the chunks of its side task, the move of the previous generation's duplicate table into
-// the tabu list.  Taking the side task last lets it
-// run in the shadow of the warps still evaluating instead of delaying every warp's first item.
+// first - in the generation loop - the P / 32 chunks of its side task (the previous generation's
+// keys join the tabu list, its duplicate table is cleared), then the (individual, row segment)
+// evaluation items, segment-major.  The launch has a warp for every item when it can, so the
+// chunks run beside the evaluations; when warps take several items, the chunks taken first keep
+// them out of the launch's tail.
 //
 // The per-item bookkeeping is arranged so that its loads leave in as few dependent round trips as
 // possible: length, start, dead flag, hash and (for the generation loop's fixed-stride rows) the
@@ -19,25 +20,45 @@ namespace items {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// Number of side-task chunks (32 table slots each).
+// Number of side-task chunks (32 slots of the previous generation each).
 __device__ __forceinline__ int move_chunks(const EvalArgs &a) {
-  return a.mv_keys ? (int)((a.mv_n + 31u) / 32u) : 0;
+  return a.mv_table ? (int)((a.mv_n + 31u) / 32u) : 0;
 }
 
-// One side-task chunk: slot 32 m + lane of table mv_keys joins the tabu list and is cleared.
+// Slot s of the previous generation: its key joins the tabu list when the slot was live.
+__device__ __forceinline__ unsigned move_slot(const EvalArgs &a, uint32_t s) {
+  const uint8_t d = a.mv_dead[s];
+  const int32_t L = a.mv_len[s];
+  const uint64_t h = a.mv_hash[s];
+  return (!d && L >= 2 && tabu_insert(a.mv_table, a.mv_tmask, h)) ? 1u : 0u;
+}
+
+// One side-task chunk: slot 32 m + lane of the previous generation joins the tabu list, and the
+// chunk clears its share of that generation's duplicate table (plain stores).
 __device__ __forceinline__ void move_chunk(const EvalArgs &a, int m, int lane) {
-  const uint32_t idx = (uint32_t)m * 32u + (uint32_t)lane;
-  unsigned added = 0u;
-  if (idx < a.mv_n) {
-    const uint64_t k = a.mv_keys[idx];
-    if (k) {
-      added = tabu_insert(a.mv_table, a.mv_tmask, k) ? 1u : 0u;
-      a.mv_keys[idx] = 0ull;
-      a.mv_slots[idx] = 0u;
-    }
+  const uint32_t s = (uint32_t)m * 32u + (uint32_t)lane;
+  unsigned added = s < a.mv_n ? move_slot(a, s) : 0u;
+  const uint32_t n_ch = (a.mv_n + 31u) / 32u, per = (a.clr_n + n_ch - 1u) / n_ch;
+  const uint32_t j1 = min(a.clr_n, ((uint32_t)m + 1u) * per);
+  for (uint32_t j = (uint32_t)m * per + (uint32_t)lane; j < j1; j += 32u) {
+    a.clr_keys[j] = 0ull;
+    a.clr_slots[j] = 0u;
   }
   added = __reduce_add_sync(kFull, added);
   if (lane == 0 && added) atomicAdd(a.mv_count, (unsigned long long)added);
+}
+
+// The whole side task, spread over every thread of the calling grid (the staged kernel).
+static __device__ __noinline__ void move_all(const EvalArgs &a) {
+  if (!a.mv_table) return;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  unsigned long long added = 0ull;
+  for (uint32_t s = tid; s < a.mv_n; s += stride) added += move_slot(a, s);
+  for (uint32_t j = tid; j < a.clr_n; j += stride) {
+    a.clr_keys[j] = 0ull;
+    a.clr_slots[j] = 0u;
+  }
+  if (added) atomicAdd(a.mv_count, added);
 }
 
 // A warp's first item is its index w in the launch (no round trip to the counter).  With at

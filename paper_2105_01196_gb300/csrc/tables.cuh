@@ -68,21 +68,3 @@ __device__ __forceinline__ bool dedup_is_dup(const uint64_t *keys, const uint32_
   }
   return false;
 }
-
-// Moves every key of a duplicate table (n slots) into the tabu list and clears the table; new
-// keys are counted in *count.  Spread over all threads of the calling grid.
-static __device__ __noinline__ void move_table_keys(uint64_t *keys, uint32_t *slots, uint32_t n,
-                                             uint64_t *table, uint32_t tmask,
-                                             unsigned long long *count) {
-  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  unsigned long long added = 0ull;
-  for (uint32_t i = tid; i < n; i += stride) {
-    const uint64_t k = keys[i];
-    if (k) {
-      added += tabu_insert(table, tmask, k) ? 1ull : 0ull;
-      keys[i] = 0ull;
-      slots[i] = 0u;
-    }
-  }
-  if (added) atomicAdd(count, added);
-}
