@@ -54,20 +54,31 @@ __device__ __forceinline__ uint4 ldg4(const uint32_t *p) {
 
 // ------------------------------------------------------------------------------- validation
 
+// One warp per individual: lane k holds columns k and k + 32 (sentinels that no column and no
+// other lane's sentinel equals past the length); a column out of range, a repeated column, a
+// start below 0 or a length outside [2, 64] sets bit 2 of *err.
 __global__ void k_validate_csr(const int32_t *__restrict__ cols, const int32_t *__restrict__ off,
                                int32_t n, int32_t C, int32_t *__restrict__ err) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n) return;  // (whole warps)
   const int s = off[i], e = off[i + 1];
   const int L = e - s;
-  bool bad = (s < 0) || L < 2 || L > EBIC_MAX_LEN;
-  for (int k = 0; k < L && !bad; ++k) {
-    const int c = cols[s + k];
-    if (c < 0 || c >= C) bad = true;
-    for (int j = 0; j < k && !bad; ++j)
-      if (cols[s + j] == c) bad = true;
+  bool bad = (s < 0) || L < 2 || L > EBIC_MAX_LEN;  // (warp-uniform)
+  if (!bad) {
+    const bool in0 = lane < L, in1 = lane + 32 < L;
+    const int c0 = in0 ? cols[s + lane] : -1 - lane;
+    const int c1 = in1 ? cols[s + 32 + lane] : -33 - lane;
+    // (every lane takes part in each collective: none sits in a short-circuited operand)
+    const unsigned m0 = __match_any_sync(kFull, c0), m1 = __match_any_sync(kFull, c1);
+    bad = (in0 && (c0 < 0 || c0 >= C)) || (in1 && (c1 < 0 || c1 >= C));
+    bad = bad || __popc(m0) > 1 || __popc(m1) > 1;
+    for (int j = 0; j < 32; ++j) {
+      const int b = __shfl_sync(kFull, c0, j);
+      bad = bad || c1 == b;
+    }
   }
-  if (bad) atomicOr(err, 2);
+  if (__any_sync(kFull, bad) && lane == 0) atomicOr(err, 2);
 }
 
 // ------------------------------------------------------------------------------- direct form
@@ -486,7 +497,7 @@ int blocks_per_sm_for(const void *kernel, size_t smem) {
 cudaError_t launch_validate_csr(const int32_t *cols, const int32_t *off, int32_t n, int32_t C,
                                 int32_t *err, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_validate_csr<<<(n + 255) / 256, 256, 0, s>>>(cols, off, n, C, err);
+  k_validate_csr<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(cols, off, n, C, err);
   return cudaGetLastError();
 }
 

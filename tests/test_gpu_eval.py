@@ -293,3 +293,30 @@ def test_bitmap_larger_than_l2_all_variants(ebic, torch_cuda):
                 p = ebic.Params.make(neg_trends=neg, ratio_num=num, ratio_den=den, mode=2,
                                      non_strict=ns)
                 assert_parity(ctx.eval_population(ci, off, p), want)
+
+
+def test_csr_validation_long_chromosomes(ebic):
+    """Repeated columns are rejected wherever they sit in a chromosome of up to 64 columns (both
+    within the first 32, both within the last 32, one in each), and one bad individual among
+    valid ones rejects the call; a valid 64-column individual passes."""
+    g = np.random.default_rng(8)
+    x = g.standard_normal((300, 100)).astype(np.float32)
+    good = [list(g.choice(100, size=L, replace=False)) for L in (64, 40, 33, 2)]
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        p = ebic.Params.make(neg_trends=1, ratio_num=1, ratio_den=2)
+
+        def csr(pop):
+            off = np.concatenate([[0], np.cumsum([len(c) for c in pop])]).astype(np.int32)
+            return np.concatenate(pop).astype(np.int32), off
+
+        ci, off = csr(good)
+        want = oracle_eval(x, ci, off, 1, 1, 2)
+        assert_parity(ctx.eval_population(ci, off, p), want)
+        for a, b in ((0, 31), (33, 50), (3, 35), (31, 32), (0, 63)):
+            bad = list(good[0])
+            bad[b] = bad[a]
+            ci, off = csr(good[1:] + [bad])
+            with pytest.raises(ebic.EbicError) as e:
+                ctx.eval_population(ci, off, p)
+            assert e.value.code == ebic.EBIC_EINVAL
