@@ -484,6 +484,11 @@ def main():
                 "avg_launch_us": avg_s * 1e6, "launches": n_l,
                 "share_of_kernel_time": se["share_of_kernel_time"],
                 "dominant_kernel": kernel_names[dominant]}
+        if dominant != "eval":
+            roof["note"] = (f"{kernel_names[dominant]} has the largest share of kernel time; it "
+                            "moves no bulk data (a chain of dependent round trips per child or "
+                            "slot), so the roofline is the evaluation kernel's, the path's only "
+                            "bandwidth-bound kernel")
     line = {"metric": METRIC, "value": units / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup),
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
