@@ -9,8 +9,8 @@
 //               mutation, tabu probe; the lowest attempt that misses the tabu list wins (step 5);
 //   k_eval_*    the persistent evaluation kernel (eval.cu, codes.cu) over the new population,
 //               skipping tabu-dead slots (step 7); it also enters the live keys into this
-//               generation's duplicate table and moves the previous generation's table into the
-//               hashed tabu list;
+//               generation's duplicate table, inserts the previous generation's live keys into
+//               the hashed tabu list and clears that generation's duplicate table;
 //   k_finish    all blocks: final dead flags (tabu or duplicate), tabu hits, fitness, candidates
 //               for the top list; then the last block to finish: tabu-hit stop test (step 6),
 //               top rank list update (step 7), column usage, counters for the next generation.
@@ -937,8 +937,7 @@ __device__ __forceinline__ SlotIn load_slot(const GenArgs &ga, const Buf &nb, in
 }
 
 // Scoring, tabu bookkeeping and the top-list update of generation g (parity par).  Every block
-// scores a share of the slots and moves a share of generation g-1's duplicate table into the tabu
-// list (clearing it for generation g+1); the last block to finish then runs the single-block part.
+// scores a share of the slots; the last block to finish then runs the single-block part.
 __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, int par) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_hits, s_live, s_lsum, s_last, s_n, s_cnt, s_stop, s_nc;
