@@ -132,6 +132,7 @@ extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_
       build_ms = ms;
     }
     a.bitmap = ctx->bitmap.as<uint32_t>();
+    a.stage_bitmap = eval_args_for(ctx).stage_bitmap;  // (the form later runs will use)
     for (int seg : kSegCandidates) {
       if (seg > passes_bitmap) break;
       double ms = 0;
