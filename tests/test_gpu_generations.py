@@ -146,6 +146,35 @@ def test_default_workload_generations(ebic):
         assert_same_state(ctx, st, gp)
 
 
+@pytest.mark.parametrize("ns", [0, 1])
+def test_generations_over_a_bitmap_larger_than_l2(ebic, ns):
+    """The generation loop over a 243 MB pair bitmap (larger than the device's L2, so the bitmap
+    kernel stages its pair words in shared memory) on a tie-heavy matrix, with ties counting for
+    both directions or not: generation by generation, then eight generations in one graph
+    replay, against the oracle."""
+    g = np.random.default_rng(21 + ns)
+    x = g.integers(-3, 4, size=(4500, 650)).astype(np.float32)
+    gp, op = both_params(ebic, mode=2, non_strict=ns, max_len=20, init_max_len=20, pop_size=96,
+                         elite=6, n_biclusters=6, seed=23)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        ctx.run_generations(gp, 0)
+        st = oebic.initialise(x, op)
+        assert_same_state(ctx, st, gp)
+        for gen in range(1, 4):
+            rep = ctx.run_generations(gp, 1)
+            assert oebic.next_generation(x, st, op)
+            assert rep.gens_done == gen == st.gen
+            assert rep.n_evaluated == st.n_evaluated
+            assert_same_state(ctx, st, gp)
+        rep = ctx.run_generations(gp, 8)
+        for _ in range(8):
+            assert oebic.next_generation(x, st, op)
+        assert rep.gens_done == st.gen == 11
+        assert rep.n_evaluated == st.n_evaluated
+        assert_same_state(ctx, st, gp)
+
+
 def test_run_parameter_errors(ebic):
     x = tiny_matrix()
     with ebic.Context(0) as ctx:
