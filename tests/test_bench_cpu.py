@@ -1,0 +1,82 @@
+"""bench.py's host-side measurement helpers, on CPU: the committed ncu traffic summary it reads,
+the kernel a form runs, the peak it divides by, the single-thread oracle baseline, and the shape
+of the reference arm's JSON line."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import bench
+from paper_2105_01196_gb300 import synth
+
+
+def test_ncu_traffic_reads_the_committed_summary():
+    d = bench.ncu_traffic("k_eval_bitmap", "default")
+    b = bench.ncu_traffic("k_eval_bitmap", "batched")
+    assert d is not None and b is not None
+    # DRAM bytes per launch stay below the algorithmic bytes (part of the pair words hit L2)
+    # and above the bitmap's share that one sweep must at least bring in once
+    assert 1e6 < d < 5.39e6
+    assert 4e8 < b < 6.59e8
+    assert bench.ncu_traffic("k_eval_bitmap", "no-such-workload") is None
+    assert bench.ncu_traffic("no_such_kernel", "default") is None
+
+
+def test_eval_kernel_names():
+    assert bench.eval_kernel_name(2, 100) == "k_eval_bitmap"
+    assert bench.eval_kernel_name(1, 1024) == "k_eval_codes"
+    assert bench.eval_kernel_name(1, 1025) == "k_eval_direct"
+    assert bench.eval_kernel_name(4, 100) == "k_eval_direct_tma"
+    assert bench.eval_kernel_name(3, 100) == "k_eval_plain"
+
+
+def test_peak_is_the_measured_copy_bandwidth():
+    peak, kind = bench.load_peaks()
+    path = os.path.join(bench.ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            assert (peak, kind) == (json.load(fh)["hbm_gbs"], "measured")
+    else:
+        assert kind == "fallback"
+    assert peak > 0
+
+
+def test_cpu_baseline_counts_oracle_evaluations():
+    w = synth.WORKLOADS["tiny"]
+    x, _, ci, off = synth.workload_inputs(w)
+    r = bench.cpu_baseline(w, x, ci, off, 0.2)
+    assert r["kind"] == "oracle" and r["cores"] == 1 and r["unit"] == bench.UNIT
+    done = int(r["sample"].split("oracle trend counts of ")[1].split()[0])
+    assert done >= 1 and r["value"] > 0
+    assert f"x {x.shape[0]} rows" in r["sample"]
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    calls = []
+
+    def fake_baseline(w, x, ci, off, seconds, trend="strict"):
+        calls.append(seconds)
+        return {"value": float(len(calls)), "unit": bench.UNIT, "cores": 1, "kind": "oracle",
+                "sample": "stub"}
+
+    monkeypatch.setattr(bench, "cpu_baseline", fake_baseline)
+
+    class Args:
+        steps, warmup, gpus, gens, mode, trend = 3, 3, 1, None, "auto", "strict"
+
+    bench.run_reference(Args, synth.WORKLOADS["tiny"], 1, 0, None)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == bench.UNIT
+    assert line["metric"] == bench.METRIC and line["higher_is_better"] is True
+    # the median of the timed steps (values 4, 5, 6 after three warm-up calls)
+    assert line["value"] == pytest.approx(5.0)
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == 5.0
+    assert line["e2e"] == {"value": 5.0, "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert len(calls) == 6 and calls[0] == pytest.approx(calls[-1] / 4)
+    # a rank other than 0 prints nothing
+    bench.run_reference(Args, synth.WORKLOADS["tiny"], 2, 1, None)
+    assert capsys.readouterr().out == ""
+    assert np.isfinite(line["ms_per_step"])
