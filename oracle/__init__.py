@@ -25,5 +25,7 @@ Modules
 Parity status: the counts, the threshold, Philox and FNV-1a are pinned by the tests in
 ``tests/test_oracle_*.py`` (hand example, brute force, invariants, published test vectors).  The
 fitness formula, the top-list rule and the evolution operators follow readings the paper does not
-fix: they are "parity unpinned" by the paper and are pinned only by invariants.
+fix: they are "parity unpinned" by the paper.  They are pinned to the text of those readings by
+scripted-word and hand-worked cases (``tests/test_oracle_operators.py``,
+``tests/test_oracle_toplist.py``) and by invariants of whole runs (``tests/test_oracle_ebic.py``).
 """
