@@ -137,3 +137,25 @@ def test_no_crossover_at_the_threshold_word(monkeypatch):
     # the word 2^30 is not below 2^30: the child copies parent 1, then delete position 0
     words = [w(1, 2), 1 << 30, op(1), w(0, 3)]
     assert child_with(monkeypatch, st, words) == [5, 6]
+
+
+def init_with(monkeypatch, words, n_cols=10, **kw):
+    s = Script(words)
+    monkeypatch.setattr(ebic, "WordStream", lambda *a: s)
+    p = Params(**dict(dict(init_min_len=2, init_max_len=4, max_len=6, seed=1), **kw))
+    c = ebic.init_individual(p, n_cols, 0)
+    assert s.words == []
+    return c
+
+
+def test_initial_chromosome(monkeypatch):
+    # length 2 + below(3) = 4; column 5, then 5 again (present, redrawn) -> 1, then 9, then 0
+    words = [w(2, 3), w(5, 10), w(5, 10), w(1, 10), w(9, 10), w(0, 10)]
+    assert init_with(monkeypatch, words) == [5, 1, 9, 0]
+
+
+def test_initial_chromosome_ends_after_64_failed_draws(monkeypatch):
+    # length 2 + below(2) = 3 with init_max_len = 3; column 0, then 64 draws of column 0: the
+    # chromosome ends there (the third column is never drawn)
+    words = [w(1, 2), w(0, 3)] + [w(0, 3)] * 64
+    assert init_with(monkeypatch, words, n_cols=3, init_max_len=3) == [0]
