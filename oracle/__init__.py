@@ -27,5 +27,6 @@ Parity status: the counts, the threshold, Philox and FNV-1a are pinned by the te
 fitness formula, the top-list rule and the evolution operators follow readings the paper does not
 fix: they are "parity unpinned" by the paper.  They are pinned to the text of those readings by
 scripted-word and hand-worked cases (``tests/test_oracle_operators.py``,
-``tests/test_oracle_toplist.py``) and by invariants of whole runs (``tests/test_oracle_ebic.py``).
+``tests/test_oracle_toplist.py``, ``tests/test_oracle_tabu.py``) and by invariants of whole runs
+(``tests/test_oracle_ebic.py``).
 """
