@@ -50,11 +50,14 @@ extern "C" {
 
 /* ----------------------------------------------------------------------------- enumerations */
 #define EBIC_MODE_AUTO 0   /* the autotuner chooses the evaluation kernel                      */
-#define EBIC_MODE_DIRECT 1 /* direct comparison of the matrix's order keys                     */
-#define EBIC_MODE_BITMAP 2 /* column-pair comparison bitmap (built on first use)               */
+#define EBIC_MODE_DIRECT 1 /* direct comparison: per-row rank codes up to 1,024 columns, the
+                              order keys above                                                 */
+#define EBIC_MODE_BITMAP 2 /* column-pair comparison bitmap (built on first use); not with
+                              last_kept (EBIC_EINVAL)                                          */
 #define EBIC_MODE_PLAIN 3  /* one kernel launch per individual (reference GPU form)            */
 #define EBIC_MODE_STAGED 4 /* direct comparison over TMA-staged row tiles in shared memory;
-                              the direct form is used where the tile does not fit (> 1536 columns) */
+                              the direct form is used where the tile does not fit (> 1536 columns)
+                              or a pair-test variant (non_strict, last_kept) is set            */
 
 #define EBIC_LAYOUT_ROW_MAJOR 0 /* x[r * cols + c] */
 #define EBIC_LAYOUT_COL_MAJOR 1 /* x[c * rows + r] */
@@ -183,8 +186,8 @@ EBIC_API int ebic_copy_bitmap(ebic_ctx *ctx, uint32_t *out, int64_t n_words);
  *   rows_neg[i]  rows with at least t(L) decreasing pairs (0 unless p->neg_trends),
  *   rows_any[i]  rows passing either direction (counted once),
  *   fitness[i]   0 if rows_any < p->min_rows, else rows_any * 2^min(L, p->col_cap).
- * Any of the four outputs may be NULL.  Only neg_trends, ratio_*, min_rows, col_cap and mode of
- * *p are read.  n_ind = 0 is valid and does nothing.
+ * Any of the four outputs may be NULL.  Only neg_trends, ratio_*, non_strict, last_kept,
+ * min_rows, col_cap and mode of *p are read.  n_ind = 0 is valid and does nothing.
  * Errors: EBIC_ESTATE (no matrix), EBIC_EINVAL (bad parameter or chromosome; nothing written),
  * EBIC_ENOMEM, EBIC_ECUDA.
  */
