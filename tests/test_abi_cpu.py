@@ -56,3 +56,20 @@ def test_struct_layout_matches_header(lib):
     assert ctypes.sizeof(lib.RunReport) == 4 * 4 + 8 + 8
     assert ctypes.sizeof(lib.TuneReport) == 4 * 4 + 4 * 8
     assert ctypes.sizeof(lib.JobResult) == 8 + 4 * 4 + 8 + 4 * 2 + 8 + 8 * 2
+
+
+def test_job_footprint_model(lib):
+    """The job server's device-memory model (pure host code): bad arguments, the pair bitmap
+    counted when the job's form is the bitmap, and the tabu list sized for every key a run can
+    insert at load factor 1/8."""
+    p = lib.Params.make(pop_size=800, mode=1)
+    assert lib.ebic_job_footprint(0, 10, p, 10) == -1
+    assert lib.ebic_job_footprint(100, 1, p, 10) == -1
+    assert lib.ebic_job_footprint(100, 10, p, -1) == -1
+    direct = lib.ebic_job_footprint(10_000, 100, p, 100)
+    bitmap = lib.ebic_job_footprint(10_000, 100, lib.Params.make(pop_size=800, mode=2), 100)
+    assert bitmap - direct >= lib.ebic_bitmap_bytes(10_000, 100)
+    short = lib.ebic_job_footprint(10_000, 100, p, 0)
+    long = lib.ebic_job_footprint(10_000, 100, p, 1000)
+    # 800 * 1,002 possible keys, 8 slots of 8 bytes each, against 800 * 2 for no generation
+    assert long - short >= 64 * 800 * 1000
