@@ -8,8 +8,10 @@ Recipe (stands in for the paper's Unibic / RecBic collections, Sec. 2.1, which a
   * background N(0, 1) float32 (or log-normal(0, 1) rounded to 0.1 for the tie-heavy workload);
   * each planted bicluster takes rows and columns without replacement; its column order is a
     random permutation; a planted row gets s ~ N(0, 1) at the first column of the order and adds
-    an increment ~ U(0.5, 1.5) at each next column, plus N(0, 0.1) noise per entry; a negative
-    bicluster stores the values along the reversed order; later biclusters overwrite earlier ones;
+    an increment ~ U(0.5, 1.5) at each next column, plus N(0, 0.1) noise per entry (on the
+    log-normal background the row is then shifted to start at exp(s), keeping its order); a
+    negative bicluster stores the values along the reversed order; later biclusters overwrite
+    earlier ones;
   * a population has lengths uniform in [len_lo, len_hi] and distinct columns drawn uniformly.
 Generators are numpy ``Generator(Philox(seed))``.
 """
@@ -115,7 +117,8 @@ def planted_matrix(rows, cols, n_bic, bic_rows, bic_cols, seed, background="norm
         vals = np.concatenate([start[:, None], start[:, None] + np.cumsum(steps, axis=1)], axis=1)
         vals = vals + g.normal(0.0, noise, size=(nr, nc))
         if background == "lognormal":
-            vals = np.abs(vals) + 0.0  # keep the planted values on the positive log-normal scale
+            # onto the positive log-normal scale by a per-row shift, which keeps each row's order
+            vals = vals - vals.min(axis=1, keepdims=True) + np.exp(start)[:, None]
         target = order if sign > 0 else order[::-1]
         x[np.ix_(ridx, target)] = vals.astype(np.float32)
         truth.append((ridx, np.asarray(order), sign))

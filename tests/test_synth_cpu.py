@@ -59,6 +59,18 @@ def test_planted_rows_follow_their_order():
     assert sum(1 for (_, _, s) in truth if s < 0) == 2   # neg_fraction 1/2
 
 
+def test_log_normal_planted_rows_stay_ordered_and_positive():
+    x, truth = synth.planted_matrix(400, 16, 3, (30, 40), (5, 8), seed=9, background="lognormal",
+                                    noise=0.0)
+    seen_rows = set()
+    for ridx, order, sign in reversed(truth):
+        target = order if sign > 0 else order[::-1]
+        clean = [k for k, r in enumerate(ridx) if r not in seen_rows]
+        vals = x[np.ix_(ridx[clean], target)]
+        assert (vals > 0).all() and (np.diff(vals, axis=1) > 0.49).all()
+        seen_rows.update(ridx.tolist())
+
+
 def test_tie_heavy_background_is_rounded():
     x, _ = synth.planted_matrix(300, 12, 1, (20, 20), (4, 4), seed=5, background="lognormal",
                                 round_to=0.1)
