@@ -377,16 +377,22 @@ EBIC_API int ebic_server_stats(ebic_server *srv, int32_t *queued, int32_t *runni
  *   x         rows * cols float32, COLUMN-major (x[c * rows + r]), device memory of `device`;
  *   col_idx, offsets  CSR population as in ebic_eval_population, device memory;
  *   outputs   device memory of `device`; any may be NULL;
- *   p         neg_trends, ratio_num/den, min_rows and col_cap are read (mode is ignored);
+ *   p         neg_trends, ratio_num/den, min_rows, col_cap, non_strict and last_kept are read
+ *             (mode and the generation-loop fields are ignored);
  *   cuda_stream  a cudaStream_t of `device` (NULL = the legacy default stream);
  *   msg       optional buffer of msg_len bytes for the message of a failure.
  * Scratch: the per-individual accumulators, a work counter and an error word live in one
  * file-scope static device array of 3 * EBIC_NOALLOC_MAX_IND + 2 int32 (768 KB), which every
- * GPU that loads the library holds until the process exits.  Its device address is looked up on
- * the first call for each device, so make that first call before any stream capture.  Every
- * call shares the array and clears the part it uses; calls whose work overlaps on the GPU (on
- * different streams or from different threads) race on it and must be serialised by the caller.
- * The call returns after the work has finished on `cuda_stream`.
+ * GPU that loads the library holds until the process exits.  CUDA loads modules lazily, so the
+ * first call on each device does a one-time set-up with that device current: it looks up the
+ * array's device address and loads this entry point's kernels, which places the array and their
+ * code in device memory.  Make that first call before any stream capture, and before a framework
+ * reserves the device's memory for its own pool (the set-up needs about 1 MB); later calls on
+ * that device load nothing.  Every call shares the array and clears the part it uses; calls
+ * whose work overlaps on the GPU (on different streams or from different threads) race on it
+ * and must be serialised by the caller.  The call reads the validation result back and
+ * synchronises `cuda_stream` before it launches the evaluation, and returns after the work has
+ * finished on `cuda_stream`.
  * Errors: EBIC_EINVAL (n_ind > EBIC_NOALLOC_MAX_IND, a host pointer, bad shape, parameter or
  * chromosome), EBIC_ENAN (NaN or Inf in x), EBIC_ECUDA.
  */

@@ -12,6 +12,11 @@
 // Host code cannot name that array's device address directly: in host code its name stands for
 // a host-side shadow.  The address is therefore fetched once per device with
 // cudaGetSymbolAddress (with that device current) and handed to the kernels.
+//
+// CUDA loads modules lazily by default, so this file's module (the array and the kernels' code)
+// is placed in device memory only when first used on a device.  The first call on each device
+// therefore does that set-up explicitly: it resolves the array's address and queries every
+// kernel's attributes, which loads all of them.  Later calls on that device load nothing.
 #include <stdio.h>
 #include <string.h>
 
@@ -37,24 +42,6 @@ static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 std::mutex g_setup_mu;
 NoAllocScratch *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on `device`, fetched on the first call for that device.
-cudaError_t scratch_for_device(int device, NoAllocScratch **out) {
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_addr[device]) {
-    int prev = -1;
-    cudaGetDevice(&prev);
-    cudaError_t e = cudaSetDevice(device);
-    if (e != cudaSuccess) return e;
-    void *ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (prev >= 0 && prev != device) cudaSetDevice(prev);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[device] = static_cast<NoAllocScratch *>(ptr);
-  }
-  *out = g_scratch_addr[device];
-  return cudaSuccess;
-}
 
 __device__ __forceinline__ int threshold(int L, int num, int den) {
   return (num * (L - 1) + den - 1) / den;
@@ -152,6 +139,38 @@ __global__ void k_na_finish(const int32_t *__restrict__ off, int32_t n, int32_t 
   }
 }
 
+using NaKernel = void (*)(const float *, int64_t, const int32_t *, const int32_t *, int32_t,
+                          int32_t, int32_t, int32_t, int32_t, NoAllocScratch *);
+// Indexed by neg_trends * 4 + non_strict * 2 + last_kept.
+const NaKernel kNaEval[8] = {k_na_eval<false, false, false>, k_na_eval<false, false, true>,
+                             k_na_eval<false, true, false>,  k_na_eval<false, true, true>,
+                             k_na_eval<true, false, false>,  k_na_eval<true, false, true>,
+                             k_na_eval<true, true, false>,   k_na_eval<true, true, true>};
+
+// Set-up for `device`, done once: with the device current, fetch the device address of the
+// scratch array and query every kernel of this file, so that the module (array and code) is in
+// device memory before the call returns.  Returns the cached address on later calls.
+cudaError_t scratch_for_device(int device, NoAllocScratch **out) {
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  if (!g_scratch_addr[device]) {
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return e;
+    void *ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_na_validate);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_na_finish);
+    for (int k = 0; k < 8 && e == cudaSuccess; ++k) e = cudaFuncGetAttributes(&fa, kNaEval[k]);
+    if (prev >= 0 && prev != device) cudaSetDevice(prev);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[device] = static_cast<NoAllocScratch *>(ptr);
+  }
+  *out = g_scratch_addr[device];
+  return cudaSuccess;
+}
+
 int fail(char *msg, int32_t msg_len, int code, const char *text) {
   if (msg && msg_len > 0) snprintf(msg, (size_t)msg_len, "%s", text);
   return code;
@@ -210,11 +229,18 @@ extern "C" int ebic_eval_population_noalloc(const float *x, int64_t rows, int32_
   cudaError_t e = scratch_for_device(device, &sc);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return fail(msg, msg_len, EBIC_ECUDA, "cudaGetSymbolAddress of the scratch array failed");
+    return fail(msg, msg_len, EBIC_ECUDA,
+                "set-up failed: the scratch array's address or the kernels could not be loaded");
   }
   int prev = -1;
-  cudaGetDevice(&prev);
-  if (prev != device) cudaSetDevice(device);
+  if (cudaGetDevice(&prev) != cudaSuccess) {
+    cudaGetLastError();
+    prev = -1;
+  }
+  if (prev != device && (e = cudaSetDevice(device)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(msg, msg_len, EBIC_ECUDA, "cudaSetDevice failed");
+  }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   int status = EBIC_OK;
   do {
@@ -254,15 +280,8 @@ extern "C" int ebic_eval_population_noalloc(const float *x, int64_t rows, int32_
     }
     int64_t grid = ((int64_t)n_ind * n_seg + kNaWarps - 1) / kNaWarps;
     if (grid > (int64_t)num_sms * 2) grid = (int64_t)num_sms * 2;
-    using NaKernel = void (*)(const float *, int64_t, const int32_t *, const int32_t *, int32_t,
-                              int32_t, int32_t, int32_t, int32_t, NoAllocScratch *);
-    static const NaKernel table[8] = {
-        k_na_eval<false, false, false>, k_na_eval<false, false, true>,
-        k_na_eval<false, true, false>,  k_na_eval<false, true, true>,
-        k_na_eval<true, false, false>,  k_na_eval<true, false, true>,
-        k_na_eval<true, true, false>,   k_na_eval<true, true, true>};
     const NaKernel kern =
-        table[(p->neg_trends ? 4 : 0) + (p->non_strict ? 2 : 0) + (p->last_kept ? 1 : 0)];
+        kNaEval[(p->neg_trends ? 4 : 0) + (p->non_strict ? 2 : 0) + (p->last_kept ? 1 : 0)];
     kern<<<(unsigned)grid, kNaThreads, 0, s>>>(x, rows, col_idx, offsets, n_ind, (int32_t)n_seg,
                                                (int32_t)seg, p->ratio_num, p->ratio_den, sc);
     if ((e = cudaGetLastError()) != cudaSuccess) break;

@@ -422,15 +422,50 @@ class Server:
 NOALLOC_MAX_IND = 65536
 
 
+def _noalloc_check(name, a, dtypes, device, min_numel=None, ndim=None):
+    """Checks one argument of the allocation-free call; never converts (a conversion would
+    allocate)."""
+    if not _is_torch(a):
+        raise EbicError(EBIC_EINVAL, f"{name} must be a CUDA tensor (caller-owned device memory)")
+    if a.device.type != "cuda" or (a.device.index or 0) != device:
+        raise EbicError(EBIC_EINVAL, f"{name} must be on cuda:{device}, not {a.device}")
+    if str(a.dtype) not in dtypes:
+        raise EbicError(EBIC_EINVAL, f"{name} must be {' or '.join(dtypes)}, not {a.dtype}")
+    if not a.is_contiguous():
+        raise EbicError(EBIC_EINVAL, f"{name} must be contiguous")
+    if ndim is not None and a.dim() != ndim:
+        raise EbicError(EBIC_EINVAL, f"{name} must be {ndim}-D, not {a.dim()}-D")
+    if min_numel is not None and a.numel() < min_numel:
+        raise EbicError(EBIC_EINVAL, f"{name} holds {a.numel()} entries, fewer than {min_numel}")
+
+
 def ebic_eval_population_noalloc(x_colmajor, col_idx, offsets, params, rows_pos=None,
                                  rows_neg=None, rows_any=None, fitness=None, device=0,
                                  stream=None):
     """Allocation-free evaluation for callers that cannot let the library allocate GPU memory.
 
-    Every array is caller-owned device memory; x_colmajor is float32 [cols, rows].  Returns the
-    outputs passed in.  Raises EbicError with the library's message on failure."""
+    Every array is caller-owned, contiguous device memory of `device`: x_colmajor float32
+    [cols, rows], col_idx and offsets int32 (offsets 1-D with n + 1 entries), rows_* int32 and
+    fitness int64/uint64 with at least n entries each (any output may be None).  Nothing is
+    converted, since a conversion would allocate: a wrong dtype, device, shape or length raises
+    EbicError(EBIC_EINVAL) before the library is called.  Returns the outputs passed in and
+    raises EbicError with the library's message on failure."""
+    _noalloc_check("x_colmajor", x_colmajor, ("torch.float32",), device, ndim=2)
+    _noalloc_check("offsets", offsets, ("torch.int32",), device, min_numel=1, ndim=1)
+    n = offsets.numel() - 1
+    _noalloc_check("col_idx", col_idx, ("torch.int32",), device, ndim=1)
+    if n > 0:
+        first, last = int(offsets[0].item()), int(offsets[-1].item())   # views: no allocation
+        if first < 0 or last < first or col_idx.numel() < last:
+            raise EbicError(EBIC_EINVAL, f"col_idx holds {col_idx.numel()} entries but offsets "
+                                         f"run from {first} to {last}")
+    for name, o, dts in (("rows_pos", rows_pos, ("torch.int32",)),
+                         ("rows_neg", rows_neg, ("torch.int32",)),
+                         ("rows_any", rows_any, ("torch.int32",)),
+                         ("fitness", fitness, ("torch.int64", "torch.uint64"))):
+        if o is not None:
+            _noalloc_check(name, o, dts, device, min_numel=n)
     cols, rows = x_colmajor.shape
-    n = (offsets.numel() if _is_torch(offsets) else offsets.size) - 1
     buf = ctypes.create_string_buffer(256)
     status = _lib.ebic_eval_population_noalloc(
         ptr(x_colmajor), int(rows), int(cols), ptr(col_idx), ptr(offsets), int(n),
