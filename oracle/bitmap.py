@@ -12,17 +12,25 @@ Test infrastructure only (see the package docstring).
 import numpy as np
 
 
+def pair_words(x, a, b):
+    """The words G[a][b][0..ceil(R/32)) of one ordered column pair."""
+    x = np.asarray(x, dtype=np.float32)
+    R = x.shape[0]
+    W = (R + 31) // 32
+    if a == b:
+        return np.zeros(W, dtype=np.uint32)
+    weights = (np.uint64(1) << np.arange(32, dtype=np.uint64))
+    bits = np.zeros(W * 32, dtype=np.uint64)
+    bits[:R] = (x[:, b] > x[:, a])
+    return (bits.reshape(W, 32) * weights).sum(axis=1).astype(np.uint32)
+
+
 def pair_bitmap(x):
     x = np.asarray(x, dtype=np.float32)
     R, C = x.shape
     W = (R + 31) // 32
     G = np.zeros((C, C, W), dtype=np.uint32)
-    weights = (np.uint64(1) << np.arange(32, dtype=np.uint64))
     for a in range(C):
         for b in range(C):
-            if a == b:
-                continue
-            bits = np.zeros(W * 32, dtype=np.uint64)
-            bits[:R] = (x[:, b] > x[:, a])
-            G[a, b] = (bits.reshape(W, 32) * weights).sum(axis=1).astype(np.uint32)
+            G[a, b] = pair_words(x, a, b)
     return G

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from oracle import counts
-from oracle.bitmap import pair_bitmap
+from oracle.bitmap import pair_bitmap, pair_words
 from oracle.params import Params
 from paper_2105_01196_gb300 import synth
 
@@ -230,3 +230,32 @@ def test_bitmap_definition_against_counts():
         popc = lambda a: sum(bin(int(w)).count("1") for w in a)
         rp, rn, _, _ = counts.eval_individual(x, cols, P())
         assert popc(acc_p) == rp and popc(acc_n) == rn
+
+
+def test_bitmap_layout_hand_worked():
+    """The word layout written out by hand: bit j of word w is row 32w + j, G[a][b] marks rows
+    where column b is strictly greater than column a, ties (including -0 against +0) set no bit,
+    subnormals compare by value, and rows past the end are 0.  40 rows, so the second word holds
+    rows 32..39 only."""
+    R = 40
+    x = np.zeros((R, 3), np.float32)
+    x[[0, 3, 31, 32, 39], 1] = 1.0          # column 1 above column 0 on these rows
+    x[[1, 33], 1] = -1.0                    # and below it on these
+    x[:, 2] = -0.0                          # -0 ties +0 everywhere ...
+    x[5, 2] = np.float32(1e-45)             # ... except a positive subnormal on row 5
+    x[34, 2] = -np.float32(1e-45)           # and a negative one on row 34
+    G = pair_bitmap(x)
+    assert G.shape == (3, 3, 2)
+    assert [int(v) for v in G[0, 1]] == [0x80000009, 0x00000081]   # rows 0, 3, 31 | 32, 39
+    assert [int(v) for v in G[1, 0]] == [0x00000002, 0x00000002]   # row 1 | row 33
+    assert [int(v) for v in G[0, 2]] == [0x00000020, 0x00000000]   # row 5
+    assert [int(v) for v in G[2, 0]] == [0x00000000, 0x00000004]   # row 34
+    # column 1 against column 2: +1 is above every entry of column 2 and -1 below; a 0 of
+    # column 1 ties -0, lies below the positive subnormal (row 5) and above the negative one
+    # (row 34)
+    assert [int(v) for v in G[2, 1]] == [0x80000009, 0x00000085]   # rows 0, 3, 31 | 32, 34, 39
+    assert [int(v) for v in G[1, 2]] == [0x00000022, 0x00000002]   # rows 1, 5 | 33
+    for a in range(3):
+        assert not G[a, a].any()
+    assert [int(v) for v in pair_words(x, 0, 1)] == [0x80000009, 0x00000081]
+
