@@ -328,8 +328,9 @@ EBIC_API int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_t 
  *     job, fills *res and, when capacity >= n_top, the top list (layout of ebic_get_toplist), and
  *     forgets the job.  res->status is the job's own status code.
  *   ebic_server_destroy lets running and admitted jobs finish and drops the queued ones.
- * ebic_job_footprint: device bytes one job holds at most (matrix keys, staging, the pair bitmap
- * when the cost model picks it, population, tabu list, tables), or -1 for bad arguments.
+ * ebic_job_footprint: device bytes one job holds at most (matrix keys, staging, rank codes and
+ * their bit planes up to 1,024 columns, the pair bitmap when the cost model picks it, population,
+ * tabu list, tables), or -1 for bad arguments.
  */
 typedef struct ebic_server ebic_server;
 

@@ -417,9 +417,16 @@ int ebic_build_bitmap(ebic_ctx *ctx) {
   const size_t bytes = (size_t)ebic_bitmap_bytes(ctx->R, ctx->C);
   EBIC_CHECK_CUDA(ctx, ctx->bitmap.ensure(bytes));
   EBIC_CHECK_CUDA(ctx, prepare_bitmap_eval());
+  // With rank codes (C <= 1,024) the words come from the codes' bit planes, else from the keys.
+  if (ctx->code_bytes) EBIC_TRY(ensure_codes(ctx));
   cudaEvent_t ev = prof_begin(ctx);
-  EBIC_CHECK_CUDA(ctx, launch_build_bitmap(ctx->keys.as<uint32_t>(), ctx->R_pad, ctx->C, ctx->Wst,
-                                           ctx->bitmap.as<uint32_t>(), ctx->stream));
+  if (ctx->code_bytes)
+    EBIC_CHECK_CUDA(ctx, launch_build_bitmap_planes(ctx->planes.as<uint32_t>(), ctx->plane_bits,
+                                                    ctx->C, ctx->Wst, ctx->bitmap.as<uint32_t>(),
+                                                    ctx->stream));
+  else
+    EBIC_CHECK_CUDA(ctx, launch_build_bitmap(ctx->keys.as<uint32_t>(), ctx->R_pad, ctx->C,
+                                             ctx->Wst, ctx->bitmap.as<uint32_t>(), ctx->stream));
   prof_end(ctx, ev, EBIC_KERNEL_BITMAP_BUILD, (double)bytes,
            (double)ctx->C * ctx->C * (double)ctx->R, 0.0);
   prof_count(ctx, EBIC_KERNEL_BITMAP_BUILD, 1);
@@ -538,14 +545,19 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
 int ensure_codes(ebic_ctx *ctx) {
   if (!ctx->code_bytes || ctx->codes_ready) return EBIC_OK;
   const int64_t S = ctx->code_stride, C = ctx->C;
+  ctx->plane_bits = code_plane_bits(ctx->C);
   EBIC_CHECK_CUDA(ctx, ctx->codes.ensure((size_t)C * S * ctx->code_bytes));
+  EBIC_CHECK_CUDA(ctx, ctx->planes.ensure((size_t)C * ctx->plane_bits * ctx->Wst * 4));
   cudaEvent_t ev = prof_begin(ctx);
   EBIC_CHECK_CUDA(ctx, launch_rank_codes(ctx->keys.as<uint32_t>(), ctx->R_pad, ctx->C,
-                                         ctx->codes.p, ctx->code_bytes, S, ctx->num_sms,
+                                         ctx->codes.p, ctx->code_bytes, S,
+                                         ctx->planes.as<uint32_t>(), ctx->Wst, ctx->num_sms,
                                          ctx->stream));
+  // algorithmic bytes: keys read, codes and planes written
   prof_end(ctx, ev, EBIC_KERNEL_RANK_CODES,
-           (double)C * ctx->R_pad * 4.0 + (double)C * S * ctx->code_bytes,
-           (double)C * C * (double)ctx->R_pad, (double)ctx->R_pad);
+           (double)C * ctx->R_pad * 4.0 + (double)C * S * ctx->code_bytes +
+               (double)C * ctx->plane_bits * ctx->Wst * 4.0,
+           (double)C * ctx->R_pad, (double)ctx->R_pad);
   prof_count(ctx, EBIC_KERNEL_RANK_CODES, 1);
   if (ctx->prof) {  // (later work on the stream is ordered after the build anyway)
     EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -615,13 +627,8 @@ int choose_mode(const ebic_ctx *ctx, int requested, int64_t n_ind, double mean_l
     free_b = 0;
   }
   if (bitmap_bytes > 0.5 * (double)free_b) return EBIC_MODE_DIRECT;
-  // Relative per-unit costs (direct gathers are ~4x cheaper per byte than a bitmap build word,
-  // bitmap eval words stream from HBM): time in units of one 32-bit access.  Codes of W bytes
-  // read W bytes per row and column, keys four.
-  const double row_bytes = ctx->code_bytes ? (double)ctx->code_bytes : 4.0;
-  const double direct = (double)n_ind * mean_len * (double)ctx->R_pad * row_bytes / 16.0;
-  const double build = C * C * Wst * 4.0;
-  const double eval_bm = (double)n_ind * (mean_len - 1.0) * Wst * 2.0;
-  return (build + expected_sweeps * eval_bm < expected_sweeps * direct) ? EBIC_MODE_BITMAP
-                                                                         : EBIC_MODE_DIRECT;
+  return cost_model_prefers_bitmap((double)ctx->R_pad, C, ctx->code_bytes, (double)n_ind,
+                                   mean_len, (double)expected_sweeps)
+             ? EBIC_MODE_BITMAP
+             : EBIC_MODE_DIRECT;
 }

@@ -29,8 +29,6 @@ namespace {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-constexpr int kRankRows = 32;                        // rows per rank-code tile
-constexpr size_t kRankSmemMax = 1024 * kRankRows * 4;  // C <= 1,024
 constexpr int kMaxDevices = 64;
 constexpr int kVec = 1;  // 16-byte loads per lane and column in one pass
 
@@ -44,41 +42,122 @@ __device__ __forceinline__ void wait_prior_grid() {
 
 // ------------------------------------------------------------------------------- rank codes
 
-// A block ranks 32 rows at a time: the rows' keys of every column are staged in shared memory
-// as [C][32] (lane = row, so a warp's loads are conflict-free), and each thread ranks four
-// columns of its row per sweep over the C keys.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_rank_codes(const uint32_t *__restrict__ keys,
-                                                         int64_t R_pad, int32_t C, int64_t S,
-                                                         T *__restrict__ codes) {
-  extern __shared__ uint32_t s_k[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t n_tiles = R_pad / kRankRows;
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int64_t r0 = tile * kRankRows;
-    __syncthreads();  // the previous tile's keys are no longer read
-    for (int c = warp; c < C; c += kWarps) s_k[c * kRankRows + lane] = keys[(int64_t)c * R_pad + r0 + lane];
-    __syncthreads();
-    for (int c0 = warp; c0 < C; c0 += 4 * kWarps) {
-      uint32_t x[4];
-      int n[4] = {0, 0, 0, 0};
+// One warp ranks one row at a time.  Its C keys (padded with 0xFFFFFFFF, above every key of a
+// finite value, to N = 32 * EPL) are sorted ascending in registers by a bitonic network, with
+// sorted position e = lane * EPL + j in register j of `lane`: compare-exchanges at distance
+// s < EPL stay inside a lane, those at s >= EPL pair lane with lane ^ (s / EPL) through one
+// shuffle.  The sorted row goes to shared memory, and the rank of each key is the number of
+// sorted keys below it, found by a branchless binary search (equal keys get equal codes, as
+// the definition requires).  A block owns 32 consecutive rows: its codes are gathered in a
+// shared [C][32] tile and written column by column (coalesced), and so are the bit planes of
+// the codes: plane p of column c, word w has bit j = bit p of code(32 w + j, c), the operand of
+// the pair-bitmap build (matrix.cu).
+constexpr int kRankRows = 32;  // rows per block tile
+
+template <int EPL>
+__device__ __forceinline__ void bitonic_sort_row(uint32_t (&v)[EPL], int lane) {
+  constexpr int LOG_EPL = EPL == 1 ? 0 : EPL == 2 ? 1 : EPL == 4 ? 2 : EPL == 8 ? 3 : EPL == 16 ? 4 : 5;
+  constexpr int LOG_N = LOG_EPL + 5;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = c0 + j * kWarps;
-        x[j] = c < C ? s_k[c * kRankRows + lane] : 0u;
-      }
-#pragma unroll 4
-      for (int k = 0; k < C; ++k) {
-        const uint32_t v = s_k[k * kRankRows + lane];
+  for (int lk = 1; lk <= LOG_N; ++lk) {
+    const int k = 1 << lk;  // size of the bitonic sequences merged in this phase
 #pragma unroll
-        for (int j = 0; j < 4; ++j) n[j] += v < x[j];
-      }
+    for (int ls = lk - 1; ls >= 0; --ls) {
+      const int st = 1 << ls;  // compare-exchange distance
+      if (st < EPL) {
+        // position e = lane * EPL + j descends in this phase when (e & k) != 0
+        const bool lane_desc = k >= EPL && ((lane * EPL) & k) != 0;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = c0 + j * kWarps;
-        if (c < C) codes[(int64_t)c * S + r0 + lane] = (T)n[j];
+        for (int j = 0; j < EPL; ++j) {
+          const int jp = j ^ st;
+          if (jp > j) {
+            const bool desc = k < EPL ? (j & k) != 0 : lane_desc;
+            const uint32_t lo = min(v[j], v[jp]), hi = max(v[j], v[jp]);
+            v[j] = desc ? hi : lo;
+            v[jp] = desc ? lo : hi;
+          }
+        }
+      } else {
+        const int ld = st / EPL;  // lane distance of the partner
+        const bool take_max = ((lane & ld) != 0) != ((lane & (k / EPL)) != 0);
+#pragma unroll
+        for (int j = 0; j < EPL; ++j) {
+          const uint32_t o = __shfl_xor_sync(kFull, v[j], ld);
+          v[j] = take_max ? max(v[j], o) : min(v[j], o);
+        }
       }
     }
+  }
+}
+
+// Index of sorted position e in a warp's shared buffer (one pad word per 32: the stores of
+// position lane * EPL + j from every lane fall in distinct banks).
+__device__ __forceinline__ int sorted_slot(int e) { return e + (e >> 5); }
+
+// #{sorted keys < q} over N sorted keys (N a power of two).
+template <int N>
+__device__ __forceinline__ int count_below(const uint32_t *srt, uint32_t q) {
+  int pos = 0;
+#pragma unroll
+  for (int step = N / 2; step >= 1; step >>= 1) {
+    const int i = pos + step - 1;
+    if (srt[sorted_slot(i)] < q) pos += step;
+  }
+  if (srt[sorted_slot(pos)] < q) ++pos;
+  return pos;
+}
+
+// T: code type (uint8_t for C <= 128, uint16_t for C <= 1,024); EPL: keys per lane
+// (32 * EPL >= C).  planes may be null (no bit planes wanted); nb planes per column.
+template <typename T, int EPL>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_rank_codes(const uint32_t *__restrict__ keys, int64_t R_pad, int32_t C, int64_t S,
+                 T *__restrict__ codes, uint32_t *__restrict__ planes, int64_t Wst, int nb) {
+  constexpr int N = 32 * EPL;
+  constexpr int kSorted = N + N / 32;              // words of one warp's sorted buffer
+  constexpr int CT = sizeof(T) == 1 ? 36 : 34;     // tile entries per column (bank spread)
+  extern __shared__ __align__(16) uint32_t s_rank[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t *srt = s_rank + warp * kSorted;
+  T *tile = reinterpret_cast<T *>(s_rank + kWarps * kSorted);  // [C][CT]
+  const int64_t n_tiles = R_pad / kRankRows;
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int64_t r0 = t * kRankRows;
+    for (int rho = warp; rho < kRankRows; rho += kWarps) {
+      const int64_t r = r0 + rho;
+      uint32_t q[EPL], v[EPL];
+#pragma unroll
+      for (int j = 0; j < EPL; ++j) {
+        const int c = j * 32 + lane;  // (any placement of the keys before sorting will do)
+        q[j] = c < C ? __ldg(keys + (int64_t)c * R_pad + r) : 0xFFFFFFFFu;
+        v[j] = q[j];
+      }
+      bitonic_sort_row<EPL>(v, lane);
+      __syncwarp();  // the previous row's searches are done with the buffer
+#pragma unroll
+      for (int j = 0; j < EPL; ++j) srt[sorted_slot(lane * EPL + j)] = v[j];
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < EPL; ++j) {
+        const int c = j * 32 + lane;
+        if (c < C) tile[c * CT + rho] = (T)count_below<N>(srt, q[j]);
+      }
+    }
+    __syncthreads();
+    const int64_t w = r0 / 32;
+    for (int c = warp; c < C; c += kWarps) {
+      const uint32_t code = tile[c * CT + lane];
+      codes[(int64_t)c * S + r0 + lane] = (T)code;
+      if (planes) {
+        uint32_t mine = 0;
+        for (int p = 0; p < nb; ++p) {
+          const uint32_t bits = __ballot_sync(kFull, (code >> p) & 1u);
+          if (lane == p) mine = bits;
+        }
+        if (lane < nb) planes[((int64_t)c * nb + lane) * Wst + w] = mine;
+      }
+    }
+    __syncthreads();  // the tile is read before the next rows overwrite it
   }
 }
 
@@ -256,43 +335,66 @@ int64_t code_stride_for(int64_t R, int code_bytes) {
   return (R + q - 1) / q * q;
 }
 
-cudaError_t launch_rank_codes(const uint32_t *keys, int64_t R_pad, int32_t C, void *codes,
-                              int code_bytes, int64_t S, int num_sms, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(codes, 0, (size_t)C * S * code_bytes, s);
-  if (e != cudaSuccess) return e;
-  const size_t smem = (size_t)C * kRankRows * 4;
-  if (smem > kRankSmemMax) return cudaErrorInvalidValue;
+int code_plane_bits(int32_t C) {
+  int nb = 1;
+  while ((1 << nb) < C) ++nb;  // codes lie in [0, C - 1]
+  return nb;
+}
+
+namespace {
+
+template <typename T, int EPL>
+cudaError_t launch_rank_epl(const uint32_t *keys, int64_t R_pad, int32_t C, T *codes, int64_t S,
+                            uint32_t *planes, int64_t Wst, int nb, int num_sms, cudaStream_t s) {
+  constexpr int N = 32 * EPL;
+  constexpr int CT = sizeof(T) == 1 ? 36 : 34;
+  const size_t smem = (size_t)kWarps * (N + N / 32) * 4 + (((size_t)C * CT * sizeof(T) + 15) & ~size_t(15));
   // one fixed limit for every context (no call lowers another's), set once per device
+  constexpr size_t kLimit = (size_t)kWarps * (1024 + 32) * 4 + (size_t)1024 * 34 * 2;
+  static_assert(kLimit <= 227 * 1024, "rank-code shared memory");
   int dev = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
   static std::mutex mu;
   static bool attr_set[kMaxDevices] = {};
   {
     std::lock_guard<std::mutex> lock(mu);
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     if (!attr_set[dev]) {
-      if ((e = cudaFuncSetAttribute(k_rank_codes<uint8_t>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)kRankSmemMax)) != cudaSuccess)
-        return e;
-      if ((e = cudaFuncSetAttribute(k_rank_codes<uint16_t>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)kRankSmemMax)) != cudaSuccess)
+      if ((e = cudaFuncSetAttribute(k_rank_codes<T, EPL>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLimit)) !=
+          cudaSuccess)
         return e;
       attr_set[dev] = true;
     }
   }
   const int64_t n_tiles = R_pad / kRankRows;
-  if (code_bytes == 1) {
-    const int64_t grid = std::min<int64_t>(n_tiles, (int64_t)num_sms * blocks_per_sm(k_rank_codes<uint8_t>, smem));
-    k_rank_codes<uint8_t><<<(unsigned)grid, kThreads, smem, s>>>(keys, R_pad, C, S,
-                                                                 static_cast<uint8_t *>(codes));
-  } else {
-    const int64_t grid = std::min<int64_t>(n_tiles, (int64_t)num_sms * blocks_per_sm(k_rank_codes<uint16_t>, smem));
-    k_rank_codes<uint16_t><<<(unsigned)grid, kThreads, smem, s>>>(keys, R_pad, C, S,
-                                                                  static_cast<uint16_t *>(codes));
-  }
+  const int64_t grid =
+      std::min<int64_t>(n_tiles, (int64_t)num_sms * blocks_per_sm(k_rank_codes<T, EPL>, smem));
+  k_rank_codes<T, EPL><<<(unsigned)grid, kThreads, smem, s>>>(keys, R_pad, C, S, codes, planes,
+                                                                Wst, nb);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_rank_codes(const uint32_t *keys, int64_t R_pad, int32_t C, void *codes,
+                              int code_bytes, int64_t S, uint32_t *planes, int64_t Wst,
+                              int num_sms, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(codes, 0, (size_t)C * S * code_bytes, s);
+  if (e != cudaSuccess) return e;
+  if (C > 1024 || code_bytes != (C <= 128 ? 1 : 2)) return cudaErrorInvalidValue;
+  const int nb = code_plane_bits(C);
+  if (code_bytes == 1) {
+    uint8_t *cd = static_cast<uint8_t *>(codes);
+    return C <= 32 ? launch_rank_epl<uint8_t, 1>(keys, R_pad, C, cd, S, planes, Wst, nb, num_sms, s)
+         : C <= 64 ? launch_rank_epl<uint8_t, 2>(keys, R_pad, C, cd, S, planes, Wst, nb, num_sms, s)
+                   : launch_rank_epl<uint8_t, 4>(keys, R_pad, C, cd, S, planes, Wst, nb, num_sms, s);
+  }
+  uint16_t *cd = static_cast<uint16_t *>(codes);
+  return C <= 256 ? launch_rank_epl<uint16_t, 8>(keys, R_pad, C, cd, S, planes, Wst, nb, num_sms, s)
+       : C <= 512 ? launch_rank_epl<uint16_t, 16>(keys, R_pad, C, cd, S, planes, Wst, nb, num_sms, s)
+                  : launch_rank_epl<uint16_t, 32>(keys, R_pad, C, cd, S, planes, Wst, nb, num_sms, s);
 }
 
 cudaError_t launch_eval_codes(const EvalArgs &a0, const PopView &pv, int num_sms, cudaStream_t s,

@@ -104,13 +104,16 @@ struct EvalArgs {
 };
 
 // Per-row rank codes (codes.cu): code width for C columns (1 for C <= 128, 2 for C <= 1024,
-// else 0 = none), rows per pass of the code kernel, padded rows per code column, the rank
-// kernel (zero-fills the padding) and the direct evaluation over codes.
+// else 0 = none), rows per pass of the code kernel, padded rows per code column, the number of
+// bit planes of the codes (bits of C - 1), the rank kernel (zero-fills the padding; writes the
+// bit planes [C][nb][Wst] too when `planes` is not null) and the direct evaluation over codes.
 int code_bytes_for(int32_t C);
 int64_t code_rows_per_pass(int code_bytes);
 int64_t code_stride_for(int64_t R, int code_bytes);
+int code_plane_bits(int32_t C);
 cudaError_t launch_rank_codes(const uint32_t *keys, int64_t R_pad, int32_t C, void *codes,
-                              int code_bytes, int64_t S, int num_sms, cudaStream_t s);
+                              int code_bytes, int64_t S, uint32_t *planes, int64_t Wst,
+                              int num_sms, cudaStream_t s);
 cudaError_t launch_eval_codes(const EvalArgs &a, const PopView &pv, int num_sms, cudaStream_t s,
                               bool pdl);
 
@@ -160,10 +163,12 @@ struct ebic_ctx {
   DirectTma dtma;
   DevBuf d_kerr;
 
-  // per-row rank codes of the loaded matrix (code_bytes 0: none), built on first use
-  DevBuf codes;
+  // per-row rank codes of the loaded matrix (code_bytes 0: none) and their bit planes
+  // [C][plane_bits][Wst] (the pair-bitmap build's operand), built together on first use
+  DevBuf codes, planes;
   int code_bytes = 0;
   int64_t code_stride = 0;
+  int plane_bits = 0;
   bool codes_ready = false;
 
   // autotuner decisions for the loaded matrix (tune.cu)
@@ -230,6 +235,9 @@ cudaError_t launch_upload(const float *x, int64_t R, int32_t C, int64_t R_pad, i
                           uint32_t *keys, int32_t *err, cudaStream_t s);
 cudaError_t launch_build_bitmap(const uint32_t *keys, int64_t R_pad, int32_t C, int64_t Wst,
                                 uint32_t *bitmap, cudaStream_t s);
+// The same bitmap from the bit planes of the rank codes (nb planes per column, nb <= 10).
+cudaError_t launch_build_bitmap_planes(const uint32_t *planes, int nb, int32_t C, int64_t Wst,
+                                       uint32_t *bitmap, cudaStream_t s);
 
 // eval.cu
 cudaError_t launch_validate_csr(const int32_t *cols, const int32_t *off, int32_t n, int32_t C,
@@ -253,6 +261,20 @@ cudaError_t launch_fitness(const EvalArgs &a, const PopView &pv, cudaStream_t s)
 cudaError_t prepare_bitmap_eval();
 int choose_mode(const ebic_ctx *ctx, int requested, int64_t n_ind, double mean_len,
                 int expected_sweeps, int last_kept);
+// The cost model behind AUTO without tuning (and the job server's footprint): whether building
+// the pair bitmap and running `sweeps` bitmap sweeps is expected to beat `sweeps` direct sweeps.
+// Costs are in units of about 1.3 ns on GB300, measured per unit on the tie-heavy workload
+// (60,000 x 1,000, P 8,192): a bitmap word built (the bit-plane build), a pair word per
+// individual and pair in a sweep (both directions), and 16 bytes of codes (or keys) gathered by
+// the direct form.
+inline bool cost_model_prefers_bitmap(double R_pad, double C, int code_bytes, double n_ind,
+                                      double mean_len, double sweeps) {
+  const double Wst = R_pad / 32.0;
+  const double build = C * C * Wst;
+  const double eval_bm = n_ind * (mean_len - 1.0) * Wst;
+  const double direct = n_ind * mean_len * R_pad * (code_bytes ? code_bytes : 4) / 16.0;
+  return build + sweeps * eval_bm < sweeps * direct;
+}
 
 // Capacities of the generation loop's hash tables (tables.cuh): powers of two at load factor
 // <= 1 / kTableSpread.  The tabu list is sized for `keys` keys, the duplicate table for P.

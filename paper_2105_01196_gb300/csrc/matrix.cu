@@ -166,6 +166,97 @@ __global__ void __launch_bounds__(kBW * 32, 4) k_build_bitmap(const uint32_t *__
   }
 }
 
+// Pair bitmap from the bit planes of the per-row rank codes (codes.cu): comparing codes is
+// comparing keys (the codes keep every within-row order), and a word of planes holds one bit of
+// 32 rows' codes, so one lane compares 32 rows at once.  Going from the lowest plane to the
+// highest, with A and B the planes of columns a and b,
+//   gt = (B & ~A) | (~(A ^ B) & gt)      lt = (A & ~B) | (~(A ^ B) & lt)
+// (each a single three-input logic operation) leave gt = [code_b > code_a] = G[a][b] and
+// lt = [code_a > code_b] = G[b][a] in every bit: a higher differing bit overrides the lower
+// ones, equal bits keep them.  Ties and pad rows (code 0 everywhere) set neither.
+// A warp owns four a-columns (their planes in registers) and one 32-word chunk of rows (a word
+// per lane, so every store is one coalesced 128-byte row piece), and walks b over the columns
+// after its own; the b planes of a block's eight warps come through L1.  Block id
+// = a-block * (chunks) + chunk, so the blocks with the most b columns start first.
+constexpr int kPA = 4;  // a-columns per warp
+
+template <int NB>
+__device__ __forceinline__ void plane_compare(const uint32_t (&A)[NB], const uint32_t (&B)[NB],
+                                              uint32_t &gt, uint32_t &lt) {
+  gt = 0u;
+  lt = 0u;
+#pragma unroll
+  for (int p = 0; p < NB; ++p) {
+    gt = (B[p] & ~A[p]) | (~(A[p] ^ B[p]) & gt);
+    lt = (A[p] & ~B[p]) | (~(A[p] ^ B[p]) & lt);
+  }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(256) k_build_bitmap_planes(const uint32_t *__restrict__ planes,
+                                                             int32_t C, int64_t Wst,
+                                                             int32_t n_chunks,
+                                                             uint32_t *__restrict__ G) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ablk = blockIdx.x / n_chunks, chunk = blockIdx.x - ablk * n_chunks;
+  const int64_t w = (int64_t)chunk * 32 + lane;
+  const bool w_ok = w < Wst;
+  const int a0 = (ablk * 8 + warp) * kPA;
+  if (a0 >= C) return;  // (the whole warp)
+  uint32_t A[kPA][NB];
+#pragma unroll
+  for (int i = 0; i < kPA; ++i)
+#pragma unroll
+    for (int p = 0; p < NB; ++p)
+      A[i][p] = (a0 + i < C && w_ok) ? __ldg(planes + ((int64_t)(a0 + i) * NB + p) * Wst + w) : 0u;
+  if (!w_ok) return;  // (no warp-wide operation follows)
+  const int64_t row = (int64_t)C * Wst;  // words between G[a][.] and G[a + 1][.]
+  // the diagonal words, and the pairs among the warp's own columns
+#pragma unroll
+  for (int i = 0; i < kPA; ++i) {
+    const int a = a0 + i;
+    if (a >= C) break;
+    G[(int64_t)a * row + (int64_t)a * Wst + w] = 0u;
+#pragma unroll
+    for (int i2 = i + 1; i2 < kPA; ++i2) {
+      const int b = a0 + i2;
+      if (b < C) {
+        uint32_t gt, lt;
+        plane_compare<NB>(A[i], A[i2], gt, lt);
+        __stcs(G + (int64_t)a * row + (int64_t)b * Wst + w, gt);
+        __stcs(G + (int64_t)b * row + (int64_t)a * Wst + w, lt);
+      }
+    }
+  }
+  // every later column b: G[a][b] at a * row + b * Wst, G[b][a] at b * row + a * Wst
+  const int b0 = a0 + kPA;
+  if (b0 >= C) return;
+  uint32_t *g_ab = G + (int64_t)a0 * row + (int64_t)b0 * Wst + w;  // a = a0; + i * row for a0 + i
+  uint32_t *g_ba = G + (int64_t)b0 * row + (int64_t)a0 * Wst + w;  // a = a0; + i * Wst
+  const uint32_t *pb = planes + (int64_t)b0 * NB * Wst + w;
+  uint32_t B[NB];
+#pragma unroll
+  for (int p = 0; p < NB; ++p) B[p] = __ldg(pb + (int64_t)p * Wst);
+  for (int b = b0; b < C; ++b) {
+    uint32_t Bn[NB];
+    const bool more = b + 1 < C;
+    pb += (int64_t)NB * Wst;
+#pragma unroll
+    for (int p = 0; p < NB; ++p) Bn[p] = more ? __ldg(pb + (int64_t)p * Wst) : 0u;
+#pragma unroll
+    for (int i = 0; i < kPA; ++i) {
+      uint32_t gt, lt;
+      plane_compare<NB>(A[i], B, gt, lt);
+      __stcs(g_ab + (int64_t)i * row, gt);
+      __stcs(g_ba + (int64_t)i * Wst, lt);
+    }
+    g_ab += Wst;
+    g_ba += row;
+#pragma unroll
+    for (int p = 0; p < NB; ++p) B[p] = Bn[p];
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_upload(const float *x, int64_t R, int32_t C, int64_t R_pad, int32_t layout,
@@ -197,5 +288,27 @@ cudaError_t launch_build_bitmap(const uint32_t *keys, int64_t R_pad, int32_t C, 
       std::min<int64_t>(max_split, std::max<int64_t>(1, (4LL * sms + gx * gy - 1) / (gx * gy)));
   dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)std::min<int64_t>(split, 65535));
   k_build_bitmap<<<grid, kBW * 32, 0, s>>>(keys, R_pad, C, Wst, bitmap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_bitmap_planes(const uint32_t *planes, int nb, int32_t C, int64_t Wst,
+                                       uint32_t *bitmap, cudaStream_t s) {
+  const int64_t n_chunks = (Wst + 31) / 32, n_ablk = (C + 8 * kPA - 1) / (8 * kPA);
+  if (n_chunks * n_ablk > 0x7FFFFFFF) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)(n_chunks * n_ablk)), block(256);
+  const int32_t nc = (int32_t)n_chunks;
+  switch (nb) {
+    case 1: k_build_bitmap_planes<1><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
+    case 2: k_build_bitmap_planes<2><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
+    case 3: k_build_bitmap_planes<3><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
+    case 4: k_build_bitmap_planes<4><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
+    case 5: k_build_bitmap_planes<5><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
+    case 6: k_build_bitmap_planes<6><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
+    case 7: k_build_bitmap_planes<7><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
+    case 8: k_build_bitmap_planes<8><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
+    case 9: k_build_bitmap_planes<9><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
+    case 10: k_build_bitmap_planes<10><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }

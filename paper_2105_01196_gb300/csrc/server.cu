@@ -33,14 +33,12 @@ int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 int job_mode(int64_t rows, int32_t cols, const ebic_params &p, int32_t n_gen) {
   if (p.mode != EBIC_MODE_AUTO) return p.mode;
   if (p.last_kept) return EBIC_MODE_DIRECT;  // no bitmap form
-  const double R_pad = (double)round_up(rows, 128), Wst = R_pad / 32.0, C = cols;
   const double mean_len = 0.5 * (p.init_min_len + p.max_len);
-  const double sweeps = (double)n_gen + 1.0;
-  const int w = code_bytes_for(cols);
-  const double direct = (double)p.pop_size * mean_len * R_pad * (w ? w : 4) / 16.0;
-  const double build = C * C * Wst * 4.0;
-  const double eval_bm = (double)p.pop_size * (mean_len - 1.0) * Wst * 2.0;
-  return build + sweeps * eval_bm < sweeps * direct ? EBIC_MODE_BITMAP : EBIC_MODE_DIRECT;
+  return cost_model_prefers_bitmap((double)round_up(rows, 128), (double)cols,
+                                   code_bytes_for(cols), (double)p.pop_size, mean_len,
+                                   (double)n_gen + 1.0)
+             ? EBIC_MODE_BITMAP
+             : EBIC_MODE_DIRECT;
 }
 
 struct Job {
@@ -160,6 +158,10 @@ int64_t ebic_job_footprint(int64_t rows, int32_t cols, const ebic_params *p, int
   bytes += rows * (int64_t)cols * 4;                      // staged host matrix
   if (job_mode(rows, cols, *p, n_gen) == EBIC_MODE_BITMAP)
     bytes += ebic_bitmap_bytes(rows, cols);               // pair bitmap
+  const int w = code_bytes_for(cols);
+  if (w)  // rank codes and their bit planes (both forms build them)
+    bytes += (int64_t)cols * code_stride_for(rows, w) * w +
+             (int64_t)cols * code_plane_bits(cols) * (R_pad / 32) * 4;
   bytes += 2 * P * (EBIC_MAX_LEN * 4 + 4 + 4 + 12 + 1 + 1 + 8 + 8);  // population buffers
   bytes += P * 12 + 64;                                   // evaluation scratch
   bytes += (int64_t)tabu_capacity(P * ((int64_t)n_gen + 2)) * 8;  // tabu list

@@ -145,21 +145,40 @@ def test_device_pointers_and_col_major(ebic, torch_cuda):
                 assert_parity(got, want)
 
 
-def test_bitmap_matches_oracle_definition(ebic):
-    g = np.random.default_rng(11)
-    for R, C in ((77, 7), (300, 20), (1030, 9)):
-        x = g.integers(0, 5, size=(R, C)).astype(np.float32)
-        want = pair_bitmap(x)                       # [C][C][ceil(R/32)]
-        with ebic.Context(0) as ctx:
-            ctx.load_matrix(x)
-            ctx.build_bitmap()
-            wst = ((R + 127) // 128) * 4
-            out = np.zeros(C * C * wst, np.uint32)
-            ctx.copy_bitmap(out)
-            got = out.reshape(C, C, wst)
-            W = want.shape[2]
-            assert np.array_equal(got[:, :, :W], want)
-            assert not got[:, :, W:].any()
+@pytest.mark.parametrize("R,C", [(77, 2), (300, 3), (130, 5), (1030, 9), (200, 16),
+                                 (64, 17), (40, 33), (33, 64), (257, 65), (129, 128),
+                                 (100, 129), (97, 256), (70, 257), (35, 512), (66, 513),
+                                 (45, 1000), (33, 1024), (40, 1025)])
+def test_bitmap_matches_oracle_definition(ebic, R, C):
+    """Every pair word against the oracle's definition: bit planes of 1 to 10 bits (built from
+    the rank codes up to 1,024 columns) and the order-key build beyond; ties, signed zeros,
+    subnormals and extreme magnitudes; rows not a multiple of 32.  Up to 129 columns every
+    pair is compared, beyond that a sample that includes the first, last and diagonal pairs."""
+    from oracle.bitmap import pair_words
+    g = np.random.default_rng(11 + R * 3 + C)
+    x = g.integers(-3, 4, size=(R, C)).astype(np.float32)
+    x[g.random((R, C)) < 0.05] = -0.0
+    x[g.random((R, C)) < 0.02] = np.float32(1e-45)
+    x[g.random((R, C)) < 0.02] = -np.float32(3e-42)
+    x[g.random((R, C)) < 0.01] = np.finfo(np.float32).max
+    x[g.random((R, C)) < 0.01] = -np.finfo(np.float32).max
+    W = (R + 31) // 32
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        ctx.build_bitmap()
+        wst = ((R + 127) // 128) * 4
+        out = np.zeros(C * C * wst, np.uint32)
+        ctx.copy_bitmap(out)
+        got = out.reshape(C, C, wst)
+    assert not got[:, :, W:].any()
+    if C <= 129:
+        assert np.array_equal(got[:, :, :W], pair_bitmap(x))
+        return
+    pairs = {(0, 1), (1, 0), (0, C - 1), (C - 1, 0), (C - 2, C - 1), (C - 1, C - 2), (5, 5),
+             (C - 1, C - 1)}
+    pairs |= {(int(a), int(b)) for a, b in g.integers(0, C, size=(300, 2))}
+    for a, b in sorted(pairs):
+        assert np.array_equal(got[a, b, :W], pair_words(x, a, b)), (a, b)
 
 
 def test_errors_are_reported(ebic, torch_cuda):
