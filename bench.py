@@ -230,26 +230,131 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def cpu_baseline(w, x, ci, off, seconds, trend="strict"):
-    """The CPU oracle as it stands, single-threaded, on a bounded sample of the workload: full
-    trend counts of the workload's individuals, cycling through the population, until `seconds`
-    pass."""
+def run_fields(w, trend="strict"):
+    """The run parameters of a workload, shared by the GPU path and the oracle baseline."""
+    return dict(neg_trends=w.neg_trends, ratio_num=w.ratio[0], ratio_den=w.ratio[1],
+                pop_size=w.pop, max_len=min(w.len_hi, 64), init_min_len=w.len_lo,
+                init_max_len=min(w.len_hi, 64), n_biclusters=max(10, w.n_bic),
+                elite=max(10, w.n_bic), tabu_hit_limit=0, seed=w.seed,
+                non_strict=int("ties" in trend), last_kept=int("last-kept" in trend))
+
+
+# --------------------------------------------------------------------------- CPU oracle baseline
+# The oracle runs unchanged; a process pool (started with "spawn", so no worker inherits a CUDA
+# context) splits its independent per-individual trend counts over the host cores.  Workers map
+# the matrix from a temporary .npy file instead of receiving a pickled copy.
+
+_POOL_X = None
+
+
+def _pool_init(path):
+    global _POOL_X
+    _POOL_X = np.load(path, mmap_mode="r")
+
+
+def _pool_eval_timed(task):
+    """Oracle trend counts of individuals start, start + stride, ... (cycling through the
+    population) until `seconds` pass; returns how many were evaluated."""
     from oracle import counts as ocounts
     from oracle.params import Params as OParams
-    p = OParams(neg_trends=w.neg_trends, ratio_num=w.ratio[0], ratio_den=w.ratio[1],
-                non_strict=int("ties" in trend), last_kept=int("last-kept" in trend))
+    ci, off, start, stride, seconds, fields = task
+    p = OParams(**fields)
     n = len(off) - 1
     t0 = time.perf_counter()
-    done = 0
+    done, i = 0, start % n
     while time.perf_counter() - t0 < seconds:
-        i = done % n
-        cols = [int(c) for c in ci[off[i]:off[i + 1]]]
-        ocounts.eval_individual(x, cols, p)
+        ocounts.eval_individual(_POOL_X, [int(c) for c in ci[off[i]:off[i + 1]]], p)
         done += 1
+        i = (i + stride) % n
+    return done
+
+
+def _pool_counts(task):
+    from oracle.ebic import row_counts
+    from oracle.params import Params as OParams
+    chroms, fields = task
+    p = OParams(**fields)
+    return [row_counts(_POOL_X, list(c), p) for c in chroms]
+
+
+class OraclePool:
+    """Worker processes on every core this process may run on (os.sched_getaffinity)."""
+
+    def __init__(self, x):
+        import multiprocessing as mp
+        self.cores = len(os.sched_getaffinity(0))
+        fd, self.path = tempfile.mkstemp(suffix=".npy")
+        os.close(fd)
+        np.save(self.path, np.ascontiguousarray(x))
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_pool_init,
+                                                 initargs=(self.path,))
+
+    def counts_map(self, fields):
+        """A counts_map for the oracle's scoring step: chromosomes split into one chunk per
+        core, counted in the workers, returned in order."""
+        def run(chroms):
+            k = max(1, -(-len(chroms) // self.cores))
+            chunks = [(chroms[i:i + k], fields) for i in range(0, len(chroms), k)]
+            return [t for part in self.pool.map(_pool_counts, chunks) for t in part]
+        return run
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+        os.unlink(self.path)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def cpu_baseline(w, x, ci, off, seconds, trend="strict", pool=None, generation=False):
+    """The CPU oracle as it stands, on a bounded sample of the workload: full trend counts of the
+    workload's individuals, cycling through the population, for `seconds` (on every worker of
+    `pool` at once, else single-threaded).  With `generation`, also one generation of the oracle's
+    EBIC loop (initial population, then one timed generation, with the pool's counts map): the
+    oracle's generations/s, measured on one generation of the workload's run."""
+    from oracle import counts as ocounts
+    from oracle.params import Params as OParams
+    fields = run_fields(w, trend)
+    n = len(off) - 1
+    t0 = time.perf_counter()
+    if pool is None:
+        p = OParams(**fields)
+        done = 0
+        while time.perf_counter() - t0 < seconds:
+            i = done % n
+            ocounts.eval_individual(x, [int(c) for c in ci[off[i]:off[i + 1]]], p)
+            done += 1
+        cores = 1
+    else:
+        cores = pool.cores
+        tasks = [(ci, off, k * (n // cores), 1, seconds, fields) for k in range(cores)]
+        done = sum(pool.pool.map(_pool_eval_timed, tasks))
     dt = time.perf_counter() - t0
-    return {"value": done * x.shape[0] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle trend counts of {done} individual evaluations (the workload's "
-                      f"{n} individuals, cycled) x {x.shape[0]} rows ({dt:.1f} s, single thread)"}
+    out = {"value": done * x.shape[0] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"oracle trend counts of {done} individual evaluations (the workload's "
+                     f"{n} individuals, cycled) x {x.shape[0]} rows ({dt:.1f} s, "
+                     + ("single thread)" if pool is None else
+                        f"{cores} worker processes, individuals split over them)")}
+    if generation:
+        from oracle import ebic as oebic
+        op = OParams(**fields)
+        cmap = pool.counts_map(fields) if pool is not None else None
+        t1 = time.perf_counter()
+        st = oebic.initialise(x, op, cmap)
+        t2 = time.perf_counter()
+        oebic.next_generation(x, st, op, cmap)
+        t3 = time.perf_counter()
+        out["generations_per_s"] = 1.0 / (t3 - t2)
+        out["generation_sample"] = (f"oracle EBIC loop on this workload: initial population "
+                                    f"({t2 - t1:.1f} s) then 1 generation timed ({t3 - t2:.2f} s)"
+                                    f" of the run's {w.generations}; "
+                                    + ("single thread" if pool is None else
+                                       f"trend counts on {cores} worker processes"))
+    return out
 
 
 def run_reference(args, w, world, rank, dist):
@@ -259,15 +364,20 @@ def run_reference(args, w, world, rank, dist):
         return
     x, _, ci, off = synth.workload_inputs(w)
     per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
-    for _ in range(args.warmup):
-        cpu_baseline(w, x, ci, off, per_step / 4, args.trend)
-    vals = []
-    t0 = time.perf_counter()
-    last = None
-    for _ in range(args.steps):
-        last = cpu_baseline(w, x, ci, off, per_step, args.trend)
-        vals.append(last["value"])
-    total = time.perf_counter() - t0
+    pool = OraclePool(x) if getattr(args, "pool", True) else None
+    try:
+        for _ in range(args.warmup):
+            cpu_baseline(w, x, ci, off, per_step / 4, args.trend, pool=pool)
+        vals = []
+        t0 = time.perf_counter()
+        last = None
+        for _ in range(args.steps):
+            last = cpu_baseline(w, x, ci, off, per_step, args.trend, pool=pool)
+            vals.append(last["value"])
+        total = time.perf_counter() - t0
+    finally:
+        if pool is not None:
+            pool.close()
     v = float(np.median(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
@@ -373,13 +483,7 @@ def main():
     outs_h.append(torch.zeros(P, dtype=torch.int64).pin_memory())
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    params = ebic.Params.make(neg_trends=w.neg_trends, ratio_num=w.ratio[0],
-                              ratio_den=w.ratio[1], pop_size=w.pop, max_len=min(w.len_hi, 64),
-                              init_min_len=w.len_lo, init_max_len=min(w.len_hi, 64),
-                              n_biclusters=max(10, w.n_bic), elite=max(10, w.n_bic),
-                              tabu_hit_limit=0, seed=w.seed, mode=MODES[args.mode],
-                              non_strict=int("ties" in args.trend),
-                              last_kept=int("last-kept" in args.trend))
+    params = ebic.Params.make(mode=MODES[args.mode], **run_fields(w, args.trend))
     ctx = ebic.Context(local, stream.cuda_stream)
     used_mode = [0]                     # evaluation form the generation loop used
 
@@ -433,7 +537,8 @@ def main():
     torch.cuda.synchronize()
     stats = {name: ctx.profile_read(kid) for name, kid in
              (("eval", ebic.KERNEL_EVAL), ("evolve", ebic.KERNEL_EVOLVE),
-              ("finish", ebic.KERNEL_FINISH), ("bitmap_build", ebic.KERNEL_BITMAP_BUILD))}
+              ("finish", ebic.KERNEL_FINISH), ("bitmap_build", ebic.KERNEL_BITMAP_BUILD),
+              ("rank_codes", ebic.KERNEL_RANK_CODES))}
     ctx.profile_enable(False)
     if dist:
         total_ms, units = reduce_over_ranks(dist, total_ms, units, dev)
@@ -471,7 +576,8 @@ def main():
     dominant = max(stats, key=lambda k: stats[k]["ms"])
     kernel_names = {"eval": eval_kernel_name(used_mode[0] if used_mode[0] else MODES[args.mode],
                                              w.cols),
-                    "evolve": "k_evolve", "finish": "k_finish", "bitmap_build": "k_build_bitmap"}
+                    "evolve": "k_evolve", "finish": "k_finish", "bitmap_build": "k_build_bitmap",
+                    "rank_codes": "k_rank_codes"}
     roof = None
     se = stats["eval"]
     if se["timed_launches"] > 0 and se["ms"] > 0:
@@ -515,7 +621,9 @@ def main():
     if not args.no_scale_roofline and w.name != "batched":
         line["roofline_at_scale"] = scale_roofline(ebic, dev, stream, peak, peak_kind)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, x, ci, off, args.cpu_seconds, args.trend)
+        with OraclePool(x) as pool:
+            line["cpu_baseline"] = cpu_baseline(w, x, ci, off, args.cpu_seconds, args.trend,
+                                                pool=pool, generation=gens > 0)
     print(json.dumps(line), flush=True)
     ctx.close()
     if dist:

@@ -233,19 +233,29 @@ def update_toplist(top, cands, p):
 
 # ----------------------------------------------------------------------------- scoring
 
-def score(x, st, p):
-    """Steps 2-3 / 7: counts and fitness of every live slot, then top list, tabu list, penalty."""
+def row_counts(x, cols, p):
+    """(rows_pos, rows_neg, rows_any) of one chromosome."""
+    pos_ok, neg_ok = row_trend_masks(x, cols, p.neg_trends, p.ratio_num, p.ratio_den,
+                                     p.non_strict, p.last_kept)
+    return int(pos_ok.sum()), int(neg_ok.sum()), int((pos_ok | neg_ok).sum())
+
+
+def score(x, st, p, counts_map=None):
+    """Steps 2-3 / 7: counts and fitness of every live slot, then top list, tabu list, penalty.
+
+    counts_map, when given, replaces the serial loop of ``row_counts`` over the live slots'
+    chromosomes (a list in slot order -> their count triples, in the same order); it lets a
+    caller spread the independent per-individual counts over several processes."""
     P = len(st.pop)
     st.fit = [0] * P
     st.rows = [(0, 0, 0)] * P
     cands = []
-    for s in range(P):
-        if st.dead[s]:
-            continue
+    live = [s for s in range(P) if not st.dead[s]]
+    chroms = [st.pop[s] for s in live]
+    counted = ([row_counts(x, c, p) for c in chroms] if counts_map is None
+               else list(counts_map(chroms)))
+    for s, (rp, rn, ra) in zip(live, counted):
         cols = st.pop[s]
-        pos_ok, neg_ok = row_trend_masks(x, cols, p.neg_trends, p.ratio_num, p.ratio_den,
-                                         p.non_strict, p.last_kept)
-        rp, rn, ra = int(pos_ok.sum()), int(neg_ok.sum()), int((pos_ok | neg_ok).sum())
         st.rows[s] = (rp, rn, ra)
         st.fit[s] = fitness(ra, len(cols), p.min_rows, p.col_cap)
         st.n_evaluated += 1
@@ -261,7 +271,7 @@ def score(x, st, p):
 
 # ----------------------------------------------------------------------------- the loop
 
-def initialise(x, p):
+def initialise(x, p, counts_map=None):
     x = check_matrix(x)
     validate(p, x.shape[1])
     st = State()
@@ -270,12 +280,12 @@ def initialise(x, p):
     st.dead = [len(c) < 2 for c in st.pop]
     st.hashes = [tabu_key(chromosome_hash(c)) for c in st.pop]
     st.hits.append(dedup(st.pop, st.dead, st.hashes, 0))
-    score(x, st, p)
+    score(x, st, p, counts_map)
     st.gen = 0
     return st
 
 
-def next_generation(x, st, p):
+def next_generation(x, st, p, counts_map=None):
     """Steps 4-8 for generation st.gen + 1; returns False when step 6 stopped the run."""
     n_cols = x.shape[1]
     g = st.gen + 1
@@ -309,18 +319,19 @@ def next_generation(x, st, p):
         st.stopped = True
         return False
     st.pop, st.dead, st.hashes = pop, dead, hashes
-    score(x, st, p)
+    score(x, st, p, counts_map)
     st.gen = g
     return True
 
 
-def run(x, p, n_gen, st=None):
-    """Initialise when ``st`` is None, then run up to n_gen generations (fewer if step 6 stops)."""
+def run(x, p, n_gen, st=None, counts_map=None):
+    """Initialise when ``st`` is None, then run up to n_gen generations (fewer if step 6 stops).
+    counts_map: see ``score``."""
     x = check_matrix(x)
     if st is None:
-        st = initialise(x, p)
+        st = initialise(x, p, counts_map)
     for _ in range(n_gen):
-        if st.stopped or not next_generation(x, st, p):
+        if st.stopped or not next_generation(x, st, p, counts_map):
             break
     return st
 

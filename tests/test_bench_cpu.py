@@ -53,10 +53,31 @@ def test_cpu_baseline_counts_oracle_evaluations():
     assert f"x {x.shape[0]} rows" in r["sample"]
 
 
+def test_cpu_baseline_pool_uses_every_core_and_matches_the_serial_oracle():
+    """The pool's counts map gives the serial oracle's run exactly (it only moves the
+    independent per-individual counts to other processes), and the baseline reports the cores
+    from the affinity mask and the oracle's generations per second."""
+    import dataclasses
+    from oracle import ebic as oebic
+    from oracle.params import Params as OParams
+    w = dataclasses.replace(synth.WORKLOADS["tiny"], generations=3)
+    x, _, ci, off = synth.workload_inputs(w)
+    fields = bench.run_fields(w)
+    with bench.OraclePool(x) as pool:
+        assert pool.cores == len(os.sched_getaffinity(0))
+        r = bench.cpu_baseline(w, x, ci, off, 0.3, pool=pool, generation=True)
+        a = oebic.run(x, OParams(**fields), 3, counts_map=pool.counts_map(fields))
+    b = oebic.run(x, OParams(**fields), 3)
+    assert [(e.cols, e.f, e.h) for e in a.top] == [(e.cols, e.f, e.h) for e in b.top]
+    assert a.pop == b.pop and a.fit == b.fit and a.rows == b.rows and a.hits == b.hits
+    assert r["cores"] == pool.cores and r["value"] > 0 and r["generations_per_s"] > 0
+    assert "1 generation timed" in r["generation_sample"]
+
+
 def test_reference_arm_line(monkeypatch, capsys):
     calls = []
 
-    def fake_baseline(w, x, ci, off, seconds, trend="strict"):
+    def fake_baseline(w, x, ci, off, seconds, trend="strict", pool=None):
         calls.append(seconds)
         return {"value": float(len(calls)), "unit": bench.UNIT, "cores": 1, "kind": "oracle",
                 "sample": "stub"}
@@ -64,7 +85,7 @@ def test_reference_arm_line(monkeypatch, capsys):
     monkeypatch.setattr(bench, "cpu_baseline", fake_baseline)
 
     class Args:
-        steps, warmup, gpus, gens, mode, trend = 3, 3, 1, None, "auto", "strict"
+        steps, warmup, gpus, gens, mode, trend, pool = 3, 3, 1, None, "auto", "strict", False
 
     bench.run_reference(Args, synth.WORKLOADS["tiny"], 1, 0, None)
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
