@@ -221,10 +221,12 @@ __device__ __forceinline__ uint32_t valid_bits(int64_t w, int64_t R) {
 // A pass covers 128 words (4096 rows) of a column pair; lane l holds words 4l..4l+3.
 constexpr int kPassWords = 128;
 
-// Staged form: each warp has kStageBytes of shared memory, one pass of NB pairs per direction.
-// The lanes copy the pair words of up to NB pairs with asynchronous copies (cp.async, 16 bytes
-// each, no registers held while they are in flight) and wait once, so an individual of np pairs
-// costs ceil(np / NB) round trips to memory.  Each lane reads back only the bytes it copied.
+// Staged form: each warp has kStageBytes of shared memory, two halves of NB / 2 pairs per
+// direction.  The lanes copy the pair words of a unit (one pass, up to NB / 2 pairs) with
+// asynchronous copies (cp.async, 16 bytes each, no registers held while they are in flight) into
+// one half while the other half's unit is counted, so two units are in flight per warp (the next
+// pass's words while the current pass is counted, for short chromosomes).  Each lane reads back
+// only the bytes it copied, so the hardware's own per-thread wait is the only synchronisation.
 constexpr uint32_t kStageBytes = 12 * 1024;
 template <bool NEG>
 __host__ __device__ constexpr int stage_pairs() {
@@ -263,6 +265,17 @@ __device__ __forceinline__ void cp_async16(uint32_t *dst, const uint32_t *src) {
 // Waits for all of this thread's asynchronous copies (a bounded hardware wait).
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
+
+// Closes this thread's current group of asynchronous copies.
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Waits until at most N of this thread's committed copy groups are pending (a hardware wait).
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // Adds four pair words per direction to the bit-sliced counters.
@@ -333,81 +346,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
     const int64_t p0 = (int64_t)seg * a.seg_passes;
     const int64_t p1 = min(p0 + a.seg_passes, passes_total);
     int cp = 0, cn = 0, ca = 0;
-    for (int64_t pass = p0; pass < p1; ++pass) {
-      const int64_t w = pass * kPassWords + lane * 4;
-      const bool act = w < Wst;  // (Wst is a multiple of 4: a lane's 4 words all exist or not)
-      const uint32_t *G = a.bitmap + w;
-      uint4 ap = ones, an = ones;
-      Cnt6 P[4], N[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        cnt_zero(P[j]);
-        cnt_zero(N[j]);
-      }
-      if (STAGE) {
-        for (int k0 = 0; k0 < np; k0 += NB) {
-          const int nb = min(NB, np - k0);
-          if (act)
-            for (int j = 0; j < nb; ++j) {
-              cp_async16(sp + j * kPassWords, G + s_pos[warp][k0 + j]);
-              if (NEG) cp_async16(sn + j * kPassWords, G + s_neg[warp][k0 + j]);
-            }
-          cp_async_wait_all();
-          if (exact) {
-            for (int j = 0; j < nb; ++j) {
-              ap = and4(ap, lds<NS>(act, sp + j * kPassWords, ones));
-              if (NEG) an = and4(an, lds<NS>(act, sn + j * kPassWords, ones));
-            }
-          } else {
-            for (int h = 0; h < nb; h += 4) {  // (the last group padded with zeros)
-              uint4 v[4], u[4];
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                const bool in = act && h + j < nb;
-                v[j] = lds<NS>(in, sp + (h + j) * kPassWords, zero4);
-                u[j] = NEG ? lds<NS>(in, sn + (h + j) * kPassWords, zero4) : zero4;
-              }
-              cnt_add_group<NEG>(P, N, v, u);
-            }
-          }
-        }
-      } else if (exact) {
-        // The pair words of a round are loaded together, the last round padded with the
-        // operation's identity, so np pairs cost ceil(np / 8) dependent load rounds.
-        for (int k = 0; k < np; k += 8) {
-          uint4 v[8], u[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const bool in = k + j < np;
-            v[j] = ldb<NS>(act && in, G + (in ? s_pos[warp][k + j] : 0), ones);
-            if (NEG) u[j] = ldb<NS>(act && in, G + (in ? s_neg[warp][k + j] : 0), ones);
-          }
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            ap = and4(ap, v[j]);
-            if (NEG) an = and4(an, u[j]);
-          }
-        }
-      } else {
-        constexpr int RC = NEG ? 4 : 8;  // pairs per round (the counters of both directions
-                                         // and 8 pairs' words exceed the register budget)
-        for (int k = 0; k < np; k += RC) {
-          uint4 v[RC], u[RC];
-#pragma unroll
-          for (int j = 0; j < RC; ++j) {
-            const bool in = k + j < np;
-            v[j] = ldb<NS>(act && in, G + (in ? s_pos[warp][k + j] : 0), zero4);
-            if (NEG) u[j] = ldb<NS>(act && in, G + (in ? s_neg[warp][k + j] : 0), zero4);
-          }
-#pragma unroll
-          for (int h = 0; h < RC; h += 4) {
-            const uint4 vv[4] = {v[h], v[h + 1], v[h + 2], v[h + 3]};
-            const uint4 uu[4] = {NEG ? u[h] : zero4, NEG ? u[h + 1] : zero4,
-                                 NEG ? u[h + 2] : zero4, NEG ? u[h + 3] : zero4};
-            cnt_add_group<NEG>(P, N, vv, uu);
-          }
-        }
-      }
+    // The counts of one pass's 4 words per lane, added to cp / cn / ca.
+    auto finish_pass = [&](int64_t w, bool act, uint4 ap, uint4 an, Cnt6 (&P)[4],
+                           Cnt6 (&N)[4]) {
       uint4 pos, neg = zero4;
       if (exact) {
         pos = act ? ap : zero4;
@@ -430,6 +371,123 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
         ca += popc4(make_uint4(pos.x | neg.x, pos.y | neg.y, pos.z | neg.z, pos.w | neg.w));
       } else {
         ca += popc4(pos);
+      }
+    };
+    if (STAGE) {
+      // Units of (pass, batch of up to H pairs per direction), staged two at a time: the copies
+      // of the next unit are in flight while the current unit is counted, across pass
+      // boundaries too (so short chromosomes, one unit per pass, still keep two passes' words
+      // in flight per warp).
+      constexpr int H = NB / 2;
+      const int nbat = (np + H - 1) / H;
+      const int n_units = (int)(p1 - p0) * nbat;
+      auto issue = [&](int u) {
+        const int64_t pass = p0 + u / nbat;
+        const int k0 = (u % nbat) * H, nb = min(H, np - k0);
+        const int64_t w = pass * kPassWords + lane * 4;
+        if (w < Wst) {
+          const uint32_t *G = a.bitmap + w;
+          uint32_t *bp = sp + (u & 1) * H * kPassWords, *bn = sn + (u & 1) * H * kPassWords;
+          for (int j = 0; j < nb; ++j) {
+            cp_async16(bp + j * kPassWords, G + s_pos[warp][k0 + j]);
+            if (NEG) cp_async16(bn + j * kPassWords, G + s_neg[warp][k0 + j]);
+          }
+        }
+        cp_async_commit();
+      };
+      uint4 ap = ones, an = ones;
+      Cnt6 P[4], N[4];
+      if (n_units > 0) issue(0);
+      for (int u = 0; u < n_units; ++u) {
+        if (u + 1 < n_units) {
+          issue(u + 1);
+          cp_async_wait<1>();
+        } else {
+          cp_async_wait<0>();
+        }
+        const int64_t pass = p0 + u / nbat;
+        const int k0 = (u % nbat) * H, nb = min(H, np - k0);
+        const int64_t w = pass * kPassWords + lane * 4;
+        const bool act = w < Wst;  // (Wst is a multiple of 4: a lane's 4 words all exist or not)
+        const uint32_t *bp = sp + (u & 1) * H * kPassWords, *bn = sn + (u & 1) * H * kPassWords;
+        if (k0 == 0) {
+          ap = ones;
+          an = ones;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            cnt_zero(P[j]);
+            cnt_zero(N[j]);
+          }
+        }
+        if (exact) {
+          for (int j = 0; j < nb; ++j) {
+            ap = and4(ap, lds<NS>(act, bp + j * kPassWords, ones));
+            if (NEG) an = and4(an, lds<NS>(act, bn + j * kPassWords, ones));
+          }
+        } else {
+          for (int h = 0; h < nb; h += 4) {  // (the last group padded with zeros)
+            uint4 v[4], uu[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const bool in = act && h + j < nb;
+              v[j] = lds<NS>(in, bp + (h + j) * kPassWords, zero4);
+              uu[j] = NEG ? lds<NS>(in, bn + (h + j) * kPassWords, zero4) : zero4;
+            }
+            cnt_add_group<NEG>(P, N, v, uu);
+          }
+        }
+        if (k0 + nb == np) finish_pass(w, act, ap, an, P, N);
+      }
+    } else {
+      for (int64_t pass = p0; pass < p1; ++pass) {
+        const int64_t w = pass * kPassWords + lane * 4;
+        const bool act = w < Wst;  // (Wst is a multiple of 4: a lane's 4 words all exist or not)
+        const uint32_t *G = a.bitmap + w;
+        uint4 ap = ones, an = ones;
+        Cnt6 P[4], N[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          cnt_zero(P[j]);
+          cnt_zero(N[j]);
+        }
+        if (exact) {
+          // The pair words of a round are loaded together, the last round padded with the
+          // operation's identity, so np pairs cost ceil(np / 8) dependent load rounds.
+          for (int k = 0; k < np; k += 8) {
+            uint4 v[8], u[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const bool in = k + j < np;
+              v[j] = ldb<NS>(act && in, G + (in ? s_pos[warp][k + j] : 0), ones);
+              if (NEG) u[j] = ldb<NS>(act && in, G + (in ? s_neg[warp][k + j] : 0), ones);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              ap = and4(ap, v[j]);
+              if (NEG) an = and4(an, u[j]);
+            }
+          }
+        } else {
+          constexpr int RC = NEG ? 4 : 8;  // pairs per round (the counters of both directions
+                                           // and 8 pairs' words exceed the register budget)
+          for (int k = 0; k < np; k += RC) {
+            uint4 v[RC], u[RC];
+#pragma unroll
+            for (int j = 0; j < RC; ++j) {
+              const bool in = k + j < np;
+              v[j] = ldb<NS>(act && in, G + (in ? s_pos[warp][k + j] : 0), zero4);
+              if (NEG) u[j] = ldb<NS>(act && in, G + (in ? s_neg[warp][k + j] : 0), zero4);
+            }
+#pragma unroll
+            for (int h = 0; h < RC; h += 4) {
+              const uint4 vv[4] = {v[h], v[h + 1], v[h + 2], v[h + 3]};
+              const uint4 uu[4] = {NEG ? u[h] : zero4, NEG ? u[h + 1] : zero4,
+                                   NEG ? u[h + 2] : zero4, NEG ? u[h + 3] : zero4};
+              cnt_add_group<NEG>(P, N, vv, uu);
+            }
+          }
+        }
+        finish_pass(w, act, ap, an, P, N);
       }
     }
     items::insert_finish(pv, ins, m.h, i);
