@@ -43,16 +43,20 @@ __device__ __forceinline__ void wait_prior_grid() {
 // ------------------------------------------------------------------------------- rank codes
 
 // One warp ranks one row at a time.  Its C keys (padded with 0xFFFFFFFF, above every key of a
-// finite value, to N = 32 * EPL) are sorted ascending in registers by a bitonic network, with
-// sorted position e = lane * EPL + j in register j of `lane`: compare-exchanges at distance
-// s < EPL stay inside a lane, those at s >= EPL pair lane with lane ^ (s / EPL) through one
-// shuffle.  The sorted row goes to shared memory, and the rank of each key is the number of
-// sorted keys below it, found by a branchless binary search (equal keys get equal codes, as
-// the definition requires).  A block owns 32 consecutive rows: its codes are gathered in a
-// shared [C][32] tile and written column by column (coalesced), and so are the bit planes of
-// the codes: plane p of column c, word w has bit j = bit p of code(32 w + j, c), the operand of
-// the pair-bitmap build (matrix.cu).
-constexpr int kRankRows = 32;  // rows per block tile
+// finite value, to N = 32 * EPL) are sorted ascending in registers, sorted position
+// e = lane * EPL + j in register j of `lane`, by a bitonic network in the form whose every
+// compare-exchange sends the minimum to the lower position: each merge phase of size k starts by
+// comparing e with its mirror e ^ (k - 1) in the k-block, then halves the distance.  Exchanges
+// at distance < EPL stay inside a lane; the others pair lanes through one shuffle.  The sorted
+// row goes to shared memory and the rank of each key is the number of sorted keys below it,
+// found by a branchless binary search (equal keys get equal codes, as the definition requires).
+// A block owns 16 consecutive rows: their keys are staged column by column with coalesced loads
+// in a shared [C][17] tile, each row's codes replace its keys in the tile, and the tile is
+// written out column by column (codes [C][S]) together with the codes' bit planes: plane p of
+// column c, word w has bit j = bit p of code(32 w + j, c), the operand of the pair-bitmap build
+// (matrix.cu); a block fills one half of each word.
+constexpr int kRankRows = 16;                 // rows per block tile
+constexpr int kTileStride = kRankRows + 1;    // tile entries per column (bank spread)
 
 template <int EPL>
 __device__ __forceinline__ void bitonic_sort_row(uint32_t (&v)[EPL], int lane) {
@@ -60,51 +64,74 @@ __device__ __forceinline__ void bitonic_sort_row(uint32_t (&v)[EPL], int lane) {
   constexpr int LOG_N = LOG_EPL + 5;
 #pragma unroll
   for (int lk = 1; lk <= LOG_N; ++lk) {
-    const int k = 1 << lk;  // size of the bitonic sequences merged in this phase
+    const int k = 1 << lk;  // size of the blocks merged in this phase
+    if (k <= EPL) {         // mirror exchange inside the lane
 #pragma unroll
-    for (int ls = lk - 1; ls >= 0; --ls) {
-      const int st = 1 << ls;  // compare-exchange distance
+      for (int j = 0; j < EPL; ++j) {
+        const int jp = j ^ (k - 1);
+        if ((j & (k >> 1)) == 0) {
+          const uint32_t lo = min(v[j], v[jp]), hi = max(v[j], v[jp]);
+          v[j] = lo;
+          v[jp] = hi;
+        }
+      }
+    } else {  // mirror exchange with lane ^ (k / EPL - 1), register EPL - 1 - j
+      const int m = k / EPL - 1;
+      const bool upper = (lane & (k / (2 * EPL))) != 0;
+#pragma unroll
+      for (int j = 0; j < EPL / 2 + (EPL == 1); ++j) {
+        const int jm = EPL - 1 - j;
+        const uint32_t oa = __shfl_xor_sync(kFull, v[jm], m);
+        const uint32_t ob = __shfl_xor_sync(kFull, v[j], m);
+        v[j] = upper ? max(v[j], oa) : min(v[j], oa);
+        if (jm != j) v[jm] = upper ? max(v[jm], ob) : min(v[jm], ob);
+      }
+    }
+#pragma unroll
+    for (int ls = lk - 2; ls >= 0; --ls) {
+      const int st = 1 << ls;  // half-cleaner distance
       if (st < EPL) {
-        // position e = lane * EPL + j descends in this phase when (e & k) != 0
-        const bool lane_desc = k >= EPL && ((lane * EPL) & k) != 0;
 #pragma unroll
         for (int j = 0; j < EPL; ++j) {
-          const int jp = j ^ st;
-          if (jp > j) {
-            const bool desc = k < EPL ? (j & k) != 0 : lane_desc;
+          if ((j & st) == 0) {
+            const int jp = j ^ st;
             const uint32_t lo = min(v[j], v[jp]), hi = max(v[j], v[jp]);
-            v[j] = desc ? hi : lo;
-            v[jp] = desc ? lo : hi;
+            v[j] = lo;
+            v[jp] = hi;
           }
         }
       } else {
-        const int ld = st / EPL;  // lane distance of the partner
-        const bool take_max = ((lane & ld) != 0) != ((lane & (k / EPL)) != 0);
+        const int ld = st / EPL;
+        const bool upper = (lane & ld) != 0;
 #pragma unroll
         for (int j = 0; j < EPL; ++j) {
           const uint32_t o = __shfl_xor_sync(kFull, v[j], ld);
-          v[j] = take_max ? max(v[j], o) : min(v[j], o);
+          v[j] = upper ? max(v[j], o) : min(v[j], o);
         }
       }
     }
   }
 }
 
-// Index of sorted position e in a warp's shared buffer (one pad word per 32: the stores of
-// position lane * EPL + j from every lane fall in distinct banks).
+// Sorted position e sits at e + e / 32 in a warp's shared buffer (one pad word per 32: the
+// stores of positions lane * EPL + j from every lane fall in distinct banks).
 __device__ __forceinline__ int sorted_slot(int e) { return e + (e >> 5); }
 
-// #{sorted keys < q} over N sorted keys (N a power of two).
+// #{sorted keys < q} over N sorted keys (N a power of two), walking the padded positions: from a
+// multiple of 32 a step s >= 32 tests element pos + s - 1 at padded offset s + s/32 - 2 and
+// moves by s + s/32; smaller steps stay inside one 32-block.
 template <int N>
 __device__ __forceinline__ int count_below(const uint32_t *srt, uint32_t q) {
-  int pos = 0;
+  const uint32_t *p = srt;
 #pragma unroll
   for (int step = N / 2; step >= 1; step >>= 1) {
-    const int i = pos + step - 1;
-    if (srt[sorted_slot(i)] < q) pos += step;
+    const int d = step >= 32 ? step + step / 32 : step;
+    const int t = step >= 32 ? d - 2 : d - 1;
+    if (p[t] < q) p += d;
   }
-  if (srt[sorted_slot(pos)] < q) ++pos;
-  return pos;
+  if (*p < q) ++p;
+  const int pp = (int)(p - srt);
+  return pp - pp / 33;
 }
 
 // T: code type (uint8_t for C <= 128, uint16_t for C <= 1,024); EPL: keys per lane
@@ -114,23 +141,26 @@ __global__ void __launch_bounds__(kThreads, 2)
     k_rank_codes(const uint32_t *__restrict__ keys, int64_t R_pad, int32_t C, int64_t S,
                  T *__restrict__ codes, uint32_t *__restrict__ planes, int64_t Wst, int nb) {
   constexpr int N = 32 * EPL;
-  constexpr int kSorted = N + N / 32;              // words of one warp's sorted buffer
-  constexpr int CT = sizeof(T) == 1 ? 36 : 34;     // tile entries per column (bank spread)
+  constexpr int kSorted = N + N / 32;  // words of one warp's sorted buffer
   extern __shared__ __align__(16) uint32_t s_rank[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *srt = s_rank + warp * kSorted;
-  T *tile = reinterpret_cast<T *>(s_rank + kWarps * kSorted);  // [C][CT]
+  uint32_t *tile = s_rank + kWarps * kSorted;  // [C][kTileStride]: keys, then codes in place
+  uint16_t *planes16 = reinterpret_cast<uint16_t *>(planes);
   const int64_t n_tiles = R_pad / kRankRows;
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const int64_t r0 = t * kRankRows;
+    for (int i = threadIdx.x; i < C * kRankRows; i += kThreads) {
+      const int c = i / kRankRows, rho = i % kRankRows;
+      tile[c * kTileStride + rho] = __ldg(keys + (int64_t)c * R_pad + r0 + rho);
+    }
+    __syncthreads();
     for (int rho = warp; rho < kRankRows; rho += kWarps) {
-      const int64_t r = r0 + rho;
-      uint32_t q[EPL], v[EPL];
+      uint32_t v[EPL];
 #pragma unroll
       for (int j = 0; j < EPL; ++j) {
         const int c = j * 32 + lane;  // (any placement of the keys before sorting will do)
-        q[j] = c < C ? __ldg(keys + (int64_t)c * R_pad + r) : 0xFFFFFFFFu;
-        v[j] = q[j];
+        v[j] = c < C ? tile[c * kTileStride + rho] : 0xFFFFFFFFu;
       }
       bitonic_sort_row<EPL>(v, lane);
       __syncwarp();  // the previous row's searches are done with the buffer
@@ -139,22 +169,29 @@ __global__ void __launch_bounds__(kThreads, 2)
       __syncwarp();
 #pragma unroll
       for (int j = 0; j < EPL; ++j) {
-        const int c = j * 32 + lane;
-        if (c < C) tile[c * CT + rho] = (T)count_below<N>(srt, q[j]);
+        const int c = j * 32 + lane;  // (this row's slot of column c: only this warp's)
+        if (c < C) tile[c * kTileStride + rho] = (uint32_t)count_below<N>(srt, tile[c * kTileStride + rho]);
       }
     }
     __syncthreads();
-    const int64_t w = r0 / 32;
-    for (int c = warp; c < C; c += kWarps) {
-      const uint32_t code = tile[c * CT + lane];
-      codes[(int64_t)c * S + r0 + lane] = (T)code;
-      if (planes) {
+    for (int i = threadIdx.x; i < C * kRankRows; i += kThreads) {
+      const int c = i / kRankRows, rho = i % kRankRows;
+      codes[(int64_t)c * S + r0 + rho] = (T)tile[c * kTileStride + rho];
+    }
+    if (planes) {
+      // two columns per warp step: lanes 0-15 hold column c's 16 rows, lanes 16-31 column c + 1's
+      const int64_t w = r0 / 32, half = (r0 / kRankRows) & 1;
+      const int sub = lane >> 4;
+      for (int c2 = 2 * warp; c2 < C; c2 += 2 * kWarps) {
+        const int c = c2 + sub;
+        const uint32_t code = c < C ? tile[c * kTileStride + (lane & 15)] : 0u;
         uint32_t mine = 0;
         for (int p = 0; p < nb; ++p) {
           const uint32_t bits = __ballot_sync(kFull, (code >> p) & 1u);
-          if (lane == p) mine = bits;
+          if ((lane & 15) == p) mine = sub ? (bits >> 16) : (bits & 0xFFFFu);
         }
-        if (lane < nb) planes[((int64_t)c * nb + lane) * Wst + w] = mine;
+        const int p = lane & 15;
+        if (p < nb && c < C) planes16[2 * (((int64_t)c * nb + p) * Wst + w) + half] = (uint16_t)mine;
       }
     }
     __syncthreads();  // the tile is read before the next rows overwrite it
@@ -347,10 +384,9 @@ template <typename T, int EPL>
 cudaError_t launch_rank_epl(const uint32_t *keys, int64_t R_pad, int32_t C, T *codes, int64_t S,
                             uint32_t *planes, int64_t Wst, int nb, int num_sms, cudaStream_t s) {
   constexpr int N = 32 * EPL;
-  constexpr int CT = sizeof(T) == 1 ? 36 : 34;
-  const size_t smem = (size_t)kWarps * (N + N / 32) * 4 + (((size_t)C * CT * sizeof(T) + 15) & ~size_t(15));
+  const size_t smem = (size_t)kWarps * (N + N / 32) * 4 + (size_t)C * kTileStride * 4;
   // one fixed limit for every context (no call lowers another's), set once per device
-  constexpr size_t kLimit = (size_t)kWarps * (1024 + 32) * 4 + (size_t)1024 * 34 * 2;
+  constexpr size_t kLimit = (size_t)kWarps * (1024 + 32) * 4 + (size_t)1024 * kTileStride * 4;
   static_assert(kLimit <= 227 * 1024, "rank-code shared memory");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

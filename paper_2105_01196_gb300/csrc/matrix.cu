@@ -171,14 +171,31 @@ __global__ void __launch_bounds__(kBW * 32, 4) k_build_bitmap(const uint32_t *__
 // 32 rows' codes, so one lane compares 32 rows at once.  Going from the lowest plane to the
 // highest, with A and B the planes of columns a and b,
 //   gt = (B & ~A) | (~(A ^ B) & gt)      lt = (A & ~B) | (~(A ^ B) & lt)
-// (each a single three-input logic operation) leave gt = [code_b > code_a] = G[a][b] and
-// lt = [code_a > code_b] = G[b][a] in every bit: a higher differing bit overrides the lower
-// ones, equal bits keep them.  Ties and pad rows (code 0 everywhere) set neither.
+// (each one three-input logic instruction, lop3 with truth tables 0x8E and 0xB2) leave
+// gt = [code_b > code_a] = G[a][b] and lt = [code_a > code_b] = G[b][a] in every bit: a higher
+// differing bit overrides the lower ones, equal bits keep them.  Ties and pad rows (code 0
+// everywhere) set neither.
 // A warp owns four a-columns (their planes in registers) and one 32-word chunk of rows (a word
-// per lane, so every store is one coalesced 128-byte row piece), and walks b over the columns
-// after its own; the b planes of a block's eight warps come through L1.  Block id
-// = a-block * (chunks) + chunk, so the blocks with the most b columns start first.
-constexpr int kPA = 4;  // a-columns per warp
+// per lane, so every store is one coalesced 128-byte row piece), and walks b over a piece of at
+// most kPiece columns after its own; the b planes of a block's eight warps come through L1.
+// The b-range of an a-block is cut into pieces so that every block has about the same work
+// (the first a-blocks pair with many more columns than the last ones).  The row chunk is the
+// fastest block index, so the blocks resident together write adjacent 128-byte pieces of the
+// same pair rows, which L2 then merges into whole sectors before they reach DRAM.
+constexpr int kPA = 4;       // a-columns per warp
+constexpr int kPiece = 128;  // b-columns per block (at most)
+constexpr int kMaxABlocks = 32;  // a-blocks of 32 columns: C <= 1,024
+
+struct PieceTable {
+  int32_t base[kMaxABlocks + 1];  // first piece of each a-block (prefix sums)
+};
+
+template <int LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+  return d;
+}
 
 template <int NB>
 __device__ __forceinline__ void plane_compare(const uint32_t (&A)[NB], const uint32_t (&B)[NB],
@@ -187,22 +204,31 @@ __device__ __forceinline__ void plane_compare(const uint32_t (&A)[NB], const uin
   lt = 0u;
 #pragma unroll
   for (int p = 0; p < NB; ++p) {
-    gt = (B[p] & ~A[p]) | (~(A[p] ^ B[p]) & gt);
-    lt = (A[p] & ~B[p]) | (~(A[p] ^ B[p]) & lt);
+    gt = lop3<0x8E>(A[p], B[p], gt);  // (B & ~A) | (~(A ^ B) & gt)
+    lt = lop3<0xB2>(A[p], B[p], lt);  // (A & ~B) | (~(A ^ B) & lt)
   }
 }
 
 template <int NB>
 __global__ void __launch_bounds__(256) k_build_bitmap_planes(const uint32_t *__restrict__ planes,
                                                              int32_t C, int64_t Wst,
-                                                             int32_t n_chunks,
+                                                             PieceTable tab,
                                                              uint32_t *__restrict__ G) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ablk = blockIdx.x / n_chunks, chunk = blockIdx.x - ablk * n_chunks;
-  const int64_t w = (int64_t)chunk * 32 + lane;
+  // this block's a-block (the last one whose first piece is at or before blockIdx.x) and piece
+  const int x = (int)blockIdx.y;  // (blockIdx.x is the row chunk: the blocks running together
+                                  // write neighbouring pieces of the same pair rows)
+  int ablk = 0;
+#pragma unroll
+  for (int step = kMaxABlocks / 2; step >= 1; step >>= 1)
+    if (ablk + step < kMaxABlocks && tab.base[ablk + step] <= x) ablk += step;
+  const int piece = x - tab.base[ablk];
+  const int64_t w = (int64_t)blockIdx.x * 32 + lane;
   const bool w_ok = w < Wst;
   const int a0 = (ablk * 8 + warp) * kPA;
-  if (a0 >= C) return;  // (the whole warp)
+  const int b_lo = ablk * 8 * kPA + piece * kPiece;           // the piece's b-range
+  const int b_hi = min(C, b_lo + kPiece);
+  if (a0 >= C || (piece > 0 && a0 + kPA >= b_hi)) return;  // (the whole warp: nothing to do)
   uint32_t A[kPA][NB];
 #pragma unroll
   for (int i = 0; i < kPA; ++i)
@@ -211,35 +237,40 @@ __global__ void __launch_bounds__(256) k_build_bitmap_planes(const uint32_t *__r
       A[i][p] = (a0 + i < C && w_ok) ? __ldg(planes + ((int64_t)(a0 + i) * NB + p) * Wst + w) : 0u;
   if (!w_ok) return;  // (no warp-wide operation follows)
   const int64_t row = (int64_t)C * Wst;  // words between G[a][.] and G[a + 1][.]
-  // the diagonal words, and the pairs among the warp's own columns
+  if (piece == 0) {
+    // the diagonal words, and the pairs among the warp's own columns
 #pragma unroll
-  for (int i = 0; i < kPA; ++i) {
-    const int a = a0 + i;
-    if (a >= C) break;
-    G[(int64_t)a * row + (int64_t)a * Wst + w] = 0u;
+    for (int i = 0; i < kPA; ++i) {
+      const int a = a0 + i;
+      if (a >= C) break;
+      G[(int64_t)a * row + (int64_t)a * Wst + w] = 0u;
 #pragma unroll
-    for (int i2 = i + 1; i2 < kPA; ++i2) {
-      const int b = a0 + i2;
-      if (b < C) {
-        uint32_t gt, lt;
-        plane_compare<NB>(A[i], A[i2], gt, lt);
-        __stcs(G + (int64_t)a * row + (int64_t)b * Wst + w, gt);
-        __stcs(G + (int64_t)b * row + (int64_t)a * Wst + w, lt);
+      for (int i2 = i + 1; i2 < kPA; ++i2) {
+        const int b = a0 + i2;
+        if (b < C) {
+          uint32_t gt, lt;
+          plane_compare<NB>(A[i], A[i2], gt, lt);
+          __stcs(G + (int64_t)a * row + (int64_t)b * Wst + w, gt);
+          __stcs(G + (int64_t)b * row + (int64_t)a * Wst + w, lt);
+        }
       }
     }
   }
-  // every later column b: G[a][b] at a * row + b * Wst, G[b][a] at b * row + a * Wst
-  const int b0 = a0 + kPA;
-  if (b0 >= C) return;
-  uint32_t *g_ab = G + (int64_t)a0 * row + (int64_t)b0 * Wst + w;  // a = a0; + i * row for a0 + i
-  uint32_t *g_ba = G + (int64_t)b0 * row + (int64_t)a0 * Wst + w;  // a = a0; + i * Wst
+  if (a0 + kPA >= b_hi) return;
+  // columns b of the piece after the warp's own: G[a][b] at a * row + b * Wst, G[b][a] at
+  // b * row + a * Wst
+  // (a + i)'s words sit i rows (or i * Wst words) past a's: 32-bit offsets from two pointers
+  const int b0 = max(a0 + kPA, b_lo);
+  uint32_t *g_ab = G + (int64_t)a0 * row + (int64_t)b0 * Wst + w;
+  uint32_t *g_ba = G + (int64_t)b0 * row + (int64_t)a0 * Wst + w;
+  const uint32_t row32 = (uint32_t)row, wst32 = (uint32_t)Wst;  // (checked at launch)
   const uint32_t *pb = planes + (int64_t)b0 * NB * Wst + w;
   uint32_t B[NB];
 #pragma unroll
   for (int p = 0; p < NB; ++p) B[p] = __ldg(pb + (int64_t)p * Wst);
-  for (int b = b0; b < C; ++b) {
+  for (int b = b0; b < b_hi; ++b) {
     uint32_t Bn[NB];
-    const bool more = b + 1 < C;
+    const bool more = b + 1 < b_hi;
     pb += (int64_t)NB * Wst;
 #pragma unroll
     for (int p = 0; p < NB; ++p) Bn[p] = more ? __ldg(pb + (int64_t)p * Wst) : 0u;
@@ -247,8 +278,8 @@ __global__ void __launch_bounds__(256) k_build_bitmap_planes(const uint32_t *__r
     for (int i = 0; i < kPA; ++i) {
       uint32_t gt, lt;
       plane_compare<NB>(A[i], B, gt, lt);
-      __stcs(g_ab + (int64_t)i * row, gt);
-      __stcs(g_ba + (int64_t)i * Wst, lt);
+      __stcs(g_ab + (uint32_t)i * row32, gt);
+      __stcs(g_ba + (uint32_t)i * wst32, lt);
     }
     g_ab += Wst;
     g_ba += row;
@@ -293,21 +324,29 @@ cudaError_t launch_build_bitmap(const uint32_t *keys, int64_t R_pad, int32_t C, 
 
 cudaError_t launch_build_bitmap_planes(const uint32_t *planes, int nb, int32_t C, int64_t Wst,
                                        uint32_t *bitmap, cudaStream_t s) {
-  const int64_t n_chunks = (Wst + 31) / 32, n_ablk = (C + 8 * kPA - 1) / (8 * kPA);
-  if (n_chunks * n_ablk > 0x7FFFFFFF) return cudaErrorInvalidValue;
-  const dim3 grid((unsigned)(n_chunks * n_ablk)), block(256);
-  const int32_t nc = (int32_t)n_chunks;
+  const int64_t n_chunks = (Wst + 31) / 32;
+  const int n_ablk = (C + 8 * kPA - 1) / (8 * kPA);
+  // (the kernel offsets rows of the bitmap by up to 3 * C * Wst words in 32 bits)
+  if (n_ablk > kMaxABlocks || n_chunks > 0x7FFFFFFF || 4 * (int64_t)C * Wst > 0xFFFFFFFFll)
+    return cudaErrorInvalidValue;
+  PieceTable tab{};
+  int total = 0;
+  for (int g = 0; g <= kMaxABlocks; ++g) {
+    tab.base[g] = total;
+    if (g < n_ablk) total += (C - g * 8 * kPA + kPiece - 1) / kPiece;  // b in [32 g, C)
+  }
+  const dim3 grid((unsigned)n_chunks, (unsigned)total), block(256);  // (total <= 32 * 8 pieces)
   switch (nb) {
-    case 1: k_build_bitmap_planes<1><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
-    case 2: k_build_bitmap_planes<2><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
-    case 3: k_build_bitmap_planes<3><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
-    case 4: k_build_bitmap_planes<4><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
-    case 5: k_build_bitmap_planes<5><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
-    case 6: k_build_bitmap_planes<6><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
-    case 7: k_build_bitmap_planes<7><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
-    case 8: k_build_bitmap_planes<8><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
-    case 9: k_build_bitmap_planes<9><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
-    case 10: k_build_bitmap_planes<10><<<grid, block, 0, s>>>(planes, C, Wst, nc, bitmap); break;
+    case 1: k_build_bitmap_planes<1><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
+    case 2: k_build_bitmap_planes<2><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
+    case 3: k_build_bitmap_planes<3><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
+    case 4: k_build_bitmap_planes<4><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
+    case 5: k_build_bitmap_planes<5><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
+    case 6: k_build_bitmap_planes<6><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
+    case 7: k_build_bitmap_planes<7><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
+    case 8: k_build_bitmap_planes<8><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
+    case 9: k_build_bitmap_planes<9><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
+    case 10: k_build_bitmap_planes<10><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
