@@ -293,9 +293,14 @@ EBIC_API int ebic_profile_read(ebic_ctx *ctx, int32_t kernel, ebic_kernel_stats 
  * device) in the direct form (several work-item sizes), the staged direct form (when its tiles
  * fit) and, when the pair bitmap fits in half of the free device memory, the bitmap form
  * (building it; several work-item sizes).  It then records for the
- * loaded matrix the form and sizes minimising build + expected_sweeps * sweep time;
- * EBIC_MODE_AUTO follows them in ebic_eval_population and ebic_run_generations until another
- * matrix is loaded.  Results never depend on the choice.  *rep (may be NULL) receives the
+ * loaded matrix the form and sizes minimising build + expected_sweeps * sweep time.  With
+ * expected_sweeps > 2 and p valid for ebic_run_generations (the staged form excepted), it also
+ * times 16 generations of a scratch run per work-item size of the chosen form (graph-replayed,
+ * after a warm-up run) and records the fastest for the generation loop; the run state is reset
+ * afterwards, so the caller's next run starts from its initial population;
+ * EBIC_MODE_AUTO follows them in ebic_eval_population and ebic_run_generations until a matrix
+ * of another shape is loaded (the measured times depend on the shape, not on the values, so a
+ * reload of the same shape keeps them).  Results never depend on the choice.  *rep (may be NULL) receives the
  * measurements.  Errors: EBIC_ESTATE (no matrix), EBIC_EINVAL (bad population or parameter,
  * n_ind < 1, expected_sweeps < 1), EBIC_ENOMEM, EBIC_ECUDA.
  */
@@ -303,7 +308,7 @@ typedef struct ebic_tune_report {
   int32_t mode;       /* chosen form: EBIC_MODE_DIRECT, EBIC_MODE_STAGED or EBIC_MODE_BITMAP */
   int32_t seg_direct; /* chosen work-item size of the direct form, passes of 128 rows (0 = default split) */
   int32_t seg_bitmap; /* the same for the bitmap form, passes of 128 words                  */
-  int32_t reserved;
+  int32_t seg_loop;   /* the same for the generation loop's evaluations in the chosen form   */
   double direct_ms;   /* best measured sweep of the direct form                               */
   double bitmap_ms;   /* best measured sweep of the bitmap form (-1 when not measured)        */
   double build_ms;    /* measured bitmap build (0 when the bitmap already existed)            */

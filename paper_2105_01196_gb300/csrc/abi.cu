@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 
 #include "internal.h"
@@ -29,6 +30,43 @@ struct DeviceGuard {
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 }  // namespace
+
+// Up to this many freed bytes stay cached in the library pool of a device (beyond it, memory
+// goes back to the device at the next synchronisation).
+constexpr uint64_t kPoolKeepBytes = 8ull << 30;
+constexpr int kPoolDevices = 64;
+
+cudaMemPool_t library_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[kPoolDevices] = {};
+  static bool tried[kPoolDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kPoolDevices) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!tried[dev]) {
+    tried[dev] = true;
+    int supported = 0;
+    if (cudaDeviceGetAttribute(&supported, cudaDevAttrMemoryPoolsSupported, dev) == cudaSuccess &&
+        supported) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.handleTypes = cudaMemHandleTypeNone;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaMemPool_t pool = nullptr;
+      if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+        uint64_t keep = kPoolKeepBytes;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = pool;
+      }
+    }
+    cudaGetLastError();
+  }
+  return pools[dev];
+}
 
 int ebic_fail(ebic_ctx *ctx, int code, const std::string &msg) {
   if (ctx) ctx->err = msg;
@@ -193,8 +231,8 @@ int stage_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *offse
     }
     total = (int64_t)offsets[n_ind] - base;
     mean_len = (double)total / n_ind;
-    EBIC_CHECK_CUDA(ctx, ctx->ev_cols.ensure((size_t)(offsets[n_ind]) * 4 + 16));
-    EBIC_CHECK_CUDA(ctx, ctx->ev_off.ensure((size_t)(n_ind + 1) * 4));
+    EBIC_CHECK_CUDA(ctx, ctx->ev_cols.ensure((size_t)(offsets[n_ind]) * 4 + 16, ctx->stream));
+    EBIC_CHECK_CUDA(ctx, ctx->ev_off.ensure((size_t)(n_ind + 1) * 4, ctx->stream));
     EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(ctx->ev_cols.p, col_idx, (size_t)offsets[n_ind] * 4,
                                          cudaMemcpyHostToDevice, s));
     EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(ctx->ev_off.p, offsets, (size_t)(n_ind + 1) * 4,
@@ -320,8 +358,9 @@ int ebic_create(ebic_ctx **out, int32_t device, void *cuda_stream) {
     }
     ctx->own_stream = true;
   }
-  if (ctx->d_err.ensure(64) != cudaSuccess || ctx->d_work.ensure(64) != cudaSuccess ||
-      ctx->d_kerr.ensure(64) != cudaSuccess ||
+  if (ctx->d_err.ensure(64, ctx->stream) != cudaSuccess ||
+      ctx->d_work.ensure(64, ctx->stream) != cudaSuccess ||
+      ctx->d_kerr.ensure(64, ctx->stream) != cudaSuccess ||
       cudaMemset(ctx->d_kerr.p, 0, 64) != cudaSuccess) {
     ebic_destroy(ctx);
     return EBIC_ENOMEM;
@@ -339,7 +378,7 @@ int ebic_destroy(ebic_ctx *ctx) {
   ctx->gen = nullptr;
   DevBuf *bufs[] = {&ctx->keys, &ctx->bitmap, &ctx->stage_x, &ctx->d_err, &ctx->d_work,
                     &ctx->ev_cols, &ctx->ev_off, &ctx->ev_out, &ctx->ev_fit, &ctx->d_kerr,
-                    &ctx->codes};
+                    &ctx->codes, &ctx->planes};
   for (DevBuf *b : bufs) b->release();
   prof_collect(ctx);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -366,9 +405,11 @@ int ebic_load_matrix(ebic_ctx *ctx, const float *x, int64_t rows, int32_t cols, 
     return ebic_fail(ctx, EBIC_EINVAL, "rows must be < 2^31 - 128");
   DeviceGuard g(ctx->device);
   EBIC_TRY(check_device_ptr(ctx, x, "x"));
+  // (the autotuner's measurements depend on the matrix's shape only, not on its values: a
+  // matrix of the same shape keeps its decisions)
+  if (rows != ctx->R || cols != ctx->C) ctx->tuned = false;
   ctx->have_matrix = false;
   ctx->bitmap_ok = false;
-  ctx->tuned = false;
   // A matrix of the same shape keeps the generation loop's buffers and captured graphs (their
   // device addresses and sizes stay valid); the run state is cleared before the next run.
   if (ctx->gen && rows == ctx->R && cols == ctx->C) {
@@ -378,10 +419,10 @@ int ebic_load_matrix(ebic_ctx *ctx, const float *x, int64_t rows, int32_t cols, 
     ctx->gen = nullptr;
   }
   const int64_t R_pad = round_up(rows, 128);
-  EBIC_CHECK_CUDA(ctx, ctx->keys.ensure((size_t)cols * R_pad * sizeof(uint32_t)));
+  EBIC_CHECK_CUDA(ctx, ctx->keys.ensure((size_t)cols * R_pad * sizeof(uint32_t), ctx->stream));
   const float *src = x;
   if (!ebic_is_device_ptr(x)) {
-    EBIC_CHECK_CUDA(ctx, ctx->stage_x.ensure((size_t)rows * cols * sizeof(float)));
+    EBIC_CHECK_CUDA(ctx, ctx->stage_x.ensure((size_t)rows * cols * sizeof(float), ctx->stream));
     EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(ctx->stage_x.p, x, (size_t)rows * cols * sizeof(float),
                                          cudaMemcpyHostToDevice, ctx->stream));
     src = ctx->stage_x.as<float>();
@@ -415,7 +456,7 @@ int ebic_build_bitmap(ebic_ctx *ctx) {
   if (ctx->bitmap_ok) return EBIC_OK;
   DeviceGuard g(ctx->device);
   const size_t bytes = (size_t)ebic_bitmap_bytes(ctx->R, ctx->C);
-  EBIC_CHECK_CUDA(ctx, ctx->bitmap.ensure(bytes));
+  EBIC_CHECK_CUDA(ctx, ctx->bitmap.ensure(bytes, ctx->stream));
   EBIC_CHECK_CUDA(ctx, prepare_bitmap_eval());
   // With rank codes (C <= 1,024) the words come from the codes' bit planes, else from the keys.
   if (ctx->code_bytes) EBIC_TRY(ensure_codes(ctx));
@@ -478,8 +519,8 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
   if (mode == EBIC_MODE_BITMAP && !ctx->bitmap_ok) EBIC_TRY(ebic_build_bitmap(ctx));
   if (direct_form_used(ctx, mode, p)) EBIC_TRY(ensure_codes(ctx));
 
-  EBIC_CHECK_CUDA(ctx, ctx->ev_out.ensure((size_t)n_ind * 3 * sizeof(int32_t)));
-  EBIC_CHECK_CUDA(ctx, ctx->ev_fit.ensure((size_t)n_ind * sizeof(uint64_t)));
+  EBIC_CHECK_CUDA(ctx, ctx->ev_out.ensure((size_t)n_ind * 3 * sizeof(int32_t), ctx->stream));
+  EBIC_CHECK_CUDA(ctx, ctx->ev_fit.ensure((size_t)n_ind * sizeof(uint64_t), ctx->stream));
   EvalArgs a = eval_args_for(ctx);
   a.neg = p->neg_trends;
   a.non_strict = p->non_strict;
@@ -546,8 +587,8 @@ int ensure_codes(ebic_ctx *ctx) {
   if (!ctx->code_bytes || ctx->codes_ready) return EBIC_OK;
   const int64_t S = ctx->code_stride, C = ctx->C;
   ctx->plane_bits = code_plane_bits(ctx->C);
-  EBIC_CHECK_CUDA(ctx, ctx->codes.ensure((size_t)C * S * ctx->code_bytes));
-  EBIC_CHECK_CUDA(ctx, ctx->planes.ensure((size_t)C * ctx->plane_bits * ctx->Wst * 4));
+  EBIC_CHECK_CUDA(ctx, ctx->codes.ensure((size_t)C * S * ctx->code_bytes, ctx->stream));
+  EBIC_CHECK_CUDA(ctx, ctx->planes.ensure((size_t)C * ctx->plane_bits * ctx->Wst * 4, ctx->stream));
   cudaEvent_t ev = prof_begin(ctx);
   EBIC_CHECK_CUDA(ctx, launch_rank_codes(ctx->keys.as<uint32_t>(), ctx->R_pad, ctx->C,
                                          ctx->codes.p, ctx->code_bytes, S,

@@ -1252,6 +1252,10 @@ void gen_mark_reset(GenState *g) {
   g->reset_pending = true;
 }
 
+void gen_drop_graphs(GenState *g) {
+  if (g) g->drop_graphs();
+}
+
 namespace {
 
 bool same_run_params(const ebic_params &a, const ebic_params &b) {
@@ -1327,10 +1331,8 @@ EvalArgs gen_eval_args(ebic_ctx *ctx, GenState *g, int k, bool has_prev) {
   a.rows_any = a.rows_neg + g->P;
   a.fitness = nullptr;
   a.work = g->work.as<int32_t>();
-  a.seg_passes = ctx->tuned ? (g->eval_mode == EBIC_MODE_BITMAP
-                                    ? ctx->seg_bitmap
-                                    : (g->eval_mode == EBIC_MODE_DIRECT ? ctx->seg_direct : 0))
-                             : 0;
+  // (the autotuner's loop size was measured in the loop, with the form it chose)
+  a.seg_passes = ctx->tuned && g->eval_mode == ctx->tuned_mode ? ctx->seg_loop : 0;
   return a;
 }
 
@@ -1473,7 +1475,13 @@ int check_run_params(ebic_ctx *ctx, const ebic_params *p) {
   return EBIC_OK;
 }
 
-#define GEN_ALLOC(buf, bytes) EBIC_CHECK_CUDA(ctx, (buf).ensure(bytes))
+}  // namespace
+
+int ebic_check_loop_params(ebic_ctx *ctx, const ebic_params *p) { return check_run_params(ctx, p); }
+
+namespace {
+
+#define GEN_ALLOC(buf, bytes) EBIC_CHECK_CUDA(ctx, (buf).ensure(bytes, ctx->stream))
 
 // Clears the run state of g (population, duplicate tables, tabu list, top list, column usage,
 // counters) on the context stream; buffers and graphs stay.
@@ -1576,7 +1584,7 @@ int ensure_tabu(ebic_ctx *ctx, GenState *g, int64_t need) {
   if (want > (1ull << 31)) return ebic_fail(ctx, EBIC_ENOMEM, "tabu list beyond 2^31 slots");
   if (g->tcap >= want) return EBIC_OK;
   DevBuf fresh;
-  EBIC_CHECK_CUDA(ctx, fresh.ensure(want * 8));
+  EBIC_CHECK_CUDA(ctx, fresh.ensure(want * 8, ctx->stream));
   EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(fresh.p, 0, want * 8, ctx->stream));
   if (g->tcap) {
     k_rehash<<<(g->tcap + 255) / 256, 256, 0, ctx->stream>>>(g->tabu.as<uint64_t>(), g->tcap,
@@ -1857,7 +1865,7 @@ int ebic_extract_biclusters(ebic_ctx *ctx, int32_t capacity, uint32_t *rowmask, 
   const bool dev = ebic_is_device_ptr(rowmask);
   uint32_t *dst = rowmask;
   if (!dev) {
-    EBIC_CHECK_CUDA(ctx, g->extract.ensure(words * 4 + 4));
+    EBIC_CHECK_CUDA(ctx, g->extract.ensure(words * 4 + 4, ctx->stream));
     dst = g->extract.as<uint32_t>();
   }
   if (words) {
@@ -1997,7 +2005,7 @@ int ebic_load_state(ebic_ctx *ctx, const ebic_params *p, const void *blob, int64
   EBIC_TRY(ensure_tabu(ctx, g, h.n_tabu + (int64_t)g->P));
   if (h.n_tabu > 0) {
     DevBuf list;
-    EBIC_CHECK_CUDA(ctx, list.ensure((size_t)h.n_tabu * 8));
+    EBIC_CHECK_CUDA(ctx, list.ensure((size_t)h.n_tabu * 8, ctx->stream));
     EBIC_CHECK_CUDA(ctx, cudaMemcpy(list.p, o, (size_t)h.n_tabu * 8, cudaMemcpyHostToDevice));
     k_tabu_load<<<(unsigned)((h.n_tabu + 255) / 256), 256, 0, ctx->stream>>>(
         list.as<uint64_t>(), h.n_tabu, g->tabu.as<uint64_t>(), g->tcap - 1);

@@ -22,16 +22,38 @@
     if (s_ != EBIC_OK) return s_; \
   } while (0)
 
-// Growable device allocation owned by a context.
+// The library's device-memory pool of the current device (created on first use; freed memory
+// stays cached in it up to a threshold, for the next allocation of any context), or null when
+// the device has no memory-pool support.
+cudaMemPool_t library_pool();
+
+// Growable device allocation owned by a context.  Memory comes from the library pool in stream
+// order on the owning context's stream: freeing waits only for that stream's earlier work (no
+// device-wide synchronisation, so one context ending does not stall the others), and a new
+// allocation is followed by one synchronisation of that stream so that host-side copies may use
+// it at once.  Without pool support, plain cudaMalloc / cudaFree.
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
-  cudaError_t ensure(size_t n) {
+  cudaStream_t s = nullptr;  // the stream the memory was allocated on (pool memory)
+  bool pooled = false;
+  cudaError_t ensure(size_t n, cudaStream_t stream) {
     if (n <= bytes && p) return cudaSuccess;
     release();
     if (n == 0) n = 16;
-    cudaError_t e = cudaMalloc(&p, n);
+    cudaMemPool_t pool = library_pool();
+    cudaError_t e;
+    if (pool) {
+      e = cudaMallocFromPoolAsync(&p, n, pool, stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+      pooled = true;
+      s = stream;
+    } else {
+      e = cudaMalloc(&p, n);
+      pooled = false;
+    }
     if (e != cudaSuccess) {
+      if (p && pooled) cudaFreeAsync(p, stream);
       p = nullptr;
       cudaGetLastError();
       return e;
@@ -40,7 +62,12 @@ struct DevBuf {
     return cudaSuccess;
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      if (pooled)
+        cudaFreeAsync(p, s);
+      else
+        cudaFree(p);
+    }
     p = nullptr;
     bytes = 0;
   }
@@ -175,6 +202,7 @@ struct ebic_ctx {
   bool tuned = false;
   int tuned_mode = EBIC_MODE_DIRECT;
   int seg_direct = 0, seg_bitmap = 0;  // work-item sizes in passes; 0 = the built-in split
+  int seg_loop = 0;                    // the same for the generation loop's evaluations
 
   // generation loop state (evolve.cu)
   struct GenState *gen = nullptr;
@@ -294,3 +322,7 @@ inline uint64_t dedup_capacity(int64_t P) { return pow2_at_least((uint64_t)(kTab
 void gen_state_free(struct GenState *g);
 // Ends the current run: the state is cleared before the next run, buffers and graphs stay.
 void gen_mark_reset(struct GenState *g);
+// Drops the captured generation graphs (they hold launch arguments that changed).
+void gen_drop_graphs(struct GenState *g);
+// The generation loop's parameter check (evolve.cu).
+int ebic_check_loop_params(ebic_ctx *ctx, const ebic_params *p);

@@ -4,7 +4,9 @@
 // work-item size (passes of 128 rows or 128 words per item) that minimise the expected time of
 // `expected_sweeps` evaluations, the bitmap build included when the bitmap does not exist yet.
 // EBIC_MODE_AUTO then follows the recorded choice, both in ebic_eval_population and in the
-// generation loop, until another matrix is loaded.
+// generation loop, until a matrix of another shape is loaded.  When a run of generations is
+// expected, the loop's own work-item size is measured in a scratch run of the loop (selection
+// soon makes its population shorter than the one given here).
 #include <float.h>
 
 #include <algorithm>
@@ -47,6 +49,63 @@ int time_eval(ebic_ctx *ctx, int mode, EvalArgs a, const PopView &pv, int seg, d
   return status;
 }
 
+const int kLoopSegCandidates[] = {0, 1, 2, 4, 8, 16};  // 0 = the built-in split
+const int kLoopGens = 16;
+
+// The generation loop's work-item size: for each candidate, a warm-up run (initial population
+// and `gens` generations, which also captures the graphs), then the same run again with its
+// generations timed by CUDA events on the context stream.  The run state is reset afterwards:
+// the caller's next run starts from its own initial population.
+int tune_loop(ebic_ctx *ctx, const ebic_params *p, int gens, int *best_out) {
+  cudaEvent_t e0, e1;
+  EBIC_CHECK_CUDA(ctx, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return ebic_fail(ctx, EBIC_ECUDA, "cudaEventCreate failed");
+  }
+  ebic_params q = *p;
+  q.mode = EBIC_MODE_AUTO;  // (the form just chosen)
+  q.use_graph = 1;
+  const int64_t passes = eval_passes(ctx, ctx->tuned_mode);
+  double best = DBL_MAX;
+  int best_seg = 0, status = EBIC_OK;
+  ebic_run_report rep;
+  for (int seg : kLoopSegCandidates) {
+    if (seg > passes) break;
+    ctx->seg_loop = seg;
+    float ms = 0.f;
+    for (int pass = 0; pass < 2 && status == EBIC_OK; ++pass) {
+      if (ctx->gen) {
+        // (the captured launches hold the work-item size: captured again in the first pass)
+        if (pass == 0) gen_drop_graphs(ctx->gen);
+        gen_mark_reset(ctx->gen);
+      }
+      status = ebic_run_generations(ctx, &q, 0, &rep);
+      if (status != EBIC_OK) break;
+      cudaError_t e = cudaEventRecord(e0, ctx->stream);
+      if (e == cudaSuccess) status = ebic_run_generations(ctx, &q, gens, &rep);
+      if (status != EBIC_OK) break;
+      if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) status = ebic_fail_cuda(ctx, e, "loop tuning", __FILE__, __LINE__);
+    }
+    if (status != EBIC_OK) break;
+    if (ms < best) {
+      best = ms;
+      best_seg = seg;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ctx->gen) {
+    gen_drop_graphs(ctx->gen);
+    gen_mark_reset(ctx->gen);
+  }
+  *best_out = best_seg;
+  return status;
+}
+
 }  // namespace
 
 extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *offsets,
@@ -69,8 +128,8 @@ extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_
   } restore{prev};
   StagedPop sp;
   EBIC_TRY(stage_population(ctx, col_idx, offsets, n_ind, false, &sp));
-  EBIC_CHECK_CUDA(ctx, ctx->ev_out.ensure((size_t)n_ind * 3 * sizeof(int32_t)));
-  EBIC_CHECK_CUDA(ctx, ctx->ev_fit.ensure((size_t)n_ind * sizeof(uint64_t)));
+  EBIC_CHECK_CUDA(ctx, ctx->ev_out.ensure((size_t)n_ind * 3 * sizeof(int32_t), ctx->stream));
+  EBIC_CHECK_CUDA(ctx, ctx->ev_fit.ensure((size_t)n_ind * sizeof(uint64_t), ctx->stream));
   EBIC_TRY(ensure_codes(ctx));  // the direct form is always measured
   EvalArgs a = eval_args_for(ctx);
   a.bitmap = nullptr;
@@ -158,10 +217,20 @@ extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_
   ctx->tuned_mode = cost_bitmap < cost_direct ? EBIC_MODE_BITMAP : direct_mode;
   ctx->seg_direct = seg_direct;
   ctx->seg_bitmap = seg_bitmap;
+  ctx->seg_loop = 0;
+  // A run of generations expected: the loop's population soon differs from this one (selection
+  // shortens it), so its work-item size is measured in the loop itself.
+  if (expected_sweeps > 2 && ctx->tuned_mode != EBIC_MODE_STAGED &&
+      ebic_check_loop_params(ctx, p) == EBIC_OK) {
+    int best_seg = 0;
+    EBIC_TRY(tune_loop(ctx, p, std::min(expected_sweeps - 1, kLoopGens), &best_seg));
+    ctx->seg_loop = best_seg;
+  }
   if (rep) {
     r.mode = ctx->tuned_mode;
     r.seg_direct = seg_direct;
     r.seg_bitmap = seg_bitmap;
+    r.seg_loop = ctx->seg_loop;
     r.direct_ms = best_direct;
     r.staged_ms = best_staged == DBL_MAX ? -1.0 : best_staged;
     r.bitmap_ms = best_bitmap == DBL_MAX ? -1.0 : best_bitmap;

@@ -315,7 +315,7 @@ def ebic_profile_read(ctx, kernel):
 
 class TuneReport(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("seg_direct", ctypes.c_int32),
-                ("seg_bitmap", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("seg_bitmap", ctypes.c_int32), ("seg_loop", ctypes.c_int32),
                 ("direct_ms", ctypes.c_double), ("bitmap_ms", ctypes.c_double),
                 ("build_ms", ctypes.c_double), ("staged_ms", ctypes.c_double)]
 

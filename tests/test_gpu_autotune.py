@@ -25,6 +25,9 @@ def test_autotune_then_auto_matches_oracle(sweeps):
         assert rep["mode"] in (ebic.MODE_DIRECT, ebic.MODE_BITMAP, ebic.MODE_STAGED)
         assert rep["direct_ms"] > 0 and rep["seg_direct"] >= 0 and rep["seg_bitmap"] >= 0
         assert rep["staged_ms"] > 0                  # 100 columns: the staged tiles fit
+        # the loop's work-item size is measured when a run is expected (and p is a valid run)
+        assert rep["seg_loop"] in (0, 1, 2, 4, 8, 16)
+        assert sweeps > 2 or rep["seg_loop"] == 0
         got = ctx.eval_population(ci, off, p)
     want = ocounts.eval_population(x, ci, off, op)
     for g_, w_ in zip(got, want):
@@ -40,9 +43,16 @@ def test_autotuned_generations_match_oracle():
     op = OParams(**base)
     with ebic.Context(0) as ctx:
         ctx.load_matrix(x)
-        ctx.autotune(ci, off, gp, 20)
+        tune = ctx.autotune(ci, off, gp, 20)        # (its scratch runs of the loop are reset)
         rep = ctx.run_generations(gp, 20)
         top = ctx.toplist()
+        pop = ctx.population(gp.pop_size)
+        ctx.load_matrix(x)                          # a same-shape reload keeps the decisions
+        rep2 = ctx.run_generations(gp, 20)
+        assert ctx.toplist() == top
     st = oebic.run(x, op, 20)
-    assert rep.gens_done == st.gen
+    assert tune["seg_loop"] in (0, 1, 2, 4, 8, 16)
+    assert rep.gens_done == rep2.gens_done == st.gen
+    assert rep.n_evaluated == rep2.n_evaluated == st.n_evaluated
     assert [(e["cols"], e["f"]) for e in top] == [(tuple(e.cols), e.f) for e in st.top]
+    assert [list(c[:n]) for c, n in zip(pop[0], pop[1])] == [list(c) for c in st.pop]
