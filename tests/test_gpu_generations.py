@@ -239,3 +239,59 @@ def test_large_population_multi_block_finish(ebic):
         assert rep.gens_done == st.gen == 4
         assert rep.n_evaluated == st.n_evaluated
         assert_same_state(ctx, st, gp)
+
+
+def long_matrix(seed, ties):
+    """700 x 128 with three planted trend biclusters of 40-64 columns, continuous values or, with
+    ties, values rounded to integers and every third row constant."""
+    x, _ = synth.planted_matrix(700, 128, 3, (80, 150), (40, 64), seed=seed, neg_fraction=0.34)
+    if ties:
+        x = np.round(x).astype(np.float32)
+        x[::3] = 1.0
+    return x
+
+
+@pytest.mark.parametrize("mode,use_graph,ns,ratio,cap,init_lo", [
+    (2, 1, 0, (1, 3), 16, 40), (1, 1, 0, (1, 3), 16, 2), (2, 0, 0, (1, 2), 16, 40),
+    (1, 0, 1, (1, 2), 16, 40), (2, 1, 1, (1, 2), 16, 2), (4, 1, 0, (1, 3), 16, 40),
+    (0, 1, 0, (1, 2), 16, 2), (1, 1, 0, (1, 1), 10, 40)])
+def test_long_chromosomes_generation_by_generation(ebic, mode, use_graph, ns, ratio, cap,
+                                                   init_lo):
+    """Chromosomes of up to 64 columns (the warp's second 32 lanes: copies, mutation shifts,
+    crossover suffixes past lane 32, the duplicate and penalty sums over 64 columns, top-list
+    entries of more than 32 columns) on a 128-column matrix: initial lengths 40-64 or 2-64;
+    bitmap, direct, staged and AUTO forms; graph-replayed and eager loops; strict and
+    ties-for-both pair tests.  Low ratios with the column exponent capped at 16 make long
+    chromosomes score best, so the population stays above 32 columns; the exact ratio lets it
+    shrink after the first generations.  Ten generations one by one, then eight in one call
+    (one graph replay), each against the oracle."""
+    x = long_matrix(31 + init_lo + ns, ties=bool(ns))
+    gp, op = both_params(ebic, mode=mode, use_graph=use_graph, non_strict=ns,
+                         ratio_num=ratio[0], ratio_den=ratio[1], col_cap=cap, max_len=64,
+                         init_min_len=init_lo, init_max_len=64, pop_size=96, elite=6,
+                         n_biclusters=6, seed=41 + mode)
+    longest = []
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        rep = ctx.run_generations(gp, 0)
+        st = oebic.initialise(x, op)
+        assert rep.n_evaluated == st.n_evaluated
+        assert_same_state(ctx, st, gp)
+        for g in range(1, 11):
+            rep = ctx.run_generations(gp, 1)
+            assert oebic.next_generation(x, st, op)
+            assert rep.gens_done == g == st.gen
+            assert rep.last_hits == st.hits[-1]
+            assert rep.n_evaluated == st.n_evaluated
+            assert_same_state(ctx, st, gp)
+            longest.append(max(len(c) for c in st.pop))
+        rep = ctx.run_generations(gp, 8)
+        for _ in range(8):
+            assert oebic.next_generation(x, st, op)
+        assert rep.gens_done == st.gen == 18
+        assert rep.n_evaluated == st.n_evaluated
+        assert_same_state(ctx, st, gp)
+    assert longest[0] > 32
+    if ratio != (1, 1):
+        assert min(longest) > 32
+        assert ns or any(len(e.cols) > 32 for e in st.top)
