@@ -1,15 +1,22 @@
 """EBIC population-evaluation benchmark on GB300.
 
 One step = one pass of the whole hot path over one synthetic workload, through the C ABI:
-  matrix upload (order keys) -> pair-bitmap build (when the autotuner picks the bitmap form)
-  -> full evaluation of the workload's population -> the EBIC generation loop (initial
-  population + `--gens` generations, graph-replayed) -> bicluster extraction of the top list.
-The metric is (individual, row) trend evaluations per second over the step; generations per
-second are reported beside it.  Default workload: 10,000 x 100 float32, population 800, lengths
-2-20, approximate ratio 0.85, negative trends, 100 generations.
+  matrix upload (order keys) -> rank codes and pair bitmap (when AUTO, as tuned, picks the
+  bitmap form) -> full evaluation of the workload's population -> the EBIC generation loop
+  (initial population + `--gens` generations, graph-replayed) -> bicluster extraction of the top
+  list.  The metric is (individual, row) trend evaluations per second over the step; generations
+  per second are reported beside it.  Default workload (the largest single-GPU one): tie-heavy,
+  60,000 x 1,000 log-normal values rounded to 0.1 with 20 planted biclusters, population 8,192,
+  lengths 2-64, approximate ratio 0.85, negative trends, 100 generations.  The autotuner runs
+  once before the warm-up steps.  Extra keys, measured after the timed region: the exact trend on
+  the same workload, the plain one-launch-per-individual form and the kernel-by-kernel loop
+  against the production forms (with identical results checked), the default and batched
+  workloads, the serving stream, and the CPU oracle on the host cores.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload default|tiny|batched|tieheavy] [--gens G] [--mode auto|...]
+                       [--workload tieheavy|default|batched|tiny|serving] [--gens G]
+                       [--mode auto|...] [--no-extras] [--no-serving] [--no-e2e]
+                       [--no-cpu-baseline]
 Multi-GPU (torchrun): every rank runs an independent job (its own seed) on its own GPU; the
 value is all ranks' evaluations divided by the slowest rank's time ("weak" scaling).
 """
@@ -39,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="default")
+    ap.add_argument("--workload", default="tieheavy")
     ap.add_argument("--gens", type=int, default=None, help="generations per step")
     ap.add_argument("--mode", default="auto", choices=list(MODES))
     ap.add_argument("--trend", default="strict",
@@ -48,8 +55,10 @@ def parse():
                          "comparison with the last kept value, or both")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-scale-roofline", action="store_true",
-                    help="skip the evaluation-kernel roofline on the batched workload")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra keys (exact trend, vs_plain, other workloads, serving)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving extra key")
+    ap.add_argument("--no-tune", action="store_true", help="AUTO without the autotuner")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--jobs", type=int, default=0, help="serving: number of jobs (0 = 256)")
     ap.add_argument("--max-running", type=int, default=8, help="serving: concurrent jobs")
@@ -117,53 +126,28 @@ def eval_kernel_name(mode, cols):
     return "k_eval_bitmap|k_eval_codes"
 
 
-def scale_roofline(ebic, dev, stream, peak, peak_kind, sweeps=20):
-    """The evaluation kernel on the batched workload (20,000 x 500, P 4,096, lengths 2-64, ratio
-    0.85, negative trends), where a sweep is large enough to reach its memory bound: bitmap
-    sweeps timed with CUDA events on the library stream after a warm-up sweep, outside the timed
-    region of the step.  Algorithmic bytes as in the main roofline."""
-    import torch
-    from paper_2105_01196_gb300 import synth
-    w = synth.WORKLOADS["batched"]
-    x, _, ci, off = synth.workload_inputs(w)
-    P = len(off) - 1
-    xd = torch.from_numpy(x).to(dev)
-    cid, offd = torch.from_numpy(ci).to(dev), torch.from_numpy(off).to(dev)
-    outs = [torch.zeros(P, dtype=torch.int32, device=dev) for _ in range(3)]
-    outs.append(torch.zeros(P, dtype=torch.int64, device=dev))
-    p = ebic.Params.make(neg_trends=1, ratio_num=w.ratio[0], ratio_den=w.ratio[1], mode=2)
-    with ebic.Context(dev.index or 0, stream.cuda_stream) as c:
-        c.load_matrix(xd)
-        c.build_bitmap()
-        c.eval_population(cid, offd, p, *outs)
-        c.profile_enable(True)
-        for _ in range(sweeps):
-            c.eval_population(cid, offd, p, *outs)
-        st = c.profile_read(ebic.KERNEL_EVAL)
-        c.profile_enable(False)
-    avg_s = st["ms"] / st["timed_launches"] / 1e3
-    per_launch = st["alg_bytes"] / st["timed_launches"]
-    achieved = per_launch / avg_s / 1e9
-    return {"workload": "batched", "kernel": "k_eval_bitmap", "bound": "hbm",
-            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": ncu_traffic("k_eval_bitmap", "batched"),
-            "peak_kind": peak_kind, "alg_bytes_per_launch": per_launch,
-            "avg_launch_us": avg_s * 1e6, "launches": st["timed_launches"],
-            "note": "bitmap (628 MB) larger than L2, so no flush between sweeps; algorithmic "
-                    "bytes count every pair word read, some of which individuals share"}
+def ncu_traffic_entry(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary
+    (profiles/traffic_<kernel>.txt: kernel, workload, bytes per launch, and the commit whose
+    kernel source the capture ran), and where it comes from; (None, None) when there is none."""
+    path = os.path.join(ROOT, "profiles", "traffic_" + kernel + ".txt")
+    if not os.path.exists(path):
+        return None, None
+    with open(path) as fh:
+        for line in fh:
+            parts = line.split()
+            if line.startswith("#") or len(parts) < 3 or parts[:2] != [kernel, workload]:
+                continue
+            src = f"profiles/traffic_{kernel}.txt ({workload}"
+            src += f", ncu capture of the kernel source at commit {parts[3]})" if len(parts) > 3 \
+                else ")"
+            return float(parts[2]), src
+    return None, None
 
 
 def ncu_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary, or None."""
-    path = os.path.join(ROOT, "profiles", "traffic_" + kernel + ".txt")
-    if not os.path.exists(path):
-        return None
-    with open(path) as fh:
-        for line in fh:
-            parts = line.split()
-            if len(parts) == 3 and not line.startswith("#") and parts[:2] == [kernel, workload]:
-                return float(parts[2])
-    return None
+    return ncu_traffic_entry(kernel, workload)[0]
 
 
 def load_peaks():
@@ -393,57 +377,277 @@ def run_reference(args, w, world, rank, dist):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args, world, rank, local, dist):
-    """Serving workload: a Poisson stream of EBIC jobs through the continuous-batching server;
-    p50/p99 job latency (arrival to completion) and jobs/s, plus the saturated throughput with
-    every job queued at once."""
-    import threading
+def serving_measure(local, max_running, n_jobs=0, seed_offset=0):
+    """The serving stream through the continuous-batching job server: every job a fresh matrix
+    shape (synth.serving_stream), population 800, ratio 0.85, 50 generations.  Phase "poisson":
+    jobs submitted at their Poisson arrival times (20 jobs/s); phase "saturated": every job queued
+    at once.  Latency = arrival (submission) to completion; p50/p99 over the jobs."""
     import torch
     from paper_2105_01196_gb300 import ebic, synth
-    torch.cuda.set_device(local)
     cfg = synth.SERVING
-    n_jobs = args.jobs if args.jobs else cfg["n_jobs"]
-    jobs, mats = synth.serving_jobs(n_jobs, seed=cfg["seed"] + 7919 * rank)
+    jobs, make = synth.serving_stream(n_jobs or cfg["n_jobs"], seed=cfg["seed"] + seed_offset)
+    mats = [make(k) for k in range(len(jobs))]
 
     def params(seed):
         return ebic.Params.make(neg_trends=1, ratio_num=cfg["ratio"][0], ratio_den=cfg["ratio"][1],
                                 pop_size=cfg["pop"], max_len=20, init_min_len=2, init_max_len=20,
                                 n_biclusters=10, elite=10, tabu_hit_limit=0, seed=seed)
-    free, total = torch.cuda.mem_get_info(local)
+    free, _ = torch.cuda.mem_get_info(local)
     budget = int(0.6 * free)
-    out = {}
+    out = {"jobs": len(jobs), "rate_per_s": cfg["rate_per_s"], "rows": list(cfg["rows"]),
+           "cols": list(cfg["cols"]), "pop": cfg["pop"], "generations": cfg["generations"],
+           "shapes": "a fresh shape per job (uniform rows x cols)", "max_running": max_running,
+           "hbm_budget_bytes": budget, "latency": "submission to completion"}
     for phase in ("poisson", "saturated"):
         lat = []
         evals = 0
-        with ebic.Server(local, hbm_budget_bytes=budget, max_running=args.max_running) as srv:
+        with ebic.Server(local, hbm_budget_bytes=budget, max_running=max_running) as srv:
             t0 = time.perf_counter()
             ids = []
-            for at, m, seed in jobs:
+            for k, (at, R, C, seed) in enumerate(jobs):
                 if phase == "poisson":
                     delay = t0 + at - time.perf_counter()
                     if delay > 0:
                         time.sleep(delay)
-                ids.append((time.perf_counter(), srv.submit(mats[m], params(seed), cfg["generations"]), m))
-            for t_sub, jid, m in ids:
+                ids.append((srv.submit(mats[k], params(seed), cfg["generations"]), R))
+            for jid, R in ids:
                 r = srv.wait(jid)
-                assert r["status"] == 0, r
+                if r["status"] != 0:
+                    raise RuntimeError(f"serving job failed: {r}")
                 lat.append(r["queued_ms"] + r["run_ms"])
-                evals += r["n_evaluated"] * mats[m].shape[0]
+                evals += r["n_evaluated"] * R
             wall = time.perf_counter() - t0
         out[phase] = {"jobs_per_s": len(jobs) / wall, "p50_ms": float(np.percentile(lat, 50)),
                       "p99_ms": float(np.percentile(lat, 99)), "wall_s": wall,
                       "evals_per_s": evals / wall}
+    return out
+
+
+def run_serving(args, world, rank, local, dist):
+    """`--workload serving`: the serving stream alone, as its own JSON line."""
+    import torch
+    torch.cuda.set_device(local)
+    out = serving_measure(local, args.max_running, args.jobs, 7919 * rank)
     if rank == 0:
         line = {"metric": "EBIC jobs/sec and p50/p99 job latency (continuous batching)",
                 "value": out["saturated"]["jobs_per_s"], "unit": "jobs/s", "n_gpus": world,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32-compare/int32", "data": "synthetic",
-                "config": {"workload": "serving", "jobs": len(jobs), "rate_per_s": cfg["rate_per_s"],
-                           "rows": list(cfg["rows"]), "cols": list(cfg["cols"]), "pop": cfg["pop"],
-                           "generations": cfg["generations"], "distinct_matrices": len(mats),
-                           "max_running": args.max_running, "hbm_budget_bytes": budget},
+                "config": {"workload": "serving", **{k: v for k, v in out.items()
+                                                    if k not in ("poisson", "saturated")}},
                 "poisson": out["poisson"], "saturated": out["saturated"]}
         print(json.dumps(line), flush=True)
+
+
+class Job:
+    """One workload on one context: device inputs, pinned host copies, and one step of the hot
+    path (upload -> evaluation sweep -> initial population + generations -> extraction)."""
+
+    def __init__(self, ebic, torch, w, dev, stream, mode, trend, gens, host_copies=True):
+        self.ebic, self.torch, self.w, self.gens = ebic, torch, w, gens
+        self.x, self.truth, self.ci, self.off = synth_inputs(w)
+        self.R, self.P = w.rows, len(self.off) - 1
+        self.x_d = torch.from_numpy(self.x).to(dev)
+        self.ci_d = torch.from_numpy(self.ci).to(dev)
+        self.off_d = torch.from_numpy(self.off).to(dev)
+        self.outs_d = [torch.zeros(self.P, dtype=torch.int32, device=dev) for _ in range(3)]
+        self.outs_d.append(torch.zeros(self.P, dtype=torch.int64, device=dev))
+        if host_copies:
+            self.x_h = torch.from_numpy(self.x).pin_memory()
+            self.outs_h = [torch.zeros(self.P, dtype=torch.int32).pin_memory() for _ in range(3)]
+            self.outs_h.append(torch.zeros(self.P, dtype=torch.int64).pin_memory())
+        self.params = ebic.Params.make(mode=MODES[mode], **run_fields(w, trend))
+        self.ctx = ebic.Context(dev.index or 0, stream.cuda_stream)
+        self.used_mode = 0
+
+    def tune(self):
+        """The autotuner on this matrix and population, for the step's expected sweeps (the
+        evaluation sweep, the initial population and every generation); AUTO then follows it."""
+        self.ctx.load_matrix(self.x_d)
+        return self.ctx.autotune(self.ci_d, self.off_d, self.params, self.gens + 2)
+
+    def step(self, host=False):
+        """One pass of the hot path; returns the (individual, row) evaluations done."""
+        ctx = self.ctx
+        if host:
+            ctx.load_matrix(self.x_h)
+            ctx.eval_population(self.ci, self.off, self.params, *self.outs_h)
+        else:
+            ctx.load_matrix(self.x_d)
+            ctx.eval_population(self.ci_d, self.off_d, self.params, *self.outs_d)
+        units = self.P * self.R
+        if self.gens > 0:
+            rep = ctx.run_generations(self.params, self.gens)
+            self.used_mode = int(rep.eval_mode)
+            units += int(rep.n_evaluated) * self.R
+            units += len(ctx.extract_biclusters(self.R)) * self.R
+        return units
+
+    def params_ratio(self):
+        return self.params.ratio_num, self.params.ratio_den
+
+    def close(self):
+        self.ctx.close()
+
+
+_INPUTS = {}
+
+
+def synth_inputs(w):
+    from paper_2105_01196_gb300 import synth
+    key = (w.name, w.seed)
+    if key not in _INPUTS:
+        _INPUTS[key] = synth.workload_inputs(w)
+    return _INPUTS[key]
+
+
+def timed_steps(job, stream, flush, steps, dist=None):
+    """`steps` steps, each from a flushed L2 (the flush outside the events), CUDA events on the
+    library's stream; returns (total ms, units)."""
+    torch = job.torch
+    total_ms, units = 0.0, 0
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        units += job.step(False)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    return total_ms, units
+
+
+def kernel_stats(job, stream, flush, steps):
+    """A second pass of the same steps with CUDA events around every kernel of the path (event
+    nodes inside the generation graphs): per-kernel durations, work and shares, and the pass's
+    own time per step (the event nodes keep consecutive kernels from overlapping)."""
+    ebic, torch, ctx = job.ebic, job.torch, job.ctx
+    ctx.profile_enable(True)
+    ms, _ = timed_steps(job, stream, flush, steps)
+    stats = {name: ctx.profile_read(kid) for name, kid in
+             (("eval", ebic.KERNEL_EVAL), ("evolve", ebic.KERNEL_EVOLVE),
+              ("finish", ebic.KERNEL_FINISH), ("bitmap_build", ebic.KERNEL_BITMAP_BUILD),
+              ("rank_codes", ebic.KERNEL_RANK_CODES))}
+    ctx.profile_enable(False)
+    tot = sum(v["ms"] for v in stats.values())
+    for v in stats.values():
+        v["avg_us"] = 1e3 * v["ms"] / v["timed_launches"] if v["timed_launches"] else None
+        v["share_of_kernel_time"] = v["ms"] / tot if tot else None
+    return stats, {"instrumented_ms_per_step": ms / steps, "kernel_ms_per_step": tot / steps}
+
+
+def eval_roofline(stats, kernel, peak, peak_kind, traffic, traffic_source):
+    se = stats["eval"]
+    if not (se["timed_launches"] > 0 and se["ms"] > 0):
+        return None
+    n_l = se["timed_launches"]
+    avg_s = se["ms"] / n_l / 1e3
+    per_launch = se["alg_bytes"] / n_l
+    achieved = per_launch / avg_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_source,
+            "kernel": kernel, "peak_kind": peak_kind, "alg_bytes_per_launch": per_launch,
+            "avg_launch_us": avg_s * 1e6, "launches": n_l,
+            "share_of_kernel_time": se["share_of_kernel_time"]}
+
+
+def workload_summary(job, stream, flush, steps, warmup, peak, peak_kind):
+    """A workload's step rate, generations/s and evaluation-kernel roofline (outside the headline's
+    timed region)."""
+    job.tune()
+    for _ in range(warmup):
+        job.step(False)
+    ms, units = timed_steps(job, stream, flush, steps)
+    stats, passes = kernel_stats(job, stream, flush, steps)
+    w = job.w
+    out = {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+           "steps": steps, "rows": w.rows, "cols": w.cols, "pop": w.pop,
+           "len": [w.len_lo, w.len_hi], "ratio": list(job.params_ratio()),
+           "generations": job.gens, "eval_form": eval_kernel_name(job.used_mode, w.cols),
+           "roofline": eval_roofline(stats, eval_kernel_name(job.used_mode, w.cols), peak,
+                                     peak_kind, None, None),
+           "kernel_ms_per_step": {k: v["ms"] / steps for k, v in stats.items()}, **passes}
+    if job.gens > 0:
+        out["generations_per_s"] = job.gens * steps / (ms / 1e3)
+    return out
+
+
+def vs_plain(job, stream, gens_loop=20):
+    """The target's comparison, on the headline workload: (1) one evaluation sweep of the
+    population in the paper's form (EBIC_MODE_PLAIN, one launch per individual) against the
+    production form (AUTO, as tuned), with equal counts and fitness checked; (2) the generation
+    loop launched kernel by kernel (use_graph = 0, the host reading the progress counters every
+    generation) against the graph-replayed loop, with equal top lists and populations checked."""
+    ebic, torch, ctx = job.ebic, job.torch, job.ctx
+    P = job.P
+    ctx.load_matrix(job.x_d)
+    res = {}
+    outs = {}
+    for name, mode in (("plain", MODES["plain"]), ("batched", MODES["auto"])):
+        p = ebic.Params.make(mode=mode, **run_fields(job.w))
+        o = [torch.zeros(P, dtype=torch.int32, device=job.x_d.device) for _ in range(3)]
+        o.append(torch.zeros(P, dtype=torch.int64, device=job.x_d.device))
+        ctx.eval_population(job.ci_d, job.off_d, p, *o)                # warm-up (and build)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.eval_population(job.ci_d, job.off_d, p, *o)
+        e1.record(stream)
+        e1.synchronize()
+        res[name + "_sweep_ms"] = e0.elapsed_time(e1)
+        outs[name] = [t.cpu().numpy() for t in o]
+    sweep_same = all(np.array_equal(a, b) for a, b in zip(outs["plain"], outs["batched"]))
+    loop = {}
+    for name, graph in (("eager", 0), ("graph", 1)):
+        p = ebic.Params.make(mode=MODES["auto"], use_graph=graph, **run_fields(job.w))
+        ctx.load_matrix(job.x_d)
+        ctx.run_generations(p, 0)                                       # initial population
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = ctx.run_generations(p, gens_loop)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        pop = ctx.population(P)
+        loop[name] = {"ms_per_generation": 1e3 * dt / gens_loop, "gens_done": rep.gens_done,
+                      "top": [(e["cols"], e["f"]) for e in ctx.toplist()],
+                      "pop": [np.asarray(a).tolist() for a in pop]}
+    loop_same = (loop["eager"]["top"] == loop["graph"]["top"]
+                 and loop["eager"]["pop"] == loop["graph"]["pop"]
+                 and loop["eager"]["gens_done"] == loop["graph"]["gens_done"] == gens_loop)
+    return {"sweep": {"plain_ms": res["plain_sweep_ms"], "batched_ms": res["batched_sweep_ms"],
+                      "speedup": res["plain_sweep_ms"] / res["batched_sweep_ms"],
+                      "plain_launches": P, "identical": bool(sweep_same)},
+            "loop": {"generations": gens_loop,
+                     "eager_ms_per_generation": loop["eager"]["ms_per_generation"],
+                     "graph_ms_per_generation": loop["graph"]["ms_per_generation"],
+                     "speedup": loop["eager"]["ms_per_generation"]
+                     / loop["graph"]["ms_per_generation"],
+                     "identical": bool(loop_same)},
+            "identical": bool(sweep_same and loop_same),
+            "timing": "sweep: CUDA events on the library stream; loop: host clock around the "
+                      "call, device synchronised on both sides"}
+
+
+def quality_variants(ebic, torch, dev, stream):
+    """Clustering error (Eq. 1) of a 100-generation run on the default workload (10,000 x 100,
+    P 800) under the paper's trend parameters: negative trends on or off, approximate ratio 0.85
+    or the exact trend (no reading of the method changes between them)."""
+    import dataclasses
+    from paper_2105_01196_gb300 import synth
+    w0 = synth.WORKLOADS["default"]
+    out = []
+    for neg, ratio in ((1, (85, 100)), (0, (85, 100)), (1, (1, 1)), (0, (1, 1))):
+        w = dataclasses.replace(w0, neg_trends=neg, ratio=ratio)
+        job = Job(ebic, torch, w, dev, stream, "auto", "strict", w.generations, host_copies=False)
+        job.step(False)
+        q = search_quality(job.ctx, job.truth, job.R, w.cols, w.generations)
+        out.append({"neg_trends": neg, "ratio": list(ratio), "ce_score": q["ce_score"],
+                    "best_pair_score_per_planted": q["best_pair_score_per_planted"]})
+        job.close()
+    return out
 
 
 def main():
@@ -470,76 +674,24 @@ def main():
     stream = torch.cuda.current_stream(dev)
     w = dataclasses.replace(w, seed=w.seed + 7919 * rank)
     gens = gens_of(args, w)
-    x, truth, ci, off = synth.workload_inputs(w)
-    R = w.rows
-    x_d = torch.from_numpy(x).to(dev)
-    ci_d = torch.from_numpy(ci).to(dev)
-    off_d = torch.from_numpy(off).to(dev)
-    P = len(off) - 1
-    outs_d = [torch.zeros(P, dtype=torch.int32, device=dev) for _ in range(3)]
-    outs_d.append(torch.zeros(P, dtype=torch.int64, device=dev))
-    x_h = torch.from_numpy(x).pin_memory()
-    outs_h = [torch.zeros(P, dtype=torch.int32).pin_memory() for _ in range(3)]
-    outs_h.append(torch.zeros(P, dtype=torch.int64).pin_memory())
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peak, peak_kind = load_peaks()
 
-    params = ebic.Params.make(mode=MODES[args.mode], **run_fields(w, args.trend))
-    ctx = ebic.Context(local, stream.cuda_stream)
-    used_mode = [0]                     # evaluation form the generation loop used
-
-    def step(host):
-        """One pass of the hot path; returns (individual,row) evaluations done."""
-        units = 0
-        if host:
-            ctx.load_matrix(x_h)
-            ctx.eval_population(ci, off, params, *outs_h)
-        else:
-            ctx.load_matrix(x_d)
-            ctx.eval_population(ci_d, off_d, params, *outs_d)
-        units += P * R
-        if gens > 0:
-            rep = ctx.run_generations(params, gens)
-            used_mode[0] = int(rep.eval_mode)
-            units += int(rep.n_evaluated) * R
-            masks = ctx.extract_biclusters(R)
-            units += len(masks) * R
-        return units
-
+    job = Job(ebic, torch, w, dev, stream, args.mode, args.trend, gens)
+    tune = job.tune() if args.mode == "auto" and not args.no_tune else None
     for _ in range(max(3, args.warmup)):
-        step(False)
+        job.step(False)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    ctx.profile_enable(True)            # reset the launch counters ...
-    ctx.profile_enable(False)           # ... and time this pass without per-kernel events
-    total_ms = 0.0
-    units = 0
-    for _ in range(args.steps):
-        flush.zero_()                   # L2 flush between timed steps (outside the events)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        units += step(False)
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-    torch.cuda.synchronize()
-    st_all = ctx.profile_read(ebic.KERNEL_ALL)
+    job.ctx.profile_enable(True)        # reset the launch counters ...
+    job.ctx.profile_enable(False)       # ... and time this pass without per-kernel events
+    total_ms, units = timed_steps(job, stream, flush, args.steps)
+    st_all = job.ctx.profile_read(ebic.KERNEL_ALL)
     clk = clocks.stop()
-    # Second pass over the same K steps with CUDA events around every kernel of the path
-    # (event-record nodes inside the generation graphs): per-kernel durations and work.
-    ctx.profile_enable(True)
-    for _ in range(args.steps):
-        flush.zero_()
-        step(False)
-    torch.cuda.synchronize()
-    stats = {name: ctx.profile_read(kid) for name, kid in
-             (("eval", ebic.KERNEL_EVAL), ("evolve", ebic.KERNEL_EVOLVE),
-              ("finish", ebic.KERNEL_FINISH), ("bitmap_build", ebic.KERNEL_BITMAP_BUILD),
-              ("rank_codes", ebic.KERNEL_RANK_CODES))}
-    ctx.profile_enable(False)
+    stats, passes = kernel_stats(job, stream, flush, args.steps)
     if dist:
         total_ms, units = reduce_over_ranks(dist, total_ms, units, dev)
 
@@ -547,56 +699,39 @@ def main():
     if not args.no_e2e:
         # End to end through the same C ABI with host buffers: the copies run inside the calls.
         # Each step is timed on the host clock from a flushed L2, like the device-timed steps.
-        e2e_units = 0
-        e2e_s = 0.0
+        e2e_units, e2e_s = 0, 0.0
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            e2e_units += step(True)
+            e2e_units += job.step(True)
             torch.cuda.synchronize()
             e2e_s += time.perf_counter() - t0
-        h2d = x.nbytes + ci.nbytes + off.nbytes
-        d2h = sum(o.numel() * o.element_size() for o in outs_h)
+        h2d = job.x.nbytes + job.ci.nbytes + job.off.nbytes
+        d2h = sum(o.numel() * o.element_size() for o in job.outs_h)
         if gens > 0:
-            d2h += 256 * ((R + 127) // 128) * 16
+            d2h += 256 * ((job.R + 127) // 128) * 16
         e2e = {"value": e2e_units / e2e_s * (world if dist else 1), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     if rank != 0:
+        job.close()
         if dist:
             dist.destroy_process_group()
         return
 
-    peak, peak_kind = load_peaks()
-    timed_ms = sum(v["ms"] for v in stats.values())
-    for v in stats.values():
-        v["avg_us"] = 1e3 * v["ms"] / v["timed_launches"] if v["timed_launches"] else None
-        v["share_of_kernel_time"] = v["ms"] / timed_ms if timed_ms else None
+    eval_name = eval_kernel_name(job.used_mode if job.used_mode else MODES[args.mode], w.cols)
+    traffic, traffic_source = ncu_traffic_entry(eval_name, w.name)
+    roof = eval_roofline(stats, eval_name, peak, peak_kind, traffic, traffic_source)
+    names = {"eval": eval_name, "evolve": "k_evolve", "finish": "k_finish",
+             "bitmap_build": "k_build_bitmap_planes" if w.cols <= 1024 else "k_build_bitmap",
+             "rank_codes": "k_rank_codes"}
     dominant = max(stats, key=lambda k: stats[k]["ms"])
-    kernel_names = {"eval": eval_kernel_name(used_mode[0] if used_mode[0] else MODES[args.mode],
-                                             w.cols),
-                    "evolve": "k_evolve", "finish": "k_finish", "bitmap_build": "k_build_bitmap",
-                    "rank_codes": "k_rank_codes"}
-    roof = None
-    se = stats["eval"]
-    if se["timed_launches"] > 0 and se["ms"] > 0:
-        n_l = se["timed_launches"]
-        avg_s = se["ms"] / n_l / 1e3
-        per_launch = se["alg_bytes"] / n_l
-        achieved = per_launch / avg_s / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak,
-                "traffic": ncu_traffic(kernel_names["eval"], w.name),
-                "kernel": kernel_names["eval"],
-                "peak_kind": peak_kind, "alg_bytes_per_launch": per_launch,
-                "avg_launch_us": avg_s * 1e6, "launches": n_l,
-                "share_of_kernel_time": se["share_of_kernel_time"],
-                "dominant_kernel": kernel_names[dominant]}
+    if roof is not None:
+        roof["dominant_kernel"] = names[dominant]
         if dominant != "eval":
-            roof["note"] = (f"{kernel_names[dominant]} has the largest share of kernel time; it "
-                            "moves no bulk data (a chain of dependent round trips per child or "
-                            "slot), so the roofline is the evaluation kernel's, the path's only "
+            roof["note"] = (f"{names[dominant]} has the largest share of kernel time; it moves "
+                            "no bulk data, so the roofline is the evaluation kernel's, the path's "
                             "bandwidth-bound kernel")
     line = {"metric": METRIC, "value": units / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup),
@@ -606,26 +741,52 @@ def main():
                        "len": [w.len_lo, w.len_hi], "ratio": list(w.ratio),
                        "neg_trends": w.neg_trends, "generations": gens, "mode": args.mode,
                        "trend": args.trend,
-                       "l2": "flushed between steps (512 MB write)",
+                       "l2": "flushed between steps (512 MB write); the pair bitmap (7.5 GB "
+                             "at 60,000 x 1,000) is larger than L2 too",
                        "kernel_stats": "CUDA events around every kernel, on the library's "
                                        "stream, over a second pass of the same K steps",
                        "parallelism": f"independent job per GPU x{world}"},
             "gpu_launches": int(st_all["launches"]),
             "roofline": roof,
             "kernels": stats,
+            "kernel_passes": dict(passes, timed_ms_per_step=total_ms / args.steps),
             "clocks": clk,
             "e2e": e2e}
+    if tune is not None:
+        line["config"]["autotune"] = {k: tune[k] for k in ("mode", "seg_direct", "seg_bitmap",
+                                                          "seg_loop", "direct_ms", "bitmap_ms",
+                                                          "build_ms", "staged_ms")}
     if gens > 0:
         line["generations_per_s"] = gens * args.steps / (total_ms / 1e3)
-        line["quality"] = search_quality(ctx, truth, R, w.cols, gens)
-    if not args.no_scale_roofline and w.name != "batched":
-        line["roofline_at_scale"] = scale_roofline(ebic, dev, stream, peak, peak_kind)
+        line["quality"] = search_quality(job.ctx, job.truth, job.R, w.cols, gens)
+    if not args.no_extras:
+        # (outside the headline's timed region)
+        if w.ratio != (1, 1):
+            ex = Job(ebic, torch, dataclasses.replace(w, ratio=(1, 1)), dev, stream, args.mode,
+                     args.trend, gens, host_copies=False)
+            line["exact_trend"] = workload_summary(ex, stream, flush, args.steps, 3, peak,
+                                                   peak_kind)
+            ex.close()
+        line["vs_plain"] = vs_plain(job, stream)
+        line["workloads"] = {}
+        for name in ("default", "batched"):
+            if name == w.name:
+                continue
+            wo = synth.WORKLOADS[name]
+            jo = Job(ebic, torch, wo, dev, stream, args.mode, args.trend, wo.generations,
+                     host_copies=False)
+            line["workloads"][name] = workload_summary(jo, stream, flush, args.steps, 3, peak,
+                                                       peak_kind)
+            jo.close()
+        line["quality_default_workload"] = quality_variants(ebic, torch, dev, stream)
+        if not args.no_serving:
+            line["serving"] = serving_measure(local, args.max_running, args.jobs)
     if not args.no_cpu_baseline:
-        with OraclePool(x) as pool:
-            line["cpu_baseline"] = cpu_baseline(w, x, ci, off, args.cpu_seconds, args.trend,
-                                                pool=pool, generation=gens > 0)
+        with OraclePool(job.x) as pool:
+            line["cpu_baseline"] = cpu_baseline(w, job.x, job.ci, job.off, args.cpu_seconds,
+                                                args.trend, pool=pool, generation=gens > 0)
     print(json.dumps(line), flush=True)
-    ctx.close()
+    job.close()
     if dist:
         dist.destroy_process_group()
 

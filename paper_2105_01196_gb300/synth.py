@@ -65,6 +65,38 @@ SERVING = dict(n_jobs=256, rate_per_s=20.0, rows=(1_000, 50_000), cols=(20, 500)
                pop=800, ratio=(85, 100), generations=50, seed=SEED_BASE + 4)
 
 
+def serving_stream(n_jobs=None, seed=None):
+    """Arrival times (s), shapes and run seeds of the serving stream, and a generator of each
+    job's matrix: a fresh shape per job (rows and columns uniform in the stream's ranges), its
+    N(0, 1) background a crop at a random offset of one pre-drawn 50,000 x 500 pool (drawing 256
+    fresh backgrounds of up to 25M values would take longer than the stream), with the job's own
+    3-10 planted biclusters.  Returns (jobs, make) with jobs = [(arrival_s, rows, cols, seed)]
+    and make(k) -> float32 [rows, cols] of job k."""
+    cfg = SERVING
+    n_jobs = cfg["n_jobs"] if n_jobs is None else n_jobs
+    g = rng(cfg["seed"] if seed is None else seed)
+    pool = g.standard_normal((cfg["rows"][1], cfg["cols"][1]), dtype=np.float32)
+    gaps = g.exponential(1.0 / cfg["rate_per_s"], size=n_jobs)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    jobs, spec = [], []
+    for k in range(n_jobs):
+        R = int(g.integers(cfg["rows"][0], cfg["rows"][1] + 1))
+        C = int(g.integers(cfg["cols"][0], cfg["cols"][1] + 1))
+        r_off = int(g.integers(0, cfg["rows"][1] - R + 1))
+        c_off = int(g.integers(0, cfg["cols"][1] - C + 1))
+        nb = int(g.integers(cfg["n_bic"][0], cfg["n_bic"][1] + 1))
+        jobs.append((float(arrivals[k]), R, C, int(g.integers(1 << 31))))
+        spec.append((r_off, c_off, nb, int(g.integers(1 << 31))))
+
+    def make(k):
+        _, R, C, _ = jobs[k]
+        r_off, c_off, nb, pseed = spec[k]
+        x = np.array(pool[r_off:r_off + R, c_off:c_off + C], dtype=np.float32, order="C")
+        plant(x, nb, (max(10, R // 100), max(20, R // 20)), (4, min(20, C // 2)), rng(pseed))
+        return x
+    return jobs, make
+
+
 def serving_jobs(n_jobs=None, n_matrices=16, seed=None):
     """Arrival times (s) and (matrix index, run seed) of the serving stream, and its matrices.
 
@@ -103,6 +135,16 @@ def planted_matrix(rows, cols, n_bic, bic_rows, bic_cols, seed, background="norm
         x = g.lognormal(0.0, 1.0, size=(rows, cols)).astype(np.float32)
     else:
         raise ValueError(background)
+    truth = plant(x, n_bic, bic_rows, bic_cols, g, background, neg_fraction, noise)
+    if round_to:
+        x = (np.round(x / round_to) * round_to).astype(np.float32)
+    return np.ascontiguousarray(x, dtype=np.float32), truth
+
+
+def plant(x, n_bic, bic_rows, bic_cols, g, background="normal", neg_fraction=0.5, noise=0.1):
+    """Plants n_bic trend biclusters into x in place (recipe in the module docstring); returns
+    their truth list of (row_idx, col_order, sign)."""
+    rows, cols = x.shape
     truth = []
     n_neg = int(round(n_bic * neg_fraction))
     for b in range(n_bic):
@@ -122,9 +164,7 @@ def planted_matrix(rows, cols, n_bic, bic_rows, bic_cols, seed, background="norm
         target = order if sign > 0 else order[::-1]
         x[np.ix_(ridx, target)] = vals.astype(np.float32)
         truth.append((ridx, np.asarray(order), sign))
-    if round_to:
-        x = (np.round(x / round_to) * round_to).astype(np.float32)
-    return np.ascontiguousarray(x, dtype=np.float32), truth
+    return truth
 
 
 def random_population(n_ind, cols, len_lo, len_hi, seed):
