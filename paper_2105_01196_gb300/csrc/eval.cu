@@ -221,12 +221,12 @@ __device__ __forceinline__ uint32_t valid_bits(int64_t w, int64_t R) {
 // A pass covers 128 words (4096 rows) of a column pair; lane l holds words 4l..4l+3.
 constexpr int kPassWords = 128;
 
-// Staged form: each warp has kStageBytes of shared memory, two halves of NB / 2 pairs per
-// direction.  The lanes copy the pair words of a unit (one pass, up to NB / 2 pairs) with
-// asynchronous copies (cp.async, 16 bytes each, no registers held while they are in flight) into
-// one half while the other half's unit is counted, so two units are in flight per warp (the next
-// pass's words while the current pass is counted, for short chromosomes).  Each lane reads back
-// only the bytes it copied, so the hardware's own per-thread wait is the only synchronisation.
+// Staged form: each warp has kStageBytes of shared memory, two halves of NB / 2 pair rows per
+// direction.  The lanes copy the pair words of a unit (up to NB / 2 rows: one pass of a batch of
+// pairs, or several passes of a short chromosome's pairs) with asynchronous copies (cp.async, 16
+// bytes each, no registers held while they are in flight) into one half while the other half's
+// unit is counted, so two units are in flight per warp.  Each lane reads back only the bytes it
+// copied, so the hardware's own per-thread wait is the only synchronisation.
 constexpr uint32_t kStageBytes = 12 * 1024;
 template <bool NEG>
 __host__ __device__ constexpr int stage_pairs() {
@@ -374,29 +374,78 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
       }
     };
     if (STAGE) {
-      // Units of (pass, batch of up to H pairs per direction), staged two at a time: the copies
-      // of the next unit are in flight while the current unit is counted, across pass
-      // boundaries too (so short chromosomes, one unit per pass, still keep two passes' words
-      // in flight per warp).
+      // Units staged two at a time: the copies of the next unit are in flight while the current
+      // unit is counted.  A unit holds up to H pair rows per direction: several consecutive
+      // passes of all pairs when the chromosome is short (np <= H: H / np passes per unit), else
+      // one pass of a batch of up to H pairs.  So a warp keeps about H rows per direction in
+      // flight however short its chromosome (the loop's evolved population is mostly one- and
+      // two-pair chromosomes).
       constexpr int H = NB / 2;
-      const int nbat = (np + H - 1) / H;
-      const int n_units = (int)(p1 - p0) * nbat;
+      const bool packed = np <= H;
+      const int ppu = packed ? H / np : 1;                  // passes per unit
+      const int nbat = packed ? 1 : (np + H - 1) / H;       // batches per pass
+      const int n_pass = (int)(p1 - p0);
+      const int n_units = packed ? (n_pass + ppu - 1) / ppu : n_pass * nbat;
       auto issue = [&](int u) {
-        const int64_t pass = p0 + u / nbat;
-        const int k0 = (u % nbat) * H, nb = min(H, np - k0);
-        const int64_t w = pass * kPassWords + lane * 4;
-        if (w < Wst) {
-          const uint32_t *G = a.bitmap + w;
-          uint32_t *bp = sp + (u & 1) * H * kPassWords, *bn = sn + (u & 1) * H * kPassWords;
-          for (int j = 0; j < nb; ++j) {
-            cp_async16(bp + j * kPassWords, G + s_pos[warp][k0 + j]);
-            if (NEG) cp_async16(bn + j * kPassWords, G + s_neg[warp][k0 + j]);
+        uint32_t *bp = sp + (u & 1) * H * kPassWords, *bn = sn + (u & 1) * H * kPassWords;
+        if (packed) {
+          const int64_t qa = p0 + (int64_t)u * ppu, qb = min(p1, qa + ppu);
+          for (int64_t q = qa; q < qb; ++q) {
+            const int64_t w = q * kPassWords + lane * 4;
+            if (w < Wst) {
+              const uint32_t *G = a.bitmap + w;
+              const int slot0 = (int)(q - qa) * np;
+              for (int j = 0; j < np; ++j) {
+                cp_async16(bp + (slot0 + j) * kPassWords, G + s_pos[warp][j]);
+                if (NEG) cp_async16(bn + (slot0 + j) * kPassWords, G + s_neg[warp][j]);
+              }
+            }
+          }
+        } else {
+          const int64_t pass = p0 + u / nbat;
+          const int k0 = (u % nbat) * H, nb = min(H, np - k0);
+          const int64_t w = pass * kPassWords + lane * 4;
+          if (w < Wst) {
+            const uint32_t *G = a.bitmap + w;
+            for (int j = 0; j < nb; ++j) {
+              cp_async16(bp + j * kPassWords, G + s_pos[warp][k0 + j]);
+              if (NEG) cp_async16(bn + j * kPassWords, G + s_neg[warp][k0 + j]);
+            }
           }
         }
         cp_async_commit();
       };
       uint4 ap = ones, an = ones;
       Cnt6 P[4], N[4];
+      // counts slots [s0, s0 + nb) of a half into the running pass
+      auto count = [&](const uint32_t *bp, const uint32_t *bn, int s0, int nb, bool act) {
+        if (exact) {
+          for (int j = 0; j < nb; ++j) {
+            ap = and4(ap, lds<NS>(act, bp + (s0 + j) * kPassWords, ones));
+            if (NEG) an = and4(an, lds<NS>(act, bn + (s0 + j) * kPassWords, ones));
+          }
+        } else {
+          for (int h = 0; h < nb; h += 4) {  // (the last group padded with zeros)
+            uint4 v[4], uu[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const bool in = act && h + j < nb;
+              v[j] = lds<NS>(in, bp + (s0 + h + j) * kPassWords, zero4);
+              uu[j] = NEG ? lds<NS>(in, bn + (s0 + h + j) * kPassWords, zero4) : zero4;
+            }
+            cnt_add_group<NEG>(P, N, v, uu);
+          }
+        }
+      };
+      auto start_pass = [&]() {
+        ap = ones;
+        an = ones;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          cnt_zero(P[j]);
+          cnt_zero(N[j]);
+        }
+      };
       if (n_units > 0) issue(0);
       for (int u = 0; u < n_units; ++u) {
         if (u + 1 < n_units) {
@@ -405,38 +454,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
         } else {
           cp_async_wait<0>();
         }
-        const int64_t pass = p0 + u / nbat;
-        const int k0 = (u % nbat) * H, nb = min(H, np - k0);
-        const int64_t w = pass * kPassWords + lane * 4;
-        const bool act = w < Wst;  // (Wst is a multiple of 4: a lane's 4 words all exist or not)
         const uint32_t *bp = sp + (u & 1) * H * kPassWords, *bn = sn + (u & 1) * H * kPassWords;
-        if (k0 == 0) {
-          ap = ones;
-          an = ones;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            cnt_zero(P[j]);
-            cnt_zero(N[j]);
-          }
-        }
-        if (exact) {
-          for (int j = 0; j < nb; ++j) {
-            ap = and4(ap, lds<NS>(act, bp + j * kPassWords, ones));
-            if (NEG) an = and4(an, lds<NS>(act, bn + j * kPassWords, ones));
+        if (packed) {
+          const int64_t qa = p0 + (int64_t)u * ppu, qb = min(p1, qa + ppu);
+          for (int64_t q = qa; q < qb; ++q) {
+            const int64_t w = q * kPassWords + lane * 4;
+            const bool act = w < Wst;  // (Wst is a multiple of 4: a lane's 4 words all exist or not)
+            start_pass();
+            count(bp, bn, (int)(q - qa) * np, np, act);
+            finish_pass(w, act, ap, an, P, N);
           }
         } else {
-          for (int h = 0; h < nb; h += 4) {  // (the last group padded with zeros)
-            uint4 v[4], uu[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const bool in = act && h + j < nb;
-              v[j] = lds<NS>(in, bp + (h + j) * kPassWords, zero4);
-              uu[j] = NEG ? lds<NS>(in, bn + (h + j) * kPassWords, zero4) : zero4;
-            }
-            cnt_add_group<NEG>(P, N, v, uu);
-          }
+          const int64_t pass = p0 + u / nbat;
+          const int k0 = (u % nbat) * H, nb = min(H, np - k0);
+          const int64_t w = pass * kPassWords + lane * 4;
+          const bool act = w < Wst;
+          if (k0 == 0) start_pass();
+          count(bp, bn, 0, nb, act);
+          if (k0 + nb == np) finish_pass(w, act, ap, an, P, N);
         }
-        if (k0 + nb == np) finish_pass(w, act, ap, an, P, N);
       }
     } else {
       for (int64_t pass = p0; pass < p1; ++pass) {
