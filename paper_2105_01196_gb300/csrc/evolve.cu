@@ -546,6 +546,8 @@ constexpr int kEvoScratch = 0, kEvoA = 8 * kS, kEvoB = 9 * kS, kEvoChild = 10 * 
 constexpr int kEvolveWarpInts = 10 * kS + kS + 4;
 // Matrices of up to this many columns have k_evolve's column-usage table in shared memory.
 constexpr int kUsageSmemMax = 4096;
+// Warps of k_evolve one SM holds at once (its registers allow 32).
+constexpr int kEvolveResidentWarps = 32;
 
 // Dynamic shared memory of a k_evolve launch with G warps.
 size_t evolve_smem(int G, int C) {
@@ -612,6 +614,74 @@ __global__ void __launch_bounds__(kMaxAttemptWarps * 32) k_evolve(GenArgs ga, Bu
   const bool dead = win < 0;
   if (dead) win = ga.A - 1;
   if (a != win) return;
+  out[lane] = lane < L ? c[lane] : 0;
+  out[lane + 32] = lane + 32 < L ? c[lane + 32] : 0;
+  if (lane == 0) {
+    nb.len[s] = L;
+    nb.hash[s] = h;
+    nb.att_dead[s] = dead;
+    nb.att_hits[s] = dead ? ga.A : win;  // (the evaluation launch enters live keys in D[par])
+  }
+}
+
+// The same step for large populations, one warp per slot and kSeqWarps slots per block: a
+// slot's attempts run one after the other in its warp, until one misses the tabu list, which is
+// the retry rule itself (the lowest missing attempt wins; all A hit: the slot is dead with the
+// last attempt's child).  Parallel attempt warps only shorten a slot's latency; when the launch
+// has more slots than the GPU holds at once, the slots themselves fill it, and a warp per slot
+// keeps four times as many of them in flight.  The block's slots share one copy of the
+// column-usage table.
+constexpr int kSeqWarps = 8;
+
+__global__ void __launch_bounds__(kSeqWarps * 32) k_evolve_seq(GenArgs ga, Buf pb, Buf nb,
+                                                               int par) {
+  extern __shared__ __align__(16) int32_t s_evo[];  // kEvolveWarpInts per warp, then usage
+  wait_prior_grid();
+  const int stopped = ga.ctl->stopped, gen = ga.ctl->gen, n_top = ga.ctl->n_top;
+  const int32_t *usage = ga.usage;
+  if (ga.C <= kUsageSmemMax) {
+    int32_t *s_usage = s_evo + kSeqWarps * kEvolveWarpInts;
+    for (int c = threadIdx.x; c < ga.C; c += blockDim.x) s_usage[c] = ga.usage[c];
+    usage = s_usage;
+  }
+  if (stopped) return;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int s = blockIdx.x * kSeqWarps + w;
+  if (s >= ga.P) return;  // (no block-wide operation follows)
+  const int g = gen + 1;
+  const int n_el = min(ga.E, n_top);
+  int32_t *out = nb.cols + (size_t)s * kS;
+  if (s < n_el) {  // elitism: copy top-list entry s (its key is already in the tabu list)
+    const TopEntry &e = ga.top[s];
+    out[lane] = lane < e.len ? e.cols[lane] : 0;
+    out[lane + 32] = lane + 32 < e.len ? e.cols[lane + 32] : 0;
+    if (lane == 0) {
+      nb.len[s] = e.len;
+      nb.hash[s] = e.h;
+      nb.att_dead[s] = 0;
+      nb.att_hits[s] = 0;
+    }
+    return;
+  }
+  int32_t *base = s_evo + w * kEvolveWarpInts;
+  int32_t *scratch = base + kEvoScratch, *A = base + kEvoA, *B = base + kEvoB;
+  int32_t *c = base + kEvoChild;
+  int L = 0, win = -1;
+  uint64_t h = 0ull;
+  for (int a = 0; a < ga.A; ++a) {
+    w_make_child(ga, pb, g, s, a, c, scratch, A, B, L, lane, usage);
+    h = chromosome_key(c, L);
+    // lane 0 probes the hashed tabu list, lane 1 generation g-1's live keys
+    const bool hit = (lane == 0 && tabu_contains(ga.tabu, ga.tmask, h)) ||
+                     (lane == 1 && tabu_contains(ga.dkeys[par ^ 1], ga.dmask, h));
+    if (!__any_sync(kFull, hit)) {
+      win = a;
+      break;
+    }
+  }
+  const bool dead = win < 0;
+  __syncwarp();
   out[lane] = lane < L ? c[lane] : 0;
   out[lane + 32] = lane + 32 < L ? c[lane + 32] : 0;
   if (lane == 0) {
@@ -1426,10 +1496,17 @@ cudaError_t launch_generation(ebic_ctx *ctx, GenState *g, int parity, cudaStream
   while (G < g->p.max_attempts) G <<= 1;
   cudaError_t e = mark(s, m, 0);
   if (e != cudaSuccess) return e;
-  if ((e = launch_pdl(k_evolve, dim3((unsigned)g->P), dim3(G * 32), evolve_smem(G, g->C), s,
-                      gen_args(ctx, g), g->buf(parity ^ 1), g->buf(parity), parity)) !=
-      cudaSuccess)
-    return e;
+  // A block of G attempt warps per slot while every slot's block fits on the GPU at once (the
+  // slot's latency is then the launch's); beyond that a warp per slot, attempts in turn.
+  if ((int64_t)g->P * G <= (int64_t)ctx->num_sms * kEvolveResidentWarps) {
+    e = launch_pdl(k_evolve, dim3((unsigned)g->P), dim3(G * 32), evolve_smem(G, g->C), s,
+                   gen_args(ctx, g), g->buf(parity ^ 1), g->buf(parity), parity);
+  } else {
+    e = launch_pdl(k_evolve_seq, dim3((unsigned)((g->P + kSeqWarps - 1) / kSeqWarps)),
+                   dim3(kSeqWarps * 32), evolve_smem(kSeqWarps, g->C), s, gen_args(ctx, g),
+                   g->buf(parity ^ 1), g->buf(parity), parity);
+  }
+  if (e != cudaSuccess) return e;
   return launch_scoring(ctx, g, parity, true, s, m);
 }
 
@@ -1560,6 +1637,9 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
                                             (int)kFinishSmemMax));
   EBIC_CHECK_CUDA(ctx, cudaFuncSetAttribute(k_evolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)evolve_smem(kMaxAttemptWarps, kUsageSmemMax)));
+  EBIC_CHECK_CUDA(ctx, cudaFuncSetAttribute(k_evolve_seq,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)evolve_smem(kSeqWarps, kUsageSmemMax)));
 
   // one block per 2,048 slots: the slot loop spread, few blocks to meet at the end (measured:
   // one block for P = 800, 8.4 against 10.2 us with two; two for P = 4,096, 13.6 against 15.2 us)

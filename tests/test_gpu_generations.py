@@ -295,3 +295,32 @@ def test_long_chromosomes_generation_by_generation(ebic, mode, use_graph, ns, ra
     if ratio != (1, 1):
         assert min(longest) > 32
         assert ns or any(len(e.cols) > 32 for e in st.top)
+
+
+@pytest.mark.parametrize("attempts,max_len,pop", [(4, 3, 1300), (16, 3, 400), (4, 64, 1500),
+                                                  (2, 3, 1300)])
+def test_sequential_attempt_form(ebic, attempts, max_len, pop):
+    """Populations whose attempt warps exceed what the GPU holds at once (P x attempts rounded
+    to a power of two > 152 SMs x 32 warps) run one warp per slot with the attempts in turn; two
+    or three columns of a 20-column matrix make tabu hits and retries frequent, 64 columns of
+    the 128-column matrix exercise the long paths.  (2 attempts x 1,300 slots stays in the
+    one-block-per-slot form: the boundary from the other side.)  Generation by generation
+    against the oracle."""
+    x = tiny_matrix() if max_len == 3 else long_matrix(77, ties=False)
+    kw = dict(init_max_len=3) if max_len == 3 else dict(init_min_len=40, init_max_len=64,
+                                                         ratio_num=1, ratio_den=3, col_cap=16)
+    gp, op = both_params(ebic, mode=2, max_attempts=attempts, max_len=max_len, pop_size=pop,
+                         elite=6, n_biclusters=6, seed=29, **kw)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        ctx.run_generations(gp, 0)
+        st = oebic.initialise(x, op)
+        hits = 0
+        for g in range(1, 7):
+            rep = ctx.run_generations(gp, 1)
+            assert oebic.next_generation(x, st, op)
+            assert rep.gens_done == g and rep.last_hits == st.hits[-1]
+            assert rep.n_evaluated == st.n_evaluated
+            assert_same_state(ctx, st, gp)
+            hits += st.hits[-1]
+    assert max_len == 64 or hits > pop // 10
