@@ -209,13 +209,31 @@ __device__ __forceinline__ void plane_compare(const uint32_t (&A)[NB], const uin
   }
 }
 
+constexpr int kBB = 16;  // b-columns per staged batch (40 KB of static shared memory at NB = 10)
+
+__device__ __forceinline__ void cp_async16_bm(void *smem, const void *gmem) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit_bm() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_wait_bm() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// The b planes of a block's piece are staged in shared memory, kBB columns at a time and
+// double-buffered (cp.async by the whole block; the next batch is in flight while the current
+// one is compared), so the eight warps share one copy and read it with constant offsets.
 template <int NB>
-__global__ void __launch_bounds__(256) k_build_bitmap_planes(const uint32_t *__restrict__ planes,
+__global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *__restrict__ planes,
                                                              int32_t C, int64_t Wst,
                                                              PieceTable tab,
                                                              uint32_t *__restrict__ G) {
+  __shared__ __align__(16) uint32_t s_b[2][kBB][NB][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // this block's a-block (the last one whose first piece is at or before blockIdx.x) and piece
+  // this block's a-block (the last one whose first piece is at or before blockIdx.y) and piece
   const int x = (int)blockIdx.y;  // (blockIdx.x is the row chunk: the blocks running together
                                   // write neighbouring pieces of the same pair rows)
   int ablk = 0;
@@ -223,21 +241,20 @@ __global__ void __launch_bounds__(256) k_build_bitmap_planes(const uint32_t *__r
   for (int step = kMaxABlocks / 2; step >= 1; step >>= 1)
     if (ablk + step < kMaxABlocks && tab.base[ablk + step] <= x) ablk += step;
   const int piece = x - tab.base[ablk];
-  const int64_t w = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t w0 = (int64_t)blockIdx.x * 32, w = w0 + lane;
   const bool w_ok = w < Wst;
   const int a0 = (ablk * 8 + warp) * kPA;
-  const int b_lo = ablk * 8 * kPA + piece * kPiece;           // the piece's b-range
+  const int b_lo = ablk * 8 * kPA + piece * kPiece;  // the piece's b-range
   const int b_hi = min(C, b_lo + kPiece);
-  if (a0 >= C || (piece > 0 && a0 + kPA >= b_hi)) return;  // (the whole warp: nothing to do)
+  const int b_first = max(b_lo, ablk * 8 * kPA + kPA);  // the first b any warp of the block needs
   uint32_t A[kPA][NB];
 #pragma unroll
   for (int i = 0; i < kPA; ++i)
 #pragma unroll
     for (int p = 0; p < NB; ++p)
       A[i][p] = (a0 + i < C && w_ok) ? __ldg(planes + ((int64_t)(a0 + i) * NB + p) * Wst + w) : 0u;
-  if (!w_ok) return;  // (no warp-wide operation follows)
   const int64_t row = (int64_t)C * Wst;  // words between G[a][.] and G[a + 1][.]
-  if (piece == 0) {
+  if (piece == 0 && a0 < C && w_ok) {
     // the diagonal words, and the pairs among the warp's own columns
 #pragma unroll
     for (int i = 0; i < kPA; ++i) {
@@ -256,35 +273,57 @@ __global__ void __launch_bounds__(256) k_build_bitmap_planes(const uint32_t *__r
       }
     }
   }
-  if (a0 + kPA >= b_hi) return;
-  // columns b of the piece after the warp's own: G[a][b] at a * row + b * Wst, G[b][a] at
-  // b * row + a * Wst
-  // (a + i)'s words sit i rows (or i * Wst words) past a's: 32-bit offsets from two pointers
-  const int b0 = max(a0 + kPA, b_lo);
-  uint32_t *g_ab = G + (int64_t)a0 * row + (int64_t)b0 * Wst + w;
-  uint32_t *g_ba = G + (int64_t)b0 * row + (int64_t)a0 * Wst + w;
-  const uint32_t row32 = (uint32_t)row, wst32 = (uint32_t)Wst;  // (checked at launch)
-  const uint32_t *pb = planes + (int64_t)b0 * NB * Wst + w;
-  uint32_t B[NB];
-#pragma unroll
-  for (int p = 0; p < NB; ++p) B[p] = __ldg(pb + (int64_t)p * Wst);
-  for (int b = b0; b < b_hi; ++b) {
-    uint32_t Bn[NB];
-    const bool more = b + 1 < b_hi;
-    pb += (int64_t)NB * Wst;
-#pragma unroll
-    for (int p = 0; p < NB; ++p) Bn[p] = more ? __ldg(pb + (int64_t)p * Wst) : 0u;
-#pragma unroll
-    for (int i = 0; i < kPA; ++i) {
-      uint32_t gt, lt;
-      plane_compare<NB>(A[i], B, gt, lt);
-      __stcs(g_ab + (uint32_t)i * row32, gt);
-      __stcs(g_ba + (uint32_t)i * wst32, lt);
+  if (b_first >= b_hi) return;  // (the whole block: no b beyond its columns in this piece)
+  // staging: batch t holds b = b_first + t kBB + bb; copy j of a batch is (bb, p, 16-byte part)
+  const int n_batches = (b_hi - b_first + kBB - 1) / kBB;
+  const int nw4 = (int)(Wst - w0 >= 32 ? 8 : (Wst - w0) / 4);  // 16-byte parts of the chunk
+                                                                // (Wst % 4 == 0)
+  auto issue = [&](int t) {
+    const int bs = b_first + t * kBB, nbb = min(kBB, b_hi - bs);
+    for (int j = threadIdx.x; j < nbb * NB * 8; j += blockDim.x) {
+      const int part = j & 7, bp = j >> 3, bb = bp / NB, p = bp - bb * NB;
+      if (part < nw4)
+        cp_async16_bm(&s_b[t & 1][bb][p][part * 4],
+                      planes + ((int64_t)(bs + bb) * NB + p) * Wst + w0 + part * 4);
     }
-    g_ab += Wst;
-    g_ba += row;
+    cp_commit_bm();
+  };
+  // G[a][b] at a * row + b * Wst, G[b][a] at b * row + a * Wst; (a + i)'s words sit i rows (or
+  // i * Wst words) past a's: 32-bit offsets from two pointers
+  const uint32_t row32 = (uint32_t)row, wst32 = (uint32_t)Wst;  // (checked at launch)
+  const bool active = a0 < C && w_ok;
+  issue(0);
+  for (int t = 0; t < n_batches; ++t) {
+    if (t + 1 < n_batches) {
+      issue(t + 1);
+      cp_wait_bm<1>();
+    } else {
+      cp_wait_bm<0>();
+    }
+    __syncthreads();  // batch t is in shared memory for every warp
+    const int bs = b_first + t * kBB, nbb = min(kBB, b_hi - bs);
+    if (active) {
+      uint32_t *g_ab = G + (int64_t)a0 * row + (int64_t)bs * Wst + w;
+      uint32_t *g_ba = G + (int64_t)bs * row + (int64_t)a0 * Wst + w;
+#pragma unroll 1
+      for (int bb = 0; bb < nbb; ++bb) {
+        if (bs + bb >= a0 + kPA) {  // (b after the warp's own columns)
+          uint32_t B[NB];
 #pragma unroll
-    for (int p = 0; p < NB; ++p) B[p] = Bn[p];
+          for (int p = 0; p < NB; ++p) B[p] = s_b[t & 1][bb][p][lane];
+#pragma unroll
+          for (int i = 0; i < kPA; ++i) {
+            uint32_t gt, lt;
+            plane_compare<NB>(A[i], B, gt, lt);
+            __stcs(g_ab + (uint32_t)i * row32, gt);
+            __stcs(g_ba + (uint32_t)i * wst32, lt);
+          }
+        }
+        g_ab += Wst;
+        g_ba += row;
+      }
+    }
+    __syncthreads();  // every warp is done with this buffer before batch t + 2 refills it
   }
 }
 
