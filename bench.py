@@ -466,15 +466,20 @@ class Job:
         self.ctx.load_matrix(self.x_d)
         return self.ctx.autotune(self.ci_d, self.off_d, self.params, self.gens + 2)
 
-    def step(self, host=False):
-        """One pass of the hot path; returns the (individual, row) evaluations done."""
+    def step(self, host=False, around_sweep=None):
+        """One pass of the hot path; returns the (individual, row) evaluations done.
+        around_sweep(0 | 1), when given, is called right before and after the evaluation sweep."""
         ctx = self.ctx
         if host:
             ctx.load_matrix(self.x_h)
             ctx.eval_population(self.ci, self.off, self.params, *self.outs_h)
         else:
             ctx.load_matrix(self.x_d)
+            if around_sweep:
+                around_sweep(0)
             ctx.eval_population(self.ci_d, self.off_d, self.params, *self.outs_d)
+            if around_sweep:
+                around_sweep(1)
         units = self.P * self.R
         if self.gens > 0:
             rep = ctx.run_generations(self.params, self.gens)
@@ -522,24 +527,50 @@ def timed_steps(job, stream, flush, steps, dist=None):
 def kernel_stats(job, stream, flush, steps):
     """A second pass of the same steps with CUDA events around every kernel of the path (event
     nodes inside the generation graphs): per-kernel durations, work and shares, and the pass's
-    own time per step (the event nodes keep consecutive kernels from overlapping)."""
+    own time per step (the event nodes keep consecutive kernels from overlapping).  The
+    evaluation kernel's launches are also split into the step's one full sweep ("eval_sweep")
+    and the generation loop's ("eval_loop")."""
     ebic, torch, ctx = job.ebic, job.torch, job.ctx
     ctx.profile_enable(True)
-    ms, _ = timed_steps(job, stream, flush, steps)
+    sweep = {"launches": 0, "timed_launches": 0, "ms": 0.0, "alg_bytes": 0.0}
+    mark = {}
+
+    def around(k):
+        st = ctx.profile_read(ebic.KERNEL_EVAL)   # (synchronises: the sweep's events are done)
+        if k == 0:
+            mark.update(st)
+        else:
+            for key in sweep:
+                sweep[key] += st[key] - mark[key]
+    total_ms = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        job.step(False, around_sweep=around)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    ms = total_ms
     stats = {name: ctx.profile_read(kid) for name, kid in
              (("eval", ebic.KERNEL_EVAL), ("evolve", ebic.KERNEL_EVOLVE),
               ("finish", ebic.KERNEL_FINISH), ("bitmap_build", ebic.KERNEL_BITMAP_BUILD),
               ("rank_codes", ebic.KERNEL_RANK_CODES))}
     ctx.profile_enable(False)
-    tot = sum(v["ms"] for v in stats.values())
+    ev = stats["eval"]
+    stats["eval_sweep"] = dict(sweep)
+    stats["eval_loop"] = {key: ev[key] - sweep[key] for key in sweep}
+    tot = sum(v["ms"] for k, v in stats.items() if k not in ("eval_sweep", "eval_loop"))
     for v in stats.values():
         v["avg_us"] = 1e3 * v["ms"] / v["timed_launches"] if v["timed_launches"] else None
         v["share_of_kernel_time"] = v["ms"] / tot if tot else None
     return stats, {"instrumented_ms_per_step": ms / steps, "kernel_ms_per_step": tot / steps}
 
 
-def eval_roofline(stats, kernel, peak, peak_kind, traffic, traffic_source):
-    se = stats["eval"]
+def eval_roofline(stats, kernel, peak, peak_kind, traffic, traffic_source, part="eval"):
+    se = stats[part]
     if not (se["timed_launches"] > 0 and se["ms"] > 0):
         return None
     n_l = se["timed_launches"]
@@ -567,8 +598,9 @@ def workload_summary(job, stream, flush, steps, warmup, peak, peak_kind):
            "len": [w.len_lo, w.len_hi], "ratio": list(job.params_ratio()),
            "generations": job.gens, "eval_form": eval_kernel_name(job.used_mode, w.cols),
            "roofline": eval_roofline(stats, eval_kernel_name(job.used_mode, w.cols), peak,
-                                     peak_kind, None, None),
-           "kernel_ms_per_step": {k: v["ms"] / steps for k, v in stats.items()}, **passes}
+                                     peak_kind, None, None,
+                                     "eval_loop" if job.gens > 0 else "eval"),
+           "kernel_ms": {k: v["ms"] / steps for k, v in stats.items()}, **passes}
     if job.gens > 0:
         out["generations_per_s"] = job.gens * steps / (ms / 1e3)
     return out
@@ -721,12 +753,22 @@ def main():
         return
 
     eval_name = eval_kernel_name(job.used_mode if job.used_mode else MODES[args.mode], w.cols)
-    traffic, traffic_source = ncu_traffic_entry(eval_name, w.name)
-    roof = eval_roofline(stats, eval_name, peak, peak_kind, traffic, traffic_source)
-    names = {"eval": eval_name, "evolve": "k_evolve", "finish": "k_finish",
+    # the evaluation kernel in the generation loop (the step's bandwidth-bound kernel with the
+    # largest share), and its one full sweep per step beside it
+    part = "eval_loop" if gens > 0 else "eval"
+    traffic, traffic_source = ncu_traffic_entry(eval_name, w.name + ("-loop" if gens > 0 else ""))
+    roof = eval_roofline(stats, eval_name, peak, peak_kind, traffic, traffic_source, part)
+    if roof is not None and gens > 0:
+        roof["launches_measured"] = "the generation loop's evaluation launches (initial population "\
+                                    "and every generation); the step's full sweep is in 'sweep'"
+        sw = eval_roofline(stats, eval_name, peak, peak_kind, *ncu_traffic_entry(eval_name, w.name),
+                           part="eval_sweep")
+        roof["sweep"] = sw
+    names = {"eval": eval_name, "evolve": "k_evolve|k_evolve_seq", "finish": "k_finish",
              "bitmap_build": "k_build_bitmap_planes" if w.cols <= 1024 else "k_build_bitmap",
              "rank_codes": "k_rank_codes"}
-    dominant = max(stats, key=lambda k: stats[k]["ms"])
+    dominant = max((k for k in stats if k not in ("eval_sweep", "eval_loop")),
+                   key=lambda k: stats[k]["ms"])
     if roof is not None:
         roof["dominant_kernel"] = names[dominant]
         if dominant != "eval":

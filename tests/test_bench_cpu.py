@@ -13,13 +13,13 @@ from paper_2105_01196_gb300 import synth
 
 
 def test_ncu_traffic_reads_the_committed_summary():
-    d = bench.ncu_traffic("k_eval_bitmap", "default")
-    b = bench.ncu_traffic("k_eval_bitmap", "batched")
-    assert d is not None and b is not None
+    d = bench.ncu_traffic("k_eval_bitmap", "default-loop")
+    t, src = bench.ncu_traffic_entry("k_eval_bitmap", "tieheavy-loop")
+    assert d is not None and t is not None
     # DRAM bytes per launch stay below the algorithmic bytes (part of the pair words hit L2)
-    # and above the bitmap's share that one sweep must at least bring in once
     assert 1e6 < d < 5.39e6
-    assert 4e8 < b < 6.59e8
+    assert 1e8 < t < 2.46e8
+    assert "traffic_k_eval_bitmap.txt" in src and "commit" in src
     assert bench.ncu_traffic("k_eval_bitmap", "no-such-workload") is None
     assert bench.ncu_traffic("no_such_kernel", "default") is None
 
