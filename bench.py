@@ -48,6 +48,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tieheavy")
     ap.add_argument("--gens", type=int, default=None, help="generations per step")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="override the workload's rows (a smaller case of it, e.g. for profiling)")
+    ap.add_argument("--cols", type=int, default=0, help="override the workload's columns")
+    ap.add_argument("--pop", type=int, default=0, help="override the workload's population")
+    ap.add_argument("--ipw", type=int, default=0,
+                    help="individuals per work item of the staged bitmap form (0: the tuner's)")
     ap.add_argument("--mode", default="auto", choices=list(MODES))
     ap.add_argument("--trend", default="strict",
                     choices=["strict", "ties", "last-kept", "ties-last-kept"],
@@ -80,6 +86,20 @@ def dist_setup(args):
 
 def gens_of(args, w):
     return w.generations if args.gens is None else args.gens
+
+
+def resized(w, args):
+    """The workload with --rows / --cols / --pop applied (planted sizes capped to fit)."""
+    import dataclasses
+    rows = args.rows or w.rows
+    cols = args.cols or w.cols
+    pop = args.pop or w.pop
+    if (rows, cols, pop) == (w.rows, w.cols, w.pop):
+        return dataclasses.replace(w)
+    cap = lambda r, n: (min(r[0], n), min(r[1], n))
+    return dataclasses.replace(w, name=f"{w.name}-{rows}x{cols}-p{pop}", rows=rows, cols=cols,
+                               pop=pop, bic_rows=cap(w.bic_rows, rows // 4),
+                               bic_cols=cap(w.bic_cols, cols), len_hi=min(w.len_hi, cols))
 
 
 def reduce_over_ranks(dist, total_ms, units, device):
@@ -443,7 +463,7 @@ class Job:
     """One workload on one context: device inputs, pinned host copies, and one step of the hot
     path (upload -> evaluation sweep -> initial population + generations -> extraction)."""
 
-    def __init__(self, ebic, torch, w, dev, stream, mode, trend, gens, host_copies=True):
+    def __init__(self, ebic, torch, w, dev, stream, mode, trend, gens, host_copies=True, ipw=0):
         self.ebic, self.torch, self.w, self.gens = ebic, torch, w, gens
         self.x, self.truth, self.ci, self.off = synth_inputs(w)
         self.R, self.P = w.rows, len(self.off) - 1
@@ -456,7 +476,7 @@ class Job:
             self.x_h = torch.from_numpy(self.x).pin_memory()
             self.outs_h = [torch.zeros(self.P, dtype=torch.int32).pin_memory() for _ in range(3)]
             self.outs_h.append(torch.zeros(self.P, dtype=torch.int64).pin_memory())
-        self.params = ebic.Params.make(mode=MODES[mode], **run_fields(w, trend))
+        self.params = ebic.Params.make(mode=MODES[mode], ipw=ipw, **run_fields(w, trend))
         self.ctx = ebic.Context(dev.index or 0, stream.cuda_stream)
         self.used_mode = 0
 
@@ -692,7 +712,7 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    w = dataclasses.replace(synth.WORKLOADS[args.workload])
+    w = resized(synth.WORKLOADS[args.workload], args)
     if args.impl == "reference":
         run_reference(args, w, world, rank, dist)
         if dist:
@@ -709,7 +729,7 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     peak, peak_kind = load_peaks()
 
-    job = Job(ebic, torch, w, dev, stream, args.mode, args.trend, gens)
+    job = Job(ebic, torch, w, dev, stream, args.mode, args.trend, gens, ipw=args.ipw)
     tune = job.tune() if args.mode == "auto" and not args.no_tune else None
     for _ in range(max(3, args.warmup)):
         job.step(False)
@@ -796,8 +816,9 @@ def main():
             "e2e": e2e}
     if tune is not None:
         line["config"]["autotune"] = {k: tune[k] for k in ("mode", "seg_direct", "seg_bitmap",
-                                                          "seg_loop", "direct_ms", "bitmap_ms",
-                                                          "build_ms", "staged_ms")}
+                                                          "seg_loop", "ipw_bitmap", "ipw_loop",
+                                                          "direct_ms", "bitmap_ms", "build_ms",
+                                                          "staged_ms")}
     if gens > 0:
         line["generations_per_s"] = gens * args.steps / (total_ms / 1e3)
         line["quality"] = search_quality(job.ctx, job.truth, job.R, w.cols, gens)

@@ -114,6 +114,10 @@ typedef struct ebic_params {
   int32_t last_kept;   /* 1: each value is compared with the last value that kept the
                           direction instead of with its predecessor; no bitmap form (mode
                           EBIC_MODE_BITMAP is rejected, AUTO takes the direct form); default 0 */
+  int32_t ipw;         /* individuals per work item of the staged bitmap form (bitmaps larger
+                          than L2, ratio below 1): 0 (default) = the autotuner's choice, 1 when
+                          untuned; 1-4 forces it.  Results never depend on it               */
+  int32_t reserved;    /* 0                                                                    */
 } ebic_params;
 
 /* Progress of a run (Sec. 2.4, steps 6 and 8). */
@@ -292,17 +296,19 @@ EBIC_API int ebic_profile_read(ebic_ctx *ctx, int32_t kernel, ebic_kernel_stats 
  * CUDA events, one evaluation sweep of the population (CSR as in ebic_eval_population, host or
  * device) in the direct form (several work-item sizes), the staged direct form (when its tiles
  * fit) and, when the pair bitmap fits in half of the free device memory, the bitmap form
- * (building it; several work-item sizes).  It then records for the
- * loaded matrix the form and sizes minimising build + expected_sweeps * sweep time.  With
- * expected_sweeps > 2 and p valid for ebic_run_generations (the staged form excepted), it also
- * times 16 generations of a scratch run per work-item size of the chosen form (graph-replayed,
- * after a warm-up run) and records the fastest for the generation loop; the run state is reset
- * afterwards, so the caller's next run starts from its initial population;
- * EBIC_MODE_AUTO follows them in ebic_eval_population and ebic_run_generations until a matrix
- * of another shape is loaded (the measured times depend on the shape, not on the values, so a
- * reload of the same shape keeps them).  Results never depend on the choice.  *rep (may be NULL) receives the
- * measurements.  Errors: EBIC_ESTATE (no matrix), EBIC_EINVAL (bad population or parameter,
- * n_ind < 1, expected_sweeps < 1), EBIC_ENOMEM, EBIC_ECUDA.
+ * (building it; several work-item sizes, and 1, 2 or 4 individuals per work item when the
+ * bitmap is larger than L2 and the ratio below 1).  It then records for the loaded matrix the
+ * form and sizes minimising build + expected_sweeps * sweep time.  With expected_sweeps > 2 and
+ * p valid for ebic_run_generations (the staged direct form excepted), it also times 16
+ * generations of a scratch run per work-item size (and group size) of the chosen form
+ * (graph-replayed, after a warm-up run) and records the fastest for the generation loop; the
+ * run state is reset afterwards, so the caller's next run starts from its initial population.
+ * EBIC_MODE_AUTO follows the decisions in ebic_eval_population and ebic_run_generations until
+ * a matrix of another shape is loaded (the measured times depend on the shape, not on the
+ * values, so a reload of the same shape keeps them); p->ipw > 0 overrides the group size.
+ * Results never depend on the choice.  *rep (may be NULL) receives the measurements.
+ * Errors: EBIC_ESTATE (no matrix), EBIC_EINVAL (bad population or parameter, n_ind < 1,
+ * expected_sweeps < 1), EBIC_ENOMEM, EBIC_ECUDA.
  */
 typedef struct ebic_tune_report {
   int32_t mode;       /* chosen form: EBIC_MODE_DIRECT, EBIC_MODE_STAGED or EBIC_MODE_BITMAP */
@@ -313,6 +319,8 @@ typedef struct ebic_tune_report {
   double bitmap_ms;   /* best measured sweep of the bitmap form (-1 when not measured)        */
   double build_ms;    /* measured bitmap build (0 when the bitmap already existed)            */
   double staged_ms;   /* best measured sweep of the staged direct form (-1 when not measured) */
+  int32_t ipw_bitmap; /* chosen individuals per work item of the staged bitmap form (1-4)     */
+  int32_t ipw_loop;   /* the same for the generation loop                                     */
 } ebic_tune_report;
 
 EBIC_API int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *offsets,
@@ -384,7 +392,7 @@ EBIC_API int ebic_server_stats(ebic_server *srv, int32_t *queued, int32_t *runni
  *   col_idx, offsets  CSR population as in ebic_eval_population, device memory;
  *   outputs   device memory of `device`; any may be NULL;
  *   p         neg_trends, ratio_num/den, min_rows, col_cap, non_strict and last_kept are read
- *             (mode and the generation-loop fields are ignored);
+ *             (mode, ipw and the generation-loop fields are ignored);
  *   cuda_stream  a cudaStream_t of `device` (NULL = the legacy default stream);
  *   msg       optional buffer of msg_len bytes for the message of a failure.
  * Scratch: the per-individual accumulators, a work counter and an error word live in one

@@ -118,6 +118,8 @@ int ebic_check_eval_params(ebic_ctx *ctx, const ebic_params *p) {
     return ebic_fail(ctx, EBIC_EINVAL, "non_strict and last_kept must be 0 or 1");
   if (p->last_kept && p->mode == EBIC_MODE_BITMAP)
     return ebic_fail(ctx, EBIC_EINVAL, "the last-kept pair test has no bitmap form");
+  if (p->ipw < 0 || p->ipw > 4 || p->reserved != 0)
+    return ebic_fail(ctx, EBIC_EINVAL, "ipw must be in [0, 4] and reserved 0");
   return EBIC_OK;
 }
 
@@ -537,6 +539,7 @@ int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *o
   a.seg_passes = ctx->tuned ? (mode == EBIC_MODE_BITMAP ? ctx->seg_bitmap
                                                       : (mode == EBIC_MODE_DIRECT ? ctx->seg_direct : 0))
                             : 0;
+  a.ipw = p->ipw > 0 ? p->ipw : (ctx->tuned && mode == EBIC_MODE_BITMAP ? ctx->ipw_bitmap : 1);
   PopView pv{};
   pv.cols = d_cols;
   pv.off = d_off;
@@ -632,6 +635,7 @@ EvalArgs eval_args_for(const ebic_ctx *ctx) {
   a.code_bytes = ctx->codes_ready ? ctx->code_bytes : 0;
   a.S = ctx->codes_ready ? ctx->code_stride : 0;
   a.stage_bitmap = ctx->bitmap_ok && (double)ebic_bitmap_bytes(ctx->R, ctx->C) > (double)ctx->l2_bytes;
+  a.ipw = 1;
   return a;
 }
 

@@ -233,6 +233,7 @@ __host__ __device__ constexpr int stage_pairs() {
   return (int)(kStageBytes / (kPassWords * 4u)) / (NEG ? 2 : 1);  // 12 with NEG, else 24
 }
 constexpr size_t kBitmapSmem = (size_t)kWarps * kStageBytes;
+constexpr int kMaxIpw = 4;  // individuals per work item of the grouped staged form, at most
 
 __device__ __forceinline__ uint4 not4(uint4 v) { return make_uint4(~v.x, ~v.y, ~v.z, ~v.w); }
 
@@ -260,11 +261,6 @@ __device__ __forceinline__ void cp_async16(uint32_t *dst, const uint32_t *src) {
                    (uint32_t)__cvta_generic_to_shared(dst)),
                "l"((uint64_t)__cvta_generic_to_global(src))
                : "memory");
-}
-
-// Waits for all of this thread's asynchronous copies (a bounded hardware wait).
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
 }
 
 // Closes this thread's current group of asynchronous copies.
@@ -302,18 +298,285 @@ __device__ __forceinline__ void cnt_add_group(Cnt6 (&P)[4], Cnt6 (&N)[4], const 
 // Staging measured slower where L2 holds the bitmap and with ratio 1; register loads inside the
 // staged kernel measured slower still (its shared memory leaves the L1 too little room for the
 // loads in flight), so that kernel stages every item.
-template <bool NEG, bool NS, bool STAGE>
+// The counts of one pass (4 words per lane) of an individual with threshold t into cp / cn /
+// ca: the AND of the pair words (exact) or the bit-sliced counters against t.
+template <bool NEG, bool NS>
+__device__ __forceinline__ void pass_counts(const EvalArgs &a, int64_t w, bool act, bool exact,
+                                            int t, uint4 ap, uint4 an, const Cnt6 (&P)[4],
+                                            const Cnt6 (&N)[4], int &cp, int &cn, int &ca) {
+  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+  uint4 pos, neg = zero4;
+  if (exact) {
+    pos = act ? ap : zero4;
+    if (NEG) neg = act ? an : zero4;
+  } else {
+    pos = make_uint4(cnt_ge(P[0], t), cnt_ge(P[1], t), cnt_ge(P[2], t), cnt_ge(P[3], t));
+    if (NEG) neg = make_uint4(cnt_ge(N[0], t), cnt_ge(N[1], t), cnt_ge(N[2], t), cnt_ge(N[3], t));
+  }
+  if (NS) {  // pad rows (and inactive lanes) hold complemented zeros: mask them out
+    const uint4 vm = act ? make_uint4(valid_bits(w, a.R), valid_bits(w + 1, a.R),
+                                      valid_bits(w + 2, a.R), valid_bits(w + 3, a.R))
+                         : zero4;
+    pos = and4(pos, vm);
+    if (NEG) neg = and4(neg, vm);
+  }
+  cp += popc4(pos);
+  if (NEG) {
+    cn += popc4(neg);
+    ca += popc4(make_uint4(pos.x | neg.x, pos.y | neg.y, pos.z | neg.z, pos.w | neg.w));
+  } else {
+    ca += popc4(pos);
+  }
+}
+
+// Staged form (the bitmap exceeds L2, ratio below 1).  A work item is a group of a.ipw
+// consecutive individuals (1 <= ipw <= kMaxIpw) and one row segment.  The group's bookkeeping
+// loads in one round (lane j holds individual j's length, dead flag and key; the columns of
+// every individual go to shared memory), and the pair words of all its live individuals form
+// one stream of units staged two at a time: the copies of the next unit, of the same individual
+// or of the next, are in flight while the current unit is counted.  A unit holds up to H pair
+// rows per direction: several consecutive passes of all pairs when the chromosome is short
+// (np <= H: H / np passes per unit), else one pass of a batch of up to H pairs.  Grouping
+// individuals keeps the stream full across the short chromosomes of the generation loop, whose
+// items are otherwise one unit each with a round trip for their bookkeeping before it.  The
+// individuals' pair-row indices (c * C + d) are computed once per item into shared memory.
+template <bool NEG, bool NS>
+__device__ __forceinline__ void bitmap_staged_items(const EvalArgs &a, const PopView &pv,
+                                                    int lane, uint32_t *sp, uint32_t *sn,
+                                                    uint32_t *pidx) {
+  constexpr int NB = stage_pairs<NEG>();
+  constexpr int H = NB / 2;
+  const int64_t Wst = a.Wst;
+  const int64_t passes_total = (Wst + kPassWords - 1) / kPassWords;
+  const int ipw = a.ipw;
+  const int32_t n_grp = (pv.n + ipw - 1) / ipw;
+  const int32_t n_side = items::move_chunks(a), n_all = n_side + n_grp * a.n_seg;
+  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+  const uint4 ones = make_uint4(kFull, kFull, kFull, kFull);
+  for (int q = items::first(); q < n_all; q = items::next(a.work, lane, q, n_all)) {
+    if (q < n_side) {
+      if (items::stopped(pv)) return;  // a stopped run changes nothing
+      items::move_chunk(a, q, lane);
+      continue;
+    }
+    const int seg = (q - n_side) / n_grp, grp = (q - n_side) - seg * n_grp;  // segment-major
+    const int i0 = grp * ipw, cnt = min(ipw, pv.n - i0);
+    // lane j < cnt: individual i0 + j's bookkeeping
+    int myL = 0, myst = 0;
+    bool mydead = true;
+    uint64_t myh = 0ull;
+    if (lane < cnt) {
+      const int i = i0 + lane;
+      if (pv.off) {
+        myst = pv.off[i];
+        myL = pv.off[i + 1] - myst;
+      } else {
+        myst = i * pv.stride;
+        myL = pv.len[i];
+      }
+      mydead = pv.dead && pv.dead[i];
+      myh = pv.dkeys ? pv.hash[i] : 0ull;
+    }
+    __syncwarp();  // (the previous item's reads of pidx are done)
+#pragma unroll
+    for (int j = 0; j < kMaxIpw; ++j) {
+      if (j < cnt) {  // (cnt is the same in every lane)
+        int c0, c1;
+        if (!pv.off) {  // fixed-stride rows: the column words load with the lengths
+          const int st = (i0 + j) * pv.stride;
+          c0 = pv.cols[st + lane];
+          c1 = pv.cols[st + 32 + lane];
+        } else {
+          const int st = __shfl_sync(kFull, myst, j), L = __shfl_sync(kFull, myL, j);
+          c0 = lane < L ? pv.cols[st + lane] : 0;
+          c1 = lane + 32 < L ? pv.cols[st + 32 + lane] : 0;
+        }
+        // pair k = (column k, column k + 1): lane k holds pairs k and 32 + k; the index of the
+        // pair word row is c * C + d for the positive direction, d * C + c for the negative
+        // (swapped when ties count both ways), below 2^32 since C <= 65,535
+        const int n0 = __shfl_down_sync(kFull, c0, 1), n1 = __shfl_down_sync(kFull, c1, 1);
+        const int c32 = __shfl_sync(kFull, c1, 0);
+        const uint32_t C = (uint32_t)a.C;
+        const uint32_t ka = (uint32_t)c0, kb = (uint32_t)(lane < 31 ? n0 : c32);
+        const uint32_t la = (uint32_t)c1, lb = (uint32_t)(lane < 31 ? n1 : 0);
+        uint32_t *pj = pidx + j * 2 * EBIC_MAX_LEN;
+        pj[lane] = NS ? kb * C + ka : ka * C + kb;
+        pj[EBIC_MAX_LEN + lane] = NS ? ka * C + kb : kb * C + ka;
+        pj[32 + lane] = NS ? lb * C + la : la * C + lb;
+        pj[EBIC_MAX_LEN + 32 + lane] = NS ? la * C + lb : lb * C + la;
+      }
+    }
+    if (items::stopped(pv)) return;  // (read with the item's loads; before any store)
+    const bool mylive = lane < cnt && !mydead && myL >= 2;
+    const unsigned live = __ballot_sync(kFull, mylive);
+    if (!live) continue;
+    // each live individual's key enters the duplicate table from its first segment's item
+    items::Insert myins{0ull, 0u, pv.dkeys != nullptr && seg == 0 && mylive};
+    if (myins.on) {
+      myins.idx = table_index(myh, pv.dmask);
+      myins.prev = atomicCAS(reinterpret_cast<unsigned long long *>(pv.dkeys + myins.idx), 0ull,
+                             (unsigned long long)myh);
+    }
+    __syncwarp();  // pidx is written
+    const int64_t p0 = (int64_t)seg * a.seg_passes;
+    const int64_t p1 = min(p0 + a.seg_passes, passes_total);
+    const int n_pass = (int)(p1 - p0);
+    // lane j: individual j's unit plan
+    const int mynp = myL - 1;
+    const bool mypacked = mynp <= H;
+    const int myppu = mypacked ? H / max(mynp, 1) : 1;   // passes per unit
+    const int mynbat = mypacked ? 1 : (mynp + H - 1) / H;  // batches per pass
+    const int myunits = !mylive ? 0 : (mypacked ? (n_pass + myppu - 1) / myppu : n_pass * mynbat);
+    auto next_live = [&](int from) -> int {  // the first live individual >= from, or kMaxIpw
+      const unsigned m = from >= 32 ? 0u : (live >> from) << from;
+      return m ? __ffs(m) - 1 : kMaxIpw;
+    };
+    auto advance = [&](int &j, int &u) {
+      if (++u >= __shfl_sync(kFull, myunits, j)) {
+        j = next_live(j + 1);
+        u = 0;
+      }
+    };
+    // copies of unit u of individual j into half b
+    auto issue = [&](int j, int u, int b) {
+      const int np = __shfl_sync(kFull, mynp, j), ppu = __shfl_sync(kFull, myppu, j);
+      const int nbat = __shfl_sync(kFull, mynbat, j);
+      const uint32_t *pj = pidx + j * 2 * EBIC_MAX_LEN;
+      uint32_t *bp = sp + b * H * kPassWords, *bn = sn + b * H * kPassWords;
+      int64_t qa, qb;
+      int k0, nb;
+      if (np <= H) {
+        qa = p0 + (int64_t)u * ppu;
+        qb = min(p1, qa + ppu);
+        k0 = 0;
+        nb = np;
+      } else {
+        qa = p0 + u / nbat;
+        qb = qa + 1;
+        k0 = (u % nbat) * H;
+        nb = min(H, np - k0);
+      }
+      for (int64_t qq = qa; qq < qb; ++qq) {
+        const int64_t w = qq * kPassWords + lane * 4;
+        if (w < Wst) {
+          const uint32_t *G = a.bitmap + w;
+          const int slot0 = (int)(qq - qa) * nb;
+          for (int k = 0; k < nb; ++k) {
+            cp_async16(bp + (slot0 + k) * kPassWords, G + (int64_t)pj[k0 + k] * Wst);
+            if (NEG)
+              cp_async16(bn + (slot0 + k) * kPassWords,
+                         G + (int64_t)pj[EBIC_MAX_LEN + k0 + k] * Wst);
+          }
+        }
+      }
+      cp_async_commit();
+    };
+    int ji = next_live(0), ui = 0, jc = ji, uc = 0, gi = 0, gc = 0;
+    int cp = 0, cn = 0, ca = 0;
+    uint4 ap = ones, an = ones;
+    Cnt6 P[4], N[4];
+    issue(ji, ui, 0);
+    ++gi;
+    advance(ji, ui);
+    while (jc < kMaxIpw) {
+      if (ji < kMaxIpw) {
+        issue(ji, ui, gi & 1);
+        ++gi;
+        advance(ji, ui);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      // count unit uc of individual jc from half gc & 1
+      const int np = __shfl_sync(kFull, mynp, jc), ppu = __shfl_sync(kFull, myppu, jc);
+      const int nbat = __shfl_sync(kFull, mynbat, jc), nu = __shfl_sync(kFull, myunits, jc);
+      const int t = threshold(np + 1, a.rnum, a.rden);
+      const bool exact = (t == np);
+      const uint32_t *bp = sp + (gc & 1) * H * kPassWords, *bn = sn + (gc & 1) * H * kPassWords;
+      ++gc;
+      int64_t qa, qb;
+      int k0, nb;
+      if (np <= H) {
+        qa = p0 + (int64_t)uc * ppu;
+        qb = min(p1, qa + ppu);
+        k0 = 0;
+        nb = np;
+      } else {
+        qa = p0 + uc / nbat;
+        qb = qa + 1;
+        k0 = (uc % nbat) * H;
+        nb = min(H, np - k0);
+      }
+      for (int64_t qq = qa; qq < qb; ++qq) {
+        const int64_t w = qq * kPassWords + lane * 4;
+        const bool act = w < Wst;  // (Wst is a multiple of 4: a lane's 4 words all exist or not)
+        const int s0 = (int)(qq - qa) * nb;
+        if (k0 == 0) {
+          ap = ones;
+          an = ones;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            cnt_zero(P[j]);
+            cnt_zero(N[j]);
+          }
+        }
+        if (exact) {
+          for (int j = 0; j < nb; ++j) {
+            ap = and4(ap, lds<NS>(act, bp + (s0 + j) * kPassWords, ones));
+            if (NEG) an = and4(an, lds<NS>(act, bn + (s0 + j) * kPassWords, ones));
+          }
+        } else {
+          for (int h = 0; h < nb; h += 4) {  // (the last group padded with zeros)
+            uint4 v[4], uu[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const bool in = act && h + j < nb;
+              v[j] = lds<NS>(in, bp + (s0 + h + j) * kPassWords, zero4);
+              uu[j] = NEG ? lds<NS>(in, bn + (s0 + h + j) * kPassWords, zero4) : zero4;
+            }
+            cnt_add_group<NEG>(P, N, v, uu);
+          }
+        }
+        if (k0 + nb == np) pass_counts<NEG, NS>(a, w, act, exact, t, ap, an, P, N, cp, cn, ca);
+      }
+      if (uc + 1 == nu) {  // the individual's last unit: its counts
+        cp = __reduce_add_sync(kFull, cp);
+        cn = __reduce_add_sync(kFull, cn);
+        ca = __reduce_add_sync(kFull, ca);
+        if (lane == 0) {
+          const int i = i0 + jc;
+          if (cp) atomicAdd(a.rows_pos + i, cp);
+          if (cn) atomicAdd(a.rows_neg + i, cn);
+          if (ca) atomicAdd(a.rows_any + i, ca);
+        }
+        cp = cn = ca = 0;
+      }
+      advance(jc, uc);
+    }
+    items::insert_finish(pv, myins, myh, i0 + lane);
+  }
+}
+
+// GROUP (with STAGE only): work items of a.ipw > 1 individuals (bitmap_staged_items); else one
+// individual per item.  Each form declares only its own shared arrays.
+template <bool NEG, bool NS, bool STAGE, bool GROUP>
 __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView pv) {
   extern __shared__ __align__(128) uint32_t s_stage[];  // kStageBytes per warp (STAGE)
-  __shared__ int64_t s_pos[kWarps][EBIC_MAX_LEN];
-  __shared__ int64_t s_neg[kWarps][EBIC_MAX_LEN];
-  __shared__ int32_t s_col[kWarps][EBIC_MAX_LEN];
+  __shared__ int64_t s_pos[GROUP ? 1 : kWarps][EBIC_MAX_LEN];
+  __shared__ int64_t s_neg[GROUP ? 1 : kWarps][EBIC_MAX_LEN];
+  __shared__ int32_t s_col[GROUP ? 1 : kWarps][EBIC_MAX_LEN];
+  __shared__ uint32_t s_pidx[GROUP ? kWarps * kMaxIpw * 2 : 1][EBIC_MAX_LEN];
   constexpr int NB = stage_pairs<NEG>();
   static_assert(NB % 4 == 0, "staged batches are read in groups of four pairs");
+  static_assert(STAGE || !GROUP, "groups of individuals are a form of the staged kernel");
   wait_prior_grid();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *sp = s_stage + (size_t)warp * (kStageBytes / 4) + lane * 4;  // pair j: sp + 128 j
   uint32_t *sn = sp + NB * kPassWords;                                    // negative direction
+  if (GROUP) {
+    bitmap_staged_items<NEG, NS>(a, pv, lane, sp, sn, &s_pidx[warp * kMaxIpw * 2][0]);
+    return;
+  }
   const int64_t Wst = a.Wst;
   const int64_t passes_total = (Wst + kPassWords - 1) / kPassWords;
   const int32_t n_side = items::move_chunks(a), n_all = n_side + pv.n * a.n_seg;
@@ -635,12 +898,15 @@ static EvalKernel direct_kernel(bool neg, bool ns, bool lk) {
   return t[(neg ? 4 : 0) + (ns ? 2 : 0) + (lk ? 1 : 0)];
 }
 
-static EvalKernel bitmap_kernel(bool neg, bool ns, bool stage) {
-  static const EvalKernel t[8] = {
-      k_eval_bitmap<false, false, false>, k_eval_bitmap<false, false, true>,
-      k_eval_bitmap<false, true, false>,  k_eval_bitmap<false, true, true>,
-      k_eval_bitmap<true, false, false>,  k_eval_bitmap<true, false, true>,
-      k_eval_bitmap<true, true, false>,   k_eval_bitmap<true, true, true>};
+static EvalKernel bitmap_kernel(bool neg, bool ns, bool stage, bool group) {
+  static const EvalKernel t[12] = {
+      k_eval_bitmap<false, false, false, false>, k_eval_bitmap<false, false, true, false>,
+      k_eval_bitmap<false, true, false, false>,  k_eval_bitmap<false, true, true, false>,
+      k_eval_bitmap<true, false, false, false>,  k_eval_bitmap<true, false, true, false>,
+      k_eval_bitmap<true, true, false, false>,   k_eval_bitmap<true, true, true, false>,
+      k_eval_bitmap<false, false, true, true>,   k_eval_bitmap<false, true, true, true>,
+      k_eval_bitmap<true, false, true, true>,    k_eval_bitmap<true, true, true, true>};
+  if (group) return t[8 + (neg ? 2 : 0) + (ns ? 1 : 0)];
   return t[(neg ? 4 : 0) + (ns ? 2 : 0) + (stage ? 1 : 0)];
 }
 
@@ -654,8 +920,8 @@ cudaError_t prepare_bitmap_eval() {
   std::lock_guard<std::mutex> lock(mu);
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   if (attr_set[dev]) return cudaSuccess;
-  for (int k = 0; k < 4; ++k)
-    if ((e = cudaFuncSetAttribute(bitmap_kernel(k & 2, k & 1, true),
+  for (int k = 0; k < 8; ++k)
+    if ((e = cudaFuncSetAttribute(bitmap_kernel(k & 2, k & 1, true, k & 4),
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kBitmapSmem)) != cudaSuccess)
       return e;
@@ -678,7 +944,9 @@ cudaError_t launch_eval_kernel(int mode, const EvalArgs &a0, const PopView &pv, 
   const bool bitmap = (mode == EBIC_MODE_BITMAP);
   const int64_t passes_total = bitmap ? (a.Wst + 127) / 128 : a.R_pad / 128;
   const bool stage = bitmap && a.stage_bitmap && a.rnum < a.rden;  // (ratio 1: all exact)
-  const EvalKernel kern = bitmap ? bitmap_kernel(a.neg, a.non_strict, stage)
+  // Individuals per work item: groups (ipw > 1) are a form of the staged kernel.
+  a.ipw = stage ? std::max(1, std::min(a0.ipw, kMaxIpw)) : 1;
+  const EvalKernel kern = bitmap ? bitmap_kernel(a.neg, a.non_strict, stage, a.ipw > 1)
                                  : direct_kernel(a.neg, a.non_strict, a.last_kept);
   const size_t smem = stage ? kBitmapSmem : 0;
   if (stage) {
@@ -687,20 +955,21 @@ cudaError_t launch_eval_kernel(int mode, const EvalArgs &a0, const PopView &pv, 
   }
   const int bps = blocks_per_sm_for((const void *)kern, smem);
   const int64_t warps = (int64_t)num_sms * bps * kWarps;
+  const int64_t n_grp = ((int64_t)pv.n + a.ipw - 1) / a.ipw;
   // Segments: the autotuner's size when it set one, else enough work items for ~8 per
   // resident warp; at most 2^30 items in total.
-  int64_t seg = a0.seg_passes > 0 ? a0.seg_passes : ((int64_t)pv.n * passes_total) / (8 * warps);
+  int64_t seg = a0.seg_passes > 0 ? a0.seg_passes : (n_grp * passes_total) / (8 * warps);
   if (seg < 1) seg = 1;
   if (seg > passes_total) seg = passes_total;
   int64_t n_seg = (passes_total + seg - 1) / seg;
-  while ((int64_t)pv.n * n_seg > (1LL << 30)) {
+  while (n_grp * n_seg > (1LL << 30)) {
     seg *= 2;
     n_seg = (passes_total + seg - 1) / seg;
   }
   a.seg_passes = (int32_t)seg;
   a.n_seg = (int32_t)n_seg;
   // (the side task's chunks count too: with a warp for every item they run beside the others)
-  const int64_t items = (int64_t)pv.n * n_seg + (a.mv_table ? (a.mv_n + 31) / 32 : 0);
+  const int64_t items = n_grp * n_seg + (a.mv_table ? (a.mv_n + 31) / 32 : 0);
   int64_t grid = (int64_t)num_sms * bps;
   const int64_t need = (items + kWarps - 1) / kWarps;
   if (grid > need) grid = need;

@@ -1332,6 +1332,7 @@ bool same_run_params(const ebic_params &a, const ebic_params &b) {
   ebic_params x = a, y = b;
   x.mode = y.mode = 0;
   x.use_graph = y.use_graph = 0;
+  x.ipw = y.ipw = 0;  // (a performance choice, like the two above)
   return memcmp(&x, &y, sizeof(x)) == 0;
 }
 
@@ -1401,8 +1402,10 @@ EvalArgs gen_eval_args(ebic_ctx *ctx, GenState *g, int k, bool has_prev) {
   a.rows_any = a.rows_neg + g->P;
   a.fitness = nullptr;
   a.work = g->work.as<int32_t>();
-  // (the autotuner's loop size was measured in the loop, with the form it chose)
-  a.seg_passes = ctx->tuned && g->eval_mode == ctx->tuned_mode ? ctx->seg_loop : 0;
+  // (the autotuner's loop sizes were measured in the loop, with the form it chose)
+  const bool tuned = ctx->tuned && g->eval_mode == ctx->tuned_mode;
+  a.seg_passes = tuned ? ctx->seg_loop : 0;
+  a.ipw = g->p.ipw > 0 ? g->p.ipw : (tuned ? ctx->ipw_loop : 1);
   return a;
 }
 
@@ -1785,6 +1788,8 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
   }
   g->p.mode = p->mode;
   g->p.use_graph = p->use_graph;
+  if (g->p.ipw != p->ipw) g->drop_graphs();  // (the captured launches hold the group size)
+  g->p.ipw = p->ipw;
   EBIC_TRY(ensure_eval_ready(ctx, g, p, n_gen));
   GenCtl c{};
   EBIC_TRY(read_ctl(ctx, g, &c));

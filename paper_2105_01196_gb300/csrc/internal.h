@@ -106,6 +106,7 @@ struct EvalArgs {
   int32_t *work;            // dynamic work counter (zeroed first)
   int32_t seg_passes;       // passes (of 128 words or 128 rows) per work item
   int32_t n_seg;            // segments per individual
+  int32_t ipw;              // individuals per work item (the staged bitmap form; else 1)
   // Optional side task of the generation loop, done by the launch's warps beside the evaluation
   // items (the staged kernel: before them): the previous generation's live keys (mv_hash[s] of
   // its slots s < mv_n with !mv_dead[s] and mv_len[s] >= 2) join the hashed tabu list
@@ -203,6 +204,7 @@ struct ebic_ctx {
   int tuned_mode = EBIC_MODE_DIRECT;
   int seg_direct = 0, seg_bitmap = 0;  // work-item sizes in passes; 0 = the built-in split
   int seg_loop = 0;                    // the same for the generation loop's evaluations
+  int ipw_bitmap = 1, ipw_loop = 1;    // individuals per work item (staged bitmap form)
 
   // generation loop state (evolve.cu)
   struct GenState *gen = nullptr;

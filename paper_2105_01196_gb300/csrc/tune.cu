@@ -20,7 +20,8 @@ const int kSegCandidates[] = {0, 1, 2, 4, 8, 16, 32};  // 0 = the built-in split
 const int kReps = 3;
 
 // Minimum over kReps of one evaluation sweep (kernel only, CUDA events on the context stream).
-int time_eval(ebic_ctx *ctx, int mode, EvalArgs a, const PopView &pv, int seg, double *ms_out) {
+int time_eval(ebic_ctx *ctx, int mode, EvalArgs a, const PopView &pv, int seg, int ipw,
+              double *ms_out) {
   cudaEvent_t e0, e1;
   EBIC_CHECK_CUDA(ctx, cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -28,6 +29,7 @@ int time_eval(ebic_ctx *ctx, int mode, EvalArgs a, const PopView &pv, int seg, d
     return ebic_fail(ctx, EBIC_ECUDA, "cudaEventCreate failed");
   }
   a.seg_passes = seg;
+  a.ipw = ipw;
   double best = DBL_MAX;
   int status = EBIC_OK;
   for (int r = 0; r < kReps && status == EBIC_OK; ++r) {
@@ -56,7 +58,8 @@ const int kLoopGens = 16;
 // and `gens` generations, which also captures the graphs), then the same run again with its
 // generations timed by CUDA events on the context stream.  The run state is reset afterwards:
 // the caller's next run starts from its own initial population.
-int tune_loop(ebic_ctx *ctx, const ebic_params *p, int gens, int *best_out) {
+int tune_loop(ebic_ctx *ctx, const ebic_params *p, int gens, int ipw_max, int *best_seg_out,
+              int *best_ipw_out) {
   cudaEvent_t e0, e1;
   EBIC_CHECK_CUDA(ctx, cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -66,13 +69,18 @@ int tune_loop(ebic_ctx *ctx, const ebic_params *p, int gens, int *best_out) {
   ebic_params q = *p;
   q.mode = EBIC_MODE_AUTO;  // (the form just chosen)
   q.use_graph = 1;
+  q.ipw = 0;                // (the candidate below)
   const int64_t passes = eval_passes(ctx, ctx->tuned_mode);
   double best = DBL_MAX;
-  int best_seg = 0, status = EBIC_OK;
+  int best_seg = 0, best_ipw = 1, status = EBIC_OK;
   ebic_run_report rep;
-  for (int seg : kLoopSegCandidates) {
-    if (seg > passes) break;
+  for (int cand = 0; status == EBIC_OK; ++cand) {
+    const int n_seg_cands = (int)(sizeof(kLoopSegCandidates) / sizeof(int));
+    const int ipw = 1 << (cand / n_seg_cands), seg = kLoopSegCandidates[cand % n_seg_cands];
+    if (ipw > ipw_max) break;
+    if (seg > passes) continue;
     ctx->seg_loop = seg;
+    ctx->ipw_loop = ipw;
     float ms = 0.f;
     for (int pass = 0; pass < 2 && status == EBIC_OK; ++pass) {
       if (ctx->gen) {
@@ -94,6 +102,7 @@ int tune_loop(ebic_ctx *ctx, const ebic_params *p, int gens, int *best_out) {
     if (ms < best) {
       best = ms;
       best_seg = seg;
+      best_ipw = ipw;
     }
   }
   cudaEventDestroy(e0);
@@ -102,7 +111,8 @@ int tune_loop(ebic_ctx *ctx, const ebic_params *p, int gens, int *best_out) {
     gen_drop_graphs(ctx->gen);
     gen_mark_reset(ctx->gen);
   }
-  *best_out = best_seg;
+  *best_seg_out = best_seg;
+  *best_ipw_out = best_ipw;
   return status;
 }
 
@@ -154,11 +164,11 @@ extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_
   const int64_t passes_direct = eval_passes(ctx, EBIC_MODE_DIRECT),
                 passes_bitmap = eval_passes(ctx, EBIC_MODE_BITMAP);
   double best_direct = DBL_MAX, best_bitmap = DBL_MAX;
-  int seg_direct = 0, seg_bitmap = 0;
+  int seg_direct = 0, seg_bitmap = 0, ipw_bitmap = 1;
   for (int seg : kSegCandidates) {
     if (seg > passes_direct) break;
     double ms = 0;
-    EBIC_TRY(time_eval(ctx, EBIC_MODE_DIRECT, a, pv, seg, &ms));
+    EBIC_TRY(time_eval(ctx, EBIC_MODE_DIRECT, a, pv, seg, 1, &ms));
     if (ms < best_direct) {
       best_direct = ms;
       seg_direct = seg;
@@ -192,20 +202,24 @@ extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_
     }
     a.bitmap = ctx->bitmap.as<uint32_t>();
     a.stage_bitmap = eval_args_for(ctx).stage_bitmap;  // (the form later runs will use)
-    for (int seg : kSegCandidates) {
-      if (seg > passes_bitmap) break;
-      double ms = 0;
-      EBIC_TRY(time_eval(ctx, EBIC_MODE_BITMAP, a, pv, seg, &ms));
-      if (ms < best_bitmap) {
-        best_bitmap = ms;
-        seg_bitmap = seg;
+    // (individuals per item: the staged form only)
+    const int ipw_max = a.stage_bitmap && p->ratio_num < p->ratio_den ? 4 : 1;
+    for (int ipw = 1; ipw <= ipw_max; ipw *= 2)
+      for (int seg : kSegCandidates) {
+        if (seg > passes_bitmap) break;
+        double ms = 0;
+        EBIC_TRY(time_eval(ctx, EBIC_MODE_BITMAP, a, pv, seg, ipw, &ms));
+        if (ms < best_bitmap) {
+          best_bitmap = ms;
+          seg_bitmap = seg;
+          ipw_bitmap = ipw;
+        }
       }
-    }
   }
   // the staged direct form, when its tiles fit in shared memory
   double best_staged = DBL_MAX;
   if (ctx->dtma.ok && !p->non_strict && !p->last_kept) {  // the staged kernel's pair test
-    EBIC_TRY(time_eval(ctx, EBIC_MODE_STAGED, a, pv, 0, &best_staged));
+    EBIC_TRY(time_eval(ctx, EBIC_MODE_STAGED, a, pv, 0, 1, &best_staged));
   }
   const int direct_mode = best_staged < best_direct ? EBIC_MODE_STAGED : EBIC_MODE_DIRECT;
   const double cost_direct = (double)expected_sweeps * (best_staged < best_direct ? best_staged
@@ -217,20 +231,28 @@ extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_
   ctx->tuned_mode = cost_bitmap < cost_direct ? EBIC_MODE_BITMAP : direct_mode;
   ctx->seg_direct = seg_direct;
   ctx->seg_bitmap = seg_bitmap;
+  ctx->ipw_bitmap = ipw_bitmap;
   ctx->seg_loop = 0;
+  ctx->ipw_loop = 1;
   // A run of generations expected: the loop's population soon differs from this one (selection
   // shortens it), so its work-item size is measured in the loop itself.
   if (expected_sweeps > 2 && ctx->tuned_mode != EBIC_MODE_STAGED &&
       ebic_check_loop_params(ctx, p) == EBIC_OK) {
-    int best_seg = 0;
-    EBIC_TRY(tune_loop(ctx, p, std::min(expected_sweeps - 1, kLoopGens), &best_seg));
+    int best_seg = 0, best_ipw = 1;
+    const bool staged = ctx->tuned_mode == EBIC_MODE_BITMAP && eval_args_for(ctx).stage_bitmap &&
+                        p->ratio_num < p->ratio_den;
+    EBIC_TRY(tune_loop(ctx, p, std::min(expected_sweeps - 1, kLoopGens), staged ? 4 : 1,
+                       &best_seg, &best_ipw));
     ctx->seg_loop = best_seg;
+    ctx->ipw_loop = best_ipw;
   }
   if (rep) {
     r.mode = ctx->tuned_mode;
     r.seg_direct = seg_direct;
     r.seg_bitmap = seg_bitmap;
     r.seg_loop = ctx->seg_loop;
+    r.ipw_bitmap = ctx->ipw_bitmap;
+    r.ipw_loop = ctx->ipw_loop;
     r.direct_ms = best_direct;
     r.staged_ms = best_staged == DBL_MAX ? -1.0 : best_staged;
     r.bitmap_ms = best_bitmap == DBL_MAX ? -1.0 : best_bitmap;

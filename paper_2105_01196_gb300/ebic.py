@@ -48,7 +48,8 @@ class Params(ctypes.Structure):
                 ("max_attempts", ctypes.c_int32), ("tabu_hit_limit", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("mode", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("non_strict", ctypes.c_int32),
-                ("last_kept", ctypes.c_int32)]
+                ("last_kept", ctypes.c_int32), ("ipw", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     @classmethod
     def make(cls, **kw):
@@ -317,7 +318,8 @@ class TuneReport(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("seg_direct", ctypes.c_int32),
                 ("seg_bitmap", ctypes.c_int32), ("seg_loop", ctypes.c_int32),
                 ("direct_ms", ctypes.c_double), ("bitmap_ms", ctypes.c_double),
-                ("build_ms", ctypes.c_double), ("staged_ms", ctypes.c_double)]
+                ("build_ms", ctypes.c_double), ("staged_ms", ctypes.c_double),
+                ("ipw_bitmap", ctypes.c_int32), ("ipw_loop", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}

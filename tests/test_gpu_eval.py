@@ -314,6 +314,29 @@ def test_bitmap_larger_than_l2_all_variants(ebic, torch_cuda):
                 assert_parity(ctx.eval_population(ci, off, p), want)
 
 
+@pytest.mark.parametrize("ipw", [2, 3, 4])
+def test_staged_groups_of_individuals(ebic, torch_cuda, ipw):
+    """The staged bitmap form with 2, 3 or 4 individuals per work item (the last group partial
+    when the population is not a multiple): one stream of staged units across the group's
+    individuals, dead-free CSR individuals of 2 to 64 columns (single and several units per
+    pass), both directions and one, ties counting both ways or not, against the oracle."""
+    R, C = 4500, 650
+    g = np.random.default_rng(91 + ipw)
+    x = tie_matrix(g, R, C)
+    lens = np.concatenate([[2, 2, 3, 7, 8, 13, 14, 64], g.integers(2, 65, size=27)])
+    ci, off = ragged_population(g, len(lens), C, lens)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        for neg, ns in ((1, 0), (1, 1), (0, 0)):
+            for num, den in ((85, 100), (1, 2)):
+                want = oracle_eval(x, ci, off, neg, num, den, ns=ns)
+                p = ebic.Params.make(neg_trends=neg, ratio_num=num, ratio_den=den, mode=2,
+                                     non_strict=ns, ipw=ipw)
+                assert_parity(ctx.eval_population(ci, off, p), want)
+        with pytest.raises(ebic.EbicError):
+            ctx.eval_population(ci, off, ebic.Params.make(ipw=5))
+
+
 def test_csr_validation_long_chromosomes(ebic):
     """Repeated columns are rejected wherever they sit in a chromosome of up to 64 columns (both
     within the first 32, both within the last 32, one in each), and one bad individual among

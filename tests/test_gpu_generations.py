@@ -146,16 +146,17 @@ def test_default_workload_generations(ebic):
         assert_same_state(ctx, st, gp)
 
 
-@pytest.mark.parametrize("ns", [0, 1])
-def test_generations_over_a_bitmap_larger_than_l2(ebic, ns):
+@pytest.mark.parametrize("ns,ipw", [(0, 0), (1, 0), (0, 3), (1, 4)])
+def test_generations_over_a_bitmap_larger_than_l2(ebic, ns, ipw):
     """The generation loop over a 243 MB pair bitmap (larger than the device's L2, so the bitmap
     kernel stages its pair words in shared memory) on a tie-heavy matrix, with ties counting for
-    both directions or not: generation by generation, then eight generations in one graph
-    replay, against the oracle."""
+    both directions or not, one individual per work item or groups of 3 or 4: generation by
+    generation, then eight generations in one graph replay, against the oracle."""
     g = np.random.default_rng(21 + ns)
     x = g.integers(-3, 4, size=(4500, 650)).astype(np.float32)
     gp, op = both_params(ebic, mode=2, non_strict=ns, max_len=20, init_max_len=20, pop_size=96,
                          elite=6, n_biclusters=6, seed=23)
+    gp.ipw = ipw                                    # (individuals per staged work item)
     with ebic.Context(0) as ctx:
         ctx.load_matrix(x)
         ctx.run_generations(gp, 0)
