@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--pop", type=int, default=0, help="override the workload's population")
     ap.add_argument("--ipw", type=int, default=0,
                     help="individuals per work item of the staged bitmap form (0: the tuner's)")
+    ap.add_argument("--fuse-pairs", type=int, default=0,
+                    help="pair limit of the evaluation inside the evolve kernel (0: the library's "
+                         "choice, -1: none)")
     ap.add_argument("--mode", default="auto", choices=list(MODES))
     ap.add_argument("--trend", default="strict",
                     choices=["strict", "ties", "last-kept", "ties-last-kept"],
@@ -65,6 +68,9 @@ def parse():
                     help="skip the extra keys (exact trend, vs_plain, other workloads, serving)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving extra key")
     ap.add_argument("--no-tune", action="store_true", help="AUTO without the autotuner")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed steps by cudaProfilerStart/Stop (for ncu "
+                         "--profile-from-start off)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--jobs", type=int, default=0, help="serving: number of jobs (0 = 256)")
     ap.add_argument("--max-running", type=int, default=8, help="serving: concurrent jobs")
@@ -463,7 +469,8 @@ class Job:
     """One workload on one context: device inputs, pinned host copies, and one step of the hot
     path (upload -> evaluation sweep -> initial population + generations -> extraction)."""
 
-    def __init__(self, ebic, torch, w, dev, stream, mode, trend, gens, host_copies=True, ipw=0):
+    def __init__(self, ebic, torch, w, dev, stream, mode, trend, gens, host_copies=True, ipw=0,
+                 fuse_pairs=0):
         self.ebic, self.torch, self.w, self.gens = ebic, torch, w, gens
         self.x, self.truth, self.ci, self.off = synth_inputs(w)
         self.R, self.P = w.rows, len(self.off) - 1
@@ -476,7 +483,8 @@ class Job:
             self.x_h = torch.from_numpy(self.x).pin_memory()
             self.outs_h = [torch.zeros(self.P, dtype=torch.int32).pin_memory() for _ in range(3)]
             self.outs_h.append(torch.zeros(self.P, dtype=torch.int64).pin_memory())
-        self.params = ebic.Params.make(mode=MODES[mode], ipw=ipw, **run_fields(w, trend))
+        self.params = ebic.Params.make(mode=MODES[mode], ipw=ipw, fuse_pairs=fuse_pairs,
+                                       **run_fields(w, trend))
         self.ctx = ebic.Context(dev.index or 0, stream.cuda_stream)
         self.used_mode = 0
 
@@ -526,11 +534,16 @@ def synth_inputs(w):
     return _INPUTS[key]
 
 
-def timed_steps(job, stream, flush, steps, dist=None):
+def timed_steps(job, stream, flush, steps, dist=None, profile_range=False):
     """`steps` steps, each from a flushed L2 (the flush outside the events), CUDA events on the
-    library's stream; returns (total ms, units)."""
+    library's stream; returns (total ms, units).  profile_range: the steps are bracketed by
+    cudaProfilerStart / Stop, so that `ncu --profile-from-start off` captures only their
+    launches."""
     torch = job.torch
     total_ms, units = 0.0, 0
+    if profile_range:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
     for _ in range(steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -541,6 +554,8 @@ def timed_steps(job, stream, flush, steps, dist=None):
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
     torch.cuda.synchronize()
+    if profile_range:
+        torch.cuda.profiler.stop()
     return total_ms, units
 
 
@@ -729,7 +744,8 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     peak, peak_kind = load_peaks()
 
-    job = Job(ebic, torch, w, dev, stream, args.mode, args.trend, gens, ipw=args.ipw)
+    job = Job(ebic, torch, w, dev, stream, args.mode, args.trend, gens, ipw=args.ipw,
+              fuse_pairs=args.fuse_pairs)
     tune = job.tune() if args.mode == "auto" and not args.no_tune else None
     for _ in range(max(3, args.warmup)):
         job.step(False)
@@ -740,7 +756,8 @@ def main():
     clocks.start()
     job.ctx.profile_enable(True)        # reset the launch counters ...
     job.ctx.profile_enable(False)       # ... and time this pass without per-kernel events
-    total_ms, units = timed_steps(job, stream, flush, args.steps)
+    total_ms, units = timed_steps(job, stream, flush, args.steps,
+                                  profile_range=args.profile_range)
     st_all = job.ctx.profile_read(ebic.KERNEL_ALL)
     clk = clocks.stop()
     stats, passes = kernel_stats(job, stream, flush, args.steps)
@@ -817,6 +834,7 @@ def main():
     if tune is not None:
         line["config"]["autotune"] = {k: tune[k] for k in ("mode", "seg_direct", "seg_bitmap",
                                                           "seg_loop", "ipw_bitmap", "ipw_loop",
+                                                          "fuse_loop",
                                                           "direct_ms", "bitmap_ms", "build_ms",
                                                           "staged_ms")}
     if gens > 0:

@@ -117,7 +117,12 @@ typedef struct ebic_params {
   int32_t ipw;         /* individuals per work item of the staged bitmap form (bitmaps larger
                           than L2, ratio below 1): 0 (default) = the autotuner's choice, 1 when
                           untuned; 1-4 forces it.  Results never depend on it               */
-  int32_t reserved;    /* 0                                                                    */
+  int32_t fuse_pairs;  /* generation loop with the bitmap form: a child of at most this many
+                          column pairs whose pair test is exact (the ratio lets no pair fail,
+                          ceil(ratio * pairs) = pairs) is evaluated by the warp that built it,
+                          inside the evolve kernel; the other slots go to the evaluation
+                          launch.  0 (default) = the library's choice, -1 = never, 1-63 = this
+                          limit.  Results never depend on it                                */
 } ebic_params;
 
 /* Progress of a run (Sec. 2.4, steps 6 and 8). */
@@ -128,7 +133,9 @@ typedef struct ebic_run_report {
   int32_t n_top;       /* entries in the top rank list                                       */
   int64_t n_evaluated; /* individuals scored since the run was initialised                   */
   int32_t eval_mode;   /* evaluation form used: EBIC_MODE_DIRECT, _STAGED or _BITMAP         */
-  int32_t reserved;
+  int32_t fuse_pairs;  /* pair limit of the evaluation inside the evolve kernel in this call
+                          (0: none; see ebic_params.fuse_pairs)                              */
+  int64_t n_fused;     /* of n_evaluated, the individuals evaluated inside the evolve kernel */
 } ebic_run_report;
 
 /* Fills *p with the library defaults.  Never fails. */
@@ -205,8 +212,10 @@ EBIC_API int ebic_eval_population(ebic_ctx *ctx, const int32_t *col_idx, const i
  * then up to n_gen generations follow: elitism (step 4), penalised tournament, crossover and one
  * of insertion/deletion/substitution/swap with tabu-list rejection (step 5), the tabu-hit stop
  * test (step 6), scoring and top-list update (step 7).  Later calls continue the same run
- * (resuming is exact: all randomness is counter-based).  Changing any parameter but mode or
- * use_graph, or loading a matrix, starts a new run.  *rep (may be NULL) receives the progress.
+ * (resuming is exact: all randomness is counter-based).  Changing any parameter but mode,
+ * use_graph, ipw or fuse_pairs, or loading a matrix, starts a new run.  With the bitmap form,
+ * short children whose pair test is exact are evaluated inside the evolve kernel (fuse_pairs);
+ * the results are the same either way.  *rep (may be NULL) receives the progress.
  * Errors: EBIC_ESTATE (no matrix), EBIC_EINVAL (bad parameter), EBIC_ENOMEM, EBIC_ECUDA,
  * EBIC_ETIMEOUT.
  */
@@ -305,7 +314,9 @@ EBIC_API int ebic_profile_read(ebic_ctx *ctx, int32_t kernel, ebic_kernel_stats 
  * run state is reset afterwards, so the caller's next run starts from its initial population.
  * EBIC_MODE_AUTO follows the decisions in ebic_eval_population and ebic_run_generations until
  * a matrix of another shape is loaded (the measured times depend on the shape, not on the
- * values, so a reload of the same shape keeps them); p->ipw > 0 overrides the group size.
+ * values, so a reload of the same shape keeps them); p->ipw > 0 overrides the group size and
+ * p->fuse_pairs != 0 the loop's fusion limit (with the bitmap form, the loop measurement first
+ * picks that limit, then the work-item and group sizes).
  * Results never depend on the choice.  *rep (may be NULL) receives the measurements.
  * Errors: EBIC_ESTATE (no matrix), EBIC_EINVAL (bad population or parameter, n_ind < 1,
  * expected_sweeps < 1), EBIC_ENOMEM, EBIC_ECUDA.
@@ -321,6 +332,9 @@ typedef struct ebic_tune_report {
   double staged_ms;   /* best measured sweep of the staged direct form (-1 when not measured) */
   int32_t ipw_bitmap; /* chosen individuals per work item of the staged bitmap form (1-4)     */
   int32_t ipw_loop;   /* the same for the generation loop                                     */
+  int32_t fuse_loop;  /* chosen pair limit of the evaluation inside the evolve kernel (bitmap
+                         form; -1: none, 0: not measured); see ebic_params.fuse_pairs          */
+  int32_t reserved;
 } ebic_tune_report;
 
 EBIC_API int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_t *offsets,

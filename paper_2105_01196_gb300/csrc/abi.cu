@@ -118,8 +118,8 @@ int ebic_check_eval_params(ebic_ctx *ctx, const ebic_params *p) {
     return ebic_fail(ctx, EBIC_EINVAL, "non_strict and last_kept must be 0 or 1");
   if (p->last_kept && p->mode == EBIC_MODE_BITMAP)
     return ebic_fail(ctx, EBIC_EINVAL, "the last-kept pair test has no bitmap form");
-  if (p->ipw < 0 || p->ipw > 4 || p->reserved != 0)
-    return ebic_fail(ctx, EBIC_EINVAL, "ipw must be in [0, 4] and reserved 0");
+  if (p->ipw < 0 || p->ipw > 4 || p->fuse_pairs < -1 || p->fuse_pairs >= EBIC_MAX_LEN)
+    return ebic_fail(ctx, EBIC_EINVAL, "ipw must be in [0, 4] and fuse_pairs in [-1, 63]");
   return EBIC_OK;
 }
 

@@ -349,7 +349,8 @@ __device__ __forceinline__ void bitmap_staged_items(const EvalArgs &a, const Pop
   const int64_t Wst = a.Wst;
   const int64_t passes_total = (Wst + kPassWords - 1) / kPassWords;
   const int ipw = a.ipw;
-  const int32_t n_grp = (pv.n + ipw - 1) / ipw;
+  const int32_t n_ind = items::count(pv);
+  const int32_t n_grp = (n_ind + ipw - 1) / ipw;
   const int32_t n_side = items::move_chunks(a), n_all = n_side + n_grp * a.n_seg;
   const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
   const uint4 ones = make_uint4(kFull, kFull, kFull, kFull);
@@ -360,13 +361,14 @@ __device__ __forceinline__ void bitmap_staged_items(const EvalArgs &a, const Pop
       continue;
     }
     const int seg = (q - n_side) / n_grp, grp = (q - n_side) - seg * n_grp;  // segment-major
-    const int i0 = grp * ipw, cnt = min(ipw, pv.n - i0);
-    // lane j < cnt: individual i0 + j's bookkeeping
-    int myL = 0, myst = 0;
+    const int i0 = grp * ipw, cnt = min(ipw, n_ind - i0);
+    // lane j < cnt: individual i0 + j's bookkeeping (its slot myi)
+    int myL = 0, myst = 0, myi = 0;
     bool mydead = true;
     uint64_t myh = 0ull;
+    if (lane < cnt) myi = items::slot(pv, i0 + lane);
     if (lane < cnt) {
-      const int i = i0 + lane;
+      const int i = myi;
       if (pv.off) {
         myst = pv.off[i];
         myL = pv.off[i + 1] - myst;
@@ -383,7 +385,7 @@ __device__ __forceinline__ void bitmap_staged_items(const EvalArgs &a, const Pop
       if (j < cnt) {  // (cnt is the same in every lane)
         int c0, c1;
         if (!pv.off) {  // fixed-stride rows: the column words load with the lengths
-          const int st = (i0 + j) * pv.stride;
+          const int st = __shfl_sync(kFull, myi, j) * pv.stride;
           c0 = pv.cols[st + lane];
           c1 = pv.cols[st + 32 + lane];
         } else {
@@ -543,8 +545,8 @@ __device__ __forceinline__ void bitmap_staged_items(const EvalArgs &a, const Pop
         cp = __reduce_add_sync(kFull, cp);
         cn = __reduce_add_sync(kFull, cn);
         ca = __reduce_add_sync(kFull, ca);
+        const int i = __shfl_sync(kFull, myi, jc);
         if (lane == 0) {
-          const int i = i0 + jc;
           if (cp) atomicAdd(a.rows_pos + i, cp);
           if (cn) atomicAdd(a.rows_neg + i, cn);
           if (ca) atomicAdd(a.rows_any + i, ca);
@@ -553,7 +555,7 @@ __device__ __forceinline__ void bitmap_staged_items(const EvalArgs &a, const Pop
       }
       advance(jc, uc);
     }
-    items::insert_finish(pv, myins, myh, i0 + lane);
+    items::insert_finish(pv, myins, myh, myi);
   }
 }
 
@@ -579,7 +581,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
   }
   const int64_t Wst = a.Wst;
   const int64_t passes_total = (Wst + kPassWords - 1) / kPassWords;
-  const int32_t n_side = items::move_chunks(a), n_all = n_side + pv.n * a.n_seg;
+  const int32_t n_ind = items::count(pv);
+  const int32_t n_side = items::move_chunks(a), n_all = n_side + n_ind * a.n_seg;
   const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
   const uint4 ones = make_uint4(kFull, kFull, kFull, kFull);
   for (int q = items::first(); q < n_all; q = items::next(a.work, lane, q, n_all)) {
@@ -588,7 +591,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
       items::move_chunk(a, q, lane);
       continue;
     }
-    const int seg = (q - n_side) / pv.n, i = (q - n_side) - seg * pv.n;  // segment-major
+    const int seg = (q - n_side) / n_ind;  // segment-major
+    const int i = items::slot(pv, (q - n_side) - seg * n_ind);
     const items::Meta m = items::load_meta(pv, i, lane);
     if (items::stopped(pv)) return;  // (read with the item's loads; before any store)
     if (m.dead || m.L < 2) continue;
@@ -939,6 +943,7 @@ cudaError_t launch_eval_kernel(int mode, const EvalArgs &a0, const PopView &pv, 
     mode = EBIC_MODE_DIRECT;
   }
   if (mode == EBIC_MODE_BITMAP && a0.last_kept) return cudaErrorInvalidValue;  // no word form
+  if (pv.list && mode != EBIC_MODE_BITMAP) return cudaErrorInvalidValue;  // (bitmap kernels only)
   if (mode == EBIC_MODE_DIRECT && a0.codes) return launch_eval_codes(a0, pv, num_sms, s, pdl);
   EvalArgs a = a0;
   const bool bitmap = (mode == EBIC_MODE_BITMAP);

@@ -6,11 +6,16 @@
 // eight consecutive generations per starting parity) and replayed:
 //   k_evolve    one block per slot, one warp per tabu attempt: elites from the top list (step
 //               4), otherwise penalised tournament, optional one-point crossover and one
-//               mutation, tabu probe; the lowest attempt that misses the tabu list wins (step 5);
+//               mutation, tabu probe; the lowest attempt that misses the tabu list wins (step 5).
+//               With the bitmap form, a live child whose pair test is exact and that has few
+//               pairs is evaluated right there by the winning warp (step 7), which also enters
+//               its key into the generation's duplicate table; the other live slots are listed
+//               for the evaluation launch;
 //   k_eval_*    the persistent evaluation kernel (eval.cu, codes.cu) over the new population,
-//               skipping tabu-dead slots (step 7); it also enters the live keys into this
-//               generation's duplicate table, inserts the previous generation's live keys into
-//               the hashed tabu list and clears that generation's duplicate table;
+//               or over the listed slots, skipping tabu-dead slots (step 7); it also enters the
+//               live keys it evaluates into this generation's duplicate table, inserts the
+//               previous generation's live keys into the hashed tabu list and clears that
+//               generation's duplicate table;
 //   k_finish    all blocks: final dead flags (tabu or duplicate), tabu hits, fitness, candidates
 //               for the top list; then the last block to finish: tabu-hit stop test (step 6),
 //               top rank list update (step 7), column usage, counters for the next generation.
@@ -52,10 +57,17 @@ struct GenCtl {
   int32_t live_cur;    // live slots of the generation being scored
   int32_t n_cand;      // top-list candidates collected by k_finish
   int32_t done;        // blocks of k_finish that have finished their slots
+  int32_t n_todo;      // slots the evolve kernel left to the evaluation launch (its list)
+  int32_t fused_cur;   // live slots of the generation being scored evaluated by the evolve kernel
+  int32_t evo_next;    // slots k_evolve_seq's warps have taken beyond their first
+  int32_t pad;
   long long n_evaluated;
   long long tabu_count;
   long long sum_len;   // sum of the lengths of all scored live slots (evaluation work)
   long long len_cur;   // the same for the generation being scored
+  long long n_fused;   // of n_evaluated, the slots the evolve kernel evaluated
+  long long fused_len; // the sum of their lengths
+  long long flen_cur;  // the same for the generation being scored
 };
 
 // One population buffer (P slots of stride kS).
@@ -83,6 +95,12 @@ struct GenArgs {
   uint64_t seed;
   int32_t P, C, K, E, T, A, max_len, init_min, init_max;
   int32_t min_rows, col_cap, ov_num, ov_den, tabu_limit;
+  // Evaluation inside the evolve kernel (fuse_np > 0, bitmap form): the pair words, the test's
+  // variant and ratio, and the list of the slots left to the evaluation launch (ctl->n_todo).
+  const uint32_t *bitmap;  // [C][C][Wst]
+  int64_t Wst, R;
+  int32_t neg, ns, rnum, rden, fuse_np;
+  int32_t *todo;
 };
 
 // Waits for the preceding kernel of a programmatic launch (no-op otherwise).
@@ -503,6 +521,170 @@ __device__ void w_make_child(const GenArgs &ga, const Buf &pb, int g, int s, int
   w_mutate(st, c, L, ga.C, ga.max_len, lane);
 }
 
+// ------------------------------------------------------- evaluation inside the evolve kernel
+//
+// A child whose pair test is exact - the threshold ceil(ratio * pairs) equals its number of
+// pairs, so a row must satisfy every pair (Sec. 2.2) - and that has at most fuse_np pairs is
+// evaluated by the warp that built it, on the pair bitmap G (bit j of word w of row a * C + b:
+// row 32 w + j has key(b) > key(a)).  A row follows the positive trend when every pair's word has
+// its bit, the negative trend when every reversed pair's word has it (ties counting both ways:
+// the complements of the opposite words, pad rows masked).  One unit is one pair row's 128 words
+// of one pass (16 bytes per lane); units are copied asynchronously into the warp's shared region,
+// two groups of kFuseGroup in flight, and each lane reads back only the bytes it copied.
+constexpr int kFuseGroup = 4;               // units per copy group
+constexpr int kFuseSlots = 2 * kFuseGroup;  // units staged per warp
+constexpr int kFuseWords = 128;             // words of one unit
+
+__device__ __forceinline__ void fuse_copy16(uint32_t *dst, const uint32_t *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"((uint64_t)__cvta_generic_to_global(src))
+               : "memory");
+}
+
+__device__ __forceinline__ void fuse_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Waits until at most N of this thread's copy groups are pending (a hardware wait).
+template <int N>
+__device__ __forceinline__ void fuse_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ uint4 fuse_and(uint4 a, uint4 b) {
+  return make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+}
+
+__device__ __forceinline__ int fuse_popc(uint4 v) {
+  return __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+}
+
+// Rows of word w that exist (bit j: row 32 w + j < R).
+__device__ __forceinline__ uint32_t fuse_valid(int64_t w, int64_t R) {
+  const int64_t n = R - 32 * w;
+  return n >= 32 ? kFull : (n <= 0 ? 0u : ((1u << n) - 1u));
+}
+
+// Whether the evolve kernel evaluates a live child of L columns itself.
+__device__ __forceinline__ bool fuse_child(const GenArgs &ga, int L) {
+  const int np = L - 1;
+  return np <= ga.fuse_np && (ga.rnum * np + ga.rden - 1) / ga.rden == np;
+}
+
+// Row counts (positive trend, negative trend, either) of the exact test of c[0 .. L-1] (L >= 2),
+// in every lane.  stage: the warp's kFuseSlots * kFuseWords words of shared memory (16-byte
+// aligned), free for this call.
+__device__ void w_eval_exact(const GenArgs &ga, const int32_t *c, int L, uint32_t *stage,
+                             int lane, int &rp, int &rn, int &ra) {
+  const int np = L - 1;
+  const bool neg = ga.neg != 0, ns = ga.ns != 0;
+  const int upp = neg ? 2 * np : np;  // units per pass: pair j's positive (then negative) row
+  const int64_t Wst = ga.Wst;
+  const int passes = (int)((Wst + kFuseWords - 1) / kFuseWords);
+  const int n_groups = (passes * upp + kFuseGroup - 1) / kFuseGroup;
+  // lane l: the word rows of pairs l and l + 32 (pair j = (c[j], c[j + 1])), positive and
+  // negative direction
+  uint32_t row_p[2] = {0u, 0u}, row_n[2] = {0u, 0u};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int j = lane + 32 * h;
+    if (j < np) {
+      const uint32_t a = (uint32_t)c[j], b = (uint32_t)c[j + 1], C = (uint32_t)ga.C;
+      row_p[h] = ns ? b * C + a : a * C + b;
+      row_n[h] = ns ? a * C + b : b * C + a;
+    }
+  }
+  int iq = 0, ir = 0;  // next unit to copy: pass, unit within the pass
+  auto issue_group = [&](int gi) {
+#pragma unroll
+    for (int k = 0; k < kFuseGroup; ++k) {
+      if (iq < passes) {
+        const int j = neg ? (ir >> 1) : ir, h = j >> 5;  // (the same in every lane)
+        const bool nd = neg && (ir & 1);
+        const uint32_t row =
+            __shfl_sync(kFull, h ? (nd ? row_n[1] : row_p[1]) : (nd ? row_n[0] : row_p[0]),
+                        j & 31);
+        const int64_t w = (int64_t)iq * kFuseWords + lane * 4;
+        if (w < Wst)  // (Wst is a multiple of 4: a lane's 4 words all exist or not)
+          fuse_copy16(stage + ((gi & 1) * kFuseGroup + k) * kFuseWords + lane * 4,
+                      ga.bitmap + (int64_t)row * Wst + w);
+        if (++ir == upp) {
+          ir = 0;
+          ++iq;
+        }
+      }
+    }
+    fuse_commit();
+  };
+  const uint4 ones = make_uint4(kFull, kFull, kFull, kFull), zero4 = make_uint4(0u, 0u, 0u, 0u);
+  uint4 ap = ones, an = ones;
+  int cq = 0, cr = 0, cp = 0, cn = 0, ca = 0;
+  __syncwarp();  // every lane's earlier use of the region is done
+  issue_group(0);
+  if (n_groups > 1) issue_group(1);
+  for (int gi = 0; gi < n_groups; ++gi) {
+    if (gi + 1 < n_groups)
+      fuse_wait<1>();
+    else
+      fuse_wait<0>();
+#pragma unroll
+    for (int k = 0; k < kFuseGroup; ++k) {
+      if (cq < passes) {
+        const int64_t w = (int64_t)cq * kFuseWords + lane * 4;
+        const bool act = w < Wst;
+        if (act) {
+          uint4 v = *reinterpret_cast<const uint4 *>(
+              stage + ((gi & 1) * kFuseGroup + k) * kFuseWords + lane * 4);
+          if (ns) v = make_uint4(~v.x, ~v.y, ~v.z, ~v.w);
+          if (neg && (cr & 1))
+            an = fuse_and(an, v);
+          else
+            ap = fuse_and(ap, v);
+        }
+        if (++cr == upp) {  // the pass is complete
+          uint4 pos = act ? ap : zero4, ng = (neg && act) ? an : zero4;
+          if (ns && act) {
+            const uint4 vm = make_uint4(fuse_valid(w, ga.R), fuse_valid(w + 1, ga.R),
+                                        fuse_valid(w + 2, ga.R), fuse_valid(w + 3, ga.R));
+            pos = fuse_and(pos, vm);
+            ng = fuse_and(ng, vm);
+          }
+          cp += fuse_popc(pos);
+          cn += fuse_popc(ng);
+          ca += fuse_popc(make_uint4(pos.x | ng.x, pos.y | ng.y, pos.z | ng.z, pos.w | ng.w));
+          ap = ones;
+          an = ones;
+          cr = 0;
+          ++cq;
+        }
+      }
+    }
+    if (gi + 2 < n_groups) issue_group(gi + 2);
+  }
+  rp = __reduce_add_sync(kFull, cp);
+  rn = __reduce_add_sync(kFull, cn);
+  ra = __reduce_add_sync(kFull, ca);
+}
+
+// The end of a live slot s's evolve step when fusion is on: the slot is evaluated here (its
+// counts stored, its key entered in generation g's duplicate table, as the evaluation launch
+// would) or listed for the evaluation launch.  Returns whether it was evaluated.
+__device__ bool fuse_or_list(const GenArgs &ga, const int32_t *c, int L, uint64_t h, int s,
+                             int par, uint32_t *stage, int lane) {
+  if (fuse_child(ga, L)) {
+    int rp, rn, ra;
+    w_eval_exact(ga, c, L, stage, lane, rp, rn, ra);
+    if (lane == 0) {
+      ga.rows_scr[s] = rp;
+      ga.rows_scr[ga.P + s] = rn;
+      ga.rows_scr[2 * ga.P + s] = ra;
+      dedup_insert(ga.dkeys[par], ga.dslot[par], ga.dmask, h, s);
+    }
+    return true;
+  }
+  if (lane == 0) ga.todo[atomicAdd(&ga.ctl->n_todo, 1)] = s;
+  return false;
+}
+
 // Step 1: the initial population, one warp per slot (generation 0, attempt 0 of the word
 // stream): length init_min + below(init_max - init_min + 1), then that many columns, each by at
 // most 64 draws that avoid the columns already present (the chromosome ends early when all 64
@@ -539,11 +721,16 @@ __global__ void __launch_bounds__(kInitWarps * 32) k_init(GenArgs ga, Buf nb) {
 // lowest attempt whose key misses the tabu list wins, which is exactly the sequential retry
 // rule; when every attempt hits, the slot is dead and keeps the last attempt's child.
 constexpr int kMaxAttemptWarps = 16;
-// Per-warp shared memory of k_evolve, in ints: 8 tournament scratch rows, the two parents and the
-// child (kS + 1 used).  Every part starts on a 16-byte boundary (the scratch rows are written with
-// 16-byte stores), and the total is a multiple of 16 bytes.
-constexpr int kEvoScratch = 0, kEvoA = 8 * kS, kEvoB = 9 * kS, kEvoChild = 10 * kS;
-constexpr int kEvolveWarpInts = 10 * kS + kS + 4;
+// Per-warp shared memory of k_evolve, in ints: the child (kS + 1 used), then 8 tournament scratch
+// rows and the two parents; once the child is final, the region after it stages the pair words
+// of its evaluation (kFuseSlots units).  Every part starts on a 16-byte boundary (the scratch
+// rows are written with 16-byte stores, the staged units by 16-byte copies), and the total is a
+// multiple of 16 bytes.
+constexpr int kEvoChild = 0, kEvoScratch = kS + 4, kEvoA = kEvoScratch + 8 * kS,
+              kEvoB = kEvoA + kS, kEvoStage = kEvoScratch;
+constexpr int kEvolveWarpInts =
+    kEvoScratch + (10 * kS > kFuseSlots * kFuseWords ? 10 * kS : kFuseSlots * kFuseWords);
+static_assert(kEvoScratch % 4 == 0, "scratch rows and staged units start on 16-byte boundaries");
 // Matrices of up to this many columns have k_evolve's column-usage table in shared memory.
 constexpr int kUsageSmemMax = 4096;
 // Warps of k_evolve one SM holds at once (its registers allow 32).
@@ -585,6 +772,7 @@ __global__ void __launch_bounds__(kMaxAttemptWarps * 32) k_evolve(GenArgs ga, Bu
         nb.hash[s] = e.h;
         nb.att_dead[s] = 0;
         nb.att_hits[s] = 0;
+        if (ga.fuse_np > 0) ga.todo[atomicAdd(&ga.ctl->n_todo, 1)] = s;
       }
     }
     return;
@@ -616,21 +804,29 @@ __global__ void __launch_bounds__(kMaxAttemptWarps * 32) k_evolve(GenArgs ga, Bu
   if (a != win) return;
   out[lane] = lane < L ? c[lane] : 0;
   out[lane + 32] = lane + 32 < L ? c[lane + 32] : 0;
+  const bool fused = !dead && ga.fuse_np > 0 &&
+                     fuse_or_list(ga, c, L, h, s, par,
+                                  reinterpret_cast<uint32_t *>(base + kEvoStage), lane);
   if (lane == 0) {
     nb.len[s] = L;
     nb.hash[s] = h;
-    nb.att_dead[s] = dead;
-    nb.att_hits[s] = dead ? ga.A : win;  // (the evaluation launch enters live keys in D[par])
+    // 1: dead; 2: live and evaluated here; 0: live, left to the evaluation launch (which enters
+    // the live keys in D[par])
+    nb.att_dead[s] = dead ? 1 : (fused ? 2 : 0);
+    nb.att_hits[s] = dead ? ga.A : win;
   }
 }
 
-// The same step for large populations, one warp per slot and kSeqWarps slots per block: a
-// slot's attempts run one after the other in its warp, until one misses the tabu list, which is
-// the retry rule itself (the lowest missing attempt wins; all A hit: the slot is dead with the
-// last attempt's child).  Parallel attempt warps only shorten a slot's latency; when the launch
-// has more slots than the GPU holds at once, the slots themselves fill it, and a warp per slot
-// keeps four times as many of them in flight.  The block's slots share one copy of the
-// column-usage table.
+// The same step for large populations, one warp per slot: a slot's attempts run one after the
+// other in its warp, until one misses the tabu list, which is the retry rule itself (the lowest
+// missing attempt wins; all A hit: the slot is dead with the last attempt's child).  Parallel
+// attempt warps only shorten a slot's latency; when the launch has more slots than the GPU holds
+// at once, the slots themselves fill it, and a warp per slot keeps four times as many of them in
+// flight.  The launch is persistent: as many blocks of kSeqWarps warps as are resident at once,
+// each warp taking its first slot by its index and later ones from a counter as it finishes, so
+// warps building children (dependent loads, little traffic) and warps evaluating them (pair-word
+// streams) overlap instead of alternating in waves of blocks.  The block's warps share one copy
+// of the column-usage table.
 constexpr int kSeqWarps = 8;
 
 __global__ void __launch_bounds__(kSeqWarps * 32) k_evolve_seq(GenArgs ga, Buf pb, Buf nb,
@@ -645,50 +841,60 @@ __global__ void __launch_bounds__(kSeqWarps * 32) k_evolve_seq(GenArgs ga, Buf p
     usage = s_usage;
   }
   if (stopped) return;
-  __syncthreads();
+  __syncthreads();  // (no block-wide operation follows)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int s = blockIdx.x * kSeqWarps + w;
-  if (s >= ga.P) return;  // (no block-wide operation follows)
+  const int W = (int)gridDim.x * kSeqWarps;
   const int g = gen + 1;
   const int n_el = min(ga.E, n_top);
-  int32_t *out = nb.cols + (size_t)s * kS;
-  if (s < n_el) {  // elitism: copy top-list entry s (its key is already in the tabu list)
-    const TopEntry &e = ga.top[s];
-    out[lane] = lane < e.len ? e.cols[lane] : 0;
-    out[lane + 32] = lane + 32 < e.len ? e.cols[lane + 32] : 0;
-    if (lane == 0) {
-      nb.len[s] = e.len;
-      nb.hash[s] = e.h;
-      nb.att_dead[s] = 0;
-      nb.att_hits[s] = 0;
-    }
-    return;
-  }
   int32_t *base = s_evo + w * kEvolveWarpInts;
   int32_t *scratch = base + kEvoScratch, *A = base + kEvoA, *B = base + kEvoB;
   int32_t *c = base + kEvoChild;
-  int L = 0, win = -1;
-  uint64_t h = 0ull;
-  for (int a = 0; a < ga.A; ++a) {
-    w_make_child(ga, pb, g, s, a, c, scratch, A, B, L, lane, usage);
-    h = chromosome_key(c, L);
-    // lane 0 probes the hashed tabu list, lane 1 generation g-1's live keys
-    const bool hit = (lane == 0 && tabu_contains(ga.tabu, ga.tmask, h)) ||
-                     (lane == 1 && tabu_contains(ga.dkeys[par ^ 1], ga.dmask, h));
-    if (!__any_sync(kFull, hit)) {
-      win = a;
-      break;
+  for (int s = blockIdx.x * kSeqWarps + w; s < ga.P;) {
+    int32_t *out = nb.cols + (size_t)s * kS;
+    if (s < n_el) {  // elitism: copy top-list entry s (its key is already in the tabu list)
+      const TopEntry &e = ga.top[s];
+      out[lane] = lane < e.len ? e.cols[lane] : 0;
+      out[lane + 32] = lane + 32 < e.len ? e.cols[lane + 32] : 0;
+      if (lane == 0) {
+        nb.len[s] = e.len;
+        nb.hash[s] = e.h;
+        nb.att_dead[s] = 0;
+        nb.att_hits[s] = 0;
+        if (ga.fuse_np > 0) ga.todo[atomicAdd(&ga.ctl->n_todo, 1)] = s;
+      }
+    } else {
+      int L = 0, win = -1;
+      uint64_t h = 0ull;
+      for (int a = 0; a < ga.A; ++a) {
+        w_make_child(ga, pb, g, s, a, c, scratch, A, B, L, lane, usage);
+        h = chromosome_key(c, L);
+        // lane 0 probes the hashed tabu list, lane 1 generation g-1's live keys
+        const bool hit = (lane == 0 && tabu_contains(ga.tabu, ga.tmask, h)) ||
+                         (lane == 1 && tabu_contains(ga.dkeys[par ^ 1], ga.dmask, h));
+        if (!__any_sync(kFull, hit)) {
+          win = a;
+          break;
+        }
+      }
+      const bool dead = win < 0;
+      __syncwarp();
+      out[lane] = lane < L ? c[lane] : 0;
+      out[lane + 32] = lane + 32 < L ? c[lane + 32] : 0;
+      const bool fused = !dead && ga.fuse_np > 0 &&
+                         fuse_or_list(ga, c, L, h, s, par,
+                                      reinterpret_cast<uint32_t *>(base + kEvoStage), lane);
+      if (lane == 0) {
+        nb.len[s] = L;
+        nb.hash[s] = h;
+        nb.att_dead[s] = dead ? 1 : (fused ? 2 : 0);  // (as in k_evolve)
+        nb.att_hits[s] = dead ? ga.A : win;
+      }
     }
-  }
-  const bool dead = win < 0;
-  __syncwarp();
-  out[lane] = lane < L ? c[lane] : 0;
-  out[lane + 32] = lane + 32 < L ? c[lane + 32] : 0;
-  if (lane == 0) {
-    nb.len[s] = L;
-    nb.hash[s] = h;
-    nb.att_dead[s] = dead;
-    nb.att_hits[s] = dead ? ga.A : win;  // (the evaluation launch enters live keys in D[par])
+    if (W >= ga.P) break;  // (every slot was some warp's first)
+    int nx = 0;
+    if (lane == 0) nx = atomicAdd(&ga.ctl->evo_next, 1);
+    s = __shfl_sync(kFull, nx, 0) + W;
+    __syncwarp();  // (the region's last reads are done before the next slot writes it)
   }
 }
 
@@ -988,14 +1194,16 @@ __device__ int sort_and_process(const GenArgs &ga, const Buf &nb, const TopSmem 
 // A slot's inputs to scoring: every load first, then the duplicate lookup (probed whatever
 // the dead flag says, so that its loads need not wait for it).
 struct SlotIn {
-  bool att_dead, in_dup;
+  bool att_dead, fused, in_dup;
   uint64_t h;
   int L, ah, rp, rn, ra;
 };
 
 __device__ __forceinline__ SlotIn load_slot(const GenArgs &ga, const Buf &nb, int par, int s) {
   SlotIn in;
-  in.att_dead = nb.att_dead[s] != 0;
+  const uint8_t ad = nb.att_dead[s];  // 1: dead; 2: live, evaluated by the evolve kernel
+  in.att_dead = ad == 1;
+  in.fused = ad == 2;
   in.h = nb.hash[s];
   in.L = nb.len[s];
   in.ah = nb.att_hits[s];
@@ -1010,7 +1218,7 @@ __device__ __forceinline__ SlotIn load_slot(const GenArgs &ga, const Buf &nb, in
 // scores a share of the slots; the last block to finish then runs the single-block part.
 __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, int par) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_hits, s_live, s_lsum, s_last, s_n, s_cnt, s_stop, s_nc;
+  __shared__ int s_hits, s_live, s_lsum, s_fused, s_flsum, s_last, s_n, s_cnt, s_stop, s_nc;
   GenCtl *ctl = ga.ctl;
   wait_prior_grid();
   // The counters, the list's last entry and this thread's first slot are loaded in one round,
@@ -1041,6 +1249,8 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
     s_hits = 0;
     s_live = 0;
     s_lsum = 0;
+    s_fused = 0;
+    s_flsum = 0;
     s_nc = 0;
   }
   __syncthreads();
@@ -1051,7 +1261,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
   // list they are skipped as duplicates, and an entry evicted by a better candidate fails the
   // same overlap test as its copy would, so leaving them out changes nothing.
   const int n_el = gen0 < 0 ? 0 : min(ga.E, n0);
-  int hits = 0, live = 0, lsum = 0;
+  int hits = 0, live = 0, lsum = 0, fused = 0, flsum = 0;
   for (int s = tid; s < ga.P; s += stride) {
     const SlotIn in = s == tid ? first : load_slot(ga, nb, par, s);
     const bool att_dead = in.att_dead;
@@ -1072,6 +1282,8 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
     hits += ah + (dup ? 1 : 0);
     live += !dead;
     lsum += dead ? 0 : L;
+    fused += (!dead && in.fused) ? 1 : 0;
+    flsum += (!dead && in.fused) ? L : 0;
     if (s >= n_el && !dead && f > 0ull && (!had_threshold || key_before(f, h, tf, th))) {
       if (single) {  // at most P <= sort_cap candidates
         const int q = atomicAdd(&s_nc, 1);
@@ -1089,18 +1301,24 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
   hits = __reduce_add_sync(kFull, hits);
   live = __reduce_add_sync(kFull, live);
   lsum = __reduce_add_sync(kFull, lsum);
+  fused = __reduce_add_sync(kFull, fused);
+  flsum = __reduce_add_sync(kFull, flsum);
   if ((threadIdx.x & 31) == 0) {
     if (hits) atomicAdd(&s_hits, hits);
     if (live) atomicAdd(&s_live, live);
     if (lsum) atomicAdd(&s_lsum, lsum);
+    if (fused) atomicAdd(&s_fused, fused);
+    if (flsum) atomicAdd(&s_flsum, flsum);
   }
   __syncthreads();
-  int hits_g, live_g, nc;
-  long long len_g;
+  int hits_g, live_g, nc, fused_g;
+  long long len_g, flen_g;
   if (single) {
     hits_g = s_hits;
     live_g = s_live;
     len_g = s_lsum;
+    fused_g = s_fused;
+    flen_g = s_flsum;
     nc = s_nc;
   } else {
     if (threadIdx.x == 0) {
@@ -1109,6 +1327,10 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
       if (s_lsum)
         atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->len_cur),
                   (unsigned long long)s_lsum);
+      if (s_fused) atomicAdd(&ctl->fused_cur, s_fused);
+      if (s_flsum)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->flen_cur),
+                  (unsigned long long)s_flsum);
       __threadfence();
       s_last = atomicAdd(&ctl->done, 1) == (int)gridDim.x - 1;
     }
@@ -1118,6 +1340,8 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
     hits_g = __ldcg(&ctl->hits_cur);
     live_g = __ldcg(&ctl->live_cur);
     len_g = __ldcg(&ctl->len_cur);
+    fused_g = __ldcg(&ctl->fused_cur);
+    flen_g = __ldcg(&ctl->flen_cur);
     nc = __ldcg(&ctl->n_cand);
   }
 
@@ -1129,6 +1353,8 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
       ctl->stopped = 1;
       ctl->n_evaluated += live_g;          // the generation was evaluated, then discarded
       ctl->sum_len += len_g;
+      ctl->n_fused += fused_g;
+      ctl->fused_len += flen_g;
     }
     return;
   }
@@ -1138,9 +1364,15 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
       ctl->gen += 1;
       ctl->n_evaluated += live_g;
       ctl->sum_len += len_g;
+      ctl->n_fused += fused_g;
+      ctl->fused_len += flen_g;
       ctl->len_cur = 0;
       ctl->hits_cur = 0;
       ctl->live_cur = 0;
+      ctl->fused_cur = 0;
+      ctl->flen_cur = 0;
+      ctl->n_todo = 0;
+      ctl->evo_next = 0;
       ctl->n_cand = 0;
       ctl->done = 0;
       *ga.work = 0;
@@ -1194,9 +1426,15 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
     ctl->gen += 1;
     ctl->n_evaluated += live_g;
     ctl->sum_len += len_g;
+    ctl->n_fused += fused_g;
+    ctl->fused_len += flen_g;
     ctl->len_cur = 0;
     ctl->hits_cur = 0;
     ctl->live_cur = 0;
+    ctl->fused_cur = 0;
+    ctl->flen_cur = 0;
+    ctl->n_todo = 0;
+    ctl->evo_next = 0;
     ctl->n_cand = 0;
     ctl->done = 0;
     *ga.work = 0;
@@ -1256,8 +1494,10 @@ struct GenState {
   const void *graph_buf = nullptr;  // codes or bitmap the captured graphs read (null: keys)
   DevBuf cols[2], len[2], att_hits[2], rows[2], att_dead[2], dead[2], hash[2], fit[2];
   DevBuf dkeys[2], dslot[2];
-  DevBuf rows_scr, work, tabu, top, ctl, usage, cand_f, cand_h, cand_s, extract;
+  DevBuf rows_scr, work, tabu, top, ctl, usage, cand_f, cand_h, cand_s, extract, todo;
   uint32_t tcap = 0, dcap = 0, ccap = 0;
+  int fuse_np = 0;  // pair limit of the evaluation inside the evolve kernel (0: none)
+  int seq_blocks = 1;  // blocks of the persistent k_evolve_seq launch
   int32_t sort_cap = 0;
   int finish_blocks = 1;
   size_t top_smem = 0;
@@ -1293,7 +1533,7 @@ struct GenState {
     for (cudaEvent_t e : cap_ev)
       if (e) cudaEventDestroy(e);
     DevBuf *all[] = {&rows_scr, &work, &tabu, &dkeys[0], &dslot[0], &dkeys[1], &dslot[1], &top,
-                     &ctl, &usage, &cand_f, &cand_h, &cand_s, &extract};
+                     &ctl, &usage, &cand_f, &cand_h, &cand_s, &extract, &todo};
     for (DevBuf *b : all) b->release();
     for (int k = 0; k < 2; ++k) {
       DevBuf *bs[] = {&cols[k], &len[k], &att_hits[k], &rows[k], &att_dead[k], &dead[k],
@@ -1332,7 +1572,8 @@ bool same_run_params(const ebic_params &a, const ebic_params &b) {
   ebic_params x = a, y = b;
   x.mode = y.mode = 0;
   x.use_graph = y.use_graph = 0;
-  x.ipw = y.ipw = 0;  // (a performance choice, like the two above)
+  x.ipw = y.ipw = 0;  // (performance choices, like the two above)
+  x.fuse_pairs = y.fuse_pairs = 0;
   return memcmp(&x, &y, sizeof(x)) == 0;
 }
 
@@ -1371,6 +1612,17 @@ GenArgs gen_args(ebic_ctx *ctx, GenState *g) {
   ga.ov_num = p.overlap_num;
   ga.ov_den = p.overlap_den;
   ga.tabu_limit = p.tabu_hit_limit;
+  if (g->fuse_np > 0) {
+    ga.bitmap = ctx->bitmap.as<uint32_t>();
+    ga.Wst = ctx->Wst;
+    ga.R = ctx->R;
+    ga.neg = p.neg_trends;
+    ga.ns = p.non_strict;
+    ga.rnum = p.ratio_num;
+    ga.rden = p.ratio_den;
+    ga.fuse_np = g->fuse_np;
+    ga.todo = g->todo.as<int32_t>();
+  }
   return ga;
 }
 
@@ -1409,7 +1661,9 @@ EvalArgs gen_eval_args(ebic_ctx *ctx, GenState *g, int k, bool has_prev) {
   return a;
 }
 
-PopView gen_view(GenState *g, int k) {
+// The population of buffer k; with `listed`, only the slots the evolve kernel left to the
+// evaluation launch.
+PopView gen_view(GenState *g, int k, bool listed) {
   PopView v{};
   v.cols = g->cols[k].as<int32_t>();
   v.len = g->len[k].as<int32_t>();
@@ -1421,6 +1675,10 @@ PopView gen_view(GenState *g, int k) {
   v.dkeys = g->dkeys[k].as<uint64_t>();
   v.dslot = g->dslot[k].as<uint32_t>();
   v.dmask = g->dcap - 1;
+  if (listed) {
+    v.list = g->todo.as<int32_t>();
+    v.list_n = &g->ctl.as<GenCtl>()->n_todo;
+  }
   return v;
 }
 
@@ -1484,8 +1742,10 @@ cudaError_t launch_scoring(ebic_ctx *ctx, GenState *g, int k, bool has_prev, cud
                            Marks *m) {
   cudaError_t e;
   if ((e = mark(s, m, 1)) != cudaSuccess) return e;
-  if ((e = launch_eval_kernel(g->eval_mode, gen_eval_args(ctx, g, k, has_prev), gen_view(g, k),
-                              ctx->num_sms, s, true)) != cudaSuccess)
+  // (the initial population has no evolve step: all of it is evaluated here)
+  const bool listed = has_prev && g->fuse_np > 0;
+  if ((e = launch_eval_kernel(g->eval_mode, gen_eval_args(ctx, g, k, has_prev),
+                              gen_view(g, k, listed), ctx->num_sms, s, true)) != cudaSuccess)
     return e;
   if ((e = mark(s, m, 2)) != cudaSuccess) return e;
   if ((e = launch_pdl(k_finish, dim3(g->finish_blocks), dim3(kTopThreads), g->top_smem, s,
@@ -1505,7 +1765,7 @@ cudaError_t launch_generation(ebic_ctx *ctx, GenState *g, int parity, cudaStream
     e = launch_pdl(k_evolve, dim3((unsigned)g->P), dim3(G * 32), evolve_smem(G, g->C), s,
                    gen_args(ctx, g), g->buf(parity ^ 1), g->buf(parity), parity);
   } else {
-    e = launch_pdl(k_evolve_seq, dim3((unsigned)((g->P + kSeqWarps - 1) / kSeqWarps)),
+    e = launch_pdl(k_evolve_seq, dim3((unsigned)g->seq_blocks),
                    dim3(kSeqWarps * 32), evolve_smem(kSeqWarps, g->C), s, gen_args(ctx, g),
                    g->buf(parity ^ 1), g->buf(parity), parity);
   }
@@ -1611,6 +1871,7 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
     GEN_ALLOC(g->fit[k], P * 8);
   }
   GEN_ALLOC(g->rows_scr, P * 3 * 4);
+  GEN_ALLOC(g->todo, P * 4);
   GEN_ALLOC(g->work, 64);
   g->dcap = (uint32_t)dedup_capacity(P);
   for (int k = 0; k < 2; ++k) {
@@ -1643,6 +1904,13 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
   EBIC_CHECK_CUDA(ctx, cudaFuncSetAttribute(k_evolve_seq,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)evolve_smem(kSeqWarps, kUsageSmemMax)));
+  int seq_per_sm = 0;
+  EBIC_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                           &seq_per_sm, k_evolve_seq, kSeqWarps * 32,
+                           evolve_smem(kSeqWarps, ctx->C)));
+  g->seq_blocks = (int)std::max<int64_t>(
+      1, std::min<int64_t>((g->P + kSeqWarps - 1) / kSeqWarps,
+                           (int64_t)ctx->num_sms * std::max(seq_per_sm, 1)));
 
   // one block per 2,048 slots: the slot loop spread, few blocks to meet at the end (measured:
   // one block for P = 800, 8.4 against 10.2 us with two; two for P = 4,096, 13.6 against 15.2 us)
@@ -1686,6 +1954,22 @@ int ensure_tabu(ebic_ctx *ctx, GenState *g, int64_t need) {
   return EBIC_OK;
 }
 
+// Pair limit of the evaluation inside the evolve kernel (0: none): the caller's, else the
+// autotuner's, else the largest pair count whose staged units (pairs x directions x passes of 128 words) stay within
+// kFuseDefaultUnits, so that evaluating a child keeps its warp about as long as building it
+// did.  Only the bitmap form has it.
+constexpr int64_t kFuseDefaultUnits = 64;
+
+int fuse_limit(const ebic_ctx *ctx, int mode, const ebic_params *p) {
+  if (mode != EBIC_MODE_BITMAP || p->fuse_pairs < 0 || p->last_kept) return 0;
+  if (p->fuse_pairs > 0) return p->fuse_pairs;
+  // (the autotuner's limit, measured in the loop with this form)
+  if (ctx->tuned && ctx->tuned_mode == mode && ctx->fuse_loop != 0)
+    return ctx->fuse_loop > 0 ? ctx->fuse_loop : 0;
+  const int64_t per_pair = (ctx->Wst + 127) / 128 * (p->neg_trends ? 2 : 1);
+  return (int)std::min<int64_t>(EBIC_MAX_LEN - 1, kFuseDefaultUnits / per_pair);
+}
+
 int ensure_eval_ready(ebic_ctx *ctx, GenState *g, const ebic_params *p, int n_gen) {
   int mode = choose_mode(ctx, p->mode, g->P, 0.5 * (p->init_min_len + p->max_len), n_gen + 1,
                          p->last_kept);
@@ -1696,11 +1980,14 @@ int ensure_eval_ready(ebic_ctx *ctx, GenState *g, const ebic_params *p, int n_ge
   // the captured graphs hold the evaluation kernel's data buffer: recapture when it changed
   const void *buf = mode == EBIC_MODE_BITMAP ? ctx->bitmap.p
                     : (direct && ctx->codes_ready ? ctx->codes.p : nullptr);
-  if (mode != g->eval_mode || buf != g->graph_buf) {
+  // (and the fusion limit, which the captured evolve launches hold)
+  const int fuse = fuse_limit(ctx, mode, p);
+  if (mode != g->eval_mode || buf != g->graph_buf || fuse != g->fuse_np) {
     g->drop_graphs();
     g->graph_buf = buf;
   }
   g->eval_mode = mode;
+  g->fuse_np = fuse;
   return EBIC_OK;
 }
 
@@ -1790,6 +2077,7 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
   g->p.use_graph = p->use_graph;
   if (g->p.ipw != p->ipw) g->drop_graphs();  // (the captured launches hold the group size)
   g->p.ipw = p->ipw;
+  g->p.fuse_pairs = p->fuse_pairs;
   EBIC_TRY(ensure_eval_ready(ctx, g, p, n_gen));
   GenCtl c{};
   EBIC_TRY(read_ctl(ctx, g, &c));
@@ -1862,13 +2150,20 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
   }
   if (ctx->prof) {
     // algorithmic work of the evaluations run by this call (live slots only)
-    const double dlen = (double)(c.sum_len - c_start.sum_len);
-    const double dlive = (double)(c.n_evaluated - c_start.n_evaluated);
+    // (split between the evaluation launches and the evolve kernel's own evaluations)
+    const double flen = (double)(c.fused_len - c_start.fused_len);
+    const double flive = (double)(c.n_fused - c_start.n_fused);
+    const double dlen = (double)(c.sum_len - c_start.sum_len) - flen;
+    const double dlive = (double)(c.n_evaluated - c_start.n_evaluated) - flive;
     const double nd = g->p.neg_trends ? 2.0 : 1.0;
     KStats &k = ctx->kst[EBIC_KERNEL_EVAL];
     k.bytes += eval_bytes(ctx, g->eval_mode, (int64_t)dlen, (int64_t)dlive, g->p.neg_trends);
     k.ops += (dlen - dlive) * (double)ctx->R * nd;
     k.units += dlive * (double)ctx->R;
+    KStats &kf = ctx->kst[EBIC_KERNEL_EVOLVE];
+    kf.bytes += eval_bytes(ctx, g->eval_mode, (int64_t)flen, (int64_t)flive, g->p.neg_trends);
+    kf.ops += (flen - flive) * (double)ctx->R * nd;
+    kf.units += flive * (double)ctx->R;
     prof_collect(ctx);
   }
   if (rep) {
@@ -1879,6 +2174,8 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
     rep->n_top = c.n_top;
     rep->n_evaluated = c.n_evaluated;
     rep->eval_mode = g->eval_mode;
+    rep->fuse_pairs = g->fuse_np;
+    rep->n_fused = c.n_fused;
   }
   return EBIC_OK;
 }
@@ -1980,7 +2277,7 @@ struct StateHeader {
   ebic_params p;
 };
 
-static const uint64_t kMagic = 0x4542494347423331ull;  // "EBICGB31"
+static const uint64_t kMagic = 0x4542494347423332ull;  // "EBICGB32"
 
 static int64_t state_fixed_size(const GenState *g) {
   const int64_t P = g->P;

@@ -78,7 +78,9 @@ struct DevBuf {
 // Population as the kernels see it: CSR (off != nullptr, len derived) or fixed-stride storage
 // with explicit lengths (off == nullptr).  dead (optional) marks slots that are not scored.  In
 // the generation loop, a slot whose key a lower slot also produced is not scored either (dkeys,
-// the duplicate table), and a set *stop flag turns the whole launch into a no-op.
+// the duplicate table), and a set *stop flag turns the whole launch into a no-op.  With a list
+// (bitmap kernels only) the launch evaluates the slots list[0 .. *list_n - 1] of the n slots
+// instead of all of them; the count is read on the device when the launch starts.
 struct PopView {
   const int32_t *cols;
   const int32_t *off;
@@ -91,6 +93,8 @@ struct PopView {
   uint64_t *dkeys;
   uint32_t *dslot;
   uint32_t dmask;
+  const int32_t *list;
+  const int32_t *list_n;
 };
 
 // Matrix geometry and the outputs of one evaluation sweep.
@@ -205,6 +209,7 @@ struct ebic_ctx {
   int seg_direct = 0, seg_bitmap = 0;  // work-item sizes in passes; 0 = the built-in split
   int seg_loop = 0;                    // the same for the generation loop's evaluations
   int ipw_bitmap = 1, ipw_loop = 1;    // individuals per work item (staged bitmap form)
+  int fuse_loop = 0;  // pair limit of the evaluation inside the evolve kernel (-1: none, 0: untuned)
 
   // generation loop state (evolve.cu)
   struct GenState *gen = nullptr;

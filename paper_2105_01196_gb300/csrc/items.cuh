@@ -25,12 +25,13 @@ __device__ __forceinline__ int move_chunks(const EvalArgs &a) {
   return a.mv_table ? (int)((a.mv_n + 31u) / 32u) : 0;
 }
 
-// Slot s of the previous generation: its key joins the tabu list when the slot was live.
+// Slot s of the previous generation: its key joins the tabu list when the slot was live (its
+// tabu flag 1 marks a dead slot; 0 and 2 are live, 2 having been evaluated by the evolve kernel).
 __device__ __forceinline__ unsigned move_slot(const EvalArgs &a, uint32_t s) {
   const uint8_t d = a.mv_dead[s];
   const int32_t L = a.mv_len[s];
   const uint64_t h = a.mv_hash[s];
-  return (!d && L >= 2 && tabu_insert(a.mv_table, a.mv_tmask, h)) ? 1u : 0u;
+  return (d != 1 && L >= 2 && tabu_insert(a.mv_table, a.mv_tmask, h)) ? 1u : 0u;
 }
 
 // One side-task chunk: slot 32 m + lane of the previous generation joins the tabu list, and the
@@ -78,6 +79,14 @@ __device__ __forceinline__ int next(int32_t *work, int lane, int q, int n_all) {
   if (lane == 0) x = atomicAdd(work, 1);
   return __shfl_sync(kFull, x, 0) + W;
 }
+
+// Individuals of the launch: the view's n, or the count of its slot list (read on the device).
+__device__ __forceinline__ int count(const PopView &pv) {
+  return pv.list ? min(*pv.list_n, pv.n) : pv.n;
+}
+
+// Slot of the launch's individual i.
+__device__ __forceinline__ int slot(const PopView &pv, int i) { return pv.list ? pv.list[i] : i; }
 
 // Whether the run has stopped (the flag is read beside an item's first loads, and tested before
 // the item's first store).

@@ -54,12 +54,17 @@ int time_eval(ebic_ctx *ctx, int mode, EvalArgs a, const PopView &pv, int seg, i
 const int kLoopSegCandidates[] = {0, 1, 2, 4, 8, 16};  // 0 = the built-in split
 const int kLoopGens = 16;
 
-// The generation loop's work-item size: for each candidate, a warm-up run (initial population
-// and `gens` generations, which also captures the graphs), then the same run again with its
-// generations timed by CUDA events on the context stream.  The run state is reset afterwards:
-// the caller's next run starts from its own initial population.
+// Pair limits of the evaluation inside the evolve kernel measured for the bitmap form (-1: none).
+const int kLoopFuseCandidates[] = {-1, 1, 2, 4, 8, 63};
+
+// The generation loop's sizes, each candidate measured in the loop itself: a warm-up run
+// (initial population and `gens` generations, which also captures the graphs), then the same
+// run again with its generations timed by CUDA events on the context stream.  First (bitmap
+// form) the pair limit of the evaluation inside the evolve kernel, with the built-in work-item
+// split; then the work-item size and group size with that limit.  The run state is reset
+// afterwards: the caller's next run starts from its own initial population.
 int tune_loop(ebic_ctx *ctx, const ebic_params *p, int gens, int ipw_max, int *best_seg_out,
-              int *best_ipw_out) {
+              int *best_ipw_out, int *best_fuse_out) {
   cudaEvent_t e0, e1;
   EBIC_CHECK_CUDA(ctx, cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -69,22 +74,16 @@ int tune_loop(ebic_ctx *ctx, const ebic_params *p, int gens, int ipw_max, int *b
   ebic_params q = *p;
   q.mode = EBIC_MODE_AUTO;  // (the form just chosen)
   q.use_graph = 1;
-  q.ipw = 0;                // (the candidate below)
+  q.ipw = 0;                // (the candidates below)
+  q.fuse_pairs = -1;
   const int64_t passes = eval_passes(ctx, ctx->tuned_mode);
-  double best = DBL_MAX;
-  int best_seg = 0, best_ipw = 1, status = EBIC_OK;
+  int status = EBIC_OK;
   ebic_run_report rep;
-  for (int cand = 0; status == EBIC_OK; ++cand) {
-    const int n_seg_cands = (int)(sizeof(kLoopSegCandidates) / sizeof(int));
-    const int ipw = 1 << (cand / n_seg_cands), seg = kLoopSegCandidates[cand % n_seg_cands];
-    if (ipw > ipw_max) break;
-    if (seg > passes) continue;
-    ctx->seg_loop = seg;
-    ctx->ipw_loop = ipw;
-    float ms = 0.f;
+  // the loop with the current candidate: *ms for its `gens` timed generations
+  auto time_loop = [&](float *ms) {
     for (int pass = 0; pass < 2 && status == EBIC_OK; ++pass) {
       if (ctx->gen) {
-        // (the captured launches hold the work-item size: captured again in the first pass)
+        // (the captured launches hold the sizes: captured again in the first pass)
         if (pass == 0) gen_drop_graphs(ctx->gen);
         gen_mark_reset(ctx->gen);
       }
@@ -95,9 +94,39 @@ int tune_loop(ebic_ctx *ctx, const ebic_params *p, int gens, int ipw_max, int *b
       if (status != EBIC_OK) break;
       if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
       if (e != cudaSuccess) status = ebic_fail_cuda(ctx, e, "loop tuning", __FILE__, __LINE__);
     }
+  };
+  double best = DBL_MAX;
+  int best_fuse = 0;  // (not measured: other forms)
+  if (ctx->tuned_mode == EBIC_MODE_BITMAP && !p->last_kept) {
+    best_fuse = -1;
+    ctx->seg_loop = 0;
+    ctx->ipw_loop = 1;
+    for (int f : kLoopFuseCandidates) {
+      q.fuse_pairs = f;
+      float ms = 0.f;
+      time_loop(&ms);
+      if (status != EBIC_OK) break;
+      if (ms < best) {
+        best = ms;
+        best_fuse = f;
+      }
+    }
+    q.fuse_pairs = best_fuse;
+  }
+  best = DBL_MAX;
+  int best_seg = 0, best_ipw = 1;
+  for (int cand = 0; status == EBIC_OK; ++cand) {
+    const int n_seg_cands = (int)(sizeof(kLoopSegCandidates) / sizeof(int));
+    const int ipw = 1 << (cand / n_seg_cands), seg = kLoopSegCandidates[cand % n_seg_cands];
+    if (ipw > ipw_max) break;
+    if (seg > passes) continue;
+    ctx->seg_loop = seg;
+    ctx->ipw_loop = ipw;
+    float ms = 0.f;
+    time_loop(&ms);
     if (status != EBIC_OK) break;
     if (ms < best) {
       best = ms;
@@ -113,6 +142,7 @@ int tune_loop(ebic_ctx *ctx, const ebic_params *p, int gens, int ipw_max, int *b
   }
   *best_seg_out = best_seg;
   *best_ipw_out = best_ipw;
+  *best_fuse_out = best_fuse;
   return status;
 }
 
@@ -234,17 +264,19 @@ extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_
   ctx->ipw_bitmap = ipw_bitmap;
   ctx->seg_loop = 0;
   ctx->ipw_loop = 1;
+  ctx->fuse_loop = 0;
   // A run of generations expected: the loop's population soon differs from this one (selection
   // shortens it), so its work-item size is measured in the loop itself.
   if (expected_sweeps > 2 && ctx->tuned_mode != EBIC_MODE_STAGED &&
       ebic_check_loop_params(ctx, p) == EBIC_OK) {
-    int best_seg = 0, best_ipw = 1;
+    int best_seg = 0, best_ipw = 1, best_fuse = 0;
     const bool staged = ctx->tuned_mode == EBIC_MODE_BITMAP && eval_args_for(ctx).stage_bitmap &&
                         p->ratio_num < p->ratio_den;
     EBIC_TRY(tune_loop(ctx, p, std::min(expected_sweeps - 1, kLoopGens), staged ? 4 : 1,
-                       &best_seg, &best_ipw));
+                       &best_seg, &best_ipw, &best_fuse));
     ctx->seg_loop = best_seg;
     ctx->ipw_loop = best_ipw;
+    ctx->fuse_loop = best_fuse;
   }
   if (rep) {
     r.mode = ctx->tuned_mode;
@@ -253,6 +285,7 @@ extern "C" int ebic_autotune(ebic_ctx *ctx, const int32_t *col_idx, const int32_
     r.seg_loop = ctx->seg_loop;
     r.ipw_bitmap = ctx->ipw_bitmap;
     r.ipw_loop = ctx->ipw_loop;
+    r.fuse_loop = ctx->fuse_loop;
     r.direct_ms = best_direct;
     r.staged_ms = best_staged == DBL_MAX ? -1.0 : best_staged;
     r.bitmap_ms = best_bitmap == DBL_MAX ? -1.0 : best_bitmap;

@@ -49,7 +49,7 @@ class Params(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("mode", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("non_strict", ctypes.c_int32),
                 ("last_kept", ctypes.c_int32), ("ipw", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("fuse_pairs", ctypes.c_int32)]
 
     @classmethod
     def make(cls, **kw):
@@ -69,10 +69,10 @@ class RunReport(ctypes.Structure):
     _fields_ = [("gens_done", ctypes.c_int32), ("stopped", ctypes.c_int32),
                 ("last_hits", ctypes.c_int32), ("n_top", ctypes.c_int32),
                 ("n_evaluated", ctypes.c_int64), ("eval_mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("fuse_pairs", ctypes.c_int32), ("n_fused", ctypes.c_int64)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 _VP = ctypes.c_void_p
@@ -319,7 +319,8 @@ class TuneReport(ctypes.Structure):
                 ("seg_bitmap", ctypes.c_int32), ("seg_loop", ctypes.c_int32),
                 ("direct_ms", ctypes.c_double), ("bitmap_ms", ctypes.c_double),
                 ("build_ms", ctypes.c_double), ("staged_ms", ctypes.c_double),
-                ("ipw_bitmap", ctypes.c_int32), ("ipw_loop", ctypes.c_int32)]
+                ("ipw_bitmap", ctypes.c_int32), ("ipw_loop", ctypes.c_int32),
+                ("fuse_loop", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}

@@ -52,6 +52,10 @@ def test_autotuned_generations_match_oracle():
         assert ctx.toplist() == top
     st = oebic.run(x, op, 20)
     assert tune["seg_loop"] in (0, 1, 2, 4, 8, 16)
+    # the loop's fusion limit is measured with the bitmap form only, and then used
+    assert tune["fuse_loop"] in ((-1, 1, 2, 4, 8, 63) if tune["mode"] == ebic.MODE_BITMAP else (0,))
+    if tune["mode"] == ebic.MODE_BITMAP:
+        assert rep.fuse_pairs == max(tune["fuse_loop"], 0) == rep2.fuse_pairs
     assert rep.gens_done == rep2.gens_done == st.gen
     assert rep.n_evaluated == rep2.n_evaluated == st.n_evaluated
     assert [(e["cols"], e["f"]) for e in top] == [(tuple(e.cols), e.f) for e in st.top]

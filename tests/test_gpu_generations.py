@@ -325,3 +325,47 @@ def test_sequential_attempt_form(ebic, attempts, max_len, pop):
             assert_same_state(ctx, st, gp)
             hits += st.hits[-1]
     assert max_len == 64 or hits > pop // 10
+
+
+@pytest.mark.parametrize("fuse,neg,ns,ratio,pop,attempts,long_", [
+    (63, 1, 0, (85, 100), 64, 4, False), (1, 1, 1, (85, 100), 64, 4, False),
+    (2, 0, 0, (1, 2), 1300, 4, False), (63, 1, 1, (85, 100), 1300, 4, False),
+    (63, 0, 0, (1, 1), 96, 4, True), (63, 1, 1, (1, 1), 1300, 4, True),
+    (-1, 1, 0, (85, 100), 64, 4, False)])
+def test_evaluation_inside_the_evolve_kernel(ebic, fuse, neg, ns, ratio, pop, attempts, long_):
+    """Children whose pair test is exact (ceil(ratio x pairs) = pairs) and that have at most
+    fuse_pairs pairs are evaluated by the warp that built them, inside the evolve kernel (one
+    block per slot for 64 and 96 slots, a warp per slot for 1,300), the rest by the evaluation
+    launch over the list of slots left to it; -1 turns it off.  Ratio 1 with chromosomes of up to
+    64 columns puts pairs 32-62 in the fused path.  Generation by generation, then eight in one
+    graph replay, against the oracle, with the number of fused evaluations checked."""
+    x = long_matrix(53, ties=bool(ns)) if long_ else tiny_matrix()
+    kw = (dict(max_len=64, init_min_len=40, init_max_len=64, col_cap=16) if long_ else {})
+    gp, op = both_params(ebic, mode=2, neg_trends=neg, non_strict=ns, ratio_num=ratio[0],
+                         ratio_den=ratio[1], pop_size=pop, max_attempts=attempts, elite=6,
+                         n_biclusters=6, seed=61 + pop, **kw)
+    gp.fuse_pairs = fuse
+    fused = 0
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        rep = ctx.run_generations(gp, 0)
+        st = oebic.initialise(x, op)
+        assert rep.n_fused == 0                      # (the initial population has no evolve step)
+        assert_same_state(ctx, st, gp)
+        for g in range(1, 6):
+            rep = ctx.run_generations(gp, 1)
+            assert oebic.next_generation(x, st, op)
+            assert rep.gens_done == g == st.gen
+            assert rep.n_evaluated == st.n_evaluated
+            assert_same_state(ctx, st, gp)
+        rep = ctx.run_generations(gp, 8)
+        for _ in range(8):
+            assert oebic.next_generation(x, st, op)
+        assert rep.gens_done == st.gen == 13
+        assert rep.n_evaluated == st.n_evaluated
+        assert_same_state(ctx, st, gp)
+        fused = rep.n_fused
+    if fuse < 0:
+        assert rep.fuse_pairs == 0 and fused == 0
+    else:
+        assert rep.fuse_pairs == fuse and 0 < fused < rep.n_evaluated

@@ -8,12 +8,15 @@ from paper_2105_01196_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("use_graph", [1, 0])
-def test_generation_kernels_are_timed(use_graph):
+@pytest.mark.parametrize("use_graph,fuse", [(1, 0), (0, 0), (1, -1)])
+def test_generation_kernels_are_timed(use_graph, fuse):
+    """The evaluations the evolve kernel does itself (fuse_pairs) count as its work; the
+    evaluation launches count the rest."""
     from paper_2105_01196_gb300 import ebic
     x, _, _, _ = synth.workload_inputs(synth.WORKLOADS["tiny"])
     p = ebic.Params.make(max_len=6, init_max_len=6, pop_size=64, elite=4, n_biclusters=4,
-                         tabu_hit_limit=0, mode=ebic.MODE_BITMAP, use_graph=use_graph)
+                         tabu_hit_limit=0, mode=ebic.MODE_BITMAP, use_graph=use_graph,
+                         fuse_pairs=fuse)
     with ebic.Context(0) as ctx:
         ctx.load_matrix(x)
         ctx.run_generations(p, 2)
@@ -28,5 +31,9 @@ def test_generation_kernels_are_timed(use_graph):
     assert ev["timed_launches"] == evo["timed_launches"] == fin["timed_launches"] == 6
     assert ev["ms"] > 0 and evo["ms"] > 0 and fin["ms"] > 0
     wst = ((x.shape[0] + 127) // 128) * 4
-    assert ev["units"] == (rep.n_evaluated - rep0.n_evaluated) * x.shape[0]
+    fused = rep.n_fused - rep0.n_fused
+    assert (fused > 0) == (fuse == 0)
+    assert ev["units"] == (rep.n_evaluated - rep0.n_evaluated - fused) * x.shape[0]
+    assert evo["units"] == fused * x.shape[0]
     assert ev["alg_bytes"] > 0 and ev["alg_bytes"] % (wst * 4) == 0
+    assert evo["alg_bytes"] % (wst * 4) == 0 and (evo["alg_bytes"] > 0) == (fuse == 0)
