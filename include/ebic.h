@@ -136,6 +136,8 @@ typedef struct ebic_run_report {
   int32_t fuse_pairs;  /* pair limit of the evaluation inside the evolve kernel in this call
                           (0: none; see ebic_params.fuse_pairs)                              */
   int64_t n_fused;     /* of n_evaluated, the individuals evaluated inside the evolve kernel */
+  int64_t n_table;     /* of n_fused, the one-pair individuals scored from the pair counts the
+                          bitmap build records (popcounts of the pair rows; C <= 1,024)     */
 } ebic_run_report;
 
 /* Fills *p with the library defaults.  Never fails. */

@@ -380,7 +380,7 @@ int ebic_destroy(ebic_ctx *ctx) {
   ctx->gen = nullptr;
   DevBuf *bufs[] = {&ctx->keys, &ctx->bitmap, &ctx->stage_x, &ctx->d_err, &ctx->d_work,
                     &ctx->ev_cols, &ctx->ev_off, &ctx->ev_out, &ctx->ev_fit, &ctx->d_kerr,
-                    &ctx->codes, &ctx->planes};
+                    &ctx->codes, &ctx->planes, &ctx->pair_cnt};
   for (DevBuf *b : bufs) b->release();
   prof_collect(ctx);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -412,6 +412,7 @@ int ebic_load_matrix(ebic_ctx *ctx, const float *x, int64_t rows, int32_t cols, 
   if (rows != ctx->R || cols != ctx->C) ctx->tuned = false;
   ctx->have_matrix = false;
   ctx->bitmap_ok = false;
+  ctx->pair_cnt_ok = false;
   // A matrix of the same shape keeps the generation loop's buffers and captured graphs (their
   // device addresses and sizes stay valid); the run state is cleared before the next run.
   if (ctx->gen && rows == ctx->R && cols == ctx->C) {
@@ -462,11 +463,17 @@ int ebic_build_bitmap(ebic_ctx *ctx) {
   EBIC_CHECK_CUDA(ctx, prepare_bitmap_eval());
   // With rank codes (C <= 1,024) the words come from the codes' bit planes, else from the keys.
   if (ctx->code_bytes) EBIC_TRY(ensure_codes(ctx));
+  // (and the pair counts, C * C words, accumulated by the same kernel)
+  if (ctx->code_bytes) {
+    const size_t nc = (size_t)ctx->C * ctx->C * sizeof(int32_t);
+    EBIC_CHECK_CUDA(ctx, ctx->pair_cnt.ensure(nc, ctx->stream));
+    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(ctx->pair_cnt.p, 0, nc, ctx->stream));
+  }
   cudaEvent_t ev = prof_begin(ctx);
   if (ctx->code_bytes)
     EBIC_CHECK_CUDA(ctx, launch_build_bitmap_planes(ctx->planes.as<uint32_t>(), ctx->plane_bits,
                                                     ctx->C, ctx->Wst, ctx->bitmap.as<uint32_t>(),
-                                                    ctx->stream));
+                                                    ctx->pair_cnt.as<int32_t>(), ctx->stream));
   else
     EBIC_CHECK_CUDA(ctx, launch_build_bitmap(ctx->keys.as<uint32_t>(), ctx->R_pad, ctx->C,
                                              ctx->Wst, ctx->bitmap.as<uint32_t>(), ctx->stream));
@@ -478,6 +485,7 @@ int ebic_build_bitmap(ebic_ctx *ctx) {
     prof_collect(ctx);
   }
   ctx->bitmap_ok = true;
+  ctx->pair_cnt_ok = ctx->code_bytes != 0;
   return EBIC_OK;
 }
 

@@ -18,6 +18,7 @@
 // the generation loop's side task (items.cuh), and add their partial counts with one atomic per
 // item.
 #include <mutex>
+#include <type_traits>
 
 #include "internal.h"
 #include "tables.cuh"
@@ -609,190 +610,199 @@ __global__ void __launch_bounds__(kThreads, 2) k_eval_bitmap(EvalArgs a, PopView
     }
     __syncwarp();
     const int t = threshold(L, a.rnum, a.rden);
-    const bool exact = (t == np);
+    const bool exact_item = (t == np);
     const int64_t p0 = (int64_t)seg * a.seg_passes;
     const int64_t p1 = min(p0 + a.seg_passes, passes_total);
     int cp = 0, cn = 0, ca = 0;
-    // The counts of one pass's 4 words per lane, added to cp / cn / ca.
-    auto finish_pass = [&](int64_t w, bool act, uint4 ap, uint4 an, Cnt6 (&P)[4],
-                           Cnt6 (&N)[4]) {
-      uint4 pos, neg = zero4;
-      if (exact) {
-        pos = act ? ap : zero4;
-        if (NEG) neg = act ? an : zero4;
-      } else {
-        pos = make_uint4(cnt_ge(P[0], t), cnt_ge(P[1], t), cnt_ge(P[2], t), cnt_ge(P[3], t));
-        if (NEG)
-          neg = make_uint4(cnt_ge(N[0], t), cnt_ge(N[1], t), cnt_ge(N[2], t), cnt_ge(N[3], t));
-      }
-      if (NS) {  // pad rows (and inactive lanes) hold complemented zeros: mask them out
-        const uint4 vm = act ? make_uint4(valid_bits(w, a.R), valid_bits(w + 1, a.R),
-                                          valid_bits(w + 2, a.R), valid_bits(w + 3, a.R))
-                             : zero4;
-        pos = and4(pos, vm);
-        if (NEG) neg = and4(neg, vm);
-      }
-      cp += popc4(pos);
-      if (NEG) {
-        cn += popc4(neg);
-        ca += popc4(make_uint4(pos.x | neg.x, pos.y | neg.y, pos.z | neg.z, pos.w | neg.w));
-      } else {
-        ca += popc4(pos);
-      }
-    };
-    if (STAGE) {
-      // Units staged two at a time: the copies of the next unit are in flight while the current
-      // unit is counted.  A unit holds up to H pair rows per direction: several consecutive
-      // passes of all pairs when the chromosome is short (np <= H: H / np passes per unit), else
-      // one pass of a batch of up to H pairs.  So a warp keeps about H rows per direction in
-      // flight however short its chromosome (the loop's evolved population is mostly one- and
-      // two-pair chromosomes).
-      constexpr int H = NB / 2;
-      const bool packed = np <= H;
-      const int ppu = packed ? H / np : 1;                  // passes per unit
-      const int nbat = packed ? 1 : (np + H - 1) / H;       // batches per pass
-      const int n_pass = (int)(p1 - p0);
-      const int n_units = packed ? (n_pass + ppu - 1) / ppu : n_pass * nbat;
-      auto issue = [&](int u) {
-        uint32_t *bp = sp + (u & 1) * H * kPassWords, *bn = sn + (u & 1) * H * kPassWords;
-        if (packed) {
-          const int64_t qa = p0 + (int64_t)u * ppu, qb = min(p1, qa + ppu);
-          for (int64_t q = qa; q < qb; ++q) {
-            const int64_t w = q * kPassWords + lane * 4;
+    // The item's passes, compiled twice: for the exact test (the AND of the pair words, no
+    // counters) and for the counting one, so that neither carries the other's work.
+    auto run = [&](auto ex) {
+      const bool exact = decltype(ex)::value;
+      // The counts of one pass's 4 words per lane, added to cp / cn / ca.
+      auto finish_pass = [&](int64_t w, bool act, uint4 ap, uint4 an, Cnt6 (&P)[4],
+                             Cnt6 (&N)[4]) {
+        uint4 pos, neg = zero4;
+        if (exact) {
+          pos = act ? ap : zero4;
+          if (NEG) neg = act ? an : zero4;
+        } else {
+          pos = make_uint4(cnt_ge(P[0], t), cnt_ge(P[1], t), cnt_ge(P[2], t), cnt_ge(P[3], t));
+          if (NEG)
+            neg = make_uint4(cnt_ge(N[0], t), cnt_ge(N[1], t), cnt_ge(N[2], t), cnt_ge(N[3], t));
+        }
+        if (NS) {  // pad rows (and inactive lanes) hold complemented zeros: mask them out
+          const uint4 vm = act ? make_uint4(valid_bits(w, a.R), valid_bits(w + 1, a.R),
+                                            valid_bits(w + 2, a.R), valid_bits(w + 3, a.R))
+                               : zero4;
+          pos = and4(pos, vm);
+          if (NEG) neg = and4(neg, vm);
+        }
+        cp += popc4(pos);
+        if (NEG) {
+          cn += popc4(neg);
+          ca += popc4(make_uint4(pos.x | neg.x, pos.y | neg.y, pos.z | neg.z, pos.w | neg.w));
+        } else {
+          ca += popc4(pos);
+        }
+      };
+      if (STAGE) {
+        // Units staged two at a time: the copies of the next unit are in flight while the current
+        // unit is counted.  A unit holds up to H pair rows per direction: several consecutive
+        // passes of all pairs when the chromosome is short (np <= H: H / np passes per unit), else
+        // one pass of a batch of up to H pairs.  So a warp keeps about H rows per direction in
+        // flight however short its chromosome (the loop's evolved population is mostly one- and
+        // two-pair chromosomes).
+        constexpr int H = NB / 2;
+        const bool packed = np <= H;
+        const int ppu = packed ? H / np : 1;                  // passes per unit
+        const int nbat = packed ? 1 : (np + H - 1) / H;       // batches per pass
+        const int n_pass = (int)(p1 - p0);
+        const int n_units = packed ? (n_pass + ppu - 1) / ppu : n_pass * nbat;
+        auto issue = [&](int u) {
+          uint32_t *bp = sp + (u & 1) * H * kPassWords, *bn = sn + (u & 1) * H * kPassWords;
+          if (packed) {
+            const int64_t qa = p0 + (int64_t)u * ppu, qb = min(p1, qa + ppu);
+            for (int64_t q = qa; q < qb; ++q) {
+              const int64_t w = q * kPassWords + lane * 4;
+              if (w < Wst) {
+                const uint32_t *G = a.bitmap + w;
+                const int slot0 = (int)(q - qa) * np;
+                for (int j = 0; j < np; ++j) {
+                  cp_async16(bp + (slot0 + j) * kPassWords, G + s_pos[warp][j]);
+                  if (NEG) cp_async16(bn + (slot0 + j) * kPassWords, G + s_neg[warp][j]);
+                }
+              }
+            }
+          } else {
+            const int64_t pass = p0 + u / nbat;
+            const int k0 = (u % nbat) * H, nb = min(H, np - k0);
+            const int64_t w = pass * kPassWords + lane * 4;
             if (w < Wst) {
               const uint32_t *G = a.bitmap + w;
-              const int slot0 = (int)(q - qa) * np;
-              for (int j = 0; j < np; ++j) {
-                cp_async16(bp + (slot0 + j) * kPassWords, G + s_pos[warp][j]);
-                if (NEG) cp_async16(bn + (slot0 + j) * kPassWords, G + s_neg[warp][j]);
+              for (int j = 0; j < nb; ++j) {
+                cp_async16(bp + j * kPassWords, G + s_pos[warp][k0 + j]);
+                if (NEG) cp_async16(bn + j * kPassWords, G + s_neg[warp][k0 + j]);
               }
             }
           }
-        } else {
-          const int64_t pass = p0 + u / nbat;
-          const int k0 = (u % nbat) * H, nb = min(H, np - k0);
-          const int64_t w = pass * kPassWords + lane * 4;
-          if (w < Wst) {
-            const uint32_t *G = a.bitmap + w;
-            for (int j = 0; j < nb; ++j) {
-              cp_async16(bp + j * kPassWords, G + s_pos[warp][k0 + j]);
-              if (NEG) cp_async16(bn + j * kPassWords, G + s_neg[warp][k0 + j]);
-            }
-          }
-        }
-        cp_async_commit();
-      };
-      uint4 ap = ones, an = ones;
-      Cnt6 P[4], N[4];
-      // counts slots [s0, s0 + nb) of a half into the running pass
-      auto count = [&](const uint32_t *bp, const uint32_t *bn, int s0, int nb, bool act) {
-        if (exact) {
-          for (int j = 0; j < nb; ++j) {
-            ap = and4(ap, lds<NS>(act, bp + (s0 + j) * kPassWords, ones));
-            if (NEG) an = and4(an, lds<NS>(act, bn + (s0 + j) * kPassWords, ones));
-          }
-        } else {
-          for (int h = 0; h < nb; h += 4) {  // (the last group padded with zeros)
-            uint4 v[4], uu[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const bool in = act && h + j < nb;
-              v[j] = lds<NS>(in, bp + (s0 + h + j) * kPassWords, zero4);
-              uu[j] = NEG ? lds<NS>(in, bn + (s0 + h + j) * kPassWords, zero4) : zero4;
-            }
-            cnt_add_group<NEG>(P, N, v, uu);
-          }
-        }
-      };
-      auto start_pass = [&]() {
-        ap = ones;
-        an = ones;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          cnt_zero(P[j]);
-          cnt_zero(N[j]);
-        }
-      };
-      if (n_units > 0) issue(0);
-      for (int u = 0; u < n_units; ++u) {
-        if (u + 1 < n_units) {
-          issue(u + 1);
-          cp_async_wait<1>();
-        } else {
-          cp_async_wait<0>();
-        }
-        const uint32_t *bp = sp + (u & 1) * H * kPassWords, *bn = sn + (u & 1) * H * kPassWords;
-        if (packed) {
-          const int64_t qa = p0 + (int64_t)u * ppu, qb = min(p1, qa + ppu);
-          for (int64_t q = qa; q < qb; ++q) {
-            const int64_t w = q * kPassWords + lane * 4;
-            const bool act = w < Wst;  // (Wst is a multiple of 4: a lane's 4 words all exist or not)
-            start_pass();
-            count(bp, bn, (int)(q - qa) * np, np, act);
-            finish_pass(w, act, ap, an, P, N);
-          }
-        } else {
-          const int64_t pass = p0 + u / nbat;
-          const int k0 = (u % nbat) * H, nb = min(H, np - k0);
-          const int64_t w = pass * kPassWords + lane * 4;
-          const bool act = w < Wst;
-          if (k0 == 0) start_pass();
-          count(bp, bn, 0, nb, act);
-          if (k0 + nb == np) finish_pass(w, act, ap, an, P, N);
-        }
-      }
-    } else {
-      for (int64_t pass = p0; pass < p1; ++pass) {
-        const int64_t w = pass * kPassWords + lane * 4;
-        const bool act = w < Wst;  // (Wst is a multiple of 4: a lane's 4 words all exist or not)
-        const uint32_t *G = a.bitmap + w;
+          cp_async_commit();
+        };
         uint4 ap = ones, an = ones;
         Cnt6 P[4], N[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          cnt_zero(P[j]);
-          cnt_zero(N[j]);
-        }
-        if (exact) {
-          // The pair words of a round are loaded together, the last round padded with the
-          // operation's identity, so np pairs cost ceil(np / 8) dependent load rounds.
-          for (int k = 0; k < np; k += 8) {
-            uint4 v[8], u[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const bool in = k + j < np;
-              v[j] = ldb<NS>(act && in, G + (in ? s_pos[warp][k + j] : 0), ones);
-              if (NEG) u[j] = ldb<NS>(act && in, G + (in ? s_neg[warp][k + j] : 0), ones);
+        // counts slots [s0, s0 + nb) of a half into the running pass
+        auto count = [&](const uint32_t *bp, const uint32_t *bn, int s0, int nb, bool act) {
+          if (exact) {
+            for (int j = 0; j < nb; ++j) {
+              ap = and4(ap, lds<NS>(act, bp + (s0 + j) * kPassWords, ones));
+              if (NEG) an = and4(an, lds<NS>(act, bn + (s0 + j) * kPassWords, ones));
             }
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              ap = and4(ap, v[j]);
-              if (NEG) an = and4(an, u[j]);
+          } else {
+            for (int h = 0; h < nb; h += 4) {  // (the last group padded with zeros)
+              uint4 v[4], uu[4];
+  #pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const bool in = act && h + j < nb;
+                v[j] = lds<NS>(in, bp + (s0 + h + j) * kPassWords, zero4);
+                uu[j] = NEG ? lds<NS>(in, bn + (s0 + h + j) * kPassWords, zero4) : zero4;
+              }
+              cnt_add_group<NEG>(P, N, v, uu);
             }
           }
-        } else {
-          constexpr int RC = NEG ? 4 : 8;  // pairs per round (the counters of both directions
-                                           // and 8 pairs' words exceed the register budget)
-          for (int k = 0; k < np; k += RC) {
-            uint4 v[RC], u[RC];
-#pragma unroll
-            for (int j = 0; j < RC; ++j) {
-              const bool in = k + j < np;
-              v[j] = ldb<NS>(act && in, G + (in ? s_pos[warp][k + j] : 0), zero4);
-              if (NEG) u[j] = ldb<NS>(act && in, G + (in ? s_neg[warp][k + j] : 0), zero4);
+        };
+        auto start_pass = [&]() {
+          ap = ones;
+          an = ones;
+  #pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            cnt_zero(P[j]);
+            cnt_zero(N[j]);
+          }
+        };
+        if (n_units > 0) issue(0);
+        for (int u = 0; u < n_units; ++u) {
+          if (u + 1 < n_units) {
+            issue(u + 1);
+            cp_async_wait<1>();
+          } else {
+            cp_async_wait<0>();
+          }
+          const uint32_t *bp = sp + (u & 1) * H * kPassWords, *bn = sn + (u & 1) * H * kPassWords;
+          if (packed) {
+            const int64_t qa = p0 + (int64_t)u * ppu, qb = min(p1, qa + ppu);
+            for (int64_t q = qa; q < qb; ++q) {
+              const int64_t w = q * kPassWords + lane * 4;
+              const bool act = w < Wst;  // (Wst is a multiple of 4: a lane's 4 words all exist or not)
+              start_pass();
+              count(bp, bn, (int)(q - qa) * np, np, act);
+              finish_pass(w, act, ap, an, P, N);
             }
-#pragma unroll
-            for (int h = 0; h < RC; h += 4) {
-              const uint4 vv[4] = {v[h], v[h + 1], v[h + 2], v[h + 3]};
-              const uint4 uu[4] = {NEG ? u[h] : zero4, NEG ? u[h + 1] : zero4,
-                                   NEG ? u[h + 2] : zero4, NEG ? u[h + 3] : zero4};
-              cnt_add_group<NEG>(P, N, vv, uu);
-            }
+          } else {
+            const int64_t pass = p0 + u / nbat;
+            const int k0 = (u % nbat) * H, nb = min(H, np - k0);
+            const int64_t w = pass * kPassWords + lane * 4;
+            const bool act = w < Wst;
+            if (k0 == 0) start_pass();
+            count(bp, bn, 0, nb, act);
+            if (k0 + nb == np) finish_pass(w, act, ap, an, P, N);
           }
         }
-        finish_pass(w, act, ap, an, P, N);
+      } else {
+        for (int64_t pass = p0; pass < p1; ++pass) {
+          const int64_t w = pass * kPassWords + lane * 4;
+          const bool act = w < Wst;  // (Wst is a multiple of 4: a lane's 4 words all exist or not)
+          const uint32_t *G = a.bitmap + w;
+          uint4 ap = ones, an = ones;
+          Cnt6 P[4], N[4];
+  #pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            cnt_zero(P[j]);
+            cnt_zero(N[j]);
+          }
+          if (exact) {
+            // The pair words of a round are loaded together, the last round padded with the
+            // operation's identity, so np pairs cost ceil(np / 8) dependent load rounds.
+            for (int k = 0; k < np; k += 8) {
+              uint4 v[8], u[8];
+  #pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const bool in = k + j < np;
+                v[j] = ldb<NS>(act && in, G + (in ? s_pos[warp][k + j] : 0), ones);
+                if (NEG) u[j] = ldb<NS>(act && in, G + (in ? s_neg[warp][k + j] : 0), ones);
+              }
+  #pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                ap = and4(ap, v[j]);
+                if (NEG) an = and4(an, u[j]);
+              }
+            }
+          } else {
+            constexpr int RC = NEG ? 4 : 8;  // pairs per round (the counters of both directions
+                                             // and 8 pairs' words exceed the register budget)
+            for (int k = 0; k < np; k += RC) {
+              uint4 v[RC], u[RC];
+  #pragma unroll
+              for (int j = 0; j < RC; ++j) {
+                const bool in = k + j < np;
+                v[j] = ldb<NS>(act && in, G + (in ? s_pos[warp][k + j] : 0), zero4);
+                if (NEG) u[j] = ldb<NS>(act && in, G + (in ? s_neg[warp][k + j] : 0), zero4);
+              }
+  #pragma unroll
+              for (int h = 0; h < RC; h += 4) {
+                const uint4 vv[4] = {v[h], v[h + 1], v[h + 2], v[h + 3]};
+                const uint4 uu[4] = {NEG ? u[h] : zero4, NEG ? u[h + 1] : zero4,
+                                     NEG ? u[h + 2] : zero4, NEG ? u[h + 3] : zero4};
+                cnt_add_group<NEG>(P, N, vv, uu);
+              }
+            }
+          }
+          finish_pass(w, act, ap, an, P, N);
+        }
       }
-    }
+    };
+    if (exact_item)
+      run(std::true_type{});
+    else
+      run(std::false_type{});
     items::insert_finish(pv, ins, m.h, i);
     cp = __reduce_add_sync(kFull, cp);
     cn = __reduce_add_sync(kFull, cn);

@@ -60,7 +60,7 @@ struct GenCtl {
   int32_t n_todo;      // slots the evolve kernel left to the evaluation launch (its list)
   int32_t fused_cur;   // live slots of the generation being scored evaluated by the evolve kernel
   int32_t evo_next;    // slots k_evolve_seq's warps have taken beyond their first
-  int32_t pad;
+  int32_t table_cur;   // of fused_cur, the one-pair slots scored from the pair-count table
   long long n_evaluated;
   long long tabu_count;
   long long sum_len;   // sum of the lengths of all scored live slots (evaluation work)
@@ -68,6 +68,7 @@ struct GenCtl {
   long long n_fused;   // of n_evaluated, the slots the evolve kernel evaluated
   long long fused_len; // the sum of their lengths
   long long flen_cur;  // the same for the generation being scored
+  long long n_table;   // of n_fused, the one-pair slots scored from the pair-count table
 };
 
 // One population buffer (P slots of stride kS).
@@ -98,6 +99,7 @@ struct GenArgs {
   // Evaluation inside the evolve kernel (fuse_np > 0, bitmap form): the pair words, the test's
   // variant and ratio, and the list of the slots left to the evaluation launch (ctl->n_todo).
   const uint32_t *bitmap;  // [C][C][Wst]
+  const int32_t *pair_cnt; // [C][C] rows of each pair row of the bitmap, or null
   int64_t Wst, R;
   int32_t neg, ns, rnum, rden, fuse_np;
   int32_t *todo;
@@ -570,6 +572,82 @@ __device__ __forceinline__ bool fuse_child(const GenArgs &ga, int L) {
   return np <= ga.fuse_np && (ga.rnum * np + ga.rden - 1) / ga.rden == np;
 }
 
+// The counts of one pass (lane's 4 words w .. w + 3; act: they exist) from the ANDs of its pair
+// rows in each direction.
+__device__ __forceinline__ void fuse_pass_counts(const GenArgs &ga, bool neg, bool ns, bool act,
+                                                 int64_t w, uint4 ap, uint4 an, int &cp, int &cn,
+                                                 int &ca) {
+  const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+  uint4 pos = act ? ap : zero4, ng = (neg && act) ? an : zero4;
+  if (ns && act) {  // (pad rows hold complemented zeros)
+    const uint4 vm = make_uint4(fuse_valid(w, ga.R), fuse_valid(w + 1, ga.R),
+                                fuse_valid(w + 2, ga.R), fuse_valid(w + 3, ga.R));
+    pos = fuse_and(pos, vm);
+    ng = fuse_and(ng, vm);
+  }
+  cp += fuse_popc(pos);
+  cn += fuse_popc(ng);
+  ca += fuse_popc(make_uint4(pos.x | ng.x, pos.y | ng.y, pos.z | ng.z, pos.w | ng.w));
+}
+
+// The exact test when a pass's UPP pair rows (pairs x directions) fit in one copy group: a group
+// holds kFuseGroup / UPP whole passes, and each lane keeps the UPP rows' addresses (src[u]: its
+// words of pass 0; unit u of a pass is pair u / 2's positive (even u) or negative row with
+// negative trends, else pair u's row).
+template <int UPP>
+__device__ void w_eval_exact_small(const GenArgs &ga, const uint32_t *const (&src)[4],
+                                   uint32_t *stage, int lane, int &cp, int &cn, int &ca) {
+  constexpr int PPG = kFuseGroup / UPP;  // passes per group
+  const bool neg = ga.neg != 0, ns = ga.ns != 0;
+  const int64_t Wst = ga.Wst;
+  const int passes = (int)((Wst + kFuseWords - 1) / kFuseWords);
+  const int n_groups = (passes + PPG - 1) / PPG;
+  uint32_t *my = stage + lane * 4;  // (unit k of half b: my + (b * kFuseGroup + k) * kFuseWords)
+  auto issue = [&](int gi) {
+#pragma unroll
+    for (int pp = 0; pp < PPG; ++pp) {
+      const int q = gi * PPG + pp;
+      if (q < passes && (int64_t)q * kFuseWords + lane * 4 < Wst) {
+#pragma unroll
+        for (int u = 0; u < UPP; ++u)
+          fuse_copy16(my + ((gi & 1) * kFuseGroup + pp * UPP + u) * kFuseWords,
+                      src[u] + (int64_t)q * kFuseWords);
+      }
+    }
+    fuse_commit();
+  };
+  const uint4 ones = make_uint4(kFull, kFull, kFull, kFull);
+  issue(0);
+  if (n_groups > 1) issue(1);
+  for (int gi = 0; gi < n_groups; ++gi) {
+    if (gi + 1 < n_groups)
+      fuse_wait<1>();
+    else
+      fuse_wait<0>();
+#pragma unroll
+    for (int pp = 0; pp < PPG; ++pp) {
+      const int q = gi * PPG + pp;
+      const int64_t w = (int64_t)q * kFuseWords + lane * 4;
+      const bool act = q < passes && w < Wst;
+      uint4 ap = ones, an = ones;
+      if (act) {
+#pragma unroll
+        for (int u = 0; u < UPP; ++u) {
+          uint4 v = *reinterpret_cast<const uint4 *>(
+              my + ((gi & 1) * kFuseGroup + pp * UPP + u) * kFuseWords);
+          if (ns) v = make_uint4(~v.x, ~v.y, ~v.z, ~v.w);
+          if (neg && (u & 1))
+            an = fuse_and(an, v);
+          else
+            ap = fuse_and(ap, v);
+        }
+      }
+      if (q < passes) fuse_pass_counts(ga, neg, ns, act, w, ap, an, cp, cn, ca);
+    }
+    if (gi + 2 < n_groups) issue(gi + 2);
+  }
+}
+
 // Row counts (positive trend, negative trend, either) of the exact test of c[0 .. L-1] (L >= 2),
 // in every lane.  stage: the warp's kFuseSlots * kFuseWords words of shared memory (16-byte
 // aligned), free for this call.
@@ -579,6 +657,32 @@ __device__ void w_eval_exact(const GenArgs &ga, const int32_t *c, int L, uint32_
   const bool neg = ga.neg != 0, ns = ga.ns != 0;
   const int upp = neg ? 2 * np : np;  // units per pass: pair j's positive (then negative) row
   const int64_t Wst = ga.Wst;
+  if (upp <= kFuseGroup) {
+    // every lane: the addresses of the pass's rows (pairs 0 .. np-1 <= 3: columns c[0 .. 4])
+    const uint32_t C = (uint32_t)ga.C;
+    const uint32_t *src[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = neg ? (u >> 1) : u;
+      const bool nd = neg && (u & 1);
+      const int jj = j < np ? j : 0;  // (rows past upp are never read)
+      const uint32_t a = (uint32_t)c[jj], b = (uint32_t)c[jj + 1];
+      const uint32_t row = (ns != nd) ? b * C + a : a * C + b;
+      src[u] = ga.bitmap + (int64_t)row * Wst + lane * 4;
+    }
+    int cp = 0, cn = 0, ca = 0;
+    __syncwarp();  // every lane's earlier use of the region is done
+    switch (upp) {
+      case 1: w_eval_exact_small<1>(ga, src, stage, lane, cp, cn, ca); break;
+      case 2: w_eval_exact_small<2>(ga, src, stage, lane, cp, cn, ca); break;
+      case 3: w_eval_exact_small<3>(ga, src, stage, lane, cp, cn, ca); break;
+      default: w_eval_exact_small<4>(ga, src, stage, lane, cp, cn, ca); break;
+    }
+    rp = __reduce_add_sync(kFull, cp);
+    rn = __reduce_add_sync(kFull, cn);
+    ra = __reduce_add_sync(kFull, ca);
+    return;
+  }
   const int passes = (int)((Wst + kFuseWords - 1) / kFuseWords);
   const int n_groups = (passes * upp + kFuseGroup - 1) / kFuseGroup;
   // lane l: the word rows of pairs l and l + 32 (pair j = (c[j], c[j + 1])), positive and
@@ -667,22 +771,44 @@ __device__ void w_eval_exact(const GenArgs &ga, const int32_t *c, int L, uint32_
 
 // The end of a live slot s's evolve step when fusion is on: the slot is evaluated here (its
 // counts stored, its key entered in generation g's duplicate table, as the evaluation launch
-// would) or listed for the evaluation launch.  Returns whether it was evaluated.
-__device__ bool fuse_or_list(const GenArgs &ga, const int32_t *c, int L, uint64_t h, int s,
-                             int par, uint32_t *stage, int lane) {
+// would) or listed for the evaluation launch.  Returns its tabu-flag value: 2 evaluated from the
+// pair words, 3 (a one-pair chromosome) from the pair-count table, 0 listed.
+__device__ int fuse_or_list(const GenArgs &ga, const int32_t *c, int L, uint64_t h, int s,
+                            int par, uint32_t *stage, int lane) {
   if (fuse_child(ga, L)) {
-    int rp, rn, ra;
-    w_eval_exact(ga, c, L, stage, lane, rp, rn, ra);
+    int rp = 0, rn = 0, ra = 0;
+    const bool table = L == 2 && ga.pair_cnt != nullptr;
+    if (table) {
+      // one pair (a, b): G[a][b] holds the rows with key(b) > key(a) and G[b][a] the others
+      // that differ (the two are disjoint); with ties counting both ways the rows of a
+      // direction are the complement of the opposite direction's, and every row holds one
+      if (lane == 0) {
+        const int a = c[0], b = c[1];
+        const int ab = ga.pair_cnt[(int64_t)a * ga.C + b], ba = ga.pair_cnt[(int64_t)b * ga.C + a];
+        const int R = (int)ga.R;
+        if (!ga.ns) {
+          rp = ab;
+          rn = ga.neg ? ba : 0;
+          ra = rp + rn;
+        } else {
+          rp = R - ba;
+          rn = ga.neg ? R - ab : 0;
+          ra = ga.neg ? R : rp;
+        }
+      }
+    } else {
+      w_eval_exact(ga, c, L, stage, lane, rp, rn, ra);
+    }
     if (lane == 0) {
       ga.rows_scr[s] = rp;
       ga.rows_scr[ga.P + s] = rn;
       ga.rows_scr[2 * ga.P + s] = ra;
       dedup_insert(ga.dkeys[par], ga.dslot[par], ga.dmask, h, s);
     }
-    return true;
+    return table ? 3 : 2;
   }
   if (lane == 0) ga.todo[atomicAdd(&ga.ctl->n_todo, 1)] = s;
-  return false;
+  return 0;
 }
 
 // Step 1: the initial population, one warp per slot (generation 0, attempt 0 of the word
@@ -804,15 +930,16 @@ __global__ void __launch_bounds__(kMaxAttemptWarps * 32) k_evolve(GenArgs ga, Bu
   if (a != win) return;
   out[lane] = lane < L ? c[lane] : 0;
   out[lane + 32] = lane + 32 < L ? c[lane + 32] : 0;
-  const bool fused = !dead && ga.fuse_np > 0 &&
-                     fuse_or_list(ga, c, L, h, s, par,
-                                  reinterpret_cast<uint32_t *>(base + kEvoStage), lane);
+  const int fused = (!dead && ga.fuse_np > 0)
+                        ? fuse_or_list(ga, c, L, h, s, par,
+                                       reinterpret_cast<uint32_t *>(base + kEvoStage), lane)
+                        : 0;
   if (lane == 0) {
     nb.len[s] = L;
     nb.hash[s] = h;
-    // 1: dead; 2: live and evaluated here; 0: live, left to the evaluation launch (which enters
-    // the live keys in D[par])
-    nb.att_dead[s] = dead ? 1 : (fused ? 2 : 0);
+    // 1: dead; 2 or 3: live and evaluated here; 0: live, left to the evaluation launch (which
+    // enters the live keys in D[par])
+    nb.att_dead[s] = dead ? 1 : fused;
     nb.att_hits[s] = dead ? ga.A : win;
   }
 }
@@ -829,7 +956,7 @@ __global__ void __launch_bounds__(kMaxAttemptWarps * 32) k_evolve(GenArgs ga, Bu
 // of the column-usage table.
 constexpr int kSeqWarps = 8;
 
-__global__ void __launch_bounds__(kSeqWarps * 32) k_evolve_seq(GenArgs ga, Buf pb, Buf nb,
+__global__ void __launch_bounds__(kSeqWarps * 32, 4) k_evolve_seq(GenArgs ga, Buf pb, Buf nb,
                                                                int par) {
   extern __shared__ __align__(16) int32_t s_evo[];  // kEvolveWarpInts per warp, then usage
   wait_prior_grid();
@@ -880,13 +1007,14 @@ __global__ void __launch_bounds__(kSeqWarps * 32) k_evolve_seq(GenArgs ga, Buf p
       __syncwarp();
       out[lane] = lane < L ? c[lane] : 0;
       out[lane + 32] = lane + 32 < L ? c[lane + 32] : 0;
-      const bool fused = !dead && ga.fuse_np > 0 &&
-                         fuse_or_list(ga, c, L, h, s, par,
-                                      reinterpret_cast<uint32_t *>(base + kEvoStage), lane);
+      const int fused = (!dead && ga.fuse_np > 0)
+                            ? fuse_or_list(ga, c, L, h, s, par,
+                                           reinterpret_cast<uint32_t *>(base + kEvoStage), lane)
+                            : 0;
       if (lane == 0) {
         nb.len[s] = L;
         nb.hash[s] = h;
-        nb.att_dead[s] = dead ? 1 : (fused ? 2 : 0);  // (as in k_evolve)
+        nb.att_dead[s] = dead ? 1 : fused;  // (as in k_evolve)
         nb.att_hits[s] = dead ? ga.A : win;
       }
     }
@@ -1194,16 +1322,17 @@ __device__ int sort_and_process(const GenArgs &ga, const Buf &nb, const TopSmem 
 // A slot's inputs to scoring: every load first, then the duplicate lookup (probed whatever
 // the dead flag says, so that its loads need not wait for it).
 struct SlotIn {
-  bool att_dead, fused, in_dup;
+  bool att_dead, fused, table, in_dup;
   uint64_t h;
   int L, ah, rp, rn, ra;
 };
 
 __device__ __forceinline__ SlotIn load_slot(const GenArgs &ga, const Buf &nb, int par, int s) {
   SlotIn in;
-  const uint8_t ad = nb.att_dead[s];  // 1: dead; 2: live, evaluated by the evolve kernel
+  const uint8_t ad = nb.att_dead[s];  // 1: dead; 2, 3: live, evaluated by the evolve kernel
   in.att_dead = ad == 1;
-  in.fused = ad == 2;
+  in.fused = ad >= 2;
+  in.table = ad == 3;
   in.h = nb.hash[s];
   in.L = nb.len[s];
   in.ah = nb.att_hits[s];
@@ -1218,7 +1347,8 @@ __device__ __forceinline__ SlotIn load_slot(const GenArgs &ga, const Buf &nb, in
 // scores a share of the slots; the last block to finish then runs the single-block part.
 __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, int par) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_hits, s_live, s_lsum, s_fused, s_flsum, s_last, s_n, s_cnt, s_stop, s_nc;
+  __shared__ int s_hits, s_live, s_lsum, s_fused, s_flsum, s_table, s_last, s_n, s_cnt, s_stop,
+      s_nc;
   GenCtl *ctl = ga.ctl;
   wait_prior_grid();
   // The counters, the list's last entry and this thread's first slot are loaded in one round,
@@ -1251,6 +1381,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
     s_lsum = 0;
     s_fused = 0;
     s_flsum = 0;
+    s_table = 0;
     s_nc = 0;
   }
   __syncthreads();
@@ -1261,7 +1392,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
   // list they are skipped as duplicates, and an entry evicted by a better candidate fails the
   // same overlap test as its copy would, so leaving them out changes nothing.
   const int n_el = gen0 < 0 ? 0 : min(ga.E, n0);
-  int hits = 0, live = 0, lsum = 0, fused = 0, flsum = 0;
+  int hits = 0, live = 0, lsum = 0, fused = 0, flsum = 0, table = 0;
   for (int s = tid; s < ga.P; s += stride) {
     const SlotIn in = s == tid ? first : load_slot(ga, nb, par, s);
     const bool att_dead = in.att_dead;
@@ -1284,6 +1415,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
     lsum += dead ? 0 : L;
     fused += (!dead && in.fused) ? 1 : 0;
     flsum += (!dead && in.fused) ? L : 0;
+    table += (!dead && in.table) ? 1 : 0;
     if (s >= n_el && !dead && f > 0ull && (!had_threshold || key_before(f, h, tf, th))) {
       if (single) {  // at most P <= sort_cap candidates
         const int q = atomicAdd(&s_nc, 1);
@@ -1303,15 +1435,17 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
   lsum = __reduce_add_sync(kFull, lsum);
   fused = __reduce_add_sync(kFull, fused);
   flsum = __reduce_add_sync(kFull, flsum);
+  table = __reduce_add_sync(kFull, table);
   if ((threadIdx.x & 31) == 0) {
     if (hits) atomicAdd(&s_hits, hits);
     if (live) atomicAdd(&s_live, live);
     if (lsum) atomicAdd(&s_lsum, lsum);
     if (fused) atomicAdd(&s_fused, fused);
     if (flsum) atomicAdd(&s_flsum, flsum);
+    if (table) atomicAdd(&s_table, table);
   }
   __syncthreads();
-  int hits_g, live_g, nc, fused_g;
+  int hits_g, live_g, nc, fused_g, table_g;
   long long len_g, flen_g;
   if (single) {
     hits_g = s_hits;
@@ -1319,6 +1453,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
     len_g = s_lsum;
     fused_g = s_fused;
     flen_g = s_flsum;
+    table_g = s_table;
     nc = s_nc;
   } else {
     if (threadIdx.x == 0) {
@@ -1328,6 +1463,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
         atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->len_cur),
                   (unsigned long long)s_lsum);
       if (s_fused) atomicAdd(&ctl->fused_cur, s_fused);
+      if (s_table) atomicAdd(&ctl->table_cur, s_table);
       if (s_flsum)
         atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->flen_cur),
                   (unsigned long long)s_flsum);
@@ -1342,6 +1478,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
     len_g = __ldcg(&ctl->len_cur);
     fused_g = __ldcg(&ctl->fused_cur);
     flen_g = __ldcg(&ctl->flen_cur);
+    table_g = __ldcg(&ctl->table_cur);
     nc = __ldcg(&ctl->n_cand);
   }
 
@@ -1355,6 +1492,7 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
       ctl->sum_len += len_g;
       ctl->n_fused += fused_g;
       ctl->fused_len += flen_g;
+      ctl->n_table += table_g;
     }
     return;
   }
@@ -1366,11 +1504,13 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
       ctl->sum_len += len_g;
       ctl->n_fused += fused_g;
       ctl->fused_len += flen_g;
+      ctl->n_table += table_g;
       ctl->len_cur = 0;
       ctl->hits_cur = 0;
       ctl->live_cur = 0;
       ctl->fused_cur = 0;
       ctl->flen_cur = 0;
+      ctl->table_cur = 0;
       ctl->n_todo = 0;
       ctl->evo_next = 0;
       ctl->n_cand = 0;
@@ -1428,11 +1568,13 @@ __global__ void __launch_bounds__(kTopThreads, 1) k_finish(GenArgs ga, Buf nb, i
     ctl->sum_len += len_g;
     ctl->n_fused += fused_g;
     ctl->fused_len += flen_g;
+    ctl->n_table += table_g;
     ctl->len_cur = 0;
     ctl->hits_cur = 0;
     ctl->live_cur = 0;
     ctl->fused_cur = 0;
     ctl->flen_cur = 0;
+    ctl->table_cur = 0;
     ctl->n_todo = 0;
     ctl->evo_next = 0;
     ctl->n_cand = 0;
@@ -1492,6 +1634,7 @@ struct GenState {
   bool initialised = false;
   bool reset_pending = false;          // the run state must be cleared before the next run
   const void *graph_buf = nullptr;  // codes or bitmap the captured graphs read (null: keys)
+  const void *graph_cnt = nullptr;  // pair-count table the captured graphs read (or null)
   DevBuf cols[2], len[2], att_hits[2], rows[2], att_dead[2], dead[2], hash[2], fit[2];
   DevBuf dkeys[2], dslot[2];
   DevBuf rows_scr, work, tabu, top, ctl, usage, cand_f, cand_h, cand_s, extract, todo;
@@ -1614,6 +1757,7 @@ GenArgs gen_args(ebic_ctx *ctx, GenState *g) {
   ga.tabu_limit = p.tabu_hit_limit;
   if (g->fuse_np > 0) {
     ga.bitmap = ctx->bitmap.as<uint32_t>();
+    ga.pair_cnt = ctx->pair_cnt_ok ? ctx->pair_cnt.as<int32_t>() : nullptr;
     ga.Wst = ctx->Wst;
     ga.R = ctx->R;
     ga.neg = p.neg_trends;
@@ -1982,9 +2126,12 @@ int ensure_eval_ready(ebic_ctx *ctx, GenState *g, const ebic_params *p, int n_ge
                     : (direct && ctx->codes_ready ? ctx->codes.p : nullptr);
   // (and the fusion limit, which the captured evolve launches hold)
   const int fuse = fuse_limit(ctx, mode, p);
-  if (mode != g->eval_mode || buf != g->graph_buf || fuse != g->fuse_np) {
+  const void *cnt = fuse > 0 && ctx->pair_cnt_ok ? ctx->pair_cnt.p : nullptr;
+  if (mode != g->eval_mode || buf != g->graph_buf || fuse != g->fuse_np ||
+      cnt != g->graph_cnt) {
     g->drop_graphs();
     g->graph_buf = buf;
+    g->graph_cnt = cnt;
   }
   g->eval_mode = mode;
   g->fuse_np = fuse;
@@ -2160,8 +2307,11 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
     k.bytes += eval_bytes(ctx, g->eval_mode, (int64_t)dlen, (int64_t)dlive, g->p.neg_trends);
     k.ops += (dlen - dlive) * (double)ctx->R * nd;
     k.units += dlive * (double)ctx->R;
+    // (a one-pair slot scored from the pair-count table reads one count per direction)
+    const double ntab = (double)(c.n_table - c_start.n_table);
     KStats &kf = ctx->kst[EBIC_KERNEL_EVOLVE];
-    kf.bytes += eval_bytes(ctx, g->eval_mode, (int64_t)flen, (int64_t)flive, g->p.neg_trends);
+    kf.bytes += eval_bytes(ctx, g->eval_mode, (int64_t)(flen - 2.0 * ntab),
+                           (int64_t)(flive - ntab), g->p.neg_trends) + ntab * 4.0 * nd;
     kf.ops += (flen - flive) * (double)ctx->R * nd;
     kf.units += flive * (double)ctx->R;
     prof_collect(ctx);
@@ -2176,6 +2326,7 @@ int ebic_run_generations(ebic_ctx *ctx, const ebic_params *p, int32_t n_gen,
     rep->eval_mode = g->eval_mode;
     rep->fuse_pairs = g->fuse_np;
     rep->n_fused = c.n_fused;
+    rep->n_table = c.n_table;
   }
   return EBIC_OK;
 }

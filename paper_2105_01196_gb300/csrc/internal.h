@@ -187,6 +187,10 @@ struct ebic_ctx {
   bool have_matrix = false;
   DevBuf keys, bitmap, stage_x;
   bool bitmap_ok = false;
+  // rows of each pair row of the bitmap (popcount of G[a][b]), [C][C]; built with the bitmap
+  // from the rank codes' bit planes (C <= 1,024), else absent
+  DevBuf pair_cnt;
+  bool pair_cnt_ok = false;
 
   // scratch for single evaluations
   DevBuf d_err, d_work, ev_cols, ev_off, ev_out, ev_fit;
@@ -270,9 +274,10 @@ cudaError_t launch_upload(const float *x, int64_t R, int32_t C, int64_t R_pad, i
                           uint32_t *keys, int32_t *err, cudaStream_t s);
 cudaError_t launch_build_bitmap(const uint32_t *keys, int64_t R_pad, int32_t C, int64_t Wst,
                                 uint32_t *bitmap, cudaStream_t s);
-// The same bitmap from the bit planes of the rank codes (nb planes per column, nb <= 10).
+// The same bitmap from the bit planes of the rank codes (nb planes per column, nb <= 10); with
+// cnt (C * C, zeroed beforehand) also each pair row's popcount, cnt[a * C + b].
 cudaError_t launch_build_bitmap_planes(const uint32_t *planes, int nb, int32_t C, int64_t Wst,
-                                       uint32_t *bitmap, cudaStream_t s);
+                                       uint32_t *bitmap, int32_t *cnt, cudaStream_t s);
 
 // eval.cu
 cudaError_t launch_validate_csr(const int32_t *cols, const int32_t *off, int32_t n, int32_t C,

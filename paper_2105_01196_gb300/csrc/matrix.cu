@@ -226,11 +226,14 @@ __device__ __forceinline__ void cp_wait_bm() {
 // The b planes of a block's piece are staged in shared memory, kBB columns at a time and
 // double-buffered (cp.async by the whole block; the next batch is in flight while the current
 // one is compared), so the eight warps share one copy and read it with constant offsets.
+// With `cnt` (zeroed beforehand), the pair counts are accumulated too: cnt[a * C + b] = the
+// rows of G[a][b] (its popcount), from each warp's 32 words by a warp sum and one atomic.
 template <int NB>
 __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *__restrict__ planes,
                                                              int32_t C, int64_t Wst,
                                                              PieceTable tab,
-                                                             uint32_t *__restrict__ G) {
+                                                             uint32_t *__restrict__ G,
+                                                             int32_t *__restrict__ cnt) {
   __shared__ __align__(16) uint32_t s_b[2][kBB][NB][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // this block's a-block (the last one whose first piece is at or before blockIdx.y) and piece
@@ -254,21 +257,32 @@ __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *
     for (int p = 0; p < NB; ++p)
       A[i][p] = (a0 + i < C && w_ok) ? __ldg(planes + ((int64_t)(a0 + i) * NB + p) * Wst + w) : 0u;
   const int64_t row = (int64_t)C * Wst;  // words between G[a][.] and G[a + 1][.]
-  if (piece == 0 && a0 < C && w_ok) {
+  // the rows of pair (a, b) in this warp's 32 words, added to cnt[a * C + b] (all lanes call it)
+  auto count = [&](int a, int b, uint32_t word) {
+    const int n = (int)__reduce_add_sync(0xFFFFFFFFu, w_ok ? (unsigned)__popc(word) : 0u);
+    if (lane == 0 && n) atomicAdd(cnt + (int64_t)a * C + b, n);
+  };
+  if (piece == 0 && a0 < C) {
     // the diagonal words, and the pairs among the warp's own columns
 #pragma unroll
     for (int i = 0; i < kPA; ++i) {
       const int a = a0 + i;
       if (a >= C) break;
-      G[(int64_t)a * row + (int64_t)a * Wst + w] = 0u;
+      if (w_ok) G[(int64_t)a * row + (int64_t)a * Wst + w] = 0u;
 #pragma unroll
       for (int i2 = i + 1; i2 < kPA; ++i2) {
         const int b = a0 + i2;
         if (b < C) {
           uint32_t gt, lt;
           plane_compare<NB>(A[i], A[i2], gt, lt);
-          __stcs(G + (int64_t)a * row + (int64_t)b * Wst + w, gt);
-          __stcs(G + (int64_t)b * row + (int64_t)a * Wst + w, lt);
+          if (w_ok) {
+            __stcs(G + (int64_t)a * row + (int64_t)b * Wst + w, gt);
+            __stcs(G + (int64_t)b * row + (int64_t)a * Wst + w, lt);
+          }
+          if (cnt) {
+            count(a, b, gt);
+            count(b, a, lt);
+          }
         }
       }
     }
@@ -291,7 +305,7 @@ __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *
   // G[a][b] at a * row + b * Wst, G[b][a] at b * row + a * Wst; (a + i)'s words sit i rows (or
   // i * Wst words) past a's: 32-bit offsets from two pointers
   const uint32_t row32 = (uint32_t)row, wst32 = (uint32_t)Wst;  // (checked at launch)
-  const bool active = a0 < C && w_ok;
+  const bool active = a0 < C;  // (the whole warp; lanes past Wst store nothing)
   issue(0);
   for (int t = 0; t < n_batches; ++t) {
     if (t + 1 < n_batches) {
@@ -315,8 +329,14 @@ __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *
           for (int i = 0; i < kPA; ++i) {
             uint32_t gt, lt;
             plane_compare<NB>(A[i], B, gt, lt);
-            __stcs(g_ab + (uint32_t)i * row32, gt);
-            __stcs(g_ba + (uint32_t)i * wst32, lt);
+            if (w_ok) {
+              __stcs(g_ab + (uint32_t)i * row32, gt);
+              __stcs(g_ba + (uint32_t)i * wst32, lt);
+            }
+            if (cnt) {
+              count(a0 + i, bs + bb, gt);
+              count(bs + bb, a0 + i, lt);
+            }
           }
         }
         g_ab += Wst;
@@ -362,7 +382,7 @@ cudaError_t launch_build_bitmap(const uint32_t *keys, int64_t R_pad, int32_t C, 
 }
 
 cudaError_t launch_build_bitmap_planes(const uint32_t *planes, int nb, int32_t C, int64_t Wst,
-                                       uint32_t *bitmap, cudaStream_t s) {
+                                       uint32_t *bitmap, int32_t *cnt, cudaStream_t s) {
   const int64_t n_chunks = (Wst + 31) / 32;
   const int n_ablk = (C + 8 * kPA - 1) / (8 * kPA);
   // (the kernel offsets rows of the bitmap by up to 3 * C * Wst words in 32 bits)
@@ -376,16 +396,16 @@ cudaError_t launch_build_bitmap_planes(const uint32_t *planes, int nb, int32_t C
   }
   const dim3 grid((unsigned)n_chunks, (unsigned)total), block(256);  // (total <= 32 * 8 pieces)
   switch (nb) {
-    case 1: k_build_bitmap_planes<1><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
-    case 2: k_build_bitmap_planes<2><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
-    case 3: k_build_bitmap_planes<3><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
-    case 4: k_build_bitmap_planes<4><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
-    case 5: k_build_bitmap_planes<5><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
-    case 6: k_build_bitmap_planes<6><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
-    case 7: k_build_bitmap_planes<7><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
-    case 8: k_build_bitmap_planes<8><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
-    case 9: k_build_bitmap_planes<9><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
-    case 10: k_build_bitmap_planes<10><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap); break;
+    case 1: k_build_bitmap_planes<1><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
+    case 2: k_build_bitmap_planes<2><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
+    case 3: k_build_bitmap_planes<3><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
+    case 4: k_build_bitmap_planes<4><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
+    case 5: k_build_bitmap_planes<5><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
+    case 6: k_build_bitmap_planes<6><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
+    case 7: k_build_bitmap_planes<7><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
+    case 8: k_build_bitmap_planes<8><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
+    case 9: k_build_bitmap_planes<9><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
+    case 10: k_build_bitmap_planes<10><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -69,7 +69,8 @@ class RunReport(ctypes.Structure):
     _fields_ = [("gens_done", ctypes.c_int32), ("stopped", ctypes.c_int32),
                 ("last_hits", ctypes.c_int32), ("n_top", ctypes.c_int32),
                 ("n_evaluated", ctypes.c_int64), ("eval_mode", ctypes.c_int32),
-                ("fuse_pairs", ctypes.c_int32), ("n_fused", ctypes.c_int64)]
+                ("fuse_pairs", ctypes.c_int32), ("n_fused", ctypes.c_int64),
+                ("n_table", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

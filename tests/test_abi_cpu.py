@@ -53,7 +53,7 @@ def test_pure_host_entry_points(lib):
 def test_struct_layout_matches_header(lib):
     import ctypes
     assert ctypes.sizeof(lib.Params) == 4 * 16 + 8 + 8 + 8 + 8
-    assert ctypes.sizeof(lib.RunReport) == 4 * 4 + 8 + 8 + 8
+    assert ctypes.sizeof(lib.RunReport) == 4 * 4 + 8 + 8 + 8 + 8
     assert ctypes.sizeof(lib.TuneReport) == 4 * 4 + 4 * 8 + 8 + 8
     assert ctypes.sizeof(lib.JobResult) == 8 + 4 * 4 + 8 + 4 * 2 + 8 + 8 * 2
 

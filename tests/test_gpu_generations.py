@@ -366,6 +366,8 @@ def test_evaluation_inside_the_evolve_kernel(ebic, fuse, neg, ns, ratio, pop, at
         assert_same_state(ctx, st, gp)
         fused = rep.n_fused
     if fuse < 0:
-        assert rep.fuse_pairs == 0 and fused == 0
+        assert rep.fuse_pairs == 0 and fused == 0 and rep.n_table == 0
     else:
+        # (one-pair children are scored from the build's pair counts: 128 columns or fewer)
         assert rep.fuse_pairs == fuse and 0 < fused < rep.n_evaluated
+        assert 0 <= rep.n_table <= fused and (long_ or rep.n_table > 0)

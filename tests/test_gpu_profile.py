@@ -36,4 +36,8 @@ def test_generation_kernels_are_timed(use_graph, fuse):
     assert ev["units"] == (rep.n_evaluated - rep0.n_evaluated - fused) * x.shape[0]
     assert evo["units"] == fused * x.shape[0]
     assert ev["alg_bytes"] > 0 and ev["alg_bytes"] % (wst * 4) == 0
-    assert evo["alg_bytes"] % (wst * 4) == 0 and (evo["alg_bytes"] > 0) == (fuse == 0)
+    # (one-pair slots scored from the pair-count table read one count per direction)
+    ntab = rep.n_table - rep0.n_table
+    words = evo["alg_bytes"] - ntab * 4 * (2 if p.neg_trends else 1)
+    assert words % (wst * 4) == 0 and (evo["alg_bytes"] > 0) == (fuse == 0)
+    assert (ntab > 0) == (fuse == 0)
