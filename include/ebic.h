@@ -191,6 +191,17 @@ EBIC_API int64_t ebic_bitmap_bytes(int64_t rows, int32_t cols);
 EBIC_API int ebic_copy_bitmap(ebic_ctx *ctx, uint32_t *out, int64_t n_words);
 
 /*
+ * Copies the pair counts the bitmap build records (cols <= 1,024: the build from the rank codes'
+ * bit planes) into `out` (host or device, n >= cols * cols uint64): for a < b, out[a * cols + b]
+ * = rows of G[a][b] (key(b) > key(a), the popcount of that pair row) in the low 32 bits and
+ * rows of G[b][a] in the high 32 bits; the other entries are 0.  A one-pair chromosome's trend
+ * counts follow from them (the generation loop scores one-pair children this way).
+ * Errors: EBIC_ESTATE (no bitmap built, or built without counts: cols > 1,024), EBIC_EINVAL (n
+ * too small), EBIC_ECUDA.
+ */
+EBIC_API int ebic_copy_pair_counts(ebic_ctx *ctx, uint64_t *out, int64_t n);
+
+/*
  * Evaluates a population (Sec. 2.4, steps 2-3: score every individual by the number of its
  * trend-preserving rows).  The population is CSR: individual i is
  * col_idx[offsets[i] .. offsets[i+1]-1], 2 <= length <= 64, distinct columns in [0, cols).

@@ -465,7 +465,7 @@ int ebic_build_bitmap(ebic_ctx *ctx) {
   if (ctx->code_bytes) EBIC_TRY(ensure_codes(ctx));
   // (and the pair counts, C * C words, accumulated by the same kernel)
   if (ctx->code_bytes) {
-    const size_t nc = (size_t)ctx->C * ctx->C * sizeof(int32_t);
+    const size_t nc = (size_t)ctx->C * ctx->C * sizeof(unsigned long long);
     EBIC_CHECK_CUDA(ctx, ctx->pair_cnt.ensure(nc, ctx->stream));
     EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(ctx->pair_cnt.p, 0, nc, ctx->stream));
   }
@@ -473,7 +473,8 @@ int ebic_build_bitmap(ebic_ctx *ctx) {
   if (ctx->code_bytes)
     EBIC_CHECK_CUDA(ctx, launch_build_bitmap_planes(ctx->planes.as<uint32_t>(), ctx->plane_bits,
                                                     ctx->C, ctx->Wst, ctx->bitmap.as<uint32_t>(),
-                                                    ctx->pair_cnt.as<int32_t>(), ctx->stream));
+                                                    ctx->pair_cnt.as<unsigned long long>(),
+                                                    ctx->stream));
   else
     EBIC_CHECK_CUDA(ctx, launch_build_bitmap(ctx->keys.as<uint32_t>(), ctx->R_pad, ctx->C,
                                              ctx->Wst, ctx->bitmap.as<uint32_t>(), ctx->stream));
@@ -497,6 +498,20 @@ int ebic_copy_bitmap(ebic_ctx *ctx, uint32_t *out, int64_t n_words) {
   DeviceGuard g(ctx->device);
   EBIC_TRY(check_device_ptr(ctx, out, "out"));
   EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(out, ctx->bitmap.p, (size_t)need * 4, cudaMemcpyDefault,
+                                       ctx->stream));
+  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return EBIC_OK;
+}
+
+int ebic_copy_pair_counts(ebic_ctx *ctx, uint64_t *out, int64_t n) {
+  if (!ctx) return EBIC_EINVAL;
+  if (!ctx->bitmap_ok || !ctx->pair_cnt_ok)
+    return ebic_fail(ctx, EBIC_ESTATE, "no pair counts built (bitmap from rank codes)");
+  const int64_t need = (int64_t)ctx->C * ctx->C;
+  if (!out || n < need) return ebic_fail(ctx, EBIC_EINVAL, "output too small");
+  DeviceGuard g(ctx->device);
+  EBIC_TRY(check_device_ptr(ctx, out, "out"));
+  EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(out, ctx->pair_cnt.p, (size_t)need * 8, cudaMemcpyDefault,
                                        ctx->stream));
   EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return EBIC_OK;
@@ -599,7 +614,9 @@ int ensure_codes(ebic_ctx *ctx) {
   const int64_t S = ctx->code_stride, C = ctx->C;
   ctx->plane_bits = code_plane_bits(ctx->C);
   EBIC_CHECK_CUDA(ctx, ctx->codes.ensure((size_t)C * S * ctx->code_bytes, ctx->stream));
-  EBIC_CHECK_CUDA(ctx, ctx->planes.ensure((size_t)C * ctx->plane_bits * ctx->Wst * 4, ctx->stream));
+  EBIC_CHECK_CUDA(ctx, ctx->planes.ensure(
+                           (size_t)C * code_plane_stride(ctx->plane_bits) * ctx->Wst * 4,
+                           ctx->stream));
   cudaEvent_t ev = prof_begin(ctx);
   EBIC_CHECK_CUDA(ctx, launch_rank_codes(ctx->keys.as<uint32_t>(), ctx->R_pad, ctx->C,
                                          ctx->codes.p, ctx->code_bytes, S,

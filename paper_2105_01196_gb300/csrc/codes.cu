@@ -54,7 +54,8 @@ __device__ __forceinline__ void wait_prior_grid() {
 // in a shared [C][17] tile, each row's codes replace its keys in the tile, and the tile is
 // written out column by column (codes [C][S]) together with the codes' bit planes: plane p of
 // column c, word w has bit j = bit p of code(32 w + j, c), the operand of the pair-bitmap build
-// (matrix.cu); a block fills one half of each word.
+// (matrix.cu), stored [C][Wst][NBP] (a word's nb planes together, NBP = nb rounded up to a
+// multiple of 4, so that they load as 16-byte vectors); a block fills one half of each word.
 constexpr int kRankRows = 16;                 // rows per block tile
 constexpr int kTileStride = kRankRows + 1;    // tile entries per column (bank spread)
 
@@ -147,6 +148,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   uint32_t *srt = s_rank + warp * kSorted;
   uint32_t *tile = s_rank + kWarps * kSorted;  // [C][kTileStride]: keys, then codes in place
   uint16_t *planes16 = reinterpret_cast<uint16_t *>(planes);
+  const int nbp = (nb + 3) & ~3;  // planes per (column, word) in the layout
   const int64_t n_tiles = R_pad / kRankRows;
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const int64_t r0 = t * kRankRows;
@@ -191,7 +193,8 @@ __global__ void __launch_bounds__(kThreads, 2)
           if ((lane & 15) == p) mine = sub ? (bits >> 16) : (bits & 0xFFFFu);
         }
         const int p = lane & 15;
-        if (p < nb && c < C) planes16[2 * (((int64_t)c * nb + p) * Wst + w) + half] = (uint16_t)mine;
+        if (p < nb && c < C)
+          planes16[2 * (((int64_t)c * Wst + w) * nbp + p) + half] = (uint16_t)mine;
       }
     }
     __syncthreads();  // the tile is read before the next rows overwrite it
@@ -377,6 +380,8 @@ int code_plane_bits(int32_t C) {
   while ((1 << nb) < C) ++nb;  // codes lie in [0, C - 1]
   return nb;
 }
+
+int code_plane_stride(int nb) { return (nb + 3) & ~3; }
 
 namespace {
 

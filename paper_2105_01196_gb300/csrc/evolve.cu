@@ -99,7 +99,8 @@ struct GenArgs {
   // Evaluation inside the evolve kernel (fuse_np > 0, bitmap form): the pair words, the test's
   // variant and ratio, and the list of the slots left to the evaluation launch (ctl->n_todo).
   const uint32_t *bitmap;  // [C][C][Wst]
-  const int32_t *pair_cnt; // [C][C] rows of each pair row of the bitmap, or null
+  // [C][C], for a < b: rows of G[a][b] | rows of G[b][a] << 32 (or null)
+  const unsigned long long *pair_cnt;
   int64_t Wst, R;
   int32_t neg, ns, rnum, rden, fuse_np;
   int32_t *todo;
@@ -784,7 +785,11 @@ __device__ int fuse_or_list(const GenArgs &ga, const int32_t *c, int L, uint64_t
       // direction are the complement of the opposite direction's, and every row holds one
       if (lane == 0) {
         const int a = c[0], b = c[1];
-        const int ab = ga.pair_cnt[(int64_t)a * ga.C + b], ba = ga.pair_cnt[(int64_t)b * ga.C + a];
+        const bool lo = a < b;  // (the table holds a pair under its lower column)
+        const unsigned long long v =
+            ga.pair_cnt[(int64_t)(lo ? a : b) * ga.C + (lo ? b : a)];
+        const int lo32 = (int)(uint32_t)v, hi32 = (int)(uint32_t)(v >> 32);
+        const int ab = lo ? lo32 : hi32, ba = lo ? hi32 : lo32;
         const int R = (int)ga.R;
         if (!ga.ns) {
           rp = ab;
@@ -1757,7 +1762,7 @@ GenArgs gen_args(ebic_ctx *ctx, GenState *g) {
   ga.tabu_limit = p.tabu_hit_limit;
   if (g->fuse_np > 0) {
     ga.bitmap = ctx->bitmap.as<uint32_t>();
-    ga.pair_cnt = ctx->pair_cnt_ok ? ctx->pair_cnt.as<int32_t>() : nullptr;
+    ga.pair_cnt = ctx->pair_cnt_ok ? ctx->pair_cnt.as<unsigned long long>() : nullptr;
     ga.Wst = ctx->Wst;
     ga.R = ctx->R;
     ga.neg = p.neg_trends;

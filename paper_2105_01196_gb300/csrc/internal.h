@@ -137,12 +137,14 @@ struct EvalArgs {
 
 // Per-row rank codes (codes.cu): code width for C columns (1 for C <= 128, 2 for C <= 1024,
 // else 0 = none), rows per pass of the code kernel, padded rows per code column, the number of
-// bit planes of the codes (bits of C - 1), the rank kernel (zero-fills the padding; writes the
-// bit planes [C][nb][Wst] too when `planes` is not null) and the direct evaluation over codes.
+// bit planes of the codes (bits of C - 1) and their stride (planes stored per column and word: nb
+// rounded up to a multiple of 4), the rank kernel (zero-fills the padding; writes the bit planes
+// [C][Wst][stride] too when `planes` is not null) and the direct evaluation over codes.
 int code_bytes_for(int32_t C);
 int64_t code_rows_per_pass(int code_bytes);
 int64_t code_stride_for(int64_t R, int code_bytes);
 int code_plane_bits(int32_t C);
+int code_plane_stride(int nb);
 cudaError_t launch_rank_codes(const uint32_t *keys, int64_t R_pad, int32_t C, void *codes,
                               int code_bytes, int64_t S, uint32_t *planes, int64_t Wst,
                               int num_sms, cudaStream_t s);
@@ -187,8 +189,9 @@ struct ebic_ctx {
   bool have_matrix = false;
   DevBuf keys, bitmap, stage_x;
   bool bitmap_ok = false;
-  // rows of each pair row of the bitmap (popcount of G[a][b]), [C][C]; built with the bitmap
-  // from the rank codes' bit planes (C <= 1,024), else absent
+  // rows of the pair rows of the bitmap, [C][C] 64-bit words: for a < b, popcount(G[a][b]) in
+  // the low and popcount(G[b][a]) in the high 32 bits; built with the bitmap from the rank
+  // codes' bit planes (C <= 1,024), else absent
   DevBuf pair_cnt;
   bool pair_cnt_ok = false;
 
@@ -200,7 +203,8 @@ struct ebic_ctx {
   DevBuf d_kerr;
 
   // per-row rank codes of the loaded matrix (code_bytes 0: none) and their bit planes
-  // [C][plane_bits][Wst] (the pair-bitmap build's operand), built together on first use
+  // [C][Wst][code_plane_stride(plane_bits)] (the pair-bitmap build's operand), built together
+  // on first use
   DevBuf codes, planes;
   int code_bytes = 0;
   int64_t code_stride = 0;
@@ -275,9 +279,11 @@ cudaError_t launch_upload(const float *x, int64_t R, int32_t C, int64_t R_pad, i
 cudaError_t launch_build_bitmap(const uint32_t *keys, int64_t R_pad, int32_t C, int64_t Wst,
                                 uint32_t *bitmap, cudaStream_t s);
 // The same bitmap from the bit planes of the rank codes (nb planes per column, nb <= 10); with
-// cnt (C * C, zeroed beforehand) also each pair row's popcount, cnt[a * C + b].
+// cnt (C * C, zeroed beforehand) also the pair rows' popcounts: for a < b, cnt[a * C + b] =
+// popcount(G[a][b]) | popcount(G[b][a]) << 32.
 cudaError_t launch_build_bitmap_planes(const uint32_t *planes, int nb, int32_t C, int64_t Wst,
-                                       uint32_t *bitmap, int32_t *cnt, cudaStream_t s);
+                                       uint32_t *bitmap, unsigned long long *cnt,
+                                       cudaStream_t s);
 
 // eval.cu
 cudaError_t launch_validate_csr(const int32_t *cols, const int32_t *off, int32_t n, int32_t C,

@@ -209,7 +209,7 @@ __device__ __forceinline__ void plane_compare(const uint32_t (&A)[NB], const uin
   }
 }
 
-constexpr int kBB = 16;  // b-columns per staged batch (40 KB of static shared memory at NB = 10)
+constexpr int kBB = 16;  // b-columns per staged batch (48 KB of static shared memory at NB = 10)
 
 __device__ __forceinline__ void cp_async16_bm(void *smem, const void *gmem) {
   const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
@@ -225,16 +225,22 @@ __device__ __forceinline__ void cp_wait_bm() {
 
 // The b planes of a block's piece are staged in shared memory, kBB columns at a time and
 // double-buffered (cp.async by the whole block; the next batch is in flight while the current
-// one is compared), so the eight warps share one copy and read it with constant offsets.
-// With `cnt` (zeroed beforehand), the pair counts are accumulated too: cnt[a * C + b] = the
-// rows of G[a][b] (its popcount), from each warp's 32 words by a warp sum and one atomic.
+// one is compared), so the eight warps share one copy and read it with constant offsets.  The
+// planes are stored [C][Wst][NBP] (NBP = NB rounded up to 4): a column's chunk of 32 words is
+// one contiguous span, copied as is, and each lane reads its word's planes as NBP / 4 16-byte
+// vectors (lanes 48 or 16 bytes apart: no bank conflicts; 32 bytes apart at NBP = 8: two-way).
+// With `cnt` (zeroed beforehand), the pair counts are accumulated too: for a < b, cnt[a * C + b]
+// holds the rows of G[a][b] (its popcount) in its low 32 bits and those of G[b][a] in its high
+// 32 bits.  Each warp adds its 32 words' counts of a pair by one warp sum (the two directions'
+// counts packed in 16-bit halves, at most 1,024 each) and one 64-bit atomic.
 template <int NB>
 __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *__restrict__ planes,
                                                              int32_t C, int64_t Wst,
                                                              PieceTable tab,
                                                              uint32_t *__restrict__ G,
-                                                             int32_t *__restrict__ cnt) {
-  __shared__ __align__(16) uint32_t s_b[2][kBB][NB][32];
+                                                             unsigned long long *__restrict__ cnt) {
+  constexpr int NBP = (NB + 3) & ~3;
+  __shared__ __align__(16) uint32_t s_b[2][kBB][32][NBP];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // this block's a-block (the last one whose first piece is at or before blockIdx.y) and piece
   const int x = (int)blockIdx.y;  // (blockIdx.x is the row chunk: the blocks running together
@@ -252,15 +258,28 @@ __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *
   const int b_first = max(b_lo, ablk * 8 * kPA + kPA);  // the first b any warp of the block needs
   uint32_t A[kPA][NB];
 #pragma unroll
-  for (int i = 0; i < kPA; ++i)
+  for (int i = 0; i < kPA; ++i) {
+    const bool on = a0 + i < C && w_ok;
+    const uint4 *src = reinterpret_cast<const uint4 *>(planes + ((int64_t)(a0 + i) * Wst + w) * NBP);
 #pragma unroll
-    for (int p = 0; p < NB; ++p)
-      A[i][p] = (a0 + i < C && w_ok) ? __ldg(planes + ((int64_t)(a0 + i) * NB + p) * Wst + w) : 0u;
+    for (int q = 0; q < NBP / 4; ++q) {
+      const uint4 v = on ? __ldg(src + q) : make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (4 * q + k < NB) A[i][4 * q + k] = e[k];
+    }
+  }
   const int64_t row = (int64_t)C * Wst;  // words between G[a][.] and G[a + 1][.]
-  // the rows of pair (a, b) in this warp's 32 words, added to cnt[a * C + b] (all lanes call it)
-  auto count = [&](int a, int b, uint32_t word) {
-    const int n = (int)__reduce_add_sync(0xFFFFFFFFu, w_ok ? (unsigned)__popc(word) : 0u);
-    if (lane == 0 && n) atomicAdd(cnt + (int64_t)a * C + b, n);
+  // this warp's 32 words' counts of G[a][b] (gt) and G[b][a] (lt), packed, summed over the lanes
+  auto warp_counts = [&](uint32_t gt, uint32_t lt) -> unsigned {
+    return __reduce_add_sync(0xFFFFFFFFu, w_ok ? (unsigned)__popc(gt) | ((unsigned)__popc(lt) << 16)
+                                               : 0u);
+  };
+  auto add_counts = [&](int a, int b, unsigned n) {  // (a < b)
+    if (n)
+      atomicAdd(cnt + (int64_t)a * C + b,
+                (unsigned long long)(n & 0xFFFFu) | ((unsigned long long)(n >> 16) << 32));
   };
   if (piece == 0 && a0 < C) {
     // the diagonal words, and the pairs among the warp's own columns
@@ -280,25 +299,24 @@ __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *
             __stcs(G + (int64_t)b * row + (int64_t)a * Wst + w, lt);
           }
           if (cnt) {
-            count(a, b, gt);
-            count(b, a, lt);
+            const unsigned n = warp_counts(gt, lt);
+            if (lane == 0) add_counts(a, b, n);
           }
         }
       }
     }
   }
   if (b_first >= b_hi) return;  // (the whole block: no b beyond its columns in this piece)
-  // staging: batch t holds b = b_first + t kBB + bb; copy j of a batch is (bb, p, 16-byte part)
+  // staging: batch t holds b = b_first + t kBB + bb; copy j of a batch is 16-byte part j % span
+  // of column bb = j / span (span: the chunk's words x NBP / 4; Wst % 4 == 0)
   const int n_batches = (b_hi - b_first + kBB - 1) / kBB;
-  const int nw4 = (int)(Wst - w0 >= 32 ? 8 : (Wst - w0) / 4);  // 16-byte parts of the chunk
-                                                                // (Wst % 4 == 0)
+  const int span = (int)(Wst - w0 >= 32 ? 32 : Wst - w0) * NBP / 4;
   auto issue = [&](int t) {
     const int bs = b_first + t * kBB, nbb = min(kBB, b_hi - bs);
-    for (int j = threadIdx.x; j < nbb * NB * 8; j += blockDim.x) {
-      const int part = j & 7, bp = j >> 3, bb = bp / NB, p = bp - bb * NB;
-      if (part < nw4)
-        cp_async16_bm(&s_b[t & 1][bb][p][part * 4],
-                      planes + ((int64_t)(bs + bb) * NB + p) * Wst + w0 + part * 4);
+    for (int j = threadIdx.x; j < nbb * span; j += blockDim.x) {
+      const int bb = j / span, part = j - bb * span;
+      cp_async16_bm(&s_b[t & 1][bb][0][0] + part * 4,
+                    planes + ((int64_t)(bs + bb) * Wst + w0) * NBP + part * 4);
     }
     cp_commit_bm();
   };
@@ -324,7 +342,14 @@ __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *
         if (bs + bb >= a0 + kPA) {  // (b after the warp's own columns)
           uint32_t B[NB];
 #pragma unroll
-          for (int p = 0; p < NB; ++p) B[p] = s_b[t & 1][bb][p][lane];
+          for (int q = 0; q < NBP / 4; ++q) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(&s_b[t & 1][bb][lane][4 * q]);
+            const uint32_t e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              if (4 * q + k < NB) B[4 * q + k] = e[k];
+          }
+          unsigned n[kPA];
 #pragma unroll
           for (int i = 0; i < kPA; ++i) {
             uint32_t gt, lt;
@@ -333,10 +358,13 @@ __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *
               __stcs(g_ab + (uint32_t)i * row32, gt);
               __stcs(g_ba + (uint32_t)i * wst32, lt);
             }
-            if (cnt) {
-              count(a0 + i, bs + bb, gt);
-              count(bs + bb, a0 + i, lt);
-            }
+            n[i] = cnt ? warp_counts(gt, lt) : 0u;
+          }
+          if (cnt && lane < kPA) {  // lane i adds pair (a0 + i, b)'s counts
+            unsigned mine = n[0];
+#pragma unroll
+            for (int i = 1; i < kPA; ++i) mine = lane == i ? n[i] : mine;
+            add_counts(a0 + lane, bs + bb, mine);
           }
         }
         g_ab += Wst;
@@ -382,7 +410,8 @@ cudaError_t launch_build_bitmap(const uint32_t *keys, int64_t R_pad, int32_t C, 
 }
 
 cudaError_t launch_build_bitmap_planes(const uint32_t *planes, int nb, int32_t C, int64_t Wst,
-                                       uint32_t *bitmap, int32_t *cnt, cudaStream_t s) {
+                                       uint32_t *bitmap, unsigned long long *cnt,
+                                       cudaStream_t s) {
   const int64_t n_chunks = (Wst + 31) / 32;
   const int n_ablk = (C + 8 * kPA - 1) / (8 * kPA);
   // (the kernel offsets rows of the bitmap by up to 3 * C * Wst words in 32 bits)

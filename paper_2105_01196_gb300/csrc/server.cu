@@ -161,7 +161,7 @@ int64_t ebic_job_footprint(int64_t rows, int32_t cols, const ebic_params *p, int
   const int w = code_bytes_for(cols);
   if (w)  // rank codes and their bit planes (both forms build them)
     bytes += (int64_t)cols * code_stride_for(rows, w) * w +
-             (int64_t)cols * code_plane_bits(cols) * (R_pad / 32) * 4;
+             (int64_t)cols * code_plane_stride(code_plane_bits(cols)) * (R_pad / 32) * 4;
   bytes += 2 * P * (EBIC_MAX_LEN * 4 + 4 + 4 + 12 + 1 + 1 + 8 + 8);  // population buffers
   bytes += P * 12 + 64;                                   // evaluation scratch
   bytes += (int64_t)tabu_capacity(P * ((int64_t)n_gen + 2)) * 8;  // tabu list

@@ -90,6 +90,7 @@ SIGNATURES = {
     "ebic_build_bitmap": (ctypes.c_int, [_VP]),
     "ebic_bitmap_bytes": (ctypes.c_int64, [_I64, _I32]),
     "ebic_copy_bitmap": (ctypes.c_int, [_VP, _VP, _I64]),
+    "ebic_copy_pair_counts": (ctypes.c_int, [_VP, _VP, _I64]),
     "ebic_eval_population": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP]),
     "ebic_run_generations": (ctypes.c_int, [_VP, _VP, _I32, _VP]),
     "ebic_get_toplist": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -215,6 +216,12 @@ def ebic_bitmap_bytes(rows, cols):
 
 def ebic_copy_bitmap(ctx, out):
     _check(ctx, _lib.ebic_copy_bitmap(ctx, ptr(out), int(out.numel() if _is_torch(out) else out.size)))
+    return out
+
+
+def ebic_copy_pair_counts(ctx, out):
+    _check(ctx, _lib.ebic_copy_pair_counts(ctx, ptr(out),
+                                           int(out.numel() if _is_torch(out) else out.size)))
     return out
 
 
@@ -511,6 +518,9 @@ class Context:
 
     def copy_bitmap(self, out):
         return ebic_copy_bitmap(self.handle, out)
+
+    def copy_pair_counts(self, out):
+        return ebic_copy_pair_counts(self.handle, out)
 
     def eval_population(self, col_idx, offsets, params, *outs):
         return ebic_eval_population(self.handle, col_idx, offsets, params, *outs)

@@ -181,6 +181,31 @@ def test_bitmap_matches_oracle_definition(ebic, R, C):
         assert np.array_equal(got[a, b, :W], pair_words(x, a, b)), (a, b)
 
 
+@pytest.mark.parametrize("R,C", [(1, 2), (33, 7), (300, 129), (129, 200), (40, 1000)])
+def test_pair_counts_match_oracle_words(ebic, R, C):
+    """The pair counts the plane build accumulates (one 64-bit atomic per pair and 32-word
+    chunk): for a < b, the popcounts of the oracle's pair words G[a][b] and G[b][a] in the low and
+    high halves, zero elsewhere; on a tie-heavy matrix with rows not a multiple of 32."""
+    from oracle.bitmap import pair_words
+    g = np.random.default_rng(5 + R + C)
+    x = g.integers(-2, 3, size=(R, C)).astype(np.float32)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        ctx.build_bitmap()
+        out = np.zeros(C * C, np.uint64)
+        ctx.copy_pair_counts(out)
+    t = out.reshape(C, C)
+    assert not np.tril(t).any()
+    pairs = [(a, b) for a in range(C) for b in range(a + 1, C)]
+    if len(pairs) > 4000:
+        idx = g.choice(len(pairs), 4000, replace=False)
+        pairs = [pairs[i] for i in idx] + [(0, 1), (0, C - 1), (C - 2, C - 1)]
+    popc = lambda w: int(np.unpackbits(np.asarray(w, np.uint32).view(np.uint8)).sum())
+    for a, b in pairs:
+        lo, hi = int(t[a, b]) & 0xFFFFFFFF, int(t[a, b]) >> 32
+        assert (lo, hi) == (popc(pair_words(x, a, b)), popc(pair_words(x, b, a))), (a, b)
+
+
 def test_errors_are_reported(ebic, torch_cuda):
     torch = torch_cuda
     x = np.ones((10, 4), np.float32)
