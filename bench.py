@@ -790,28 +790,51 @@ def main():
         return
 
     eval_name = eval_kernel_name(job.used_mode if job.used_mode else MODES[args.mode], w.cols)
-    # the evaluation kernel in the generation loop (the step's bandwidth-bound kernel with the
-    # largest share), and its one full sweep per step beside it
-    part = "eval_loop" if gens > 0 else "eval"
-    traffic, traffic_source = ncu_traffic_entry(eval_name, w.name + ("-loop" if gens > 0 else ""))
-    roof = eval_roofline(stats, eval_name, peak, peak_kind, traffic, traffic_source, part)
-    if roof is not None and gens > 0:
-        roof["launches_measured"] = "the generation loop's evaluation launches (initial population "\
-                                    "and every generation); the step's full sweep is in 'sweep'"
-        sw = eval_roofline(stats, eval_name, peak, peak_kind, *ncu_traffic_entry(eval_name, w.name),
-                           part="eval_sweep")
-        roof["sweep"] = sw
-    names = {"eval": eval_name, "evolve": "k_evolve|k_evolve_seq", "finish": "k_finish",
+    # (the library's choice: a warp per slot once the slots' attempt warps exceed the GPU's)
+    g_att = 1
+    while g_att < job.params.max_attempts:
+        g_att *= 2
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    evolve_name = "k_evolve_seq" if job.P * g_att > sms * 32 else "k_evolve"
+    names = {"eval": eval_name, "evolve": evolve_name, "finish": "k_finish",
              "bitmap_build": "k_build_bitmap_planes" if w.cols <= 1024 else "k_build_bitmap",
              "rank_codes": "k_rank_codes"}
     dominant = max((k for k in stats if k not in ("eval_sweep", "eval_loop")),
                    key=lambda k: stats[k]["ms"])
+    loop_tag = w.name + ("-loop" if gens > 0 else "")
+    # The generation loop's evaluations: with the bitmap form the evolve kernel scores its short
+    # exact children itself (the pair words it reads are its algorithmic bytes) and the
+    # evaluation launches score the rest.  The roofline is the kernel with the larger share of
+    # the two, the other one and the step's one full sweep beside it.
+    part = "eval_loop" if gens > 0 else "eval"
+    roof_eval = eval_roofline(stats, eval_name, peak, peak_kind,
+                              *ncu_traffic_entry(eval_name, loop_tag), part)
+    roof_evolve = None
+    if gens > 0 and stats["evolve"]["alg_bytes"] > 0:
+        roof_evolve = eval_roofline(stats, evolve_name, peak, peak_kind,
+                                    *ncu_traffic_entry("k_evolve_seq", loop_tag), "evolve")
+    if roof_evolve is not None and stats["evolve"]["ms"] >= stats["eval_loop"]["ms"]:
+        roof = roof_evolve
+        roof["launches_measured"] = ("the generation loop's evolve launches; their algorithmic "
+                                     "bytes are the pair words (and pair counts) of the children "
+                                     "they evaluate; they also build every child (dependent "
+                                     "loads, no bulk data)")
+        roof["eval_launches"] = roof_eval
+    else:
+        roof = roof_eval
+        if roof is not None and gens > 0:
+            roof["launches_measured"] = ("the generation loop's evaluation launches (initial "
+                                         "population and every generation)")
+            if roof_evolve is not None:
+                roof["evolve_launches"] = roof_evolve
+    if roof is not None and gens > 0:
+        roof["sweep"] = eval_roofline(stats, eval_name, peak, peak_kind,
+                                      *ncu_traffic_entry(eval_name, w.name), part="eval_sweep")
     if roof is not None:
         roof["dominant_kernel"] = names[dominant]
-        if dominant != "eval":
+        if dominant not in ("eval", "evolve"):
             roof["note"] = (f"{names[dominant]} has the largest share of kernel time; it moves "
-                            "no bulk data, so the roofline is the evaluation kernel's, the path's "
-                            "bandwidth-bound kernel")
+                            "no bulk data, so the roofline is the evaluation's")
     line = {"metric": METRIC, "value": units / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup),
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",

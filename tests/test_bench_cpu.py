@@ -16,9 +16,12 @@ def test_ncu_traffic_reads_the_committed_summary():
     d = bench.ncu_traffic("k_eval_bitmap", "default-loop")
     t, src = bench.ncu_traffic_entry("k_eval_bitmap", "tieheavy-loop")
     assert d is not None and t is not None
-    # DRAM bytes per launch stay below the algorithmic bytes (part of the pair words hit L2)
+    # DRAM bytes per launch stay below the algorithmic bytes (part of the pair words hit L2;
+    # the loop launches' mean includes the initial population's full sweep)
     assert 1e6 < d < 5.39e6
-    assert 1e8 < t < 2.46e8
+    assert 3e7 < t < 1.3e8
+    e, src_e = bench.ncu_traffic_entry("k_evolve_seq", "tieheavy-loop")
+    assert 3e7 < e < 1.3e8 and "traffic_k_evolve_seq.txt" in src_e
     assert "traffic_k_eval_bitmap.txt" in src and "commit" in src
     assert bench.ncu_traffic("k_eval_bitmap", "no-such-workload") is None
     assert bench.ncu_traffic("no_such_kernel", "default") is None
