@@ -2061,10 +2061,12 @@ int gen_create(ebic_ctx *ctx, const ebic_params *p) {
       1, std::min<int64_t>((g->P + kSeqWarps - 1) / kSeqWarps,
                            (int64_t)ctx->num_sms * std::max(seq_per_sm, 1)));
 
-  // one block per 2,048 slots: the slot loop spread, few blocks to meet at the end (measured:
-  // one block for P = 800, 8.4 against 10.2 us with two; two for P = 4,096, 13.6 against 15.2 us)
+  // one block per 1,024 slots (a slot per thread): the slot loop spread, few blocks to meet at
+  // the end (measured: one block for P = 800, 8.4 against 10.2 us with two; with the evaluation
+  // inside the evolve kernel, 16.3 against 18.6 us at P = 8,192 and 12.0 against 14.6 us at
+  // P = 4,096 over one block per 2,048 slots)
   g->finish_blocks = (int)std::max<int64_t>(
-      1, std::min<int64_t>((g->P + 2 * kTopThreads - 1) / (2 * kTopThreads), ctx->num_sms));
+      1, std::min<int64_t>((g->P + kTopThreads - 1) / kTopThreads, ctx->num_sms));
   EBIC_CHECK_CUDA(ctx, cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
   for (cudaEvent_t &e : g->cap_ev) EBIC_CHECK_CUDA(ctx, cudaEventCreate(&e));
   return gen_reset(ctx, g);
