@@ -181,13 +181,16 @@ __global__ void __launch_bounds__(kBW * 32, 4) k_build_bitmap(const uint32_t *__
 // The b-range of an a-block is cut into pieces so that every block has about the same work
 // (the first a-blocks pair with many more columns than the last ones).  The row chunk is the
 // fastest block index, so the blocks resident together write adjacent 128-byte pieces of the
-// same pair rows, which L2 then merges into whole sectors before they reach DRAM.
+// same pair rows, which L2 then merges into whole sectors before they reach DRAM.  Piece p of
+// a-block g starts at column 32 (g + 4 p); the pieces run in the order of that start (then of
+// g), so the blocks in flight together read the same b planes, which stay in L2 between them.
 constexpr int kPA = 4;       // a-columns per warp
 constexpr int kPiece = 128;  // b-columns per block (at most)
 constexpr int kMaxABlocks = 32;  // a-blocks of 32 columns: C <= 1,024
+constexpr int kMaxPieces = kMaxABlocks * (1024 / kPiece);
 
 struct PieceTable {
-  int32_t base[kMaxABlocks + 1];  // first piece of each a-block (prefix sums)
+  uint16_t item[kMaxPieces];  // piece y of the launch: a-block << 8 | piece within the a-block
 };
 
 template <int LUT>
@@ -242,14 +245,10 @@ __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *
   constexpr int NBP = (NB + 3) & ~3;
   __shared__ __align__(16) uint32_t s_b[2][kBB][32][NBP];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // this block's a-block (the last one whose first piece is at or before blockIdx.y) and piece
-  const int x = (int)blockIdx.y;  // (blockIdx.x is the row chunk: the blocks running together
-                                  // write neighbouring pieces of the same pair rows)
-  int ablk = 0;
-#pragma unroll
-  for (int step = kMaxABlocks / 2; step >= 1; step >>= 1)
-    if (ablk + step < kMaxABlocks && tab.base[ablk + step] <= x) ablk += step;
-  const int piece = x - tab.base[ablk];
+  // this block's a-block and piece (blockIdx.x is the row chunk: the blocks running together
+  // write neighbouring pieces of the same pair rows)
+  const int item = tab.item[blockIdx.y];
+  const int ablk = item >> 8, piece = item & 0xFF;
   const int64_t w0 = (int64_t)blockIdx.x * 32, w = w0 + lane;
   const bool w_ok = w < Wst;
   const int a0 = (ablk * 8 + warp) * kPA;
@@ -417,12 +416,16 @@ cudaError_t launch_build_bitmap_planes(const uint32_t *planes, int nb, int32_t C
   // (the kernel offsets rows of the bitmap by up to 3 * C * Wst words in 32 bits)
   if (n_ablk > kMaxABlocks || n_chunks > 0x7FFFFFFF || 4 * (int64_t)C * Wst > 0xFFFFFFFFll)
     return cudaErrorInvalidValue;
+  // every (a-block g, piece p) with b in [32 g, C), in the order of the piece's first column
+  // 32 (g + 4 p), then of g
   PieceTable tab{};
   int total = 0;
-  for (int g = 0; g <= kMaxABlocks; ++g) {
-    tab.base[g] = total;
-    if (g < n_ablk) total += (C - g * 8 * kPA + kPiece - 1) / kPiece;  // b in [32 g, C)
-  }
+  const int k_max = (C + 8 * kPA - 1) / (8 * kPA);
+  for (int k = 0; k < k_max; ++k)
+    for (int g = k % 4; g <= k && g < n_ablk; g += 4) {
+      const int piece = (k - g) / 4;  // (starts at column 32 k < C)
+      tab.item[total++] = (uint16_t)(g << 8 | piece);
+    }
   const dim3 grid((unsigned)n_chunks, (unsigned)total), block(256);  // (total <= 32 * 8 pieces)
   switch (nb) {
     case 1: k_build_bitmap_planes<1><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
