@@ -480,7 +480,10 @@ class Job:
         self.outs_d = [torch.zeros(self.P, dtype=torch.int32, device=dev) for _ in range(3)]
         self.outs_d.append(torch.zeros(self.P, dtype=torch.int64, device=dev))
         if host_copies:
+            # (every input the end-to-end step copies comes from pinned host memory)
             self.x_h = torch.from_numpy(self.x).pin_memory()
+            self.ci_h = torch.from_numpy(self.ci).pin_memory()
+            self.off_h = torch.from_numpy(self.off).pin_memory()
             self.outs_h = [torch.zeros(self.P, dtype=torch.int32).pin_memory() for _ in range(3)]
             self.outs_h.append(torch.zeros(self.P, dtype=torch.int64).pin_memory())
         self.params = ebic.Params.make(mode=MODES[mode], ipw=ipw, fuse_pairs=fuse_pairs,
@@ -500,7 +503,7 @@ class Job:
         ctx = self.ctx
         if host:
             ctx.load_matrix(self.x_h)
-            ctx.eval_population(self.ci, self.off, self.params, *self.outs_h)
+            ctx.eval_population(self.ci_h, self.off_h, self.params, *self.outs_h)
         else:
             ctx.load_matrix(self.x_d)
             if around_sweep:
