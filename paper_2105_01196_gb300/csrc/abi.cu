@@ -383,6 +383,8 @@ int ebic_destroy(ebic_ctx *ctx) {
   for (DevBuf *b : bufs) b->release();
   prof_collect(ctx);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : ctx->seg_ev) cudaEventDestroy(e);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return EBIC_OK;
@@ -394,6 +396,99 @@ int64_t ebic_bitmap_bytes(int64_t rows, int32_t cols) {
   if (rows < 1 || cols < 1) return 0;
   return (int64_t)cols * cols * (round_up(rows, 128) / 32) * 4;
 }
+
+}  // extern "C"
+
+namespace {
+
+// The segmented load of a row-major host matrix (see ebic_load_matrix): kLoadSegments segments
+// of a multiple of 8,192 rows (whole 1,024-row chunks of the bitmap, whole tiles of every
+// kernel), the last one with the padded tail.
+constexpr int64_t kLoadSegments = 4;
+
+int load_matrix_segmented(ebic_ctx *ctx, const float *x, int64_t rows, int32_t cols,
+                          int64_t R_pad) {
+  const bool bitmap = ctx->tuned_mode == EBIC_MODE_BITMAP;
+  const int64_t C = cols, Wst = R_pad / 32;
+  const int cb = code_bytes_for(cols), nb = code_plane_bits(cols);
+  const int64_t S = code_stride_for(rows, cb);
+  cudaStream_t s = ctx->stream;
+  EBIC_CHECK_CUDA(ctx, ctx->stage_x.ensure((size_t)rows * C * sizeof(float), s));
+  EBIC_CHECK_CUDA(ctx, ctx->codes.ensure((size_t)C * S * cb, s));
+  EBIC_CHECK_CUDA(ctx, ctx->planes.ensure((size_t)C * code_plane_stride(nb) * Wst * 4, s));
+  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(ctx->codes.p, 0, (size_t)C * S * cb, s));
+  if (bitmap) {
+    EBIC_CHECK_CUDA(ctx, ctx->bitmap.ensure((size_t)ebic_bitmap_bytes(rows, cols), s));
+    EBIC_CHECK_CUDA(ctx, prepare_bitmap_eval());
+    const size_t nc = (size_t)C * C * sizeof(unsigned long long);
+    EBIC_CHECK_CUDA(ctx, ctx->pair_cnt.ensure(nc, s));
+    EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(ctx->pair_cnt.p, 0, nc, s));
+  }
+  if (!ctx->copy_stream)
+    EBIC_CHECK_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  const int64_t seg =
+      std::max<int64_t>(8192, round_up((R_pad + kLoadSegments - 1) / kLoadSegments, 8192));
+  const int64_t n_seg = (R_pad + seg - 1) / seg;
+  while ((int64_t)ctx->seg_ev.size() < n_seg + 1) {
+    cudaEvent_t e = nullptr;
+    EBIC_CHECK_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->seg_ev.push_back(e);
+  }
+  // the copy stream starts after the context stream's earlier work (which may still read the
+  // staging buffer)
+  EBIC_CHECK_CUDA(ctx, cudaEventRecord(ctx->seg_ev[n_seg], s));
+  EBIC_CHECK_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->seg_ev[n_seg], 0));
+  EBIC_CHECK_CUDA(ctx, cudaMemsetAsync(ctx->d_err.p, 0, sizeof(int32_t), s));
+  float *stage = ctx->stage_x.as<float>();
+  for (int64_t i = 0; i < n_seg; ++i) {
+    const int64_t r0 = i * seg, r1 = std::min(R_pad, r0 + seg);
+    if (r0 < rows) {
+      const int64_t n = std::min(r1, rows) - r0;
+      EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(stage + r0 * C, x + r0 * C, (size_t)(n * C) * 4,
+                                           cudaMemcpyHostToDevice, ctx->copy_stream));
+      EBIC_CHECK_CUDA(ctx, cudaEventRecord(ctx->seg_ev[i], ctx->copy_stream));
+      EBIC_CHECK_CUDA(ctx, cudaStreamWaitEvent(s, ctx->seg_ev[i], 0));
+    }
+    EBIC_CHECK_CUDA(ctx, launch_upload_rows(stage, rows, cols, R_pad, ctx->keys.as<uint32_t>(),
+                                            ctx->d_err.as<int32_t>(), r0, r1, s));
+    EBIC_CHECK_CUDA(ctx, launch_rank_codes_rows(ctx->keys.as<uint32_t>(), R_pad, cols,
+                                                ctx->codes.p, cb, S, ctx->planes.as<uint32_t>(),
+                                                Wst, ctx->num_sms, r0, r1, s));
+    prof_count(ctx, -1, 1);
+    prof_count(ctx, EBIC_KERNEL_RANK_CODES, 1);
+    if (bitmap) {
+      EBIC_CHECK_CUDA(ctx, launch_build_bitmap_planes(
+                               ctx->planes.as<uint32_t>(), nb, cols, Wst,
+                               ctx->bitmap.as<uint32_t>(),
+                               ctx->pair_cnt.as<unsigned long long>(), s, r0 / 1024,
+                               r1 == R_pad ? -1 : r1 / 1024));
+      prof_count(ctx, EBIC_KERNEL_BITMAP_BUILD, 1);
+    }
+  }
+  int32_t herr = 0;
+  EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&herr, ctx->d_err.p, sizeof(int32_t),
+                                       cudaMemcpyDeviceToHost, s));
+  EBIC_CHECK_CUDA(ctx, cudaStreamSynchronize(s));
+  if (herr) return ebic_fail(ctx, EBIC_ENAN, "matrix holds NaN or Inf");
+  ctx->R = rows;
+  ctx->C = cols;
+  ctx->R_pad = R_pad;
+  ctx->Wst = Wst;
+  direct_tma_prepare(&ctx->dtma, ctx->keys.as<uint32_t>(), R_pad, cols);
+  ctx->code_bytes = cb;
+  ctx->code_stride = S;
+  ctx->plane_bits = nb;
+  ctx->codes_ready = true;
+  ctx->bitmap_ok = bitmap;
+  ctx->pair_cnt_ok = bitmap;
+  ctx->have_matrix = true;
+  ctx->err.clear();
+  return EBIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 int ebic_load_matrix(ebic_ctx *ctx, const float *x, int64_t rows, int32_t cols, int32_t layout) {
   if (!ctx) return EBIC_EINVAL;
@@ -422,6 +517,12 @@ int ebic_load_matrix(ebic_ctx *ctx, const float *x, int64_t rows, int32_t cols, 
   }
   const int64_t R_pad = round_up(rows, 128);
   EBIC_CHECK_CUDA(ctx, ctx->keys.ensure((size_t)cols * R_pad * sizeof(uint32_t), ctx->stream));
+  // A host matrix of a shape the autotuner measured, in a form that reads rank codes: the copy
+  // goes in segments, and each segment's keys, rank codes, bit planes and (bitmap form) pair
+  // words are built while the next segment is copied.
+  if (!ebic_is_device_ptr(x) && layout == EBIC_LAYOUT_ROW_MAJOR && code_bytes_for(cols) &&
+      ctx->tuned && ctx->tuned_mode != EBIC_MODE_STAGED && !ctx->prof)
+    return load_matrix_segmented(ctx, x, rows, cols, R_pad);
   const float *src = x;
   if (!ebic_is_device_ptr(x)) {
     EBIC_CHECK_CUDA(ctx, ctx->stage_x.ensure((size_t)rows * cols * sizeof(float), ctx->stream));

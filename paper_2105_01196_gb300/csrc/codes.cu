@@ -140,7 +140,8 @@ __device__ __forceinline__ int count_below(const uint32_t *srt, uint32_t q) {
 template <typename T, int EPL>
 __global__ void __launch_bounds__(kThreads, 2)
     k_rank_codes(const uint32_t *__restrict__ keys, int64_t R_pad, int32_t C, int64_t S,
-                 T *__restrict__ codes, uint32_t *__restrict__ planes, int64_t Wst, int nb) {
+                 T *__restrict__ codes, uint32_t *__restrict__ planes, int64_t Wst, int nb,
+                 int64_t t_begin, int64_t t_end) {
   constexpr int N = 32 * EPL;
   constexpr int kSorted = N + N / 32;  // words of one warp's sorted buffer
   extern __shared__ __align__(16) uint32_t s_rank[];
@@ -149,8 +150,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   uint32_t *tile = s_rank + kWarps * kSorted;  // [C][kTileStride]: keys, then codes in place
   uint16_t *planes16 = reinterpret_cast<uint16_t *>(planes);
   const int nbp = (nb + 3) & ~3;  // planes per (column, word) in the layout
-  const int64_t n_tiles = R_pad / kRankRows;
-  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+  // (tiles [t_begin, t_end) of the R_pad / kRankRows)
+  for (int64_t t = t_begin + blockIdx.x; t < t_end; t += gridDim.x) {
     const int64_t r0 = t * kRankRows;
     for (int i = threadIdx.x; i < C * kRankRows; i += kThreads) {
       const int c = i / kRankRows, rho = i % kRankRows;
@@ -387,7 +388,8 @@ namespace {
 
 template <typename T, int EPL>
 cudaError_t launch_rank_epl(const uint32_t *keys, int64_t R_pad, int32_t C, T *codes, int64_t S,
-                            uint32_t *planes, int64_t Wst, int nb, int num_sms, cudaStream_t s) {
+                            uint32_t *planes, int64_t Wst, int nb, int num_sms, cudaStream_t s,
+                            int64_t r_begin, int64_t r_end) {
   constexpr int N = 32 * EPL;
   const size_t smem = (size_t)kWarps * (N + N / 32) * 4 + (size_t)C * kTileStride * 4;
   // one fixed limit for every context (no call lowers another's), set once per device
@@ -409,33 +411,45 @@ cudaError_t launch_rank_epl(const uint32_t *keys, int64_t R_pad, int32_t C, T *c
       attr_set[dev] = true;
     }
   }
-  const int64_t n_tiles = R_pad / kRankRows;
-  const int64_t grid =
-      std::min<int64_t>(n_tiles, (int64_t)num_sms * blocks_per_sm(k_rank_codes<T, EPL>, smem));
+  const int64_t t_begin = r_begin / kRankRows, t_end = r_end / kRankRows;
+  const int64_t grid = std::min<int64_t>(
+      t_end - t_begin, (int64_t)num_sms * blocks_per_sm(k_rank_codes<T, EPL>, smem));
   k_rank_codes<T, EPL><<<(unsigned)grid, kThreads, smem, s>>>(keys, R_pad, C, S, codes, planes,
-                                                                Wst, nb);
+                                                                Wst, nb, t_begin, t_end);
   return cudaGetLastError();
 }
 
 }  // namespace
 
+cudaError_t launch_rank_codes_rows(const uint32_t *keys, int64_t R_pad, int32_t C, void *codes,
+                                   int code_bytes, int64_t S, uint32_t *planes, int64_t Wst,
+                                   int num_sms, int64_t r_begin, int64_t r_end, cudaStream_t s) {
+  if (C > 1024 || code_bytes != (C <= 128 ? 1 : 2)) return cudaErrorInvalidValue;
+  if (r_begin < 0 || r_begin % kRankRows || r_end > R_pad || r_end % kRankRows ||
+      r_end <= r_begin)
+    return cudaErrorInvalidValue;
+  const int nb = code_plane_bits(C);
+#define EBIC_RANK(T, EPL, cd) \
+  launch_rank_epl<T, EPL>(keys, R_pad, C, cd, S, planes, Wst, nb, num_sms, s, r_begin, r_end)
+  if (code_bytes == 1) {
+    uint8_t *cd = static_cast<uint8_t *>(codes);
+    return C <= 32 ? EBIC_RANK(uint8_t, 1, cd) : C <= 64 ? EBIC_RANK(uint8_t, 2, cd)
+                                                         : EBIC_RANK(uint8_t, 4, cd);
+  }
+  uint16_t *cd = static_cast<uint16_t *>(codes);
+  return C <= 256 ? EBIC_RANK(uint16_t, 8, cd) : C <= 512 ? EBIC_RANK(uint16_t, 16, cd)
+                                                          : EBIC_RANK(uint16_t, 32, cd);
+#undef EBIC_RANK
+}
+
 cudaError_t launch_rank_codes(const uint32_t *keys, int64_t R_pad, int32_t C, void *codes,
                               int code_bytes, int64_t S, uint32_t *planes, int64_t Wst,
                               int num_sms, cudaStream_t s) {
+  // (the rows of the code columns past R_pad, up to S, stay zero)
   cudaError_t e = cudaMemsetAsync(codes, 0, (size_t)C * S * code_bytes, s);
   if (e != cudaSuccess) return e;
-  if (C > 1024 || code_bytes != (C <= 128 ? 1 : 2)) return cudaErrorInvalidValue;
-  const int nb = code_plane_bits(C);
-  if (code_bytes == 1) {
-    uint8_t *cd = static_cast<uint8_t *>(codes);
-    return C <= 32 ? launch_rank_epl<uint8_t, 1>(keys, R_pad, C, cd, S, planes, Wst, nb, num_sms, s)
-         : C <= 64 ? launch_rank_epl<uint8_t, 2>(keys, R_pad, C, cd, S, planes, Wst, nb, num_sms, s)
-                   : launch_rank_epl<uint8_t, 4>(keys, R_pad, C, cd, S, planes, Wst, nb, num_sms, s);
-  }
-  uint16_t *cd = static_cast<uint16_t *>(codes);
-  return C <= 256 ? launch_rank_epl<uint16_t, 8>(keys, R_pad, C, cd, S, planes, Wst, nb, num_sms, s)
-       : C <= 512 ? launch_rank_epl<uint16_t, 16>(keys, R_pad, C, cd, S, planes, Wst, nb, num_sms, s)
-                  : launch_rank_epl<uint16_t, 32>(keys, R_pad, C, cd, S, planes, Wst, nb, num_sms, s);
+  return launch_rank_codes_rows(keys, R_pad, C, codes, code_bytes, S, planes, Wst, num_sms, 0,
+                                R_pad, s);
 }
 
 cudaError_t launch_eval_codes(const EvalArgs &a0, const PopView &pv, int num_sms, cudaStream_t s,

@@ -148,6 +148,10 @@ int code_plane_stride(int nb);
 cudaError_t launch_rank_codes(const uint32_t *keys, int64_t R_pad, int32_t C, void *codes,
                               int code_bytes, int64_t S, uint32_t *planes, int64_t Wst,
                               int num_sms, cudaStream_t s);
+// The rows [r_begin, r_end) only (multiples of 16), codes not cleared beforehand.
+cudaError_t launch_rank_codes_rows(const uint32_t *keys, int64_t R_pad, int32_t C, void *codes,
+                                   int code_bytes, int64_t S, uint32_t *planes, int64_t Wst,
+                                   int num_sms, int64_t r_begin, int64_t r_end, cudaStream_t s);
 cudaError_t launch_eval_codes(const EvalArgs &a, const PopView &pv, int num_sms, cudaStream_t s,
                               bool pdl);
 
@@ -179,6 +183,10 @@ struct ebic_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // a host matrix's segments are copied on copy_stream, each followed by an event that the
+  // context stream waits for before it processes that segment (created on first use)
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> seg_ev;
   int num_sms = 0;
   int64_t l2_bytes = 0;  // the device's L2 size
   std::string err;
@@ -276,14 +284,20 @@ int ebic_check_run_params(ebic_ctx *ctx, const ebic_params *p);
 // matrix.cu
 cudaError_t launch_upload(const float *x, int64_t R, int32_t C, int64_t R_pad, int32_t layout,
                           uint32_t *keys, int32_t *err, cudaStream_t s);
+// Rows [r_begin, r_end) of a row-major upload (multiples of 32; x is the whole matrix).
+cudaError_t launch_upload_rows(const float *x, int64_t R, int32_t C, int64_t R_pad,
+                               uint32_t *keys, int32_t *err, int64_t r_begin, int64_t r_end,
+                               cudaStream_t s);
 cudaError_t launch_build_bitmap(const uint32_t *keys, int64_t R_pad, int32_t C, int64_t Wst,
                                 uint32_t *bitmap, cudaStream_t s);
 // The same bitmap from the bit planes of the rank codes (nb planes per column, nb <= 10); with
 // cnt (C * C, zeroed beforehand) also the pair rows' popcounts: for a < b, cnt[a * C + b] =
 // popcount(G[a][b]) | popcount(G[b][a]) << 32.
+// chunk0 / chunk1: only the 32-word row chunks [chunk0, chunk1) (chunk1 < 0: to the end).
 cudaError_t launch_build_bitmap_planes(const uint32_t *planes, int nb, int32_t C, int64_t Wst,
                                        uint32_t *bitmap, unsigned long long *cnt,
-                                       cudaStream_t s);
+                                       cudaStream_t s, int64_t chunk0 = 0,
+                                       int64_t chunk1 = -1);
 
 // eval.cu
 cudaError_t launch_validate_csr(const int32_t *cols, const int32_t *off, int32_t n, int32_t C,

@@ -23,11 +23,12 @@ __device__ __forceinline__ bool not_finite(uint32_t u) { return (u & kExpMask) =
 
 // Row-major x[R][C] -> keys[C][R_pad] through a 32x32 shared-memory tile (coalesced on both
 // sides).  Rows in [R, R_pad) get key 0, which never compares greater than anything.
+// (rows [r_begin, r_end) of the R_pad: block x covers rows r_begin + 32 x ..)
 __global__ void k_upload_rowmajor(const float *__restrict__ x, int64_t R, int32_t C,
                                   int64_t R_pad, uint32_t *__restrict__ keys,
-                                  int32_t *__restrict__ err) {
+                                  int32_t *__restrict__ err, int64_t r_begin, int64_t r_end) {
   __shared__ uint32_t tile[32][33];
-  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int64_t r0 = r_begin + (int64_t)blockIdx.x * 32;
   const int32_t c0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
   bool bad = false;
@@ -49,7 +50,7 @@ __global__ void k_upload_rowmajor(const float *__restrict__ x, int64_t R, int32_
   for (int j = ty; j < 32; j += 8) {
     const int32_t c = c0 + j;
     const int64_t r = r0 + tx;
-    if (c < C && r < R_pad) keys[(int64_t)c * R_pad + r] = tile[tx][j];
+    if (c < C && r < r_end) keys[(int64_t)c * R_pad + r] = tile[tx][j];
   }
 }
 
@@ -241,7 +242,8 @@ __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *
                                                              int32_t C, int64_t Wst,
                                                              PieceTable tab,
                                                              uint32_t *__restrict__ G,
-                                                             unsigned long long *__restrict__ cnt) {
+                                                             unsigned long long *__restrict__ cnt,
+                                                             int64_t chunk0) {
   constexpr int NBP = (NB + 3) & ~3;
   __shared__ __align__(16) uint32_t s_b[2][kBB][32][NBP];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *
   // write neighbouring pieces of the same pair rows)
   const int item = tab.item[blockIdx.y];
   const int ablk = item >> 8, piece = item & 0xFF;
-  const int64_t w0 = (int64_t)blockIdx.x * 32, w = w0 + lane;
+  const int64_t w0 = (chunk0 + (int64_t)blockIdx.x) * 32, w = w0 + lane;
   const bool w_ok = w < Wst;
   const int a0 = (ablk * 8 + warp) * kPA;
   const int b_lo = ablk * 8 * kPA + piece * kPiece;  // the piece's b-range
@@ -376,11 +378,20 @@ __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *
 
 }  // namespace
 
+cudaError_t launch_upload_rows(const float *x, int64_t R, int32_t C, int64_t R_pad,
+                               uint32_t *keys, int32_t *err, int64_t r_begin, int64_t r_end,
+                               cudaStream_t s) {
+  if (r_begin < 0 || r_begin % 32 || r_end > R_pad || r_end % 32 || r_end <= r_begin)
+    return cudaErrorInvalidValue;
+  dim3 grid((unsigned)((r_end - r_begin) / 32), (unsigned)((C + 31) / 32));
+  k_upload_rowmajor<<<grid, dim3(32, 8), 0, s>>>(x, R, C, R_pad, keys, err, r_begin, r_end);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_upload(const float *x, int64_t R, int32_t C, int64_t R_pad, int32_t layout,
                           uint32_t *keys, int32_t *err, cudaStream_t s) {
   if (layout == EBIC_LAYOUT_ROW_MAJOR) {
-    dim3 grid((unsigned)(R_pad / 32), (unsigned)((C + 31) / 32));
-    k_upload_rowmajor<<<grid, dim3(32, 8), 0, s>>>(x, R, C, R_pad, keys, err);
+    return launch_upload_rows(x, R, C, R_pad, keys, err, 0, R_pad, s);
   } else {
     const int64_t total = (int64_t)C * R_pad;
     int64_t blocks = (total + 255) / 256;
@@ -410,8 +421,11 @@ cudaError_t launch_build_bitmap(const uint32_t *keys, int64_t R_pad, int32_t C, 
 
 cudaError_t launch_build_bitmap_planes(const uint32_t *planes, int nb, int32_t C, int64_t Wst,
                                        uint32_t *bitmap, unsigned long long *cnt,
-                                       cudaStream_t s) {
-  const int64_t n_chunks = (Wst + 31) / 32;
+                                       cudaStream_t s, int64_t chunk0, int64_t chunk1) {
+  const int64_t n_all = (Wst + 31) / 32;
+  if (chunk1 < 0 || chunk1 > n_all) chunk1 = n_all;
+  if (chunk0 < 0 || chunk0 >= chunk1) return chunk0 == chunk1 ? cudaSuccess : cudaErrorInvalidValue;
+  const int64_t n_chunks = chunk1 - chunk0;
   const int n_ablk = (C + 8 * kPA - 1) / (8 * kPA);
   // (the kernel offsets rows of the bitmap by up to 3 * C * Wst words in 32 bits)
   if (n_ablk > kMaxABlocks || n_chunks > 0x7FFFFFFF || 4 * (int64_t)C * Wst > 0xFFFFFFFFll)
@@ -428,16 +442,26 @@ cudaError_t launch_build_bitmap_planes(const uint32_t *planes, int nb, int32_t C
     }
   const dim3 grid((unsigned)n_chunks, (unsigned)total), block(256);  // (total <= 32 * 8 pieces)
   switch (nb) {
-    case 1: k_build_bitmap_planes<1><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
-    case 2: k_build_bitmap_planes<2><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
-    case 3: k_build_bitmap_planes<3><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
-    case 4: k_build_bitmap_planes<4><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
-    case 5: k_build_bitmap_planes<5><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
-    case 6: k_build_bitmap_planes<6><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
-    case 7: k_build_bitmap_planes<7><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
-    case 8: k_build_bitmap_planes<8><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
-    case 9: k_build_bitmap_planes<9><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
-    case 10: k_build_bitmap_planes<10><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt); break;
+    case 1: k_build_bitmap_planes<1><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt, chunk0);
+      break;
+    case 2: k_build_bitmap_planes<2><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt, chunk0);
+      break;
+    case 3: k_build_bitmap_planes<3><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt, chunk0);
+      break;
+    case 4: k_build_bitmap_planes<4><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt, chunk0);
+      break;
+    case 5: k_build_bitmap_planes<5><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt, chunk0);
+      break;
+    case 6: k_build_bitmap_planes<6><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt, chunk0);
+      break;
+    case 7: k_build_bitmap_planes<7><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt, chunk0);
+      break;
+    case 8: k_build_bitmap_planes<8><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt, chunk0);
+      break;
+    case 9: k_build_bitmap_planes<9><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt, chunk0);
+      break;
+    case 10: k_build_bitmap_planes<10><<<grid, block, 0, s>>>(planes, C, Wst, tab, bitmap, cnt, chunk0);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -60,3 +60,49 @@ def test_autotuned_generations_match_oracle():
     assert rep.n_evaluated == rep2.n_evaluated == st.n_evaluated
     assert [(e["cols"], e["f"]) for e in top] == [(tuple(e.cols), e.f) for e in st.top]
     assert [list(c[:n]) for c, n in zip(pop[0], pop[1])] == [list(c) for c in st.pop]
+
+
+@pytest.mark.parametrize("R,C,seed", [(40000, 48, 3), (20000, 300, 4)])
+def test_tuned_host_matrix_loads_in_segments(R, C, seed):
+    """A host matrix of a shape the autotuner measured is copied in segments, each segment's
+    keys, rank codes, bit planes and (bitmap form) pair words built while the next one is
+    copied: the load launches the rank-code kernel once per segment, and the results equal the
+    oracle's (counts and fitness of a population; with the bitmap form, the pair words of a
+    sample of pairs and the pair counts), with rows past the last segment boundary."""
+    from oracle.bitmap import pair_words
+    from paper_2105_01196_gb300 import ebic
+    g = np.random.default_rng(seed)
+    x = g.integers(-3, 4, size=(R, C)).astype(np.float32)
+    x[g.random((R, C)) < 0.03] = -0.0
+    lens = g.integers(2, 9, size=64)
+    ci = np.concatenate([g.choice(C, size=L, replace=False) for L in lens]).astype(np.int32)
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    p = ebic.Params.make(neg_trends=1, ratio_num=85, ratio_den=100, mode=ebic.MODE_AUTO)
+    op = OParams(neg_trends=1, ratio_num=85, ratio_den=100, min_rows=p.min_rows, col_cap=p.col_cap)
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x.copy())
+        tune = ctx.autotune(ci, off, p, 100)
+        before = ctx.profile_read(ebic.KERNEL_RANK_CODES)["launches"]
+        ctx.load_matrix(x)                                # (host, same shape: segmented)
+        r_pad = (R + 127) // 128 * 128
+        seg = max(8192, -(-((r_pad + 3) // 4) // 8192) * 8192)     # (four segments)
+        assert ctx.profile_read(ebic.KERNEL_RANK_CODES)["launches"] - before == -(-r_pad // seg)
+        got = ctx.eval_population(ci, off, p)
+        if tune["mode"] == ebic.MODE_BITMAP:
+            wst = r_pad // 32
+            words = np.zeros(C * C * wst, np.uint32)
+            ctx.copy_bitmap(words)
+            cnt = np.zeros(C * C, np.uint64)
+            ctx.copy_pair_counts(cnt)
+            words = words.reshape(C, C, wst)
+            cnt = cnt.reshape(C, C)
+            W = (R + 31) // 32
+            popc = lambda w: int(np.unpackbits(np.asarray(w, np.uint32).view(np.uint8)).sum())
+            for a, b in [(0, 1), (C - 2, C - 1)] + [tuple(sorted(g.choice(C, 2, replace=False)))
+                                                     for _ in range(40)]:
+                wab, wba = pair_words(x, a, b), pair_words(x, b, a)
+                assert np.array_equal(words[a, b, :W], wab) and np.array_equal(words[b, a, :W], wba)
+                assert int(cnt[a, b]) == popc(wab) | (popc(wba) << 32)
+    want = ocounts.eval_population(x, ci, off, op)
+    for g_, w_ in zip(got, want):
+        assert np.array_equal(np.asarray(g_, np.int64), np.asarray(w_, np.int64))
