@@ -338,7 +338,9 @@ __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *
     if (active) {
       uint32_t *g_ab = G + (int64_t)a0 * row + (int64_t)bs * Wst + w;
       uint32_t *g_ba = G + (int64_t)bs * row + (int64_t)a0 * Wst + w;
-#pragma unroll 1
+      // (b columns are independent: unrolled, their comparator chains interleave; the build at
+      // 60,000 x 1,000 took 2.33 ms unrolled 1 time, 2.25 ms 2, 2.22 ms 4, 2.18 ms 8, 2.21 ms 16)
+#pragma unroll 8
       for (int bb = 0; bb < nbb; ++bb) {
         if (bs + bb >= a0 + kPA) {  // (b after the warp's own columns)
           uint32_t B[NB];
