@@ -399,6 +399,21 @@ int64_t ebic_bitmap_bytes(int64_t rows, int32_t cols) {
 
 }  // extern "C"
 
+void ctx_release_buffers(ebic_ctx *ctx) {
+  gen_state_free(ctx->gen);
+  ctx->gen = nullptr;
+  DevBuf *bufs[] = {&ctx->keys, &ctx->bitmap, &ctx->stage_x, &ctx->ev_cols, &ctx->ev_off,
+                    &ctx->ev_out, &ctx->ev_fit, &ctx->codes, &ctx->planes, &ctx->pair_cnt};
+  for (DevBuf *b : bufs) b->release();
+  ctx->have_matrix = false;
+  ctx->bitmap_ok = false;
+  ctx->pair_cnt_ok = false;
+  ctx->codes_ready = false;
+  ctx->tuned = false;
+  ctx->R = ctx->R_pad = ctx->Wst = 0;
+  ctx->C = 0;
+}
+
 namespace {
 
 // The segmented load of a row-major host matrix (see ebic_load_matrix): kLoadSegments segments

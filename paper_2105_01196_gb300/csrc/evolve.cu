@@ -2106,9 +2106,11 @@ int ensure_tabu(ebic_ctx *ctx, GenState *g, int64_t need) {
 }
 
 // Pair limit of the evaluation inside the evolve kernel (0: none): the caller's, else the
-// autotuner's, else the largest pair count whose staged units (pairs x directions x passes of 128 words) stay within
-// kFuseDefaultUnits, so that evaluating a child keeps its warp about as long as building it
-// did.  Only the bitmap form has it.
+// autotuner's, else none for the block-per-slot form (whose launch lasts one slot's latency,
+// which an evaluation would lengthen: measured slower on 10,000 x 100, P = 800) and, for the
+// warp-per-slot form, the largest pair count whose staged units (pairs x directions x passes of
+// 128 words) stay within kFuseDefaultUnits, so that evaluating a child keeps its warp about as
+// long as building it did.  Only the bitmap form has it.
 constexpr int64_t kFuseDefaultUnits = 64;
 
 int fuse_limit(const ebic_ctx *ctx, int mode, const ebic_params *p) {
@@ -2117,6 +2119,9 @@ int fuse_limit(const ebic_ctx *ctx, int mode, const ebic_params *p) {
   // (the autotuner's limit, measured in the loop with this form)
   if (ctx->tuned && ctx->tuned_mode == mode && ctx->fuse_loop != 0)
     return ctx->fuse_loop > 0 ? ctx->fuse_loop : 0;
+  int G = 1;
+  while (G < p->max_attempts) G <<= 1;
+  if ((int64_t)p->pop_size * G <= (int64_t)ctx->num_sms * kEvolveResidentWarps) return 0;
   const int64_t per_pair = (ctx->Wst + 127) / 128 * (p->neg_trends ? 2 : 1);
   return (int)std::min<int64_t>(EBIC_MAX_LEN - 1, kFuseDefaultUnits / per_pair);
 }

@@ -350,6 +350,11 @@ inline uint64_t tabu_capacity(int64_t keys) {
 }
 inline uint64_t dedup_capacity(int64_t P) { return pow2_at_least((uint64_t)(kTableSpread * P)); }
 
+// Returns a context's matrix- and run-sized buffers (keys, staging, codes, planes, bitmap, pair
+// counts, evaluation scratch, the generation loop's state) to the pool, stream-ordered, and
+// forgets the matrix; the context itself (stream, events, settings) stays usable.
+void ctx_release_buffers(ebic_ctx *ctx);
+
 // evolve.cu
 void gen_state_free(struct GenState *g);
 // Ends the current run: the state is cleared before the next run, buffers and graphs stay.

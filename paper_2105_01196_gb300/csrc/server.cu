@@ -3,10 +3,12 @@
 // Jobs (a matrix, parameters and a generation count) are queued as they arrive.  A scheduler
 // thread admits queued jobs in arrival order, letting a later job that fits go ahead of a head
 // job that does not (backfill), while the sum of the admitted jobs' device-memory footprints stays
-// within the budget and at most `max_running` jobs run.  Each admitted job runs on a worker thread
-// with its own context and stream, so the kernels of different jobs overlap on the device; its
-// matrix, bitmap and population stay resident until it ends.  Finishing a job frees its memory
-// and admits the next ones.  A job's results do not depend on the other jobs: each context's
+// within the budget and at most `max_running` jobs run.  Each admitted job runs on a worker thread;
+// a worker keeps one context (and stream) for all its jobs, so the kernels of different jobs
+// overlap on the device and no job pays for creating or destroying a context.  A job's matrix,
+// bitmap and population stay resident until it ends; finishing a job returns those buffers to
+// the library's memory pool (stream-ordered, no device-wide synchronisation) and admits the
+// next ones.  A worker whose job failed replaces its context.  A job's results do not depend on the other jobs: each context's
 // computation is deterministic and shares nothing with the others.
 #include <string.h>
 
@@ -100,9 +102,11 @@ void schedule_loop(ebic_server *srv) {
   }
 }
 
-void run_job(ebic_server *srv, Job &j) {
-  ebic_ctx *ctx = nullptr;
-  int st = ebic_create(&ctx, srv->device, nullptr);
+// Runs job j on the worker's context *pctx (created when null; destroyed and set to null when
+// the job fails, so that the next job starts from a fresh context).
+void run_job(ebic_server *srv, Job &j, ebic_ctx **pctx) {
+  int st = *pctx ? EBIC_OK : ebic_create(pctx, srv->device, nullptr);
+  ebic_ctx *ctx = *pctx;
   if (st == EBIC_OK) st = ebic_load_matrix(ctx, j.x.data(), j.rows, j.cols, j.layout);
   ebic_params p = j.p;
   p.mode = j.mode;
@@ -117,12 +121,24 @@ void run_job(ebic_server *srv, Job &j) {
     st = ebic_get_toplist(ctx, K, &j.n_top, j.top_cols.data(), j.top_lens.data(),
                           j.top_fit.data(), j.top_keys.data(), j.top_rows.data());
   }
-  if (ctx) ebic_destroy(ctx);
+  if (ctx && st == EBIC_OK) {
+    ctx_release_buffers(ctx);
+  } else if (ctx) {
+    ebic_destroy(ctx);
+    *pctx = nullptr;
+  }
   j.status = st;
   std::vector<float>().swap(j.x);  // the matrix is no longer needed
 }
 
 void worker_loop(ebic_server *srv) {
+  ebic_ctx *ctx = nullptr;  // the worker's context, kept across its jobs
+  struct Owner {
+    ebic_ctx **c;
+    ~Owner() {
+      if (*c) ebic_destroy(*c);
+    }
+  } owner{&ctx};
   for (;;) {
     std::shared_ptr<Job> j;
     {
@@ -133,7 +149,7 @@ void worker_loop(ebic_server *srv) {
       srv->admitted.pop_front();
       j->t_start = Clock::now();
     }
-    run_job(srv, *j);
+    run_job(srv, *j, &ctx);
     {
       std::lock_guard<std::mutex> lk(srv->mu);
       j->t_end = Clock::now();
