@@ -3,7 +3,7 @@
 // chromosome hashes, tabu-hit termination; parameters of Sec. 2.4's last paragraph).
 //
 // One generation is three kernels, captured as CUDA graphs (one per buffer parity, and one of
-// eight consecutive generations per starting parity) and replayed:
+// sixteen consecutive generations per starting parity) and replayed:
 //   k_evolve    one block per slot, one warp per tabu attempt: elites from the top list (step
 //               4), otherwise penalised tournament, optional one-point crossover and one
 //               mutation, tabu probe; the lowest attempt that misses the tabu list wins (step 5).
@@ -2185,7 +2185,7 @@ int capture_graph(ebic_ctx *ctx, GenState *g, int parity, int profiled) {
 }
 
 constexpr int kKernelsPerGeneration = 3;
-constexpr int kGraphGenerations = 8;  // even: a chunk ends on the parity it started with
+constexpr int kGraphGenerations = 16;  // even: a chunk ends on the parity it started with
 
 // The graph of kGraphGenerations generations starting at `parity` (no event marks).
 int capture_multi(ebic_ctx *ctx, GenState *g, int parity) {

@@ -151,7 +151,7 @@ def test_generations_over_a_bitmap_larger_than_l2(ebic, ns, ipw):
     """The generation loop over a 243 MB pair bitmap (larger than the device's L2, so the bitmap
     kernel stages its pair words in shared memory) on a tie-heavy matrix, with ties counting for
     both directions or not, one individual per work item or groups of 3 or 4: generation by
-    generation, then eight generations in one graph replay, against the oracle."""
+    generation, then sixteen generations in one graph replay, against the oracle."""
     g = np.random.default_rng(21 + ns)
     x = g.integers(-3, 4, size=(4500, 650)).astype(np.float32)
     gp, op = both_params(ebic, mode=2, non_strict=ns, max_len=20, init_max_len=20, pop_size=96,
@@ -168,10 +168,10 @@ def test_generations_over_a_bitmap_larger_than_l2(ebic, ns, ipw):
             assert rep.gens_done == gen == st.gen
             assert rep.n_evaluated == st.n_evaluated
             assert_same_state(ctx, st, gp)
-        rep = ctx.run_generations(gp, 8)
-        for _ in range(8):
+        rep = ctx.run_generations(gp, 16)
+        for _ in range(16):
             assert oebic.next_generation(x, st, op)
-        assert rep.gens_done == st.gen == 11
+        assert rep.gens_done == st.gen == 19
         assert rep.n_evaluated == st.n_evaluated
         assert_same_state(ctx, st, gp)
 
@@ -264,7 +264,7 @@ def test_long_chromosomes_generation_by_generation(ebic, mode, use_graph, ns, ra
     bitmap, direct, staged and AUTO forms; graph-replayed and eager loops; strict and
     ties-for-both pair tests.  Low ratios with the column exponent capped at 16 make long
     chromosomes score best, so the population stays above 32 columns; the exact ratio lets it
-    shrink after the first generations.  Ten generations one by one, then eight in one call
+    shrink after the first generations.  Ten generations one by one, then sixteen in one call
     (one graph replay), each against the oracle."""
     x = long_matrix(31 + init_lo + ns, ties=bool(ns))
     gp, op = both_params(ebic, mode=mode, use_graph=use_graph, non_strict=ns,
@@ -286,10 +286,10 @@ def test_long_chromosomes_generation_by_generation(ebic, mode, use_graph, ns, ra
             assert rep.n_evaluated == st.n_evaluated
             assert_same_state(ctx, st, gp)
             longest.append(max(len(c) for c in st.pop))
-        rep = ctx.run_generations(gp, 8)
-        for _ in range(8):
+        rep = ctx.run_generations(gp, 16)
+        for _ in range(16):
             assert oebic.next_generation(x, st, op)
-        assert rep.gens_done == st.gen == 18
+        assert rep.gens_done == st.gen == 26
         assert rep.n_evaluated == st.n_evaluated
         assert_same_state(ctx, st, gp)
     assert longest[0] > 32
@@ -337,7 +337,7 @@ def test_evaluation_inside_the_evolve_kernel(ebic, fuse, neg, ns, ratio, pop, at
     fuse_pairs pairs are evaluated by the warp that built them, inside the evolve kernel (one
     block per slot for 64 and 96 slots, a warp per slot for 1,300), the rest by the evaluation
     launch over the list of slots left to it; -1 turns it off.  Ratio 1 with chromosomes of up to
-    64 columns puts pairs 32-62 in the fused path.  Generation by generation, then eight in one
+    64 columns puts pairs 32-62 in the fused path.  Generation by generation, then sixteen in one
     graph replay, against the oracle, with the number of fused evaluations checked."""
     x = long_matrix(53, ties=bool(ns)) if long_ else tiny_matrix()
     kw = (dict(max_len=64, init_min_len=40, init_max_len=64, col_cap=16) if long_ else {})
@@ -358,10 +358,10 @@ def test_evaluation_inside_the_evolve_kernel(ebic, fuse, neg, ns, ratio, pop, at
             assert rep.gens_done == g == st.gen
             assert rep.n_evaluated == st.n_evaluated
             assert_same_state(ctx, st, gp)
-        rep = ctx.run_generations(gp, 8)
-        for _ in range(8):
+        rep = ctx.run_generations(gp, 16)
+        for _ in range(16):
             assert oebic.next_generation(x, st, op)
-        assert rep.gens_done == st.gen == 13
+        assert rep.gens_done == st.gen == 21
         assert rep.n_evaluated == st.n_evaluated
         assert_same_state(ctx, st, gp)
         fused = rep.n_fused
