@@ -233,10 +233,13 @@ __device__ __forceinline__ void cp_wait_bm() {
 // planes are stored [C][Wst][NBP] (NBP = NB rounded up to 4): a column's chunk of 32 words is
 // one contiguous span, copied as is, and each lane reads its word's planes as NBP / 4 16-byte
 // vectors (lanes 48 or 16 bytes apart: no bank conflicts; 32 bytes apart at NBP = 8: two-way).
-// With `cnt` (zeroed beforehand), the pair counts are accumulated too: for a < b, cnt[a * C + b]
-// holds the rows of G[a][b] (its popcount) in its low 32 bits and those of G[b][a] in its high
-// 32 bits.  Each warp adds its 32 words' counts of a pair by one warp sum (the two directions'
+// The pair counts are accumulated too (cnt, zeroed beforehand): for a < b, cnt[a * C + b] holds
+// the rows of G[a][b] (its popcount) in its low 32 bits and those of G[b][a] in its high 32
+// bits.  Each warp adds its 32 words' counts of a pair by one warp sum (the two directions'
 // counts packed in 16-bit halves, at most 1,024 each) and one 64-bit atomic.
+// In the last row chunk, lanes past Wst hold zero planes for a (not loaded) and for b (their
+// staged words are zeroed once and never copied): every such row compares equal, so their words
+// are zero (and not stored) and add nothing to the sums.
 template <int NB>
 __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *__restrict__ planes,
                                                              int32_t C, int64_t Wst,
@@ -274,8 +277,7 @@ __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *
   const int64_t row = (int64_t)C * Wst;  // words between G[a][.] and G[a + 1][.]
   // this warp's 32 words' counts of G[a][b] (gt) and G[b][a] (lt), packed, summed over the lanes
   auto warp_counts = [&](uint32_t gt, uint32_t lt) -> unsigned {
-    return __reduce_add_sync(0xFFFFFFFFu, w_ok ? (unsigned)__popc(gt) | ((unsigned)__popc(lt) << 16)
-                                               : 0u);
+    return __reduce_add_sync(0xFFFFFFFFu, (unsigned)__popc(gt) + ((unsigned)__popc(lt) << 16));
   };
   auto add_counts = [&](int a, int b, unsigned n) {  // (a < b)
     if (n)
@@ -299,10 +301,8 @@ __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *
             __stcs(G + (int64_t)a * row + (int64_t)b * Wst + w, gt);
             __stcs(G + (int64_t)b * row + (int64_t)a * Wst + w, lt);
           }
-          if (cnt) {
-            const unsigned n = warp_counts(gt, lt);
-            if (lane == 0) add_counts(a, b, n);
-          }
+          const unsigned n = warp_counts(gt, lt);
+          if (lane == 0) add_counts(a, b, n);
         }
       }
     }
@@ -311,7 +311,14 @@ __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *
   // staging: batch t holds b = b_first + t kBB + bb; copy j of a batch is 16-byte part j % span
   // of column bb = j / span (span: the chunk's words x NBP / 4; Wst % 4 == 0)
   const int n_batches = (b_hi - b_first + kBB - 1) / kBB;
-  const int span = (int)(Wst - w0 >= 32 ? 32 : Wst - w0) * NBP / 4;
+  const int valid = (int)(Wst - w0 >= 32 ? 32 : Wst - w0);  // words of this chunk
+  const int span = valid * NBP / 4;
+  if (valid < 32) {  // the tail lanes' staged words, in both buffers
+    for (int j = threadIdx.x; j < 2 * kBB * (32 - valid) * NBP; j += blockDim.x) {
+      const int k = j % NBP, l = valid + (j / NBP) % (32 - valid), bb = j / (NBP * (32 - valid));
+      (&s_b[0][0][0][0])[((int64_t)bb * 32 + l) * NBP + k] = 0u;
+    }
+  }
   auto issue = [&](int t) {
     const int bs = b_first + t * kBB, nbb = min(kBB, b_hi - bs);
     for (int j = threadIdx.x; j < nbb * span; j += blockDim.x) {
@@ -335,40 +342,41 @@ __global__ void __launch_bounds__(256, 2) k_build_bitmap_planes(const uint32_t *
     }
     __syncthreads();  // batch t is in shared memory for every warp
     const int bs = b_first + t * kBB, nbb = min(kBB, b_hi - bs);
-    if (active) {
-      uint32_t *g_ab = G + (int64_t)a0 * row + (int64_t)bs * Wst + w;
-      uint32_t *g_ba = G + (int64_t)bs * row + (int64_t)a0 * Wst + w;
+    const int bb0 = max(0, a0 + kPA - bs);  // the first b after the warp's own columns
+    if (active && bb0 < nbb) {
+      uint32_t *g_ab = G + (int64_t)a0 * row + (int64_t)(bs + bb0) * Wst + w;
+      uint32_t *g_ba = G + (int64_t)(bs + bb0) * row + (int64_t)a0 * Wst + w;
       // (b columns are independent: unrolled, their comparator chains interleave; the build at
-      // 60,000 x 1,000 took 2.33 ms unrolled 1 time, 2.25 ms 2, 2.22 ms 4, 2.18 ms 8, 2.21 ms 16)
-#pragma unroll 8
-      for (int bb = 0; bb < nbb; ++bb) {
-        if (bs + bb >= a0 + kPA) {  // (b after the warp's own columns)
-          uint32_t B[NB];
+      // 60,000 x 1,000 took 2.00 ms unrolled 4 times, 2.21-2.22 ms 1 or 2 times, 2.21 ms 8 times,
+      // 2.17 ms 16 times; with a test of b against the warp's columns inside the loop, a select of
+      // the tail lanes' counts and the counts optional, 2.33 ms rolled and 2.18 ms at best)
+#pragma unroll 4
+      for (int bb = bb0; bb < nbb; ++bb) {
+        uint32_t B[NB];
 #pragma unroll
-          for (int q = 0; q < NBP / 4; ++q) {
-            const uint4 v = *reinterpret_cast<const uint4 *>(&s_b[t & 1][bb][lane][4 * q]);
-            const uint32_t e[4] = {v.x, v.y, v.z, v.w};
+        for (int q = 0; q < NBP / 4; ++q) {
+          const uint4 v = *reinterpret_cast<const uint4 *>(&s_b[t & 1][bb][lane][4 * q]);
+          const uint32_t e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-              if (4 * q + k < NB) B[4 * q + k] = e[k];
+          for (int k = 0; k < 4; ++k)
+            if (4 * q + k < NB) B[4 * q + k] = e[k];
+        }
+        unsigned n[kPA];
+#pragma unroll
+        for (int i = 0; i < kPA; ++i) {
+          uint32_t gt, lt;
+          plane_compare<NB>(A[i], B, gt, lt);
+          if (w_ok) {
+            __stcs(g_ab + (uint32_t)i * row32, gt);
+            __stcs(g_ba + (uint32_t)i * wst32, lt);
           }
-          unsigned n[kPA];
+          n[i] = warp_counts(gt, lt);
+        }
+        if (lane < kPA) {  // lane i adds pair (a0 + i, b)'s counts
+          unsigned mine = n[0];
 #pragma unroll
-          for (int i = 0; i < kPA; ++i) {
-            uint32_t gt, lt;
-            plane_compare<NB>(A[i], B, gt, lt);
-            if (w_ok) {
-              __stcs(g_ab + (uint32_t)i * row32, gt);
-              __stcs(g_ba + (uint32_t)i * wst32, lt);
-            }
-            n[i] = cnt ? warp_counts(gt, lt) : 0u;
-          }
-          if (cnt && lane < kPA) {  // lane i adds pair (a0 + i, b)'s counts
-            unsigned mine = n[0];
-#pragma unroll
-            for (int i = 1; i < kPA; ++i) mine = lane == i ? n[i] : mine;
-            add_counts(a0 + lane, bs + bb, mine);
-          }
+          for (int i = 1; i < kPA; ++i) mine = lane == i ? n[i] : mine;
+          add_counts(a0 + lane, bs + bb, mine);
         }
         g_ab += Wst;
         g_ba += row;
@@ -429,6 +437,7 @@ cudaError_t launch_build_bitmap_planes(const uint32_t *planes, int nb, int32_t C
   if (chunk0 < 0 || chunk0 >= chunk1) return chunk0 == chunk1 ? cudaSuccess : cudaErrorInvalidValue;
   const int64_t n_chunks = chunk1 - chunk0;
   const int n_ablk = (C + 8 * kPA - 1) / (8 * kPA);
+  if (!cnt) return cudaErrorInvalidValue;  // (the pair counts are always accumulated)
   // (the kernel offsets rows of the bitmap by up to 3 * C * Wst words in 32 bits)
   if (n_ablk > kMaxABlocks || n_chunks > 0x7FFFFFFF || 4 * (int64_t)C * Wst > 0xFFFFFFFFll)
     return cudaErrorInvalidValue;
