@@ -471,14 +471,12 @@ int load_matrix_segmented(ebic_ctx *ctx, const float *x, int64_t rows, int32_t c
                                                 Wst, ctx->num_sms, r0, r1, s));
     prof_count(ctx, -1, 1);
     prof_count(ctx, EBIC_KERNEL_RANK_CODES, 1);
-    if (bitmap) {
-      EBIC_CHECK_CUDA(ctx, launch_build_bitmap_planes(
-                               ctx->planes.as<uint32_t>(), nb, cols, Wst,
-                               ctx->bitmap.as<uint32_t>(),
-                               ctx->pair_cnt.as<unsigned long long>(), s, r0 / 1024,
-                               r1 == R_pad ? -1 : r1 / 1024));
-      prof_count(ctx, EBIC_KERNEL_BITMAP_BUILD, 1);
-    }
+  }
+  if (bitmap) {
+    EBIC_CHECK_CUDA(ctx, launch_build_bitmap_planes(ctx->planes.as<uint32_t>(), nb, cols, Wst,
+                                                    ctx->bitmap.as<uint32_t>(),
+                                                    ctx->pair_cnt.as<unsigned long long>(), s));
+    prof_count(ctx, EBIC_KERNEL_BITMAP_BUILD, 1);
   }
   int32_t herr = 0;
   EBIC_CHECK_CUDA(ctx, cudaMemcpyAsync(&herr, ctx->d_err.p, sizeof(int32_t),
@@ -533,8 +531,8 @@ int ebic_load_matrix(ebic_ctx *ctx, const float *x, int64_t rows, int32_t cols, 
   const int64_t R_pad = round_up(rows, 128);
   EBIC_CHECK_CUDA(ctx, ctx->keys.ensure((size_t)cols * R_pad * sizeof(uint32_t), ctx->stream));
   // A host matrix of a shape the autotuner measured, in a form that reads rank codes: the copy
-  // goes in segments, and each segment's keys, rank codes, bit planes and (bitmap form) pair
-  // words are built while the next segment is copied.
+  // goes in segments, and each segment's keys, rank codes and bit planes are built while the
+  // next segment is copied; the pair words (bitmap form) follow in one launch over every row.
   if (!ebic_is_device_ptr(x) && layout == EBIC_LAYOUT_ROW_MAJOR && code_bytes_for(cols) &&
       ctx->tuned && ctx->tuned_mode != EBIC_MODE_STAGED && !ctx->prof)
     return load_matrix_segmented(ctx, x, rows, cols, R_pad);

@@ -65,10 +65,11 @@ def test_autotuned_generations_match_oracle():
 @pytest.mark.parametrize("R,C,seed", [(40000, 48, 3), (20000, 300, 4)])
 def test_tuned_host_matrix_loads_in_segments(R, C, seed):
     """A host matrix of a shape the autotuner measured is copied in segments, each segment's
-    keys, rank codes, bit planes and (bitmap form) pair words built while the next one is
-    copied: the load launches the rank-code kernel once per segment, and the results equal the
-    oracle's (counts and fitness of a population; with the bitmap form, the pair words of a
-    sample of pairs and the pair counts), with rows past the last segment boundary."""
+    keys, rank codes and bit planes built while the next one is copied, then (bitmap form) the
+    pair words and counts in one launch: the load launches the rank-code kernel once per segment
+    and the bitmap build once, and the results equal the oracle's (counts and fitness of a
+    population; with the bitmap form, the pair words of a sample of pairs and the pair counts),
+    with rows past the last segment boundary."""
     from oracle.bitmap import pair_words
     from paper_2105_01196_gb300 import ebic
     g = np.random.default_rng(seed)
@@ -83,10 +84,13 @@ def test_tuned_host_matrix_loads_in_segments(R, C, seed):
         ctx.load_matrix(x.copy())
         tune = ctx.autotune(ci, off, p, 100)
         before = ctx.profile_read(ebic.KERNEL_RANK_CODES)["launches"]
+        built = ctx.profile_read(ebic.KERNEL_BITMAP_BUILD)["launches"]
         ctx.load_matrix(x)                                # (host, same shape: segmented)
         r_pad = (R + 127) // 128 * 128
         seg = max(8192, -(-((r_pad + 3) // 4) // 8192) * 8192)     # (four segments)
         assert ctx.profile_read(ebic.KERNEL_RANK_CODES)["launches"] - before == -(-r_pad // seg)
+        assert ctx.profile_read(ebic.KERNEL_BITMAP_BUILD)["launches"] - built == \
+            (1 if tune["mode"] == ebic.MODE_BITMAP else 0)
         got = ctx.eval_population(ci, off, p)
         if tune["mode"] == ebic.MODE_BITMAP:
             wst = r_pad // 32
