@@ -145,18 +145,23 @@ def test_device_pointers_and_col_major(ebic, torch_cuda):
                 assert_parity(got, want)
 
 
+@pytest.mark.parametrize("values", ["ties", "distinct"])
 @pytest.mark.parametrize("R,C", [(77, 2), (300, 3), (130, 5), (1030, 9), (200, 16),
                                  (64, 17), (40, 33), (33, 64), (257, 65), (129, 128),
                                  (100, 129), (97, 256), (70, 257), (35, 512), (66, 513),
                                  (45, 1000), (33, 1024), (40, 1025)])
-def test_bitmap_matches_oracle_definition(ebic, R, C):
-    """Every pair word against the oracle's definition: bit planes of 1 to 10 bits (built from
-    the rank codes up to 1,024 columns) and the order-key build beyond; ties, signed zeros,
-    subnormals and extreme magnitudes; rows not a multiple of 32.  Up to 129 columns every
-    pair is compared, beyond that a sample that includes the first, last and diagonal pairs."""
+def test_bitmap_matches_oracle_definition(ebic, R, C, values):
+    """Every pair word against the oracle's definition: from the bit planes of the rank codes up
+    to 1,024 columns (1 to 10 planes) and the order-key build beyond; values -3..3 (many ties)
+    or distinct ones, with signed zeros, subnormals and extreme magnitudes; rows not a multiple
+    of 32.  Up to 129 columns every pair is compared, beyond that a sample that includes the
+    first, last and diagonal pairs."""
     from oracle.bitmap import pair_words
-    g = np.random.default_rng(11 + R * 3 + C)
-    x = g.integers(-3, 4, size=(R, C)).astype(np.float32)
+    g = np.random.default_rng(11 + R * 3 + C + (values == "distinct"))
+    if values == "ties":
+        x = g.integers(-3, 4, size=(R, C)).astype(np.float32)
+    else:
+        x = g.standard_normal((R, C)).astype(np.float32)
     x[g.random((R, C)) < 0.05] = -0.0
     x[g.random((R, C)) < 0.02] = np.float32(1e-45)
     x[g.random((R, C)) < 0.02] = -np.float32(3e-42)
@@ -179,6 +184,39 @@ def test_bitmap_matches_oracle_definition(ebic, R, C):
     pairs |= {(int(a), int(b)) for a, b in g.integers(0, C, size=(300, 2))}
     for a, b in sorted(pairs):
         assert np.array_equal(got[a, b, :W], pair_words(x, a, b)), (a, b)
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 4, 5, 9, 17, 33, 129, 257, 513, 1000])
+def test_bitmap_rows_of_few_distinct_values(ebic, D):
+    """Rows that hold at most D distinct values (one row all D of them; D at the bit boundaries
+    of D - 1, a constant matrix at D = 1): pair words of a sample of pairs and their pair counts
+    against the oracle."""
+    from oracle.bitmap import pair_words
+    g = np.random.default_rng(900 + D)
+    C = max(D + 3, 4) if D < 1000 else 1000
+    R = 300
+    levels = np.sort(g.standard_normal(D)).astype(np.float32)
+    x = levels[g.integers(0, D, size=(R, C))]
+    x[0, :D] = levels[g.permutation(D)]  # (row 0 holds every level)
+    W = (R + 31) // 32
+    with ebic.Context(0) as ctx:
+        ctx.load_matrix(x)
+        ctx.build_bitmap()
+        wst = ((R + 127) // 128) * 4
+        out = np.zeros(C * C * wst, np.uint32)
+        ctx.copy_bitmap(out)
+        cnt = np.zeros(C * C, np.uint64)
+        ctx.copy_pair_counts(cnt)
+    got = out.reshape(C, C, wst)
+    cnt = cnt.reshape(C, C)
+    popc = lambda w: int(np.unpackbits(np.asarray(w, np.uint32).view(np.uint8)).sum())
+    pairs = {(0, 1), (0, C - 1), (C - 2, C - 1)}
+    pairs |= {tuple(sorted((int(a), int(b)))) for a, b in g.integers(0, C, size=(200, 2)) if a != b}
+    for a, b in sorted(pairs):
+        wab, wba = pair_words(x, a, b), pair_words(x, b, a)
+        assert np.array_equal(got[a, b, :W], wab) and np.array_equal(got[b, a, :W], wba), (a, b)
+        assert int(cnt[a, b]) == popc(wab) | (popc(wba) << 32), (a, b)
+    assert not got[:, :, W:].any()
 
 
 @pytest.mark.parametrize("R,C", [(1, 2), (33, 7), (300, 129), (129, 200), (40, 1000)])
