@@ -2184,7 +2184,6 @@ int capture_graph(ebic_ctx *ctx, GenState *g, int parity, int profiled) {
   return EBIC_OK;
 }
 
-constexpr int kKernelsPerGeneration = 3;
 constexpr int kGraphGenerations = 16;  // even: a chunk ends on the parity it started with
 
 // The graph of kGraphGenerations generations starting at `parity` (no event marks).
