@@ -10,7 +10,7 @@ the chromosome / trend definition of Sec. 2.3 ("EBIC" paragraph), the nine-step 
 Sec. 2.4 ("EBIC.jl"), the evolutionary strategies of Sec. 2.3 (elitism, penalised tournament,
 tabu list) and the parameters of Sec. 2.4 (negative trends, approximate-trend threshold, allowed
 overlap, iterations, number of biclusters).  Where the paper is silent the module that implements
-the step states the reading it takes; the same readings are listed in the design notes.
+the step states the reading it takes.
 
 Modules
   philox   Philox4x32-10 counter-based generator (Salmon et al., SC'11) and the word stream.

@@ -13,7 +13,7 @@ Steps as the paper lists them:
   8. the new population replaces the old one; back to 4;
   9. the top rank list's chromosomes are scored once more and their accepted rows are returned.
 
-Readings where the paper is silent (each is stated again in the design notes):
+Readings where the paper is silent:
   * Random words come from the Philox stream (generation g, slot s, attempt a), see ``philox``.
   * Initialisation (g = 0): length = init_min_len + below(init_max_len - init_min_len + 1), then
     columns drawn uniformly, a column already present is redrawn (at most 64 draws per column;

@@ -2,7 +2,7 @@
 allowed overlap, number of iterations and of biclusters; Table 1: ``-n 20000``).
 
 The paper names these parameters but gives no defaults other than the iteration cap.  The defaults
-below are readings, documented with the design notes:
+below are readings of the paper, one per parameter:
   ratio_num/ratio_den  approximate-trend ratio as a rational; 1/1 is the exact trend.
   min_rows             fewer accepted rows than this gives fitness 0.
   col_cap              fitness column exponent cap.

@@ -1,6 +1,5 @@
 """The seeded input recipe (no GPU): workload shapes, planted structure, population ranges and
-determinism are what the design notes state, so the tests and the benchmark measure the
-documented workloads."""
+determinism, so that the tests and the benchmark measure the workloads the recipe defines."""
 
 import numpy as np
 import pytest
