@@ -533,7 +533,8 @@ __device__ void w_make_child(const GenArgs &ga, const Buf &pb, int g, int s, int
 // its bit, the negative trend when every reversed pair's word has it (ties counting both ways:
 // the complements of the opposite words, pad rows masked).  One unit is one pair row's 128 words
 // of one pass (16 bytes per lane); units are copied asynchronously into the warp's shared region,
-// two groups of kFuseGroup in flight, and each lane reads back only the bytes it copied.
+// two groups of kFuseGroup in flight (four with a region borrowed from a warp of the block that
+// has no slot left), and each lane reads back only the bytes it copied.
 constexpr int kFuseGroup = 4;               // units per copy group
 constexpr int kFuseSlots = 2 * kFuseGroup;  // units staged per warp
 constexpr int kFuseWords = 128;             // words of one unit
@@ -594,16 +595,22 @@ __device__ __forceinline__ void fuse_pass_counts(const GenArgs &ga, bool neg, bo
 // The exact test when a pass's UPP pair rows (pairs x directions) fit in one copy group: a group
 // holds kFuseGroup / UPP whole passes, and each lane keeps the UPP rows' addresses (src[u]: its
 // words of pass 0; unit u of a pass is pair u / 2's positive (even u) or negative row with
-// negative trends, else pair u's row).
-template <int UPP>
+// negative trends, else pair u's row).  NG groups are in flight: 2 in the warp's own region, 4
+// with a second region (stage2) borrowed from a warp of the block that has no slot left.
+template <int UPP, int NG>
 __device__ void w_eval_exact_small(const GenArgs &ga, const uint32_t *const (&src)[4],
-                                   uint32_t *stage, int lane, int &cp, int &cn, int &ca) {
+                                   uint32_t *stage, uint32_t *stage2, int lane, int &cp, int &cn,
+                                   int &ca) {
   constexpr int PPG = kFuseGroup / UPP;  // passes per group
   const bool neg = ga.neg != 0, ns = ga.ns != 0;
   const int64_t Wst = ga.Wst;
   const int passes = (int)((Wst + kFuseWords - 1) / kFuseWords);
   const int n_groups = (passes + PPG - 1) / PPG;
-  uint32_t *my = stage + lane * 4;  // (unit k of half b: my + (b * kFuseGroup + k) * kFuseWords)
+  // group gi's units: half gi & 1 of the own region, or of the borrowed one when gi % NG >= 2
+  auto unit = [&](int gi, int k) -> uint32_t * {
+    uint32_t *base = (NG > 2 && (gi % NG) >= 2) ? stage2 : stage;
+    return base + lane * 4 + ((gi & 1) * kFuseGroup + k) * kFuseWords;
+  };
   auto issue = [&](int gi) {
 #pragma unroll
     for (int pp = 0; pp < PPG; ++pp) {
@@ -611,17 +618,23 @@ __device__ void w_eval_exact_small(const GenArgs &ga, const uint32_t *const (&sr
       if (q < passes && (int64_t)q * kFuseWords + lane * 4 < Wst) {
 #pragma unroll
         for (int u = 0; u < UPP; ++u)
-          fuse_copy16(my + ((gi & 1) * kFuseGroup + pp * UPP + u) * kFuseWords,
-                      src[u] + (int64_t)q * kFuseWords);
+          fuse_copy16(unit(gi, pp * UPP + u), src[u] + (int64_t)q * kFuseWords);
       }
     }
     fuse_commit();
   };
   const uint4 ones = make_uint4(kFull, kFull, kFull, kFull);
-  issue(0);
-  if (n_groups > 1) issue(1);
+#pragma unroll
+  for (int gi = 0; gi < NG; ++gi)
+    if (gi < n_groups) issue(gi);
   for (int gi = 0; gi < n_groups; ++gi) {
-    if (gi + 1 < n_groups)
+    // (groups after gi still pending: at most NG - 1)
+    const int later = min(NG - 1, n_groups - 1 - gi);
+    if (NG > 2 && later >= 3)
+      fuse_wait<3>();
+    else if (NG > 2 && later == 2)
+      fuse_wait<2>();
+    else if (later >= 1)
       fuse_wait<1>();
     else
       fuse_wait<0>();
@@ -634,8 +647,7 @@ __device__ void w_eval_exact_small(const GenArgs &ga, const uint32_t *const (&sr
       if (act) {
 #pragma unroll
         for (int u = 0; u < UPP; ++u) {
-          uint4 v = *reinterpret_cast<const uint4 *>(
-              my + ((gi & 1) * kFuseGroup + pp * UPP + u) * kFuseWords);
+          uint4 v = *reinterpret_cast<const uint4 *>(unit(gi, pp * UPP + u));
           if (ns) v = make_uint4(~v.x, ~v.y, ~v.z, ~v.w);
           if (neg && (u & 1))
             an = fuse_and(an, v);
@@ -645,15 +657,16 @@ __device__ void w_eval_exact_small(const GenArgs &ga, const uint32_t *const (&sr
       }
       if (q < passes) fuse_pass_counts(ga, neg, ns, act, w, ap, an, cp, cn, ca);
     }
-    if (gi + 2 < n_groups) issue(gi + 2);
+    if (gi + NG < n_groups) issue(gi + NG);
   }
 }
 
 // Row counts (positive trend, negative trend, either) of the exact test of c[0 .. L-1] (L >= 2),
 // in every lane.  stage: the warp's kFuseSlots * kFuseWords words of shared memory (16-byte
-// aligned), free for this call.
+// aligned), free for this call; stage2: a second such region (borrowed), or null.  Only passes of
+// at most kFuseGroup pair rows use the second region.
 __device__ void w_eval_exact(const GenArgs &ga, const int32_t *c, int L, uint32_t *stage,
-                             int lane, int &rp, int &rn, int &ra) {
+                             uint32_t *stage2, int lane, int &rp, int &rn, int &ra) {
   const int np = L - 1;
   const bool neg = ga.neg != 0, ns = ga.ns != 0;
   const int upp = neg ? 2 * np : np;  // units per pass: pair j's positive (then negative) row
@@ -673,11 +686,20 @@ __device__ void w_eval_exact(const GenArgs &ga, const int32_t *c, int L, uint32_
     }
     int cp = 0, cn = 0, ca = 0;
     __syncwarp();  // every lane's earlier use of the region is done
-    switch (upp) {
-      case 1: w_eval_exact_small<1>(ga, src, stage, lane, cp, cn, ca); break;
-      case 2: w_eval_exact_small<2>(ga, src, stage, lane, cp, cn, ca); break;
-      case 3: w_eval_exact_small<3>(ga, src, stage, lane, cp, cn, ca); break;
-      default: w_eval_exact_small<4>(ga, src, stage, lane, cp, cn, ca); break;
+    if (stage2) {
+      switch (upp) {
+        case 1: w_eval_exact_small<1, 4>(ga, src, stage, stage2, lane, cp, cn, ca); break;
+        case 2: w_eval_exact_small<2, 4>(ga, src, stage, stage2, lane, cp, cn, ca); break;
+        case 3: w_eval_exact_small<3, 4>(ga, src, stage, stage2, lane, cp, cn, ca); break;
+        default: w_eval_exact_small<4, 4>(ga, src, stage, stage2, lane, cp, cn, ca); break;
+      }
+    } else {
+      switch (upp) {
+        case 1: w_eval_exact_small<1, 2>(ga, src, stage, stage, lane, cp, cn, ca); break;
+        case 2: w_eval_exact_small<2, 2>(ga, src, stage, stage, lane, cp, cn, ca); break;
+        case 3: w_eval_exact_small<3, 2>(ga, src, stage, stage, lane, cp, cn, ca); break;
+        default: w_eval_exact_small<4, 2>(ga, src, stage, stage, lane, cp, cn, ca); break;
+      }
     }
     rp = __reduce_add_sync(kFull, cp);
     rn = __reduce_add_sync(kFull, cn);
@@ -770,12 +792,27 @@ __device__ void w_eval_exact(const GenArgs &ga, const int32_t *c, int L, uint32_
   ra = __reduce_add_sync(kFull, ca);
 }
 
+// Per-warp shared memory of k_evolve, in ints: the child (kS + 1 used), then 8 tournament scratch
+// rows and the two parents; once the child is final, the region after it stages the pair words
+// of its evaluation (kFuseSlots units).  Every part starts on a 16-byte boundary (the scratch
+// rows are written with 16-byte stores, the staged units by 16-byte copies), and the total is a
+// multiple of 16 bytes.
+constexpr int kEvoChild = 0, kEvoScratch = kS + 4, kEvoA = kEvoScratch + 8 * kS,
+              kEvoB = kEvoA + kS, kEvoStage = kEvoScratch;
+constexpr int kEvolveWarpInts =
+    kEvoScratch + (10 * kS > kFuseSlots * kFuseWords ? 10 * kS : kFuseSlots * kFuseWords);
+static_assert(kEvoScratch % 4 == 0, "scratch rows and staged units start on 16-byte boundaries");
+
 // The end of a live slot s's evolve step when fusion is on: the slot is evaluated here (its
 // counts stored, its key entered in generation g's duplicate table, as the evaluation launch
 // would) or listed for the evaluation launch.  Returns its tabu-flag value: 2 evaluated from the
 // pair words, 3 (a one-pair chromosome) from the pair-count table, 0 listed.
+// s_free (k_evolve_seq; null otherwise): bit w set while warp w of the block has no slot left,
+// its region (of kEvolveWarpInts ints from `regions`) then free; a pair-word evaluation borrows
+// one such region for two more copy groups in flight and gives it back at its end.
 __device__ int fuse_or_list(const GenArgs &ga, const int32_t *c, int L, uint64_t h, int s,
-                            int par, uint32_t *stage, int lane) {
+                            int par, uint32_t *stage, int lane, int32_t *regions,
+                            uint32_t *s_free) {
   if (fuse_child(ga, L)) {
     int rp = 0, rn = 0, ra = 0;
     const bool table = L == 2 && ga.pair_cnt != nullptr;
@@ -802,7 +839,25 @@ __device__ int fuse_or_list(const GenArgs &ga, const int32_t *c, int L, uint64_t
         }
       }
     } else {
-      w_eval_exact(ga, c, L, stage, lane, rp, rn, ra);
+      int lent = -1;  // the warp whose region is borrowed
+      if (s_free) {
+        if (lane == 0) {
+          const uint32_t m = *reinterpret_cast<volatile uint32_t *>(s_free);
+          if (m) {
+            const uint32_t bit = m & (0u - m);  // (the lowest free region)
+            if (atomicAnd(s_free, ~bit) & bit) lent = __ffs(bit) - 1;
+          }
+        }
+        lent = __shfl_sync(kFull, lent, 0);
+      }
+      uint32_t *stage2 =
+          lent >= 0 ? reinterpret_cast<uint32_t *>(regions + lent * kEvolveWarpInts + kEvoStage)
+                    : nullptr;
+      w_eval_exact(ga, c, L, stage, stage2, lane, rp, rn, ra);
+      if (lent >= 0) {
+        __syncwarp();  // (every lane's copies into it have landed and been read)
+        if (lane == 0) atomicOr(s_free, 1u << lent);
+      }
     }
     if (lane == 0) {
       ga.rows_scr[s] = rp;
@@ -852,16 +907,6 @@ __global__ void __launch_bounds__(kInitWarps * 32) k_init(GenArgs ga, Buf nb) {
 // lowest attempt whose key misses the tabu list wins, which is exactly the sequential retry
 // rule; when every attempt hits, the slot is dead and keeps the last attempt's child.
 constexpr int kMaxAttemptWarps = 16;
-// Per-warp shared memory of k_evolve, in ints: the child (kS + 1 used), then 8 tournament scratch
-// rows and the two parents; once the child is final, the region after it stages the pair words
-// of its evaluation (kFuseSlots units).  Every part starts on a 16-byte boundary (the scratch
-// rows are written with 16-byte stores, the staged units by 16-byte copies), and the total is a
-// multiple of 16 bytes.
-constexpr int kEvoChild = 0, kEvoScratch = kS + 4, kEvoA = kEvoScratch + 8 * kS,
-              kEvoB = kEvoA + kS, kEvoStage = kEvoScratch;
-constexpr int kEvolveWarpInts =
-    kEvoScratch + (10 * kS > kFuseSlots * kFuseWords ? 10 * kS : kFuseSlots * kFuseWords);
-static_assert(kEvoScratch % 4 == 0, "scratch rows and staged units start on 16-byte boundaries");
 // Matrices of up to this many columns have k_evolve's column-usage table in shared memory.
 constexpr int kUsageSmemMax = 4096;
 // Warps of k_evolve one SM holds at once (its registers allow 32).
@@ -937,7 +982,8 @@ __global__ void __launch_bounds__(kMaxAttemptWarps * 32) k_evolve(GenArgs ga, Bu
   out[lane + 32] = lane + 32 < L ? c[lane + 32] : 0;
   const int fused = (!dead && ga.fuse_np > 0)
                         ? fuse_or_list(ga, c, L, h, s, par,
-                                       reinterpret_cast<uint32_t *>(base + kEvoStage), lane)
+                                       reinterpret_cast<uint32_t *>(base + kEvoStage), lane,
+                                       nullptr, nullptr)
                         : 0;
   if (lane == 0) {
     nb.len[s] = L;
@@ -964,6 +1010,7 @@ constexpr int kSeqWarps = 8;
 __global__ void __launch_bounds__(kSeqWarps * 32, 4) k_evolve_seq(GenArgs ga, Buf pb, Buf nb,
                                                                int par) {
   extern __shared__ __align__(16) int32_t s_evo[];  // kEvolveWarpInts per warp, then usage
+  __shared__ uint32_t s_free;  // bit w: warp w has no slot left, its region free to borrow
   wait_prior_grid();
   const int stopped = ga.ctl->stopped, gen = ga.ctl->gen, n_top = ga.ctl->n_top;
   const int32_t *usage = ga.usage;
@@ -973,6 +1020,7 @@ __global__ void __launch_bounds__(kSeqWarps * 32, 4) k_evolve_seq(GenArgs ga, Bu
     usage = s_usage;
   }
   if (stopped) return;
+  if (threadIdx.x == 0) s_free = 0u;
   __syncthreads();  // (no block-wide operation follows)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int W = (int)gridDim.x * kSeqWarps;
@@ -1014,7 +1062,8 @@ __global__ void __launch_bounds__(kSeqWarps * 32, 4) k_evolve_seq(GenArgs ga, Bu
       out[lane + 32] = lane + 32 < L ? c[lane + 32] : 0;
       const int fused = (!dead && ga.fuse_np > 0)
                             ? fuse_or_list(ga, c, L, h, s, par,
-                                           reinterpret_cast<uint32_t *>(base + kEvoStage), lane)
+                                           reinterpret_cast<uint32_t *>(base + kEvoStage), lane,
+                                           s_evo, &s_free)
                             : 0;
       if (lane == 0) {
         nb.len[s] = L;
@@ -1029,6 +1078,9 @@ __global__ void __launch_bounds__(kSeqWarps * 32, 4) k_evolve_seq(GenArgs ga, Bu
     s = __shfl_sync(kFull, nx, 0) + W;
     __syncwarp();  // (the region's last reads are done before the next slot writes it)
   }
+  // no slot left: the warp's region can stage a sibling's evaluation
+  __syncwarp();
+  if (lane == 0) atomicOr(&s_free, 1u << w);
 }
 
 __device__ __forceinline__ bool key_before(uint64_t fa, uint64_t ha, uint64_t fb, uint64_t hb) {
