@@ -22,6 +22,7 @@ value is all ranks' evaluations divided by the slowest rank's time ("weak" scali
 """
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -152,10 +153,34 @@ def eval_kernel_name(mode, cols):
     return "k_eval_bitmap|k_eval_codes"
 
 
+# The source files each kernel with a committed traffic summary is compiled from.  A summary row
+# carries a hash of them as they were when the capture ran; a row whose hash differs from the
+# files now describes an earlier kernel and is not reported.
+KERNEL_SOURCES = {
+    "k_evolve_seq": ["evolve.cu", "tables.cuh"],
+    "k_eval_bitmap": ["eval.cu", "items.cuh", "trend.cuh", "tables.cuh"],
+}
+
+
+def kernel_source_hash(kernel):
+    """First 12 hex digits of the SHA-256 of the kernel's source files (name, NUL, contents, NUL
+    each, in the listed order), or None for a kernel without a list."""
+    files = KERNEL_SOURCES.get(kernel)
+    if not files:
+        return None
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2105_01196_gb300", "csrc", f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read() + b"\0")
+    return h.hexdigest()[:12]
+
+
 def ncu_traffic_entry(kernel, workload):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary
-    (profiles/traffic_<kernel>.txt: kernel, workload, bytes per launch, and the commit whose
-    kernel source the capture ran), and where it comes from; (None, None) when there is none."""
+    (profiles/traffic_<kernel>.txt: kernel, workload, bytes per launch, the commit whose kernel
+    source the capture ran, and the hash of that source), and where it comes from; (None, None)
+    when there is none, (None, why) when the row's source hash is missing or differs from the
+    kernel's source files now."""
     path = os.path.join(ROOT, "profiles", "traffic_" + kernel + ".txt")
     if not os.path.exists(path):
         return None, None
@@ -167,6 +192,9 @@ def ncu_traffic_entry(kernel, workload):
             src = f"profiles/traffic_{kernel}.txt ({workload}"
             src += f", ncu capture of the kernel source at commit {parts[3]})" if len(parts) > 3 \
                 else ")"
+            now = kernel_source_hash(kernel)
+            if len(parts) < 5 or now is None or parts[4] != now:
+                return None, src + ": stale, the kernel's source changed since the capture"
             return float(parts[2]), src
     return None, None
 

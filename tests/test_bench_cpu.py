@@ -13,18 +13,46 @@ from paper_2105_01196_gb300 import synth
 
 
 def test_ncu_traffic_reads_the_committed_summary():
-    d = bench.ncu_traffic("k_eval_bitmap", "default-loop")
-    t, src = bench.ncu_traffic_entry("k_eval_bitmap", "tieheavy-loop")
-    assert d is not None and t is not None
+    """Each committed row is read with its source; a row whose kernel source has changed since
+    its capture is reported stale (no traffic), a current one within the expected bounds."""
+    def fresh_or_stale(kernel, workload, lo, hi):
+        v, src = bench.ncu_traffic_entry(kernel, workload)
+        assert src is not None and f"traffic_{kernel}.txt" in src and "commit" in src
+        if v is None:
+            assert "stale" in src
+        else:
+            assert lo < v < hi
     # DRAM bytes per launch stay below the algorithmic bytes (part of the pair words hit L2;
     # the loop launches' mean includes the initial population's full sweep)
-    assert 0 < d < 5.39e6      # (the default bitmap stays in L2 between launches)
-    assert 3e7 < t < 1.3e8
-    e, src_e = bench.ncu_traffic_entry("k_evolve_seq", "tieheavy-loop")
-    assert 3e7 < e < 1.3e8 and "traffic_k_evolve_seq.txt" in src_e
-    assert "traffic_k_eval_bitmap.txt" in src and "commit" in src
+    fresh_or_stale("k_eval_bitmap", "default-loop", 0, 5.39e6)  # (the bitmap stays in L2)
+    fresh_or_stale("k_eval_bitmap", "tieheavy-loop", 3e7, 1.3e8)
+    fresh_or_stale("k_evolve_seq", "tieheavy-loop", 3e7, 1.3e8)
     assert bench.ncu_traffic("k_eval_bitmap", "no-such-workload") is None
     assert bench.ncu_traffic("no_such_kernel", "default") is None
+
+
+def test_ncu_traffic_row_goes_stale_with_its_kernel_source(tmp_path, monkeypatch):
+    """A summary row counts only while the hash of its kernel's source files matches: the same
+    files give the traffic, an edited file (or a row without a hash) gives none."""
+    csrc = tmp_path / "paper_2105_01196_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    for f in bench.KERNEL_SOURCES["k_evolve_seq"]:
+        with open(os.path.join(bench.ROOT, "paper_2105_01196_gb300", "csrc", f), "rb") as fh:
+            (csrc / f).write_bytes(fh.read())
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h = bench.kernel_source_hash("k_evolve_seq")
+    assert h is not None and len(h) == 12
+    row = tmp_path / "profiles" / "traffic_k_evolve_seq.txt"
+    row.write_text(f"# header\nk_evolve_seq w1 1000 abc1234 {h}\nk_evolve_seq w2 2000 abc1234\n")
+    assert bench.ncu_traffic_entry("k_evolve_seq", "w1")[0] == 1000.0
+    v, src = bench.ncu_traffic_entry("k_evolve_seq", "w2")
+    assert v is None and "stale" in src
+    with open(csrc / "evolve.cu", "ab") as fh:
+        fh.write(b"\n// edited\n")
+    assert bench.kernel_source_hash("k_evolve_seq") != h
+    v, src = bench.ncu_traffic_entry("k_evolve_seq", "w1")
+    assert v is None and "stale" in src and "abc1234" in src
 
 
 def test_eval_kernel_names():
