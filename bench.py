@@ -664,7 +664,10 @@ def workload_summary(job, stream, flush, steps, warmup, peak, peak_kind):
            "len": [w.len_lo, w.len_hi], "ratio": list(job.params_ratio()),
            "generations": job.gens, "eval_form": eval_kernel_name(job.used_mode, w.cols),
            "roofline": eval_roofline(stats, eval_kernel_name(job.used_mode, w.cols), peak,
-                                     peak_kind, None, None,
+                                     peak_kind,
+                                     *ncu_traffic_entry(eval_kernel_name(job.used_mode, w.cols),
+                                                        w.name + ("-loop" if job.gens > 0
+                                                                  else "")),
                                      "eval_loop" if job.gens > 0 else "eval"),
            "kernel_ms": {k: v["ms"] / steps for k, v in stats.items()}, **passes}
     if job.gens > 0:
